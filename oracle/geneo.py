@@ -1,0 +1,168 @@
+"""GenEO coarse space (Sec. 3.2 and Sec. 3.3.2-3.3.3).
+
+Per subdomain j (Sec. 3.3.2, eqm:matrixForm):
+    A_{Omega_j} p = lambda (X_j A_{Omega_j^o} X_j) p,  ||p||_2 = 1,
+with A_{Omega_j} the Neumann stiffness matrix assembled from the elements of
+Omega_j (no artificial Dirichlet conditions) and A_{Omega_j^o} the one
+assembled from the overlap elements only.  Global Dirichlet dofs keep an
+identity row in A_{Omega_j}; X_j is zero there so they carry infinite
+eigenvalues.
+
+The eigenpairs come from the shift-and-invert transformation with a small
+negative shift sigma (Sec. 3.3.2): with S = A - sigma B (SPD for sigma < 0),
+    B p = mu S p,  lambda = sigma + 1 / mu,
+so the smallest lambda are the largest mu.  Small problems use a dense
+symmetric-definite solver on (B, S); large ones use ARPACK's shift-invert
+mode on (A, B, sigma), the method the paper uses.
+
+Coarse basis (Sec. 3.3.2): Phi_{i(j,k)} = R_j^T X_j p_k^j; coarse matrix
+(Sec. 3.3.3) A_H = Phi^T A Phi with the fully assembled global A.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import fem
+
+DENSE_LIMIT = 3000
+INF_MU_RTOL = 1e-12    # mu below this times 1/|sigma| means lambda = infinity
+
+
+def local_node_map(p, nodes):
+    nn = (p["nx"] + 1) * (p["ny"] + 1) * (p["nz"] + 1)
+    m = -np.ones(nn, np.int64)
+    m[nodes] = np.arange(nodes.size)
+    return m
+
+
+def local_matrices(p, s):
+    """(A_{Omega_j}, A_{Omega_j^o}) on the dofs of all nodes of Omega_j.
+
+    Global Dirichlet dofs: A gets an identity row/column, A^o a zero one.
+    """
+    nm = local_node_map(p, s.neu_nodes)
+    nloc = s.neu_nodes.size
+    A = fem.assemble_stiffness(p, s.elems, nm, nloc)
+    if s.ovl_elems.size:
+        Ao = fem.assemble_stiffness(p, s.ovl_elems, nm, nloc)
+    else:
+        Ao = sp.csr_matrix((3 * nloc, 3 * nloc))
+    dmask = np.zeros(3 * ((p["nx"] + 1) * (p["ny"] + 1) * (p["nz"] + 1)), bool)
+    dmask[np.asarray(p["dirichlet_dofs"], np.int64)] = True
+    ld = np.nonzero(dmask[s.neu_dofs])[0]
+    zeros = np.zeros(ld.size)
+    A, _ = fem.apply_dirichlet(A, np.zeros(A.shape[0]), ld, zeros, diag=1.0)
+    Ao, _ = fem.apply_dirichlet(Ao, np.zeros(Ao.shape[0]), ld, zeros, diag=0.0)
+    return A, Ao
+
+
+def eigenpairs(A, B, nev, sigma, method="auto"):
+    """Smallest nev eigenpairs of A p = lambda B p (eqm:matrixForm), ||p|| = 1.
+
+    Returns (lam ascending, P with unit-2-norm columns).
+    """
+    n = A.shape[0]
+    nev = min(nev, n - 1)
+    if method == "auto":
+        method = "dense" if n <= DENSE_LIMIT else "arpack"
+    if method == "dense":
+        Ad = A.toarray()
+        Bd = B.toarray()
+        S = Ad - sigma * Bd
+        mu, V = sla.eigh(Bd, S)                     # ascending mu
+        mu = mu[::-1][:nev]
+        V = V[:, ::-1][:, :nev]
+        # mu -> 0 marks the infinite eigenvalues (null space of B)
+        finite = mu > INF_MU_RTOL / abs(sigma)
+        lam = np.full(mu.shape, np.inf)
+        lam[finite] = sigma + 1.0 / mu[finite]
+    elif method == "arpack":
+        lam, V = spla.eigsh(A.tocsc(), k=nev, M=B.tocsc(), sigma=sigma,
+                            which="LM", tol=1e-12, maxiter=20000)
+        order = np.argsort(lam)
+        lam, V = lam[order], V[:, order]
+    else:
+        raise ValueError(method)
+    V = V / np.linalg.norm(V, axis=0, keepdims=True)
+    return lam, V
+
+
+def threshold(p, s):
+    """Default eigenvalue threshold diam(Omega_j) / width(Omega_j^o) (Sec. 3.2).
+
+    Reading of the footnote for a 3D box: diam = circumradius of Omega_j's box
+    (half its diagonal); width = inradius of the overlap shell = O times the
+    smallest element edge in Omega_j (half the shell thickness 2 O h).
+    """
+    x, y, z = p["x"], p["y"], p["z"]
+    (x0, x1), (y0, y1), (z0, z1) = s.ebox
+    diam = 0.5 * np.sqrt((x[x1] - x[x0]) ** 2 + (y[y1] - y[y0]) ** 2
+                         + (z[z1] - z[z0]) ** 2)
+    hmin = min(np.min(np.diff(x[x0:x1 + 1])), np.min(np.diff(y[y0:y1 + 1])),
+               np.min(np.diff(z[z0:z1 + 1])))
+    O = p["partition"][3]
+    return diam / (O * hmin)
+
+
+CLUSTER_RTOL = 1e-6
+CLUSTER_ATOL = 1e-9
+
+
+def select_modes(lam, fixed_modes, tau, max_modes):
+    """Number of modes m_j kept (Sec. 3.2: all lambda below the threshold).
+
+    fixed_modes > 0 keeps exactly that many; otherwise lambda <= tau, capped at
+    max_modes.  Infinite eigenvalues (null space of B) are never kept.  If the cut falls inside a cluster of (numerically) equal
+    eigenvalues, the whole cluster is dropped so the selected span is unique.
+    """
+    nfin = int(np.sum(np.isfinite(lam)))
+    if fixed_modes > 0:
+        m = min(fixed_modes, nfin)
+    else:
+        m = int(np.sum(lam <= tau))
+        m = min(m, max_modes, nfin)
+    while 0 < m < nfin:
+        a, b = lam[m - 1], lam[m]
+        if abs(b - a) <= CLUSTER_RTOL * max(abs(a), abs(b)) + CLUSTER_ATOL:
+            m -= 1
+        else:
+            break
+    return m
+
+
+def coarse_space(p, subs, A, eig_method="auto"):
+    """GenEO coarse basis Z (ndof x N_H, sparse) and per-subdomain data.
+
+    Returns (Z, info) with info[j] = dict(lam, m, tau).
+    """
+    md = p["modes"]
+    sigma = md["shift"]
+    fixed, cap = md["fixed_modes"], md["max_modes"]
+    cols, info = [], []
+    ndof = A.shape[0]
+    for s in subs:
+        Aj, Aoj = local_matrices(p, s)
+        Xd = sp.diags(s.X)
+        Bj = (Xd @ Aoj @ Xd).tocsr()
+        nev = (fixed if fixed > 0 else cap) + 1
+        lam, P = eigenpairs(Aj, Bj, nev, sigma, eig_method)
+        tau = md["threshold"] if md["threshold"] > 0 else threshold(p, s)
+        m = select_modes(lam, fixed, tau, cap)
+        for k in range(m):
+            phi = np.zeros(ndof)
+            phi[s.neu_dofs] = s.X * P[:, k]
+            cols.append(phi)
+        info.append(dict(lam=lam, m=m, tau=tau, P=P[:, :m]))
+    if cols:
+        Z = sp.csc_matrix(np.array(cols).T)
+    else:
+        Z = sp.csc_matrix((ndof, 0))
+    return Z, info
+
+
+def coarse_matrix(A, Z):
+    """A_H = R_H A R_H^T with R_H^T = Z (Sec. 3.3.3); dense."""
+    return (Z.T @ (A @ Z)).toarray()
