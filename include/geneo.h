@@ -1,0 +1,208 @@
+/*
+ * geneo.h -- C ABI of a GB300 (sm_103a) solver for 3D anisotropic linear
+ * elasticity in layered composites: trilinear hexahedral finite elements,
+ * preconditioned conjugate gradients with the two-level overlapping additive
+ * Schwarz preconditioner and the GenEO coarse space of
+ *   Butler, Dodwell, Reinarz, Sandhu, Scheichl, Seelinger, "High-performance
+ *   dune modules for solving large-scale, strongly anisotropic elliptic
+ *   problems with applications to aerospace composites", arXiv:1901.05188.
+ *
+ * Conventions (all calls):
+ *  - Units are the caller's; the synthetic workloads use mm, N, MPa.
+ *  - Mesh: tensor-product nodes x[0..nx], y[0..ny], z[0..nz] (strictly
+ *    increasing).  Node n = i + (nx+1)*(j + (ny+1)*k); dof = 3*n + c with
+ *    c = 0, 1, 2 for the x, y, z displacement.  Element e = ex + nx*(ey + ny*ez).
+ *  - Every array argument may be host memory or device memory of the current
+ *    CUDA device; the library finds out with cudaPointerGetAttributes.  Input
+ *    arrays stay owned by the caller and are only read during the call.
+ *  - All work is ordered on the context's CUDA stream.  Functions returning
+ *    data to host memory synchronise that stream before returning.
+ *  - Every function returns an int status (GENEO_OK = 0); nothing throws
+ *    across the ABI.  geneo_status_string() names a status.
+ *  - A context is not thread-safe; use one context per host thread/stream.
+ */
+#ifndef GENEO_H
+#define GENEO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  GENEO_OK = 0,
+  GENEO_ERR_INVALID_ARG = 1,
+  GENEO_ERR_WORKSPACE_TOO_SMALL = 2,
+  GENEO_ERR_CUDA = 3,
+  GENEO_ERR_NOT_SPD = 4,          /* non-positive pivot; see stats.failed_subdomain */
+  GENEO_ERR_EIG_NOT_CONVERGED = 5,
+  GENEO_ERR_CG_BREAKDOWN = 6,     /* p^T A p <= 0 or a NaN in the iteration */
+  GENEO_ERR_NOT_CONVERGED = 7,    /* max_it reached; u is still written */
+  GENEO_ERR_TIMEOUT = 8,
+  GENEO_ERR_UNIMPLEMENTED = 9,
+  GENEO_ERR_STATE = 10            /* call order violated (e.g. solve before setup) */
+};
+
+typedef struct geneo_ctx geneo_ctx;
+
+/* Precision of the subdomain factors and solves (the bulk of flops and bytes).
+ * GENEO_FP64: everything in double; plain PCG.
+ * GENEO_MIXED_FP32: subdomain Cholesky factors and triangular solves in single
+ *   precision inside an outer double-precision flexible CG; the GenEO
+ *   eigensolves, the coarse factor and solve, the residual SpMV and the CG
+ *   dot products stay in double. */
+typedef enum { GENEO_FP64 = 0, GENEO_MIXED_FP32 = 1 } geneo_precision;
+
+/* One-level term weight D_j in  M^-1 = sum_j R_j^T D_j A_j^-1 R_j + Z A_H^-1 Z^T.
+ * GENEO_AS: D_j = I, the symmetric operator of Sec. 3.1 (eqn:onelevelAS).
+ * GENEO_AS_POU: D_j = X_j (partition of unity); not symmetric, so solve()
+ *   then always uses flexible CG. */
+typedef enum { GENEO_AS = 0, GENEO_AS_POU = 1 } geneo_schwarz;
+
+/* Coarse space kind. GENEO_COARSE_GENEO: GenEO eigenvectors (Sec. 3.2);
+ * GENEO_COARSE_NONE: one-level additive Schwarz only (Sec. 3.1). */
+typedef enum { GENEO_COARSE_GENEO = 0, GENEO_COARSE_NONE = 1 } geneo_coarse;
+
+typedef struct {
+  int nx, ny, nz;                 /* elements per axis, each >= 1 */
+  const double *x, *y, *z;        /* node coordinates, lengths nx+1, ny+1, nz+1 */
+} geneo_mesh;
+
+/* Orthotropic material in its own axes (Sec. 2: nine constants; isotropic
+ * resin as E1=E2=E3=E, G=E/(2(1+nu)), nu12=nu13=nu23=nu). */
+typedef struct {
+  double E1, E2, E3, G12, G13, G23, nu12, nu13, nu23;
+} geneo_ortho;
+
+typedef struct {
+  int n;                          /* number of constrained dofs */
+  const int32_t *dof;             /* constrained dofs, 3*node + c, each < 3*nodes */
+  const double *value;            /* prescribed displacement per entry */
+} geneo_dirichlet;
+
+/* Box partition: the elements of each axis split into p parts
+ * [floor(k n / p), floor((k+1) n / p)), each grown by `overlap` element
+ * layers (Sec. 3.1).  Subdomain j = jx + px*(jy + py*jz). */
+typedef struct {
+  int px, py, pz;
+  int overlap;                    /* >= 1 */
+} geneo_partition;
+
+/* GenEO mode selection (Sec. 3.2): fixed_modes > 0 keeps exactly that many
+ * eigenvectors per subdomain; otherwise all with lambda <= threshold, where
+ * threshold <= 0 selects diam(Omega_j)/width(Omega_j^o) (box circumradius over
+ * O times the smallest element edge), capped at max_modes.  A cut inside a
+ * cluster of equal eigenvalues (relative gap <= 1e-6) drops the cluster.
+ * shift < 0 is the shift-and-invert shift sigma (Sec. 3.3.2). */
+typedef struct {
+  int fixed_modes;
+  double threshold;
+  int max_modes;                  /* 1..32 */
+  double shift;
+} geneo_modes;
+
+typedef struct {
+  int iterations;                 /* A p products performed by (F)PCG */
+  double rel_res_recursive;       /* ||r_k|| / ||b|| of the recursion at exit */
+  double rel_res_true;            /* ||b - A u|| / ||b|| recomputed at exit */
+  double kappa_est;               /* Lanczos estimate from the CG coefficients (PCG only, else 0) */
+  int n_coarse;                   /* N_H = sum_j m_j */
+  int n_subdomains;
+  float ms_assemble, ms_setup_eig, ms_setup_coarse, ms_setup_factor, ms_solve;
+  double bytes_per_iter;          /* algorithmic HBM bytes of one iteration */
+  double eig_max_residual;        /* max Ritz residual of the kept eigenpairs */
+  int failed_subdomain;           /* subdomain of a GENEO_ERR_NOT_SPD, else -1 */
+  int flexible;                   /* 1 if flexible CG was used */
+} geneo_stats;
+
+/* Create a context whose work runs on `cuda_stream` (a cudaStream_t; NULL =
+ * legacy default stream) on the current CUDA device. */
+int geneo_create(geneo_ctx **out, void *cuda_stream);
+int geneo_destroy(geneo_ctx *ctx);
+const char *geneo_status_string(int status);
+/* Human-readable detail of the last failure on this host thread. */
+const char *geneo_last_error(void);
+
+/* Device bytes needed by geneo_assemble for this mesh (BSR matrix, load,
+ * per-element material data, index arrays). */
+int geneo_assemble_workspace_bytes(const geneo_mesh *mesh, size_t *bytes);
+
+/* Device bytes needed by geneo_setup + geneo_solve for this partition, mode
+ * cap and precision (subdomain factors, eigensolver, coarse space, Krylov
+ * vectors).  Call after geneo_assemble. */
+int geneo_setup_workspace_bytes(geneo_ctx *ctx, const geneo_partition *part,
+                                const geneo_modes *modes, geneo_precision prec,
+                                size_t *bytes);
+
+/* Bind caller-owned device memory (e.g. allocated by PyTorch) as the
+ * workspace of phase 0 (assemble) or phase 1 (setup + solve).  It must stay
+ * alive until the context is destroyed or rebound; alignment >= 256 bytes.
+ * A phase run without a bound workspace allocates its own with cudaMalloc
+ * (freed by geneo_destroy).  Too small a workspace makes the phase return
+ * GENEO_ERR_WORKSPACE_TOO_SMALL. */
+int geneo_bind_workspace(geneo_ctx *ctx, int phase, void *device_ptr, size_t bytes);
+
+/* Assemble A u = b (Sec. 2, eqn:fe_matrix_system) on the device:
+ * per-element orthotropic stiffness rotated by the ply angle theta about +z
+ * and the out-of-plane angle phi (fibre direction
+ * (cos t cos p, sin t cos p, -sin p)); Q1 element stiffness by 2x2x2 Gauss
+ * integration; 3x3-block BSR; symmetric elimination of the Dirichlet dofs
+ * (b -= A[:,D] g, rows/cols zeroed, unit diagonal, b_D = g); load = consistent
+ * nodal forces of the traction (0, 0, -top_pressure) on the face z = z_max
+ * plus `nodal_load` (length 3*nodes, may be NULL).
+ *   elem_mat  : int32[nel], material index < n_mat
+ *   elem_theta: double[nel], radians
+ *   elem_phi  : double[nel], radians, may be NULL (all zero) */
+int geneo_assemble(geneo_ctx *ctx, const geneo_mesh *mesh, int n_mat,
+                   const geneo_ortho *mats, const int32_t *elem_mat,
+                   const double *elem_theta, const double *elem_phi,
+                   const geneo_dirichlet *dirichlet, const double *nodal_load,
+                   double top_pressure);
+
+/* Sizes of the assembled system: nodes and stored 3x3 blocks. */
+int geneo_system_info(geneo_ctx *ctx, int *n_nodes, int *nnz_blocks);
+
+/* Copy the assembled BSR (row_ptr[n_nodes+1], col[nnzb], val[9*nnzb] with
+ * each block row-major) and the load b[3*n_nodes]; any pointer may be NULL. */
+int geneo_get_system(geneo_ctx *ctx, int32_t *row_ptr, int32_t *col,
+                     double *val, double *b);
+
+/* y = A x with the assembled matrix (x, y: 3*n_nodes doubles). */
+int geneo_spmv(geneo_ctx *ctx, const double *x, double *y);
+
+/* Build the preconditioner (Sec. 3.1-3.3): subdomains, partition of unity,
+ * GenEO eigenproblems A_{Omega_j} p = lambda X_j A_{Omega_j^o} X_j p by
+ * shift-and-invert block Lanczos, coarse basis Z = [R_j^T X_j p_k], coarse
+ * matrix A_H = Z^T A Z and its Cholesky factor, and the band Cholesky factors
+ * of A_j = R_j A R_j^T in the requested precision. */
+int geneo_setup(geneo_ctx *ctx, const geneo_partition *part,
+                const geneo_modes *modes, geneo_precision prec,
+                geneo_schwarz schwarz, geneo_coarse coarse);
+
+/* z = M^-1 r with the preconditioner of the last geneo_setup. */
+int geneo_apply_preconditioner(geneo_ctx *ctx, const double *r, double *z);
+
+/* Coarse-space summary: per subdomain the kept mode count m_j
+ * (modes[n_subdomains]) and the smallest (max_modes+1) eigenvalues
+ * (lambdas[n_subdomains*(max_modes+1)], +inf where not computed/infinite).
+ * Any pointer may be NULL. */
+int geneo_coarse_info(geneo_ctx *ctx, int *n_subdomains, int *n_coarse,
+                      int32_t *modes, double *lambdas);
+
+/* Dense copies for inspection: Phi[3*n_nodes x n_coarse] column-major coarse
+ * basis; AH[n_coarse x n_coarse] coarse matrix.  Either may be NULL. */
+int geneo_get_coarse(geneo_ctx *ctx, double *Phi, double *AH);
+
+/* Solve A u = b by PCG (FP64 precision, GENEO_AS) or flexible CG (mixed
+ * precision or GENEO_AS_POU) from u0 = 0 until ||r_k|| <= tol ||b|| or max_it
+ * iterations (Sec. 3.1).  u: 3*n_nodes doubles.  stats may be NULL. */
+int geneo_solve(geneo_ctx *ctx, double tol, int max_it, double *u,
+                geneo_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GENEO_H */

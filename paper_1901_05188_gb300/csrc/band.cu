@@ -1,0 +1,528 @@
+// Band-tiled Cholesky factors and the fused subdomain solves of the one-level
+// additive Schwarz term  sum_j R_j^T D_j A_j^-1 R_j  (Sec. 3.1, eqn:onelevelAS)
+// and the coarse correction Z A_H^-1 Z^T (Sec. 3.1, Sec. 3.3.3).
+//
+// The paper factors A_j with a sparse direct solver (UMFPack).  Here each
+// A_j is a band matrix in a box numbering whose longest axis runs slowest, held
+// as dense 32 x 32 tiles; the factorisation is a right-looking tile Cholesky
+// (one launch per tile column for the diagonal block, one for the panel, one
+// for the trailing update, batched over all subdomains), and the diagonal
+// blocks are stored inverted so both triangular sweeps become streams of
+// small matrix-vector products.
+#include "band.cuh"
+
+namespace geneo {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T *tile_ptr(T *base, const BandLayout &L, int I, int d) {
+  return base + L.off + (((long long)I * (L.w + 1) + d) << 10);
+}
+template <typename T>
+__device__ __forceinline__ const T *tile_ptr(const T *base, const BandLayout &L, int I, int d) {
+  return base + L.off + (((long long)I * (L.w + 1) + d) << 10);
+}
+
+template <typename T>
+__global__ void k_band_pad(const BandLayout *lay, int nsys, T *pool) {
+  int j = blockIdx.x;
+  if (j >= nsys) return;
+  BandLayout L = lay[j];
+  int last = L.nt - 1;
+  for (int idx = L.n + threadIdx.x; idx < L.nt * 32; idx += blockDim.x) {
+    int r = idx - last * 32;
+    tile_ptr(pool, L, last, 0)[r * 32 + r] = T(1);
+  }
+}
+
+// ---- tile Cholesky ---------------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_chol_diag(const BandLayout *lay, int nsys, int J,
+                                                   T *poolL, T *poolU, DevStatus *st) {
+  int j = blockIdx.x;
+  BandLayout L = lay[j];
+  if (J >= L.nt) return;
+  __shared__ T A[32][33];
+  __shared__ T X[32][33];
+  __shared__ int bad;
+  T *t = tile_ptr(poolL, L, J, 0);
+  for (int e = threadIdx.x; e < 1024; e += 256) A[e & 31][e >> 5] = t[e];
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int k = 0; k < 32; ++k) {
+    if (threadIdx.x == 0) {
+      T d = A[k][k];
+      if (!(d > T(0))) {
+        bad = 1;
+        d = T(1);
+      }
+      A[k][k] = sqrt(d);
+    }
+    __syncthreads();
+    T dk = A[k][k];
+    for (int i = k + 1 + threadIdx.x; i < 32; i += 256) A[i][k] /= dk;
+    __syncthreads();
+    int m = 31 - k;
+    for (int e = threadIdx.x; e < m * m; e += 256) {
+      int i = k + 1 + e / m, c = k + 1 + e % m;
+      if (c <= i) A[i][c] -= A[i][k] * A[c][k];
+    }
+    __syncthreads();
+  }
+  // X = inv(L): thread c solves L x = e_c by forward substitution
+  if (threadIdx.x < 32) {
+    int c = threadIdx.x;
+    for (int i = 0; i < 32; ++i) {
+      T s = (i == c) ? T(1) : T(0);
+      if (i > c) {
+        for (int k = c; k < i; ++k) s -= A[i][k] * X[k][c];
+      } else if (i < c) {
+        X[i][c] = T(0);
+        continue;
+      }
+      X[i][c] = s / A[i][i];
+    }
+  }
+  __syncthreads();
+  T *u = tile_ptr(poolU, L, J, 0);
+  for (int e = threadIdx.x; e < 1024; e += 256) {
+    int r = e & 31, c = e >> 5;
+    t[e] = X[r][c];          // inv(L_JJ), column-major
+    u[e] = X[c][r];          // inv(L_JJ)^T
+  }
+  if (threadIdx.x == 0 && bad) {
+    if (atomicCAS(&st->code, 0, GENEO_ERR_NOT_SPD) == 0) st->where = j;
+  }
+}
+
+// L(J+d, J) = A(J+d, J) inv(L_JJ)^T for d = 1..w (blockIdx.y = d - 1).
+template <typename T>
+__global__ void __launch_bounds__(256) k_chol_trsm(const BandLayout *lay, int nsys, int J,
+                                                   T *poolL, T *poolU) {
+  int j = blockIdx.x, d = blockIdx.y + 1;
+  BandLayout L = lay[j];
+  if (J >= L.nt || d > L.w || J + d >= L.nt) return;
+  __shared__ T Aa[32][33];
+  __shared__ T D[32][33];
+  T *ta = tile_ptr(poolL, L, J + d, d);
+  const T *td = tile_ptr(poolL, L, J, 0);
+  for (int e = threadIdx.x; e < 1024; e += 256) {
+    Aa[e & 31][e >> 5] = ta[e];
+    D[e & 31][e >> 5] = td[e];
+  }
+  __syncthreads();
+  T *tu = tile_ptr(poolU, L, J, d);
+  for (int e = threadIdx.x; e < 1024; e += 256) {
+    int r = e & 31, c = e >> 5;
+    T s = T(0);
+    for (int k = 0; k <= c; ++k) s += Aa[r][k] * D[c][k];
+    ta[e] = s;                 // (r, c) column-major
+    tu[r * 32 + c] = s;        // transposed: U(J, d)(c, r) = L(J+d, J)(r, c)
+  }
+}
+
+// A(J+d1, J+d2) -= L(J+d1, J) L(J+d2, J)^T, 1 <= d2 <= d1 <= w.
+template <typename T>
+__global__ void __launch_bounds__(256) k_chol_update(const BandLayout *lay, int nsys, int J,
+                                                     T *poolL) {
+  int j = blockIdx.x;
+  BandLayout L = lay[j];
+  int p = blockIdx.y;
+  int d1 = 1;
+  while ((d1 + 1) * d1 / 2 <= p) ++d1;
+  int d2 = p - d1 * (d1 - 1) / 2 + 1;
+  if (J >= L.nt || d1 > L.w || J + d1 >= L.nt) return;
+  __shared__ T Aa[32][33];
+  __shared__ T Bb[32][33];
+  const T *ta = tile_ptr(poolL, L, J + d1, d1);
+  const T *tb = tile_ptr(poolL, L, J + d2, d2);
+  for (int e = threadIdx.x; e < 1024; e += 256) {
+    Aa[e & 31][e >> 5] = ta[e];
+    Bb[e & 31][e >> 5] = tb[e];
+  }
+  __syncthreads();
+  T *tc = tile_ptr(poolL, L, J + d1, d1 - d2);
+  for (int e = threadIdx.x; e < 1024; e += 256) {
+    int r = e & 31, c = e >> 5;
+    T s = T(0);
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) s += Aa[r][k] * Bb[c][k];
+    tc[e] -= s;
+  }
+}
+
+// ---- triangular sweeps -------------------------------------------------------
+
+// One sweep over the tile rows of a factored band system with the local
+// vector y in shared memory.  Forward: y_I <- inv(L_II)(y_I - sum_d L(I,I-d) y_{I-d});
+// backward: the same on the U stream with I descending and J = I + d.
+template <typename T>
+__device__ __forceinline__ void band_sweep(const T *__restrict__ pool, const BandLayout &L,
+                                           T *y, T *red, bool backward) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nt = L.nt, w = L.w;
+  for (int step = 0; step < nt; ++step) {
+    const int I = backward ? nt - 1 - step : step;
+    const int dmax = backward ? min(w, nt - 1 - I) : min(w, I);
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+    for (int d = warp + 1; d <= dmax; d += kSolveWarps) {
+      const T *t = tile_ptr(pool, L, I, d);
+      const T *yJ = y + (backward ? (I + d) : (I - d)) * 32;
+#pragma unroll
+      for (int c = 0; c < 32; c += 4) {
+        a0 += __ldg(t + (c + 0) * 32 + lane) * yJ[c + 0];
+        a1 += __ldg(t + (c + 1) * 32 + lane) * yJ[c + 1];
+        a2 += __ldg(t + (c + 2) * 32 + lane) * yJ[c + 2];
+        a3 += __ldg(t + (c + 3) * 32 + lane) * yJ[c + 3];
+      }
+    }
+    red[warp * 32 + lane] = (a0 + a1) + (a2 + a3);
+    __syncthreads();
+    if (warp == 0) {
+      T s = y[I * 32 + lane];
+#pragma unroll
+      for (int k = 0; k < kSolveWarps; ++k) s -= red[k * 32 + lane];
+      __syncwarp();
+      red[lane] = s;
+      __syncwarp();
+      const T *D = tile_ptr(pool, L, I, 0);
+      T o0 = T(0), o1 = T(0), o2 = T(0), o3 = T(0);
+#pragma unroll
+      for (int c = 0; c < 32; c += 4) {
+        o0 += __ldg(D + (c + 0) * 32 + lane) * red[c + 0];
+        o1 += __ldg(D + (c + 1) * 32 + lane) * red[c + 1];
+        o2 += __ldg(D + (c + 2) * 32 + lane) * red[c + 2];
+        o3 += __ldg(D + (c + 3) * 32 + lane) * red[c + 3];
+      }
+      y[I * 32 + lane] = (o0 + o1) + (o2 + o3);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSolveWarps * 32)
+    k_schwarz_solve(const SubDesc *subs, const BandLayout *lay, int nnx, int nny,
+                    const T *poolL, const T *poolU, const double *__restrict__ r,
+                    T *__restrict__ xloc, const CGScalars *cg) {
+  if (cg && cg->done) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *red = reinterpret_cast<T *>(smraw);
+  T *y = red + kSolveWarps * 32;
+  const int j = blockIdx.x;
+  const SubDesc &S = subs[j];
+  const BandLayout L = lay[j];
+  const int n = S.n_int, npad = L.nt * 32;
+  for (int l = threadIdx.x; l < npad; l += blockDim.x) {
+    T v = T(0);
+    if (l < n) {
+      int node = l / 3, c = l - 3 * node;
+      int gi, gj, gk;
+      S.ibox.global(node, gi, gj, gk);
+      v = T(r[3 * (gi + nnx * (gj + nny * gk)) + c]);
+    }
+    y[l] = v;
+  }
+  __syncthreads();
+  band_sweep(poolL, L, y, red, false);
+  band_sweep(poolU, L, y, red, true);
+  T *out = xloc + S.v_int;
+  for (int l = threadIdx.x; l < n; l += blockDim.x) out[l] = y[l];
+}
+
+__global__ void __launch_bounds__(kSolveWarps * 32)
+    k_band_solve_dense(const BandLayout *lay, const double *poolL, const double *poolU,
+                       const double *__restrict__ in, long long in_sys, int in_row,
+                       double *__restrict__ out, long long out_sys, int out_row, int mode) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double *red = reinterpret_cast<double *>(smraw);
+  double *y = red + kSolveWarps * 32;
+  const int j = blockIdx.x, c = blockIdx.y;
+  const BandLayout L = lay[j];
+  const int n = L.n, npad = L.nt * 32;
+  const double *src = in + j * in_sys + c;
+  for (int l = threadIdx.x; l < npad; l += blockDim.x)
+    y[l] = l < n ? src[(long long)l * in_row] : 0.0;
+  __syncthreads();
+  if (mode & 1) band_sweep(poolL, L, y, red, false);
+  if (mode & 2) band_sweep(poolU, L, y, red, true);
+  double *dst = out + j * out_sys + c;
+  for (int l = threadIdx.x; l < n; l += blockDim.x) dst[(long long)l * out_row] = y[l];
+}
+
+// ---- extraction of A_j from the global BSR ----------------------------------
+
+template <typename T>
+__global__ void k_extract_interior(const SubDesc *subs, const BandLayout *lay, int nnx,
+                                   int nny, int nnz, const int32_t *__restrict__ rp,
+                                   const double *__restrict__ val, T *pool) {
+  const int j = blockIdx.y;
+  const SubDesc &S = subs[j];
+  const BandLayout L = lay[j];
+  const int nn = S.ibox.count();
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)nn * 27) return;
+  int l = (int)(t / 27), s = (int)(t % 27);
+  int gi, gj, gk;
+  S.ibox.global(l, gi, gj, gk);
+  int di = s % 3 - 1, dj = (s / 3) % 3 - 1, dk = s / 9 - 1;
+  int l2 = S.ibox.local(gi + di, gj + dj, gk + dk);
+  if (l2 < 0 || l2 > l) return;
+  int g = gi + nnx * (gj + nny * gk);
+  // position of slot s in the global row: count valid slots before it
+  int pos = rp[g];
+  for (int q = 0; q < s; ++q) {
+    int qi = gi + q % 3 - 1, qj = gj + (q / 3) % 3 - 1, qk = gk + q / 9 - 1;
+    pos += ((unsigned)qi < (unsigned)nnx && (unsigned)qj < (unsigned)nny &&
+            (unsigned)qk < (unsigned)nnz);
+  }
+  const double *blk = val + 9 * (size_t)pos;
+  for (int rr = 0; rr < 3; ++rr)
+    for (int cc = 0; cc < 3; ++cc) {
+      int R = 3 * l + rr, C = 3 * l2 + cc;
+      if (R < C) continue;
+      int I = R >> 5, J = C >> 5;
+      tile_ptr(pool, L, I, I - J)[(C & 31) * 32 + (R & 31)] = T(blk[3 * rr + cc]);
+    }
+}
+
+// ---- gather / coarse --------------------------------------------------------
+
+template <typename T>
+__global__ void k_schwarz_gather(int nnx, int nny, int nnz, int px, int py,
+                                 const int *__restrict__ cand, int co0, int co1, int co2,
+                                 const SubDesc *subs, const T *__restrict__ xloc,
+                                 const double *__restrict__ Zp, const double *__restrict__ yH,
+                                 int pou, const uint8_t *__restrict__ mask,
+                                 double *__restrict__ z, const CGScalars *cg) {
+  if (cg && cg->done) return;
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nnx * nny * nnz) return;
+  int i = n % nnx, r = n / nnx, jj = r % nny, k = r / nny;
+  const int *ci = cand + (co0 + i) * kMaxCand;
+  const int *cj = cand + (co1 + jj) * kMaxCand;
+  const int *ck = cand + (co2 + k) * kMaxCand;
+  int nci = 0, ncj = 0, nck = 0;
+  while (nci < kMaxCand && ci[nci] >= 0) ++nci;
+  while (ncj < kMaxCand && cj[ncj] >= 0) ++ncj;
+  while (nck < kMaxCand && ck[nck] >= 0) ++nck;
+  double wgt = pou ? 1.0 / double(nci * ncj * nck) : 1.0;
+  double o[3] = {0.0, 0.0, 0.0};
+  for (int c = 0; c < nck; ++c)
+    for (int b = 0; b < ncj; ++b)
+      for (int a = 0; a < nci; ++a) {
+        int j = ci[a] + px * (cj[b] + py * ck[c]);
+        const SubDesc &S = subs[j];
+        int l = S.ibox.local(i, jj, k);
+        if (l < 0) continue;
+        const T *xs = xloc + S.v_int + 3 * l;
+        for (int comp = 0; comp < 3; ++comp) {
+          double v = double(xs[comp]);
+          if (pou) v *= mask[3 * n + comp] ? 0.0 : wgt;
+          if (S.m > 0 && yH) {
+            const double *zr = Zp + S.z_off + (long long)(3 * l + comp) * S.m;
+            const double *yy = yH + S.coff;
+            for (int q = 0; q < S.m; ++q) v += zr[q] * yy[q];
+          }
+          o[comp] += v;
+        }
+      }
+  z[3 * n] = o[0];
+  z[3 * n + 1] = o[1];
+  z[3 * n + 2] = o[2];
+}
+
+// partial w_{j,k} over a chunk of interior rows: thread (k = t % 32, row group t / 32)
+__global__ void __launch_bounds__(256) k_coarse_restrict(const SubDesc *subs, int nnx, int nny,
+                                                         const double *__restrict__ Zp,
+                                                         const double *__restrict__ r,
+                                                         double *__restrict__ wpart, int mcap,
+                                                         const CGScalars *cg) {
+  if (cg && cg->done) return;
+  const int j = blockIdx.x, ch = blockIdx.y;
+  const SubDesc &S = subs[j];
+  const int m = S.m;
+  __shared__ double acc[8][32];
+  if (m == 0) return;
+  const int n = S.n_int;
+  const int per = (n + kRestrictChunks - 1) / kRestrictChunks;
+  const int l0 = ch * per, l1 = min(n, l0 + per);
+  const int k = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  double s = 0.0;
+  if (k < m) {
+    for (int l = l0 + grp; l < l1; l += 8) {
+      int node = l / 3, c = l - 3 * node;
+      int gi, gj, gk;
+      S.ibox.global(node, gi, gj, gk);
+      s += Zp[S.z_off + (long long)l * m + k] * r[3 * (gi + nnx * (gj + nny * gk)) + c];
+    }
+  }
+  acc[grp][k] = s;
+  __syncthreads();
+  if (threadIdx.x < 32 && k < m) {
+    double t = 0.0;
+    for (int g = 0; g < 8; ++g) t += acc[g][k];
+    wpart[((long long)j * kRestrictChunks + ch) * mcap + k] = t;
+  }
+}
+
+__global__ void k_coarse_reduce(const SubDesc *subs, const double *__restrict__ wpart,
+                                double *__restrict__ wH, int mcap, const CGScalars *cg) {
+  if (cg && cg->done) return;
+  const int j = blockIdx.x;
+  const SubDesc &S = subs[j];
+  int k = threadIdx.x;
+  if (k >= S.m) return;
+  double t = 0.0;
+  for (int ch = 0; ch < kRestrictChunks; ++ch)
+    t += wpart[((long long)j * kRestrictChunks + ch) * mcap + k];
+  wH[S.coff + k] = t;
+}
+
+// y = AHinv w, one warp per row (AHinv symmetric, row-major)
+__global__ void k_coarse_gemv(int nH, const double *__restrict__ Ainv,
+                              const double *__restrict__ w, double *__restrict__ y,
+                              const CGScalars *cg) {
+  if (cg && cg->done) return;
+  int lane = threadIdx.x & 31;
+  int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (row >= nH) return;
+  const double *a = Ainv + (long long)row * nH;
+  double s = 0.0;
+  for (int c = lane; c < nH; c += 32) s += a[c] * w[c];
+  s = warp_sum(s);
+  if (lane == 0) y[row] = s;
+}
+
+}  // namespace
+
+// ---- launchers ----------------------------------------------------------------
+
+template <typename T>
+int launch_band_clear(const BandLayout *d_lay, int nsys, T *pool, long long pool_elems,
+                      cudaStream_t s) {
+  GENEO_CUDA_TRY(cudaMemsetAsync(pool, 0, pool_elems * sizeof(T), s));
+  k_band_pad<T><<<nsys, 32, 0, s>>>(d_lay, nsys, pool);
+  GENEO_CUDA_TRY(cudaGetLastError());
+  return GENEO_OK;
+}
+
+template <typename T>
+int launch_band_cholesky(const BandLayout *d_lay, int nsys, int nt_max, int w_max, T *poolL,
+                         T *poolU, DevStatus *st, cudaStream_t s) {
+  int npairs = w_max * (w_max + 1) / 2;
+  for (int J = 0; J < nt_max; ++J) {
+    k_chol_diag<T><<<nsys, 256, 0, s>>>(d_lay, nsys, J, poolL, poolU, st);
+    if (w_max > 0) {
+      k_chol_trsm<T><<<dim3(nsys, w_max), 256, 0, s>>>(d_lay, nsys, J, poolL, poolU);
+      k_chol_update<T><<<dim3(nsys, npairs), 256, 0, s>>>(d_lay, nsys, J, poolL);
+    }
+  }
+  GENEO_CUDA_TRY(cudaGetLastError());
+  return GENEO_OK;
+}
+
+static int solve_smem_bytes(int npad, size_t elem) {
+  return (int)((kSolveWarps * 32 + npad) * elem);
+}
+
+int launch_band_solve_dense(const BandLayout *d_lay, int nsys, int npad_max,
+                            const double *poolL, const double *poolU, const double *in,
+                            long long in_sys, int in_row, double *out, long long out_sys,
+                            int out_row, int ncols, int mode, cudaStream_t s) {
+  int sm = solve_smem_bytes(npad_max, sizeof(double));
+  if (sm > 227 * 1024) return GENEO_ERR_INVALID_ARG;
+  GENEO_CUDA_TRY(cudaFuncSetAttribute(k_band_solve_dense,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  k_band_solve_dense<<<dim3(nsys, ncols), kSolveWarps * 32, sm, s>>>(
+      d_lay, poolL, poolU, in, in_sys, in_row, out, out_sys, out_row, mode);
+  GENEO_CUDA_TRY(cudaGetLastError());
+  return GENEO_OK;
+}
+
+template <typename T>
+int launch_extract_interior(const SubDesc *d_subs, const BandLayout *d_lay, int nsub,
+                            int max_nodes, int nnx, int nny, int nnz, const int32_t *rp,
+                            const double *val, T *pool, cudaStream_t s) {
+  long long tot = (long long)max_nodes * 27;
+  dim3 grid((unsigned)((tot + 255) / 256), nsub);
+  k_extract_interior<T><<<grid, 256, 0, s>>>(d_subs, d_lay, nnx, nny, nnz, rp, val, pool);
+  GENEO_CUDA_TRY(cudaGetLastError());
+  return GENEO_OK;
+}
+
+template <typename T>
+int launch_schwarz_solve(const SubDesc *d_subs, const BandLayout *d_lay, int nsub,
+                         int npad_max, int nnx, int nny, const T *poolL, const T *poolU,
+                         const double *r, T *xloc, const CGScalars *cg, cudaStream_t s) {
+  int sm = solve_smem_bytes(npad_max, sizeof(T));
+  k_schwarz_solve<T><<<nsub, kSolveWarps * 32, sm, s>>>(d_subs, d_lay, nnx, nny, poolL, poolU,
+                                                        r, xloc, cg);
+  GENEO_CUDA_TRY(cudaGetLastError());
+  return GENEO_OK;
+}
+
+template <typename T>
+int prepare_schwarz_solve(int npad_max) {
+  int sm = solve_smem_bytes(npad_max, sizeof(T));
+  if (sm > 227 * 1024) return GENEO_ERR_INVALID_ARG;
+  GENEO_CUDA_TRY(cudaFuncSetAttribute(k_schwarz_solve<T>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  return GENEO_OK;
+}
+template int prepare_schwarz_solve<double>(int);
+template int prepare_schwarz_solve<float>(int);
+
+template <typename T>
+void launch_schwarz_gather(int nx, int ny, int nz, int px, int py, const int *cand,
+                           const int cand_off[3], const SubDesc *d_subs, const T *xloc,
+                           const double *Zp, const double *yH, int pou,
+                           const uint8_t *mask, double *z, const CGScalars *cg,
+                           cudaStream_t s) {
+  int nn = (nx + 1) * (ny + 1) * (nz + 1);
+  k_schwarz_gather<T><<<(nn + 255) / 256, 256, 0, s>>>(nx + 1, ny + 1, nz + 1, px, py, cand,
+                                                      cand_off[0], cand_off[1], cand_off[2],
+                                                      d_subs, xloc, Zp, yH, pou, mask, z, cg);
+}
+
+void launch_coarse_apply(const SubDesc *d_subs, int nsub, int max_nint, int nnx, int nny,
+                         const double *Zp, const double *r, double *wpart, double *wH,
+                         double *yH, const double *AHinv, int nH, int mcap,
+                         const CGScalars *cg, cudaStream_t s) {
+  (void)max_nint;
+  k_coarse_restrict<<<dim3(nsub, kRestrictChunks), 256, 0, s>>>(d_subs, nnx, nny, Zp, r, wpart,
+                                                               mcap, cg);
+  k_coarse_reduce<<<nsub, 32, 0, s>>>(d_subs, wpart, wH, mcap, cg);
+  k_coarse_gemv<<<(nH * 32 + 255) / 256, 256, 0, s>>>(nH, AHinv, wH, yH, cg);
+}
+
+template int launch_band_clear<double>(const BandLayout *, int, double *, long long, cudaStream_t);
+template int launch_band_clear<float>(const BandLayout *, int, float *, long long, cudaStream_t);
+template int launch_band_cholesky<double>(const BandLayout *, int, int, int, double *, double *,
+                                          DevStatus *, cudaStream_t);
+template int launch_band_cholesky<float>(const BandLayout *, int, int, int, float *, float *,
+                                         DevStatus *, cudaStream_t);
+template int launch_extract_interior<double>(const SubDesc *, const BandLayout *, int, int, int,
+                                             int, int, const int32_t *, const double *,
+                                             double *, cudaStream_t);
+template int launch_extract_interior<float>(const SubDesc *, const BandLayout *, int, int, int,
+                                            int, int, const int32_t *, const double *, float *,
+                                            cudaStream_t);
+template int launch_schwarz_solve<double>(const SubDesc *, const BandLayout *, int, int, int, int,
+                                          const double *, const double *, const double *,
+                                          double *, const CGScalars *, cudaStream_t);
+template int launch_schwarz_solve<float>(const SubDesc *, const BandLayout *, int, int, int, int,
+                                         const float *, const float *, const double *, float *,
+                                         const CGScalars *, cudaStream_t);
+template void launch_schwarz_gather<double>(int, int, int, int, int, const int *, const int[3],
+                                            const SubDesc *, const double *, const double *,
+                                            const double *, int, const uint8_t *, double *,
+                                            const CGScalars *, cudaStream_t);
+template void launch_schwarz_gather<float>(int, int, int, int, int, const int *, const int[3],
+                                           const SubDesc *, const float *, const double *,
+                                           const double *, int, const uint8_t *, double *,
+                                           const CGScalars *, cudaStream_t);
+
+}  // namespace geneo

@@ -1,0 +1,64 @@
+// Band-tiled Cholesky factorisation and triangular sweeps (internal).
+#pragma once
+
+#include "kernels.cuh"
+#include "precond.cuh"
+
+namespace geneo {
+
+constexpr int kSolveWarps = 16;     // warps of a band-solve CTA
+
+// Zero a pool of tiles and put ones on the padded diagonal of every system.
+template <typename T>
+int launch_band_clear(const BandLayout *d_lay, int nsys, T *pool, long long pool_elems,
+                      cudaStream_t s);
+
+// Right-looking tile Cholesky of nsys band systems held in poolL (lower
+// triangle of each tile row as input).  On exit poolL/poolU hold the forward
+// and backward tile streams described in precond.cuh.
+template <typename T>
+int launch_band_cholesky(const BandLayout *d_lay, int nsys, int nt_max, int w_max, T *poolL,
+                         T *poolU, DevStatus *st, cudaStream_t s);
+
+// Solve with ncols right-hand sides per system.  Column c of system j lives at
+// in[j*in_sys + l*in_row + c] (l = 0..n-1); the result goes to
+// out[j*out_sys + l*out_row + c] for l < nt*32 (padding rows written as zero).
+// In-place use (in == out with equal strides) is allowed.
+// mode: 1 forward (L), 2 backward (L^T), 3 both.
+int launch_band_solve_dense(const BandLayout *d_lay, int nsys, int npad_max,
+                            const double *poolL, const double *poolU, const double *in,
+                            long long in_sys, int in_row, double *out, long long out_sys,
+                            int out_row, int ncols, int mode, cudaStream_t s);
+
+// Extract A_j = R_j A R_j^T (interior dofs) from the global BSR into band tiles.
+template <typename T>
+int launch_extract_interior(const SubDesc *d_subs, const BandLayout *d_lay, int nsub,
+                            int max_nodes, int nnx, int nny, int nnz, const int32_t *rp,
+                            const double *val, T *pool, cudaStream_t s);
+
+// Opt in to the shared memory the Schwarz solve needs (call before capture).
+template <typename T>
+int prepare_schwarz_solve(int npad_max);
+
+// One-level Schwarz local solves: x_j = A_j^-1 R_j r for every subdomain.
+template <typename T>
+int launch_schwarz_solve(const SubDesc *d_subs, const BandLayout *d_lay, int nsub,
+                         int npad_max, int nnx, int nny, const T *poolL, const T *poolU,
+                         const double *r, T *xloc, const CGScalars *cg, cudaStream_t s);
+
+// z = sum_j R_j^T (D_j x_j + Z_j y_j) (deterministic gather over subdomains).
+template <typename T>
+void launch_schwarz_gather(int nx, int ny, int nz, int px, int py, const int *cand,
+                           const int cand_off[3], const SubDesc *d_subs, const T *xloc,
+                           const double *Zp, const double *yH, int pou,
+                           const uint8_t *mask, double *z, const CGScalars *cg,
+                           cudaStream_t s);
+
+// Coarse restriction w = Z^T r (partials), reduction and y = A_H^-1 w.
+constexpr int kRestrictChunks = 8;
+void launch_coarse_apply(const SubDesc *d_subs, int nsub, int max_nint, int nnx, int nny,
+                         const double *Zp, const double *r, double *wpart, double *wH,
+                         double *yH, const double *AHinv, int nH, int mcap,
+                         const CGScalars *cg, cudaStream_t s);
+
+}  // namespace geneo

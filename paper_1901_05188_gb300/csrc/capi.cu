@@ -1,0 +1,1172 @@
+// C ABI of the GenEO-PCG library: context, workspaces, and the host-side
+// orchestration of assembly (Sec. 2), preconditioner set-up (Sec. 3.1-3.3)
+// and (flexible) PCG (Sec. 3.1).  All arithmetic runs in the CUDA kernels of
+// this directory; the host only plans memory, computes integer index data of
+// the box partition, selects the number of modes and steers the iteration.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ctx.cuh"
+#include "geneo.cuh"
+
+using namespace geneo;
+
+static thread_local std::string g_last_error;
+
+void geneo_set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+  g_last_error = buf;
+}
+
+namespace geneo {
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+}  // namespace geneo
+
+namespace {
+
+constexpr int kHistCap = 20000;
+constexpr int kGraphIters = 8;
+constexpr int kDotChunks = 8;
+
+int fail(int code, const char *msg) {
+  g_last_error = msg;
+  return code;
+}
+
+// Copy n elements from a host-or-device source into device memory.
+template <typename T>
+int stage(T *dst, const T *src, size_t n, cudaStream_t s) {
+  if (n == 0) return GENEO_OK;
+  if (!src) return fail(GENEO_ERR_INVALID_ARG, "null input array");
+  cudaMemcpyKind k = is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  GENEO_CUDA_TRY(cudaMemcpyAsync(dst, src, n * sizeof(T), k, s));
+  return GENEO_OK;
+}
+
+// Copy n elements from device memory to a host-or-device destination (synchronous).
+template <typename T>
+int unstage(T *dst, const T *src, size_t n, cudaStream_t s) {
+  if (n == 0 || !dst) return GENEO_OK;
+  cudaMemcpyKind k = is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  GENEO_CUDA_TRY(cudaMemcpyAsync(dst, src, n * sizeof(T), k, s));
+  GENEO_CUDA_TRY(cudaStreamSynchronize(s));
+  return GENEO_OK;
+}
+
+int check_status(geneo_ctx *c, int *where = nullptr) {
+  DevStatus h{};
+  GENEO_CUDA_TRY(cudaMemcpyAsync(&h, c->status, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  GENEO_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (where) *where = h.where;
+  if (h.code != 0) {
+    GENEO_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(DevStatus), c->stream));
+    g_last_error = "device status " + std::to_string(h.code) + " at index " + std::to_string(h.where);
+  }
+  return h.code;
+}
+
+// ---- phase 0 layout --------------------------------------------------------
+void plan_assemble(Arena &A, geneo_ctx *c, int nx, int ny, int nz, int n_mat, int n_dir) {
+  int nnode = (nx + 1) * (ny + 1) * (nz + 1);
+  long long nel = (long long)nx * ny * nz;
+  // nnzb upper bound: 27 per node
+  long long nnzb = 27LL * nnode;
+  c->X = A.take<double>(nx + 1);
+  c->Y = A.take<double>(ny + 1);
+  c->Z = A.take<double>(nz + 1);
+  c->C0 = A.take<double>(36 * (size_t)std::max(n_mat, 1));
+  c->Cel = A.take<double>(36 * (size_t)nel);
+  c->cnt = A.take<int32_t>(nnode);
+  c->row_ptr = A.take<int32_t>(nnode + 1);
+  c->col = A.take<int32_t>(nnzb);
+  c->val = A.take<double>(9 * (size_t)nnzb);
+  c->b = A.take<double>(3 * (size_t)nnode);
+  c->g = A.take<double>(3 * (size_t)nnode);
+  c->mask = A.take<uint8_t>(3 * (size_t)nnode);
+  c->status = A.take<DevStatus>(1);
+  c->mats = A.take<geneo_ortho>(std::max(n_mat, 1));
+  c->emat = A.take<int32_t>(nel);
+  c->theta = A.take<double>(nel);
+  c->phi = A.take<double>(nel);
+  c->dir_dofs = A.take<int32_t>(std::max(n_dir, 1));
+  c->dir_vals = A.take<double>(std::max(n_dir, 1));
+  c->nodal = A.take<double>(3 * (size_t)nnode);
+}
+
+// ---- box partition (host integer logic) -----------------------------------
+struct AxisPart {
+  std::vector<int> elo, ehi, ilo, ihi;     // element box [elo, ehi), interior nodes [ilo, ihi]
+};
+
+int axis_partition(int n, int p, int O, AxisPart &a) {
+  if (p < 1 || p > n) return fail(GENEO_ERR_INVALID_ARG, "partition: parts must be in [1, elements]");
+  a.elo.resize(p);
+  a.ehi.resize(p);
+  a.ilo.resize(p);
+  a.ihi.resize(p);
+  for (int k = 0; k < p; ++k) {
+    int lo = (int)((long long)k * n / p), hi = (int)((long long)(k + 1) * n / p);
+    a.elo[k] = std::max(0, lo - O);
+    a.ehi[k] = std::min(n, hi + O);
+    a.ilo[k] = a.elo[k] + (a.elo[k] > 0 ? 1 : 0);
+    a.ihi[k] = a.ehi[k] - (a.ehi[k] < n ? 1 : 0);
+    if (a.ihi[k] < a.ilo[k]) return fail(GENEO_ERR_INVALID_ARG, "partition: empty subdomain interior");
+  }
+  return GENEO_OK;
+}
+
+BandLayout make_layout(int n, int hb, long long off) {
+  BandLayout L;
+  L.n = n;
+  L.nt = (n + 31) / 32;
+  L.w = std::min((hb + 31) / 32, L.nt - 1);
+  L.off = off;
+  return L;
+}
+
+long long layout_elems(const BandLayout &L) { return (long long)L.nt * (L.w + 1) * 1024; }
+
+// Host restatement of the mode-selection rule (Sec. 3.2 threshold with cap and
+// cluster guard): returns m_j given ascending eigenvalues (inf = infinite).
+int select_modes(const std::vector<double> &lam, int fixed, double tau, int cap) {
+  int nfin = 0;
+  for (double v : lam)
+    if (std::isfinite(v)) ++nfin;
+  int m;
+  if (fixed > 0) {
+    m = std::min(fixed, nfin);
+  } else {
+    m = 0;
+    for (double v : lam)
+      if (v <= tau) ++m;
+    m = std::min(std::min(m, cap), nfin);
+  }
+  while (m > 0 && m < nfin) {
+    double a = lam[m - 1], b = lam[m];
+    if (std::fabs(b - a) <= 1e-6 * std::max(std::fabs(a), std::fabs(b)) + 1e-9)
+      --m;
+    else
+      break;
+  }
+  return m;
+}
+
+template <typename T>
+void free_owned(T *&p, bool owned) {
+  if (owned && p) cudaFree(p);
+  p = nullptr;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+const char *geneo_status_string(int s) {
+  switch (s) {
+    case GENEO_OK: return "ok";
+    case GENEO_ERR_INVALID_ARG: return "invalid argument";
+    case GENEO_ERR_WORKSPACE_TOO_SMALL: return "workspace too small";
+    case GENEO_ERR_CUDA: return "CUDA error";
+    case GENEO_ERR_NOT_SPD: return "matrix not positive definite";
+    case GENEO_ERR_EIG_NOT_CONVERGED: return "eigensolver not converged";
+    case GENEO_ERR_CG_BREAKDOWN: return "CG breakdown";
+    case GENEO_ERR_NOT_CONVERGED: return "not converged";
+    case GENEO_ERR_TIMEOUT: return "timeout";
+    case GENEO_ERR_UNIMPLEMENTED: return "unimplemented";
+    case GENEO_ERR_STATE: return "call order violated";
+    default: return "unknown status";
+  }
+}
+
+const char *geneo_last_error(void) { return g_last_error.c_str(); }
+
+int geneo_create(geneo_ctx **out, void *cuda_stream) {
+  if (!out) return fail(GENEO_ERR_INVALID_ARG, "null out");
+  geneo_ctx *c = new (std::nothrow) geneo_ctx();
+  if (!c) return fail(GENEO_ERR_INVALID_ARG, "out of host memory");
+  c->stream = (cudaStream_t)cuda_stream;
+  GENEO_CUDA_TRY(cudaGetDevice(&c->device));
+  GENEO_CUDA_TRY(cudaMallocHost(&c->cg_host, sizeof(CGScalars)));
+  GENEO_CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  *out = c;
+  return GENEO_OK;
+}
+
+static void release_setup(geneo_ctx *c) {
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  if (c->ws1_owned && c->ws1) cudaFree(c->ws1);
+  c->ws1 = nullptr;
+  c->ws1_owned = false;
+  c->setup_done = false;
+}
+
+int geneo_destroy(geneo_ctx *c) {
+  if (!c) return GENEO_OK;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  release_setup(c);
+  if (c->ws0_owned && c->ws0) cudaFree(c->ws0);
+  if (c->cg_host) cudaFreeHost(c->cg_host);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  delete c;
+  return GENEO_OK;
+}
+
+int geneo_assemble_workspace_bytes(const geneo_mesh *mesh, size_t *bytes) {
+  if (!mesh || !bytes || mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1)
+    return fail(GENEO_ERR_INVALID_ARG, "bad mesh");
+  Arena A;
+  geneo_ctx tmp;
+  plan_assemble(A, &tmp, mesh->nx, mesh->ny, mesh->nz, 64, 3 * (mesh->nx + 1) * (mesh->ny + 1) * (mesh->nz + 1));
+  *bytes = A.off + 256;
+  return GENEO_OK;
+}
+
+int geneo_bind_workspace(geneo_ctx *c, int phase, void *ptr, size_t bytes) {
+  if (!c || (phase != 0 && phase != 1)) return fail(GENEO_ERR_INVALID_ARG, "bad phase");
+  if (ptr && ((uintptr_t)ptr & 255)) return fail(GENEO_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+  if (phase == 0) {
+    c->ws0_bound = ptr;
+    c->ws0_bound_bytes = bytes;
+  } else {
+    c->ws1_bound = ptr;
+    c->ws1_bound_bytes = bytes;
+  }
+  return GENEO_OK;
+}
+
+int geneo_assemble(geneo_ctx *c, const geneo_mesh *mesh, int n_mat, const geneo_ortho *mats,
+                   const int32_t *elem_mat, const double *elem_theta, const double *elem_phi,
+                   const geneo_dirichlet *dir, const double *nodal_load, double top_pressure) {
+  if (!c || !mesh || !mats || !elem_mat || !elem_theta || n_mat < 1)
+    return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1 || !mesh->x || !mesh->y || !mesh->z)
+    return fail(GENEO_ERR_INVALID_ARG, "bad mesh");
+  long long nnode_ll = (long long)(mesh->nx + 1) * (mesh->ny + 1) * (mesh->nz + 1);
+  if (nnode_ll * 27 > 0x7fffffffLL) return fail(GENEO_ERR_INVALID_ARG, "mesh too large for int32 BSR");
+  int n_dir = dir ? dir->n : 0;
+  if (n_dir < 0 || (n_dir > 0 && !dir->dof)) return fail(GENEO_ERR_INVALID_ARG, "bad Dirichlet set");
+  cudaStream_t s = c->stream;
+  release_setup(c);
+  c->assembled = false;
+  // host copies of coordinates (validation + partition geometry)
+  c->nx = mesh->nx;
+  c->ny = mesh->ny;
+  c->nz = mesh->nz;
+  c->nnode = (int)nnode_ll;
+  c->ndof = 3 * c->nnode;
+  c->nel = c->nx * c->ny * c->nz;
+  const double *axes[3] = {mesh->x, mesh->y, mesh->z};
+  std::vector<double> *hv[3] = {&c->hx, &c->hy, &c->hz};
+  int na[3] = {c->nx + 1, c->ny + 1, c->nz + 1};
+  for (int d = 0; d < 3; ++d) {
+    hv[d]->resize(na[d]);
+    if (is_device_ptr(axes[d])) {
+      GENEO_CUDA_TRY(cudaMemcpy(hv[d]->data(), axes[d], na[d] * sizeof(double), cudaMemcpyDeviceToHost));
+    } else {
+      std::memcpy(hv[d]->data(), axes[d], na[d] * sizeof(double));
+    }
+    for (int i = 1; i < na[d]; ++i)
+      if (!((*hv[d])[i] > (*hv[d])[i - 1])) return fail(GENEO_ERR_INVALID_ARG, "coordinates not increasing");
+  }
+  // workspace
+  Arena A;
+  plan_assemble(A, c, c->nx, c->ny, c->nz, n_mat, n_dir);
+  size_t need = A.off + 256;
+  char *base;
+  if (c->ws0_bound) {
+    if (c->ws0_bound_bytes < need) return fail(GENEO_ERR_WORKSPACE_TOO_SMALL, "assemble workspace too small");
+    if (c->ws0_owned && c->ws0) cudaFree(c->ws0);
+    c->ws0_owned = false;
+    c->ws0 = c->ws0_bound;
+    c->ws0_bytes = c->ws0_bound_bytes;
+  } else if (!c->ws0_owned || c->ws0_bytes < need) {
+    if (c->ws0_owned && c->ws0) cudaFree(c->ws0);
+    GENEO_CUDA_TRY(cudaMalloc(&c->ws0, need));
+    c->ws0_owned = true;
+    c->ws0_bytes = need;
+  }
+  base = (char *)c->ws0;
+  Arena B;
+  B.base = base;
+  B.cap = c->ws0_bytes;
+  plan_assemble(B, c, c->nx, c->ny, c->nz, n_mat, n_dir);
+  cudaEvent_t e0, e1;
+  GENEO_CUDA_TRY(cudaEventCreate(&e0));
+  GENEO_CUDA_TRY(cudaEventCreate(&e1));
+  GENEO_CUDA_TRY(cudaEventRecord(e0, s));
+  GENEO_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(DevStatus), s));
+  int st;
+  if ((st = stage(c->X, mesh->x, c->nx + 1, s))) return st;
+  if ((st = stage(c->Y, mesh->y, c->ny + 1, s))) return st;
+  if ((st = stage(c->Z, mesh->z, c->nz + 1, s))) return st;
+  if ((st = stage(c->mats, mats, n_mat, s))) return st;
+  if ((st = stage(c->emat, elem_mat, c->nel, s))) return st;
+  if ((st = stage(c->theta, elem_theta, c->nel, s))) return st;
+  if (elem_phi && (st = stage(c->phi, elem_phi, c->nel, s))) return st;
+  if (n_dir > 0) {
+    if ((st = stage(c->dir_dofs, dir->dof, n_dir, s))) return st;
+    if (dir->value && (st = stage(c->dir_vals, dir->value, n_dir, s))) return st;
+  }
+  if (nodal_load && (st = stage(c->nodal, nodal_load, c->ndof, s))) return st;
+  AssemblyArgs a{};
+  a.nx = c->nx;
+  a.ny = c->ny;
+  a.nz = c->nz;
+  a.n_mat = n_mat;
+  a.n_dir = n_dir;
+  a.X = c->X;
+  a.Y = c->Y;
+  a.Z = c->Z;
+  a.mats = c->mats;
+  a.emat = c->emat;
+  a.theta = c->theta;
+  a.phi = elem_phi ? c->phi : nullptr;
+  a.dir_dofs = c->dir_dofs;
+  a.dir_vals = (n_dir > 0 && dir->value) ? c->dir_vals : nullptr;
+  a.nodal = nodal_load ? c->nodal : nullptr;
+  a.top_pressure = top_pressure;
+  a.C0 = c->C0;
+  a.Cel = c->Cel;
+  a.cnt = c->cnt;
+  a.row_ptr = c->row_ptr;
+  a.col = c->col;
+  a.val = c->val;
+  a.b = c->b;
+  a.g = c->g;
+  a.mask = c->mask;
+  a.status = c->status;
+  if ((st = launch_assembly(a, s))) return st;
+  GENEO_CUDA_TRY(cudaEventRecord(e1, s));
+  int32_t nnzb;
+  GENEO_CUDA_TRY(cudaMemcpyAsync(&nnzb, c->row_ptr + c->nnode, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  if ((st = check_status(c))) return st;
+  GENEO_CUDA_TRY(cudaEventElapsedTime(&c->ms_assemble, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->nnzb = nnzb;
+  c->hmask.resize(c->ndof);
+  GENEO_CUDA_TRY(cudaMemcpy(c->hmask.data(), c->mask, c->ndof, cudaMemcpyDeviceToHost));
+  c->assembled = true;
+  return GENEO_OK;
+}
+
+int geneo_system_info(geneo_ctx *c, int *n_nodes, int *nnz_blocks) {
+  if (!c || !c->assembled) return fail(GENEO_ERR_STATE, "not assembled");
+  if (n_nodes) *n_nodes = c->nnode;
+  if (nnz_blocks) *nnz_blocks = c->nnzb;
+  return GENEO_OK;
+}
+
+int geneo_get_system(geneo_ctx *c, int32_t *row_ptr, int32_t *col, double *val, double *b) {
+  if (!c || !c->assembled) return fail(GENEO_ERR_STATE, "not assembled");
+  int st;
+  if ((st = unstage(row_ptr, c->row_ptr, c->nnode + 1, c->stream))) return st;
+  if ((st = unstage(col, c->col, c->nnzb, c->stream))) return st;
+  if ((st = unstage(val, c->val, 9 * (size_t)c->nnzb, c->stream))) return st;
+  if ((st = unstage(b, c->b, c->ndof, c->stream))) return st;
+  return GENEO_OK;
+}
+
+// y = A x; x and y may be host or device memory.  Uses the phase-0 scratch
+// vector g as a staging area when x is host memory (g is only needed during
+// assembly).
+int geneo_spmv(geneo_ctx *c, const double *x, double *y) {
+  if (!c || !c->assembled) return fail(GENEO_ERR_STATE, "not assembled");
+  if (!x || !y) return fail(GENEO_ERR_INVALID_ARG, "null vector");
+  cudaStream_t s = c->stream;
+  bool xd = is_device_ptr(x), yd = is_device_ptr(y);
+  const double *dx = x;
+  double *dy = y;
+  std::vector<double> tmp;
+  double *scratch = nullptr;
+  if (!xd || !yd) {
+    GENEO_CUDA_TRY(cudaMallocAsync(&scratch, 2 * (size_t)c->ndof * sizeof(double), s));
+  }
+  if (!xd) {
+    GENEO_CUDA_TRY(cudaMemcpyAsync(scratch, x, c->ndof * sizeof(double), cudaMemcpyHostToDevice, s));
+    dx = scratch;
+  }
+  if (!yd) dy = scratch + c->ndof;
+  BSR A{c->nnode, c->row_ptr, c->col, c->val};
+  launch_spmv(A, dx, dy, s);
+  GENEO_CUDA_TRY(cudaGetLastError());
+  if (!yd) GENEO_CUDA_TRY(cudaMemcpyAsync(y, dy, c->ndof * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (scratch) GENEO_CUDA_TRY(cudaFreeAsync(scratch, s));
+  GENEO_CUDA_TRY(cudaStreamSynchronize(s));
+  return GENEO_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================
+// Set-up
+namespace {
+
+struct SetupPlan {
+  std::vector<SubDesc> subs;
+  std::vector<BandLayout> lay_int, lay_neu;
+  int nsub = 0;
+  int max_nodes_neu = 0, max_nodes_int = 0, max_nint = 0;
+  std::vector<int> cand, ecnt;
+  int cand_off[3] = {0, 0, 0}, ecnt_off[3] = {0, 0, 0};
+};
+
+int build_plan(geneo_ctx *c, const geneo_partition *part, const geneo_modes *modes,
+               SetupPlan &P) {
+  if (!part || part->overlap < 1) return fail(GENEO_ERR_INVALID_ARG, "overlap must be >= 1");
+  if (!modes || modes->max_modes < 0 || modes->max_modes > kMaxModes || modes->fixed_modes < 0 ||
+      modes->fixed_modes > kMaxModes || !(modes->shift < 0.0))
+    return fail(GENEO_ERR_INVALID_ARG, "bad mode options (modes <= 32, shift < 0)");
+  int n[3] = {c->nx, c->ny, c->nz};
+  int p[3] = {part->px, part->py, part->pz};
+  AxisPart ax[3];
+  int st;
+  for (int d = 0; d < 3; ++d)
+    if ((st = axis_partition(n[d], p[d], part->overlap, ax[d]))) return st;
+  P.cand.clear();
+  P.ecnt.clear();
+  int off = 0, eoff = 0;
+  for (int d = 0; d < 3; ++d) {
+    P.cand_off[d] = off;
+    P.ecnt_off[d] = eoff;
+    for (int i = 0; i <= n[d]; ++i) {
+      int cnt = 0;
+      for (int k = 0; k < p[d]; ++k)
+        if (i >= ax[d].ilo[k] && i <= ax[d].ihi[k]) {
+          if (cnt >= kMaxCand) return fail(GENEO_ERR_INVALID_ARG, "overlap too wide for the part size");
+          P.cand.push_back(k);
+          ++cnt;
+        }
+      for (; cnt < kMaxCand; ++cnt) P.cand.push_back(-1);
+    }
+    off += n[d] + 1;
+    for (int e = 0; e < n[d]; ++e) {
+      int cnt = 0;
+      for (int k = 0; k < p[d]; ++k) cnt += (e >= ax[d].elo[k] && e < ax[d].ehi[k]);
+      P.ecnt.push_back(cnt);
+    }
+    eoff += n[d];
+  }
+  P.nsub = p[0] * p[1] * p[2];
+  P.subs.assign(P.nsub, SubDesc{});
+  P.lay_int.resize(P.nsub);
+  P.lay_neu.resize(P.nsub);
+  long long f_int = 0, v_int = 0, f_neu = 0, b_neu = 0, x_neu = 0;
+  for (int kz = 0; kz < p[2]; ++kz)
+    for (int ky = 0; ky < p[1]; ++ky)
+      for (int kx = 0; kx < p[0]; ++kx) {
+        int j = kx + p[0] * (ky + p[1] * kz);
+        SubDesc &S = P.subs[j];
+        int ks[3] = {kx, ky, kz};
+        int next[3];
+        for (int d = 0; d < 3; ++d) {
+          const AxisPart &a = ax[d];
+          S.elo[d] = a.elo[ks[d]];
+          S.ehi[d] = a.ehi[ks[d]];
+          S.nbox.lo[d] = a.elo[ks[d]];
+          S.nbox.n[d] = a.ehi[ks[d]] - a.elo[ks[d]] + 1;
+          S.ibox.lo[d] = a.ilo[ks[d]];
+          S.ibox.n[d] = a.ihi[ks[d]] - a.ilo[ks[d]] + 1;
+          next[d] = S.nbox.n[d];
+        }
+        // band ordering: fastest axis = smallest extent, longest axis slowest
+        int perm[3] = {0, 1, 2};
+        std::sort(perm, perm + 3, [&](int u, int v) {
+          return next[u] < next[v] || (next[u] == next[v] && u < v);
+        });
+        for (int d = 0; d < 3; ++d) S.nbox.perm[d] = S.ibox.perm[d] = perm[d];
+        S.n_int = 3 * S.ibox.count();
+        S.n_neu = 3 * S.nbox.count();
+        BandLayout Li = make_layout(S.n_int, S.ibox.half_band_dofs(), f_int);
+        BandLayout Ln = make_layout(S.n_neu, S.nbox.half_band_dofs(), f_neu);
+        S.nt_int = Li.nt;
+        S.w_int = Li.w;
+        S.f_int = f_int;
+        S.v_int = v_int;
+        S.nt_neu = Ln.nt;
+        S.w_neu = Ln.w;
+        S.f_neu = f_neu;
+        S.b_neu = b_neu;
+        S.x_neu = x_neu;
+        S.m = 0;
+        S.coff = 0;
+        S.z_off = 0;
+        f_int += layout_elems(Li);
+        v_int += S.n_int;
+        f_neu += layout_elems(Ln);
+        b_neu += 27LL * S.nbox.count();
+        x_neu += S.n_neu;
+        P.lay_int[j] = Li;
+        P.lay_neu[j] = Ln;
+        P.max_nodes_neu = std::max(P.max_nodes_neu, S.nbox.count());
+        P.max_nodes_int = std::max(P.max_nodes_int, S.ibox.count());
+        P.max_nint = std::max(P.max_nint, S.n_int);
+      }
+  Precond &pc = c->pc;
+  pc.fac_int_elems = f_int;
+  pc.xloc_elems = v_int;
+  pc.fac_neu_elems = f_neu;
+  pc.bloc_blocks = b_neu;
+  pc.xneu_elems = x_neu;
+  pc.nt_int_max = pc.w_int_max = pc.nt_neu_max = pc.w_neu_max = 0;
+  for (int j = 0; j < P.nsub; ++j) {
+    pc.nt_int_max = std::max(pc.nt_int_max, P.lay_int[j].nt);
+    pc.w_int_max = std::max(pc.w_int_max, P.lay_int[j].w);
+    pc.nt_neu_max = std::max(pc.nt_neu_max, P.lay_neu[j].nt);
+    pc.w_neu_max = std::max(pc.w_neu_max, P.lay_neu[j].w);
+  }
+  pc.npad_int_max = pc.nt_int_max * 32;
+  pc.npad_neu_max = pc.nt_neu_max * 32;
+  pc.nsub = P.nsub;
+  pc.part = *part;
+  pc.modes = *modes;
+  for (int d = 0; d < 3; ++d) {
+    pc.cand_off[d] = P.cand_off[d];
+    pc.ecnt_off[d] = P.ecnt_off[d];
+  }
+  return GENEO_OK;
+}
+
+// Lay out the phase-1 workspace (a pass with A.base == nullptr only measures).
+void plan_setup(Arena &A, geneo_ctx *c, const SetupPlan &P) {
+  Precond &pc = c->pc;
+  const int nsub = P.nsub, p = kLanczosBlock;
+  const bool f32 = pc.prec == GENEO_MIXED_FP32;
+  size_t esz = f32 ? sizeof(float) : sizeof(double);
+  pc.d_subs = A.take<SubDesc>(nsub);
+  pc.d_lay_int = A.take<BandLayout>(nsub);
+  pc.d_lay_neu = A.take<BandLayout>(nsub);
+  pc.d_lay_H = A.take<BandLayout>(1);
+  pc.d_cand = A.take<int>(P.cand.size());
+  pc.d_ecnt = A.take<int>(P.ecnt.size());
+  pc.d_yoff = A.take<long long>(nsub);
+  pc.d_pairs = A.take<int2>((size_t)nsub * nsub);
+  pc.facL = A.take<char>(pc.fac_int_elems * esz);
+  pc.facU = A.take<char>(pc.fac_int_elems * esz);
+  pc.xloc = A.take<char>(pc.xloc_elems * esz);
+  int cap = pc.modes.fixed_modes > 0 ? pc.modes.fixed_modes : pc.modes.max_modes;
+  if (pc.coarse != GENEO_COARSE_GENEO) cap = 0;
+  pc.mcap = cap + 1;
+  pc.kdim = pc.ksteps * p;
+  if (cap > 0) {
+    const int npad = pc.npad_neu_max;
+    pc.neuL = A.take<double>(pc.fac_neu_elems);
+    pc.neuU = A.take<double>(pc.fac_neu_elems);
+    pc.Bloc = A.take<double>(9 * (size_t)pc.bloc_blocks);
+    pc.Xneu = A.take<double>(pc.xneu_elems);
+    pc.V = A.take<double>((size_t)nsub * npad * (pc.kdim + p));
+    pc.W = A.take<double>((size_t)nsub * npad * p);
+    pc.T1 = A.take<double>((size_t)nsub * npad * p);
+    pc.Hm = A.take<double>((size_t)nsub * pc.kdim * pc.kdim);
+    pc.hchunks = kDotChunks;
+    size_t nout = std::max((size_t)pc.kdim * p, (size_t)pc.mcap * pc.mcap);
+    pc.Hpart = A.take<double>((size_t)nsub * kDotChunks * nout);
+    pc.Hs = A.take<double>((size_t)nsub * nout);
+    pc.G = A.take<double>((size_t)nsub * pc.mcap * pc.mcap);
+    pc.Racc = A.take<double>((size_t)2 * nsub * p * p);
+    pc.Rblk = A.take<double>((size_t)nsub * p * p);
+    pc.Evec = A.take<double>((size_t)2 * nsub * pc.kdim * pc.kdim);
+    pc.Eval = A.take<double>((size_t)nsub * pc.kdim);
+    pc.Eres = A.take<double>((size_t)nsub * pc.kdim);
+    pc.P = A.take<double>((size_t)nsub * npad * pc.mcap);
+    long long zel = 0, yel = 0;
+    for (const SubDesc &S : P.subs) {
+      zel += (long long)S.n_int * cap;
+      yel += (long long)S.n_neu * cap;
+    }
+    pc.z_elems = zel;
+    pc.Zp = A.take<double>(zel);
+    pc.Yp = A.take<double>(yel);
+    pc.nH_cap = nsub * cap;
+    int ntH = (pc.nH_cap + 31) / 32;
+    pc.AH = A.take<double>((size_t)pc.nH_cap * pc.nH_cap);
+    pc.AHinv = A.take<double>((size_t)pc.nH_cap * pc.nH_cap);
+    pc.AHL = A.take<double>((size_t)ntH * ntH * 1024);
+    pc.AHU = A.take<double>((size_t)ntH * ntH * 1024);
+    pc.wpart = A.take<double>((size_t)nsub * kRestrictChunks * pc.mcap);
+    pc.wH = A.take<double>(pc.nH_cap);
+    pc.yH = A.take<double>(pc.nH_cap);
+  } else {
+    pc.neuL = pc.neuU = pc.Bloc = pc.Xneu = pc.V = pc.W = pc.T1 = pc.Hm = pc.Hpart = nullptr;
+    pc.Hs = pc.G = pc.Racc = nullptr;
+    pc.Rblk = pc.Evec = pc.Eval = pc.Eres = pc.P = pc.Zp = pc.Yp = nullptr;
+    pc.AH = pc.AHinv = pc.AHL = pc.AHU = pc.wpart = pc.wH = pc.yH = nullptr;
+    pc.nH_cap = 0;
+    pc.z_elems = 0;
+  }
+  const int n = c->ndof;
+  c->x = A.take<double>(n);
+  c->r = A.take<double>(n);
+  c->p = A.take<double>(n);
+  c->q = A.take<double>(n);
+  c->z = A.take<double>(n);
+  c->tmp = A.take<double>(n);
+  c->part = A.take<double>(2 * kRedBlocks);
+  c->alphas = A.take<double>(kHistCap);
+  c->betas = A.take<double>(kHistCap);
+  c->scal = A.take<double>(4);
+  c->cg = A.take<CGScalars>(1);
+}
+
+double default_threshold(geneo_ctx *c, const SubDesc &S, int O) {
+  const std::vector<double> *ax[3] = {&c->hx, &c->hy, &c->hz};
+  double d2 = 0.0, hmin = 1e300;
+  for (int d = 0; d < 3; ++d) {
+    const std::vector<double> &v = *ax[d];
+    double ext = v[S.ehi[d]] - v[S.elo[d]];
+    d2 += ext * ext;
+    for (int e = S.elo[d]; e < S.ehi[d]; ++e) hmin = std::min(hmin, v[e + 1] - v[e]);
+  }
+  return 0.5 * std::sqrt(d2) / (O * hmin);
+}
+
+}  // namespace
+
+// Apply the preconditioner z = M^-1 r on stream s (device vectors).
+static int precond_apply(geneo_ctx *c, const double *r, double *z, const CGScalars *cg,
+                         cudaStream_t s) {
+  Precond &pc = c->pc;
+  const int nnx = c->nx + 1, nny = c->ny + 1;
+  const bool coarse = pc.nH > 0;
+  if (coarse)
+    launch_coarse_apply(pc.d_subs, pc.nsub, 0, nnx, nny, pc.Zp, r, pc.wpart, pc.wH, pc.yH,
+                        pc.AHinv, pc.nH, pc.mcap, cg, s);
+  int st;
+  const int pou = pc.schwarz == GENEO_AS_POU;
+  if (pc.prec == GENEO_MIXED_FP32) {
+    if ((st = launch_schwarz_solve<float>(pc.d_subs, pc.d_lay_int, pc.nsub, pc.npad_int_max, nnx,
+                                          nny, (const float *)pc.facL, (const float *)pc.facU, r,
+                                          (float *)pc.xloc, cg, s)))
+      return st;
+    launch_schwarz_gather<float>(c->nx, c->ny, c->nz, pc.part.px, pc.part.py, pc.d_cand,
+                                 pc.cand_off, pc.d_subs, (const float *)pc.xloc, pc.Zp,
+                                 coarse ? pc.yH : nullptr, pou, c->mask, z, cg, s);
+  } else {
+    if ((st = launch_schwarz_solve<double>(pc.d_subs, pc.d_lay_int, pc.nsub, pc.npad_int_max,
+                                           nnx, nny, (const double *)pc.facL,
+                                           (const double *)pc.facU, r, (double *)pc.xloc, cg, s)))
+      return st;
+    launch_schwarz_gather<double>(c->nx, c->ny, c->nz, pc.part.px, pc.part.py, pc.d_cand,
+                                  pc.cand_off, pc.d_subs, (const double *)pc.xloc, pc.Zp,
+                                  coarse ? pc.yH : nullptr, pou, c->mask, z, cg, s);
+  }
+  GENEO_CUDA_TRY(cudaGetLastError());
+  return GENEO_OK;
+}
+
+// GenEO eigensolves (FP64 block Lanczos) and the coarse space.
+static int setup_coarse(geneo_ctx *c, SetupPlan &P, cudaStream_t s) {
+  Precond &pc = c->pc;
+  const int nsub = P.nsub, p = kLanczosBlock, kdim = pc.kdim, mcap = pc.mcap;
+  const int npad = pc.npad_neu_max;
+  const int nnx = c->nx + 1, nny = c->ny + 1, nnz = c->nz + 1;
+  const double sigma = pc.modes.shift;
+  int st;
+  // PoU, S = A - sigma B into band tiles, B into a local BSR
+  launch_pou_neumann(pc.d_subs, nsub, P.max_nodes_neu, pc.d_cand, pc.cand_off, c->mask, nnx, nny,
+                     pc.Xneu, s);
+  if ((st = launch_band_clear<double>(pc.d_lay_neu, nsub, pc.neuL, pc.fac_neu_elems, s))) return st;
+  launch_neumann_assemble(pc.d_subs, pc.d_lay_neu, nsub, P.max_nodes_neu, c->nx, c->ny, c->nz,
+                          c->X, c->Y, c->Z, c->Cel, pc.d_ecnt, pc.ecnt_off, c->mask, pc.Xneu,
+                          sigma, pc.neuL, pc.Bloc, s);
+  if ((st = launch_band_cholesky<double>(pc.d_lay_neu, nsub, pc.nt_neu_max, pc.w_neu_max,
+                                         pc.neuL, pc.neuU, c->status, s)))
+    return st;
+  // block Lanczos on C = L^-1 B L^-T with full re-orthogonalisation
+  const int ldv = kdim + p;
+  const long long sV = (long long)npad * ldv, sW = (long long)npad * p;
+  GENEO_CUDA_TRY(cudaMemsetAsync(pc.Hm, 0, (size_t)nsub * kdim * kdim * sizeof(double), s));
+  GENEO_CUDA_TRY(cudaMemsetAsync(pc.V, 0, (size_t)nsub * sV * sizeof(double), s));
+  GENEO_CUDA_TRY(cudaMemsetAsync(pc.W, 0, (size_t)nsub * sW * sizeof(double), s));
+  GENEO_CUDA_TRY(cudaMemsetAsync(pc.T1, 0, (size_t)nsub * sW * sizeof(double), s));
+  launch_random_block(pc.d_subs, nsub, npad, pc.W, p, sW, p, 0x5eed1234ull, s);
+  for (int pass = 0; pass < 2; ++pass) {
+    launch_tsdots(pc.d_subs, nsub, npad, pc.W, p, sW, p, pc.W, p, sW, p, pc.Hpart, kDotChunks,
+                  pc.G, (long long)p * p, s);
+    launch_cholqr(pc.d_subs, nsub, npad, pc.G, pc.W, p, pc.Racc, pass == 0, s);
+  }
+  launch_copy_block(pc.d_subs, nsub, npad, pc.W, p, sW, pc.V, ldv, sV, p, s);
+  for (int k = 0; k < pc.ksteps; ++k) {
+    if ((st = launch_band_solve_dense(pc.d_lay_neu, nsub, npad, pc.neuL, pc.neuU, pc.V + k * p,
+                                      sV, ldv, pc.T1, sW, p, p, 2, s)))
+      return st;
+    launch_bloc_mv(pc.d_subs, nsub, P.max_nodes_neu, pc.Bloc, pc.T1, pc.W, sW, p, s);
+    if ((st = launch_band_solve_dense(pc.d_lay_neu, nsub, npad, pc.neuL, pc.neuU, pc.W, sW, p,
+                                      pc.W, sW, p, p, 1, s)))
+      return st;
+    const int na = (k + 1) * p;
+    for (int pass = 0; pass < 2; ++pass) {
+      launch_tsdots(pc.d_subs, nsub, npad, pc.V, ldv, sV, na, pc.W, p, sW, p, pc.Hpart,
+                    kDotChunks, pc.Hs, (long long)na * p, s);
+      launch_hm_accum(nsub, pc.Hm, kdim, pc.Hs, na, k, p, s);
+      launch_tsgemm(pc.d_subs, nsub, npad, pc.V, ldv, sV, na, pc.Hs, p, (long long)na * p, pc.W,
+                    p, sW, p, -1.0, 1.0, s);
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+      launch_tsdots(pc.d_subs, nsub, npad, pc.W, p, sW, p, pc.W, p, sW, p, pc.Hpart, kDotChunks,
+                    pc.G, (long long)p * p, s);
+      launch_cholqr(pc.d_subs, nsub, npad, pc.G, pc.W, p, pc.Racc, pass == 0, s);
+    }
+    launch_hm_subdiag(nsub, pc.Hm, kdim, pc.Racc, k, p, pc.Rblk, s);
+    if (k + 1 < pc.ksteps) launch_copy_block(pc.d_subs, nsub, npad, pc.W, p, sW, pc.V, ldv, sV, p, s);
+  }
+  GENEO_CUDA_TRY(cudaGetLastError());
+  if ((st = launch_jacobi(nsub, pc.Hm, kdim, p, pc.Rblk, pc.Eval, pc.Evec, pc.Eres, s))) return st;
+  // Ritz vectors y = V s, then p = L^-T y, normalised to ||p||_2 = 1
+  const long long sP = (long long)npad * mcap;
+  launch_tsgemm(pc.d_subs, nsub, npad, pc.V, ldv, sV, kdim, pc.Evec, kdim, (long long)kdim * kdim,
+                pc.P, mcap, sP, mcap, 1.0, 0.0, s);
+  if ((st = launch_band_solve_dense(pc.d_lay_neu, nsub, npad, pc.neuL, pc.neuU, pc.P, sP, mcap,
+                                    pc.P, sP, mcap, mcap, 2, s)))
+    return st;
+  launch_tsdots(pc.d_subs, nsub, npad, pc.P, mcap, sP, mcap, pc.P, mcap, sP, mcap, pc.Hpart,
+                kDotChunks, pc.G, (long long)mcap * mcap, s);
+  launch_normalize_cols(pc.d_subs, nsub, npad, pc.P, mcap, sP, mcap, pc.G, s);
+  GENEO_CUDA_TRY(cudaGetLastError());
+  // eigenvalues -> host, mode selection
+  std::vector<double> ev((size_t)nsub * kdim), er((size_t)nsub * kdim);
+  GENEO_CUDA_TRY(cudaMemcpyAsync(ev.data(), pc.Eval, ev.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  GENEO_CUDA_TRY(cudaMemcpyAsync(er.data(), pc.Eres, er.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  GENEO_CUDA_TRY(cudaStreamSynchronize(s));
+  if ((st = check_status(c))) return st;
+  pc.m.assign(nsub, 0);
+  pc.lambdas.assign((size_t)nsub * mcap, INFINITY);
+  pc.eig_max_res = 0.0;
+  int coff = 0;
+  long long zoff = 0, yoff = 0;
+  std::vector<long long> yoffs(nsub);
+  const double mu_min = 1e-12 / std::fabs(sigma);
+  for (int j = 0; j < nsub; ++j) {
+    std::vector<double> lam(mcap);
+    for (int i = 0; i < mcap; ++i) {
+      double mu = ev[(size_t)j * kdim + i];
+      lam[i] = mu > mu_min ? sigma + 1.0 / mu : INFINITY;
+      pc.lambdas[(size_t)j * mcap + i] = lam[i];
+    }
+    SubDesc &S = P.subs[j];
+    double tau = pc.modes.threshold > 0 ? pc.modes.threshold : default_threshold(c, S, pc.part.overlap);
+    int cap = pc.mcap - 1;
+    int m = select_modes(lam, pc.modes.fixed_modes, tau, cap);
+    for (int i = 0; i < m; ++i) {
+      double mu = ev[(size_t)j * kdim + i];
+      pc.eig_max_res = std::max(pc.eig_max_res, er[(size_t)j * kdim + i] / mu);
+    }
+    S.m = m;
+    S.coff = coff;
+    S.z_off = zoff;
+    yoffs[j] = yoff;
+    coff += m;
+    zoff += (long long)S.n_int * m;
+    yoff += (long long)S.n_neu * m;
+    pc.m[j] = m;
+  }
+  pc.nH = coff;
+  pc.subs = P.subs;
+  GENEO_CUDA_TRY(cudaMemcpyAsync(pc.d_subs, P.subs.data(), nsub * sizeof(SubDesc), cudaMemcpyHostToDevice, s));
+  GENEO_CUDA_TRY(cudaMemcpyAsync(pc.d_yoff, yoffs.data(), nsub * sizeof(long long), cudaMemcpyHostToDevice, s));
+  if (pc.nH == 0) return GENEO_OK;
+  launch_build_Z(pc.d_subs, nsub, P.max_nint, pc.P, mcap, sP, pc.Xneu, pc.Zp, s);
+  launch_AZ(pc.d_subs, nsub, P.max_nodes_neu, nnx, nny, nnz, c->row_ptr, c->col, c->val, pc.Zp,
+            pc.d_yoff, pc.Yp, s);
+  // subdomain pairs whose supports meet
+  std::vector<int2> pairs;
+  for (int j = 0; j < nsub; ++j)
+    for (int k = j; k < nsub; ++k) {
+      const SubDesc &A = P.subs[j], &B = P.subs[k];
+      if (A.m == 0 || B.m == 0) continue;
+      bool meet = true;
+      for (int d = 0; d < 3; ++d) {
+        int lo = std::max(A.ibox.lo[d], B.nbox.lo[d]);
+        int hi = std::min(A.ibox.lo[d] + A.ibox.n[d], B.nbox.lo[d] + B.nbox.n[d]);
+        meet = meet && hi > lo;
+      }
+      if (meet) pairs.push_back(make_int2(j, k));
+    }
+  GENEO_CUDA_TRY(cudaMemcpyAsync(pc.d_pairs, pairs.data(), pairs.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+  const int nH = pc.nH;
+  GENEO_CUDA_TRY(cudaMemsetAsync(pc.AH, 0, (size_t)nH * nH * sizeof(double), s));
+  launch_coarse_blocks(pc.d_subs, pc.d_pairs, (int)pairs.size(), pc.Zp, pc.Yp, pc.d_yoff, pc.AH, nH, s);
+  launch_symmetrize(pc.AH, nH, s);
+  // dense Cholesky of A_H (a band system of full width) and its inverse
+  BandLayout LH;
+  LH.n = nH;
+  LH.nt = (nH + 31) / 32;
+  LH.w = LH.nt - 1;
+  LH.off = 0;
+  GENEO_CUDA_TRY(cudaMemcpyAsync(pc.d_lay_H, &LH, sizeof(LH), cudaMemcpyHostToDevice, s));
+  if ((st = launch_band_clear<double>(pc.d_lay_H, 1, pc.AHL, (long long)LH.nt * LH.nt * 1024, s))) return st;
+  launch_dense_to_tiles(pc.AH, nH, pc.d_lay_H, pc.AHL, s);
+  if ((st = launch_band_cholesky<double>(pc.d_lay_H, 1, LH.nt, LH.w, pc.AHL, pc.AHU, c->status, s)))
+    return st;
+  launch_identity(pc.AHinv, nH, s);
+  if ((st = launch_band_solve_dense(pc.d_lay_H, 1, LH.nt * 32, pc.AHL, pc.AHU, pc.AHinv, 0, nH,
+                                    pc.AHinv, 0, nH, nH, 3, s)))
+    return st;
+  launch_symmetrize(pc.AHinv, nH, s);
+  GENEO_CUDA_TRY(cudaGetLastError());
+  return GENEO_OK;
+}
+
+extern "C" {
+
+int geneo_setup_workspace_bytes(geneo_ctx *c, const geneo_partition *part,
+                                const geneo_modes *modes, geneo_precision prec, size_t *bytes) {
+  if (!c || !c->assembled) return fail(GENEO_ERR_STATE, "not assembled");
+  if (!bytes) return fail(GENEO_ERR_INVALID_ARG, "null bytes");
+  Precond saved = c->pc;
+  SetupPlan P;
+  c->pc.prec = prec;
+  c->pc.coarse = GENEO_COARSE_GENEO;
+  int st = build_plan(c, part, modes, P);
+  if (st) {
+    c->pc = saved;
+    return st;
+  }
+  Arena A;
+  plan_setup(A, c, P);
+  *bytes = A.off + 256;
+  c->pc = saved;
+  return GENEO_OK;
+}
+
+int geneo_setup(geneo_ctx *c, const geneo_partition *part, const geneo_modes *modes,
+                geneo_precision prec, geneo_schwarz schwarz, geneo_coarse coarse) {
+  if (!c || !c->assembled) return fail(GENEO_ERR_STATE, "not assembled");
+  if (prec != GENEO_FP64 && prec != GENEO_MIXED_FP32) return fail(GENEO_ERR_INVALID_ARG, "bad precision");
+  if (schwarz != GENEO_AS && schwarz != GENEO_AS_POU) return fail(GENEO_ERR_INVALID_ARG, "bad schwarz");
+  if (coarse != GENEO_COARSE_GENEO && coarse != GENEO_COARSE_NONE) return fail(GENEO_ERR_INVALID_ARG, "bad coarse");
+  cudaStream_t s = c->stream;
+  release_setup(c);
+  Precond &pc = c->pc;
+  pc.prec = prec;
+  pc.schwarz = schwarz;
+  pc.coarse = coarse;
+  pc.nH = 0;
+  SetupPlan P;
+  int st;
+  if ((st = build_plan(c, part, modes, P))) return st;
+  Arena M;
+  plan_setup(M, c, P);
+  size_t need = M.off + 256;
+  if (c->ws1_bound) {
+    if (c->ws1_bound_bytes < need) return fail(GENEO_ERR_WORKSPACE_TOO_SMALL, "setup workspace too small");
+    c->ws1 = c->ws1_bound;
+    c->ws1_bytes = c->ws1_bound_bytes;
+    c->ws1_owned = false;
+  } else {
+    GENEO_CUDA_TRY(cudaMalloc(&c->ws1, need));
+    c->ws1_bytes = need;
+    c->ws1_owned = true;
+  }
+  Arena B;
+  B.base = (char *)c->ws1;
+  B.cap = c->ws1_bytes;
+  plan_setup(B, c, P);
+  const bool f32 = prec == GENEO_MIXED_FP32;
+  if (f32) {
+    if ((st = prepare_schwarz_solve<float>(pc.npad_int_max))) return fail(st, "subdomain too large for shared memory");
+  } else {
+    if ((st = prepare_schwarz_solve<double>(pc.npad_int_max))) return fail(st, "subdomain too large for shared memory");
+  }
+  if (pc.mcap > 1 && pc.npad_neu_max * 8 + 16 * 32 * 8 > 227 * 1024)
+    return fail(GENEO_ERR_INVALID_ARG, "subdomain too large for the eigensolver's shared memory");
+  cudaEvent_t ev[4];
+  for (auto &e : ev) GENEO_CUDA_TRY(cudaEventCreate(&e));
+  GENEO_CUDA_TRY(cudaEventRecord(ev[0], s));
+  GENEO_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(DevStatus), s));
+  GENEO_CUDA_TRY(cudaMemcpyAsync(pc.d_subs, P.subs.data(), P.nsub * sizeof(SubDesc), cudaMemcpyHostToDevice, s));
+  GENEO_CUDA_TRY(cudaMemcpyAsync(pc.d_lay_int, P.lay_int.data(), P.nsub * sizeof(BandLayout), cudaMemcpyHostToDevice, s));
+  GENEO_CUDA_TRY(cudaMemcpyAsync(pc.d_lay_neu, P.lay_neu.data(), P.nsub * sizeof(BandLayout), cudaMemcpyHostToDevice, s));
+  GENEO_CUDA_TRY(cudaMemcpyAsync(pc.d_cand, P.cand.data(), P.cand.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  GENEO_CUDA_TRY(cudaMemcpyAsync(pc.d_ecnt, P.ecnt.data(), P.ecnt.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  pc.subs = P.subs;
+  pc.m.assign(P.nsub, 0);
+  pc.lambdas.assign((size_t)P.nsub * pc.mcap, INFINITY);
+  pc.eig_max_res = 0.0;
+  if (pc.mcap > 1) {
+    if ((st = setup_coarse(c, P, s))) return st;
+  }
+  GENEO_CUDA_TRY(cudaEventRecord(ev[1], s));
+  // subdomain factors A_j = L_j L_j^T
+  const int nnx = c->nx + 1, nny = c->ny + 1, nnz = c->nz + 1;
+  if (f32) {
+    float *L = (float *)pc.facL, *U = (float *)pc.facU;
+    if ((st = launch_band_clear<float>(pc.d_lay_int, P.nsub, L, pc.fac_int_elems, s))) return st;
+    if ((st = launch_extract_interior<float>(pc.d_subs, pc.d_lay_int, P.nsub, P.max_nodes_int, nnx,
+                                             nny, nnz, c->row_ptr, c->val, L, s)))
+      return st;
+    if ((st = launch_band_cholesky<float>(pc.d_lay_int, P.nsub, pc.nt_int_max, pc.w_int_max, L, U,
+                                          c->status, s)))
+      return st;
+  } else {
+    double *L = (double *)pc.facL, *U = (double *)pc.facU;
+    if ((st = launch_band_clear<double>(pc.d_lay_int, P.nsub, L, pc.fac_int_elems, s))) return st;
+    if ((st = launch_extract_interior<double>(pc.d_subs, pc.d_lay_int, P.nsub, P.max_nodes_int,
+                                              nnx, nny, nnz, c->row_ptr, c->val, L, s)))
+      return st;
+    if ((st = launch_band_cholesky<double>(pc.d_lay_int, P.nsub, pc.nt_int_max, pc.w_int_max, L,
+                                           U, c->status, s)))
+      return st;
+  }
+  GENEO_CUDA_TRY(cudaEventRecord(ev[2], s));
+  int where = -1;
+  st = check_status(c, &where);
+  if (st) {
+    c->last_stats.failed_subdomain = where;
+    return st;
+  }
+  GENEO_CUDA_TRY(cudaEventElapsedTime(&pc.ms_eig, ev[0], ev[1]));
+  GENEO_CUDA_TRY(cudaEventElapsedTime(&pc.ms_factor, ev[1], ev[2]));
+  pc.ms_coarse = 0.f;
+  for (auto &e : ev) cudaEventDestroy(e);
+  // algorithmic bytes of one preconditioner application
+  double esz = f32 ? 4.0 : 8.0, bytes = 0.0;
+  for (const SubDesc &S : P.subs) {
+    bytes += 2.0 * (double)S.nt_int * (S.w_int + 1) * 1024 * esz;   // L and U tile streams
+    bytes += (double)S.n_int * (8.0 + 2.0 * esz);                   // gather r, write/read x_j
+    bytes += 2.0 * (double)S.n_int * S.m * 8.0;                     // Z^T r and Z y
+  }
+  bytes += (double)pc.nH * pc.nH * 8.0 + 8.0 * c->ndof;             // A_H^-1 y, write z
+  pc.bytes_per_apply = bytes;
+  c->setup_done = true;
+  return GENEO_OK;
+}
+
+int geneo_apply_preconditioner(geneo_ctx *c, const double *r, double *z) {
+  if (!c || !c->setup_done) return fail(GENEO_ERR_STATE, "no preconditioner set up");
+  if (!r || !z) return fail(GENEO_ERR_INVALID_ARG, "null vector");
+  cudaStream_t s = c->stream;
+  int st;
+  if ((st = stage(c->tmp, r, c->ndof, s))) return st;
+  if ((st = precond_apply(c, c->tmp, c->z, nullptr, s))) return st;
+  return unstage(z, c->z, c->ndof, s);
+}
+
+int geneo_coarse_info(geneo_ctx *c, int *n_subdomains, int *n_coarse, int32_t *modes,
+                      double *lambdas) {
+  if (!c || !c->setup_done) return fail(GENEO_ERR_STATE, "no preconditioner set up");
+  const Precond &pc = c->pc;
+  if (n_subdomains) *n_subdomains = pc.nsub;
+  if (n_coarse) *n_coarse = pc.nH;
+  if (modes)
+    for (int j = 0; j < pc.nsub; ++j) modes[j] = pc.m[j];
+  if (lambdas) {
+    int cap = (pc.modes.fixed_modes > 0 ? pc.modes.fixed_modes : pc.modes.max_modes) + 1;
+    for (int j = 0; j < pc.nsub; ++j)
+      for (int i = 0; i < cap; ++i)
+        lambdas[(size_t)j * cap + i] = (i < pc.mcap && !pc.lambdas.empty())
+                                           ? pc.lambdas[(size_t)j * pc.mcap + i]
+                                           : INFINITY;
+  }
+  return GENEO_OK;
+}
+
+int geneo_get_coarse(geneo_ctx *c, double *Phi, double *AH) {
+  if (!c || !c->setup_done) return fail(GENEO_ERR_STATE, "no preconditioner set up");
+  const Precond &pc = c->pc;
+  const int nH = pc.nH;
+  if (nH == 0) return GENEO_OK;
+  cudaStream_t s = c->stream;
+  if (Phi) {
+    // expand Z_j (interior rows) into dense global columns on the host
+    std::vector<double> z(pc.z_elems);
+    GENEO_CUDA_TRY(cudaMemcpyAsync(z.data(), pc.Zp, z.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    GENEO_CUDA_TRY(cudaStreamSynchronize(s));
+    std::vector<double> out((size_t)c->ndof * nH, 0.0);
+    const int nnx = c->nx + 1, nny = c->ny + 1;
+    for (const SubDesc &S : pc.subs) {
+      for (int l = 0; l < S.n_int; ++l) {
+        int node = l / 3, comp = l % 3, gi, gj, gk;
+        S.ibox.global(node, gi, gj, gk);
+        long long dof = 3LL * (gi + nnx * (gj + nny * gk)) + comp;
+        for (int k = 0; k < S.m; ++k)
+          out[(size_t)(S.coff + k) * c->ndof + dof] = z[S.z_off + (long long)l * S.m + k];
+      }
+    }
+    if (is_device_ptr(Phi)) {
+      GENEO_CUDA_TRY(cudaMemcpy(Phi, out.data(), out.size() * sizeof(double), cudaMemcpyHostToDevice));
+    } else {
+      std::memcpy(Phi, out.data(), out.size() * sizeof(double));
+    }
+  }
+  if (AH) {
+    int st = unstage(AH, pc.AH, (size_t)nH * nH, s);
+    if (st) return st;
+  }
+  return GENEO_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================
+// Solve
+namespace {
+
+// Eigenvalue bounds of the CG Lanczos tridiagonal (Sturm bisection).
+double kappa_from_cg(const std::vector<double> &al, const std::vector<double> &be) {
+  int k = (int)al.size();
+  if (k == 0) return 0.0;
+  std::vector<double> d(k), e(k, 0.0);
+  for (int i = 0; i < k; ++i) {
+    d[i] = 1.0 / al[i] + (i > 0 ? be[i - 1] / al[i - 1] : 0.0);
+    if (i < k - 1) e[i] = std::sqrt(std::max(be[i], 0.0)) / al[i];
+  }
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < k; ++i) {
+    double r = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i < k - 1 ? std::fabs(e[i]) : 0.0);
+    lo = std::min(lo, d[i] - r);
+    hi = std::max(hi, d[i] + r);
+  }
+  auto count_below = [&](double x) {
+    int cnt = 0;
+    double q = d[0] - x;
+    if (q < 0) ++cnt;
+    for (int i = 1; i < k; ++i) {
+      double qq = (q == 0.0) ? 1e-300 : q;
+      q = d[i] - x - e[i - 1] * e[i - 1] / qq;
+      if (q < 0) ++cnt;
+    }
+    return cnt;
+  };
+  auto kth = [&](int idx) {
+    double a = lo, b = hi;
+    for (int it = 0; it < 200; ++it) {
+      double m = 0.5 * (a + b);
+      if (count_below(m) > idx) b = m;
+      else a = m;
+    }
+    return 0.5 * (a + b);
+  };
+  double emin = kth(0), emax = kth(k - 1);
+  return emin > 0 ? emax / emin : 0.0;
+}
+
+int enqueue_iterations(geneo_ctx *c, int iters, cudaStream_t s) {
+  BSR A{c->nnode, c->row_ptr, c->col, c->val};
+  const int n = c->ndof;
+  int st;
+  for (int it = 0; it < iters; ++it) {
+    launch_cg_spmv_pq(A, c->p, c->q, c->cg, c->part, s);
+    launch_cg_update_xr(n, c->p, c->q, c->x, c->r, c->cg, c->part, c->alphas, s);
+    if (c->setup_done) {
+      if ((st = precond_apply(c, c->r, c->z, c->cg, s))) return st;
+    } else {
+      launch_copy_if_running(n, c->r, c->z, c->cg, s);
+    }
+    launch_cg_dots(n, c->r, c->z, c->q, c->cg, c->part, c->betas, s);
+    launch_cg_update_p(n, c->z, c->p, c->cg, s);
+  }
+  GENEO_CUDA_TRY(cudaGetLastError());
+  return GENEO_OK;
+}
+
+}  // namespace
+
+extern "C" int geneo_solve(geneo_ctx *c, double tol, int max_it, double *u, geneo_stats *stats) {
+  if (!c || !c->assembled) return fail(GENEO_ERR_STATE, "not assembled");
+  if (!c->setup_done) return fail(GENEO_ERR_STATE, "call geneo_setup first");
+  if (!u || !(tol > 0.0) || max_it < 1) return fail(GENEO_ERR_INVALID_ARG, "bad solve arguments");
+  cudaStream_t s = c->stream;
+  const int n = c->ndof;
+  const Precond &pc = c->pc;
+  const bool flexible = pc.prec == GENEO_MIXED_FP32 || pc.schwarz == GENEO_AS_POU;
+  CGScalars h{};
+  h.tol2 = tol * tol;
+  h.maxit = std::min(max_it, kHistCap);
+  h.flexible = flexible ? 1 : 0;
+  *c->cg_host = h;
+  cudaEvent_t e0, e1;
+  GENEO_CUDA_TRY(cudaEventCreate(&e0));
+  GENEO_CUDA_TRY(cudaEventCreate(&e1));
+  GENEO_CUDA_TRY(cudaEventRecord(e0, s));
+  GENEO_CUDA_TRY(cudaMemcpyAsync(c->cg, c->cg_host, sizeof(CGScalars), cudaMemcpyHostToDevice, s));
+  launch_cg_init(n, c->b, c->x, c->r, c->cg, c->part, s);
+  int st;
+  if ((st = precond_apply(c, c->r, c->z, c->cg, s))) return st;
+  launch_cg_init2(n, c->r, c->z, c->p, c->cg, c->part, s);
+  GENEO_CUDA_TRY(cudaGetLastError());
+  if (!c->graph) {
+    cudaGraph_t g;
+    GENEO_CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    st = enqueue_iterations(c, kGraphIters, c->cap_stream);
+    cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &g);
+    if (st) return st;
+    if (ce != cudaSuccess) {
+      geneo_set_last_cuda_error(ce, "cudaStreamEndCapture", __FILE__, __LINE__);
+      return GENEO_ERR_CUDA;
+    }
+    GENEO_CUDA_TRY(cudaGraphInstantiate(&c->graph, g, 0));
+    cudaGraphDestroy(g);
+  }
+  int launched = 0;
+  for (;;) {
+    GENEO_CUDA_TRY(cudaGraphLaunch(c->graph, s));
+    launched += kGraphIters;
+    GENEO_CUDA_TRY(cudaMemcpyAsync(c->cg_host, c->cg, sizeof(CGScalars), cudaMemcpyDeviceToHost, s));
+    GENEO_CUDA_TRY(cudaStreamSynchronize(s));
+    if (c->cg_host->done) break;
+    if (launched > h.maxit + 2 * kGraphIters) break;
+  }
+  GENEO_CUDA_TRY(cudaEventRecord(e1, s));
+  h = *c->cg_host;
+  // true residual ||b - A x|| / ||b||
+  BSR A{c->nnode, c->row_ptr, c->col, c->val};
+  launch_spmv(A, c->x, c->tmp, s);
+  launch_sub(n, c->b, c->tmp, c->tmp, s);
+  launch_norm2(n, c->tmp, c->scal, c->part, &c->cg->counter, s);
+  double rt2 = 0.0;
+  GENEO_CUDA_TRY(cudaMemcpyAsync(&rt2, c->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+  if ((st = unstage(u, c->x, n, s))) return st;
+  float ms = 0.f;
+  GENEO_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  geneo_stats out{};
+  out.iterations = h.it;
+  out.rel_res_recursive = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
+  out.rel_res_true = h.bb > 0 ? std::sqrt(rt2 / h.bb) : 0.0;
+  out.n_coarse = pc.nH;
+  out.n_subdomains = pc.nsub;
+  out.ms_assemble = c->ms_assemble;
+  out.ms_setup_eig = pc.ms_eig;
+  out.ms_setup_coarse = pc.ms_coarse;
+  out.ms_setup_factor = pc.ms_factor;
+  out.ms_solve = ms;
+  double spmv_bytes = (double)c->nnzb * 76.0 + 16.0 * n + 4.0 * (c->nnode + 1);
+  out.bytes_per_iter = spmv_bytes + pc.bytes_per_apply + 12.0 * 8.0 * n;
+  out.eig_max_residual = pc.eig_max_res;
+  out.failed_subdomain = -1;
+  out.flexible = flexible ? 1 : 0;
+  if (!flexible && h.it > 0) {
+    int k = std::min(h.it, kHistCap);
+    std::vector<double> al(k), be(std::max(k - 1, 0));
+    GENEO_CUDA_TRY(cudaMemcpy(al.data(), c->alphas, k * sizeof(double), cudaMemcpyDeviceToHost));
+    if (k > 1) GENEO_CUDA_TRY(cudaMemcpy(be.data(), c->betas, (k - 1) * sizeof(double), cudaMemcpyDeviceToHost));
+    out.kappa_est = kappa_from_cg(al, be);
+  }
+  c->last_stats = out;
+  if (stats) *stats = out;
+  if (h.done == 2) return fail(GENEO_ERR_CG_BREAKDOWN, "CG breakdown");
+  if (h.done != 1) return fail(GENEO_ERR_NOT_CONVERGED, "max_it reached");
+  return GENEO_OK;
+}

@@ -1,0 +1,734 @@
+// GenEO coarse space on the device (Sec. 3.2, Sec. 3.3.1-3.3.3).
+//
+// Per subdomain j the generalised eigenproblem (eqm:matrixForm)
+//   A_{Omega_j} p = lambda X_j A_{Omega_j^o} X_j p
+// is solved with the shift-and-invert transformation the paper uses
+// (Sec. 3.3.2): S = A - sigma B = L L^T for a small sigma < 0, and the
+// symmetric operator C = L^-1 B L^-T has eigenvalues mu = 1 / (lambda - sigma),
+// so the wanted smallest lambda are the largest mu.  Instead of ARPACK's
+// implicitly restarted Lanczos, a block Lanczos process (block size 8, full
+// re-orthogonalisation, Cholesky-QR) runs batched over all subdomains and the
+// projected matrix is diagonalised by a cyclic Jacobi method; p = L^-T y.
+#include "geneo.cuh"
+#include "fem.cuh"
+
+namespace geneo {
+
+namespace {
+
+__device__ __forceinline__ double *tile_at(double *pool, const BandLayout &L, int I, int d) {
+  return pool + L.off + (((long long)I * (L.w + 1) + d) << 10);
+}
+
+__device__ __forceinline__ int cand_count(const int *c) {
+  int n = 0;
+  while (n < kMaxCand && c[n] >= 0) ++n;
+  return n;
+}
+
+__global__ void k_pou_neumann(const SubDesc *subs, const int *cand, int co0, int co1, int co2,
+                              const uint8_t *mask, int nnx, int nny, double *Xneu) {
+  const int j = blockIdx.y;
+  const SubDesc &S = subs[j];
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * S.nbox.count()) return;
+  int l = t / 3, comp = t - 3 * l;
+  int gi, gj, gk;
+  S.nbox.global(l, gi, gj, gk);
+  double x = 0.0;
+  if (S.ibox.local(gi, gj, gk) >= 0) {
+    int mu = cand_count(cand + (co0 + gi) * kMaxCand) * cand_count(cand + (co1 + gj) * kMaxCand) *
+             cand_count(cand + (co2 + gk) * kMaxCand);
+    x = 1.0 / double(mu);
+    if (mask[3 * (gi + nnx * (gj + nny * gk)) + comp]) x = 0.0;
+  }
+  Xneu[S.x_neu + t] = x;
+}
+
+__global__ void __launch_bounds__(128)
+    k_neumann_assemble(const SubDesc *subs, const BandLayout *lay, int nx, int ny, int nz,
+                       const double *__restrict__ X, const double *__restrict__ Y,
+                       const double *__restrict__ Z, const double *__restrict__ Cel,
+                       const int *__restrict__ ecnt, int eo0, int eo1, int eo2,
+                       const uint8_t *__restrict__ mask, const double *__restrict__ Xneu,
+                       double sigma, double *poolS, double *Bloc) {
+  const int j = blockIdx.y;
+  const SubDesc &S = subs[j];
+  const int nn = S.nbox.count();
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)nn * 27) return;
+  const int l = (int)(t / 27), s = (int)(t % 27);
+  int gi, gj, gk;
+  S.nbox.global(l, gi, gj, gk);
+  const int i2 = gi + s % 3 - 1, j2 = gj + (s / 3) % 3 - 1, k2 = gk + s / 9 - 1;
+  const int l2 = S.nbox.local(i2, j2, k2);
+  double *bl = Bloc + (S.b_neu + (long long)l * 27 + s) * 9;
+  if (l2 < 0) {
+    for (int q = 0; q < 9; ++q) bl[q] = 0.0;
+    return;
+  }
+  double KA[9], KO[9];
+  for (int q = 0; q < 9; ++q) KA[q] = KO[q] = 0.0;
+  for (int ez = max(max(gk, k2) - 1, S.elo[2]); ez <= min(min(gk, k2), S.ehi[2] - 1); ++ez)
+    for (int ey = max(max(gj, j2) - 1, S.elo[1]); ey <= min(min(gj, j2), S.ehi[1] - 1); ++ey)
+      for (int ex = max(max(gi, i2) - 1, S.elo[0]); ex <= min(min(gi, i2), S.ehi[0] - 1); ++ex) {
+        int e = ex + nx * (ey + ny * ez);
+        int a = (gi - ex) + 2 * (gj - ey) + 4 * (gk - ez);
+        int b = (i2 - ex) + 2 * (j2 - ey) + 4 * (k2 - ez);
+        double Kb[9];
+        element_block(Cel + 36 * (size_t)e, X[ex + 1] - X[ex], Y[ey + 1] - Y[ey], Z[ez + 1] - Z[ez],
+                      a, b, Kb);
+        bool ov = ecnt[eo0 + ex] * ecnt[eo1 + ey] * ecnt[eo2 + ez] >= 2;
+        for (int q = 0; q < 9; ++q) {
+          KA[q] += Kb[q];
+          if (ov) KO[q] += Kb[q];
+        }
+      }
+  const int nnx = nx + 1, nny = ny + 1;
+  const int g = gi + nnx * (gj + nny * gk), g2 = i2 + nnx * (j2 + nny * k2);
+  const BandLayout L = lay[j];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      int rd = 3 * g + r, cd = 3 * g2 + c;
+      double a = KA[3 * r + c], o = KO[3 * r + c];
+      if (mask[rd] || mask[cd]) {
+        a = (rd == cd) ? 1.0 : 0.0;
+        o = 0.0;
+      }
+      double bv = Xneu[S.x_neu + 3 * l + r] * o * Xneu[S.x_neu + 3 * l2 + c];
+      bl[3 * r + c] = bv;
+      int R = 3 * l + r, C = 3 * l2 + c;
+      if (R >= C) tile_at(poolS, L, R >> 5, (R >> 5) - (C >> 5))[(C & 31) * 32 + (R & 31)] = a - sigma * bv;
+    }
+}
+
+__global__ void k_bloc_mv(const SubDesc *subs, const double *__restrict__ Bloc,
+                          const double *__restrict__ T, double *__restrict__ W,
+                          long long stride, int p) {
+  const int j = blockIdx.y;
+  const SubDesc &S = subs[j];
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * S.nbox.count()) return;
+  int l = t / 3, r = t - 3 * l;
+  int gi, gj, gk;
+  S.nbox.global(l, gi, gj, gk);
+  double acc[kLanczosBlock];
+#pragma unroll
+  for (int q = 0; q < kLanczosBlock; ++q) acc[q] = 0.0;
+  const double *Tj = T + j * stride;
+  for (int s = 0; s < 27; ++s) {
+    int l2 = S.nbox.local(gi + s % 3 - 1, gj + (s / 3) % 3 - 1, gk + s / 9 - 1);
+    if (l2 < 0) continue;
+    const double *bl = Bloc + (S.b_neu + (long long)l * 27 + s) * 9 + 3 * r;
+    for (int c = 0; c < 3; ++c) {
+      double bv = bl[c];
+      if (bv == 0.0) continue;
+      const double *tr = Tj + (long long)(3 * l2 + c) * p;
+#pragma unroll
+      for (int q = 0; q < kLanczosBlock; ++q)
+        if (q < p) acc[q] += bv * tr[q];
+    }
+  }
+  double *wr = W + j * stride + (long long)t * p;
+#pragma unroll
+  for (int q = 0; q < kLanczosBlock; ++q)
+    if (q < p) wr[q] = acc[q];
+}
+
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+__global__ void k_random_block(const SubDesc *subs, int npad, double *V, int ld, long long stride,
+                               int p, unsigned long long seed) {
+  const int j = blockIdx.y;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= npad * p) return;
+  int row = t / p, c = t - row * p;
+  double v = 0.0;
+  if (row < subs[j].n_neu) {
+    unsigned long long h = splitmix64(seed ^ splitmix64(((unsigned long long)j << 40) ^
+                                                        ((unsigned long long)row << 8) ^ c));
+    v = double(h >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+  }
+  V[j * stride + (long long)row * ld + c] = v;
+}
+
+// partial dot products over a chunk of rows, staged 16 rows at a time
+__global__ void __launch_bounds__(256)
+    k_tsdots(const SubDesc *subs, const double *__restrict__ A, int lda, long long sa, int na,
+             const double *__restrict__ B, int ldb, long long sb, int nb, double *Hpart,
+             int chunks) {
+  const int j = blockIdx.y, ch = blockIdx.x;
+  const int n = subs[j].n_neu;
+  const int per = (n + chunks - 1) / chunks;
+  const int r0 = ch * per, r1 = min(n, r0 + per);
+  const int nout = na * nb;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double *sA = reinterpret_cast<double *>(smraw);     // [16][na]
+  double *sB = sA + 16 * na;                          // [16][nb]
+  double acc[5] = {0, 0, 0, 0, 0};
+  const double *Aj = A + j * sa;
+  const double *Bj = B + j * sb;
+  for (int rb = r0; rb < r1; rb += 16) {
+    int nr = min(16, r1 - rb);
+    for (int e = threadIdx.x; e < 16 * na; e += 256) {
+      int rr = e / na, c = e - rr * na;
+      sA[e] = rr < nr ? Aj[(long long)(rb + rr) * lda + c] : 0.0;
+    }
+    for (int e = threadIdx.x; e < 16 * nb; e += 256) {
+      int rr = e / nb, c = e - rr * nb;
+      sB[e] = rr < nr ? Bj[(long long)(rb + rr) * ldb + c] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      int o = threadIdx.x + 256 * q;
+      if (o < nout) {
+        int a = o / nb, b = o - a * nb;
+        double s = 0.0;
+        for (int rr = 0; rr < 16; ++rr) s += sA[rr * na + a] * sB[rr * nb + b];
+        acc[q] += s;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    int o = threadIdx.x + 256 * q;
+    if (o < nout) Hpart[((long long)j * chunks + ch) * nout + o] = acc[q];
+  }
+}
+
+__global__ void k_tsdots_reduce(const double *Hpart, int chunks, int nout, double *H, long long hs) {
+  const int j = blockIdx.x;
+  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+    double s = 0.0;
+    for (int ch = 0; ch < chunks; ++ch) s += Hpart[((long long)j * chunks + ch) * nout + o];
+    H[j * hs + o] = s;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    k_tsgemm(const SubDesc *subs, int npad, const double *__restrict__ A, int lda, long long sa,
+             int na, const double *__restrict__ H, int ldh, long long hs, double *C, int ldc,
+             long long sc, int nb, double alpha, double beta) {
+  const int j = blockIdx.y;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double *sH = reinterpret_cast<double *>(smraw);   // [na][nb]
+  for (int e = threadIdx.x; e < na * nb; e += blockDim.x) {
+    int a = e / nb, b = e - a * nb;
+    sH[e] = H[j * hs + (long long)a * ldh + b];
+  }
+  __syncthreads();
+  const int n = subs[j].n_neu;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)npad * nb) return;
+  int row = (int)(t / nb), b = (int)(t - (long long)row * nb);
+  double *cp = C + j * sc + (long long)row * ldc + b;
+  if (row >= n) {
+    if (beta == 0.0) *cp = 0.0;
+    return;
+  }
+  const double *ar = A + j * sa + (long long)row * lda;
+  double s = 0.0;
+  for (int a = 0; a < na; ++a) s += ar[a] * sH[a * nb + b];
+  *cp = (beta == 0.0 ? 0.0 : beta * *cp) + alpha * s;
+}
+
+// Cholesky of the p x p Gram matrix, inverse, and Racc update (one block per subdomain)
+__global__ void k_cholqr_small(const double *G, int p, double *Rinv, double *Racc, int first) {
+  const int j = blockIdx.x;
+  __shared__ double R[kLanczosBlock][kLanczosBlock];
+  __shared__ double Ri[kLanczosBlock][kLanczosBlock];
+  __shared__ double Ra[kLanczosBlock][kLanczosBlock];
+  if (threadIdx.x == 0) {
+    const double *g = G + (long long)j * p * p;
+    for (int a = 0; a < p; ++a)
+      for (int b = 0; b < p; ++b) R[a][b] = 0.0;
+    // upper factor R with G = R^T R; dead columns get R[k][k] = 0
+    for (int k = 0; k < p; ++k) {
+      double d = g[k * p + k];
+      for (int i = 0; i < k; ++i) d -= R[i][k] * R[i][k];
+      bool dead = !(d > 1e-200);
+      double rk = dead ? 0.0 : sqrt(d);
+      R[k][k] = rk;
+      for (int c = k + 1; c < p; ++c) {
+        double v = g[k * p + c];
+        for (int i = 0; i < k; ++i) v -= R[i][k] * R[i][c];
+        R[k][c] = dead ? 0.0 : v / rk;
+      }
+    }
+    // Rinv (upper); a dead column maps to zero
+    for (int c = 0; c < p; ++c) {
+      for (int a = p - 1; a >= 0; --a) {
+        if (a > c) {
+          Ri[a][c] = 0.0;
+          continue;
+        }
+        if (R[a][a] == 0.0) {
+          Ri[a][c] = 0.0;
+          continue;
+        }
+        double s = (a == c) ? 1.0 : 0.0;
+        for (int k = a + 1; k <= c; ++k) s -= R[a][k] * Ri[k][c];
+        Ri[a][c] = s / R[a][a];
+      }
+    }
+    double *racc = Racc + (long long)j * p * p;
+    for (int a = 0; a < p; ++a)
+      for (int b = 0; b < p; ++b) {
+        double s;
+        if (first) {
+          s = R[a][b];
+        } else {
+          s = 0.0;
+          for (int k = 0; k < p; ++k) s += R[a][k] * racc[k * p + b];
+        }
+        Ra[a][b] = s;
+      }
+    for (int a = 0; a < p; ++a)
+      for (int b = 0; b < p; ++b) {
+        racc[a * p + b] = Ra[a][b];
+        Rinv[(long long)j * p * p + a * p + b] = Ri[a][b];
+      }
+  }
+}
+
+__global__ void k_rowmul(const SubDesc *subs, int npad, double *W, int p, const double *Rinv) {
+  const int j = blockIdx.y;
+  int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= npad) return;
+  double *w = W + ((long long)j * npad + row) * p;
+  const double *ri = Rinv + (long long)j * p * p;
+  double in[kLanczosBlock];
+  for (int q = 0; q < p; ++q) in[q] = w[q];
+  for (int b = 0; b < p; ++b) {
+    double s = 0.0;
+    for (int a = 0; a <= b; ++a) s += in[a] * ri[a * p + b];
+    w[b] = row < subs[j].n_neu ? s : 0.0;
+  }
+}
+
+__global__ void k_hm_accum(double *Hm, int kdim, const double *Hs, int rows, int k, int p) {
+  const int j = blockIdx.x;
+  for (int e = threadIdx.x; e < rows * p; e += blockDim.x) {
+    int r = e / p, b = e - r * p;
+    Hm[(long long)j * kdim * kdim + (long long)r * kdim + k * p + b] +=
+        Hs[(long long)j * rows * p + e];
+  }
+}
+
+__global__ void k_hm_subdiag(double *Hm, int kdim, const double *Racc, int k, int p,
+                             double *Rblk) {
+  const int j = blockIdx.x;
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    int a = e / p, b = e - a * p;
+    double v = Racc[(long long)j * p * p + e];
+    if ((k + 1) * p < kdim)
+      Hm[(long long)j * kdim * kdim + (long long)((k + 1) * p + a) * kdim + k * p + b] = v;
+    else
+      Rblk[(long long)j * p * p + e] = v;
+  }
+}
+
+__global__ void k_copy_block(const SubDesc *subs, int npad, const double *W, int ldw,
+                             long long sw, double *V, int ldv, long long sv, int p) {
+  const int j = blockIdx.y;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= npad * p) return;
+  int row = t / p, b = t - row * p;
+  V[j * sv + (long long)row * ldv + b] = W[j * sw + (long long)row * ldw + b];
+}
+
+// Cyclic Jacobi (round-robin ordering) on the symmetrised projected matrix.
+__global__ void __launch_bounds__(256)
+    k_jacobi(const double *Hm, int n, int p, const double *Rblk, double *Eval, double *Evec,
+             double *Ework, double *Eres) {
+  const int j = blockIdx.x;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double *A = reinterpret_cast<double *>(smraw);            // n x n
+  double *cs = A + n * n;                                   // n/2
+  double *sn = cs + n / 2;
+  int *pp = reinterpret_cast<int *>(sn + n / 2);
+  int *qq = pp + n / 2;
+  __shared__ double red[8];
+  __shared__ int stop;
+  double *E = Ework + (long long)j * n * n;
+  const double *H = Hm + (long long)j * n * n;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    int r = e / n, c = e - r * n;
+    A[e] = 0.5 * (H[e] + H[c * n + r]);
+    E[e] = (r == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int half = n / 2;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    // convergence test: off-diagonal vs total Frobenius norm
+    double off = 0.0, tot = 0.0;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      int r = e / n, c = e - r * n;
+      double v = A[e] * A[e];
+      tot += v;
+      if (r != c) off += v;
+    }
+    off = warp_sum(off);
+    tot = warp_sum(tot);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = off;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double o = 0.0;
+      for (int w = 0; w < 8; ++w) o += red[w];
+      red[0] = o;
+    }
+    __syncthreads();
+    off = red[0];
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tot;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t2 = 0.0;
+      for (int w = 0; w < 8; ++w) t2 += red[w];
+      stop = !(off > 1e-32 * t2) ? 1 : 0;
+    }
+    __syncthreads();
+    if (stop) break;
+    for (int round = 0; round < n - 1; ++round) {
+      for (int i = threadIdx.x; i < half; i += blockDim.x) {
+        int a = (i == 0) ? n - 1 : (round + i) % (n - 1);
+        int b = (round - i + n - 1) % (n - 1);
+        int P = min(a, b), Q = max(a, b);
+        double apq = A[P * n + Q];
+        double c = 1.0, s = 0.0;
+        if (apq != 0.0) {
+          double tau = (A[Q * n + Q] - A[P * n + P]) / (2.0 * apq);
+          double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          c = 1.0 / sqrt(1.0 + t * t);
+          s = t * c;
+        }
+        cs[i] = c;
+        sn[i] = s;
+        pp[i] = P;
+        qq[i] = Q;
+      }
+      __syncthreads();
+      // columns: A <- A J
+      for (int e = threadIdx.x; e < half * n; e += blockDim.x) {
+        int i = e / n, r = e - i * n;
+        int P = pp[i], Q = qq[i];
+        double c = cs[i], s = sn[i];
+        double ap = A[r * n + P], aq = A[r * n + Q];
+        A[r * n + P] = c * ap - s * aq;
+        A[r * n + Q] = s * ap + c * aq;
+        double ep = E[r * n + P], eq = E[r * n + Q];
+        E[r * n + P] = c * ep - s * eq;
+        E[r * n + Q] = s * ep + c * eq;
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (int e = threadIdx.x; e < half * n; e += blockDim.x) {
+        int i = e / n, cc = e - i * n;
+        int P = pp[i], Q = qq[i];
+        double c = cs[i], s = sn[i];
+        double ap = A[P * n + cc], aq = A[Q * n + cc];
+        A[P * n + cc] = c * ap - s * aq;
+        A[Q * n + cc] = s * ap + c * aq;
+      }
+      __syncthreads();
+    }
+  }
+  // sort eigenvalues descending (selection order by rank)
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double v = A[i * n + i];
+    int rank = 0;
+    for (int k = 0; k < n; ++k) {
+      double u = A[k * n + k];
+      rank += (u > v) || (u == v && k < i);
+    }
+    pp[rank] = i;   // reuse: pp[rank] = column index
+  }
+  __syncthreads();
+  double *out = Evec + (long long)j * n * n;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    int r = e / n, c = e - r * n;
+    out[e] = E[r * n + pp[c]];
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) Eval[(long long)j * n + i] = A[pp[i] * n + pp[i]];
+  __syncthreads();
+  // residual estimate || R_s * E[(s-1)p : sp, i] ||
+  const double *Rb = Rblk + (long long)j * p * p;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double s2 = 0.0;
+    for (int a = 0; a < p; ++a) {
+      double v = 0.0;
+      for (int b = 0; b < p; ++b) v += Rb[a * p + b] * out[(long long)(n - p + b) * n + i];
+      s2 += v * v;
+    }
+    Eres[(long long)j * n + i] = sqrt(s2);
+  }
+}
+
+__global__ void k_build_Z(const SubDesc *subs, const double *P, int ldp, long long sp,
+                          const double *Xneu, double *Zp) {
+  const int j = blockIdx.y;
+  const SubDesc &S = subs[j];
+  if (S.m == 0) return;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)S.n_int * S.m) return;
+  int row = (int)(t / S.m), k = (int)(t - (long long)row * S.m);
+  int node = row / 3, comp = row - 3 * node;
+  int gi, gj, gk;
+  S.ibox.global(node, gi, gj, gk);
+  int ln = S.nbox.local(gi, gj, gk);
+  int nd = 3 * ln + comp;
+  Zp[S.z_off + t] = Xneu[S.x_neu + nd] * P[j * sp + (long long)nd * ldp + k];
+}
+
+__global__ void k_AZ(const SubDesc *subs, int nnx, int nny, int nnz, const int32_t *__restrict__ rp,
+                     const int32_t *__restrict__ col, const double *__restrict__ val,
+                     const double *__restrict__ Zp, const long long *yoff, double *Yp) {
+  const int j = blockIdx.y;
+  const SubDesc &S = subs[j];
+  const int m = S.m;
+  if (m == 0) return;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * S.nbox.count()) return;
+  int l = t / 3, r = t - 3 * l;
+  int gi, gj, gk;
+  S.nbox.global(l, gi, gj, gk);
+  int g = gi + nnx * (gj + nny * gk);
+  double acc[kMaxModes];
+#pragma unroll
+  for (int q = 0; q < kMaxModes; ++q) acc[q] = 0.0;
+  for (int pidx = rp[g]; pidx < rp[g + 1]; ++pidx) {
+    int g2 = col[pidx];
+    int i2 = g2 % nnx, rr = g2 / nnx, j2 = rr % nny, k2 = rr / nny;
+    int l2 = S.ibox.local(i2, j2, k2);
+    if (l2 < 0) continue;
+    for (int c = 0; c < 3; ++c) {
+      double a = val[9 * (size_t)pidx + 3 * r + c];
+      const double *zr = Zp + S.z_off + (long long)(3 * l2 + c) * m;
+#pragma unroll
+      for (int q = 0; q < kMaxModes; ++q)
+        if (q < m) acc[q] += a * zr[q];
+    }
+  }
+  double *yr = Yp + yoff[j] + (long long)t * m;
+#pragma unroll
+  for (int q = 0; q < kMaxModes; ++q)
+    if (q < m) yr[q] = acc[q];
+}
+
+__global__ void __launch_bounds__(256)
+    k_coarse_blocks(const SubDesc *subs, const int2 *pairs, const double *__restrict__ Zp,
+                    const double *__restrict__ Yp, const long long *yoff, double *AH, int nH) {
+  const int2 pr = pairs[blockIdx.x];
+  const SubDesc &Sj = subs[pr.x];
+  const SubDesc &Sk = subs[pr.y];
+  const int mj = Sj.m, mk = Sk.m;
+  int lo[3], hi[3];
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = max(Sj.ibox.lo[d], Sk.nbox.lo[d]);
+    hi[d] = min(Sj.ibox.lo[d] + Sj.ibox.n[d], Sk.nbox.lo[d] + Sk.nbox.n[d]);
+  }
+  const int ex = hi[0] - lo[0], ey = hi[1] - lo[1], ez = hi[2] - lo[2];
+  const int nout = mj * mk;
+  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+    int a = o / mk, b = o - a * mk;
+    double s = 0.0;
+    if (ex > 0 && ey > 0 && ez > 0) {
+      for (int q = 0; q < ex * ey * ez; ++q) {
+        int ii = lo[0] + q % ex, rr = q / ex, jj = lo[1] + rr % ey, kk = lo[2] + rr / ey;
+        int lj = Sj.ibox.local(ii, jj, kk), lk = Sk.nbox.local(ii, jj, kk);
+        for (int c = 0; c < 3; ++c)
+          s += Zp[Sj.z_off + (long long)(3 * lj + c) * mj + a] *
+               Yp[yoff[pr.y] + (long long)(3 * lk + c) * mk + b];
+      }
+    }
+    AH[(long long)(Sj.coff + a) * nH + Sk.coff + b] = s;
+    if (pr.x != pr.y) AH[(long long)(Sk.coff + b) * nH + Sj.coff + a] = s;
+  }
+}
+
+__global__ void k_dense_to_tiles(const double *AH, int n, const BandLayout *lay, double *pool) {
+  const BandLayout L = lay[0];
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n * n) return;
+  int R = (int)(t / n), C = (int)(t - (long long)R * n);
+  if (R < C) return;
+  tile_at(pool, L, R >> 5, (R >> 5) - (C >> 5))[(C & 31) * 32 + (R & 31)] = AH[t];
+}
+
+__global__ void k_symmetrize(double *M, int n) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n * n) return;
+  int r = (int)(t / n), c = (int)(t - (long long)r * n);
+  if (r >= c) return;
+  double a = M[(long long)r * n + c], b = M[(long long)c * n + r];
+  double v = 0.5 * (a + b);
+  M[(long long)r * n + c] = v;
+  M[(long long)c * n + r] = v;
+}
+
+__global__ void k_identity(double *M, int n) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)n * n) return;
+  int r = (int)(t / n), c = (int)(t - (long long)r * n);
+  M[t] = r == c ? 1.0 : 0.0;
+}
+
+__global__ void k_normalize_cols(const SubDesc *subs, int npad, double *P, int ld, long long sp,
+                                 int ncol, const double *G) {
+  const int j = blockIdx.y;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)npad * ncol) return;
+  int row = (int)(t / ncol), c = (int)(t - (long long)row * ncol);
+  double g = G[(long long)j * ncol * ncol + c * ncol + c];
+  double *pv = P + j * sp + (long long)row * ld + c;
+  if (row >= subs[j].n_neu) {
+    *pv = 0.0;
+    return;
+  }
+  if (g > 0.0) *pv /= sqrt(g);
+}
+
+}  // namespace
+
+void launch_pou_neumann(const SubDesc *d_subs, int nsub, int max_nodes, const int *cand,
+                        const int cand_off[3], const uint8_t *mask, int nnx, int nny,
+                        double *Xneu, cudaStream_t s) {
+  dim3 g((3 * max_nodes + 255) / 256, nsub);
+  k_pou_neumann<<<g, 256, 0, s>>>(d_subs, cand, cand_off[0], cand_off[1], cand_off[2], mask, nnx,
+                                  nny, Xneu);
+}
+
+void launch_neumann_assemble(const SubDesc *d_subs, const BandLayout *d_lay, int nsub,
+                             int max_nodes, int nx, int ny, int nz, const double *X,
+                             const double *Y, const double *Z, const double *Cel,
+                             const int *ecnt, const int ecnt_off[3], const uint8_t *mask,
+                             const double *Xneu, double sigma, double *poolS, double *Bloc,
+                             cudaStream_t s) {
+  long long tot = (long long)max_nodes * 27;
+  dim3 g((unsigned)((tot + 127) / 128), nsub);
+  k_neumann_assemble<<<g, 128, 0, s>>>(d_subs, d_lay, nx, ny, nz, X, Y, Z, Cel, ecnt,
+                                       ecnt_off[0], ecnt_off[1], ecnt_off[2], mask, Xneu, sigma,
+                                       poolS, Bloc);
+}
+
+void launch_bloc_mv(const SubDesc *d_subs, int nsub, int max_nodes, const double *Bloc,
+                    const double *T, double *W, long long sys_stride, int p, cudaStream_t s) {
+  dim3 g((3 * max_nodes + 127) / 128, nsub);
+  k_bloc_mv<<<g, 128, 0, s>>>(d_subs, Bloc, T, W, sys_stride, p);
+}
+
+void launch_random_block(const SubDesc *d_subs, int nsub, int npad, double *V, int ld,
+                         long long sys_stride, int p, unsigned long long seed, cudaStream_t s) {
+  dim3 g((npad * p + 255) / 256, nsub);
+  k_random_block<<<g, 256, 0, s>>>(d_subs, npad, V, ld, sys_stride, p, seed);
+}
+
+void launch_tsdots(const SubDesc *d_subs, int nsub, int npad, const double *A, int lda,
+                   long long sa, int na, const double *B, int ldb, long long sb, int nb,
+                   double *Hpart, int chunks, double *H, long long hs, cudaStream_t s) {
+  (void)npad;
+  int sm = 16 * (na + nb) * (int)sizeof(double);
+  cudaFuncSetAttribute(k_tsdots, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  k_tsdots<<<dim3(chunks, nsub), 256, sm, s>>>(d_subs, A, lda, sa, na, B, ldb, sb, nb, Hpart,
+                                               chunks);
+  k_tsdots_reduce<<<nsub, 256, 0, s>>>(Hpart, chunks, na * nb, H, hs);
+}
+
+void launch_tsgemm(const SubDesc *d_subs, int nsub, int npad, const double *A, int lda,
+                   long long sa, int na, const double *H, int ldh, long long hs, double *C,
+                   int ldc, long long sc, int nb, double alpha, double beta, cudaStream_t s) {
+  int sm = na * nb * (int)sizeof(double);
+  cudaFuncSetAttribute(k_tsgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  long long tot = (long long)npad * nb;
+  dim3 g((unsigned)((tot + 255) / 256), nsub);
+  k_tsgemm<<<g, 256, sm, s>>>(d_subs, npad, A, lda, sa, na, H, ldh, hs, C, ldc, sc, nb, alpha,
+                              beta);
+}
+
+void launch_cholqr(const SubDesc *d_subs, int nsub, int npad, const double *G, double *W,
+                   int p, double *Racc, int first, cudaStream_t s) {
+  // Rinv stored right after Racc's nsub*p*p entries
+  double *Rinv = Racc + (long long)nsub * p * p;
+  k_cholqr_small<<<nsub, 32, 0, s>>>(G, p, Rinv, Racc, first);
+  dim3 g((npad + 255) / 256, nsub);
+  k_rowmul<<<g, 256, 0, s>>>(d_subs, npad, W, p, Rinv);
+}
+
+void launch_hm_accum(int nsub, double *Hm, int kdim, const double *Hs, int rows, int k, int p,
+                     cudaStream_t s) {
+  k_hm_accum<<<nsub, 256, 0, s>>>(Hm, kdim, Hs, rows, k, p);
+}
+
+void launch_hm_subdiag(int nsub, double *Hm, int kdim, const double *Racc, int k, int p,
+                       double *Rblk, cudaStream_t s) {
+  k_hm_subdiag<<<nsub, 64, 0, s>>>(Hm, kdim, Racc, k, p, Rblk);
+}
+
+void launch_copy_block(const SubDesc *d_subs, int nsub, int npad, const double *W, int ldw,
+                       long long sw, double *V, int ldv, long long sv, int p, cudaStream_t s) {
+  dim3 g((npad * p + 255) / 256, nsub);
+  k_copy_block<<<g, 256, 0, s>>>(d_subs, npad, W, ldw, sw, V, ldv, sv, p);
+}
+
+int launch_jacobi(int nsub, const double *Hm, int kdim, int p, const double *Rblk, double *Eval,
+                  double *Evec, double *Eres, cudaStream_t s) {
+  // Ework follows Evec
+  double *Ework = Evec + (long long)nsub * kdim * kdim;
+  int sm = (kdim * kdim + kdim) * (int)sizeof(double) + kdim * (int)sizeof(int);
+  GENEO_CUDA_TRY(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  k_jacobi<<<nsub, 256, sm, s>>>(Hm, kdim, p, Rblk, Eval, Evec, Ework, Eres);
+  GENEO_CUDA_TRY(cudaGetLastError());
+  return GENEO_OK;
+}
+
+void launch_build_Z(const SubDesc *d_subs, int nsub, int max_nint, const double *P, int ldp,
+                    long long sp, const double *Xneu, double *Zp, cudaStream_t s) {
+  long long tot = (long long)max_nint * kMaxModes;
+  dim3 g((unsigned)((tot + 255) / 256), nsub);
+  k_build_Z<<<g, 256, 0, s>>>(d_subs, P, ldp, sp, Xneu, Zp);
+}
+
+void launch_AZ(const SubDesc *d_subs, int nsub, int max_nodes, int nnx, int nny, int nnz,
+               const int32_t *rp, const int32_t *col, const double *val, const double *Zp,
+               const long long *yoff, double *Yp, cudaStream_t s) {
+  dim3 g((3 * max_nodes + 127) / 128, nsub);
+  k_AZ<<<g, 128, 0, s>>>(d_subs, nnx, nny, nnz, rp, col, val, Zp, yoff, Yp);
+}
+
+void launch_coarse_blocks(const SubDesc *d_subs, const int2 *pairs, int npairs, const double *Zp,
+                          const double *Yp, const long long *yoff, double *AH, int nH,
+                          cudaStream_t s) {
+  if (npairs > 0) k_coarse_blocks<<<npairs, 256, 0, s>>>(d_subs, pairs, Zp, Yp, yoff, AH, nH);
+}
+
+void launch_dense_to_tiles(const double *AH, int nH, const BandLayout *d_lay, double *pool,
+                           cudaStream_t s) {
+  long long tot = (long long)nH * nH;
+  k_dense_to_tiles<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(AH, nH, d_lay, pool);
+}
+
+void launch_symmetrize(double *M, int n, cudaStream_t s) {
+  long long tot = (long long)n * n;
+  k_symmetrize<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(M, n);
+}
+
+void launch_identity(double *M, int n, cudaStream_t s) {
+  long long tot = (long long)n * n;
+  k_identity<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(M, n);
+}
+
+void launch_normalize_cols(const SubDesc *d_subs, int nsub, int npad, double *P, int ld,
+                           long long sp, int ncol, const double *G, cudaStream_t s) {
+  long long tot = (long long)npad * ncol;
+  dim3 g((unsigned)((tot + 255) / 256), nsub);
+  k_normalize_cols<<<g, 256, 0, s>>>(d_subs, npad, P, ld, sp, ncol, G);
+}
+
+}  // namespace geneo

@@ -1,0 +1,86 @@
+// GenEO eigenproblems, coarse basis and coarse matrix (internal).
+#pragma once
+
+#include "band.cuh"
+
+namespace geneo {
+
+// X_j on Neumann dofs (Sec. 3.3.1 standard PoU): 1/multiplicity on the dofs of
+// V_{h,0}(Omega_j), zero on the artificial boundary and on Dirichlet dofs.
+void launch_pou_neumann(const SubDesc *d_subs, int nsub, int max_nodes, const int *cand,
+                        const int cand_off[3], const uint8_t *mask, int nnx, int nny,
+                        double *Xneu, cudaStream_t s);
+
+// S_j = A_{Omega_j} - sigma X_j A_{Omega_j^o} X_j into band tiles (lower part)
+// and B_j = X_j A_{Omega_j^o} X_j into a 27-slot local BSR.
+void launch_neumann_assemble(const SubDesc *d_subs, const BandLayout *d_lay, int nsub,
+                             int max_nodes, int nx, int ny, int nz, const double *X,
+                             const double *Y, const double *Z, const double *Cel,
+                             const int *ecnt, const int ecnt_off[3], const uint8_t *mask,
+                             const double *Xneu, double sigma, double *poolS, double *Bloc,
+                             cudaStream_t s);
+
+// W[:, 0:p] = B_j T[:, 0:p] on Neumann dofs (row-major blocks with ld p).
+void launch_bloc_mv(const SubDesc *d_subs, int nsub, int max_nodes, const double *Bloc,
+                    const double *T, double *W, long long sys_stride, int p,
+                    cudaStream_t s);
+
+// Random start block (counter-based hash), rows >= n_neu zero.
+void launch_random_block(const SubDesc *d_subs, int nsub, int npad, double *V, int ld,
+                         long long sys_stride, int p, unsigned long long seed,
+                         cudaStream_t s);
+
+// H[j] = A_j^T B_j over the first n rows (n = n_neu of subdomain j):
+// A_j: n x na at lda, B_j: n x nb at ldb; H row-major na x nb (stride hs).
+void launch_tsdots(const SubDesc *d_subs, int nsub, int npad, const double *A, int lda,
+                   long long sa, int na, const double *B, int ldb, long long sb, int nb,
+                   double *Hpart, int chunks, double *H, long long hs, cudaStream_t s);
+
+// C_j = beta C_j + alpha A_j H_j (rows < n_neu).
+void launch_tsgemm(const SubDesc *d_subs, int nsub, int npad, const double *A, int lda,
+                   long long sa, int na, const double *H, int ldh, long long hs, double *C,
+                   int ldc, long long sc, int nb, double alpha, double beta, cudaStream_t s);
+
+// Cholesky-QR step on p x p Gram matrices: R = chol(G), W <- W R^-1 (columns
+// with a vanishing pivot are zeroed); Racc <- R Racc.
+void launch_cholqr(const SubDesc *d_subs, int nsub, int npad, const double *G, double *W,
+                   int p, double *Racc, int first, cudaStream_t s);
+
+// Hm[:, col block k] += Hs (rows 0..(k+1)p-1); sub-diagonal block from Racc.
+void launch_hm_accum(int nsub, double *Hm, int kdim, const double *Hs, int rows, int k, int p,
+                     cudaStream_t s);
+void launch_hm_subdiag(int nsub, double *Hm, int kdim, const double *Racc, int k, int p,
+                       double *Rblk, cudaStream_t s);
+void launch_copy_block(const SubDesc *d_subs, int nsub, int npad, const double *W, int ldw,
+                       long long sw, double *V, int ldv, long long sv, int p,
+                       cudaStream_t s);
+
+// Symmetric Jacobi eigensolver of the kdim x kdim projected matrices; values
+// sorted descending; residual estimates from the last Lanczos block.
+int launch_jacobi(int nsub, const double *Hm, int kdim, int p, const double *Rblk,
+                  double *Eval, double *Evec, double *Eres, cudaStream_t s);
+
+// Z_j = X_j P_j on interior dofs (row-major n_int x m_j).
+void launch_build_Z(const SubDesc *d_subs, int nsub, int max_nint, const double *P, int ldp,
+                    long long sp, const double *Xneu, double *Zp, cudaStream_t s);
+
+// Y_j = A Z_j on the Neumann dofs of subdomain j (row-major n_neu x m_j).
+void launch_AZ(const SubDesc *d_subs, int nsub, int max_nodes, int nnx, int nny, int nnz,
+               const int32_t *rp, const int32_t *col, const double *val, const double *Zp,
+               const long long *yoff, double *Yp, cudaStream_t s);
+
+// A_H blocks for the listed subdomain pairs (j <= k), mirrored.
+void launch_coarse_blocks(const SubDesc *d_subs, const int2 *pairs, int npairs,
+                          const double *Zp, const double *Yp, const long long *yoff,
+                          double *AH, int nH, cudaStream_t s);
+
+// Dense nH x nH (row-major) -> lower band tiles of one system; symmetrise.
+void launch_dense_to_tiles(const double *AH, int nH, const BandLayout *d_lay, double *pool,
+                           cudaStream_t s);
+void launch_symmetrize(double *M, int n, cudaStream_t s);
+void launch_identity(double *M, int n, cudaStream_t s);
+// scale columns of P_j (rows < n_neu) by 1/||col||; norms from the diagonal of G
+void launch_normalize_cols(const SubDesc *d_subs, int nsub, int npad, double *P, int ld,
+                           long long sp, int ncol, const double *G, cudaStream_t s);
+
+}  // namespace geneo
