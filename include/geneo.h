@@ -195,6 +195,17 @@ int geneo_coarse_info(geneo_ctx *ctx, int *n_subdomains, int *n_coarse,
  * basis; AH[n_coarse x n_coarse] coarse matrix.  Either may be NULL. */
 int geneo_get_coarse(geneo_ctx *ctx, double *Phi, double *AH);
 
+/* Inspection of one subdomain's matrices, assembled afresh on the device:
+ * kind 0: A_j = R_j A R_j^T on the dofs of V_{h,0}(Omega_j) (Sec. 3.1);
+ * kind 1: S_j = A_{Omega_j} - shift * X_j A_{Omega_j^o} X_j on all dofs of
+ *         Omega_j (the shifted GenEO pencil, Sec. 3.3.2);
+ * kind 2: B_j = X_j A_{Omega_j^o} X_j (eqm:matrixForm).
+ * dense: n x n row-major (n = 3 x nodes of the set; NULL to skip); gdof[n]:
+ * global dof of each local row (may be NULL).  Needs a preceding geneo_setup
+ * call (it may have failed after planning); kinds 1-2 need the GenEO coarse
+ * space.  Allocates scratch with cudaMallocAsync. */
+int geneo_debug_local_matrix(geneo_ctx *ctx, int sub, int kind, double *dense, int32_t *gdof);
+
 /* Solve A u = b by PCG (FP64 precision, GENEO_AS) or flexible CG (mixed
  * precision or GENEO_AS_POU) from u0 = 0 until ||r_k|| <= tol ||b|| or max_it
  * iterations (Sec. 3.1).  u: 3*n_nodes doubles.  stats may be NULL. */

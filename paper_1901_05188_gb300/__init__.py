@@ -95,6 +95,7 @@ _SIGS = {
     "geneo_coarse_info": [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), _P, _P],
     "geneo_get_coarse": [_P, _P, _P],
     "geneo_solve": [_P, C.c_double, C.c_int, _P, C.POINTER(geneo_stats)],
+    "geneo_debug_local_matrix": [_P, C.c_int, C.c_int, _P, _P],
 }
 EXPORTED = tuple(_SIGS)
 
@@ -212,6 +213,10 @@ def geneo_coarse_info(ctx, modes=None, lambdas=None):
 
 def geneo_get_coarse(ctx, Phi=None, AH=None):
     _check(load().geneo_get_coarse(ctx, _ptr(Phi), _ptr(AH)))
+
+
+def geneo_debug_local_matrix(ctx, sub, kind, dense=None, gdof=None):
+    _check(load().geneo_debug_local_matrix(ctx, sub, kind, _ptr(dense), _ptr(gdof)))
 
 
 def geneo_solve(ctx, tol, max_it, u, raise_on_nonconvergence=True):
@@ -333,6 +338,15 @@ class GeneoSolver:
         z = np.zeros(self.ndof) if isinstance(r, np.ndarray) else self.torch.empty_like(r)
         geneo_apply_preconditioner(self.ctx, np.ascontiguousarray(r) if isinstance(r, np.ndarray) else r, z)
         return z
+
+    def local_matrix(self, sub, kind):
+        """(dense matrix, global dofs) of subdomain `sub`: 0 A_j, 1 S_j, 2 B_j."""
+        gd = np.full(self.ndof, -1, np.int32)
+        geneo_debug_local_matrix(self.ctx, sub, kind, None, gd)
+        n = int(np.sum(gd >= 0))
+        M = np.zeros((n, n))
+        geneo_debug_local_matrix(self.ctx, sub, kind, M, gd)
+        return M, gd[:n].copy()
 
     def coarse_info(self):
         ns = self.part.px * self.part.py * self.part.pz

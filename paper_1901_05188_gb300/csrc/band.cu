@@ -47,6 +47,7 @@ __global__ void __launch_bounds__(256) k_chol_diag(const BandLayout *lay, int ns
   __shared__ T A[32][33];
   __shared__ T X[32][33];
   __shared__ int bad;
+  __shared__ int badrow;
   T *t = tile_ptr(poolL, L, J, 0);
   for (int e = threadIdx.x; e < 1024; e += 256) A[e & 31][e >> 5] = t[e];
   if (threadIdx.x == 0) bad = 0;
@@ -55,6 +56,7 @@ __global__ void __launch_bounds__(256) k_chol_diag(const BandLayout *lay, int ns
     if (threadIdx.x == 0) {
       T d = A[k][k];
       if (!(d > T(0))) {
+        if (!bad) badrow = J * 32 + k;
         bad = 1;
         d = T(1);
       }
@@ -93,7 +95,10 @@ __global__ void __launch_bounds__(256) k_chol_diag(const BandLayout *lay, int ns
     u[e] = X[c][r];          // inv(L_JJ)^T
   }
   if (threadIdx.x == 0 && bad) {
-    if (atomicCAS(&st->code, 0, GENEO_ERR_NOT_SPD) == 0) st->where = j;
+    if (atomicCAS(&st->code, 0, GENEO_ERR_NOT_SPD) == 0) {
+      st->where = j;
+      st->detail = badrow;
+    }
   }
 }
 

@@ -75,7 +75,8 @@ int check_status(geneo_ctx *c, int *where = nullptr) {
   if (where) *where = h.where;
   if (h.code != 0) {
     GENEO_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(DevStatus), c->stream));
-    g_last_error = "device status " + std::to_string(h.code) + " at index " + std::to_string(h.where);
+    g_last_error = "device status " + std::to_string(h.code) + " at index " + std::to_string(h.where) +
+                   " detail " + std::to_string(h.detail);
   }
   return h.code;
 }
@@ -582,7 +583,7 @@ void plan_setup(Arena &A, geneo_ctx *c, const SetupPlan &P) {
     size_t nout = std::max((size_t)pc.kdim * p, (size_t)pc.mcap * pc.mcap);
     pc.Hpart = A.take<double>((size_t)nsub * kDotChunks * nout);
     pc.Hs = A.take<double>((size_t)nsub * nout);
-    pc.G = A.take<double>((size_t)nsub * pc.mcap * pc.mcap);
+    pc.G = A.take<double>((size_t)nsub * std::max(pc.mcap * pc.mcap, p * p));
     pc.Racc = A.take<double>((size_t)2 * nsub * p * p);
     pc.Rblk = A.take<double>((size_t)nsub * p * p);
     pc.Evec = A.take<double>((size_t)2 * nsub * pc.kdim * pc.kdim);
@@ -621,7 +622,7 @@ void plan_setup(Arena &A, geneo_ctx *c, const SetupPlan &P) {
   c->q = A.take<double>(n);
   c->z = A.take<double>(n);
   c->tmp = A.take<double>(n);
-  c->part = A.take<double>(2 * kRedBlocks);
+  c->part = A.take<double>(8 * kRedBlocks);   // the fused SpMV-dot kernel runs 4 x kRedBlocks blocks
   c->alphas = A.take<double>(kHistCap);
   c->betas = A.take<double>(kHistCap);
   c->scal = A.take<double>(4);
@@ -1168,5 +1169,85 @@ extern "C" int geneo_solve(geneo_ctx *c, double tol, int max_it, double *u, gene
   if (stats) *stats = out;
   if (h.done == 2) return fail(GENEO_ERR_CG_BREAKDOWN, "CG breakdown");
   if (h.done != 1) return fail(GENEO_ERR_NOT_CONVERGED, "max_it reached");
+  return GENEO_OK;
+}
+
+// ============================================================================
+// Inspection of the subdomain matrices (parity tests of the set-up steps).
+extern "C" int geneo_debug_local_matrix(geneo_ctx *c, int sub, int kind, double *dense,
+                                        int32_t *gdof) {
+  if (!c || !c->ws1 || !c->pc.d_subs) return fail(GENEO_ERR_STATE, "no preconditioner planned");
+  Precond &pc = c->pc;
+  if (sub < 0 || sub >= pc.nsub || kind < 0 || kind > 2) return fail(GENEO_ERR_INVALID_ARG, "bad sub/kind");
+  if (kind > 0 && !pc.Xneu) return fail(GENEO_ERR_STATE, "no GenEO data (coarse space disabled)");
+  cudaStream_t s = c->stream;
+  const SubDesc &S = pc.subs[sub];
+  const NodeBox &box = kind == 0 ? S.ibox : S.nbox;
+  const int n = 3 * box.count();
+  const int nnx = c->nx + 1, nny = c->ny + 1, nnz = c->nz + 1;
+  if (gdof) {
+    for (int l = 0; l < box.count(); ++l) {
+      int gi, gj, gk;
+      box.global(l, gi, gj, gk);
+      for (int comp = 0; comp < 3; ++comp) gdof[3 * l + comp] = 3 * (gi + nnx * (gj + nny * gk)) + comp;
+    }
+  }
+  if (!dense) return GENEO_OK;
+  std::vector<double> out((size_t)n * n, 0.0);
+  if (kind == 2) {
+    std::vector<double> bl((size_t)27 * 9 * box.count());
+    GENEO_CUDA_TRY(cudaMemcpyAsync(bl.data(), pc.Bloc + S.b_neu * 9, bl.size() * sizeof(double),
+                                   cudaMemcpyDeviceToHost, s));
+    GENEO_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int l = 0; l < box.count(); ++l) {
+      int gi, gj, gk;
+      box.global(l, gi, gj, gk);
+      for (int q = 0; q < 27; ++q) {
+        int l2 = box.local(gi + q % 3 - 1, gj + (q / 3) % 3 - 1, gk + q / 9 - 1);
+        if (l2 < 0) continue;
+        for (int r = 0; r < 3; ++r)
+          for (int cc = 0; cc < 3; ++cc)
+            out[(size_t)(3 * l + r) * n + 3 * l2 + cc] = bl[((size_t)l * 27 + q) * 9 + 3 * r + cc];
+      }
+    }
+  } else {
+    BandLayout L = make_layout(n, box.half_band_dofs(), 0);
+    long long el = layout_elems(L);
+    double *tmp = nullptr;
+    BandLayout *dl = nullptr;
+    GENEO_CUDA_TRY(cudaMallocAsync(&tmp, el * sizeof(double), s));
+    GENEO_CUDA_TRY(cudaMallocAsync(&dl, sizeof(BandLayout), s));
+    GENEO_CUDA_TRY(cudaMemcpyAsync(dl, &L, sizeof(L), cudaMemcpyHostToDevice, s));
+    int st = launch_band_clear<double>(dl, 1, tmp, el, s);
+    if (!st) {
+      if (kind == 0)
+        st = launch_extract_interior<double>(pc.d_subs + sub, dl, 1, box.count(), nnx, nny, nnz,
+                                             c->row_ptr, c->val, tmp, s);
+      else
+        launch_neumann_assemble(pc.d_subs + sub, dl, 1, box.count(), c->nx, c->ny, c->nz, c->X,
+                                c->Y, c->Z, c->Cel, pc.d_ecnt, pc.ecnt_off, c->mask, pc.Xneu,
+                                pc.modes.shift, tmp, pc.Bloc, s);
+    }
+    std::vector<double> tiles(el);
+    GENEO_CUDA_TRY(cudaMemcpyAsync(tiles.data(), tmp, el * sizeof(double), cudaMemcpyDeviceToHost, s));
+    GENEO_CUDA_TRY(cudaFreeAsync(tmp, s));
+    GENEO_CUDA_TRY(cudaFreeAsync(dl, s));
+    GENEO_CUDA_TRY(cudaStreamSynchronize(s));
+    if (st) return st;
+    for (int I = 0; I < L.nt; ++I)
+      for (int d = 0; d <= L.w && d <= I; ++d)
+        for (int e = 0; e < 1024; ++e) {
+          int R = I * 32 + (e & 31), C = (I - d) * 32 + (e >> 5);
+          if (R >= n || C >= n || R < C) continue;
+          double v = tiles[((size_t)I * (L.w + 1) + d) * 1024 + e];
+          out[(size_t)R * n + C] = v;
+          out[(size_t)C * n + R] = v;
+        }
+  }
+  if (is_device_ptr(dense)) {
+    GENEO_CUDA_TRY(cudaMemcpy(dense, out.data(), out.size() * sizeof(double), cudaMemcpyHostToDevice));
+  } else {
+    std::memcpy(dense, out.data(), out.size() * sizeof(double));
+  }
   return GENEO_OK;
 }

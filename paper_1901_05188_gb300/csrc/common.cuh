@@ -32,6 +32,7 @@ constexpr int kRedThreads = 256;
 struct DevStatus {
   int code;        // 0 = ok, else GENEO_ERR_*
   int where;       // subdomain / index of the failure
+  int detail;      // e.g. the row of a failed pivot
 };
 
 // ---------------------------------------------------------------------------
