@@ -199,11 +199,14 @@ int geneo_get_coarse(geneo_ctx *ctx, double *Phi, double *AH);
  * kind 0: A_j = R_j A R_j^T on the dofs of V_{h,0}(Omega_j) (Sec. 3.1);
  * kind 1: S_j = A_{Omega_j} - shift * X_j A_{Omega_j^o} X_j on all dofs of
  *         Omega_j (the shifted GenEO pencil, Sec. 3.3.2);
- * kind 2: B_j = X_j A_{Omega_j^o} X_j (eqm:matrixForm).
+ * kind 2: B_j = X_j A_{Omega_j^o} X_j (eqm:matrixForm);
+ * kind 3, 4: the band Cholesky factor of kind 0, 1 computed afresh in FP64:
+ *         the dense lower block-band with each 32 x 32 diagonal block
+ *         replaced by its inverse (the storage the triangular sweeps use).
  * dense: n x n row-major (n = 3 x nodes of the set; NULL to skip); gdof[n]:
  * global dof of each local row (may be NULL).  Needs a preceding geneo_setup
- * call (it may have failed after planning); kinds 1-2 need the GenEO coarse
- * space.  Allocates scratch with cudaMallocAsync. */
+ * call (it may have failed after planning); kinds 1, 2, 4 need the GenEO
+ * coarse space.  Allocates scratch with cudaMallocAsync. */
 int geneo_debug_local_matrix(geneo_ctx *ctx, int sub, int kind, double *dense, int32_t *gdof);
 
 /* Solve A u = b by PCG (FP64 precision, GENEO_AS) or flexible CG (mixed

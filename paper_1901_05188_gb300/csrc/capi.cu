@@ -569,6 +569,7 @@ void plan_setup(Arena &A, geneo_ctx *c, const SetupPlan &P) {
   if (pc.coarse != GENEO_COARSE_GENEO) cap = 0;
   pc.mcap = cap + 1;
   pc.kdim = pc.ksteps * p;
+  pc.kkeep = pc.kdim / 2;
   if (cap > 0) {
     const int npad = pc.npad_neu_max;
     pc.neuL = A.take<double>(pc.fac_neu_elems);
@@ -576,6 +577,7 @@ void plan_setup(Arena &A, geneo_ctx *c, const SetupPlan &P) {
     pc.Bloc = A.take<double>(9 * (size_t)pc.bloc_blocks);
     pc.Xneu = A.take<double>(pc.xneu_elems);
     pc.V = A.take<double>((size_t)nsub * npad * (pc.kdim + p));
+    pc.Vt = A.take<double>((size_t)nsub * npad * pc.kkeep);
     pc.W = A.take<double>((size_t)nsub * npad * p);
     pc.T1 = A.take<double>((size_t)nsub * npad * p);
     pc.Hm = A.take<double>((size_t)nsub * pc.kdim * pc.kdim);
@@ -693,9 +695,12 @@ static int setup_coarse(geneo_ctx *c, SetupPlan &P, cudaStream_t s) {
   if ((st = launch_band_cholesky<double>(pc.d_lay_neu, nsub, pc.nt_neu_max, pc.w_neu_max,
                                          pc.neuL, pc.neuU, c->status, s)))
     return st;
-  // block Lanczos on C = L^-1 B L^-T with full re-orthogonalisation
+  // Thick-restart block Lanczos on C = L^-1 B L^-T with full re-orthogonalisation.
   const int ldv = kdim + p;
   const long long sV = (long long)npad * ldv, sW = (long long)npad * p;
+  const int kk = pc.kkeep;                       // Ritz vectors kept at a restart
+  const long long sT = (long long)npad * kk;
+  const double abs_tiny = 1e-24 / (sigma * sigma);   // ||C|| <= 1/|sigma|
   GENEO_CUDA_TRY(cudaMemsetAsync(pc.Hm, 0, (size_t)nsub * kdim * kdim * sizeof(double), s));
   GENEO_CUDA_TRY(cudaMemsetAsync(pc.V, 0, (size_t)nsub * sV * sizeof(double), s));
   GENEO_CUDA_TRY(cudaMemsetAsync(pc.W, 0, (size_t)nsub * sW * sizeof(double), s));
@@ -704,35 +709,66 @@ static int setup_coarse(geneo_ctx *c, SetupPlan &P, cudaStream_t s) {
   for (int pass = 0; pass < 2; ++pass) {
     launch_tsdots(pc.d_subs, nsub, npad, pc.W, p, sW, p, pc.W, p, sW, p, pc.Hpart, kDotChunks,
                   pc.G, (long long)p * p, s);
-    launch_cholqr(pc.d_subs, nsub, npad, pc.G, pc.W, p, pc.Racc, pass == 0, s);
+    launch_cholqr(pc.d_subs, nsub, npad, pc.G, pc.W, p, pc.Racc, pass == 0, 0.0, s);
   }
   launch_copy_block(pc.d_subs, nsub, npad, pc.W, p, sW, pc.V, ldv, sV, p, s);
-  for (int k = 0; k < pc.ksteps; ++k) {
-    if ((st = launch_band_solve_dense(pc.d_lay_neu, nsub, npad, pc.neuL, pc.neuU, pc.V + k * p,
-                                      sV, ldv, pc.T1, sW, p, p, 2, s)))
-      return st;
-    launch_bloc_mv(pc.d_subs, nsub, P.max_nodes_neu, pc.Bloc, pc.T1, pc.W, sW, p, s);
-    if ((st = launch_band_solve_dense(pc.d_lay_neu, nsub, npad, pc.neuL, pc.neuU, pc.W, sW, p,
-                                      pc.W, sW, p, p, 1, s)))
-      return st;
-    const int na = (k + 1) * p;
-    for (int pass = 0; pass < 2; ++pass) {
-      launch_tsdots(pc.d_subs, nsub, npad, pc.V, ldv, sV, na, pc.W, p, sW, p, pc.Hpart,
-                    kDotChunks, pc.Hs, (long long)na * p, s);
-      launch_hm_accum(nsub, pc.Hm, kdim, pc.Hs, na, k, p, s);
-      launch_tsgemm(pc.d_subs, nsub, npad, pc.V, ldv, sV, na, pc.Hs, p, (long long)na * p, pc.W,
-                    p, sW, p, -1.0, 1.0, s);
+  std::vector<double> ev((size_t)nsub * kdim), er((size_t)nsub * kdim);
+  int first_block = 0;
+  pc.eig_cycles = 0;
+  for (int cycle = 0; cycle < pc.max_cycles; ++cycle) {
+    for (int k = first_block; k < pc.ksteps; ++k) {
+      // W = L^-1 B L^-T V_k
+      if ((st = launch_band_solve_dense(pc.d_lay_neu, nsub, npad, pc.neuL, pc.neuU, pc.V + k * p,
+                                        sV, ldv, pc.T1, sW, p, p, 2, s)))
+        return st;
+      launch_bloc_mv(pc.d_subs, nsub, P.max_nodes_neu, pc.Bloc, pc.T1, pc.W, sW, p, s);
+      if ((st = launch_band_solve_dense(pc.d_lay_neu, nsub, npad, pc.neuL, pc.neuU, pc.W, sW, p,
+                                        pc.W, sW, p, p, 1, s)))
+        return st;
+      const int na = (k + 1) * p;
+      for (int pass = 0; pass < 2; ++pass) {
+        launch_tsdots(pc.d_subs, nsub, npad, pc.V, ldv, sV, na, pc.W, p, sW, p, pc.Hpart,
+                      kDotChunks, pc.Hs, (long long)na * p, s);
+        launch_hm_accum(nsub, pc.Hm, kdim, pc.Hs, na, k, p, s);
+        launch_tsgemm(pc.d_subs, nsub, npad, pc.V, ldv, sV, na, pc.Hs, p, (long long)na * p,
+                      pc.W, p, sW, p, -1.0, 1.0, s);
+      }
+      for (int pass = 0; pass < 2; ++pass) {
+        launch_tsdots(pc.d_subs, nsub, npad, pc.W, p, sW, p, pc.W, p, sW, p, pc.Hpart,
+                      kDotChunks, pc.G, (long long)p * p, s);
+        launch_cholqr(pc.d_subs, nsub, npad, pc.G, pc.W, p, pc.Racc, pass == 0, abs_tiny, s);
+      }
+      launch_hm_subdiag(nsub, pc.Hm, kdim, pc.Racc, k, p, pc.Rblk, s);
+      if (k + 1 < pc.ksteps)
+        launch_copy_block(pc.d_subs, nsub, npad, pc.W, p, sW, pc.V + (k + 1) * p, ldv, sV, p, s);
     }
-    for (int pass = 0; pass < 2; ++pass) {
-      launch_tsdots(pc.d_subs, nsub, npad, pc.W, p, sW, p, pc.W, p, sW, p, pc.Hpart, kDotChunks,
-                    pc.G, (long long)p * p, s);
-      launch_cholqr(pc.d_subs, nsub, npad, pc.G, pc.W, p, pc.Racc, pass == 0, s);
-    }
-    launch_hm_subdiag(nsub, pc.Hm, kdim, pc.Racc, k, p, pc.Rblk, s);
-    if (k + 1 < pc.ksteps) launch_copy_block(pc.d_subs, nsub, npad, pc.W, p, sW, pc.V, ldv, sV, p, s);
+    GENEO_CUDA_TRY(cudaGetLastError());
+    if ((st = launch_jacobi(nsub, pc.Hm, kdim, p, pc.Rblk, pc.Eval, pc.Evec, pc.Eres, s))) return st;
+    ++pc.eig_cycles;
+    GENEO_CUDA_TRY(cudaMemcpyAsync(ev.data(), pc.Eval, ev.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    GENEO_CUDA_TRY(cudaMemcpyAsync(er.data(), pc.Eres, er.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    GENEO_CUDA_TRY(cudaStreamSynchronize(s));
+    // converged when every wanted Ritz pair has residual <= tol * theta
+    bool conv = true;
+    for (int j = 0; j < nsub && conv; ++j)
+      for (int i = 0; i < mcap; ++i) {
+        double th = ev[(size_t)j * kdim + i];
+        if (!(th > 1e-12 / std::fabs(sigma))) break;      // infinite eigenvalues follow
+        if (!(er[(size_t)j * kdim + i] <= pc.eig_tol * th)) {
+          conv = false;
+          break;
+        }
+      }
+    if (conv || cycle + 1 == pc.max_cycles) break;
+    // restart: V[:, :kk] = V S[:, :kk], V[:, kk:kk+p] = next Lanczos block
+    launch_tsgemm(pc.d_subs, nsub, npad, pc.V, ldv, sV, kdim, pc.Evec, kdim,
+                  (long long)kdim * kdim, pc.Vt, kk, sT, kk, 1.0, 0.0, s);
+    for (int b = 0; b < kk / p; ++b)
+      launch_copy_block(pc.d_subs, nsub, npad, pc.Vt + b * p, kk, sT, pc.V + b * p, ldv, sV, p, s);
+    launch_copy_block(pc.d_subs, nsub, npad, pc.W, p, sW, pc.V + kk, ldv, sV, p, s);
+    launch_restart_hm(nsub, pc.Hm, kdim, pc.Eval, pc.Evec, pc.Rblk, kk, p, s);
+    first_block = kk / p;
   }
-  GENEO_CUDA_TRY(cudaGetLastError());
-  if ((st = launch_jacobi(nsub, pc.Hm, kdim, p, pc.Rblk, pc.Eval, pc.Evec, pc.Eres, s))) return st;
   // Ritz vectors y = V s, then p = L^-T y, normalised to ||p||_2 = 1
   const long long sP = (long long)npad * mcap;
   launch_tsgemm(pc.d_subs, nsub, npad, pc.V, ldv, sV, kdim, pc.Evec, kdim, (long long)kdim * kdim,
@@ -744,10 +780,7 @@ static int setup_coarse(geneo_ctx *c, SetupPlan &P, cudaStream_t s) {
                 kDotChunks, pc.G, (long long)mcap * mcap, s);
   launch_normalize_cols(pc.d_subs, nsub, npad, pc.P, mcap, sP, mcap, pc.G, s);
   GENEO_CUDA_TRY(cudaGetLastError());
-  // eigenvalues -> host, mode selection
-  std::vector<double> ev((size_t)nsub * kdim), er((size_t)nsub * kdim);
-  GENEO_CUDA_TRY(cudaMemcpyAsync(ev.data(), pc.Eval, ev.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-  GENEO_CUDA_TRY(cudaMemcpyAsync(er.data(), pc.Eres, er.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  // mode selection on the converged eigenvalues
   GENEO_CUDA_TRY(cudaStreamSynchronize(s));
   if ((st = check_status(c))) return st;
   pc.m.assign(nsub, 0);
@@ -783,6 +816,7 @@ static int setup_coarse(geneo_ctx *c, SetupPlan &P, cudaStream_t s) {
   }
   pc.nH = coff;
   pc.subs = P.subs;
+  pc.eig_done = true;
   GENEO_CUDA_TRY(cudaMemcpyAsync(pc.d_subs, P.subs.data(), nsub * sizeof(SubDesc), cudaMemcpyHostToDevice, s));
   GENEO_CUDA_TRY(cudaMemcpyAsync(pc.d_yoff, yoffs.data(), nsub * sizeof(long long), cudaMemcpyHostToDevice, s));
   if (pc.nH == 0) return GENEO_OK;
@@ -863,6 +897,7 @@ int geneo_setup(geneo_ctx *c, const geneo_partition *part, const geneo_modes *mo
   pc.schwarz = schwarz;
   pc.coarse = coarse;
   pc.nH = 0;
+  pc.eig_done = false;
   SetupPlan P;
   int st;
   if ((st = build_plan(c, part, modes, P))) return st;
@@ -965,7 +1000,7 @@ int geneo_apply_preconditioner(geneo_ctx *c, const double *r, double *z) {
 
 int geneo_coarse_info(geneo_ctx *c, int *n_subdomains, int *n_coarse, int32_t *modes,
                       double *lambdas) {
-  if (!c || !c->setup_done) return fail(GENEO_ERR_STATE, "no preconditioner set up");
+  if (!c || !(c->setup_done || c->pc.eig_done)) return fail(GENEO_ERR_STATE, "no preconditioner set up");
   const Precond &pc = c->pc;
   if (n_subdomains) *n_subdomains = pc.nsub;
   if (n_coarse) *n_coarse = pc.nH;
@@ -983,7 +1018,7 @@ int geneo_coarse_info(geneo_ctx *c, int *n_subdomains, int *n_coarse, int32_t *m
 }
 
 int geneo_get_coarse(geneo_ctx *c, double *Phi, double *AH) {
-  if (!c || !c->setup_done) return fail(GENEO_ERR_STATE, "no preconditioner set up");
+  if (!c || !(c->setup_done || c->pc.eig_done)) return fail(GENEO_ERR_STATE, "no preconditioner set up");
   const Precond &pc = c->pc;
   const int nH = pc.nH;
   if (nH == 0) return GENEO_OK;
@@ -1178,11 +1213,14 @@ extern "C" int geneo_debug_local_matrix(geneo_ctx *c, int sub, int kind, double 
                                         int32_t *gdof) {
   if (!c || !c->ws1 || !c->pc.d_subs) return fail(GENEO_ERR_STATE, "no preconditioner planned");
   Precond &pc = c->pc;
-  if (sub < 0 || sub >= pc.nsub || kind < 0 || kind > 2) return fail(GENEO_ERR_INVALID_ARG, "bad sub/kind");
-  if (kind > 0 && !pc.Xneu) return fail(GENEO_ERR_STATE, "no GenEO data (coarse space disabled)");
+  if (sub < 0 || sub >= pc.nsub || kind < 0 || kind > 4) return fail(GENEO_ERR_INVALID_ARG, "bad sub/kind");
+  if ((kind == 1 || kind == 2 || kind == 4) && !pc.Xneu)
+    return fail(GENEO_ERR_STATE, "no GenEO data (coarse space disabled)");
   cudaStream_t s = c->stream;
   const SubDesc &S = pc.subs[sub];
-  const NodeBox &box = kind == 0 ? S.ibox : S.nbox;
+  const bool factor = kind >= 3;
+  const int base_kind = kind == 3 ? 0 : (kind == 4 ? 1 : kind);
+  const NodeBox &box = base_kind == 0 ? S.ibox : S.nbox;
   const int n = 3 * box.count();
   const int nnx = c->nx + 1, nny = c->ny + 1, nnz = c->nz + 1;
   if (gdof) {
@@ -1218,9 +1256,11 @@ extern "C" int geneo_debug_local_matrix(geneo_ctx *c, int sub, int kind, double 
     GENEO_CUDA_TRY(cudaMallocAsync(&tmp, el * sizeof(double), s));
     GENEO_CUDA_TRY(cudaMallocAsync(&dl, sizeof(BandLayout), s));
     GENEO_CUDA_TRY(cudaMemcpyAsync(dl, &L, sizeof(L), cudaMemcpyHostToDevice, s));
+    double *tmpU = nullptr;
+    if (factor) GENEO_CUDA_TRY(cudaMallocAsync(&tmpU, el * sizeof(double), s));
     int st = launch_band_clear<double>(dl, 1, tmp, el, s);
     if (!st) {
-      if (kind == 0)
+      if (base_kind == 0)
         st = launch_extract_interior<double>(pc.d_subs + sub, dl, 1, box.count(), nnx, nny, nnz,
                                              c->row_ptr, c->val, tmp, s);
       else
@@ -1228,20 +1268,30 @@ extern "C" int geneo_debug_local_matrix(geneo_ctx *c, int sub, int kind, double 
                                 c->Y, c->Z, c->Cel, pc.d_ecnt, pc.ecnt_off, c->mask, pc.Xneu,
                                 pc.modes.shift, tmp, pc.Bloc, s);
     }
+    if (!st && factor) {
+      GENEO_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(DevStatus), s));
+      st = launch_band_cholesky<double>(dl, 1, L.nt, L.w, tmp, tmpU, c->status, s);
+    }
     std::vector<double> tiles(el);
     GENEO_CUDA_TRY(cudaMemcpyAsync(tiles.data(), tmp, el * sizeof(double), cudaMemcpyDeviceToHost, s));
     GENEO_CUDA_TRY(cudaFreeAsync(tmp, s));
     GENEO_CUDA_TRY(cudaFreeAsync(dl, s));
+    if (tmpU) GENEO_CUDA_TRY(cudaFreeAsync(tmpU, s));
     GENEO_CUDA_TRY(cudaStreamSynchronize(s));
     if (st) return st;
+    if (factor && (st = check_status(c))) return st;
     for (int I = 0; I < L.nt; ++I)
       for (int d = 0; d <= L.w && d <= I; ++d)
         for (int e = 0; e < 1024; ++e) {
           int R = I * 32 + (e & 31), C = (I - d) * 32 + (e >> 5);
-          if (R >= n || C >= n || R < C) continue;
+          if (R >= n || C >= n) continue;
           double v = tiles[((size_t)I * (L.w + 1) + d) * 1024 + e];
-          out[(size_t)R * n + C] = v;
-          out[(size_t)C * n + R] = v;
+          if (factor) {
+            out[(size_t)R * n + C] = v;      // tile storage as is (lower blocks)
+          } else if (R >= C) {
+            out[(size_t)R * n + C] = v;
+            out[(size_t)C * n + R] = v;
+          }
         }
   }
   if (is_device_ptr(dense)) {

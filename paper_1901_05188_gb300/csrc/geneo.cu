@@ -240,7 +240,8 @@ __global__ void __launch_bounds__(256)
 }
 
 // Cholesky of the p x p Gram matrix, inverse, and Racc update (one block per subdomain)
-__global__ void k_cholqr_small(const double *G, int p, double *Rinv, double *Racc, int first) {
+__global__ void k_cholqr_small(const double *G, int p, double *Rinv, double *Racc, int first,
+                               double abs_tiny) {
   const int j = blockIdx.x;
   __shared__ double R[kLanczosBlock][kLanczosBlock];
   __shared__ double Ri[kLanczosBlock][kLanczosBlock];
@@ -253,7 +254,9 @@ __global__ void k_cholqr_small(const double *G, int p, double *Rinv, double *Rac
     for (int k = 0; k < p; ++k) {
       double d = g[k * p + k];
       for (int i = 0; i < k; ++i) d -= R[i][k] * R[i][k];
-      bool dead = !(d > 1e-200);
+      // numerically dependent (angle to the block's span below 1e-7) or
+      // negligible against the operator scale: deflate the column
+      bool dead = !(d > 1e-14 * g[k * p + k]) || !(d > abs_tiny);
       double rk = dead ? 0.0 : sqrt(d);
       R[k][k] = rk;
       for (int c = k + 1; c < p; ++c) {
@@ -332,6 +335,25 @@ __global__ void k_hm_subdiag(double *Hm, int kdim, const double *Racc, int k, in
       Hm[(long long)j * kdim * kdim + (long long)((k + 1) * p + a) * kdim + k * p + b] = v;
     else
       Rblk[(long long)j * p * p + e] = v;
+  }
+}
+
+__global__ void k_restart_hm(double *Hm, int kdim, const double *Eval, const double *Evec,
+                             const double *Rblk, int kk, int p) {
+  const int j = blockIdx.x;
+  double *H = Hm + (long long)j * kdim * kdim;
+  const double *S = Evec + (long long)j * kdim * kdim;
+  const double *R = Rblk + (long long)j * p * p;
+  for (int e = threadIdx.x; e < kdim * kdim; e += blockDim.x) {
+    int r = e / kdim, c = e - r * kdim;
+    double v = 0.0;
+    if (r < kk && c < kk) {
+      v = (r == c) ? Eval[(long long)j * kdim + r] : 0.0;
+    } else if (r >= kk && r < kk + p && c < kk) {
+      int a = r - kk;
+      for (int b = 0; b < p; ++b) v += R[a * p + b] * S[(long long)(kdim - p + b) * kdim + c];
+    }
+    H[e] = v;
   }
 }
 
@@ -653,10 +675,10 @@ void launch_tsgemm(const SubDesc *d_subs, int nsub, int npad, const double *A, i
 }
 
 void launch_cholqr(const SubDesc *d_subs, int nsub, int npad, const double *G, double *W,
-                   int p, double *Racc, int first, cudaStream_t s) {
+                   int p, double *Racc, int first, double abs_tiny, cudaStream_t s) {
   // Rinv stored right after Racc's nsub*p*p entries
   double *Rinv = Racc + (long long)nsub * p * p;
-  k_cholqr_small<<<nsub, 32, 0, s>>>(G, p, Rinv, Racc, first);
+  k_cholqr_small<<<nsub, 32, 0, s>>>(G, p, Rinv, Racc, first, abs_tiny);
   dim3 g((npad + 255) / 256, nsub);
   k_rowmul<<<g, 256, 0, s>>>(d_subs, npad, W, p, Rinv);
 }
@@ -669,6 +691,11 @@ void launch_hm_accum(int nsub, double *Hm, int kdim, const double *Hs, int rows,
 void launch_hm_subdiag(int nsub, double *Hm, int kdim, const double *Racc, int k, int p,
                        double *Rblk, cudaStream_t s) {
   k_hm_subdiag<<<nsub, 64, 0, s>>>(Hm, kdim, Racc, k, p, Rblk);
+}
+
+void launch_restart_hm(int nsub, double *Hm, int kdim, const double *Eval, const double *Evec,
+                       const double *Rblk, int kk, int p, cudaStream_t s) {
+  k_restart_hm<<<nsub, 256, 0, s>>>(Hm, kdim, Eval, Evec, Rblk, kk, p);
 }
 
 void launch_copy_block(const SubDesc *d_subs, int nsub, int npad, const double *W, int ldw,

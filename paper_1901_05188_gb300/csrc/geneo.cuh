@@ -44,7 +44,10 @@ void launch_tsgemm(const SubDesc *d_subs, int nsub, int npad, const double *A, i
 // Cholesky-QR step on p x p Gram matrices: R = chol(G), W <- W R^-1 (columns
 // with a vanishing pivot are zeroed); Racc <- R Racc.
 void launch_cholqr(const SubDesc *d_subs, int nsub, int npad, const double *G, double *W,
-                   int p, double *Racc, int first, cudaStream_t s);
+                   int p, double *Racc, int first, double abs_tiny, cudaStream_t s);
+// Thick restart: Hm <- diag(theta_0..kk-1) with the coupling block R_s S[last p rows, :kk].
+void launch_restart_hm(int nsub, double *Hm, int kdim, const double *Eval, const double *Evec,
+                       const double *Rblk, int kk, int p, cudaStream_t s);
 
 // Hm[:, col block k] += Hs (rows 0..(k+1)p-1); sub-diagonal block from Racc.
 void launch_hm_accum(int nsub, double *Hm, int kdim, const double *Hs, int rows, int k, int p,

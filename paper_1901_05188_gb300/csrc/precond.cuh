@@ -45,8 +45,13 @@ struct Precond {
   double *neuL = nullptr, *neuU = nullptr;   // factor of S = A - sigma B
   double *Bloc = nullptr;         // 27-slot local BSR of B (9 doubles per block)
   double *Xneu = nullptr;         // PoU on Neumann dofs
-  int ksteps = 16;                // Lanczos block steps
+  int ksteps = 16;                // Lanczos block steps per cycle (basis size kdim = p * ksteps)
   int kdim = 0;                   // p * ksteps
+  int kkeep = 0;                  // Ritz vectors kept at a thick restart
+  int max_cycles = 12;            // restart cycles
+  int eig_cycles = 0;
+  double eig_tol = 1e-8;          // Ritz residual <= eig_tol * theta (bounds the eigenvalue error)
+  double *Vt = nullptr;           // restart scratch [nsub][npad][kkeep]
   double *V = nullptr;            // Lanczos basis [nsub][npad_neu][kdim + p] row-major
   double *W = nullptr;            // [nsub][npad_neu][p]
   double *T1 = nullptr;           // work block [nsub][npad_neu][p]
@@ -71,6 +76,7 @@ struct Precond {
   std::vector<int> m;
   std::vector<double> lambdas;    // [nsub][mcap]
   double eig_max_res = 0.0;
+  bool eig_done = false;          // eigenpairs selected and Z built
   float ms_eig = 0.f, ms_coarse = 0.f, ms_factor = 0.f;
   double bytes_per_apply = 0.0;
 };

@@ -52,3 +52,31 @@ def test_local_matrices_match_oracle(pkg, name):
         assert np.abs(Bg - Br).max() <= 1e-12 * max(np.abs(Br).max(), 1e-300), ("B_j", j)
         assert np.linalg.eigvalsh(Sg).min() > 0
     s.close()
+
+
+@pytest.mark.parametrize("name,kind", [("tiny", 3), ("tiny", 4), ("c1", 3), ("c1", 4)])
+def test_band_cholesky_matches_dense(pkg, name, kind):
+    # The tile Cholesky (Sec. 3.3.3 exact local solves) against LAPACK on the
+    # same matrix: off-diagonal blocks of L and inverted diagonal blocks.
+    p = workloads.config(name)
+    s = pkg.GeneoSolver()
+    s.assemble(p)
+    try:
+        s.setup(p, pkg.GENEO_FP64)
+    except pkg.GeneoError:
+        pass
+    for j in range(len(decomp.partition(p))):
+        M, gd = s.local_matrix(j, kind - 3)
+        F, _ = s.local_matrix(j, kind)
+        L = np.linalg.cholesky(M)
+        n = M.shape[0]
+        nt = (n + 31) // 32
+        for I in range(nt):
+            r0, r1 = 32 * I, min(n, 32 * I + 32)
+            Dinv = np.linalg.inv(L[r0:r1, r0:r1])
+            assert np.abs(F[r0:r1, r0:r1] - Dinv).max() <= 1e-9 * np.abs(Dinv).max(), (j, I)
+            if I > 0:
+                off = F[r0:r1, :r0]
+                ref = L[r0:r1, :r0]
+                assert np.abs(off - ref).max() <= 1e-9 * np.abs(L).max(), (j, I)
+    s.close()
