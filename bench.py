@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""GenEO-PCG time-to-solution benchmark on GB300.
+
+Workload (default): the 64x32x24-element laminated block (160,875 dofs,
+12 plies drawn from {0, +-45, 90} with 11 one-element resin interlayers),
+clamped at x = 0 under 1 MPa top pressure, 4x4x2 subdomains with overlap 1,
+GenEO threshold rule capped at 20 modes per subdomain, PCG to ||r||/||b|| <= 1e-8.
+
+One step = the whole method on one synthetic problem: assembly of A u = b,
+the GenEO set-up (eigenproblems, coarse space, subdomain factors) and the
+(F)PCG solve, all on the GPU through the library's C ABI.  `value` times
+steps whose inputs already sit in device memory; `e2e` times the same step
+from host arrays with the host<->device copies inside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--config c2] [--precision fp64|mixed]
+
+Multi-GPU: the path does not shard (one GPU per problem, no collectives), so
+N ranks run N independent replicas (weak scaling); value = max-over-ranks time
+divided by the solves all ranks completed.
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload and extrapolates to one full solve.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GenEO-PCG time-to-1e-8 relative residual"
+UNIT = "ms"
+TOL = 1e-8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(p, prec):
+    s = dict(workload=f"{p['name']}: {p['nx']}x{p['ny']}x{p['nz']} Q1 hex laminate, "
+                      f"{3 * (p['nx'] + 1) * (p['ny'] + 1) * (p['nz'] + 1)} dofs",
+             partition="x".join(str(v) for v in p["partition"][:3]) + f", overlap {p['partition'][3]}",
+             modes=("fixed %d" % p["modes"]["fixed_modes"] if p["modes"]["fixed_modes"]
+                    else "threshold rule, cap %d" % p["modes"]["max_modes"]),
+             precision=prec, tol=TOL,
+             l2="working set (BSR + band factors) > 129 MB L2; no flush needed")
+    return s
+
+
+# ---------------------------------------------------------------------------
+# clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5], f[6], f[7], f[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[2:]) if v.lower() == "active"})
+        return dict(sm_mhz=statistics.median(r[0] for r in rows), sm_max_mhz=max(r[1] for r in rows),
+                    samples=len(rows), reasons=reasons)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (the baseline arm)
+
+def oracle_sample(p, gpu_iterations):
+    """Time a bounded sample of the oracle on this workload and extrapolate to
+    one full solve: 1/8 of the element assembly (x8), one of the GenEO
+    eigensolves (x subdomains), four subdomain factorisations (x subdomains/4),
+    and per iteration an SpMV on the sampled rows (x8) plus the four subdomain
+    solves (x subdomains/4), times the iteration count.
+    Returns (ms, sample description, threads used)."""
+    import contextlib
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    from oracle import decomp, fem, geneo
+    try:
+        from threadpoolctl import threadpool_limits
+        ctx, threads = threadpool_limits(limits=1), 1
+    except ImportError:           # BLAS keeps its default; the sparse kernels are serial
+        ctx, threads = contextlib.nullcontext(), os.cpu_count() or 1
+    with ctx:
+        nel = p["nx"] * p["ny"] * p["nz"]
+        t0 = time.perf_counter()
+        A8 = fem.assemble_stiffness(p, np.arange(0, nel, 8))
+        t_asm = (time.perf_counter() - t0) * 8
+        subs = decomp.partition(p)
+        ns = len(subs)
+        j = min(ns - 1, ns // 2 + 1)
+        m = p["modes"]
+        nev = (m["fixed_modes"] if m["fixed_modes"] > 0 else m["max_modes"]) + 1
+        t0 = time.perf_counter()
+        Aj, Aoj = geneo.local_matrices(p, subs[j])
+        Xd = sp.diags(subs[j].X)
+        geneo.eigenpairs(Aj, (Xd @ Aoj @ Xd).tocsr(), nev, m["shift"])
+        t_eig = (time.perf_counter() - t0) * ns
+        idx = sorted({min(ns - 1, k * ns // 4) for k in range(4)})
+        t0 = time.perf_counter()
+        lus = []
+        for k in idx:
+            Ak, _ = geneo.local_matrices(p, subs[k])
+            lus.append((spla.splu(Ak.tocsc()), Ak.shape[0]))
+        t_fac = (time.perf_counter() - t0) * ns / len(idx)
+        x = np.ones(A8.shape[0])
+        t0 = time.perf_counter()
+        for _ in range(3):
+            A8 @ x
+        t_spmv = (time.perf_counter() - t0) / 3 * 8
+        t0 = time.perf_counter()
+        for _ in range(3):
+            for lu, n in lus:
+                lu.solve(np.ones(n))
+        t_sub = (time.perf_counter() - t0) / 3 * ns / len(idx)
+        total = t_asm + t_eig + t_fac + gpu_iterations * (t_spmv + t_sub)
+    sample = (f"FP64 oracle sample: assembly of 1/8 of the elements (x8), 1 of {ns} GenEO "
+              f"eigensolves (x{ns}), {len(idx)} of {ns} subdomain factorisations, per-iteration "
+              f"SpMV on 1/8 of the elements (x8) + {len(idx)} subdomain solves, "
+              f"x {gpu_iterations} iterations")
+    return total * 1000.0, sample, threads
+
+
+def run_reference(args):
+    import workloads
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    p = workloads.config(args.config)
+    iters = 103 if args.config == "c2" else 60
+    gold = os.path.join(ROOT, "tests", "golden", f"{args.config}_oracle.json")
+    if os.path.exists(gold):
+        iters = json.load(open(gold))["iterations"]
+    for _ in range(args.warmup):
+        oracle_sample(p, iters)
+    times = []
+    sample, threads = "", 1
+    for _ in range(args.steps):
+        ms, sample, threads = oracle_sample(p, iters)
+        times.append(ms)
+    v = statistics.mean(times)
+    line = dict(metric=METRIC, value=v, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=v, higher_is_better=False, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
+                config=workload_config(p, "fp64"),
+                cpu_baseline=dict(value=v, unit=UNIT, cores=threads, kind="oracle", sample=sample),
+                e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+
+def device_problem(p, torch, dev):
+    q = dict(p)
+    for k in ("x", "y", "z", "elem_theta", "elem_phi", "dirichlet_values"):
+        q[k] = torch.as_tensor(np.ascontiguousarray(p[k], dtype=np.float64), device=dev)
+    for k in ("elem_mat", "dirichlet_dofs"):
+        q[k] = torch.as_tensor(np.ascontiguousarray(p[k], dtype=np.int32), device=dev)
+    return q
+
+
+def host_bytes(p):
+    n = 0
+    for k in ("x", "y", "z", "elem_theta", "elem_phi", "dirichlet_values", "elem_mat",
+              "dirichlet_dofs", "materials"):
+        n += np.asarray(p[k]).nbytes
+    return n
+
+
+def one_solve(pkg, s, p, prec, out):
+    s.assemble(p)
+    s.setup(p, prec)
+    u, st = s.solve(tol=TOL, max_it=5000, out=out)
+    return st
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    import workloads
+    import paper_1901_05188_gb300 as pkg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    pkg.load(build_if_missing=True)
+    prec = pkg.GENEO_FP64 if args.precision == "fp64" else pkg.GENEO_MIXED_FP32
+    p = workloads.config(args.config)
+    pd = device_problem(p, torch, dev)
+    s = pkg.GeneoSolver()
+    ndof = 3 * (p["nx"] + 1) * (p["ny"] + 1) * (p["nz"] + 1)
+    u_dev = torch.empty(ndof, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        st = one_solve(pkg, s, pd, prec, u_dev)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = pkg.geneo_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        stats.append(one_solve(pkg, s, pd, prec, u_dev))
+    e1.record(stream)
+    barrier()
+    launches = pkg.geneo_launch_count() - l0
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    t = torch.tensor([ms_total], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_step = float(t.item()) / args.steps
+    value = ms_step / world
+    st = stats[-1]
+
+    # end-to-end through the C ABI from host arrays (copies inside the region)
+    e2e = None
+    if not args.no_e2e:
+        u_host = torch.empty(ndof, dtype=torch.float64, pin_memory=True).numpy()
+        one_solve(pkg, s, p, prec, u_host)
+        barrier()
+        e0.record(stream)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            one_solve(pkg, s, p, prec, u_host)
+        e1.record(stream)
+        barrier()
+        wall = (time.perf_counter() - t0) * 1000.0 / args.steps
+        e2e = dict(value=max(e0.elapsed_time(e1) / args.steps, wall) / world, unit=UNIT,
+                   h2d_bytes_per_step=host_bytes(p), d2h_bytes_per_step=8 * ndof)
+
+    # roofline of the dominant per-iteration kernel (Schwarz local solves)
+    peak, peak_kind = measured_peaks()
+    ms_k, by_k, fl_k = pkg.geneo_profile(s.ctx, 0, 20)
+    achieved = by_k / (ms_k * 1e-3) / 1e9
+    roof = dict(bound="hbm", kernel="k_schwarz_solve (one-level local band solves)",
+                achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
+                peak_source=f"{peak_kind} hbm_gbs", traffic=None,
+                ms_per_launch=ms_k, algorithmic_bytes=by_k)
+    ms_sp, by_sp, _ = pkg.geneo_profile(s.ctx, 1, 50)
+    ms_pc, by_pc, _ = pkg.geneo_profile(s.ctx, 2, 20)
+    kernels = dict(spmv=dict(ms=ms_sp, gbs=by_sp / (ms_sp * 1e-3) / 1e9),
+                   precond_apply=dict(ms=ms_pc, gbs=by_pc / (ms_pc * 1e-3) / 1e9))
+
+    # accuracy against the oracle's stored summary (sampled displacements)
+    acc = None
+    gold = os.path.join(ROOT, "tests", "golden", f"{args.config}_oracle.json")
+    if os.path.exists(gold):
+        g = json.load(open(gold))
+        u = u_dev.cpu().numpy()
+        us = u[::g["sample_stride"]][:len(g["u_samples"])]
+        ref = np.asarray(g["u_samples"])
+        acc = dict(rel_err_samples=float(np.linalg.norm(us - ref) / np.linalg.norm(ref)),
+                   oracle_iterations=g["iterations"])
+
+    mixed = None
+    if not args.no_mixed and args.precision == "fp64":
+        for _ in range(2):
+            stm = one_solve(pkg, s, pd, pkg.GENEO_MIXED_FP32, u_dev)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(args.steps):
+            stm = one_solve(pkg, s, pd, pkg.GENEO_MIXED_FP32, u_dev)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        mixed = dict(ms_per_solve=e0.elapsed_time(e1) / args.steps, iterations=stm["iterations"],
+                     rel_res_true=stm["rel_res_true"], ms_setup=stm["ms_setup_eig"] + stm["ms_setup_factor"],
+                     ms_solve=stm["ms_solve"])
+        if acc is not None:
+            u = u_dev.cpu().numpy()
+            us = u[::g["sample_stride"]][:len(g["u_samples"])]
+            mixed["rel_err_samples"] = float(np.linalg.norm(us - ref) / np.linalg.norm(ref))
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ms_cpu, sample, threads = oracle_sample(p, st["iterations"])
+        cpu = dict(value=ms_cpu, unit=UNIT, cores=threads, kind="oracle", sample=sample)
+
+    if rank == 0:
+        line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
+                    warmup=args.warmup, ms_per_step=ms_step, higher_is_better=False,
+                    scaling="weak", vs_baseline=None,
+                    dtype="f64" if args.precision == "fp64" else "f64+f32",
+                    data="synthetic", config=workload_config(p, args.precision),
+                    roofline=roof, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
+                    clocks=clk, iterations=st["iterations"], rel_res_true=st["rel_res_true"],
+                    n_coarse=st["n_coarse"], kappa_est=st["kappa_est"],
+                    phases_ms=dict(assemble=st["ms_assemble"], setup_eig_coarse=st["ms_setup_eig"],
+                                   setup_factor=st["ms_setup_factor"], solve=st["ms_solve"]),
+                    bytes_per_iter=st["bytes_per_iter"], kernels=kernels,
+                    accuracy_vs_oracle=acc, mixed_precision=mixed)
+        print(json.dumps(line))
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

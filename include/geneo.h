@@ -124,6 +124,9 @@ int geneo_destroy(geneo_ctx *ctx);
 const char *geneo_status_string(int status);
 /* Human-readable detail of the last failure on this host thread. */
 const char *geneo_last_error(void);
+/* Number of kernel launches this library has enqueued in this process so far
+ * (a CUDA-graph launch counts its kernel nodes).  Not thread-safe. */
+long long geneo_launch_count(void);
 
 /* Device bytes needed by geneo_assemble for this mesh (BSR matrix, load,
  * per-element material data, index arrays). */
@@ -208,6 +211,16 @@ int geneo_get_coarse(geneo_ctx *ctx, double *Phi, double *AH);
  * call (it may have failed after planning); kinds 1, 2, 4 need the GenEO
  * coarse space.  Allocates scratch with cudaMallocAsync. */
 int geneo_debug_local_matrix(geneo_ctx *ctx, int sub, int kind, double *dense, int32_t *gdof);
+
+/* Time `reps` back-to-back launches of one hot kernel on the context stream
+ * with CUDA events (after one warm-up launch) and report its algorithmic
+ * traffic: what 0 = the one-level Schwarz local solves (Sec. 3.1,
+ * eqn:onelevelAS: gather, forward and backward band sweeps, both factor
+ * streams), 1 = the BSR SpMV, 2 = the whole preconditioner application.
+ * Outputs (any may be NULL): mean ms per launch, bytes and flops per launch.
+ * Needs geneo_setup; overwrites the solver's internal work vectors. */
+int geneo_profile(geneo_ctx *ctx, int what, int reps, double *ms_per_launch, double *bytes,
+                  double *flops);
 
 /* Solve A u = b by PCG (FP64 precision, GENEO_AS) or flexible CG (mixed
  * precision or GENEO_AS_POU) from u0 = 0 until ||r_k|| <= tol ||b|| or max_it

@@ -80,6 +80,7 @@ _SIGS = {
     "geneo_destroy": [_P],
     "geneo_status_string": [C.c_int],
     "geneo_last_error": [],
+    "geneo_launch_count": [],
     "geneo_assemble_workspace_bytes": [C.POINTER(geneo_mesh), C.POINTER(C.c_size_t)],
     "geneo_setup_workspace_bytes": [_P, C.POINTER(geneo_partition), C.POINTER(geneo_modes),
                                     C.c_int, C.POINTER(C.c_size_t)],
@@ -96,6 +97,8 @@ _SIGS = {
     "geneo_get_coarse": [_P, _P, _P],
     "geneo_solve": [_P, C.c_double, C.c_int, _P, C.POINTER(geneo_stats)],
     "geneo_debug_local_matrix": [_P, C.c_int, C.c_int, _P, _P],
+    "geneo_profile": [_P, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                      C.POINTER(C.c_double)],
 }
 EXPORTED = tuple(_SIGS)
 
@@ -117,7 +120,8 @@ def load(build_if_missing: bool = False):
     for name, args in _SIGS.items():
         f = getattr(lib, name)
         f.argtypes = args
-        f.restype = C.c_char_p if name in ("geneo_status_string", "geneo_last_error") else C.c_int
+        f.restype = (C.c_char_p if name in ("geneo_status_string", "geneo_last_error")
+                     else C.c_longlong if name == "geneo_launch_count" else C.c_int)
     _lib = lib
     return lib
 
@@ -153,6 +157,10 @@ def geneo_create(stream=None):
 
 def geneo_destroy(ctx):
     _check(load().geneo_destroy(ctx))
+
+
+def geneo_launch_count():
+    return int(load().geneo_launch_count())
 
 
 def geneo_status_string(status):
@@ -217,6 +225,12 @@ def geneo_get_coarse(ctx, Phi=None, AH=None):
 
 def geneo_debug_local_matrix(ctx, sub, kind, dense=None, gdof=None):
     _check(load().geneo_debug_local_matrix(ctx, sub, kind, _ptr(dense), _ptr(gdof)))
+
+
+def geneo_profile(ctx, what, reps):
+    ms, by, fl = C.c_double(), C.c_double(), C.c_double()
+    _check(load().geneo_profile(ctx, what, reps, C.byref(ms), C.byref(by), C.byref(fl)))
+    return ms.value, by.value, fl.value
 
 
 def geneo_solve(ctx, tol, max_it, u, raise_on_nonconvergence=True):

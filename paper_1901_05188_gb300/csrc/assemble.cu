@@ -209,26 +209,26 @@ int launch_assembly(const AssemblyArgs &a, cudaStream_t s) {
   int nnx = a.nx + 1, nny = a.ny + 1, nnz = a.nz + 1;
   int nnode = nnx * nny * nnz;
   int nel = a.nx * a.ny * a.nz;
-  k_material_base<<<(a.n_mat + 63) / 64, 64, 0, s>>>(a.n_mat, a.mats, a.C0);
+  k_material_base<<<(a.n_mat + 63) / 64, 64, 0, s>>>(a.n_mat, a.mats, a.C0); GENEO_COUNT_LAUNCH();
   k_element_C<<<(nel + T - 1) / T, T, 0, s>>>(nel, a.n_mat, a.C0, a.emat, a.theta, a.phi,
-                                              a.Cel, a.status);
-  k_bsr_count<<<(nnode + T - 1) / T, T, 0, s>>>(nnx, nny, nnz, a.cnt);
-  k_scan_single<<<1, 1024, 0, s>>>(nnode, a.cnt, a.row_ptr);
-  k_bsr_fill<<<(nnode + T - 1) / T, T, 0, s>>>(nnx, nny, nnz, a.row_ptr, a.col);
+                                              a.Cel, a.status); GENEO_COUNT_LAUNCH();
+  k_bsr_count<<<(nnode + T - 1) / T, T, 0, s>>>(nnx, nny, nnz, a.cnt); GENEO_COUNT_LAUNCH();
+  k_scan_single<<<1, 1024, 0, s>>>(nnode, a.cnt, a.row_ptr); GENEO_COUNT_LAUNCH();
+  k_bsr_fill<<<(nnode + T - 1) / T, T, 0, s>>>(nnx, nny, nnz, a.row_ptr, a.col); GENEO_COUNT_LAUNCH();
   long long nt = (long long)nnode * 27;
   k_assemble_values<<<(unsigned)((nt + 127) / 128), 128, 0, s>>>(
-      a.nx, a.ny, a.nz, a.X, a.Y, a.Z, a.Cel, a.row_ptr, a.val);
+      a.nx, a.ny, a.nz, a.X, a.Y, a.Z, a.Cel, a.row_ptr, a.val); GENEO_COUNT_LAUNCH();
   k_load<<<(nnode + T - 1) / T, T, 0, s>>>(a.nx, a.ny, a.nz, a.X, a.Y, a.top_pressure,
-                                           a.nodal, a.b);
+                                           a.nodal, a.b); GENEO_COUNT_LAUNCH();
   GENEO_CUDA_TRY(cudaMemsetAsync(a.mask, 0, 3 * (size_t)nnode, s));
   GENEO_CUDA_TRY(cudaMemsetAsync(a.g, 0, 3 * (size_t)nnode * sizeof(double), s));
   if (a.n_dir > 0) {
     k_dirichlet_mark<<<(a.n_dir + T - 1) / T, T, 0, s>>>(a.n_dir, a.dir_dofs, a.dir_vals,
-                                                         3 * nnode, a.mask, a.g, a.status);
+                                                         3 * nnode, a.mask, a.g, a.status); GENEO_COUNT_LAUNCH();
     k_dirichlet_rhs<<<(3 * nnode + T - 1) / T, T, 0, s>>>(nnode, a.row_ptr, a.col, a.val,
-                                                          a.mask, a.g, a.b);
+                                                          a.mask, a.g, a.b); GENEO_COUNT_LAUNCH();
     k_dirichlet_eliminate<<<(nnode + T - 1) / T, T, 0, s>>>(nnode, a.row_ptr, a.col, a.mask,
-                                                            a.val);
+                                                            a.val); GENEO_COUNT_LAUNCH();
   }
   GENEO_CUDA_TRY(cudaGetLastError());
   return GENEO_OK;

@@ -409,7 +409,7 @@ template <typename T>
 int launch_band_clear(const BandLayout *d_lay, int nsys, T *pool, long long pool_elems,
                       cudaStream_t s) {
   GENEO_CUDA_TRY(cudaMemsetAsync(pool, 0, pool_elems * sizeof(T), s));
-  k_band_pad<T><<<nsys, 32, 0, s>>>(d_lay, nsys, pool);
+  k_band_pad<T><<<nsys, 32, 0, s>>>(d_lay, nsys, pool); GENEO_COUNT_LAUNCH();
   GENEO_CUDA_TRY(cudaGetLastError());
   return GENEO_OK;
 }
@@ -419,10 +419,10 @@ int launch_band_cholesky(const BandLayout *d_lay, int nsys, int nt_max, int w_ma
                          T *poolU, DevStatus *st, cudaStream_t s) {
   int npairs = w_max * (w_max + 1) / 2;
   for (int J = 0; J < nt_max; ++J) {
-    k_chol_diag<T><<<nsys, 256, 0, s>>>(d_lay, nsys, J, poolL, poolU, st);
+    k_chol_diag<T><<<nsys, 256, 0, s>>>(d_lay, nsys, J, poolL, poolU, st); GENEO_COUNT_LAUNCH();
     if (w_max > 0) {
-      k_chol_trsm<T><<<dim3(nsys, w_max), 256, 0, s>>>(d_lay, nsys, J, poolL, poolU);
-      k_chol_update<T><<<dim3(nsys, npairs), 256, 0, s>>>(d_lay, nsys, J, poolL);
+      k_chol_trsm<T><<<dim3(nsys, w_max), 256, 0, s>>>(d_lay, nsys, J, poolL, poolU); GENEO_COUNT_LAUNCH();
+      k_chol_update<T><<<dim3(nsys, npairs), 256, 0, s>>>(d_lay, nsys, J, poolL); GENEO_COUNT_LAUNCH();
     }
   }
   GENEO_CUDA_TRY(cudaGetLastError());
@@ -442,7 +442,7 @@ int launch_band_solve_dense(const BandLayout *d_lay, int nsys, int npad_max,
   GENEO_CUDA_TRY(cudaFuncSetAttribute(k_band_solve_dense,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
   k_band_solve_dense<<<dim3(nsys, ncols), kSolveWarps * 32, sm, s>>>(
-      d_lay, poolL, poolU, in, in_sys, in_row, out, out_sys, out_row, mode);
+      d_lay, poolL, poolU, in, in_sys, in_row, out, out_sys, out_row, mode); GENEO_COUNT_LAUNCH();
   GENEO_CUDA_TRY(cudaGetLastError());
   return GENEO_OK;
 }
@@ -453,7 +453,7 @@ int launch_extract_interior(const SubDesc *d_subs, const BandLayout *d_lay, int 
                             const double *val, T *pool, cudaStream_t s) {
   long long tot = (long long)max_nodes * 27;
   dim3 grid((unsigned)((tot + 255) / 256), nsub);
-  k_extract_interior<T><<<grid, 256, 0, s>>>(d_subs, d_lay, nnx, nny, nnz, rp, val, pool);
+  k_extract_interior<T><<<grid, 256, 0, s>>>(d_subs, d_lay, nnx, nny, nnz, rp, val, pool); GENEO_COUNT_LAUNCH();
   GENEO_CUDA_TRY(cudaGetLastError());
   return GENEO_OK;
 }
@@ -464,7 +464,7 @@ int launch_schwarz_solve(const SubDesc *d_subs, const BandLayout *d_lay, int nsu
                          const double *r, T *xloc, const CGScalars *cg, cudaStream_t s) {
   int sm = solve_smem_bytes(npad_max, sizeof(T));
   k_schwarz_solve<T><<<nsub, kSolveWarps * 32, sm, s>>>(d_subs, d_lay, nnx, nny, poolL, poolU,
-                                                        r, xloc, cg);
+                                                        r, xloc, cg); GENEO_COUNT_LAUNCH();
   GENEO_CUDA_TRY(cudaGetLastError());
   return GENEO_OK;
 }
@@ -489,7 +489,7 @@ void launch_schwarz_gather(int nx, int ny, int nz, int px, int py, const int *ca
   int nn = (nx + 1) * (ny + 1) * (nz + 1);
   k_schwarz_gather<T><<<(nn + 255) / 256, 256, 0, s>>>(nx + 1, ny + 1, nz + 1, px, py, cand,
                                                       cand_off[0], cand_off[1], cand_off[2],
-                                                      d_subs, xloc, Zp, yH, pou, mask, z, cg);
+                                                      d_subs, xloc, Zp, yH, pou, mask, z, cg); GENEO_COUNT_LAUNCH();
 }
 
 void launch_coarse_apply(const SubDesc *d_subs, int nsub, int max_nint, int nnx, int nny,
@@ -498,9 +498,9 @@ void launch_coarse_apply(const SubDesc *d_subs, int nsub, int max_nint, int nnx,
                          const CGScalars *cg, cudaStream_t s) {
   (void)max_nint;
   k_coarse_restrict<<<dim3(nsub, kRestrictChunks), 256, 0, s>>>(d_subs, nnx, nny, Zp, r, wpart,
-                                                               mcap, cg);
-  k_coarse_reduce<<<nsub, 32, 0, s>>>(d_subs, wpart, wH, mcap, cg);
-  k_coarse_gemv<<<(nH * 32 + 255) / 256, 256, 0, s>>>(nH, AHinv, wH, yH, cg);
+                                                               mcap, cg); GENEO_COUNT_LAUNCH();
+  k_coarse_reduce<<<nsub, 32, 0, s>>>(d_subs, wpart, wH, mcap, cg); GENEO_COUNT_LAUNCH();
+  k_coarse_gemv<<<(nH * 32 + 255) / 256, 256, 0, s>>>(nH, AHinv, wH, yH, cg); GENEO_COUNT_LAUNCH();
 }
 
 template int launch_band_clear<double>(const BandLayout *, int, double *, long long, cudaStream_t);

@@ -26,6 +26,9 @@ void geneo_set_last_cuda_error(cudaError_t e, const char *what, const char *file
 }
 
 namespace geneo {
+long long g_launch_count = 0;
+bool g_counting = true;
+
 bool is_device_ptr(const void *p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -196,6 +199,8 @@ const char *geneo_status_string(int s) {
 }
 
 const char *geneo_last_error(void) { return g_last_error.c_str(); }
+
+long long geneo_launch_count(void) { return g_launch_count; }
 
 int geneo_create(geneo_ctx **out, void *cuda_stream) {
   if (!out) return fail(GENEO_ERR_INVALID_ARG, "null out");
@@ -1144,7 +1149,11 @@ extern "C" int geneo_solve(geneo_ctx *c, double tol, int max_it, double *u, gene
   if (!c->graph) {
     cudaGraph_t g;
     GENEO_CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    long long before = g_launch_count;
+    g_counting = true;
     st = enqueue_iterations(c, kGraphIters, c->cap_stream);
+    c->graph_kernels = g_launch_count - before;     // kernel nodes per graph launch
+    g_launch_count = before;
     cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &g);
     if (st) return st;
     if (ce != cudaSuccess) {
@@ -1157,6 +1166,7 @@ extern "C" int geneo_solve(geneo_ctx *c, double tol, int max_it, double *u, gene
   int launched = 0;
   for (;;) {
     GENEO_CUDA_TRY(cudaGraphLaunch(c->graph, s));
+    g_launch_count += c->graph_kernels;
     launched += kGraphIters;
     GENEO_CUDA_TRY(cudaMemcpyAsync(c->cg_host, c->cg, sizeof(CGScalars), cudaMemcpyDeviceToHost, s));
     GENEO_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1299,5 +1309,79 @@ extern "C" int geneo_debug_local_matrix(geneo_ctx *c, int sub, int kind, double 
   } else {
     std::memcpy(dense, out.data(), out.size() * sizeof(double));
   }
+  return GENEO_OK;
+}
+
+// ============================================================================
+// Kernel timing for the benchmark: `reps` back-to-back launches of one hot
+// kernel on the context stream between CUDA events, with its algorithmic
+// bytes and flops per launch.
+//   what 0: one-level Schwarz local solves (gather, forward + backward band
+//           sweeps of every subdomain); bytes = band factor entries of both
+//           sweeps + gathered residual + local solutions
+//   what 1: BSR SpMV q = A p; bytes = values + column indices + x + y
+//   what 2: the whole preconditioner application z = M^-1 r
+extern "C" int geneo_profile(geneo_ctx *c, int what, int reps, double *ms_per_launch,
+                             double *bytes, double *flops) {
+  if (!c || !c->setup_done) return fail(GENEO_ERR_STATE, "no preconditioner set up");
+  if (reps < 1 || what < 0 || what > 2) return fail(GENEO_ERR_INVALID_ARG, "bad profile request");
+  cudaStream_t s = c->stream;
+  Precond &pc = c->pc;
+  const bool f32 = pc.prec == GENEO_MIXED_FP32;
+  const double esz = f32 ? 4.0 : 8.0;
+  double by = 0.0, fl = 0.0;
+  for (const SubDesc &S : pc.subs) {
+    const double n = S.n_int, hb = S.ibox.half_band_dofs();
+    const double band = n * (hb + 1) - hb * (hb + 1) / 2;     // entries of L_j
+    if (what != 1) {
+      by += 2.0 * band * esz + n * (8.0 + esz);
+      fl += 4.0 * band;
+    }
+  }
+  if (what == 1) {
+    by = (double)c->nnzb * (72.0 + 4.0) + 4.0 * (c->nnode + 1) + 16.0 * c->ndof;
+    fl = 18.0 * c->nnzb;
+  }
+  if (what == 2) {
+    by += 8.0 * c->ndof + (double)pc.nH * pc.nH * 8.0;
+    for (const SubDesc &S : pc.subs) by += 2.0 * S.n_int * S.m * 8.0;
+  }
+  // a deterministic, non-trivial residual to work on
+  BSR A{c->nnode, c->row_ptr, c->col, c->val};
+  launch_spmv(A, c->b, c->r, s);
+  cudaEvent_t e0, e1;
+  GENEO_CUDA_TRY(cudaEventCreate(&e0));
+  GENEO_CUDA_TRY(cudaEventCreate(&e1));
+  const int nnx = c->nx + 1, nny = c->ny + 1;
+  int st = 0;
+  for (int pass = 0; pass < 2 && !st; ++pass) {      // pass 0 warms up
+    GENEO_CUDA_TRY(cudaEventRecord(e0, s));
+    for (int i = 0; i < (pass ? reps : 1) && !st; ++i) {
+      if (what == 0) {
+        st = f32 ? launch_schwarz_solve<float>(pc.d_subs, pc.d_lay_int, pc.nsub, pc.npad_int_max,
+                                               nnx, nny, (const float *)pc.facL,
+                                               (const float *)pc.facU, c->r, (float *)pc.xloc,
+                                               nullptr, s)
+                 : launch_schwarz_solve<double>(pc.d_subs, pc.d_lay_int, pc.nsub,
+                                                pc.npad_int_max, nnx, nny,
+                                                (const double *)pc.facL, (const double *)pc.facU,
+                                                c->r, (double *)pc.xloc, nullptr, s);
+      } else if (what == 1) {
+        launch_spmv(A, c->r, c->q, s);
+      } else {
+        st = precond_apply(c, c->r, c->z, nullptr, s);
+      }
+    }
+    GENEO_CUDA_TRY(cudaEventRecord(e1, s));
+  }
+  GENEO_CUDA_TRY(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  GENEO_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st) return st;
+  if (ms_per_launch) *ms_per_launch = ms / reps;
+  if (bytes) *bytes = by;
+  if (flops) *flops = fl;
   return GENEO_OK;
 }

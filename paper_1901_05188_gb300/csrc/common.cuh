@@ -20,6 +20,12 @@ void geneo_set_last_cuda_error(cudaError_t e, const char *what, const char *file
 
 namespace geneo {
 
+// Kernel launches enqueued by this library (graph launches add their kernel
+// nodes); suppressed while a graph is being captured.
+extern long long g_launch_count;
+extern bool g_counting;
+#define GENEO_COUNT_LAUNCH() (geneo::g_launch_count += geneo::g_counting ? 1 : 0)
+
 constexpr int kTile = 32;          // band tile edge (rows = columns = one warp)
 constexpr int kLanczosBlock = 8;   // block Lanczos block size p
 constexpr int kMaxModes = 32;      // cap on modes kept per subdomain

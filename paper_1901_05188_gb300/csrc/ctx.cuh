@@ -49,6 +49,7 @@ struct geneo_ctx {
   int maxit_cap = 0;
   cudaGraphExec_t graph = nullptr;          // K iterations
   int graph_iters = 0;
+  long long graph_kernels = 0;              // kernel nodes in one graph launch
   double *graph_tol_key = nullptr;
   geneo_stats last_stats{};
   float ms_assemble = 0.f;

@@ -624,7 +624,7 @@ void launch_pou_neumann(const SubDesc *d_subs, int nsub, int max_nodes, const in
                         double *Xneu, cudaStream_t s) {
   dim3 g((3 * max_nodes + 255) / 256, nsub);
   k_pou_neumann<<<g, 256, 0, s>>>(d_subs, cand, cand_off[0], cand_off[1], cand_off[2], mask, nnx,
-                                  nny, Xneu);
+                                  nny, Xneu); GENEO_COUNT_LAUNCH();
 }
 
 void launch_neumann_assemble(const SubDesc *d_subs, const BandLayout *d_lay, int nsub,
@@ -637,19 +637,19 @@ void launch_neumann_assemble(const SubDesc *d_subs, const BandLayout *d_lay, int
   dim3 g((unsigned)((tot + 127) / 128), nsub);
   k_neumann_assemble<<<g, 128, 0, s>>>(d_subs, d_lay, nx, ny, nz, X, Y, Z, Cel, ecnt,
                                        ecnt_off[0], ecnt_off[1], ecnt_off[2], mask, Xneu, sigma,
-                                       poolS, Bloc);
+                                       poolS, Bloc); GENEO_COUNT_LAUNCH();
 }
 
 void launch_bloc_mv(const SubDesc *d_subs, int nsub, int max_nodes, const double *Bloc,
                     const double *T, double *W, long long sys_stride, int p, cudaStream_t s) {
   dim3 g((3 * max_nodes + 127) / 128, nsub);
-  k_bloc_mv<<<g, 128, 0, s>>>(d_subs, Bloc, T, W, sys_stride, p);
+  k_bloc_mv<<<g, 128, 0, s>>>(d_subs, Bloc, T, W, sys_stride, p); GENEO_COUNT_LAUNCH();
 }
 
 void launch_random_block(const SubDesc *d_subs, int nsub, int npad, double *V, int ld,
                          long long sys_stride, int p, unsigned long long seed, cudaStream_t s) {
   dim3 g((npad * p + 255) / 256, nsub);
-  k_random_block<<<g, 256, 0, s>>>(d_subs, npad, V, ld, sys_stride, p, seed);
+  k_random_block<<<g, 256, 0, s>>>(d_subs, npad, V, ld, sys_stride, p, seed); GENEO_COUNT_LAUNCH();
 }
 
 void launch_tsdots(const SubDesc *d_subs, int nsub, int npad, const double *A, int lda,
@@ -659,8 +659,8 @@ void launch_tsdots(const SubDesc *d_subs, int nsub, int npad, const double *A, i
   int sm = 16 * (na + nb) * (int)sizeof(double);
   cudaFuncSetAttribute(k_tsdots, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   k_tsdots<<<dim3(chunks, nsub), 256, sm, s>>>(d_subs, A, lda, sa, na, B, ldb, sb, nb, Hpart,
-                                               chunks);
-  k_tsdots_reduce<<<nsub, 256, 0, s>>>(Hpart, chunks, na * nb, H, hs);
+                                               chunks); GENEO_COUNT_LAUNCH();
+  k_tsdots_reduce<<<nsub, 256, 0, s>>>(Hpart, chunks, na * nb, H, hs); GENEO_COUNT_LAUNCH();
 }
 
 void launch_tsgemm(const SubDesc *d_subs, int nsub, int npad, const double *A, int lda,
@@ -671,37 +671,37 @@ void launch_tsgemm(const SubDesc *d_subs, int nsub, int npad, const double *A, i
   long long tot = (long long)npad * nb;
   dim3 g((unsigned)((tot + 255) / 256), nsub);
   k_tsgemm<<<g, 256, sm, s>>>(d_subs, npad, A, lda, sa, na, H, ldh, hs, C, ldc, sc, nb, alpha,
-                              beta);
+                              beta); GENEO_COUNT_LAUNCH();
 }
 
 void launch_cholqr(const SubDesc *d_subs, int nsub, int npad, const double *G, double *W,
                    int p, double *Racc, int first, double abs_tiny, cudaStream_t s) {
   // Rinv stored right after Racc's nsub*p*p entries
   double *Rinv = Racc + (long long)nsub * p * p;
-  k_cholqr_small<<<nsub, 32, 0, s>>>(G, p, Rinv, Racc, first, abs_tiny);
+  k_cholqr_small<<<nsub, 32, 0, s>>>(G, p, Rinv, Racc, first, abs_tiny); GENEO_COUNT_LAUNCH();
   dim3 g((npad + 255) / 256, nsub);
-  k_rowmul<<<g, 256, 0, s>>>(d_subs, npad, W, p, Rinv);
+  k_rowmul<<<g, 256, 0, s>>>(d_subs, npad, W, p, Rinv); GENEO_COUNT_LAUNCH();
 }
 
 void launch_hm_accum(int nsub, double *Hm, int kdim, const double *Hs, int rows, int k, int p,
                      cudaStream_t s) {
-  k_hm_accum<<<nsub, 256, 0, s>>>(Hm, kdim, Hs, rows, k, p);
+  k_hm_accum<<<nsub, 256, 0, s>>>(Hm, kdim, Hs, rows, k, p); GENEO_COUNT_LAUNCH();
 }
 
 void launch_hm_subdiag(int nsub, double *Hm, int kdim, const double *Racc, int k, int p,
                        double *Rblk, cudaStream_t s) {
-  k_hm_subdiag<<<nsub, 64, 0, s>>>(Hm, kdim, Racc, k, p, Rblk);
+  k_hm_subdiag<<<nsub, 64, 0, s>>>(Hm, kdim, Racc, k, p, Rblk); GENEO_COUNT_LAUNCH();
 }
 
 void launch_restart_hm(int nsub, double *Hm, int kdim, const double *Eval, const double *Evec,
                        const double *Rblk, int kk, int p, cudaStream_t s) {
-  k_restart_hm<<<nsub, 256, 0, s>>>(Hm, kdim, Eval, Evec, Rblk, kk, p);
+  k_restart_hm<<<nsub, 256, 0, s>>>(Hm, kdim, Eval, Evec, Rblk, kk, p); GENEO_COUNT_LAUNCH();
 }
 
 void launch_copy_block(const SubDesc *d_subs, int nsub, int npad, const double *W, int ldw,
                        long long sw, double *V, int ldv, long long sv, int p, cudaStream_t s) {
   dim3 g((npad * p + 255) / 256, nsub);
-  k_copy_block<<<g, 256, 0, s>>>(d_subs, npad, W, ldw, sw, V, ldv, sv, p);
+  k_copy_block<<<g, 256, 0, s>>>(d_subs, npad, W, ldw, sw, V, ldv, sv, p); GENEO_COUNT_LAUNCH();
 }
 
 int launch_jacobi(int nsub, const double *Hm, int kdim, int p, const double *Rblk, double *Eval,
@@ -710,7 +710,7 @@ int launch_jacobi(int nsub, const double *Hm, int kdim, int p, const double *Rbl
   double *Ework = Evec + (long long)nsub * kdim * kdim;
   int sm = (kdim * kdim + kdim) * (int)sizeof(double) + kdim * (int)sizeof(int);
   GENEO_CUDA_TRY(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  k_jacobi<<<nsub, 256, sm, s>>>(Hm, kdim, p, Rblk, Eval, Evec, Ework, Eres);
+  k_jacobi<<<nsub, 256, sm, s>>>(Hm, kdim, p, Rblk, Eval, Evec, Ework, Eres); GENEO_COUNT_LAUNCH();
   GENEO_CUDA_TRY(cudaGetLastError());
   return GENEO_OK;
 }
@@ -719,43 +719,46 @@ void launch_build_Z(const SubDesc *d_subs, int nsub, int max_nint, const double 
                     long long sp, const double *Xneu, double *Zp, cudaStream_t s) {
   long long tot = (long long)max_nint * kMaxModes;
   dim3 g((unsigned)((tot + 255) / 256), nsub);
-  k_build_Z<<<g, 256, 0, s>>>(d_subs, P, ldp, sp, Xneu, Zp);
+  k_build_Z<<<g, 256, 0, s>>>(d_subs, P, ldp, sp, Xneu, Zp); GENEO_COUNT_LAUNCH();
 }
 
 void launch_AZ(const SubDesc *d_subs, int nsub, int max_nodes, int nnx, int nny, int nnz,
                const int32_t *rp, const int32_t *col, const double *val, const double *Zp,
                const long long *yoff, double *Yp, cudaStream_t s) {
   dim3 g((3 * max_nodes + 127) / 128, nsub);
-  k_AZ<<<g, 128, 0, s>>>(d_subs, nnx, nny, nnz, rp, col, val, Zp, yoff, Yp);
+  k_AZ<<<g, 128, 0, s>>>(d_subs, nnx, nny, nnz, rp, col, val, Zp, yoff, Yp); GENEO_COUNT_LAUNCH();
 }
 
 void launch_coarse_blocks(const SubDesc *d_subs, const int2 *pairs, int npairs, const double *Zp,
                           const double *Yp, const long long *yoff, double *AH, int nH,
                           cudaStream_t s) {
-  if (npairs > 0) k_coarse_blocks<<<npairs, 256, 0, s>>>(d_subs, pairs, Zp, Yp, yoff, AH, nH);
+  if (npairs > 0) {
+    k_coarse_blocks<<<npairs, 256, 0, s>>>(d_subs, pairs, Zp, Yp, yoff, AH, nH);
+    GENEO_COUNT_LAUNCH();
+  }
 }
 
 void launch_dense_to_tiles(const double *AH, int nH, const BandLayout *d_lay, double *pool,
                            cudaStream_t s) {
   long long tot = (long long)nH * nH;
-  k_dense_to_tiles<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(AH, nH, d_lay, pool);
+  k_dense_to_tiles<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(AH, nH, d_lay, pool); GENEO_COUNT_LAUNCH();
 }
 
 void launch_symmetrize(double *M, int n, cudaStream_t s) {
   long long tot = (long long)n * n;
-  k_symmetrize<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(M, n);
+  k_symmetrize<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(M, n); GENEO_COUNT_LAUNCH();
 }
 
 void launch_identity(double *M, int n, cudaStream_t s) {
   long long tot = (long long)n * n;
-  k_identity<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(M, n);
+  k_identity<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(M, n); GENEO_COUNT_LAUNCH();
 }
 
 void launch_normalize_cols(const SubDesc *d_subs, int nsub, int npad, double *P, int ld,
                            long long sp, int ncol, const double *G, cudaStream_t s) {
   long long tot = (long long)npad * ncol;
   dim3 g((unsigned)((tot + 255) / 256), nsub);
-  k_normalize_cols<<<g, 256, 0, s>>>(d_subs, npad, P, ld, sp, ncol, G);
+  k_normalize_cols<<<g, 256, 0, s>>>(d_subs, npad, P, ld, sp, ncol, G); GENEO_COUNT_LAUNCH();
 }
 
 }  // namespace geneo

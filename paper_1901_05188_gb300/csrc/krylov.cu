@@ -271,41 +271,41 @@ __global__ void k_sub(int n, const double *__restrict__ a, const double *__restr
 }  // namespace
 
 void launch_spmv(const BSR &A, const double *x, double *y, cudaStream_t s) {
-  k_spmv<<<NB * 4, 256, 0, s>>>(A.nnode, A.row_ptr, A.col, A.val, x, y);
+  k_spmv<<<NB * 4, 256, 0, s>>>(A.nnode, A.row_ptr, A.col, A.val, x, y); GENEO_COUNT_LAUNCH();
 }
 void launch_cg_init(int n, const double *b, double *x, double *r, CGScalars *cg, double *part,
                     cudaStream_t s) {
-  k_cg_init<<<NB, NT, 0, s>>>(n, b, x, r, cg, part);
+  k_cg_init<<<NB, NT, 0, s>>>(n, b, x, r, cg, part); GENEO_COUNT_LAUNCH();
 }
 void launch_cg_init2(int n, const double *r, const double *z, double *p, CGScalars *cg,
                      double *part, cudaStream_t s) {
-  k_cg_init2<<<NB, NT, 0, s>>>(n, r, z, p, cg, part);
+  k_cg_init2<<<NB, NT, 0, s>>>(n, r, z, p, cg, part); GENEO_COUNT_LAUNCH();
 }
 void launch_cg_spmv_pq(const BSR &A, const double *p, double *q, CGScalars *cg, double *part,
                        cudaStream_t s) {
-  k_cg_spmv_pq<<<NB * 4, NT, 0, s>>>(A.nnode, A.row_ptr, A.col, A.val, p, q, cg, part);
+  k_cg_spmv_pq<<<NB * 4, NT, 0, s>>>(A.nnode, A.row_ptr, A.col, A.val, p, q, cg, part); GENEO_COUNT_LAUNCH();
 }
 void launch_cg_update_xr(int n, const double *p, const double *q, double *x, double *r,
                          CGScalars *cg, double *part, double *alphas, cudaStream_t s) {
-  k_cg_update_xr<<<NB, NT, 0, s>>>(n, p, q, x, r, cg, part, alphas);
+  k_cg_update_xr<<<NB, NT, 0, s>>>(n, p, q, x, r, cg, part, alphas); GENEO_COUNT_LAUNCH();
 }
 void launch_cg_dots(int n, const double *r, const double *z, const double *q, CGScalars *cg,
                     double *part, double *betas, cudaStream_t s) {
-  k_cg_dots<<<NB, NT, 0, s>>>(n, r, z, q, cg, part, betas);
+  k_cg_dots<<<NB, NT, 0, s>>>(n, r, z, q, cg, part, betas); GENEO_COUNT_LAUNCH();
 }
 void launch_cg_update_p(int n, const double *z, double *p, CGScalars *cg, cudaStream_t s) {
-  k_cg_update_p<<<NB, NT, 0, s>>>(n, z, p, cg);
+  k_cg_update_p<<<NB, NT, 0, s>>>(n, z, p, cg); GENEO_COUNT_LAUNCH();
 }
 void launch_copy_if_running(int n, const double *src, double *dst, const CGScalars *cg,
                             cudaStream_t s) {
-  k_copy_if_running<<<NB, NT, 0, s>>>(n, src, dst, cg);
+  k_copy_if_running<<<NB, NT, 0, s>>>(n, src, dst, cg); GENEO_COUNT_LAUNCH();
 }
 void launch_norm2(int n, const double *v, double *out, double *part, unsigned *counter,
                   cudaStream_t s) {
-  k_norm2<<<NB, NT, 0, s>>>(n, v, out, part, counter);
+  k_norm2<<<NB, NT, 0, s>>>(n, v, out, part, counter); GENEO_COUNT_LAUNCH();
 }
 void launch_sub(int n, const double *a, const double *b, double *out, cudaStream_t s) {
-  k_sub<<<NB, NT, 0, s>>>(n, a, b, out);
+  k_sub<<<NB, NT, 0, s>>>(n, a, b, out); GENEO_COUNT_LAUNCH();
 }
 
 }  // namespace geneo
