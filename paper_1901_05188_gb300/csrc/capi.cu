@@ -25,6 +25,8 @@ void geneo_set_last_cuda_error(cudaError_t e, const char *what, const char *file
   g_last_error = buf;
 }
 
+void geneo_set_last_message(const char *msg) { g_last_error = msg; }
+
 namespace geneo {
 long long g_launch_count = 0;
 bool g_counting = true;
@@ -748,7 +750,9 @@ static int setup_coarse(geneo_ctx *c, SetupPlan &P, cudaStream_t s) {
         launch_copy_block(pc.d_subs, nsub, npad, pc.W, p, sW, pc.V + (k + 1) * p, ldv, sV, p, s);
     }
     GENEO_CUDA_TRY(cudaGetLastError());
-    if ((st = launch_jacobi(nsub, pc.Hm, kdim, p, pc.Rblk, pc.Eval, pc.Evec, pc.Eres, s))) return st;
+    if ((st = launch_ritz_eig(nsub, pc.Hm, kdim, std::max(kk, mcap), p, pc.Rblk, pc.Eval, pc.Evec,
+                              pc.Eres, s)))
+      return st;
     ++pc.eig_cycles;
     GENEO_CUDA_TRY(cudaMemcpyAsync(ev.data(), pc.Eval, ev.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
     GENEO_CUDA_TRY(cudaMemcpyAsync(er.data(), pc.Eres, er.size() * sizeof(double), cudaMemcpyDeviceToHost, s));

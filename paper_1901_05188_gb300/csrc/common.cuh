@@ -17,6 +17,7 @@
   } while (0)
 
 void geneo_set_last_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+void geneo_set_last_message(const char *msg);
 
 namespace geneo {
 

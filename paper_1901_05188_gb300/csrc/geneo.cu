@@ -366,130 +366,270 @@ __global__ void k_copy_block(const SubDesc *subs, int npad, const double *W, int
   V[j * sv + (long long)row * ldv + b] = W[j * sw + (long long)row * ldw + b];
 }
 
-// Cyclic Jacobi (round-robin ordering) on the symmetrised projected matrix.
+// Ritz pairs of the symmetrised projected matrix H (n x n, n <= kMaxKdim):
+// Householder reduction to tridiagonal form (H = Q T Q^T), the nw largest
+// eigenvalues of T by Sturm-sequence bisection, their eigenvectors by inverse
+// iteration (re-orthogonalised inside clusters of close eigenvalues), and the
+// back-transformation y = Q x.  One block per subdomain; eigenvalues are
+// returned in descending order, columns nw..n-1 of Evec are zero.
+constexpr int kMaxKdim = 128;
+
+__device__ __forceinline__ int sturm_count(const double *d, const double *e2, int n, double x,
+                                           double pivmin) {
+  // number of eigenvalues of T smaller than x
+  int cnt = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  if (q < 0) ++cnt;
+  for (int i = 1; i < n; ++i) {
+    q = d[i] - x - e2[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    if (q < 0) ++cnt;
+  }
+  return cnt;
+}
+
 __global__ void __launch_bounds__(256)
-    k_jacobi(const double *Hm, int n, int p, const double *Rblk, double *Eval, double *Evec,
-             double *Ework, double *Eres) {
+    k_ritz_eig(const double *Hm, int n, int nw, int p, const double *Rblk, double *Eval,
+               double *Evec, double *Eres) {
   const int j = blockIdx.x;
+  const int ld = n + 1;
   extern __shared__ __align__(16) unsigned char smraw[];
-  double *A = reinterpret_cast<double *>(smraw);            // n x n
-  double *cs = A + n * n;                                   // n/2
-  double *sn = cs + n / 2;
-  int *pp = reinterpret_cast<int *>(sn + n / 2);
-  int *qq = pp + n / 2;
+  double *A = reinterpret_cast<double *>(smraw);   // n x ld, Householder vectors below diagonal
+  double *d = A + n * ld;                          // diagonal of T
+  double *e = d + n;                               // off-diagonal of T
+  double *e2 = e + n;                              // squares
+  double *lam = e2 + n;                            // wanted eigenvalues (descending)
+  double *vs = lam + n;                            // current Householder vector / work
+  double *ps = vs + n;                             // A v / q
   __shared__ double red[8];
-  __shared__ int stop;
-  double *E = Ework + (long long)j * n * n;
+  __shared__ double bounds[2];
   const double *H = Hm + (long long)j * n * n;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    int r = e / n, c = e - r * n;
-    A[e] = 0.5 * (H[e] + H[c * n + r]);
-    E[e] = (r == c) ? 1.0 : 0.0;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int t = tid; t < n * n; t += blockDim.x) {
+    int r = t / n, c = t - r * n;
+    A[r * ld + c] = 0.5 * (H[t] + H[c * n + r]);
   }
   __syncthreads();
-  const int half = n / 2;
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    // convergence test: off-diagonal vs total Frobenius norm
-    double off = 0.0, tot = 0.0;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-      int r = e / n, c = e - r * n;
-      double v = A[e] * A[e];
-      tot += v;
-      if (r != c) off += v;
-    }
-    off = warp_sum(off);
-    tot = warp_sum(tot);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = off;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double o = 0.0;
-      for (int w = 0; w < 8; ++w) o += red[w];
-      red[0] = o;
-    }
-    __syncthreads();
-    off = red[0];
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = tot;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t2 = 0.0;
-      for (int w = 0; w < 8; ++w) t2 += red[w];
-      stop = !(off > 1e-32 * t2) ? 1 : 0;
-    }
-    __syncthreads();
-    if (stop) break;
-    for (int round = 0; round < n - 1; ++round) {
-      for (int i = threadIdx.x; i < half; i += blockDim.x) {
-        int a = (i == 0) ? n - 1 : (round + i) % (n - 1);
-        int b = (round - i + n - 1) % (n - 1);
-        int P = min(a, b), Q = max(a, b);
-        double apq = A[P * n + Q];
-        double c = 1.0, s = 0.0;
-        if (apq != 0.0) {
-          double tau = (A[Q * n + Q] - A[P * n + P]) / (2.0 * apq);
-          double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-          c = 1.0 / sqrt(1.0 + t * t);
-          s = t * c;
-        }
-        cs[i] = c;
-        sn[i] = s;
-        pp[i] = P;
-        qq[i] = Q;
-      }
-      __syncthreads();
-      // columns: A <- A J
-      for (int e = threadIdx.x; e < half * n; e += blockDim.x) {
-        int i = e / n, r = e - i * n;
-        int P = pp[i], Q = qq[i];
-        double c = cs[i], s = sn[i];
-        double ap = A[r * n + P], aq = A[r * n + Q];
-        A[r * n + P] = c * ap - s * aq;
-        A[r * n + Q] = s * ap + c * aq;
-        double ep = E[r * n + P], eq = E[r * n + Q];
-        E[r * n + P] = c * ep - s * eq;
-        E[r * n + Q] = s * ep + c * eq;
-      }
-      __syncthreads();
-      // rows: A <- J^T A
-      for (int e = threadIdx.x; e < half * n; e += blockDim.x) {
-        int i = e / n, cc = e - i * n;
-        int P = pp[i], Q = qq[i];
-        double c = cs[i], s = sn[i];
-        double ap = A[P * n + cc], aq = A[Q * n + cc];
-        A[P * n + cc] = c * ap - s * aq;
-        A[Q * n + cc] = s * ap + c * aq;
-      }
-      __syncthreads();
-    }
-  }
-  // sort eigenvalues descending (selection order by rank)
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double v = A[i * n + i];
-    int rank = 0;
-    for (int k = 0; k < n; ++k) {
-      double u = A[k * n + k];
-      rank += (u > v) || (u == v && k < i);
-    }
-    pp[rank] = i;   // reuse: pp[rank] = column index
-  }
-  __syncthreads();
-  double *out = Evec + (long long)j * n * n;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    int r = e / n, c = e - r * n;
-    out[e] = E[r * n + pp[c]];
-  }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) Eval[(long long)j * n + i] = A[pp[i] * n + pp[i]];
-  __syncthreads();
-  // residual estimate || R_s * E[(s-1)p : sp, i] ||
-  const double *Rb = Rblk + (long long)j * p * p;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  // ---- Householder tridiagonalisation (lower)
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;
     double s2 = 0.0;
+    for (int i = tid; i < m; i += blockDim.x) {
+      double x = A[(k + 1 + i) * ld + k];
+      s2 += x * x;
+    }
+    s2 = warp_sum(s2);
+    if (lane == 0) red[warp] = s2;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < 8; ++w) t += red[w];
+      double x0 = A[(k + 1) * ld + k];
+      double nrm = sqrt(t);
+      double alpha = (x0 >= 0.0) ? -nrm : nrm;
+      double vnorm2 = t - x0 * x0 + (x0 - alpha) * (x0 - alpha);
+      d[k] = A[k * ld + k];
+      if (nrm == 0.0 || vnorm2 <= 0.0) {
+        e[k] = 0.0;
+        red[0] = 0.0;           // no reflection
+      } else {
+        e[k] = alpha;
+        red[0] = 1.0 / sqrt(vnorm2);
+        red[1] = alpha;
+      }
+    }
+    __syncthreads();
+    const double inv = red[0];
+    if (inv == 0.0) {
+      for (int i = tid; i < m; i += blockDim.x) A[(k + 1 + i) * ld + k] = 0.0;
+      __syncthreads();
+      continue;
+    }
+    const double alpha = red[1];
+    for (int i = tid; i < m; i += blockDim.x) {
+      double v = A[(k + 1 + i) * ld + k] - (i == 0 ? alpha : 0.0);
+      v *= inv;
+      vs[i] = v;
+      A[(k + 1 + i) * ld + k] = v;       // keep v for the back-transformation
+    }
+    __syncthreads();
+    // p = A_sub v
+    for (int i = tid; i < m; i += blockDim.x) {
+      const double *row = A + (k + 1 + i) * ld + (k + 1);
+      double s = 0.0;
+      for (int c = 0; c < m; ++c) s += row[c] * vs[c];
+      ps[i] = s;
+    }
+    __syncthreads();
+    double b = 0.0;
+    for (int i = tid; i < m; i += blockDim.x) b += vs[i] * ps[i];
+    b = warp_sum(b);
+    if (lane == 0) red[warp] = b;
+    __syncthreads();
+    double beta = 0.0;
+    for (int w = 0; w < 8; ++w) beta += red[w];
+    __syncthreads();
+    for (int i = tid; i < m; i += blockDim.x) ps[i] = 2.0 * ps[i] - 2.0 * beta * vs[i];
+    __syncthreads();
+    // A_sub -= v q^T + q v^T
+    for (int t = tid; t < m * m; t += blockDim.x) {
+      int r = t / m, c = t - r * m;
+      A[(k + 1 + r) * ld + (k + 1 + c)] -= vs[r] * ps[c] + ps[r] * vs[c];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (n >= 2) {
+      d[n - 2] = A[(n - 2) * ld + (n - 2)];
+      e[n - 2] = A[(n - 1) * ld + (n - 2)];
+    }
+    d[n - 1] = A[(n - 1) * ld + (n - 1)];
+    e[n - 1] = 0.0;
+    double lo = 1e300, hi = -1e300, mx = 0.0;
+    for (int i = 0; i < n; ++i) {
+      double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + fabs(e[i]);
+      lo = fmin(lo, d[i] - r);
+      hi = fmax(hi, d[i] + r);
+      mx = fmax(mx, fabs(d[i]) + r);
+    }
+    bounds[0] = lo - 1e-12 * mx - 1e-300;
+    bounds[1] = hi + 1e-12 * mx + 1e-300;
+    red[0] = mx;
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += blockDim.x) e2[i] = e[i] * e[i];
+  __syncthreads();
+  const double tnorm = red[0];
+  const double pivmin = fmax(1e-290, 1e-30 * tnorm * tnorm) / fmax(tnorm, 1e-300);
+  // ---- bisection: thread q finds the q-th largest eigenvalue
+  for (int q = tid; q < nw; q += blockDim.x) {
+    const int target = n - 1 - q;          // index from the bottom
+    double a = bounds[0], bnd = bounds[1];
+    for (int it = 0; it < 200; ++it) {
+      double mid = 0.5 * (a + bnd);
+      if (sturm_count(d, e2, n, mid, pivmin) > target) bnd = mid;
+      else a = mid;
+      if (bnd - a <= 2.2e-16 * (fabs(a) + fabs(bnd)) + 1e-300) break;
+    }
+    lam[q] = 0.5 * (a + bnd);
+  }
+  __syncthreads();
+  // ---- inverse iteration on T - lam I (partial pivoting), vectors to Evec columns
+  double *Ev = Evec + (long long)j * n * n;
+  for (int q = tid; q < nw; q += blockDim.x) {
+    double u0[kMaxKdim], u1[kMaxKdim], u2[kMaxKdim], lm[kMaxKdim], x[kMaxKdim];
+    unsigned char piv[kMaxKdim];
+    const double lq = lam[q];
+    const double tiny = 1e-15 * fmax(tnorm, 1e-300);
+    for (int i = 0; i < n; ++i) {
+      u0[i] = d[i] - lq;
+      u1[i] = (i + 1 < n) ? e[i] : 0.0;
+      u2[i] = 0.0;
+    }
+    for (int i = 0; i + 1 < n; ++i) {
+      double sub = e[i];
+      if (fabs(u0[i]) >= fabs(sub)) {
+        piv[i] = 0;
+        if (fabs(u0[i]) < tiny) u0[i] = (u0[i] >= 0 ? tiny : -tiny);
+        lm[i] = sub / u0[i];
+        u0[i + 1] -= lm[i] * u1[i];
+      } else {
+        piv[i] = 1;
+        lm[i] = u0[i] / sub;
+        double t0 = u0[i + 1], t1 = (i + 2 < n) ? u1[i + 1] : 0.0;
+        u0[i] = sub;
+        double n11 = u1[i] - lm[i] * t0;
+        double n12 = -lm[i] * t1;
+        u1[i] = t0;
+        u2[i] = t1;
+        u0[i + 1] = n11;
+        if (i + 2 < n) u1[i + 1] = n12;
+      }
+    }
+    if (fabs(u0[n - 1]) < tiny) u0[n - 1] = (u0[n - 1] >= 0 ? tiny : -tiny);
+    // deterministic start vector
+    unsigned long long h = 0x9E3779B97F4A7C15ull * (unsigned long long)(q + 1) ^ (unsigned long long)j;
+    for (int i = 0; i < n; ++i) {
+      h = splitmix64(h + i);
+      x[i] = double(h >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+    }
+    for (int it = 0; it < 3; ++it) {
+      for (int i = 0; i + 1 < n; ++i) {
+        if (piv[i]) {
+          double t = x[i];
+          x[i] = x[i + 1];
+          x[i + 1] = t;
+        }
+        x[i + 1] -= lm[i] * x[i];
+      }
+      x[n - 1] /= u0[n - 1];
+      if (n >= 2) x[n - 2] = (x[n - 2] - u1[n - 2] * x[n - 1]) / u0[n - 2];
+      for (int i = n - 3; i >= 0; --i) x[i] = (x[i] - u1[i] * x[i + 1] - u2[i] * x[i + 2]) / u0[i];
+      double s = 0.0;
+      for (int i = 0; i < n; ++i) s += x[i] * x[i];
+      s = 1.0 / sqrt(s);
+      for (int i = 0; i < n; ++i) x[i] *= s;
+    }
+    for (int i = 0; i < n; ++i) Ev[(long long)i * n + q] = x[i];
+  }
+  for (int t = tid; t < n * n; t += blockDim.x) {
+    int c = t - (t / n) * n;
+    if (c >= nw) Ev[t] = 0.0;
+  }
+  __syncthreads();
+  // ---- re-orthogonalise inside clusters of close eigenvalues (warp 0, in order)
+  if (warp == 0) {
+    const double ctol = 1e-7 * fmax(fabs(lam[0]), 1e-300);
+    int c0 = 0;
+    for (int q = 1; q < nw; ++q) {
+      if (fabs(lam[q] - lam[q - 1]) > ctol) {
+        c0 = q;
+        continue;
+      }
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int r = c0; r < q; ++r) {
+          double s = 0.0;
+          for (int i = lane; i < n; i += 32) s += Ev[(long long)i * n + r] * Ev[(long long)i * n + q];
+          s = warp_sum(s);
+          for (int i = lane; i < n; i += 32) Ev[(long long)i * n + q] -= s * Ev[(long long)i * n + r];
+          __syncwarp();
+        }
+        double s = 0.0;
+        for (int i = lane; i < n; i += 32) s += Ev[(long long)i * n + q] * Ev[(long long)i * n + q];
+        s = warp_sum(s);
+        s = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+        for (int i = lane; i < n; i += 32) Ev[(long long)i * n + q] *= s;
+        __syncwarp();
+      }
+    }
+  }
+  __syncthreads();
+  // ---- back-transformation y = H_0 H_1 ... H_{n-3} x (thread q owns column q)
+  for (int q = tid; q < nw; q += blockDim.x) {
+    double x[kMaxKdim];
+    for (int i = 0; i < n; ++i) x[i] = Ev[(long long)i * n + q];
+    for (int k = n - 3; k >= 0; --k) {
+      double s = 0.0;
+      for (int i = k + 1; i < n; ++i) s += A[i * ld + k] * x[i];
+      s *= 2.0;
+      for (int i = k + 1; i < n; ++i) x[i] -= s * A[i * ld + k];
+    }
+    for (int i = 0; i < n; ++i) Ev[(long long)i * n + q] = x[i];
+    Eval[(long long)j * n + q] = lam[q];
+    // residual estimate || R_s y[n-p .. n-1] ||
+    const double *Rb = Rblk + (long long)j * p * p;
+    double r2 = 0.0;
     for (int a = 0; a < p; ++a) {
       double v = 0.0;
-      for (int b = 0; b < p; ++b) v += Rb[a * p + b] * out[(long long)(n - p + b) * n + i];
-      s2 += v * v;
+      for (int b = 0; b < p; ++b) v += Rb[a * p + b] * x[n - p + b];
+      r2 += v * v;
     }
-    Eres[(long long)j * n + i] = sqrt(s2);
+    Eres[(long long)j * n + q] = sqrt(r2);
+  }
+  for (int q = nw + tid; q < n; q += blockDim.x) {
+    Eval[(long long)j * n + q] = 0.0;
+    Eres[(long long)j * n + q] = 0.0;
   }
 }
 
@@ -704,13 +844,12 @@ void launch_copy_block(const SubDesc *d_subs, int nsub, int npad, const double *
   k_copy_block<<<g, 256, 0, s>>>(d_subs, npad, W, ldw, sw, V, ldv, sv, p); GENEO_COUNT_LAUNCH();
 }
 
-int launch_jacobi(int nsub, const double *Hm, int kdim, int p, const double *Rblk, double *Eval,
-                  double *Evec, double *Eres, cudaStream_t s) {
-  // Ework follows Evec
-  double *Ework = Evec + (long long)nsub * kdim * kdim;
-  int sm = (kdim * kdim + kdim) * (int)sizeof(double) + kdim * (int)sizeof(int);
-  GENEO_CUDA_TRY(cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  k_jacobi<<<nsub, 256, sm, s>>>(Hm, kdim, p, Rblk, Eval, Evec, Ework, Eres); GENEO_COUNT_LAUNCH();
+int launch_ritz_eig(int nsub, const double *Hm, int kdim, int nw, int p, const double *Rblk,
+                    double *Eval, double *Evec, double *Eres, cudaStream_t s) {
+  if (kdim > kMaxKdim || nw > kdim) return GENEO_ERR_INVALID_ARG;
+  int sm = (kdim * (kdim + 1) + 6 * kdim) * (int)sizeof(double);
+  GENEO_CUDA_TRY(cudaFuncSetAttribute(k_ritz_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  k_ritz_eig<<<nsub, 256, sm, s>>>(Hm, kdim, nw, p, Rblk, Eval, Evec, Eres); GENEO_COUNT_LAUNCH();
   GENEO_CUDA_TRY(cudaGetLastError());
   return GENEO_OK;
 }

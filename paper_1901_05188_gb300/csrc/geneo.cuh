@@ -58,10 +58,11 @@ void launch_copy_block(const SubDesc *d_subs, int nsub, int npad, const double *
                        long long sw, double *V, int ldv, long long sv, int p,
                        cudaStream_t s);
 
-// Symmetric Jacobi eigensolver of the kdim x kdim projected matrices; values
-// sorted descending; residual estimates from the last Lanczos block.
-int launch_jacobi(int nsub, const double *Hm, int kdim, int p, const double *Rblk,
-                  double *Eval, double *Evec, double *Eres, cudaStream_t s);
+// The nw largest Ritz pairs of the kdim x kdim projected matrices (Householder
+// tridiagonalisation, bisection, inverse iteration); values descending;
+// residual estimates from the last Lanczos block.
+int launch_ritz_eig(int nsub, const double *Hm, int kdim, int nw, int p, const double *Rblk,
+                    double *Eval, double *Evec, double *Eres, cudaStream_t s);
 
 // Z_j = X_j P_j on interior dofs (row-major n_int x m_j).
 void launch_build_Z(const SubDesc *d_subs, int nsub, int max_nint, const double *P, int ldp,
