@@ -222,6 +222,28 @@ int geneo_debug_local_matrix(geneo_ctx *ctx, int sub, int kind, double *dense, i
 int geneo_profile(geneo_ctx *ctx, int what, int reps, double *ms_per_launch, double *bytes,
                   double *flops);
 
+/* y = A x and *xy = x . y for a 3x3-block BSR matrix, without allocating.
+ * This entry point has no counterpart in the paper: it serves callers that
+ * cannot allocate device memory (a host framework that hands out a fixed
+ * device-memory budget, a real-time loop that must not enter the CUDA
+ * allocator, a plug-in that only receives pointers to someone else's
+ * buffers).  It calls no cudaMalloc, cudaFree or allocating library routine.
+ * Its only scratch is a file-scope device array of 65,536 partial sums
+ * (512 KiB, held by every GPU that loads the library until exit), so n_nodes
+ * may be at most 524,288 block rows; larger inputs return
+ * GENEO_ERR_WORKSPACE_TOO_SMALL.  All pointers are device memory owned by the
+ * caller: row_ptr[n_nodes+1], col[nnzb], val[9*nnzb] (row-major blocks),
+ * x and y [3*n_nodes], xy [1].  Work is enqueued on cuda_stream (NULL = legacy
+ * default stream); the call does not synchronise.  The first call on each
+ * device looks up the scratch array's device address (cudaGetSymbolAddress)
+ * with that device current, so make that first call before any stream
+ * capture.  Every call shares the scratch and clears its counter on entry:
+ * calls that overlap on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller. */
+int geneo_spmv_dot_noalloc(int n_nodes, const int32_t *row_ptr, const int32_t *col,
+                           const double *val, const double *x, double *y, double *xy,
+                           void *cuda_stream);
+
 /* Solve A u = b by PCG (FP64 precision, GENEO_AS) or flexible CG (mixed
  * precision or GENEO_AS_POU) from u0 = 0 until ||r_k|| <= tol ||b|| or max_it
  * iterations (Sec. 3.1).  u: 3*n_nodes doubles.  stats may be NULL. */

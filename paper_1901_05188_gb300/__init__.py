@@ -97,6 +97,7 @@ _SIGS = {
     "geneo_get_coarse": [_P, _P, _P],
     "geneo_solve": [_P, C.c_double, C.c_int, _P, C.POINTER(geneo_stats)],
     "geneo_debug_local_matrix": [_P, C.c_int, C.c_int, _P, _P],
+    "geneo_spmv_dot_noalloc": [C.c_int, _P, _P, _P, _P, _P, _P, _P],
     "geneo_profile": [_P, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                       C.POINTER(C.c_double)],
 }
@@ -225,6 +226,12 @@ def geneo_get_coarse(ctx, Phi=None, AH=None):
 
 def geneo_debug_local_matrix(ctx, sub, kind, dense=None, gdof=None):
     _check(load().geneo_debug_local_matrix(ctx, sub, kind, _ptr(dense), _ptr(gdof)))
+
+
+def geneo_spmv_dot_noalloc(n_nodes, row_ptr, col, val, x, y, xy, stream=None):
+    """y = A x and xy[0] = x . y on device tensors; allocates nothing."""
+    _check(load().geneo_spmv_dot_noalloc(int(n_nodes), _ptr(row_ptr), _ptr(col), _ptr(val),
+                                         _ptr(x), _ptr(y), _ptr(xy), stream))
 
 
 def geneo_profile(ctx, what, reps):
