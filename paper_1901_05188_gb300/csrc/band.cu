@@ -46,58 +46,59 @@ __global__ void __launch_bounds__(256) k_chol_diag(const BandLayout *lay, int ns
   if (J >= L.nt) return;
   __shared__ T A[32][33];
   __shared__ T X[32][33];
+  __shared__ T rd[32];
   __shared__ int bad;
-  __shared__ int badrow;
   T *t = tile_ptr(poolL, L, J, 0);
   for (int e = threadIdx.x; e < 1024; e += 256) A[e & 31][e >> 5] = t[e];
-  if (threadIdx.x == 0) bad = 0;
+  if (threadIdx.x == 0) bad = -1;
   __syncthreads();
-  for (int k = 0; k < 32; ++k) {
-    if (threadIdx.x == 0) {
-      T d = A[k][k];
-      if (!(d > T(0))) {
-        if (!bad) badrow = J * 32 + k;
-        bad = 1;
-        d = T(1);
-      }
-      A[k][k] = sqrt(d);
-    }
-    __syncthreads();
-    T dk = A[k][k];
-    for (int i = k + 1 + threadIdx.x; i < 32; i += 256) A[i][k] /= dk;
-    __syncthreads();
-    int m = 31 - k;
-    for (int e = threadIdx.x; e < m * m; e += 256) {
-      int i = k + 1 + e / m, c = k + 1 + e % m;
-      if (c <= i) A[i][c] -= A[i][k] * A[c][k];
-    }
-    __syncthreads();
-  }
-  // X = inv(L): thread c solves L x = e_c by forward substitution
+  // unblocked right-looking Cholesky by one warp (no block barriers, one
+  // reciprocal per column instead of a division per entry)
   if (threadIdx.x < 32) {
-    int c = threadIdx.x;
+    const int lane = threadIdx.x;
+    for (int k = 0; k < 32; ++k) {
+      T dkk = A[k][k];
+      if (!(dkk > T(0))) {
+        if (lane == 0 && bad < 0) bad = J * 32 + k;
+        dkk = T(1);
+      }
+      T lkk = sqrt(dkk);
+      T inv = T(1) / lkk;
+      __syncwarp();
+      if (lane == k) A[k][k] = lkk;
+      if (lane > k) A[lane][k] *= inv;
+      __syncwarp();
+      if (lane > k) {
+        const T aik = A[lane][k];
+        for (int c = k + 1; c <= lane; ++c) A[lane][c] -= aik * A[c][k];
+      }
+      __syncwarp();
+    }
+    rd[lane] = T(1) / A[lane][lane];
+    __syncwarp();
+    // X = inv(L): lane c solves L x = e_c
+    const int c = lane;
     for (int i = 0; i < 32; ++i) {
-      T s = (i == c) ? T(1) : T(0);
-      if (i > c) {
-        for (int k = c; k < i; ++k) s -= A[i][k] * X[k][c];
-      } else if (i < c) {
+      if (i < c) {
         X[i][c] = T(0);
         continue;
       }
-      X[i][c] = s / A[i][i];
+      T s = (i == c) ? T(1) : T(0);
+      for (int k = c; k < i; ++k) s -= A[i][k] * X[k][c];
+      X[i][c] = s * rd[i];
     }
   }
   __syncthreads();
   T *u = tile_ptr(poolU, L, J, 0);
   for (int e = threadIdx.x; e < 1024; e += 256) {
-    int r = e & 31, c = e >> 5;
-    t[e] = X[r][c];          // inv(L_JJ), column-major
-    u[e] = X[c][r];          // inv(L_JJ)^T
+    int r = e & 31, cc = e >> 5;
+    t[e] = X[r][cc];          // inv(L_JJ), column-major
+    u[e] = X[cc][r];          // inv(L_JJ)^T
   }
-  if (threadIdx.x == 0 && bad) {
+  if (threadIdx.x == 0 && bad >= 0) {
     if (atomicCAS(&st->code, 0, GENEO_ERR_NOT_SPD) == 0) {
       st->where = j;
-      st->detail = badrow;
+      st->detail = bad;
     }
   }
 }
@@ -205,36 +206,6 @@ __device__ __forceinline__ void band_sweep(const T *__restrict__ pool, const Ban
     }
     __syncthreads();
   }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kSolveWarps * 32)
-    k_schwarz_solve(const SubDesc *subs, const BandLayout *lay, int nnx, int nny,
-                    const T *poolL, const T *poolU, const double *__restrict__ r,
-                    T *__restrict__ xloc, const CGScalars *cg) {
-  if (cg && cg->done) return;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T *red = reinterpret_cast<T *>(smraw);
-  T *y = red + kSolveWarps * 32;
-  const int j = blockIdx.x;
-  const SubDesc &S = subs[j];
-  const BandLayout L = lay[j];
-  const int n = S.n_int, npad = L.nt * 32;
-  for (int l = threadIdx.x; l < npad; l += blockDim.x) {
-    T v = T(0);
-    if (l < n) {
-      int node = l / 3, c = l - 3 * node;
-      int gi, gj, gk;
-      S.ibox.global(node, gi, gj, gk);
-      v = T(r[3 * (gi + nnx * (gj + nny * gk)) + c]);
-    }
-    y[l] = v;
-  }
-  __syncthreads();
-  band_sweep(poolL, L, y, red, false);
-  band_sweep(poolU, L, y, red, true);
-  T *out = xloc + S.v_int;
-  for (int l = threadIdx.x; l < n; l += blockDim.x) out[l] = y[l];
 }
 
 __global__ void __launch_bounds__(kSolveWarps * 32)
@@ -459,28 +430,6 @@ int launch_extract_interior(const SubDesc *d_subs, const BandLayout *d_lay, int 
 }
 
 template <typename T>
-int launch_schwarz_solve(const SubDesc *d_subs, const BandLayout *d_lay, int nsub,
-                         int npad_max, int nnx, int nny, const T *poolL, const T *poolU,
-                         const double *r, T *xloc, const CGScalars *cg, cudaStream_t s) {
-  int sm = solve_smem_bytes(npad_max, sizeof(T));
-  k_schwarz_solve<T><<<nsub, kSolveWarps * 32, sm, s>>>(d_subs, d_lay, nnx, nny, poolL, poolU,
-                                                        r, xloc, cg); GENEO_COUNT_LAUNCH();
-  GENEO_CUDA_TRY(cudaGetLastError());
-  return GENEO_OK;
-}
-
-template <typename T>
-int prepare_schwarz_solve(int npad_max) {
-  int sm = solve_smem_bytes(npad_max, sizeof(T));
-  if (sm > 227 * 1024) return GENEO_ERR_INVALID_ARG;
-  GENEO_CUDA_TRY(cudaFuncSetAttribute(k_schwarz_solve<T>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
-  return GENEO_OK;
-}
-template int prepare_schwarz_solve<double>(int);
-template int prepare_schwarz_solve<float>(int);
-
-template <typename T>
 void launch_schwarz_gather(int nx, int ny, int nz, int px, int py, const int *cand,
                            const int cand_off[3], const SubDesc *d_subs, const T *xloc,
                            const double *Zp, const double *yH, int pou,
@@ -515,12 +464,6 @@ template int launch_extract_interior<double>(const SubDesc *, const BandLayout *
 template int launch_extract_interior<float>(const SubDesc *, const BandLayout *, int, int, int,
                                             int, int, const int32_t *, const double *, float *,
                                             cudaStream_t);
-template int launch_schwarz_solve<double>(const SubDesc *, const BandLayout *, int, int, int, int,
-                                          const double *, const double *, const double *,
-                                          double *, const CGScalars *, cudaStream_t);
-template int launch_schwarz_solve<float>(const SubDesc *, const BandLayout *, int, int, int, int,
-                                         const float *, const float *, const double *, float *,
-                                         const CGScalars *, cudaStream_t);
 template void launch_schwarz_gather<double>(int, int, int, int, int, const int *, const int[3],
                                             const SubDesc *, const double *, const double *,
                                             const double *, int, const uint8_t *, double *,

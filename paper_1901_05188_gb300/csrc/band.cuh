@@ -40,11 +40,16 @@ int launch_extract_interior(const SubDesc *d_subs, const BandLayout *d_lay, int 
 template <typename T>
 int prepare_schwarz_solve(int npad_max);
 
-// One-level Schwarz local solves: x_j = A_j^-1 R_j r for every subdomain.
+// One-level Schwarz local solves: x_j = A_j^-1 R_j r for every subdomain, one
+// thread-block cluster of `cluster` CTAs (1, 2, 4 or 8) per subdomain.
 template <typename T>
 int launch_schwarz_solve(const SubDesc *d_subs, const BandLayout *d_lay, int nsub,
                          int npad_max, int nnx, int nny, const T *poolL, const T *poolU,
-                         const double *r, T *xloc, const CGScalars *cg, cudaStream_t s);
+                         const double *r, T *xloc, const CGScalars *cg, int cluster,
+                         DevStatus *status, cudaStream_t s);
+// Cluster size that fills the GPU: the largest power of two <= 8 with
+// 2 * nsub * size <= number of SMs (at least 1).
+int schwarz_cluster_size(int nsub, int sm_count);
 
 // z = sum_j R_j^T (D_j x_j + Z_j y_j) (deterministic gather over subdomains).
 template <typename T>

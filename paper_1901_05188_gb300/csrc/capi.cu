@@ -666,7 +666,7 @@ static int precond_apply(geneo_ctx *c, const double *r, double *z, const CGScala
   if (pc.prec == GENEO_MIXED_FP32) {
     if ((st = launch_schwarz_solve<float>(pc.d_subs, pc.d_lay_int, pc.nsub, pc.npad_int_max, nnx,
                                           nny, (const float *)pc.facL, (const float *)pc.facU, r,
-                                          (float *)pc.xloc, cg, s)))
+                                          (float *)pc.xloc, cg, pc.cluster, c->status, s)))
       return st;
     launch_schwarz_gather<float>(c->nx, c->ny, c->nz, pc.part.px, pc.part.py, pc.d_cand,
                                  pc.cand_off, pc.d_subs, (const float *)pc.xloc, pc.Zp,
@@ -674,7 +674,8 @@ static int precond_apply(geneo_ctx *c, const double *r, double *z, const CGScala
   } else {
     if ((st = launch_schwarz_solve<double>(pc.d_subs, pc.d_lay_int, pc.nsub, pc.npad_int_max,
                                            nnx, nny, (const double *)pc.facL,
-                                           (const double *)pc.facU, r, (double *)pc.xloc, cg, s)))
+                                           (const double *)pc.facU, r, (double *)pc.xloc, cg,
+                                           pc.cluster, c->status, s)))
       return st;
     launch_schwarz_gather<double>(c->nx, c->ny, c->nz, pc.part.px, pc.part.py, pc.d_cand,
                                   pc.cand_off, pc.d_subs, (const double *)pc.xloc, pc.Zp,
@@ -928,6 +929,9 @@ int geneo_setup(geneo_ctx *c, const geneo_partition *part, const geneo_modes *mo
   B.cap = c->ws1_bytes;
   plan_setup(B, c, P);
   const bool f32 = prec == GENEO_MIXED_FP32;
+  int sms = 0;
+  GENEO_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+  pc.cluster = schwarz_cluster_size(P.nsub, sms);
   if (f32) {
     if ((st = prepare_schwarz_solve<float>(pc.npad_int_max))) return fail(st, "subdomain too large for shared memory");
   } else {
@@ -1168,14 +1172,20 @@ extern "C" int geneo_solve(geneo_ctx *c, double tol, int max_it, double *u, gene
     cudaGraphDestroy(g);
   }
   int launched = 0;
+  DevStatus dst{};
   for (;;) {
     GENEO_CUDA_TRY(cudaGraphLaunch(c->graph, s));
     g_launch_count += c->graph_kernels;
     launched += kGraphIters;
     GENEO_CUDA_TRY(cudaMemcpyAsync(c->cg_host, c->cg, sizeof(CGScalars), cudaMemcpyDeviceToHost, s));
+    GENEO_CUDA_TRY(cudaMemcpyAsync(&dst, c->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     GENEO_CUDA_TRY(cudaStreamSynchronize(s));
-    if (c->cg_host->done) break;
+    if (c->cg_host->done || dst.code != 0) break;
     if (launched > h.maxit + 2 * kGraphIters) break;
+  }
+  if (dst.code != 0) {
+    int code = check_status(c);
+    return fail(code, "device status set during the iteration (e.g. a synchronisation time-out)");
   }
   GENEO_CUDA_TRY(cudaEventRecord(e1, s));
   h = *c->cg_host;
@@ -1365,11 +1375,11 @@ extern "C" int geneo_profile(geneo_ctx *c, int what, int reps, double *ms_per_la
         st = f32 ? launch_schwarz_solve<float>(pc.d_subs, pc.d_lay_int, pc.nsub, pc.npad_int_max,
                                                nnx, nny, (const float *)pc.facL,
                                                (const float *)pc.facU, c->r, (float *)pc.xloc,
-                                               nullptr, s)
+                                               nullptr, pc.cluster, c->status, s)
                  : launch_schwarz_solve<double>(pc.d_subs, pc.d_lay_int, pc.nsub,
                                                 pc.npad_int_max, nnx, nny,
                                                 (const double *)pc.facL, (const double *)pc.facU,
-                                                c->r, (double *)pc.xloc, nullptr, s);
+                                                c->r, (double *)pc.xloc, nullptr, pc.cluster, c->status, s);
       } else if (what == 1) {
         launch_spmv(A, c->r, c->q, s);
       } else {

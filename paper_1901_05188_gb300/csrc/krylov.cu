@@ -34,30 +34,48 @@ __device__ __forceinline__ double sum_partials(const double *part, int n, double
   return block_sum<NT>(v, sh);
 }
 
-// One warp per block row: the row's 9*nb values are read contiguously by the
-// warp (coalesced), lane e handles value e: block e/9, entry (r, c).
+// One warp per block row.  Lanes 8r..8r+7 own output component r (lanes
+// 24..31 idle): lane q of group r multiplies row r of blocks q, q+8, q+16,
+// q+24 with x, so each stored value takes exactly one FMA (FP64 issue is the
+// scarce resource on this GPU), all loads are issued before the products, and
+// the group sum is three xor-shuffles.  The row's values are contiguous, so
+// the group's loads stay inside a few L1 lines.
 __device__ __forceinline__ void spmv_row(const int32_t *__restrict__ rp,
                                          const int32_t *__restrict__ col,
                                          const double *__restrict__ val,
                                          const double *__restrict__ x, int row, int lane,
                                          double &y0, double &y1, double &y2) {
-  int base = rp[row];
-  int ne = 9 * (rp[row + 1] - base);
-  const double *v = val + 9 * (size_t)base;
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-  for (int e = lane; e < ne; e += 32) {
-    int blk = (e * 57) >> 9;          // e / 9 for e < 256
-    int rc = e - 9 * blk;
-    int r = (rc * 11) >> 5;           // rc / 3 for rc < 9
-    int c = rc - 3 * r;
-    double prod = __ldg(v + e) * __ldg(x + 3 * __ldg(col + base + blk) + c);
-    if (r == 0) a0 += prod;
-    else if (r == 1) a1 += prod;
-    else a2 += prod;
+  const int base = rp[row];
+  const int nb = rp[row + 1] - base;
+  const int r = lane >> 3, q = lane & 7;
+  double acc = 0.0;
+  if (r < 3) {
+    double vv[12], xx[12];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int b = q + 8 * k;
+      if (b < nb) {
+        const double *vb = val + 9 * (size_t)(base + b) + 3 * r;
+        const double *xb = x + 3 * __ldg(col + base + b);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          vv[3 * k + c] = __ldg(vb + c);
+          xx[3 * k + c] = __ldg(xb + c);
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) vv[3 * k + c] = xx[3 * k + c] = 0.0;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc = fma(vv[k], xx[k], acc);
   }
-  y0 = warp_sum(a0);
-  y1 = warp_sum(a1);
-  y2 = warp_sum(a2);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+  y0 = __shfl_sync(0xffffffffu, acc, 0);
+  y1 = __shfl_sync(0xffffffffu, acc, 8);
+  y2 = __shfl_sync(0xffffffffu, acc, 16);
 }
 
 __global__ void __launch_bounds__(256) k_spmv(int nnode, const int32_t *__restrict__ rp,

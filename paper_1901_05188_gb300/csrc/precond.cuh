@@ -25,6 +25,7 @@ struct Precond {
   geneo_schwarz schwarz = GENEO_AS;
   geneo_coarse coarse = GENEO_COARSE_GENEO;
   int nsub = 0;
+  int cluster = 1;                // CTAs per subdomain in the Schwarz local solves
   std::vector<SubDesc> subs;
   SubDesc *d_subs = nullptr;
   BandLayout *d_lay_int = nullptr, *d_lay_neu = nullptr, *d_lay_H = nullptr;
