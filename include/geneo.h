@@ -115,6 +115,7 @@ typedef struct {
   double eig_max_residual;        /* max Ritz residual of the kept eigenpairs */
   int failed_subdomain;           /* subdomain of a GENEO_ERR_NOT_SPD, else -1 */
   int flexible;                   /* 1 if flexible CG was used */
+  int eig_cycles;                 /* block-Lanczos restart cycles of the last set-up */
 } geneo_stats;
 
 /* Create a context whose work runs on `cuda_stream` (a cudaStream_t; NULL =
@@ -216,7 +217,9 @@ int geneo_debug_local_matrix(geneo_ctx *ctx, int sub, int kind, double *dense, i
  * with CUDA events (after one warm-up launch) and report its algorithmic
  * traffic: what 0 = the one-level Schwarz local solves (Sec. 3.1,
  * eqn:onelevelAS: gather, forward and backward band sweeps, both factor
- * streams), 1 = the BSR SpMV, 2 = the whole preconditioner application.
+ * streams), 1 = the BSR SpMV, 2 = the whole preconditioner application,
+ * 3 = one FP64 backward sweep of the GenEO eigensolver's band solves with 8
+ * right-hand sides per subdomain (Sec. 3.3.2 shift-and-invert operator).
  * Outputs (any may be NULL): mean ms per launch, bytes and flops per launch.
  * Needs geneo_setup; overwrites the solver's internal work vectors. */
 int geneo_profile(geneo_ctx *ctx, int what, int reps, double *ms_per_launch, double *bytes,

@@ -62,7 +62,7 @@ class geneo_stats(C.Structure):
                 ("ms_setup_coarse", C.c_float), ("ms_setup_factor", C.c_float),
                 ("ms_solve", C.c_float), ("bytes_per_iter", C.c_double),
                 ("eig_max_residual", C.c_double), ("failed_subdomain", C.c_int),
-                ("flexible", C.c_int)]
+                ("flexible", C.c_int), ("eig_cycles", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

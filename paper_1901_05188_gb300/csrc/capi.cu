@@ -1217,6 +1217,7 @@ extern "C" int geneo_solve(geneo_ctx *c, double tol, int max_it, double *u, gene
   out.eig_max_residual = pc.eig_max_res;
   out.failed_subdomain = -1;
   out.flexible = flexible ? 1 : 0;
+  out.eig_cycles = pc.eig_cycles;
   if (!flexible && h.it > 0) {
     int k = std::min(h.it, kHistCap);
     std::vector<double> al(k), be(std::max(k - 1, 0));
@@ -1335,12 +1336,15 @@ extern "C" int geneo_debug_local_matrix(geneo_ctx *c, int sub, int kind, double 
 //           sweeps + gathered residual + local solutions
 //   what 1: BSR SpMV q = A p; bytes = values + column indices + x + y
 //   what 2: the whole preconditioner application z = M^-1 r
+//   what 3: one FP64 sweep of the GenEO eigensolver's band solves (all
+//           subdomains, 8 right-hand sides); flops = 2 x 8 x entries of L_j
 extern "C" int geneo_profile(geneo_ctx *c, int what, int reps, double *ms_per_launch,
                              double *bytes, double *flops) {
   if (!c || !c->setup_done) return fail(GENEO_ERR_STATE, "no preconditioner set up");
-  if (reps < 1 || what < 0 || what > 2) return fail(GENEO_ERR_INVALID_ARG, "bad profile request");
-  cudaStream_t s = c->stream;
   Precond &pc = c->pc;
+  if (reps < 1 || what < 0 || what > 3) return fail(GENEO_ERR_INVALID_ARG, "bad profile request");
+  if (what == 3 && !pc.neuL) return fail(GENEO_ERR_STATE, "no GenEO eigensolver data");
+  cudaStream_t s = c->stream;
   const bool f32 = pc.prec == GENEO_MIXED_FP32;
   const double esz = f32 ? 4.0 : 8.0;
   double by = 0.0, fl = 0.0;
@@ -1359,6 +1363,15 @@ extern "C" int geneo_profile(geneo_ctx *c, int what, int reps, double *ms_per_la
   if (what == 2) {
     by += 8.0 * c->ndof + (double)pc.nH * pc.nH * 8.0;
     for (const SubDesc &S : pc.subs) by += 2.0 * S.n_int * S.m * 8.0;
+  }
+  if (what == 3) {
+    by = fl = 0.0;
+    for (const SubDesc &S : pc.subs) {
+      const double n = S.n_neu, hb = S.nbox.half_band_dofs();
+      const double band = n * (hb + 1) - hb * (hb + 1) / 2;
+      by += band * 8.0 + 2.0 * n * kLanczosBlock * 8.0;
+      fl += 2.0 * kLanczosBlock * band;
+    }
   }
   // a deterministic, non-trivial residual to work on
   BSR A{c->nnode, c->row_ptr, c->col, c->val};
@@ -1382,6 +1395,11 @@ extern "C" int geneo_profile(geneo_ctx *c, int what, int reps, double *ms_per_la
                                                 c->r, (double *)pc.xloc, nullptr, pc.cluster, c->status, s);
       } else if (what == 1) {
         launch_spmv(A, c->r, c->q, s);
+      } else if (what == 3) {
+        const int p = kLanczosBlock, ldv = pc.kdim + p, npad = pc.npad_neu_max;
+        st = launch_band_solve_dense(pc.d_lay_neu, pc.nsub, npad, pc.neuL, pc.neuU, pc.V,
+                                     (long long)npad * ldv, ldv, pc.T1, (long long)npad * p, p, p,
+                                     2, s);
       } else {
         st = precond_apply(c, c->r, c->z, nullptr, s);
       }
