@@ -39,63 +39,64 @@ __global__ void k_band_pad(const BandLayout *lay, int nsys, T *pool) {
 // ---- tile Cholesky ---------------------------------------------------------
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_chol_diag(const BandLayout *lay, int nsys, int J,
-                                                   T *poolL, T *poolU, DevStatus *st) {
+__global__ void __launch_bounds__(1024) k_chol_diag(const BandLayout *lay, int nsys, int J,
+                                                    T *poolL, T *poolU, DevStatus *st) {
   int j = blockIdx.x;
   BandLayout L = lay[j];
   if (J >= L.nt) return;
   __shared__ T A[32][33];
   __shared__ T X[32][33];
-  __shared__ T rd[32];
+  __shared__ T Y[32][33];
+  __shared__ T piv[2];
   __shared__ int bad;
+  const int tid = threadIdx.x, r = tid & 31, cc = tid >> 5;   // thread (r, cc) owns entry (r, cc)
   T *t = tile_ptr(poolL, L, J, 0);
-  for (int e = threadIdx.x; e < 1024; e += 256) A[e & 31][e >> 5] = t[e];
-  if (threadIdx.x == 0) bad = -1;
+  A[r][cc] = t[cc * 32 + r];
+  if (tid == 0) bad = -1;
   __syncthreads();
-  // unblocked right-looking Cholesky by one warp (no block barriers, one
-  // reciprocal per column instead of a division per entry)
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    for (int k = 0; k < 32; ++k) {
-      T dkk = A[k][k];
-      if (!(dkk > T(0))) {
-        if (lane == 0 && bad < 0) bad = J * 32 + k;
-        dkk = T(1);
+  // right-looking Cholesky, one entry per thread: three barriers per column
+  for (int k = 0; k < 32; ++k) {
+    if (tid == 0) {
+      T d = A[k][k];
+      if (!(d > T(0))) {
+        if (bad < 0) bad = J * 32 + k;
+        d = T(1);
       }
-      T lkk = sqrt(dkk);
-      T inv = T(1) / lkk;
-      __syncwarp();
-      if (lane == k) A[k][k] = lkk;
-      if (lane > k) A[lane][k] *= inv;
-      __syncwarp();
-      if (lane > k) {
-        const T aik = A[lane][k];
-        for (int c = k + 1; c <= lane; ++c) A[lane][c] -= aik * A[c][k];
-      }
-      __syncwarp();
+      T l = sqrt(d);
+      piv[0] = l;
+      piv[1] = T(1) / l;
     }
-    rd[lane] = T(1) / A[lane][lane];
-    __syncwarp();
-    // X = inv(L): lane c solves L x = e_c
-    const int c = lane;
-    for (int i = 0; i < 32; ++i) {
-      if (i < c) {
-        X[i][c] = T(0);
-        continue;
-      }
-      T s = (i == c) ? T(1) : T(0);
-      for (int k = c; k < i; ++k) s -= A[i][k] * X[k][c];
-      X[i][c] = s * rd[i];
-    }
+    __syncthreads();
+    if (cc == k && r >= k) A[r][k] = (r == k) ? piv[0] : A[r][k] * piv[1];
+    __syncthreads();
+    if (cc > k && r >= cc) A[r][cc] -= A[r][k] * A[cc][k];
+    __syncthreads();
   }
+  // inverse of the lower-triangular factor by recursive doubling:
+  // inv([[P, 0], [Q, R]]) = [[iP, 0], [-iR Q iP, iR]]
+  X[r][cc] = (r == cc) ? T(1) / A[r][r] : T(0);
   __syncthreads();
+  for (int b = 1; b < 32; b <<= 1) {
+    // pairs of b x b diagonal blocks at s and s + b, s = multiple of 2b
+    const int s = (r / (2 * b)) * (2 * b);
+    const bool lower = (r >= s + b) && (cc >= s) && (cc < s + b);   // block (R-row, P-col)
+    T v = T(0);
+    if (lower) {   // Y = Q iP  (Q = A[s+b.., s..s+b), iP = X[s.., s..])
+      for (int k = cc; k < s + b; ++k) v += A[r][k] * X[k][cc];
+    }
+    Y[r][cc] = v;
+    __syncthreads();
+    if (lower) {   // X_lower = -iR Y
+      T w = T(0);
+      for (int k = s + b; k <= r; ++k) w += X[r][k] * Y[k][cc];
+      X[r][cc] = -w;
+    }
+    __syncthreads();
+  }
   T *u = tile_ptr(poolU, L, J, 0);
-  for (int e = threadIdx.x; e < 1024; e += 256) {
-    int r = e & 31, cc = e >> 5;
-    t[e] = X[r][cc];          // inv(L_JJ), column-major
-    u[e] = X[cc][r];          // inv(L_JJ)^T
-  }
-  if (threadIdx.x == 0 && bad >= 0) {
+  t[cc * 32 + r] = X[r][cc];    // inv(L_JJ), column-major
+  u[cc * 32 + r] = X[cc][r];    // inv(L_JJ)^T
+  if (tid == 0 && bad >= 0) {
     if (atomicCAS(&st->code, 0, GENEO_ERR_NOT_SPD) == 0) {
       st->where = j;
       st->detail = bad;
@@ -208,7 +209,7 @@ __device__ __forceinline__ void band_sweep(const T *__restrict__ pool, const Ban
   }
 }
 
-__global__ void __launch_bounds__(kSolveWarps * 32)
+__global__ void __launch_bounds__(kSolveWarps * 32, 2)
     k_band_solve_dense(const BandLayout *lay, const double *poolL, const double *poolU,
                        const double *__restrict__ in, long long in_sys, int in_row,
                        double *__restrict__ out, long long out_sys, int out_row, int mode) {
@@ -390,7 +391,7 @@ int launch_band_cholesky(const BandLayout *d_lay, int nsys, int nt_max, int w_ma
                          T *poolU, DevStatus *st, cudaStream_t s) {
   int npairs = w_max * (w_max + 1) / 2;
   for (int J = 0; J < nt_max; ++J) {
-    k_chol_diag<T><<<nsys, 256, 0, s>>>(d_lay, nsys, J, poolL, poolU, st); GENEO_COUNT_LAUNCH();
+    k_chol_diag<T><<<nsys, 1024, 0, s>>>(d_lay, nsys, J, poolL, poolU, st); GENEO_COUNT_LAUNCH();
     if (w_max > 0) {
       k_chol_trsm<T><<<dim3(nsys, w_max), 256, 0, s>>>(d_lay, nsys, J, poolL, poolU); GENEO_COUNT_LAUNCH();
       k_chol_update<T><<<dim3(nsys, npairs), 256, 0, s>>>(d_lay, nsys, J, poolL); GENEO_COUNT_LAUNCH();
