@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=10,
+                    help="requests of the serving sample (uneven laminate blocks)")
     return ap.parse_args()
 
 
@@ -395,6 +398,22 @@ def run_ours(args):
             us = u[::g["sample_stride"]][:len(g["u_samples"])]
             mixed["rel_err_samples"] = float(np.linalg.norm(us - ref) / np.linalg.norm(ref))
 
+    # serving: a seeded stream of uneven solve requests through the
+    # continuous-batching server (burst, then Poisson at half its throughput)
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serve and args.serve_requests > 0:
+        from paper_1901_05188_gb300.serve import serve_benchmark
+        sv = serve_benchmark(n=args.serve_requests, seed=4, prec=pkg.GENEO_MIXED_FP32, slots=4,
+                             rate_factors=(None, 0.5))
+        serving = dict(workload=f"{sv['requests']} laminate blocks, {min(sv['dofs'])}-"
+                                f"{max(sv['dofs'])} dofs (log-uniform 2e4-2e6, seed 4), "
+                                f"{sv['repeats']} repeated structures with new loads",
+                       precision=sv["precision"], slots=sv["slots"],
+                       runs=[{k: r[k] for k in ("arrivals", "n", "p50_ms", "p99_ms", "mean_ms",
+                                                "solves_per_s", "reused", "peak_inflight",
+                                                "peak_mem_gb", "failed") if k in r}
+                             for r in sv["runs"]])
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ms_cpu, sample, threads = oracle_sample(p, st["iterations"])
@@ -412,7 +431,7 @@ def run_ours(args):
                     phases_ms=dict(assemble=st["ms_assemble"], setup_eig_coarse=st["ms_setup_eig"],
                                    setup_factor=st["ms_setup_factor"], solve=st["ms_solve"]),
                     bytes_per_iter=st["bytes_per_iter"], kernels=kernels,
-                    accuracy_vs_oracle=acc, mixed_precision=mixed)
+                    accuracy_vs_oracle=acc, mixed_precision=mixed, serving=serving)
         print(json.dumps(line))
     s.close()
     if world > 1:

@@ -140,6 +140,13 @@ int geneo_setup_workspace_bytes(geneo_ctx *ctx, const geneo_partition *part,
                                 const geneo_modes *modes, geneo_precision prec,
                                 size_t *bytes);
 
+/* Host-only estimate of both workspaces (assemble, setup + solve) for a
+ * problem that has not been assembled yet; used to admit requests by device
+ * memory.  Either output may be NULL.  Touches no device state. */
+int geneo_estimate_workspace_bytes(const geneo_mesh *mesh, const geneo_partition *part,
+                                   const geneo_modes *modes, geneo_precision prec,
+                                   size_t *assemble_bytes, size_t *setup_bytes);
+
 /* Bind caller-owned device memory (e.g. allocated by PyTorch) as the
  * workspace of phase 0 (assemble) or phase 1 (setup + solve).  It must stay
  * alive until the context is destroyed or rebound; alignment >= 256 bytes.
@@ -164,6 +171,15 @@ int geneo_assemble(geneo_ctx *ctx, const geneo_mesh *mesh, int n_mat,
                    const double *elem_theta, const double *elem_phi,
                    const geneo_dirichlet *dirichlet, const double *nodal_load,
                    double top_pressure);
+
+/* Replace the load of the assembled system (Sec. 2, the right-hand side of
+ * eqn:fe_matrix_system) without touching the matrix, the preconditioner or
+ * the captured iteration: b = f + lift on free rows and b_D = g, where f is
+ * the traction (0, 0, -top_pressure) on z = z_max plus `nodal_load` (host or
+ * device, 3*nodes doubles, may be NULL) and lift = -A[:,D] g is kept from
+ * geneo_assemble (same Dirichlet set and values).  The next geneo_solve
+ * solves with the new b.  Errors: GENEO_ERR_STATE before geneo_assemble. */
+int geneo_set_load(geneo_ctx *ctx, const double *nodal_load, double top_pressure);
 
 /* Sizes of the assembled system: nodes and stored 3x3 blocks. */
 int geneo_system_info(geneo_ctx *ctx, int *n_nodes, int *nnz_blocks);

@@ -85,8 +85,12 @@ _SIGS = {
     "geneo_setup_workspace_bytes": [_P, C.POINTER(geneo_partition), C.POINTER(geneo_modes),
                                     C.c_int, C.POINTER(C.c_size_t)],
     "geneo_bind_workspace": [_P, C.c_int, _P, C.c_size_t],
+    "geneo_estimate_workspace_bytes": [C.POINTER(geneo_mesh), C.POINTER(geneo_partition),
+                                       C.POINTER(geneo_modes), C.c_int, C.POINTER(C.c_size_t),
+                                       C.POINTER(C.c_size_t)],
     "geneo_assemble": [_P, C.POINTER(geneo_mesh), C.c_int, _P, _P, _P, _P,
                        C.POINTER(geneo_dirichlet), _P, C.c_double],
+    "geneo_set_load": [_P, _P, C.c_double],
     "geneo_system_info": [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "geneo_get_system": [_P, _P, _P, _P, _P],
     "geneo_spmv": [_P, _P, _P],
@@ -181,6 +185,13 @@ def geneo_setup_workspace_bytes(ctx, part, modes, prec):
     return n.value
 
 
+def geneo_estimate_workspace_bytes(mesh, part, modes, prec):
+    a, s = C.c_size_t(), C.c_size_t()
+    _check(load().geneo_estimate_workspace_bytes(C.byref(mesh), C.byref(part), C.byref(modes),
+                                                 prec, C.byref(a), C.byref(s)))
+    return a.value, s.value
+
+
 def geneo_bind_workspace(ctx, phase, ptr, nbytes):
     _check(load().geneo_bind_workspace(ctx, phase, ptr, nbytes))
 
@@ -190,6 +201,10 @@ def geneo_assemble(ctx, mesh, mats, elem_mat, elem_theta, elem_phi, dirichlet, n
     _check(load().geneo_assemble(ctx, C.byref(mesh), len(mats), C.cast(mats, C.c_void_p),
                                  _ptr(elem_mat), _ptr(elem_theta), _ptr(elem_phi),
                                  C.byref(dirichlet), _ptr(nodal_load), float(top_pressure)))
+
+
+def geneo_set_load(ctx, nodal_load, top_pressure):
+    _check(load().geneo_set_load(ctx, _ptr(nodal_load), float(top_pressure)))
 
 
 def geneo_system_info(ctx):
@@ -318,6 +333,18 @@ class GeneoSolver:
         geneo_assemble(self.ctx, mesh, mats, emat, th, ph, dirichlet, nl, p["top_pressure"])
         self.nnode, self.nnzb = geneo_system_info(self.ctx)
         self.ndof = 3 * self.nnode
+
+    def set_load(self, nodal_load=None, top_pressure=0.0):
+        """New load on the resident system (matrix and preconditioner unchanged)."""
+        if isinstance(nodal_load, np.ndarray):
+            nodal_load = np.ascontiguousarray(nodal_load, dtype=np.float64)
+        if nodal_load is not None:
+            n = nodal_load.size if isinstance(nodal_load, np.ndarray) else nodal_load.numel()
+            if n != self.ndof:
+                raise ValueError(f"nodal_load has {n} entries, the system {self.ndof}")
+            if not isinstance(nodal_load, np.ndarray) and nodal_load.dtype != self.torch.float64:
+                raise TypeError("nodal_load must be float64")
+        geneo_set_load(self.ctx, nodal_load, top_pressure)
 
     @staticmethod
     def partition_of(p):

@@ -163,16 +163,18 @@ __global__ void k_dirichlet_mark(int nd, const int32_t *__restrict__ dofs,
   g[d] = vals ? vals[t] : 0.0;
 }
 
-// b_i -= sum_{c in D} A_ic g_c on free rows; b_i = g_i on Dirichlet rows.
-__global__ void k_dirichlet_rhs(int nnode, const int32_t *__restrict__ row_ptr,
-                                const int32_t *__restrict__ col, const double *__restrict__ val,
-                                const uint8_t *__restrict__ mask, const double *__restrict__ g,
-                                double *__restrict__ b) {
+// Lifting of the Dirichlet data (Sec. 2, u = g on the clamped face):
+// lift_i = -sum_{c in D} A_ic g_c on free rows, lift_i = g_i on Dirichlet rows.
+// It is kept so that a new load reuses it without the eliminated columns.
+__global__ void k_dirichlet_lift(int nnode, const int32_t *__restrict__ row_ptr,
+                                 const int32_t *__restrict__ col, const double *__restrict__ val,
+                                 const uint8_t *__restrict__ mask, const double *__restrict__ g,
+                                 double *__restrict__ lift) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 3 * nnode) return;
   int n = t / 3, r = t % 3;
   if (mask[t]) {
-    b[t] = g[t];
+    lift[t] = g[t];
     return;
   }
   double s = 0.0;
@@ -181,7 +183,15 @@ __global__ void k_dirichlet_rhs(int nnode, const int32_t *__restrict__ row_ptr,
     for (int c = 0; c < 3; ++c)
       if (mask[3 * cn + c]) s += val[9 * (size_t)p + 3 * r + c] * g[3 * cn + c];
   }
-  b[t] -= s;
+  lift[t] = -s;
+}
+
+// b_i = f_i + lift_i on free rows, b_i = g_i on Dirichlet rows.
+__global__ void k_apply_lift(int n3, const uint8_t *__restrict__ mask,
+                             const double *__restrict__ lift, double *__restrict__ b) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n3) return;
+  b[t] = mask[t] ? lift[t] : b[t] + lift[t];
 }
 
 // Zero Dirichlet rows and columns, unit diagonal.
@@ -225,10 +235,23 @@ int launch_assembly(const AssemblyArgs &a, cudaStream_t s) {
   if (a.n_dir > 0) {
     k_dirichlet_mark<<<(a.n_dir + T - 1) / T, T, 0, s>>>(a.n_dir, a.dir_dofs, a.dir_vals,
                                                          3 * nnode, a.mask, a.g, a.status); GENEO_COUNT_LAUNCH();
-    k_dirichlet_rhs<<<(3 * nnode + T - 1) / T, T, 0, s>>>(nnode, a.row_ptr, a.col, a.val,
-                                                          a.mask, a.g, a.b); GENEO_COUNT_LAUNCH();
+    k_dirichlet_lift<<<(3 * nnode + T - 1) / T, T, 0, s>>>(nnode, a.row_ptr, a.col, a.val,
+                                                           a.mask, a.g, a.lift); GENEO_COUNT_LAUNCH();
+    k_apply_lift<<<(3 * nnode + T - 1) / T, T, 0, s>>>(3 * nnode, a.mask, a.lift, a.b); GENEO_COUNT_LAUNCH();
     k_dirichlet_eliminate<<<(nnode + T - 1) / T, T, 0, s>>>(nnode, a.row_ptr, a.col, a.mask,
                                                             a.val); GENEO_COUNT_LAUNCH();
+  }
+  GENEO_CUDA_TRY(cudaGetLastError());
+  return GENEO_OK;
+}
+
+int launch_load(const AssemblyArgs &a, cudaStream_t s) {
+  const int T = 256;
+  int nnode = (a.nx + 1) * (a.ny + 1) * (a.nz + 1);
+  k_load<<<(nnode + T - 1) / T, T, 0, s>>>(a.nx, a.ny, a.nz, a.X, a.Y, a.top_pressure,
+                                           a.nodal, a.b); GENEO_COUNT_LAUNCH();
+  if (a.n_dir > 0) {
+    k_apply_lift<<<(3 * nnode + T - 1) / T, T, 0, s>>>(3 * nnode, a.mask, a.lift, a.b); GENEO_COUNT_LAUNCH();
   }
   GENEO_CUDA_TRY(cudaGetLastError());
   return GENEO_OK;

@@ -411,8 +411,7 @@ int launch_band_solve_dense(const BandLayout *d_lay, int nsys, int npad_max,
                             int out_row, int ncols, int mode, cudaStream_t s) {
   int sm = solve_smem_bytes(npad_max, sizeof(double));
   if (sm > 227 * 1024) return GENEO_ERR_INVALID_ARG;
-  GENEO_CUDA_TRY(cudaFuncSetAttribute(k_band_solve_dense,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  if (int st = ensure_smem(k_band_solve_dense, sm)) return st;
   k_band_solve_dense<<<dim3(nsys, ncols), kSolveWarps * 32, sm, s>>>(
       d_lay, poolL, poolU, in, in_sys, in_row, out, out_sys, out_row, mode); GENEO_COUNT_LAUNCH();
   GENEO_CUDA_TRY(cudaGetLastError());

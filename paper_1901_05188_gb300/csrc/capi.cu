@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <unordered_map>
 #include <new>
 #include <string>
 #include <vector>
@@ -28,8 +29,20 @@ void geneo_set_last_cuda_error(cudaError_t e, const char *what, const char *file
 void geneo_set_last_message(const char *msg) { g_last_error = msg; }
 
 namespace geneo {
-long long g_launch_count = 0;
-bool g_counting = true;
+std::atomic<long long> g_launch_count{0};
+thread_local bool g_counting = true;
+thread_local long long g_thread_launches = 0;
+
+int ensure_smem_raw(const void *func, int bytes) {
+  static std::mutex mu;
+  static std::unordered_map<const void *, int> set_to;
+  std::lock_guard<std::mutex> g(mu);
+  int &cur = set_to[func];
+  if (bytes <= cur) return GENEO_OK;
+  GENEO_CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  cur = bytes;
+  return GENEO_OK;
+}
 
 bool is_device_ptr(const void *p) {
   if (!p) return false;
@@ -43,6 +56,15 @@ bool is_device_ptr(const void *p) {
 }  // namespace geneo
 
 namespace {
+
+// Blocking copy ordered on the context's stream (the legacy default stream
+// would not order against non-blocking streams of the caller).
+cudaError_t copy_sync(const geneo_ctx *c, void *dst, const void *src, size_t bytes,
+                      cudaMemcpyKind kind) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, kind, c->stream);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(c->stream);
+}
 
 constexpr int kHistCap = 20000;
 constexpr int kGraphIters = 8;
@@ -103,6 +125,7 @@ void plan_assemble(Arena &A, geneo_ctx *c, int nx, int ny, int nz, int n_mat, in
   c->val = A.take<double>(9 * (size_t)nnzb);
   c->b = A.take<double>(3 * (size_t)nnode);
   c->g = A.take<double>(3 * (size_t)nnode);
+  c->lift = A.take<double>(3 * (size_t)nnode);
   c->mask = A.take<uint8_t>(3 * (size_t)nnode);
   c->status = A.take<DevStatus>(1);
   c->mats = A.take<geneo_ortho>(std::max(n_mat, 1));
@@ -202,7 +225,7 @@ const char *geneo_status_string(int s) {
 
 const char *geneo_last_error(void) { return g_last_error.c_str(); }
 
-long long geneo_launch_count(void) { return g_launch_count; }
+long long geneo_launch_count(void) { return g_launch_count.load(); }
 
 int geneo_create(geneo_ctx **out, void *cuda_stream) {
   if (!out) return fail(GENEO_ERR_INVALID_ARG, "null out");
@@ -289,7 +312,7 @@ int geneo_assemble(geneo_ctx *c, const geneo_mesh *mesh, int n_mat, const geneo_
   for (int d = 0; d < 3; ++d) {
     hv[d]->resize(na[d]);
     if (is_device_ptr(axes[d])) {
-      GENEO_CUDA_TRY(cudaMemcpy(hv[d]->data(), axes[d], na[d] * sizeof(double), cudaMemcpyDeviceToHost));
+      GENEO_CUDA_TRY(copy_sync(c, hv[d]->data(), axes[d], na[d] * sizeof(double), cudaMemcpyDeviceToHost));
     } else {
       std::memcpy(hv[d]->data(), axes[d], na[d] * sizeof(double));
     }
@@ -361,8 +384,10 @@ int geneo_assemble(geneo_ctx *c, const geneo_mesh *mesh, int n_mat, const geneo_
   a.val = c->val;
   a.b = c->b;
   a.g = c->g;
+  a.lift = c->lift;
   a.mask = c->mask;
   a.status = c->status;
+  c->n_dir = n_dir;
   if ((st = launch_assembly(a, s))) return st;
   GENEO_CUDA_TRY(cudaEventRecord(e1, s));
   int32_t nnzb;
@@ -373,8 +398,29 @@ int geneo_assemble(geneo_ctx *c, const geneo_mesh *mesh, int n_mat, const geneo_
   cudaEventDestroy(e1);
   c->nnzb = nnzb;
   c->hmask.resize(c->ndof);
-  GENEO_CUDA_TRY(cudaMemcpy(c->hmask.data(), c->mask, c->ndof, cudaMemcpyDeviceToHost));
+  GENEO_CUDA_TRY(copy_sync(c, c->hmask.data(), c->mask, c->ndof, cudaMemcpyDeviceToHost));
   c->assembled = true;
+  return GENEO_OK;
+}
+
+int geneo_set_load(geneo_ctx *c, const double *nodal_load, double top_pressure) {
+  if (!c || !c->assembled) return fail(GENEO_ERR_STATE, "not assembled");
+  cudaStream_t s = c->stream;
+  int st;
+  if (nodal_load && (st = stage(c->nodal, nodal_load, c->ndof, s))) return st;
+  AssemblyArgs a{};
+  a.nx = c->nx;
+  a.ny = c->ny;
+  a.nz = c->nz;
+  a.n_dir = c->n_dir;
+  a.X = c->X;
+  a.Y = c->Y;
+  a.nodal = nodal_load ? c->nodal : nullptr;
+  a.top_pressure = top_pressure;
+  a.b = c->b;
+  a.lift = c->lift;
+  a.mask = c->mask;
+  if ((st = launch_load(a, s))) return st;
   return GENEO_OK;
 }
 
@@ -894,6 +940,30 @@ int geneo_setup_workspace_bytes(geneo_ctx *c, const geneo_partition *part,
   return GENEO_OK;
 }
 
+int geneo_estimate_workspace_bytes(const geneo_mesh *mesh, const geneo_partition *part,
+                                   const geneo_modes *modes, geneo_precision prec,
+                                   size_t *assemble_bytes, size_t *setup_bytes) {
+  if (!mesh || mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1)
+    return fail(GENEO_ERR_INVALID_ARG, "bad mesh");
+  int st;
+  if (assemble_bytes && (st = geneo_assemble_workspace_bytes(mesh, assemble_bytes))) return st;
+  if (!setup_bytes) return GENEO_OK;
+  geneo_ctx tmp;                       // host-only: plans sizes, touches no device state
+  tmp.nx = mesh->nx;
+  tmp.ny = mesh->ny;
+  tmp.nz = mesh->nz;
+  tmp.nnode = (mesh->nx + 1) * (mesh->ny + 1) * (mesh->nz + 1);
+  tmp.ndof = 3 * tmp.nnode;
+  tmp.pc.prec = prec;
+  tmp.pc.coarse = GENEO_COARSE_GENEO;
+  SetupPlan P;
+  if ((st = build_plan(&tmp, part, modes, P))) return st;
+  Arena A;
+  plan_setup(A, &tmp, P);
+  *setup_bytes = A.off + 256;
+  return GENEO_OK;
+}
+
 int geneo_setup(geneo_ctx *c, const geneo_partition *part, const geneo_modes *modes,
                 geneo_precision prec, geneo_schwarz schwarz, geneo_coarse coarse) {
   if (!c || !c->assembled) return fail(GENEO_ERR_STATE, "not assembled");
@@ -1053,7 +1123,7 @@ int geneo_get_coarse(geneo_ctx *c, double *Phi, double *AH) {
       }
     }
     if (is_device_ptr(Phi)) {
-      GENEO_CUDA_TRY(cudaMemcpy(Phi, out.data(), out.size() * sizeof(double), cudaMemcpyHostToDevice));
+      GENEO_CUDA_TRY(copy_sync(c, Phi, out.data(), out.size() * sizeof(double), cudaMemcpyHostToDevice));
     } else {
       std::memcpy(Phi, out.data(), out.size() * sizeof(double));
     }
@@ -1157,11 +1227,12 @@ extern "C" int geneo_solve(geneo_ctx *c, double tol, int max_it, double *u, gene
   if (!c->graph) {
     cudaGraph_t g;
     GENEO_CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-    long long before = g_launch_count;
-    g_counting = true;
+    // count the kernel nodes of one graph launch without counting the capture
+    g_counting = false;
+    const long long before = g_thread_launches;
     st = enqueue_iterations(c, kGraphIters, c->cap_stream);
-    c->graph_kernels = g_launch_count - before;     // kernel nodes per graph launch
-    g_launch_count = before;
+    c->graph_kernels = g_thread_launches - before;   // kernel nodes of one graph launch
+    g_counting = true;
     cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &g);
     if (st) return st;
     if (ce != cudaSuccess) {
@@ -1175,7 +1246,7 @@ extern "C" int geneo_solve(geneo_ctx *c, double tol, int max_it, double *u, gene
   DevStatus dst{};
   for (;;) {
     GENEO_CUDA_TRY(cudaGraphLaunch(c->graph, s));
-    g_launch_count += c->graph_kernels;
+    g_launch_count.fetch_add(c->graph_kernels);
     launched += kGraphIters;
     GENEO_CUDA_TRY(cudaMemcpyAsync(c->cg_host, c->cg, sizeof(CGScalars), cudaMemcpyDeviceToHost, s));
     GENEO_CUDA_TRY(cudaMemcpyAsync(&dst, c->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
@@ -1221,8 +1292,8 @@ extern "C" int geneo_solve(geneo_ctx *c, double tol, int max_it, double *u, gene
   if (!flexible && h.it > 0) {
     int k = std::min(h.it, kHistCap);
     std::vector<double> al(k), be(std::max(k - 1, 0));
-    GENEO_CUDA_TRY(cudaMemcpy(al.data(), c->alphas, k * sizeof(double), cudaMemcpyDeviceToHost));
-    if (k > 1) GENEO_CUDA_TRY(cudaMemcpy(be.data(), c->betas, (k - 1) * sizeof(double), cudaMemcpyDeviceToHost));
+    GENEO_CUDA_TRY(copy_sync(c, al.data(), c->alphas, k * sizeof(double), cudaMemcpyDeviceToHost));
+    if (k > 1) GENEO_CUDA_TRY(copy_sync(c, be.data(), c->betas, (k - 1) * sizeof(double), cudaMemcpyDeviceToHost));
     out.kappa_est = kappa_from_cg(al, be);
   }
   c->last_stats = out;
@@ -1320,7 +1391,7 @@ extern "C" int geneo_debug_local_matrix(geneo_ctx *c, int sub, int kind, double 
         }
   }
   if (is_device_ptr(dense)) {
-    GENEO_CUDA_TRY(cudaMemcpy(dense, out.data(), out.size() * sizeof(double), cudaMemcpyHostToDevice));
+    GENEO_CUDA_TRY(copy_sync(c, dense, out.data(), out.size() * sizeof(double), cudaMemcpyHostToDevice));
   } else {
     std::memcpy(dense, out.data(), out.size() * sizeof(double));
   }

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <atomic>
 #include <stddef.h>
 
 #include "../../include/geneo.h"
@@ -22,10 +24,24 @@ void geneo_set_last_message(const char *msg);
 namespace geneo {
 
 // Kernel launches enqueued by this library (graph launches add their kernel
-// nodes); suppressed while a graph is being captured.
-extern long long g_launch_count;
-extern bool g_counting;
-#define GENEO_COUNT_LAUNCH() (geneo::g_launch_count += geneo::g_counting ? 1 : 0)
+// nodes); a thread that is capturing a graph counts them only in its own
+// thread-local counter, so the global count is not inflated by captures.
+extern std::atomic<long long> g_launch_count;   // all threads, enqueued launches
+extern thread_local bool g_counting;             // false while this thread captures a graph
+extern thread_local long long g_thread_launches; // this thread's launches incl. captured ones
+#define GENEO_COUNT_LAUNCH()                                                              \
+  (++geneo::g_thread_launches,                                                            \
+   geneo::g_launch_count.fetch_add(geneo::g_counting ? 1 : 0, std::memory_order_relaxed))
+
+// Raise a kernel's dynamic shared memory limit to at least `bytes`.  The limit
+// is a process-wide attribute of the function, so contexts on concurrent host
+// threads only ever raise it (under a lock): a smaller problem set up on one
+// thread cannot lower the limit under another thread's pending launch.
+int ensure_smem_raw(const void *func, int bytes);
+template <typename F>
+inline int ensure_smem(F *func, int bytes) {
+  return ensure_smem_raw(reinterpret_cast<const void *>(func), bytes);
+}
 
 constexpr int kTile = 32;          // band tile edge (rows = columns = one warp)
 constexpr int kLanczosBlock = 8;   // block Lanczos block size p

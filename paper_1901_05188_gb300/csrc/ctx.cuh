@@ -26,6 +26,8 @@ struct geneo_ctx {
   double *Cel = nullptr, *C0 = nullptr;
   int32_t *row_ptr = nullptr, *col = nullptr, *cnt = nullptr;
   double *val = nullptr, *b = nullptr, *g = nullptr;
+  double *lift = nullptr;                  // Dirichlet lifting (kept for new loads)
+  int n_dir = 0;
   uint8_t *mask = nullptr;
   geneo::DevStatus *status = nullptr;
   // staging of caller inputs

@@ -797,7 +797,7 @@ void launch_tsdots(const SubDesc *d_subs, int nsub, int npad, const double *A, i
                    double *Hpart, int chunks, double *H, long long hs, cudaStream_t s) {
   (void)npad;
   int sm = 16 * (na + nb) * (int)sizeof(double);
-  cudaFuncSetAttribute(k_tsdots, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  (void)ensure_smem(k_tsdots, sm);   // a failure surfaces as a launch error
   k_tsdots<<<dim3(chunks, nsub), 256, sm, s>>>(d_subs, A, lda, sa, na, B, ldb, sb, nb, Hpart,
                                                chunks); GENEO_COUNT_LAUNCH();
   k_tsdots_reduce<<<nsub, 256, 0, s>>>(Hpart, chunks, na * nb, H, hs); GENEO_COUNT_LAUNCH();
@@ -807,7 +807,7 @@ void launch_tsgemm(const SubDesc *d_subs, int nsub, int npad, const double *A, i
                    long long sa, int na, const double *H, int ldh, long long hs, double *C,
                    int ldc, long long sc, int nb, double alpha, double beta, cudaStream_t s) {
   int sm = na * nb * (int)sizeof(double);
-  cudaFuncSetAttribute(k_tsgemm, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  (void)ensure_smem(k_tsgemm, sm);
   long long tot = (long long)npad * nb;
   dim3 g((unsigned)((tot + 255) / 256), nsub);
   k_tsgemm<<<g, 256, sm, s>>>(d_subs, npad, A, lda, sa, na, H, ldh, hs, C, ldc, sc, nb, alpha,
@@ -848,7 +848,7 @@ int launch_ritz_eig(int nsub, const double *Hm, int kdim, int nw, int p, const d
                     double *Eval, double *Evec, double *Eres, cudaStream_t s) {
   if (kdim > kMaxKdim || nw > kdim) return GENEO_ERR_INVALID_ARG;
   int sm = (kdim * (kdim + 1) + 6 * kdim) * (int)sizeof(double);
-  GENEO_CUDA_TRY(cudaFuncSetAttribute(k_ritz_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+  if (int st = ensure_smem(k_ritz_eig, sm)) return st;
   k_ritz_eig<<<nsub, 256, sm, s>>>(Hm, kdim, nw, p, Rblk, Eval, Evec, Eres); GENEO_COUNT_LAUNCH();
   GENEO_CUDA_TRY(cudaGetLastError());
   return GENEO_OK;

@@ -18,10 +18,13 @@ struct AssemblyArgs {
   double *C0, *Cel;                 // per-material / per-element Voigt stiffness
   int32_t *cnt, *row_ptr, *col;
   double *val, *b, *g;
+  double *lift;                     // Dirichlet lifting: g on Dirichlet rows, -A_FD g on free rows
   uint8_t *mask;
   DevStatus *status;
 };
 int launch_assembly(const AssemblyArgs &a, cudaStream_t s);
+// Right-hand side only (load kernel + stored lifting): b = mask ? lift : f + lift.
+int launch_load(const AssemblyArgs &a, cudaStream_t s);
 
 // Scalars of one (F)PCG solve, resident on the device.
 struct CGScalars {

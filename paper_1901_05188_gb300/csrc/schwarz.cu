@@ -198,10 +198,7 @@ int launch_c(const SubDesc *d_subs, const BandLayout *d_lay, int nsub, int npad_
 
 template <typename T, int C>
 int prepare_c(int npad_max) {
-  GENEO_CUDA_TRY(cudaFuncSetAttribute(k_schwarz_cluster<T, C>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      smem_bytes<T>(npad_max, C)));
-  return GENEO_OK;
+  return ensure_smem(k_schwarz_cluster<T, C>, smem_bytes<T>(npad_max, C));
 }
 
 }  // namespace

@@ -1,0 +1,108 @@
+"""Serving loop on the GPU: a request's result does not depend on its company.
+
+Each problem is solved alone (one context, nothing else on the GPU), then the
+same problems are served together through the continuous-batching server with
+several slots whose kernels overlap.  The library's reductions are
+deterministic and every slot owns its context and stream, so solutions and
+iteration counts must agree bit for bit.  A repeated key must reuse the slot's
+resident factors and still give the same solution.
+"""
+import numpy as np
+import pytest
+
+from gpu_common import require_gpu
+from workloads import config, make_block
+
+pytestmark = pytest.mark.gpu
+
+
+def _problems():
+    thr = dict(fixed_modes=0, threshold=0.0, max_modes=20, shift=-0.01)
+    return [
+        ("c1", config("c1")),
+        ("small", config("small")),
+        ("c1p2", config("c1", pressure=2.5)),
+        ("slab", make_block(20, 10, 6, [45, -45, 0], resin_between=True,
+                            partition=(4, 2, 1, 1), modes=thr, name="slab")),
+        ("tiny", config("tiny")),
+        ("wr", make_block(16, 12, 8, [0, 90, 90, 0], partition=(2, 3, 2, 1),
+                          modes=thr, wrinkle=(10.0, 4.0), name="wr")),
+    ]
+
+
+def _alone(pkg, prob, prec):
+    s = pkg.GeneoSolver()
+    try:
+        s.assemble(prob)
+        s.setup(prob, prec)
+        u, st = s.solve(tol=1e-8, max_it=5000)
+    finally:
+        s.close()
+    return u, st
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_same_result_alone_and_in_mix(prec):
+    pkg = require_gpu()
+    from paper_1901_05188_gb300.serve import GeneoServer, latency_summary
+    probs = _problems()
+    # the first structures again with another load: the server may answer
+    # them from a slot that holds their factors
+    again = []
+    for k, p in probs[:3]:
+        q = dict(p)
+        q["top_pressure"] = 3.0 * p["top_pressure"] + 0.5
+        again.append((k, q))
+    alone = [_alone(pkg, p, prec) for _, p in probs + again]
+    srv = GeneoServer(slots=4)
+    try:
+        reqs = [(k, srv.submit(p, prec=prec, key=k)) for k, p in probs + again]
+        for _, r in reqs:
+            r.wait(600)
+    finally:
+        srv.close()
+    assert srv.peak_inflight > 1, "requests did not overlap"
+    for (k, r), (u0, st0) in zip(reqs, alone):
+        assert r.error is None, (k, r.error)
+        assert r.stats["iterations"] == st0["iterations"], k
+        assert np.array_equal(r.u, u0), (k, float(np.max(np.abs(r.u - u0))))
+    assert latency_summary([r for _, r in reqs])["n"] == len(reqs)
+
+
+def test_reuse_resident_factors():
+    pkg = require_gpu()
+    from paper_1901_05188_gb300.serve import GeneoServer
+    p = config("small")
+    srv = GeneoServer(slots=1)
+    try:
+        first = srv.submit(p, key="small").wait(600)
+        again = srv.submit(p, key="small").wait(600)
+        q = dict(p)
+        q["top_pressure"] = 2.0
+        other = srv.submit(q, key="small").wait(600)
+    finally:
+        srv.close()
+    assert first.error is None and again.error is None and other.error is None
+    assert (first.reused, again.reused, other.reused) == (False, True, True)
+    assert np.array_equal(first.u, again.u)
+    # linear in the load: twice the pressure, twice the displacement
+    assert np.allclose(other.u, 2.0 * first.u / p["top_pressure"], rtol=0, atol=1e-7 * np.abs(other.u).max())
+    # the resident solve skips assembly and set-up
+    assert again.t_done - again.t_start < first.t_done - first.t_start
+
+
+def test_memory_estimate_covers_bound_workspace():
+    pkg = require_gpu()
+    from paper_1901_05188_gb300.serve import request_memory
+    for _, p in _problems():
+        for prec in (0, 1):
+            est = request_memory(p, prec)
+            s = pkg.GeneoSolver()
+            try:
+                s.assemble(p)
+                s.setup(p, prec)
+                bound = sum(w.numel() for w in s._ws if w is not None)
+            finally:
+                s.close()
+            # the estimate is the two workspaces; the binding adds 256 B of alignment each
+            assert est + 512 >= bound >= est, (p["name"], prec, est, bound)
