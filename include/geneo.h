@@ -62,8 +62,12 @@ typedef enum { GENEO_FP64 = 0, GENEO_MIXED_FP32 = 1 } geneo_precision;
 typedef enum { GENEO_AS = 0, GENEO_AS_POU = 1 } geneo_schwarz;
 
 /* Coarse space kind. GENEO_COARSE_GENEO: GenEO eigenvectors (Sec. 3.2);
- * GENEO_COARSE_NONE: one-level additive Schwarz only (Sec. 3.1). */
-typedef enum { GENEO_COARSE_GENEO = 0, GENEO_COARSE_NONE = 1 } geneo_coarse;
+ * GENEO_COARSE_NONE: one-level additive Schwarz only (Sec. 3.1);
+ * GENEO_COARSE_ZEM: zero energy modes, the comparison of Sec. 5 (Table 1):
+ * the six rigid displacements of every floating subdomain (none for a
+ * subdomain touching the Dirichlet boundary), weighted by the same partition
+ * of unity; the mode options other than the shift are ignored. */
+typedef enum { GENEO_COARSE_GENEO = 0, GENEO_COARSE_NONE = 1, GENEO_COARSE_ZEM = 2 } geneo_coarse;
 
 typedef struct {
   int nx, ny, nz;                 /* elements per axis, each >= 1 */
@@ -116,6 +120,8 @@ typedef struct {
   int failed_subdomain;           /* subdomain of a GENEO_ERR_NOT_SPD, else -1 */
   int flexible;                   /* 1 if flexible CG was used */
   int eig_cycles;                 /* block-Lanczos restart cycles of the last set-up */
+  int schwarz_cluster;            /* CTAs per subdomain chosen for the local solves */
+  int schwarz_rows;               /* tile rows per cluster barrier chosen for them */
 } geneo_stats;
 
 /* Create a context whose work runs on `cuda_stream` (a cudaStream_t; NULL =

@@ -17,6 +17,12 @@ mode on (A, B, sigma), the method the paper uses.
 
 Coarse basis (Sec. 3.3.2): Phi_{i(j,k)} = R_j^T X_j p_k^j; coarse matrix
 (Sec. 3.3.3) A_H = Phi^T A Phi with the fully assembled global A.
+
+The zero-energy-mode coarse space (ZEM, the comparison of Sec. 5, Example 1
+and Table 1) keeps instead the kernel of every local Neumann problem: the six
+rigid displacements of a floating subdomain, none for a subdomain that
+touches the clamped boundary (its Neumann matrix is non-singular), stitched
+with the same partition of unity.
 """
 from __future__ import annotations
 
@@ -166,3 +172,52 @@ def coarse_space(p, subs, A, eig_method="auto"):
 def coarse_matrix(A, Z):
     """A_H = R_H A R_H^T with R_H^T = Z (Sec. 3.3.3); dense."""
     return (Z.T @ (A @ Z)).toarray()
+
+
+def rigid_body_modes(p, nodes):
+    """The six rigid displacements of `nodes` (3 dofs each), ||column||_2 = 1.
+
+    Columns: translations along x, y, z; rotations about the x, y and z axes
+    through the centre of the nodes' bounding box (u = omega x (X - c)).
+    """
+    nnx, nny = p["nx"] + 1, p["ny"] + 1
+    i = nodes % nnx
+    j = (nodes // nnx) % nny
+    k = nodes // (nnx * nny)
+    X = np.stack([np.asarray(p["x"])[i], np.asarray(p["y"])[j], np.asarray(p["z"])[k]], axis=1)
+    c = 0.5 * (X.min(axis=0) + X.max(axis=0))
+    d = X - c
+    n = nodes.size
+    R = np.zeros((3 * n, 6))
+    for a in range(3):
+        R[a::3, a] = 1.0
+    # omega = e_x: (0, -dz, dy); e_y: (dz, 0, -dx); e_z: (-dy, dx, 0)
+    R[1::3, 3], R[2::3, 3] = -d[:, 2], d[:, 1]
+    R[0::3, 4], R[2::3, 4] = d[:, 2], -d[:, 0]
+    R[0::3, 5], R[1::3, 5] = -d[:, 1], d[:, 0]
+    return R / np.linalg.norm(R, axis=0)
+
+
+def zem_space(p, subs, A):
+    """ZEM coarse basis Z (ndof x N_H, sparse): R_j^T X_j r_k for the rigid
+    modes r_k of every floating subdomain (no global Dirichlet dof in Omega_j).
+
+    Returns (Z, info) with info[j] = dict(lam, m, floating) (lam = 0 for the
+    kept modes: they span the kernel of A_{Omega_j}).
+    """
+    ndof = A.shape[0]
+    dmask = np.zeros(ndof, bool)
+    dmask[np.asarray(p["dirichlet_dofs"], np.int64)] = True
+    cols, info = [], []
+    for s in subs:
+        floating = not dmask[s.neu_dofs].any()
+        m = 6 if floating else 0
+        if m:
+            R = rigid_body_modes(p, s.neu_nodes)
+            for k in range(m):
+                phi = np.zeros(ndof)
+                phi[s.neu_dofs] = s.X * R[:, k]
+                cols.append(phi)
+        info.append(dict(lam=np.zeros(m), m=m, floating=floating))
+    Z = sp.csc_matrix(np.array(cols).T) if cols else sp.csc_matrix((ndof, 0))
+    return Z, info

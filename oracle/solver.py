@@ -23,6 +23,9 @@ def setup(p, precond="geneo", weight="none", eig_method="auto", A=None, b=None):
     if precond == "geneo":
         Z, info = geneo.coarse_space(p, subs, A, eig_method)
         M = krylov.TwoLevelAS(A, subs, Z, weight)
+    elif precond == "zem":
+        Z, info = geneo.zem_space(p, subs, A)
+        M = krylov.TwoLevelAS(A, subs, Z, weight)
     elif precond == "as":
         M = krylov.OneLevelAS(A, subs, weight)
     elif precond == "none":
@@ -53,7 +56,7 @@ def solve(p, precond="geneo", tol=1e-8, maxit=2000, flexible=None,
     if st["info"] is not None:
         out["modes"] = [d["m"] for d in st["info"]]
         out["lambdas"] = [d["lam"] for d in st["info"]]
-        out["taus"] = [d["tau"] for d in st["info"]]
+        out["taus"] = [d.get("tau") for d in st["info"]]
         out["n_coarse"] = int(sum(out["modes"]))
         out["eig_info"] = st["info"]
     else:

@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libgeneo.so")
 
 GENEO_FP64, GENEO_MIXED_FP32 = 0, 1
 GENEO_AS, GENEO_AS_POU = 0, 1
-GENEO_COARSE_GENEO, GENEO_COARSE_NONE = 0, 1
+GENEO_COARSE_GENEO, GENEO_COARSE_NONE, GENEO_COARSE_ZEM = 0, 1, 2
 
 STATUS = {0: "GENEO_OK", 1: "GENEO_ERR_INVALID_ARG", 2: "GENEO_ERR_WORKSPACE_TOO_SMALL",
           3: "GENEO_ERR_CUDA", 4: "GENEO_ERR_NOT_SPD", 5: "GENEO_ERR_EIG_NOT_CONVERGED",
@@ -62,7 +62,8 @@ class geneo_stats(C.Structure):
                 ("ms_setup_coarse", C.c_float), ("ms_setup_factor", C.c_float),
                 ("ms_solve", C.c_float), ("bytes_per_iter", C.c_double),
                 ("eig_max_residual", C.c_double), ("failed_subdomain", C.c_int),
-                ("flexible", C.c_int), ("eig_cycles", C.c_int)]
+                ("flexible", C.c_int), ("eig_cycles", C.c_int),
+                ("schwarz_cluster", C.c_int), ("schwarz_rows", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -38,6 +38,24 @@ __global__ void k_band_pad(const BandLayout *lay, int nsys, T *pool) {
 
 // ---- tile Cholesky ---------------------------------------------------------
 
+// 1/sqrt(d) for d > 0: single-precision estimate refined by Newton's iteration
+// for f(y) = 1/y^2 - d, y <- y (3 - d y^2) / 2, which doubles the number of
+// correct bits per step (24 -> 48 -> full double).  The pivot is on the serial
+// path of the diagonal-block factorisation, where a few dependent FP64
+// operations are much cheaper than a correctly rounded square root and
+// division; the factor only needs the pivot to working precision.
+__device__ __forceinline__ double inv_sqrt_pos(double d) {
+  double y = (double)rsqrtf((float)d);
+  if (!(d >= 1e-30 && d <= 1e30)) return 1.0 / sqrt(d);   // outside float range: exact path
+  y = y * (1.5 - 0.5 * d * y * y);
+  y = y * (1.5 - 0.5 * d * y * y);
+  return y;
+}
+__device__ __forceinline__ float inv_sqrt_pos(float d) {
+  float y = rsqrtf(d);
+  return y * (1.5f - 0.5f * d * y * y);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(1024) k_chol_diag(const BandLayout *lay, int nsys, int J,
                                                     T *poolL, T *poolU, DevStatus *st) {
@@ -62,9 +80,9 @@ __global__ void __launch_bounds__(1024) k_chol_diag(const BandLayout *lay, int n
         if (bad < 0) bad = J * 32 + k;
         d = T(1);
       }
-      T l = sqrt(d);
-      piv[0] = l;
-      piv[1] = T(1) / l;
+      const T y = inv_sqrt_pos(d);
+      piv[0] = d * y;          // sqrt(d)
+      piv[1] = y;              // 1 / sqrt(d)
     }
     __syncthreads();
     if (cc == k && r >= k) A[r][k] = (r == k) ? piv[0] : A[r][k] * piv[1];
@@ -131,15 +149,27 @@ __global__ void __launch_bounds__(256) k_chol_trsm(const BandLayout *lay, int ns
 }
 
 // A(J+d1, J+d2) -= L(J+d1, J) L(J+d2, J)^T, 1 <= d2 <= d1 <= w.
+// part 0: every pair; part 1: the next tile column only (d2 = 1, blockIdx.y =
+// d1 - 1); part 2: the rest (d2 >= 2).
 template <typename T>
 __global__ void __launch_bounds__(256) k_chol_update(const BandLayout *lay, int nsys, int J,
-                                                     T *poolL) {
+                                                     T *poolL, int part) {
   int j = blockIdx.x;
   BandLayout L = lay[j];
   int p = blockIdx.y;
-  int d1 = 1;
-  while ((d1 + 1) * d1 / 2 <= p) ++d1;
-  int d2 = p - d1 * (d1 - 1) / 2 + 1;
+  int d1, d2;
+  if (part == 1) {
+    d1 = p + 1;
+    d2 = 1;
+  } else if (part == 2) {
+    d1 = 2;
+    while (d1 * (d1 - 1) / 2 <= p) ++d1;
+    d2 = p - (d1 - 1) * (d1 - 2) / 2 + 2;
+  } else {
+    d1 = 1;
+    while ((d1 + 1) * d1 / 2 <= p) ++d1;
+    d2 = p - d1 * (d1 - 1) / 2 + 1;
+  }
   if (J >= L.nt || d1 > L.w || J + d1 >= L.nt) return;
   __shared__ T Aa[32][33];
   __shared__ T Bb[32][33];
@@ -165,14 +195,32 @@ __global__ void __launch_bounds__(256) k_chol_update(const BandLayout *lay, int 
 // One sweep over the tile rows of a factored band system with the local
 // vector y in shared memory.  Forward: y_I <- inv(L_II)(y_I - sum_d L(I,I-d) y_{I-d});
 // backward: the same on the U stream with I descending and J = I + d.
+//
+// Warp w multiplies the tiles d = w+1, w+1+16, ... of the row; the per-row
+// chain (sum of the warps' partials, inverted diagonal block) runs on warps
+// 0..3, one per SM sub-partition, each taking 8 of the 32 columns, because on
+// this GPU a warp's dependent FP64 instructions are the critical path.
+constexpr int kChainW = 4;
+
+__device__ __forceinline__ void solve_chain_bar() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kChainW * 32) : "memory");
+}
+
 template <typename T>
 __device__ __forceinline__ void band_sweep(const T *__restrict__ pool, const BandLayout &L,
-                                           T *y, T *red, bool backward) {
+                                           T *y, T *red, T *chn, bool backward) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nt = L.nt, w = L.w;
+  int buf = 0;
   for (int step = 0; step < nt; ++step) {
     const int I = backward ? nt - 1 - step : step;
     const int dmax = backward ? min(w, nt - 1 - I) : min(w, I);
+    T dv[8];
+    if (warp < kChainW) {                       // this warp's columns of inv(L_II), early
+      const T *D = tile_ptr(pool, L, I, 0) + warp * 256;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) dv[k] = __ldg(D + k * 32 + lane);
+    }
     T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
     for (int d = warp + 1; d <= dmax; d += kSolveWarps) {
       const T *t = tile_ptr(pool, L, I, d);
@@ -187,23 +235,27 @@ __device__ __forceinline__ void band_sweep(const T *__restrict__ pool, const Ban
     }
     red[warp * 32 + lane] = (a0 + a1) + (a2 + a3);
     __syncthreads();
-    if (warp == 0) {
-      T s = y[I * 32 + lane];
+    if (warp < kChainW) {
+      T pr = red[warp * 32 + lane];
 #pragma unroll
-      for (int k = 0; k < kSolveWarps; ++k) s -= red[k * 32 + lane];
-      __syncwarp();
-      red[lane] = s;
-      __syncwarp();
-      const T *D = tile_ptr(pool, L, I, 0);
-      T o0 = T(0), o1 = T(0), o2 = T(0), o3 = T(0);
+      for (int k = warp + kChainW; k < kSolveWarps; k += kChainW) pr += red[k * 32 + lane];
+      T *cb = chn + (buf & 1) * (kChainW * 32);
+      cb[warp * 32 + lane] = pr;
+      solve_chain_bar();
+      ++buf;
+      const T s = y[I * 32 + lane] - (((cb[lane] + cb[32 + lane]) + cb[64 + lane]) + cb[96 + lane]);
+      T o0 = T(0), o1 = T(0);
 #pragma unroll
-      for (int c = 0; c < 32; c += 4) {
-        o0 += __ldg(D + (c + 0) * 32 + lane) * red[c + 0];
-        o1 += __ldg(D + (c + 1) * 32 + lane) * red[c + 1];
-        o2 += __ldg(D + (c + 2) * 32 + lane) * red[c + 2];
-        o3 += __ldg(D + (c + 3) * 32 + lane) * red[c + 3];
+      for (int k = 0; k < 8; k += 2) {
+        o0 += dv[k] * __shfl_sync(0xffffffffu, s, warp * 8 + k);
+        o1 += dv[k + 1] * __shfl_sync(0xffffffffu, s, warp * 8 + k + 1);
       }
-      y[I * 32 + lane] = (o0 + o1) + (o2 + o3);
+      cb = chn + (buf & 1) * (kChainW * 32);
+      cb[warp * 32 + lane] = o0 + o1;
+      solve_chain_bar();
+      ++buf;
+      const T yI = ((cb[lane] + cb[32 + lane]) + cb[64 + lane]) + cb[96 + lane];
+      if (warp == 0) y[I * 32 + lane] = yI;
     }
     __syncthreads();
   }
@@ -214,8 +266,9 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 2)
                        const double *__restrict__ in, long long in_sys, int in_row,
                        double *__restrict__ out, long long out_sys, int out_row, int mode) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  double *red = reinterpret_cast<double *>(smraw);
-  double *y = red + kSolveWarps * 32;
+  double *red = reinterpret_cast<double *>(smraw);     // [kSolveWarps][32]
+  double *chn = red + kSolveWarps * 32;                // [2][kChainW][32]
+  double *y = chn + 2 * kChainW * 32;
   const int j = blockIdx.x, c = blockIdx.y;
   const BandLayout L = lay[j];
   const int n = L.n, npad = L.nt * 32;
@@ -223,8 +276,8 @@ __global__ void __launch_bounds__(kSolveWarps * 32, 2)
   for (int l = threadIdx.x; l < npad; l += blockDim.x)
     y[l] = l < n ? src[(long long)l * in_row] : 0.0;
   __syncthreads();
-  if (mode & 1) band_sweep(poolL, L, y, red, false);
-  if (mode & 2) band_sweep(poolU, L, y, red, true);
+  if (mode & 1) band_sweep(poolL, L, y, red, chn, false);
+  if (mode & 2) band_sweep(poolU, L, y, red, chn, true);
   double *dst = out + j * out_sys + c;
   for (int l = threadIdx.x; l < n; l += blockDim.x) dst[(long long)l * out_row] = y[l];
 }
@@ -388,21 +441,47 @@ int launch_band_clear(const BandLayout *d_lay, int nsys, T *pool, long long pool
 
 template <typename T>
 int launch_band_cholesky(const BandLayout *d_lay, int nsys, int nt_max, int w_max, T *poolL,
-                         T *poolU, DevStatus *st, cudaStream_t s) {
-  int npairs = w_max * (w_max + 1) / 2;
-  for (int J = 0; J < nt_max; ++J) {
-    k_chol_diag<T><<<nsys, 1024, 0, s>>>(d_lay, nsys, J, poolL, poolU, st); GENEO_COUNT_LAUNCH();
-    if (w_max > 0) {
-      k_chol_trsm<T><<<dim3(nsys, w_max), 256, 0, s>>>(d_lay, nsys, J, poolL, poolU); GENEO_COUNT_LAUNCH();
-      k_chol_update<T><<<dim3(nsys, npairs), 256, 0, s>>>(d_lay, nsys, J, poolL); GENEO_COUNT_LAUNCH();
+                         T *poolU, DevStatus *st, cudaStream_t s, cudaStream_t side) {
+  const int npairs = w_max * (w_max + 1) / 2;
+  if (!side || w_max == 0) {
+    for (int J = 0; J < nt_max; ++J) {
+      k_chol_diag<T><<<nsys, 1024, 0, s>>>(d_lay, nsys, J, poolL, poolU, st); GENEO_COUNT_LAUNCH();
+      if (w_max > 0) {
+        k_chol_trsm<T><<<dim3(nsys, w_max), 256, 0, s>>>(d_lay, nsys, J, poolL, poolU); GENEO_COUNT_LAUNCH();
+        k_chol_update<T><<<dim3(nsys, npairs), 256, 0, s>>>(d_lay, nsys, J, poolL, 0); GENEO_COUNT_LAUNCH();
+      }
     }
+    GENEO_CUDA_TRY(cudaGetLastError());
+    return GENEO_OK;
   }
+  // Look-ahead: once tile column J+1 has received its update from column J
+  // (part 1), its diagonal block and panel are factored on the side stream
+  // while the main stream applies the rest of column J's trailing update.
+  cudaEvent_t e_main, e_side;
+  GENEO_CUDA_TRY(cudaEventCreateWithFlags(&e_main, cudaEventDisableTiming));
+  GENEO_CUDA_TRY(cudaEventCreateWithFlags(&e_side, cudaEventDisableTiming));
+  k_chol_diag<T><<<nsys, 1024, 0, s>>>(d_lay, nsys, 0, poolL, poolU, st); GENEO_COUNT_LAUNCH();
+  k_chol_trsm<T><<<dim3(nsys, w_max), 256, 0, s>>>(d_lay, nsys, 0, poolL, poolU); GENEO_COUNT_LAUNCH();
+  for (int J = 0; J + 1 < nt_max; ++J) {
+    k_chol_update<T><<<dim3(nsys, w_max), 256, 0, s>>>(d_lay, nsys, J, poolL, 1); GENEO_COUNT_LAUNCH();
+    GENEO_CUDA_TRY(cudaEventRecord(e_main, s));
+    GENEO_CUDA_TRY(cudaStreamWaitEvent(side, e_main, 0));
+    k_chol_diag<T><<<nsys, 1024, 0, side>>>(d_lay, nsys, J + 1, poolL, poolU, st); GENEO_COUNT_LAUNCH();
+    k_chol_trsm<T><<<dim3(nsys, w_max), 256, 0, side>>>(d_lay, nsys, J + 1, poolL, poolU); GENEO_COUNT_LAUNCH();
+    if (npairs > w_max) {
+      k_chol_update<T><<<dim3(nsys, npairs - w_max), 256, 0, s>>>(d_lay, nsys, J, poolL, 2); GENEO_COUNT_LAUNCH();
+    }
+    GENEO_CUDA_TRY(cudaEventRecord(e_side, side));
+    GENEO_CUDA_TRY(cudaStreamWaitEvent(s, e_side, 0));
+  }
+  cudaEventDestroy(e_main);
+  cudaEventDestroy(e_side);
   GENEO_CUDA_TRY(cudaGetLastError());
   return GENEO_OK;
 }
 
 static int solve_smem_bytes(int npad, size_t elem) {
-  return (int)((kSolveWarps * 32 + npad) * elem);
+  return (int)((kSolveWarps * 32 + 2 * kChainW * 32 + npad) * elem);
 }
 
 int launch_band_solve_dense(const BandLayout *d_lay, int nsys, int npad_max,
@@ -455,9 +534,9 @@ void launch_coarse_apply(const SubDesc *d_subs, int nsub, int max_nint, int nnx,
 template int launch_band_clear<double>(const BandLayout *, int, double *, long long, cudaStream_t);
 template int launch_band_clear<float>(const BandLayout *, int, float *, long long, cudaStream_t);
 template int launch_band_cholesky<double>(const BandLayout *, int, int, int, double *, double *,
-                                          DevStatus *, cudaStream_t);
+                                          DevStatus *, cudaStream_t, cudaStream_t);
 template int launch_band_cholesky<float>(const BandLayout *, int, int, int, float *, float *,
-                                         DevStatus *, cudaStream_t);
+                                         DevStatus *, cudaStream_t, cudaStream_t);
 template int launch_extract_interior<double>(const SubDesc *, const BandLayout *, int, int, int,
                                              int, int, const int32_t *, const double *,
                                              double *, cudaStream_t);

@@ -15,10 +15,12 @@ int launch_band_clear(const BandLayout *d_lay, int nsys, T *pool, long long pool
 
 // Right-looking tile Cholesky of nsys band systems held in poolL (lower
 // triangle of each tile row as input).  On exit poolL/poolU hold the forward
-// and backward tile streams described in precond.cuh.
+// and backward tile streams described in precond.cuh.  With a side stream the
+// next tile column is factored there while `s` applies the trailing update
+// (the work is ordered by events and complete on `s` at return).
 template <typename T>
 int launch_band_cholesky(const BandLayout *d_lay, int nsys, int nt_max, int w_max, T *poolL,
-                         T *poolU, DevStatus *st, cudaStream_t s);
+                         T *poolU, DevStatus *st, cudaStream_t s, cudaStream_t side = nullptr);
 
 // Solve with ncols right-hand sides per system.  Column c of system j lives at
 // in[j*in_sys + l*in_row + c] (l = 0..n-1); the result goes to
@@ -41,11 +43,12 @@ template <typename T>
 int prepare_schwarz_solve(int npad_max);
 
 // One-level Schwarz local solves: x_j = A_j^-1 R_j r for every subdomain, one
-// thread-block cluster of `cluster` CTAs (1, 2, 4 or 8) per subdomain.
+// thread-block cluster of `cluster` CTAs (1, 2, 4 or 8) per subdomain, `rows`
+// tile rows (1, 2 or 4) per cluster barrier.
 template <typename T>
 int launch_schwarz_solve(const SubDesc *d_subs, const BandLayout *d_lay, int nsub,
                          int npad_max, int nnx, int nny, const T *poolL, const T *poolU,
-                         const double *r, T *xloc, const CGScalars *cg, int cluster,
+                         const double *r, T *xloc, const CGScalars *cg, int cluster, int rows,
                          DevStatus *status, cudaStream_t s);
 // Cluster size that fills the GPU: the largest power of two <= 8 with
 // 2 * nsub * size <= number of SMs (at least 1).

@@ -6,11 +6,15 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <initializer_list>
+#include <map>
 #include <mutex>
-#include <unordered_map>
 #include <new>
 #include <string>
+#include <tuple>
+#include <unordered_map>
 #include <vector>
 
 #include "ctx.cuh"
@@ -235,6 +239,7 @@ int geneo_create(geneo_ctx **out, void *cuda_stream) {
   GENEO_CUDA_TRY(cudaGetDevice(&c->device));
   GENEO_CUDA_TRY(cudaMallocHost(&c->cg_host, sizeof(CGScalars)));
   GENEO_CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  GENEO_CUDA_TRY(cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking));
   *out = c;
   return GENEO_OK;
 }
@@ -258,6 +263,7 @@ int geneo_destroy(geneo_ctx *c) {
   if (c->ws0_owned && c->ws0) cudaFree(c->ws0);
   if (c->cg_host) cudaFreeHost(c->cg_host);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->side_stream) cudaStreamDestroy(c->side_stream);
   delete c;
   return GENEO_OK;
 }
@@ -619,31 +625,38 @@ void plan_setup(Arena &A, geneo_ctx *c, const SetupPlan &P) {
   pc.facU = A.take<char>(pc.fac_int_elems * esz);
   pc.xloc = A.take<char>(pc.xloc_elems * esz);
   int cap = pc.modes.fixed_modes > 0 ? pc.modes.fixed_modes : pc.modes.max_modes;
-  if (pc.coarse != GENEO_COARSE_GENEO) cap = 0;
+  if (pc.coarse == GENEO_COARSE_NONE) cap = 0;
+  if (pc.coarse == GENEO_COARSE_ZEM) cap = 6;     // the rigid displacements
   pc.mcap = cap + 1;
   pc.kdim = pc.ksteps * p;
   pc.kkeep = pc.kdim / 2;
   if (cap > 0) {
     const int npad = pc.npad_neu_max;
-    pc.neuL = A.take<double>(pc.fac_neu_elems);
-    pc.neuU = A.take<double>(pc.fac_neu_elems);
-    pc.Bloc = A.take<double>(9 * (size_t)pc.bloc_blocks);
+    const bool eig = pc.coarse == GENEO_COARSE_GENEO;
+    pc.neuL = pc.neuU = pc.Bloc = pc.V = pc.Vt = pc.W = pc.T1 = pc.Hm = nullptr;
+    pc.Racc = pc.Rblk = pc.Evec = pc.Eval = pc.Eres = nullptr;
+    if (eig) {   // shift-invert block Lanczos of the GenEO eigenproblems
+      pc.neuL = A.take<double>(pc.fac_neu_elems);
+      pc.neuU = A.take<double>(pc.fac_neu_elems);
+      pc.Bloc = A.take<double>(9 * (size_t)pc.bloc_blocks);
+      pc.V = A.take<double>((size_t)nsub * npad * (pc.kdim + p));
+      pc.Vt = A.take<double>((size_t)nsub * npad * pc.kkeep);
+      pc.W = A.take<double>((size_t)nsub * npad * p);
+      pc.T1 = A.take<double>((size_t)nsub * npad * p);
+      pc.Hm = A.take<double>((size_t)nsub * pc.kdim * pc.kdim);
+      pc.Racc = A.take<double>((size_t)2 * nsub * p * p);
+      pc.Rblk = A.take<double>((size_t)nsub * p * p);
+      pc.Evec = A.take<double>((size_t)2 * nsub * pc.kdim * pc.kdim);
+      pc.Eval = A.take<double>((size_t)nsub * pc.kdim);
+      pc.Eres = A.take<double>((size_t)nsub * pc.kdim);
+    }
     pc.Xneu = A.take<double>(pc.xneu_elems);
-    pc.V = A.take<double>((size_t)nsub * npad * (pc.kdim + p));
-    pc.Vt = A.take<double>((size_t)nsub * npad * pc.kkeep);
-    pc.W = A.take<double>((size_t)nsub * npad * p);
-    pc.T1 = A.take<double>((size_t)nsub * npad * p);
-    pc.Hm = A.take<double>((size_t)nsub * pc.kdim * pc.kdim);
     pc.hchunks = kDotChunks;
-    size_t nout = std::max((size_t)pc.kdim * p, (size_t)pc.mcap * pc.mcap);
+    size_t nout = eig ? std::max((size_t)pc.kdim * p, (size_t)pc.mcap * pc.mcap)
+                      : (size_t)pc.mcap * pc.mcap;
     pc.Hpart = A.take<double>((size_t)nsub * kDotChunks * nout);
     pc.Hs = A.take<double>((size_t)nsub * nout);
     pc.G = A.take<double>((size_t)nsub * std::max(pc.mcap * pc.mcap, p * p));
-    pc.Racc = A.take<double>((size_t)2 * nsub * p * p);
-    pc.Rblk = A.take<double>((size_t)nsub * p * p);
-    pc.Evec = A.take<double>((size_t)2 * nsub * pc.kdim * pc.kdim);
-    pc.Eval = A.take<double>((size_t)nsub * pc.kdim);
-    pc.Eres = A.take<double>((size_t)nsub * pc.kdim);
     pc.P = A.take<double>((size_t)nsub * npad * pc.mcap);
     long long zel = 0, yel = 0;
     for (const SubDesc &S : P.subs) {
@@ -663,7 +676,7 @@ void plan_setup(Arena &A, geneo_ctx *c, const SetupPlan &P) {
     pc.wH = A.take<double>(pc.nH_cap);
     pc.yH = A.take<double>(pc.nH_cap);
   } else {
-    pc.neuL = pc.neuU = pc.Bloc = pc.Xneu = pc.V = pc.W = pc.T1 = pc.Hm = pc.Hpart = nullptr;
+    pc.neuL = pc.neuU = pc.Bloc = pc.Xneu = pc.V = pc.Vt = pc.W = pc.T1 = pc.Hm = pc.Hpart = nullptr;
     pc.Hs = pc.G = pc.Racc = nullptr;
     pc.Rblk = pc.Evec = pc.Eval = pc.Eres = pc.P = pc.Zp = pc.Yp = nullptr;
     pc.AH = pc.AHinv = pc.AHL = pc.AHU = pc.wpart = pc.wH = pc.yH = nullptr;
@@ -712,7 +725,7 @@ static int precond_apply(geneo_ctx *c, const double *r, double *z, const CGScala
   if (pc.prec == GENEO_MIXED_FP32) {
     if ((st = launch_schwarz_solve<float>(pc.d_subs, pc.d_lay_int, pc.nsub, pc.npad_int_max, nnx,
                                           nny, (const float *)pc.facL, (const float *)pc.facU, r,
-                                          (float *)pc.xloc, cg, pc.cluster, c->status, s)))
+                                          (float *)pc.xloc, cg, pc.cluster, pc.rows, c->status, s)))
       return st;
     launch_schwarz_gather<float>(c->nx, c->ny, c->nz, pc.part.px, pc.part.py, pc.d_cand,
                                  pc.cand_off, pc.d_subs, (const float *)pc.xloc, pc.Zp,
@@ -721,7 +734,7 @@ static int precond_apply(geneo_ctx *c, const double *r, double *z, const CGScala
     if ((st = launch_schwarz_solve<double>(pc.d_subs, pc.d_lay_int, pc.nsub, pc.npad_int_max,
                                            nnx, nny, (const double *)pc.facL,
                                            (const double *)pc.facU, r, (double *)pc.xloc, cg,
-                                           pc.cluster, c->status, s)))
+                                           pc.cluster, pc.rows, c->status, s)))
       return st;
     launch_schwarz_gather<double>(c->nx, c->ny, c->nz, pc.part.px, pc.part.py, pc.d_cand,
                                   pc.cand_off, pc.d_subs, (const double *)pc.xloc, pc.Zp,
@@ -732,11 +745,61 @@ static int precond_apply(geneo_ctx *c, const double *r, double *z, const CGScala
 }
 
 // GenEO eigensolves (FP64 block Lanczos) and the coarse space.
+static int build_coarse_operator(geneo_ctx *c, SetupPlan &P, const std::vector<long long> &yoffs,
+                                 cudaStream_t s);
+
+// Zero-energy-mode coarse space: the rigid displacements of every floating
+// subdomain (no global Dirichlet dof among its nodes), unit 2-norm, weighted
+// by the partition of unity like the GenEO modes.
+static int setup_coarse_zem(geneo_ctx *c, SetupPlan &P, cudaStream_t s) {
+  Precond &pc = c->pc;
+  const int nsub = P.nsub, mcap = pc.mcap, npad = pc.npad_neu_max;
+  const int nnx = c->nx + 1, nny = c->ny + 1;
+  const long long sP = (long long)npad * mcap;
+  launch_pou_neumann(pc.d_subs, nsub, P.max_nodes_neu, pc.d_cand, pc.cand_off, c->mask, nnx, nny,
+                     pc.Xneu, s);
+  launch_rigid_modes(pc.d_subs, nsub, npad, c->X, c->Y, c->Z, pc.P, mcap, sP, s);
+  launch_tsdots(pc.d_subs, nsub, npad, pc.P, mcap, sP, mcap, pc.P, mcap, sP, mcap, pc.Hpart,
+                kDotChunks, pc.G, (long long)mcap * mcap, s);
+  launch_normalize_cols(pc.d_subs, nsub, npad, pc.P, mcap, sP, mcap, pc.G, s);
+  GENEO_CUDA_TRY(cudaGetLastError());
+  pc.m.assign(nsub, 0);
+  pc.lambdas.assign((size_t)nsub * mcap, INFINITY);
+  pc.eig_max_res = 0.0;
+  pc.eig_cycles = 0;
+  int coff = 0;
+  long long zoff = 0, yoff = 0;
+  std::vector<long long> yoffs(nsub);
+  for (int j = 0; j < nsub; ++j) {
+    SubDesc &S = P.subs[j];
+    bool floating = true;
+    for (int l = 0; l < S.nbox.count() && floating; ++l) {
+      int gi, gj, gk;
+      S.nbox.global(l, gi, gj, gk);
+      const long long n = gi + (long long)nnx * (gj + (long long)nny * gk);
+      floating = !(c->hmask[3 * n] | c->hmask[3 * n + 1] | c->hmask[3 * n + 2]);
+    }
+    const int m = floating ? 6 : 0;
+    for (int i = 0; i < m; ++i) pc.lambdas[(size_t)j * mcap + i] = 0.0;
+    S.m = m;
+    S.coff = coff;
+    S.z_off = zoff;
+    yoffs[j] = yoff;
+    coff += m;
+    zoff += (long long)S.n_int * m;
+    yoff += (long long)S.n_neu * m;
+    pc.m[j] = m;
+  }
+  pc.nH = coff;
+  return build_coarse_operator(c, P, yoffs, s);
+}
+
 static int setup_coarse(geneo_ctx *c, SetupPlan &P, cudaStream_t s) {
   Precond &pc = c->pc;
+  if (pc.coarse == GENEO_COARSE_ZEM) return setup_coarse_zem(c, P, s);
   const int nsub = P.nsub, p = kLanczosBlock, kdim = pc.kdim, mcap = pc.mcap;
   const int npad = pc.npad_neu_max;
-  const int nnx = c->nx + 1, nny = c->ny + 1, nnz = c->nz + 1;
+  const int nnx = c->nx + 1, nny = c->ny + 1;
   const double sigma = pc.modes.shift;
   int st;
   // PoU, S = A - sigma B into band tiles, B into a local BSR
@@ -747,7 +810,7 @@ static int setup_coarse(geneo_ctx *c, SetupPlan &P, cudaStream_t s) {
                           c->X, c->Y, c->Z, c->Cel, pc.d_ecnt, pc.ecnt_off, c->mask, pc.Xneu,
                           sigma, pc.neuL, pc.Bloc, s);
   if ((st = launch_band_cholesky<double>(pc.d_lay_neu, nsub, pc.nt_neu_max, pc.w_neu_max,
-                                         pc.neuL, pc.neuU, c->status, s)))
+                                         pc.neuL, pc.neuU, c->status, s, c->side_stream)))
     return st;
   // Thick-restart block Lanczos on C = L^-1 B L^-T with full re-orthogonalisation.
   const int ldv = kdim + p;
@@ -871,6 +934,19 @@ static int setup_coarse(geneo_ctx *c, SetupPlan &P, cudaStream_t s) {
     pc.m[j] = m;
   }
   pc.nH = coff;
+  return build_coarse_operator(c, P, yoffs, s);
+}
+
+// Z_j = X_j P_j (first m_j columns), Y = A Z, A_H = Z^T Y over the pairs of
+// subdomains whose supports meet, and the explicit inverse of A_H from its
+// Cholesky factor (Sec. 3.3.2-3.3.3).  S.m, S.coff and pc.nH are set.
+static int build_coarse_operator(geneo_ctx *c, SetupPlan &P, const std::vector<long long> &yoffs,
+                                 cudaStream_t s) {
+  Precond &pc = c->pc;
+  const int nsub = P.nsub, mcap = pc.mcap;
+  const long long sP = (long long)pc.npad_neu_max * mcap;
+  const int nnx = c->nx + 1, nny = c->ny + 1, nnz = c->nz + 1;
+  int st;
   pc.subs = P.subs;
   pc.eig_done = true;
   GENEO_CUDA_TRY(cudaMemcpyAsync(pc.d_subs, P.subs.data(), nsub * sizeof(SubDesc), cudaMemcpyHostToDevice, s));
@@ -933,9 +1009,15 @@ int geneo_setup_workspace_bytes(geneo_ctx *c, const geneo_partition *part,
     c->pc = saved;
     return st;
   }
-  Arena A;
-  plan_setup(A, c, P);
-  *bytes = A.off + 256;
+  // the largest of the coarse-space kinds, so one binding serves every kind
+  size_t most = 0;
+  for (geneo_coarse k : {GENEO_COARSE_GENEO, GENEO_COARSE_ZEM}) {
+    c->pc.coarse = k;
+    Arena A;
+    plan_setup(A, c, P);
+    most = std::max(most, A.off + 256);
+  }
+  *bytes = most;
   c->pc = saved;
   return GENEO_OK;
 }
@@ -955,21 +1037,127 @@ int geneo_estimate_workspace_bytes(const geneo_mesh *mesh, const geneo_partition
   tmp.nnode = (mesh->nx + 1) * (mesh->ny + 1) * (mesh->nz + 1);
   tmp.ndof = 3 * tmp.nnode;
   tmp.pc.prec = prec;
-  tmp.pc.coarse = GENEO_COARSE_GENEO;
   SetupPlan P;
   if ((st = build_plan(&tmp, part, modes, P))) return st;
-  Arena A;
-  plan_setup(A, &tmp, P);
-  *setup_bytes = A.off + 256;
+  size_t most = 0;
+  for (geneo_coarse k : {GENEO_COARSE_GENEO, GENEO_COARSE_ZEM}) {
+    tmp.pc.coarse = k;
+    Arena A;
+    plan_setup(A, &tmp, P);
+    most = std::max(most, A.off + 256);
+  }
+  *setup_bytes = most;
   return GENEO_OK;
 }
+
+}  // extern "C"
+
+// ---- autotuning of the Schwarz local-solve launch ---------------------------
+// The launch shape of the local solves (CTAs per subdomain, tile rows per
+// cluster barrier) is chosen by timing the candidates on the factors just
+// built; the choice is cached for the process, keyed by precision, subdomain
+// count, largest padded subdomain, largest band width and SM count, so a
+// repeated set-up of the same shape does not tune again.  GENEO_SCHWARZ_CLUSTER
+// and GENEO_SCHWARZ_ROWS fix either dimension.
+struct TuneKey {
+  int prec, nsub, npad, w, sms;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(prec, nsub, npad, w, sms) < std::tie(o.prec, o.nsub, o.npad, o.w, o.sms);
+  }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, std::pair<int, int>> g_tune;
+
+static int env_choice(const char *name, std::initializer_list<int> allowed) {
+  const char *e = std::getenv(name);
+  if (!e) return 0;
+  int v = std::atoi(e);
+  for (int a : allowed)
+    if (a == v) return v;
+  return 0;
+}
+
+static int schwarz_once(geneo_ctx *c, int cluster, int rows, cudaStream_t s) {
+  Precond &pc = c->pc;
+  const int nnx = c->nx + 1, nny = c->ny + 1;
+  if (pc.prec == GENEO_MIXED_FP32)
+    return launch_schwarz_solve<float>(pc.d_subs, pc.d_lay_int, pc.nsub, pc.npad_int_max, nnx, nny,
+                                       (const float *)pc.facL, (const float *)pc.facU, c->b,
+                                       (float *)pc.xloc, nullptr, cluster, rows, c->status, s);
+  return launch_schwarz_solve<double>(pc.d_subs, pc.d_lay_int, pc.nsub, pc.npad_int_max, nnx, nny,
+                                      (const double *)pc.facL, (const double *)pc.facU, c->b,
+                                      (double *)pc.xloc, nullptr, cluster, rows, c->status, s);
+}
+
+static int tune_schwarz(geneo_ctx *c, const SetupPlan &P, cudaStream_t s) {
+  Precond &pc = c->pc;
+  const TuneKey key{(int)pc.prec, P.nsub, pc.npad_int_max, pc.w_int_max, pc.sms};
+  const int fc = env_choice("GENEO_SCHWARZ_CLUSTER", {1, 2, 4, 8});
+  const int fr = env_choice("GENEO_SCHWARZ_ROWS", {1, 2, 4});
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end() && !fc && !fr) {
+      pc.cluster = it->second.first;
+      pc.rows = it->second.second;
+      return GENEO_OK;
+    }
+  }
+  std::vector<int> cs, rs;
+  if (fc) {
+    cs = {fc};
+  } else {
+    // one wave of clusters: nsub * C CTAs on distinct SMs
+    for (int C : {1, 2, 4, 8})
+      if (C == 1 || P.nsub * C <= pc.sms) cs.push_back(C);
+  }
+  if (fr) rs = {fr};
+  else if (pc.prec == GENEO_MIXED_FP32) rs = {1, 2, 4};
+  else rs = {1, 2};
+  if (cs.size() * rs.size() == 1) {
+    pc.cluster = cs[0];
+    pc.rows = rs[0];
+    return GENEO_OK;
+  }
+  cudaEvent_t e0, e1;
+  GENEO_CUDA_TRY(cudaEventCreate(&e0));
+  GENEO_CUDA_TRY(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int st;
+  for (int C : cs)
+    for (int R : rs) {
+      if ((st = schwarz_once(c, C, R, s))) return st;          // warm-up
+      GENEO_CUDA_TRY(cudaEventRecord(e0, s));
+      for (int k = 0; k < 2; ++k)
+        if ((st = schwarz_once(c, C, R, s))) return st;
+      GENEO_CUDA_TRY(cudaEventRecord(e1, s));
+      GENEO_CUDA_TRY(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      GENEO_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        pc.cluster = C;
+        pc.rows = R;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!fc && !fr) {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune[key] = {pc.cluster, pc.rows};
+  }
+  return GENEO_OK;
+}
+
+extern "C" {
 
 int geneo_setup(geneo_ctx *c, const geneo_partition *part, const geneo_modes *modes,
                 geneo_precision prec, geneo_schwarz schwarz, geneo_coarse coarse) {
   if (!c || !c->assembled) return fail(GENEO_ERR_STATE, "not assembled");
   if (prec != GENEO_FP64 && prec != GENEO_MIXED_FP32) return fail(GENEO_ERR_INVALID_ARG, "bad precision");
   if (schwarz != GENEO_AS && schwarz != GENEO_AS_POU) return fail(GENEO_ERR_INVALID_ARG, "bad schwarz");
-  if (coarse != GENEO_COARSE_GENEO && coarse != GENEO_COARSE_NONE) return fail(GENEO_ERR_INVALID_ARG, "bad coarse");
+  if (coarse != GENEO_COARSE_GENEO && coarse != GENEO_COARSE_NONE && coarse != GENEO_COARSE_ZEM)
+    return fail(GENEO_ERR_INVALID_ARG, "bad coarse");
   cudaStream_t s = c->stream;
   release_setup(c);
   Precond &pc = c->pc;
@@ -1002,12 +1190,14 @@ int geneo_setup(geneo_ctx *c, const geneo_partition *part, const geneo_modes *mo
   int sms = 0;
   GENEO_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
   pc.cluster = schwarz_cluster_size(P.nsub, sms);
+  pc.rows = 1;
+  pc.sms = sms;
   if (f32) {
     if ((st = prepare_schwarz_solve<float>(pc.npad_int_max))) return fail(st, "subdomain too large for shared memory");
   } else {
     if ((st = prepare_schwarz_solve<double>(pc.npad_int_max))) return fail(st, "subdomain too large for shared memory");
   }
-  if (pc.mcap > 1 && pc.npad_neu_max * 8 + 16 * 32 * 8 > 227 * 1024)
+  if (pc.coarse == GENEO_COARSE_GENEO && pc.mcap > 1 && pc.npad_neu_max * 8 + 16 * 32 * 8 > 227 * 1024)
     return fail(GENEO_ERR_INVALID_ARG, "subdomain too large for the eigensolver's shared memory");
   cudaEvent_t ev[4];
   for (auto &e : ev) GENEO_CUDA_TRY(cudaEventCreate(&e));
@@ -1035,7 +1225,7 @@ int geneo_setup(geneo_ctx *c, const geneo_partition *part, const geneo_modes *mo
                                              nny, nnz, c->row_ptr, c->val, L, s)))
       return st;
     if ((st = launch_band_cholesky<float>(pc.d_lay_int, P.nsub, pc.nt_int_max, pc.w_int_max, L, U,
-                                          c->status, s)))
+                                          c->status, s, c->side_stream)))
       return st;
   } else {
     double *L = (double *)pc.facL, *U = (double *)pc.facU;
@@ -1044,7 +1234,7 @@ int geneo_setup(geneo_ctx *c, const geneo_partition *part, const geneo_modes *mo
                                               nnx, nny, nnz, c->row_ptr, c->val, L, s)))
       return st;
     if ((st = launch_band_cholesky<double>(pc.d_lay_int, P.nsub, pc.nt_int_max, pc.w_int_max, L,
-                                           U, c->status, s)))
+                                           U, c->status, s, c->side_stream)))
       return st;
   }
   GENEO_CUDA_TRY(cudaEventRecord(ev[2], s));
@@ -1058,6 +1248,7 @@ int geneo_setup(geneo_ctx *c, const geneo_partition *part, const geneo_modes *mo
   GENEO_CUDA_TRY(cudaEventElapsedTime(&pc.ms_factor, ev[1], ev[2]));
   pc.ms_coarse = 0.f;
   for (auto &e : ev) cudaEventDestroy(e);
+  if ((st = tune_schwarz(c, P, s))) return st;
   // algorithmic bytes of one preconditioner application
   double esz = f32 ? 4.0 : 8.0, bytes = 0.0;
   for (const SubDesc &S : P.subs) {
@@ -1289,6 +1480,8 @@ extern "C" int geneo_solve(geneo_ctx *c, double tol, int max_it, double *u, gene
   out.failed_subdomain = -1;
   out.flexible = flexible ? 1 : 0;
   out.eig_cycles = pc.eig_cycles;
+  out.schwarz_cluster = pc.cluster;
+  out.schwarz_rows = pc.rows;
   if (!flexible && h.it > 0) {
     int k = std::min(h.it, kHistCap);
     std::vector<double> al(k), be(std::max(k - 1, 0));
@@ -1310,8 +1503,8 @@ extern "C" int geneo_debug_local_matrix(geneo_ctx *c, int sub, int kind, double 
   if (!c || !c->ws1 || !c->pc.d_subs) return fail(GENEO_ERR_STATE, "no preconditioner planned");
   Precond &pc = c->pc;
   if (sub < 0 || sub >= pc.nsub || kind < 0 || kind > 4) return fail(GENEO_ERR_INVALID_ARG, "bad sub/kind");
-  if ((kind == 1 || kind == 2 || kind == 4) && !pc.Xneu)
-    return fail(GENEO_ERR_STATE, "no GenEO data (coarse space disabled)");
+  if ((kind == 1 || kind == 2 || kind == 4) && !pc.Bloc)
+    return fail(GENEO_ERR_STATE, "no GenEO eigenproblem data (GenEO coarse space not set up)");
   cudaStream_t s = c->stream;
   const SubDesc &S = pc.subs[sub];
   const bool factor = kind >= 3;
@@ -1459,11 +1652,11 @@ extern "C" int geneo_profile(geneo_ctx *c, int what, int reps, double *ms_per_la
         st = f32 ? launch_schwarz_solve<float>(pc.d_subs, pc.d_lay_int, pc.nsub, pc.npad_int_max,
                                                nnx, nny, (const float *)pc.facL,
                                                (const float *)pc.facU, c->r, (float *)pc.xloc,
-                                               nullptr, pc.cluster, c->status, s)
+                                               nullptr, pc.cluster, pc.rows, c->status, s)
                  : launch_schwarz_solve<double>(pc.d_subs, pc.d_lay_int, pc.nsub,
                                                 pc.npad_int_max, nnx, nny,
                                                 (const double *)pc.facL, (const double *)pc.facU,
-                                                c->r, (double *)pc.xloc, nullptr, pc.cluster, c->status, s);
+                                                c->r, (double *)pc.xloc, nullptr, pc.cluster, pc.rows, c->status, s);
       } else if (what == 1) {
         launch_spmv(A, c->r, c->q, s);
       } else if (what == 3) {

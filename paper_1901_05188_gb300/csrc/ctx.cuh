@@ -10,6 +10,7 @@
 struct geneo_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;        // private stream used only to capture graphs
+  cudaStream_t side_stream = nullptr;       // private stream for look-ahead factorisation
   int device = 0;
 
   // ---- mesh / assembled system (phase 0)

@@ -757,7 +757,49 @@ __global__ void k_normalize_cols(const SubDesc *subs, int npad, double *P, int l
   if (g > 0.0) *pv /= sqrt(g);
 }
 
+// Rigid displacements of the Neumann nodes of every subdomain (Sec. 5, zero
+// energy modes): P[j][row][k] for k < 6 -- translations along x, y, z and
+// rotations omega x (X - c) about the axes through the centre c of the
+// subdomain's node box; columns 6.. and the padding rows are zero.
+__global__ void k_rigid_modes(const SubDesc *subs, int npad, const double *__restrict__ X,
+                              const double *__restrict__ Y, const double *__restrict__ Z,
+                              double *P, int ld, long long sp) {
+  const int j = blockIdx.y;
+  const SubDesc &S = subs[j];
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)npad * ld) return;
+  const int row = (int)(t / ld), k = (int)(t - (long long)row * ld);
+  double v = 0.0;
+  if (row < S.n_neu && k < 6) {
+    const int node = row / 3, comp = row - 3 * node;
+    int gi, gj, gk;
+    S.nbox.global(node, gi, gj, gk);
+    const NodeBox &B = S.nbox;
+    const double dx = X[gi] - 0.5 * (X[B.lo[0]] + X[B.lo[0] + B.n[0] - 1]);
+    const double dy = Y[gj] - 0.5 * (Y[B.lo[1]] + Y[B.lo[1] + B.n[1] - 1]);
+    const double dz = Z[gk] - 0.5 * (Z[B.lo[2]] + Z[B.lo[2] + B.n[2] - 1]);
+    if (k < 3) {
+      v = comp == k ? 1.0 : 0.0;
+    } else if (k == 3) {          // about x: (0, -dz, dy)
+      v = comp == 1 ? -dz : (comp == 2 ? dy : 0.0);
+    } else if (k == 4) {          // about y: (dz, 0, -dx)
+      v = comp == 0 ? dz : (comp == 2 ? -dx : 0.0);
+    } else {                      // about z: (-dy, dx, 0)
+      v = comp == 0 ? -dy : (comp == 1 ? dx : 0.0);
+    }
+  }
+  P[j * sp + t] = v;
+}
+
 }  // namespace
+
+void launch_rigid_modes(const SubDesc *d_subs, int nsub, int npad, const double *X,
+                        const double *Y, const double *Z, double *P, int ld, long long sp,
+                        cudaStream_t s) {
+  long long tot = (long long)npad * ld;
+  dim3 g((unsigned)((tot + 255) / 256), nsub);
+  k_rigid_modes<<<g, 256, 0, s>>>(d_subs, npad, X, Y, Z, P, ld, sp); GENEO_COUNT_LAUNCH();
+}
 
 void launch_pou_neumann(const SubDesc *d_subs, int nsub, int max_nodes, const int *cand,
                         const int cand_off[3], const uint8_t *mask, int nnx, int nny,

@@ -84,6 +84,11 @@ void launch_dense_to_tiles(const double *AH, int nH, const BandLayout *d_lay, do
 void launch_symmetrize(double *M, int n, cudaStream_t s);
 void launch_identity(double *M, int n, cudaStream_t s);
 // scale columns of P_j (rows < n_neu) by 1/||col||; norms from the diagonal of G
+// The six rigid displacements of each subdomain's Neumann nodes into P
+// (row-major, leading dimension ld >= 6, system stride sp; other entries 0).
+void launch_rigid_modes(const SubDesc *d_subs, int nsub, int npad, const double *X,
+                        const double *Y, const double *Z, double *P, int ld, long long sp,
+                        cudaStream_t s);
 void launch_normalize_cols(const SubDesc *d_subs, int nsub, int npad, double *P, int ld,
                            long long sp, int ncol, const double *G, cudaStream_t s);
 

@@ -26,6 +26,8 @@ struct Precond {
   geneo_coarse coarse = GENEO_COARSE_GENEO;
   int nsub = 0;
   int cluster = 1;                // CTAs per subdomain in the Schwarz local solves
+  int rows = 1;                   // tile rows per cluster barrier in the Schwarz local solves
+  int sms = 0;                    // SM count of the device
   std::vector<SubDesc> subs;
   SubDesc *d_subs = nullptr;
   BandLayout *d_lay_int = nullptr, *d_lay_neu = nullptr, *d_lay_H = nullptr;

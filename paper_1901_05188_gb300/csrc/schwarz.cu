@@ -3,13 +3,18 @@
 //
 // Each of the C CTAs of a cluster keeps a full copy of the local vector y_j in
 // shared memory and owns the band tiles d = 1 + c + kC of every tile row.  A
-// step of a sweep: every CTA multiplies its tiles with the already solved
-// blocks of y, pushes its 32 partial sums into the partial buffer of every
-// CTA of the cluster (distributed shared memory), one cluster barrier, then
-// every CTA applies the inverted diagonal block to y_I - sum of partials
-// itself, so y_I appears in all copies without a second exchange.  Tiles of
-// the next step are loaded into registers during the barrier phase and the
-// step after that is prefetched into L2.
+// step of a sweep solves R consecutive tile rows I_0..I_{R-1}.  All warps
+// multiply their tiles with the already solved blocks of y (the "far" tiles:
+// row I_r, distance d > r); per-CTA partial sums go into the partial buffer of
+// every CTA of the cluster (distributed shared memory); one cluster barrier;
+// then the chain warps of every CTA finish the R rows themselves: subtract the
+// partials, the couplings inside the group (L(I_r, I_r-d), d <= r) and apply
+// the inverted diagonal block, so each y_I appears in all copies without a
+// second exchange.  The chain runs on four warps (one per SM sub-partition),
+// each taking 8 of the 32 columns of every chain tile, because on this GPU a
+// warp's dependent FP64 instructions are the critical path.  Tiles of the next
+// step are loaded into registers during the barrier phase and the step after
+// that is prefetched into L2.
 #include <cooperative_groups.h>
 
 #include "band.cuh"
@@ -20,7 +25,8 @@ namespace geneo {
 
 namespace {
 
-constexpr int kClWarps = 16;        // warp 0: diagonal block; warps 1..15: off-diagonal tiles
+constexpr int kClWarps = 16;        // all warps multiply far tiles
+constexpr int kChain = 4;           // warps 0..3 also run the per-row chain
 constexpr int kGroups = 4;          // a tile is split into 4 units of 8 columns
 
 template <typename T>
@@ -32,109 +38,246 @@ __device__ __forceinline__ void prefetch_l2(const void *p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
-// The unit u = (t, g) of CTA c in tile row I: tile d = 1 + c + t*C, columns 8g..8g+7.
-template <int C>
-__device__ __forceinline__ int unit_tile(int u, int c) {
-  return 1 + c + (u / kGroups) * C;
+__device__ __forceinline__ void chain_bar() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kChain * 32) : "memory");
 }
 
-template <typename T, int C>
-__device__ void cluster_sweep(const cg::cluster_group &cluster, const T *__restrict__ pool,
-                              const BandLayout &L, T *y, T *red, T *part, bool backward) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c = (int)cluster.block_rank();
-  const int nt = L.nt, w = L.w;
-  const int cw = warp - 1;                      // compute-warp index (-1 for warp 0)
-  constexpr int kLinesPerUnit = 8 * 32 * (int)sizeof(T) / 128;
-  T nx[8];                                      // register copy of the next step's first unit
-  auto dmax_of = [&](int I) { return backward ? min(w, nt - 1 - I) : min(w, I); };
-  auto row_of = [&](int step) { return backward ? nt - 1 - step : step; };
-  auto load_unit = [&](int I, int u, T *dst) {
-    const int d = unit_tile<C>(u, c);
-    if (cw < 0 || d > dmax_of(I)) return;
-    const T *t = tile_at(pool, L, I, d) + (u % kGroups) * 8 * 32;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) dst[k] = __ldg(t + k * 32 + lane);
-  };
-  if (nt > 0) load_unit(row_of(0), cw, nx);
-  T dv[32];                                     // warp 0: inverted diagonal tile, lane's row
-  if (warp == 0 && nt > 0) {
-    const T *D = tile_at(pool, L, row_of(0), 0);
-#pragma unroll
-    for (int k = 0; k < 32; ++k) dv[k] = __ldg(D + k * 32 + lane);
+// Far tiles of row r of a step owned by CTA c: d = 1 + c + t*C for t in
+// [t0, t0 + n), with r + 1 <= d <= dmax.
+template <int C>
+__device__ __forceinline__ void far_tiles(int r, int dmax, int c, int &t0, int &n) {
+  t0 = (r > c) ? (r - c + C - 1) / C : 0;
+  const int d0 = 1 + c + t0 * C;
+  n = (dmax >= d0) ? (dmax - d0) / C + 1 : 0;
+}
+
+template <typename T, int C, int R>
+struct Sweep {
+  const T *pool;
+  BandLayout L;
+  int c, nt, w;
+  bool backward;
+
+  __device__ __forceinline__ bool valid(int step, int r) const { return step * R + r < nt; }
+  __device__ __forceinline__ int row(int step, int r) const {
+    const int q = step * R + r;
+    return backward ? nt - 1 - q : q;
   }
-  for (int step = 0; step < nt; ++step) {
-    const int I = row_of(step);
-    const int dm = dmax_of(I);
-    const int par = step & 1;
-    if (step + 2 < nt && cw >= 0) {             // L2 prefetch two steps ahead
-      const int I2 = row_of(step + 2);
-      for (int u = cw; unit_tile<C>(u, c) <= dmax_of(I2); u += kClWarps - 1)
-        if (lane < kLinesPerUnit)
-          prefetch_l2(tile_at(pool, L, I2, unit_tile<C>(u, c)) + (u % kGroups) * 256 +
-                      lane * (128 / sizeof(T)));
+  __device__ __forceinline__ int dmax(int I) const {
+    return backward ? min(w, nt - 1 - I) : min(w, I);
+  }
+  // unit u of a step -> (r, d, g); false if the step has fewer units
+  __device__ __forceinline__ bool unit(int step, int u, int &r, int &d, int &g) const {
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      if (!valid(step, q)) return false;
+      int t0, n;
+      far_tiles<C>(q, dmax(row(step, q)), c, t0, n);
+      if (u < kGroups * n) {
+        r = q;
+        d = 1 + c + (t0 + u / kGroups) * C;
+        g = u % kGroups;
+        return true;
+      }
+      u -= kGroups * n;
     }
-    T a0 = T(0), a1 = T(0);
-    if (cw >= 0) {
-      for (int u = cw; unit_tile<C>(u, c) <= dm; u += kClWarps - 1) {
-        const int d = unit_tile<C>(u, c);
-        const T *yJ = y + (backward ? (I + d) : (I - d)) * 32 + (u % kGroups) * 8;
-        T v[8];
-        if (u == cw) {
+    return false;
+  }
+  __device__ __forceinline__ const T *unit_ptr(int step, int r, int d, int g) const {
+    return tile_at(pool, L, row(step, r), d) + g * 8 * 32;
+  }
+};
+
+template <typename T, int C, int R>
+__device__ void cluster_sweep(const cg::cluster_group &cluster, const T *__restrict__ pool,
+                              const BandLayout &L, T *y, T *red, T *chn, T *part,
+                              bool backward) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  Sweep<T, C, R> S{pool, L, (int)cluster.block_rank(), L.nt, L.w, backward};
+  const int c = S.c;
+  const int nsteps = (S.nt + R - 1) / R;
+  constexpr int kLinesPerUnit = 8 * 32 * (int)sizeof(T) / 128;
+  constexpr int kNear = R * (R - 1) / 2;       // couplings inside a group of R rows
+  T nx[8];                                      // register copy of this warp's next first unit
+  bool have_nx = false;
+  {
+    int r, d, g;
+    if (nsteps > 0 && S.unit(0, warp, r, d, g)) {
+      const T *t = S.unit_ptr(0, r, d, g);
 #pragma unroll
-          for (int k = 0; k < 8; ++k) v[k] = nx[k];
-        } else {
-          const T *t = tile_at(pool, L, I, d) + (u % kGroups) * 8 * 32;
+      for (int k = 0; k < 8; ++k) nx[k] = __ldg(t + k * 32 + lane);
+      have_nx = true;
+    }
+  }
+  int buf = 0;                                  // rotating chain buffer
+  for (int step = 0; step < nsteps; ++step) {
+    const int par = step & 1;
+    // chain tiles of this step: columns 8*warp..8*warp+7 of every inverted
+    // diagonal block and every coupling inside the group
+    T dv[R][8];
+    T nv[kNear > 0 ? kNear : 1][8];
+    if (warp < kChain) {
 #pragma unroll
-          for (int k = 0; k < 8; ++k) v[k] = __ldg(t + k * 32 + lane);
-        }
+      for (int r = 0; r < R; ++r) {
+        if (!S.valid(step, r)) break;
+        const int I = S.row(step, r);
+        const T *D = tile_at(pool, L, I, 0) + warp * 8 * 32;
 #pragma unroll
-        for (int k = 0; k < 8; k += 2) {
-          a0 += v[k] * yJ[k];
-          a1 += v[k + 1] * yJ[k + 1];
+        for (int k = 0; k < 8; ++k) dv[r][k] = __ldg(D + k * 32 + lane);
+#pragma unroll
+        for (int d = 1; d <= r; ++d) {         // zero outside the band (d > w)
+          const T *N = tile_at(pool, L, I, d) + warp * 8 * 32;
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            nv[r * (r - 1) / 2 + d - 1][k] = d <= S.w ? __ldg(N + k * 32 + lane) : T(0);
         }
       }
-      if (step + 1 < nt) load_unit(row_of(step + 1), cw, nx);   // in flight over the barrier
     }
-    red[warp * 32 + lane] = a0 + a1;
+    if (step + 2 < nsteps) {                    // L2 prefetch two steps ahead
+      int r, d, g;
+      for (int u = warp; S.unit(step + 2, u, r, d, g); u += kClWarps)
+        if (lane < kLinesPerUnit)
+          prefetch_l2(S.unit_ptr(step + 2, r, d, g) + lane * (128 / sizeof(T)));
+      if (warp < kChain && lane < kLinesPerUnit) {
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          if (!S.valid(step + 2, q)) break;
+          const int I = S.row(step + 2, q);
+#pragma unroll
+          for (int d = 0; d <= q; ++d)
+            if (d <= S.w)
+              prefetch_l2(tile_at(pool, L, I, d) + warp * 8 * 32 + lane * (128 / sizeof(T)));
+        }
+      }
+    }
+    // far tiles
+    T acc[R][2];
+#pragma unroll
+    for (int q = 0; q < R; ++q) acc[q][0] = acc[q][1] = T(0);
+    {
+      // B units per warp in flight at once (their loads are issued before any FMA)
+      constexpr int B = sizeof(T) == 8 ? 2 : 4;
+      bool first = true;
+      for (int u = warp;; u += B * kClWarps) {
+        T v[B][8];
+        int rb[B], db[B], gb[B];
+        bool ok[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+          ok[b] = S.unit(step, u + b * kClWarps, rb[b], db[b], gb[b]);
+          if (!ok[b]) continue;
+          if (b == 0 && first && have_nx) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[b][e] = nx[e];
+          } else {
+            const T *t = S.unit_ptr(step, rb[b], db[b], gb[b]);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[b][e] = __ldg(t + e * 32 + lane);
+          }
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+          if (!ok[b]) continue;
+          const int I = S.row(step, rb[b]);
+          const T *yJ = y + (backward ? (I + db[b]) : (I - db[b])) * 32 + gb[b] * 8;
+          T a0 = T(0), a1 = T(0);
+#pragma unroll
+          for (int e = 0; e < 8; e += 2) {
+            a0 += v[b][e] * yJ[e];
+            a1 += v[b][e + 1] * yJ[e + 1];
+          }
+#pragma unroll
+          for (int q = 0; q < R; ++q)
+            if (q == rb[b]) {
+              acc[q][0] += a0;
+              acc[q][1] += a1;
+            }
+        }
+        first = false;
+        if (!ok[B - 1]) break;
+      }
+      have_nx = false;
+      int r, d, g;
+      if (step + 1 < nsteps && S.unit(step + 1, warp, r, d, g)) {   // in flight over the barriers
+        const T *t = S.unit_ptr(step + 1, r, d, g);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) nx[e] = __ldg(t + e * 32 + lane);
+        have_nx = true;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) red[(warp * R + q) * 32 + lane] = acc[q][0] + acc[q][1];
     __syncthreads();
-    if (warp == 0) {
-      T s = T(0);
+    if (warp < kChain) {
+      // CTA partial of each row: warps w, w+4, w+8, w+12, then the four sums
+      T *cb = chn + (buf & 1) * (kChain * R * 32);
 #pragma unroll
-      for (int k = 1; k < kClWarps; ++k) s += red[k * 32 + lane];
+      for (int q = 0; q < R; ++q) {
+        T s = red[(warp * R + q) * 32 + lane];
 #pragma unroll
-      for (int q = 0; q < C; ++q) {
-        T *dst = cluster.map_shared_rank(part, q);
-        dst[(par * C + c) * 32 + lane] = s;
+        for (int k = warp + kChain; k < kClWarps; k += kChain) s += red[(k * R + q) * 32 + lane];
+        cb[(warp * R + q) * 32 + lane] = s;
+      }
+      chain_bar();
+      ++buf;
+      T tot[R];
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        tot[q] = cb[q * 32 + lane];
+#pragma unroll
+        for (int k = 1; k < kChain; ++k) tot[q] += cb[(k * R + q) * 32 + lane];
+      }
+      for (int dst = warp; dst < C; dst += kChain) {
+        T *p = cluster.map_shared_rank(part, dst);
+#pragma unroll
+        for (int q = 0; q < R; ++q) p[((par * R + q) * C + c) * 32 + lane] = tot[q];
       }
     }
     cluster.sync();
-    if (warp == 0) {
-      T s = y[I * 32 + lane];
+    if (warp < kChain) {
+      T yr[R];
 #pragma unroll
-      for (int q = 0; q < C; ++q) s -= part[(par * C + q) * 32 + lane];
-      red[lane] = s;
-      __syncwarp();
-      T o0 = T(0), o1 = T(0), o2 = T(0), o3 = T(0);
+      for (int r = 0; r < R; ++r) {
+        if (!S.valid(step, r)) break;
+        const int I = S.row(step, r);
+        T s = y[I * 32 + lane];
 #pragma unroll
-      for (int k = 0; k < 32; k += 4) {
-        o0 += dv[k] * red[k];
-        o1 += dv[k + 1] * red[k + 1];
-        o2 += dv[k + 2] * red[k + 2];
-        o3 += dv[k + 3] * red[k + 3];
-      }
-      y[I * 32 + lane] = (o0 + o1) + (o2 + o3);
-      if (step + 1 < nt) {
-        const T *D = tile_at(pool, L, row_of(step + 1), 0);
+        for (int q = 0; q < C; ++q) s -= part[((par * R + r) * C + q) * 32 + lane];
+        if (r > 0) {                            // couplings to the rows solved in this step
+          T pn0 = T(0), pn1 = T(0);
 #pragma unroll
-        for (int k = 0; k < 32; ++k) dv[k] = __ldg(D + k * 32 + lane);
+          for (int d = 1; d <= r; ++d)
+#pragma unroll
+            for (int k = 0; k < 8; k += 2) {
+              pn0 += nv[r * (r - 1) / 2 + d - 1][k] * __shfl_sync(0xffffffffu, yr[r - d], warp * 8 + k);
+              pn1 += nv[r * (r - 1) / 2 + d - 1][k + 1] *
+                     __shfl_sync(0xffffffffu, yr[r - d], warp * 8 + k + 1);
+            }
+          T *cb = chn + (buf & 1) * (kChain * R * 32);
+          cb[warp * 32 + lane] = pn0 + pn1;
+          chain_bar();
+          ++buf;
+          s -= ((cb[lane] + cb[32 + lane]) + cb[64 + lane]) + cb[96 + lane];
+        }
+        T po0 = T(0), po1 = T(0);
+#pragma unroll
+        for (int k = 0; k < 8; k += 2) {
+          po0 += dv[r][k] * __shfl_sync(0xffffffffu, s, warp * 8 + k);
+          po1 += dv[r][k + 1] * __shfl_sync(0xffffffffu, s, warp * 8 + k + 1);
+        }
+        T *cb = chn + (buf & 1) * (kChain * R * 32);
+        cb[warp * 32 + lane] = po0 + po1;
+        chain_bar();
+        ++buf;
+        yr[r] = ((cb[lane] + cb[32 + lane]) + cb[64 + lane]) + cb[96 + lane];
+        if (warp == 0) y[I * 32 + lane] = yr[r];
       }
     }
     __syncthreads();
   }
 }
 
-template <typename T, int C>
+template <typename T, int C, int R>
 __global__ void __launch_bounds__(kClWarps * 32)
     k_schwarz_cluster(const SubDesc *subs, const BandLayout *lay, int nnx, int nny,
                       const T *poolL, const T *poolU, const double *__restrict__ r,
@@ -142,9 +285,10 @@ __global__ void __launch_bounds__(kClWarps * 32)
   if (cgs && cgs->done) return;           // the same for every CTA of the cluster
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smraw[];
-  T *red = reinterpret_cast<T *>(smraw);  // [kClWarps][32]
-  T *part = red + kClWarps * 32;          // [2][C][32]
-  T *y = part + 2 * C * 32;               // [npad]
+  T *red = reinterpret_cast<T *>(smraw);  // [kClWarps][R][32]
+  T *chn = red + kClWarps * R * 32;       // [2][kChain][R][32]
+  T *part = chn + 2 * kChain * R * 32;    // [2][R][C][32]
+  T *y = part + 2 * R * C * 32;           // [npad]
   const int j = blockIdx.x / C;
   const SubDesc &S = subs[j];
   const BandLayout L = lay[j];
@@ -160,8 +304,8 @@ __global__ void __launch_bounds__(kClWarps * 32)
     y[l] = v;
   }
   cluster.sync();                          // every CTA's shared memory is live
-  cluster_sweep<T, C>(cluster, poolL, L, y, red, part, false);
-  cluster_sweep<T, C>(cluster, poolU, L, y, red, part, true);
+  cluster_sweep<T, C, R>(cluster, poolL, L, y, red, chn, part, false);
+  cluster_sweep<T, C, R>(cluster, poolU, L, y, red, chn, part, true);
   if (cluster.block_rank() == 0) {
     T *out = xloc + S.v_int;
     for (int l = threadIdx.x; l < n; l += blockDim.x) out[l] = y[l];
@@ -170,18 +314,18 @@ __global__ void __launch_bounds__(kClWarps * 32)
 }
 
 template <typename T>
-int smem_bytes(int npad, int C) {
-  return (kClWarps * 32 + 2 * C * 32 + npad) * (int)sizeof(T);
+int smem_bytes(int npad, int C, int R) {
+  return ((kClWarps + 2 * kChain + 2 * C) * R * 32 + npad) * (int)sizeof(T);
 }
 
-template <typename T, int C>
-int launch_c(const SubDesc *d_subs, const BandLayout *d_lay, int nsub, int npad_max, int nnx,
-             int nny, const T *poolL, const T *poolU, const double *r, T *xloc,
-             const CGScalars *cgs, cudaStream_t s) {
+template <typename T, int C, int R>
+int launch_cr(const SubDesc *d_subs, const BandLayout *d_lay, int nsub, int npad_max, int nnx,
+              int nny, const T *poolL, const T *poolU, const double *r, T *xloc,
+              const CGScalars *cgs, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nsub * C);
   cfg.blockDim = dim3(kClWarps * 32);
-  cfg.dynamicSmemBytes = smem_bytes<T>(npad_max, C);
+  cfg.dynamicSmemBytes = smem_bytes<T>(npad_max, C, R);
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -190,15 +334,29 @@ int launch_c(const SubDesc *d_subs, const BandLayout *d_lay, int nsub, int npad_
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_schwarz_cluster<T, C>, d_subs, d_lay, nnx, nny,
+  GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_schwarz_cluster<T, C, R>, d_subs, d_lay, nnx, nny,
                                     poolL, poolU, r, xloc, cgs));
   GENEO_COUNT_LAUNCH();
   return GENEO_OK;
 }
 
 template <typename T, int C>
+int launch_c(int rows, const SubDesc *d_subs, const BandLayout *d_lay, int nsub, int npad_max,
+             int nnx, int nny, const T *poolL, const T *poolU, const double *r, T *xloc,
+             const CGScalars *cgs, cudaStream_t s) {
+  switch (rows) {
+    case 4: return launch_cr<T, C, 4>(d_subs, d_lay, nsub, npad_max, nnx, nny, poolL, poolU, r, xloc, cgs, s);
+    case 2: return launch_cr<T, C, 2>(d_subs, d_lay, nsub, npad_max, nnx, nny, poolL, poolU, r, xloc, cgs, s);
+    default: return launch_cr<T, C, 1>(d_subs, d_lay, nsub, npad_max, nnx, nny, poolL, poolU, r, xloc, cgs, s);
+  }
+}
+
+template <typename T, int C>
 int prepare_c(int npad_max) {
-  return ensure_smem(k_schwarz_cluster<T, C>, smem_bytes<T>(npad_max, C));
+  int st;
+  if ((st = ensure_smem(k_schwarz_cluster<T, C, 1>, smem_bytes<T>(npad_max, C, 1)))) return st;
+  if ((st = ensure_smem(k_schwarz_cluster<T, C, 2>, smem_bytes<T>(npad_max, C, 2)))) return st;
+  return ensure_smem(k_schwarz_cluster<T, C, 4>, smem_bytes<T>(npad_max, C, 4));
 }
 
 }  // namespace
@@ -213,7 +371,7 @@ int schwarz_cluster_size(int nsub, int sm_count) {
 
 template <typename T>
 int prepare_schwarz_solve(int npad_max) {
-  if (smem_bytes<T>(npad_max, 8) > 227 * 1024) return GENEO_ERR_INVALID_ARG;
+  if (smem_bytes<T>(npad_max, 8, 4) > 227 * 1024) return GENEO_ERR_INVALID_ARG;
   int st;
   if ((st = prepare_c<T, 1>(npad_max))) return st;
   if ((st = prepare_c<T, 2>(npad_max))) return st;
@@ -224,14 +382,14 @@ int prepare_schwarz_solve(int npad_max) {
 template <typename T>
 int launch_schwarz_solve(const SubDesc *d_subs, const BandLayout *d_lay, int nsub, int npad_max,
                          int nnx, int nny, const T *poolL, const T *poolU, const double *r,
-                         T *xloc, const CGScalars *cgs, int cluster, DevStatus *status,
-                         cudaStream_t s) {
+                         T *xloc, const CGScalars *cgs, int cluster, int rows,
+                         DevStatus *status, cudaStream_t s) {
   (void)status;
   switch (cluster) {
-    case 8: return launch_c<T, 8>(d_subs, d_lay, nsub, npad_max, nnx, nny, poolL, poolU, r, xloc, cgs, s);
-    case 4: return launch_c<T, 4>(d_subs, d_lay, nsub, npad_max, nnx, nny, poolL, poolU, r, xloc, cgs, s);
-    case 2: return launch_c<T, 2>(d_subs, d_lay, nsub, npad_max, nnx, nny, poolL, poolU, r, xloc, cgs, s);
-    default: return launch_c<T, 1>(d_subs, d_lay, nsub, npad_max, nnx, nny, poolL, poolU, r, xloc, cgs, s);
+    case 8: return launch_c<T, 8>(rows, d_subs, d_lay, nsub, npad_max, nnx, nny, poolL, poolU, r, xloc, cgs, s);
+    case 4: return launch_c<T, 4>(rows, d_subs, d_lay, nsub, npad_max, nnx, nny, poolL, poolU, r, xloc, cgs, s);
+    case 2: return launch_c<T, 2>(rows, d_subs, d_lay, nsub, npad_max, nnx, nny, poolL, poolU, r, xloc, cgs, s);
+    default: return launch_c<T, 1>(rows, d_subs, d_lay, nsub, npad_max, nnx, nny, poolL, poolU, r, xloc, cgs, s);
   }
 }
 
@@ -239,10 +397,10 @@ template int prepare_schwarz_solve<double>(int);
 template int prepare_schwarz_solve<float>(int);
 template int launch_schwarz_solve<double>(const SubDesc *, const BandLayout *, int, int, int, int,
                                           const double *, const double *, const double *,
-                                          double *, const CGScalars *, int, DevStatus *,
+                                          double *, const CGScalars *, int, int, DevStatus *,
                                           cudaStream_t);
 template int launch_schwarz_solve<float>(const SubDesc *, const BandLayout *, int, int, int, int,
                                          const float *, const float *, const double *, float *,
-                                         const CGScalars *, int, DevStatus *, cudaStream_t);
+                                         const CGScalars *, int, int, DevStatus *, cudaStream_t);
 
 }  // namespace geneo

@@ -114,8 +114,9 @@ class GeneoServer:
 
     Memory model: a slot keeps the device workspace of its largest request
     (the library's workspaces only grow), so the budget is charged with the
-    sum over slots of their resident bytes.  Admission is FIFO: the head of
-    the queue is placed on an idle slot that already holds its key (no
+    sum over slots of their resident bytes.  Admission is FIFO (a request
+    whose key is resident in a busy slot waits for that slot and lets later
+    requests pass): a request is placed on an idle slot that holds its key (no
     assembly or set-up), else on an idle slot holding no resident problem,
     else on the idle slot whose growth to the request's size keeps the total
     lowest; in every case only if the new total fits the budget.
@@ -199,20 +200,39 @@ class GeneoServer:
             return None
         return best[1], False
 
+    def _next(self):
+        """(request, slot, reuse) to start now, or None.  Lock held.
+
+        FIFO, except that a request whose structure is resident in a busy slot
+        waits for that slot (it will only solve there) and lets the requests
+        behind it go first; the first request that may start anywhere but does
+        not fit the memory budget stops the scan (no bypass by size).
+        """
+        busy_keys = {self.slot_key[s] for s in range(self.nslots)
+                     if not self.idle[s] and self.slot_key[s] is not None}
+        for req in self.queue:
+            if req.key is not None and (req.key, req.prec) in busy_keys:
+                continue
+            placed = self._place(req)
+            if placed is None:
+                return None
+            return (req,) + placed
+        return None
+
     def _dispatch(self):
         while True:
             with self.lock:
-                placed = None
+                nxt = None
                 while not self.closed or self.queue:
                     if self.queue:
-                        placed = self._place(self.queue[0])
-                        if placed is not None:
+                        nxt = self._next()
+                        if nxt is not None:
                             break
                     self.lock.wait(0.05)
-                if placed is None:
+                if nxt is None:
                     return
-                req = self.queue.popleft()
-                slot, reuse = placed
+                req, slot, reuse = nxt
+                self.queue.remove(req)
                 self.idle[slot] = False
                 self.slot_mem[slot] = max(self.slot_mem[slot], req.mem)
                 self.slot_key[slot] = None if req.key is None else (req.key, req.prec)

@@ -161,3 +161,18 @@ def test_latency_summary():
     assert s["n"] == 10 and s["failed"] == 0
     assert 0 < s["p50_ms"] <= s["p99_ms"] <= s["max_ms"]
     assert s["solves_per_s"] > 0
+
+
+def test_repeated_key_waits_for_its_resident_slot():
+    # a burst: A, A, B with two slots.  The second A waits for the slot that
+    # holds A (reuse) while B takes the other slot.
+    srv, ex = make_server(slots=2, budget=100, duration=0.05)
+    a1 = srv.submit({"id": "A", "mem": 20}, key="A")
+    a2 = srv.submit({"id": "A", "mem": 20}, key="A")
+    b = srv.submit({"id": "B", "mem": 20}, key="B")
+    for r in (a1, a2, b):
+        r.wait(10)
+    srv.close()
+    assert a2.reused and a2.slot == a1.slot
+    assert b.slot != a1.slot and not b.reused
+    assert b.t_start < a2.t_start          # B went ahead of the waiting A
