@@ -439,16 +439,35 @@ int launch_band_clear(const BandLayout *d_lay, int nsys, T *pool, long long pool
   return GENEO_OK;
 }
 
+// Trailing update of tile column J (part 0 all pairs, 1 the next tile column,
+// 2 the rest): FP32 factors on the tensor cores (3xTF32), FP64 on the FMA units.
+template <typename T>
+int launch_update(const BandLayout *d_lay, int nsys, int J, int w_max, T *poolL, int part,
+                  DevStatus *st, cudaStream_t s) {
+  const int npairs = w_max * (w_max + 1) / 2;
+  if constexpr (sizeof(T) == 4) {
+    if (use_tensor_cores()) return launch_chol_update_tc(d_lay, nsys, J, w_max, poolL, part, st, s);
+  }
+  const int ny = part == 1 ? w_max : (part == 2 ? npairs - w_max : npairs);
+  if (ny > 0) {
+    k_chol_update<T><<<dim3(nsys, ny), 256, 0, s>>>(d_lay, nsys, J, poolL, part); GENEO_COUNT_LAUNCH();
+  }
+  return GENEO_OK;
+}
+
 template <typename T>
 int launch_band_cholesky(const BandLayout *d_lay, int nsys, int nt_max, int w_max, T *poolL,
                          T *poolU, DevStatus *st, cudaStream_t s, cudaStream_t side) {
-  const int npairs = w_max * (w_max + 1) / 2;
+  int rc;
+  if constexpr (sizeof(T) == 4) {
+    if (use_tensor_cores() && (rc = prepare_chol_update_tc())) return rc;
+  }
   if (!side || w_max == 0) {
     for (int J = 0; J < nt_max; ++J) {
       k_chol_diag<T><<<nsys, 1024, 0, s>>>(d_lay, nsys, J, poolL, poolU, st); GENEO_COUNT_LAUNCH();
       if (w_max > 0) {
         k_chol_trsm<T><<<dim3(nsys, w_max), 256, 0, s>>>(d_lay, nsys, J, poolL, poolU); GENEO_COUNT_LAUNCH();
-        k_chol_update<T><<<dim3(nsys, npairs), 256, 0, s>>>(d_lay, nsys, J, poolL, 0); GENEO_COUNT_LAUNCH();
+        if ((rc = launch_update<T>(d_lay, nsys, J, w_max, poolL, 0, st, s))) return rc;
       }
     }
     GENEO_CUDA_TRY(cudaGetLastError());
@@ -463,14 +482,12 @@ int launch_band_cholesky(const BandLayout *d_lay, int nsys, int nt_max, int w_ma
   k_chol_diag<T><<<nsys, 1024, 0, s>>>(d_lay, nsys, 0, poolL, poolU, st); GENEO_COUNT_LAUNCH();
   k_chol_trsm<T><<<dim3(nsys, w_max), 256, 0, s>>>(d_lay, nsys, 0, poolL, poolU); GENEO_COUNT_LAUNCH();
   for (int J = 0; J + 1 < nt_max; ++J) {
-    k_chol_update<T><<<dim3(nsys, w_max), 256, 0, s>>>(d_lay, nsys, J, poolL, 1); GENEO_COUNT_LAUNCH();
+    if ((rc = launch_update<T>(d_lay, nsys, J, w_max, poolL, 1, st, s))) return rc;
     GENEO_CUDA_TRY(cudaEventRecord(e_main, s));
     GENEO_CUDA_TRY(cudaStreamWaitEvent(side, e_main, 0));
     k_chol_diag<T><<<nsys, 1024, 0, side>>>(d_lay, nsys, J + 1, poolL, poolU, st); GENEO_COUNT_LAUNCH();
     k_chol_trsm<T><<<dim3(nsys, w_max), 256, 0, side>>>(d_lay, nsys, J + 1, poolL, poolU); GENEO_COUNT_LAUNCH();
-    if (npairs > w_max) {
-      k_chol_update<T><<<dim3(nsys, npairs - w_max), 256, 0, s>>>(d_lay, nsys, J, poolL, 2); GENEO_COUNT_LAUNCH();
-    }
+    if ((rc = launch_update<T>(d_lay, nsys, J, w_max, poolL, 2, st, s))) return rc;
     GENEO_CUDA_TRY(cudaEventRecord(e_side, side));
     GENEO_CUDA_TRY(cudaStreamWaitEvent(s, e_side, 0));
   }

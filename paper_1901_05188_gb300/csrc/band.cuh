@@ -32,6 +32,15 @@ int launch_band_solve_dense(const BandLayout *d_lay, int nsys, int npad_max,
                             long long in_sys, int in_row, double *out, long long out_sys,
                             int out_row, int ncols, int mode, cudaStream_t s);
 
+// FP32 trailing update of tile column J on the tensor cores (3xTF32 tcgen05
+// MMAs, blocks of 4 x 4 tiles); part as for the band Cholesky's update
+// (0 all, 1 the first block column, 2 the other block columns).
+int prepare_chol_update_tc();
+int launch_chol_update_tc(const BandLayout *d_lay, int nsys, int J, int w_max, float *poolL,
+                          int part, DevStatus *status, cudaStream_t s);
+// Tensor cores for the FP32 factor updates unless GENEO_TENSOR_CORES=0.
+bool use_tensor_cores();
+
 // Extract A_j = R_j A R_j^T (interior dofs) from the global BSR into band tiles.
 template <typename T>
 int launch_extract_interior(const SubDesc *d_subs, const BandLayout *d_lay, int nsub,
