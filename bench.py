@@ -431,6 +431,8 @@ def run_ours(args):
                     phases_ms=dict(assemble=st["ms_assemble"], setup_eig_coarse=st["ms_setup_eig"],
                                    setup_factor=st["ms_setup_factor"], solve=st["ms_solve"]),
                     bytes_per_iter=st["bytes_per_iter"], kernels=kernels,
+                    schwarz_launch=dict(cluster=st["schwarz_cluster"], rows=st["schwarz_rows"],
+                                        chosen_by="set-up autotuner"),
                     accuracy_vs_oracle=acc, mixed_precision=mixed, serving=serving)
         print(json.dumps(line))
     s.close()

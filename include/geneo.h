@@ -114,6 +114,8 @@ typedef struct {
   double kappa_est;               /* Lanczos estimate from the CG coefficients (PCG only, else 0) */
   int n_coarse;                   /* N_H = sum_j m_j */
   int n_subdomains;
+  /* CUDA-event times; the subdomain factorisation (ms_setup_factor) runs on its
+   * own streams concurrently with the GenEO eigensolve (ms_setup_eig) */
   float ms_assemble, ms_setup_eig, ms_setup_coarse, ms_setup_factor, ms_solve;
   double bytes_per_iter;          /* algorithmic HBM bytes of one iteration */
   double eig_max_residual;        /* max Ritz residual of the kept eigenpairs */

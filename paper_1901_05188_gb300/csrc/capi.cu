@@ -240,6 +240,8 @@ int geneo_create(geneo_ctx **out, void *cuda_stream) {
   GENEO_CUDA_TRY(cudaMallocHost(&c->cg_host, sizeof(CGScalars)));
   GENEO_CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
   GENEO_CUDA_TRY(cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking));
+  GENEO_CUDA_TRY(cudaStreamCreateWithFlags(&c->fac_stream, cudaStreamNonBlocking));
+  GENEO_CUDA_TRY(cudaStreamCreateWithFlags(&c->fac_side, cudaStreamNonBlocking));
   *out = c;
   return GENEO_OK;
 }
@@ -264,6 +266,8 @@ int geneo_destroy(geneo_ctx *c) {
   if (c->cg_host) cudaFreeHost(c->cg_host);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->side_stream) cudaStreamDestroy(c->side_stream);
+  if (c->fac_stream) cudaStreamDestroy(c->fac_stream);
+  if (c->fac_side) cudaStreamDestroy(c->fac_side);
   delete c;
   return GENEO_OK;
 }
@@ -1212,39 +1216,55 @@ int geneo_setup(geneo_ctx *c, const geneo_partition *part, const geneo_modes *mo
   pc.m.assign(P.nsub, 0);
   pc.lambdas.assign((size_t)P.nsub * pc.mcap, INFINITY);
   pc.eig_max_res = 0.0;
-  if (pc.mcap > 1) {
-    if ((st = setup_coarse(c, P, s))) return st;
-  }
-  GENEO_CUDA_TRY(cudaEventRecord(ev[1], s));
-  // subdomain factors A_j = L_j L_j^T
+  // Subdomain factors A_j = L_j L_j^T on their own pair of streams, overlapping
+  // the GenEO eigensolve (the two share no buffers).  The main stream waits
+  // for the extraction, which reads the subdomain descriptors that the coarse
+  // set-up rewrites later.
+  cudaStream_t fs = c->fac_stream;
+  cudaEvent_t e_ready, e_extracted;
+  GENEO_CUDA_TRY(cudaEventCreateWithFlags(&e_ready, cudaEventDisableTiming));
+  GENEO_CUDA_TRY(cudaEventCreateWithFlags(&e_extracted, cudaEventDisableTiming));
+  GENEO_CUDA_TRY(cudaEventRecord(e_ready, s));
+  GENEO_CUDA_TRY(cudaStreamWaitEvent(fs, e_ready, 0));
+  GENEO_CUDA_TRY(cudaEventRecord(ev[1], fs));
   const int nnx = c->nx + 1, nny = c->ny + 1, nnz = c->nz + 1;
   if (f32) {
     float *L = (float *)pc.facL, *U = (float *)pc.facU;
-    if ((st = launch_band_clear<float>(pc.d_lay_int, P.nsub, L, pc.fac_int_elems, s))) return st;
+    if ((st = launch_band_clear<float>(pc.d_lay_int, P.nsub, L, pc.fac_int_elems, fs))) return st;
     if ((st = launch_extract_interior<float>(pc.d_subs, pc.d_lay_int, P.nsub, P.max_nodes_int, nnx,
-                                             nny, nnz, c->row_ptr, c->val, L, s)))
+                                             nny, nnz, c->row_ptr, c->val, L, fs)))
       return st;
+    GENEO_CUDA_TRY(cudaEventRecord(e_extracted, fs));
     if ((st = launch_band_cholesky<float>(pc.d_lay_int, P.nsub, pc.nt_int_max, pc.w_int_max, L, U,
-                                          c->status, s, c->side_stream)))
+                                          c->status, fs, c->fac_side)))
       return st;
   } else {
     double *L = (double *)pc.facL, *U = (double *)pc.facU;
-    if ((st = launch_band_clear<double>(pc.d_lay_int, P.nsub, L, pc.fac_int_elems, s))) return st;
+    if ((st = launch_band_clear<double>(pc.d_lay_int, P.nsub, L, pc.fac_int_elems, fs))) return st;
     if ((st = launch_extract_interior<double>(pc.d_subs, pc.d_lay_int, P.nsub, P.max_nodes_int,
-                                              nnx, nny, nnz, c->row_ptr, c->val, L, s)))
+                                              nnx, nny, nnz, c->row_ptr, c->val, L, fs)))
       return st;
+    GENEO_CUDA_TRY(cudaEventRecord(e_extracted, fs));
     if ((st = launch_band_cholesky<double>(pc.d_lay_int, P.nsub, pc.nt_int_max, pc.w_int_max, L,
-                                           U, c->status, s, c->side_stream)))
+                                           U, c->status, fs, c->fac_side)))
       return st;
   }
-  GENEO_CUDA_TRY(cudaEventRecord(ev[2], s));
+  GENEO_CUDA_TRY(cudaEventRecord(ev[2], fs));
+  GENEO_CUDA_TRY(cudaStreamWaitEvent(s, e_extracted, 0));
+  if (pc.mcap > 1) {
+    if ((st = setup_coarse(c, P, s))) return st;
+  }
+  GENEO_CUDA_TRY(cudaEventRecord(ev[3], s));
+  GENEO_CUDA_TRY(cudaStreamWaitEvent(s, ev[2], 0));
+  cudaEventDestroy(e_ready);
+  cudaEventDestroy(e_extracted);
   int where = -1;
   st = check_status(c, &where);
   if (st) {
     c->last_stats.failed_subdomain = where;
     return st;
   }
-  GENEO_CUDA_TRY(cudaEventElapsedTime(&pc.ms_eig, ev[0], ev[1]));
+  GENEO_CUDA_TRY(cudaEventElapsedTime(&pc.ms_eig, ev[0], ev[3]));
   GENEO_CUDA_TRY(cudaEventElapsedTime(&pc.ms_factor, ev[1], ev[2]));
   pc.ms_coarse = 0.f;
   for (auto &e : ev) cudaEventDestroy(e);

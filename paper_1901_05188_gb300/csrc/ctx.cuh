@@ -11,6 +11,8 @@ struct geneo_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;        // private stream used only to capture graphs
   cudaStream_t side_stream = nullptr;       // private stream for look-ahead factorisation
+  cudaStream_t fac_stream = nullptr;        // subdomain factorisation, overlapping the eigensolve
+  cudaStream_t fac_side = nullptr;          // its look-ahead stream
   int device = 0;
 
   // ---- mesh / assembled system (phase 0)
