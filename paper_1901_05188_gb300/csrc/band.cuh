@@ -53,7 +53,8 @@ int prepare_schwarz_solve(int npad_max);
 
 // One-level Schwarz local solves: x_j = A_j^-1 R_j r for every subdomain, one
 // thread-block cluster of `cluster` CTAs (1, 2, 4 or 8) per subdomain, `rows`
-// tile rows (1, 2 or 4) per cluster barrier.
+// tile rows (1, 2 or 4) per cluster barrier, or rows = 0 for the look-ahead
+// sweep (the next row's far tiles overlap the current row's chain).
 template <typename T>
 int launch_schwarz_solve(const SubDesc *d_subs, const BandLayout *d_lay, int nsub,
                          int npad_max, int nnx, int nny, const T *poolL, const T *poolU,

@@ -639,6 +639,7 @@ void plan_setup(Arena &A, geneo_ctx *c, const SetupPlan &P) {
     const bool eig = pc.coarse == GENEO_COARSE_GENEO;
     pc.neuL = pc.neuU = pc.Bloc = pc.V = pc.Vt = pc.W = pc.T1 = pc.Hm = nullptr;
     pc.Racc = pc.Rblk = pc.Evec = pc.Eval = pc.Eres = nullptr;
+    pc.gate = nullptr;
     if (eig) {   // shift-invert block Lanczos of the GenEO eigenproblems
       pc.neuL = A.take<double>(pc.fac_neu_elems);
       pc.neuU = A.take<double>(pc.fac_neu_elems);
@@ -649,6 +650,7 @@ void plan_setup(Arena &A, geneo_ctx *c, const SetupPlan &P) {
       pc.T1 = A.take<double>((size_t)nsub * npad * p);
       pc.Hm = A.take<double>((size_t)nsub * pc.kdim * pc.kdim);
       pc.Racc = A.take<double>((size_t)2 * nsub * p * p);
+      pc.gate = A.take<int>(nsub);
       pc.Rblk = A.take<double>((size_t)nsub * p * p);
       pc.Evec = A.take<double>((size_t)2 * nsub * pc.kdim * pc.kdim);
       pc.Eval = A.take<double>((size_t)nsub * pc.kdim);
@@ -683,6 +685,7 @@ void plan_setup(Arena &A, geneo_ctx *c, const SetupPlan &P) {
     pc.neuL = pc.neuU = pc.Bloc = pc.Xneu = pc.V = pc.Vt = pc.W = pc.T1 = pc.Hm = pc.Hpart = nullptr;
     pc.Hs = pc.G = pc.Racc = nullptr;
     pc.Rblk = pc.Evec = pc.Eval = pc.Eres = pc.P = pc.Zp = pc.Yp = nullptr;
+    pc.gate = nullptr;
     pc.AH = pc.AHinv = pc.AHL = pc.AHU = pc.wpart = pc.wH = pc.yH = nullptr;
     pc.nH_cap = 0;
     pc.z_elems = 0;
@@ -847,12 +850,20 @@ static int setup_coarse(geneo_ctx *c, SetupPlan &P, cudaStream_t s) {
                                         pc.W, sW, p, p, 1, s)))
         return st;
       const int na = (k + 1) * p;
+      // full re-orthogonalisation against V: a second pass only for the
+      // subdomains where the first one removed most of a column
       for (int pass = 0; pass < 2; ++pass) {
+        const int *gate = pass == 0 ? nullptr : pc.gate;
+        if (pass == 1) {
+          launch_tsdots(pc.d_subs, nsub, npad, pc.W, p, sW, p, pc.W, p, sW, p, pc.Hpart,
+                        kDotChunks, pc.G, (long long)p * p, s);
+          launch_reorth_gate(nsub, pc.G, p, pc.Hs, na, (long long)na * p, pc.gate, s);
+        }
         launch_tsdots(pc.d_subs, nsub, npad, pc.V, ldv, sV, na, pc.W, p, sW, p, pc.Hpart,
-                      kDotChunks, pc.Hs, (long long)na * p, s);
+                      kDotChunks, pc.Hs, (long long)na * p, s, gate);
         launch_hm_accum(nsub, pc.Hm, kdim, pc.Hs, na, k, p, s);
         launch_tsgemm(pc.d_subs, nsub, npad, pc.V, ldv, sV, na, pc.Hs, p, (long long)na * p,
-                      pc.W, p, sW, p, -1.0, 1.0, s);
+                      pc.W, p, sW, p, -1.0, 1.0, s, gate);
       }
       for (int pass = 0; pass < 2; ++pass) {
         launch_tsdots(pc.d_subs, nsub, npad, pc.W, p, sW, p, pc.W, p, sW, p, pc.Hpart,
@@ -1062,7 +1073,7 @@ int geneo_estimate_workspace_bytes(const geneo_mesh *mesh, const geneo_partition
 // built; the choice is cached for the process, keyed by precision, subdomain
 // count, largest padded subdomain, largest band width and SM count, so a
 // repeated set-up of the same shape does not tune again.  GENEO_SCHWARZ_CLUSTER
-// and GENEO_SCHWARZ_ROWS fix either dimension.
+// and GENEO_SCHWARZ_ROWS (0 = the look-ahead sweep) fix either dimension.
 struct TuneKey {
   int prec, nsub, npad, w, sms;
   bool operator<(const TuneKey &o) const {
@@ -1097,11 +1108,13 @@ static int tune_schwarz(geneo_ctx *c, const SetupPlan &P, cudaStream_t s) {
   Precond &pc = c->pc;
   const TuneKey key{(int)pc.prec, P.nsub, pc.npad_int_max, pc.w_int_max, pc.sms};
   const int fc = env_choice("GENEO_SCHWARZ_CLUSTER", {1, 2, 4, 8});
-  const int fr = env_choice("GENEO_SCHWARZ_ROWS", {1, 2, 4});
+  const int fr = env_choice("GENEO_SCHWARZ_ROWS", {0, 1, 2, 4});
+  const char *fr_env = std::getenv("GENEO_SCHWARZ_ROWS");
+  const bool fr_set = fr_env && (fr || fr_env[0] == '0');
   {
     std::lock_guard<std::mutex> g(g_tune_mu);
     auto it = g_tune.find(key);
-    if (it != g_tune.end() && !fc && !fr) {
+    if (it != g_tune.end() && !fc && !fr_set) {
       pc.cluster = it->second.first;
       pc.rows = it->second.second;
       return GENEO_OK;
@@ -1115,9 +1128,9 @@ static int tune_schwarz(geneo_ctx *c, const SetupPlan &P, cudaStream_t s) {
     for (int C : {1, 2, 4, 8})
       if (C == 1 || P.nsub * C <= pc.sms) cs.push_back(C);
   }
-  if (fr) rs = {fr};
-  else if (pc.prec == GENEO_MIXED_FP32) rs = {1, 2, 4};
-  else rs = {1, 2};
+  if (fr_set) rs = {fr};
+  else if (pc.prec == GENEO_MIXED_FP32) rs = {0, 1, 2, 4};
+  else rs = {0, 1, 2};
   if (cs.size() * rs.size() == 1) {
     pc.cluster = cs[0];
     pc.rows = rs[0];
@@ -1146,7 +1159,7 @@ static int tune_schwarz(geneo_ctx *c, const SetupPlan &P, cudaStream_t s) {
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (!fc && !fr) {
+  if (!fc && !fr_set) {
     std::lock_guard<std::mutex> g(g_tune_mu);
     g_tune[key] = {pc.cluster, pc.rows};
   }

@@ -161,8 +161,9 @@ __global__ void k_random_block(const SubDesc *subs, int npad, double *V, int ld,
 __global__ void __launch_bounds__(256)
     k_tsdots(const SubDesc *subs, const double *__restrict__ A, int lda, long long sa, int na,
              const double *__restrict__ B, int ldb, long long sb, int nb, double *Hpart,
-             int chunks) {
+             int chunks, const int *gate) {
   const int j = blockIdx.y, ch = blockIdx.x;
+  if (gate && !gate[j]) return;                       // the reduction writes zeros
   const int n = subs[j].n_neu;
   const int per = (n + chunks - 1) / chunks;
   const int r0 = ch * per, r1 = min(n, r0 + per);
@@ -203,20 +204,48 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-__global__ void k_tsdots_reduce(const double *Hpart, int chunks, int nout, double *H, long long hs) {
+__global__ void k_tsdots_reduce(const double *Hpart, int chunks, int nout, double *H, long long hs,
+                                const int *gate) {
   const int j = blockIdx.x;
+  const bool skip = gate && !gate[j];
   for (int o = threadIdx.x; o < nout; o += blockDim.x) {
     double s = 0.0;
-    for (int ch = 0; ch < chunks; ++ch) s += Hpart[((long long)j * chunks + ch) * nout + o];
+    if (!skip)
+      for (int ch = 0; ch < chunks; ++ch) s += Hpart[((long long)j * chunks + ch) * nout + o];
     H[j * hs + o] = s;
   }
+}
+
+// Second re-orthogonalisation pass needed?  After one projection W -= V H,
+// column b of W has squared norm G_bb and lost sum_a H_ab^2; the pass is
+// repeated where more than half of the column's squared norm was removed,
+// G_bb < sum_a H_ab^2 (the criterion of Daniel, Gragg, Kaufman and Stewart with
+// eta = 1/sqrt(2): "twice is enough").
+__global__ void k_reorth_gate(const double *G, int p, const double *H, int na, long long hs,
+                              int *gate) {
+  const int j = blockIdx.x;
+  __shared__ int need;
+  if (threadIdx.x == 0) need = 0;
+  __syncthreads();
+  if (threadIdx.x < p) {
+    const int b = threadIdx.x;
+    double lost = 0.0;
+    for (int a = 0; a < na; ++a) {
+      const double h = H[j * hs + (long long)a * p + b];
+      lost += h * h;
+    }
+    if (!(G[(long long)j * p * p + b * p + b] >= lost)) atomicOr(&need, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) gate[j] = need;
 }
 
 __global__ void __launch_bounds__(256)
     k_tsgemm(const SubDesc *subs, int npad, const double *__restrict__ A, int lda, long long sa,
              int na, const double *__restrict__ H, int ldh, long long hs, double *C, int ldc,
-             long long sc, int nb, double alpha, double beta) {
+             long long sc, int nb, double alpha, double beta, const int *gate) {
   const int j = blockIdx.y;
+  if (gate && !gate[j]) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   double *sH = reinterpret_cast<double *>(smraw);   // [na][nb]
   for (int e = threadIdx.x; e < na * nb; e += blockDim.x) {
@@ -836,24 +865,31 @@ void launch_random_block(const SubDesc *d_subs, int nsub, int npad, double *V, i
 
 void launch_tsdots(const SubDesc *d_subs, int nsub, int npad, const double *A, int lda,
                    long long sa, int na, const double *B, int ldb, long long sb, int nb,
-                   double *Hpart, int chunks, double *H, long long hs, cudaStream_t s) {
+                   double *Hpart, int chunks, double *H, long long hs, cudaStream_t s,
+                   const int *gate) {
   (void)npad;
   int sm = 16 * (na + nb) * (int)sizeof(double);
   (void)ensure_smem(k_tsdots, sm);   // a failure surfaces as a launch error
   k_tsdots<<<dim3(chunks, nsub), 256, sm, s>>>(d_subs, A, lda, sa, na, B, ldb, sb, nb, Hpart,
-                                               chunks); GENEO_COUNT_LAUNCH();
-  k_tsdots_reduce<<<nsub, 256, 0, s>>>(Hpart, chunks, na * nb, H, hs); GENEO_COUNT_LAUNCH();
+                                               chunks, gate); GENEO_COUNT_LAUNCH();
+  k_tsdots_reduce<<<nsub, 256, 0, s>>>(Hpart, chunks, na * nb, H, hs, gate); GENEO_COUNT_LAUNCH();
+}
+
+void launch_reorth_gate(int nsub, const double *G, int p, const double *H, int na, long long hs,
+                        int *gate, cudaStream_t s) {
+  k_reorth_gate<<<nsub, 32, 0, s>>>(G, p, H, na, hs, gate); GENEO_COUNT_LAUNCH();
 }
 
 void launch_tsgemm(const SubDesc *d_subs, int nsub, int npad, const double *A, int lda,
                    long long sa, int na, const double *H, int ldh, long long hs, double *C,
-                   int ldc, long long sc, int nb, double alpha, double beta, cudaStream_t s) {
+                   int ldc, long long sc, int nb, double alpha, double beta, cudaStream_t s,
+                   const int *gate) {
   int sm = na * nb * (int)sizeof(double);
   (void)ensure_smem(k_tsgemm, sm);
   long long tot = (long long)npad * nb;
   dim3 g((unsigned)((tot + 255) / 256), nsub);
   k_tsgemm<<<g, 256, sm, s>>>(d_subs, npad, A, lda, sa, na, H, ldh, hs, C, ldc, sc, nb, alpha,
-                              beta); GENEO_COUNT_LAUNCH();
+                              beta, gate); GENEO_COUNT_LAUNCH();
 }
 
 void launch_cholqr(const SubDesc *d_subs, int nsub, int npad, const double *G, double *W,

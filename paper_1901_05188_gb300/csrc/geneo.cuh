@@ -32,14 +32,23 @@ void launch_random_block(const SubDesc *d_subs, int nsub, int npad, double *V, i
 
 // H[j] = A_j^T B_j over the first n rows (n = n_neu of subdomain j):
 // A_j: n x na at lda, B_j: n x nb at ldb; H row-major na x nb (stride hs).
+// Per-system flag: repeat the projection of W against V where the first pass
+// removed more than half of some column's squared norm (G = W^T W after the
+// pass, H the removed coefficients, na x p per system with stride hs).
+void launch_reorth_gate(int nsub, const double *G, int p, const double *H, int na, long long hs,
+                        int *gate, cudaStream_t s);
 void launch_tsdots(const SubDesc *d_subs, int nsub, int npad, const double *A, int lda,
                    long long sa, int na, const double *B, int ldb, long long sb, int nb,
-                   double *Hpart, int chunks, double *H, long long hs, cudaStream_t s);
+                   double *Hpart, int chunks, double *H, long long hs, cudaStream_t s,
+                   const int *gate = nullptr);
 
 // C_j = beta C_j + alpha A_j H_j (rows < n_neu).
+// gate[j] == 0 (when gate is given) skips system j: the products leave C
+// unchanged and the dot products return zeros.
 void launch_tsgemm(const SubDesc *d_subs, int nsub, int npad, const double *A, int lda,
                    long long sa, int na, const double *H, int ldh, long long hs, double *C,
-                   int ldc, long long sc, int nb, double alpha, double beta, cudaStream_t s);
+                   int ldc, long long sc, int nb, double alpha, double beta, cudaStream_t s,
+                   const int *gate = nullptr);
 
 // Cholesky-QR step on p x p Gram matrices: R = chol(G), W <- W R^-1 (columns
 // with a vanishing pivot are zeroed); Racc <- R Racc.

@@ -34,48 +34,31 @@ __device__ __forceinline__ double sum_partials(const double *part, int n, double
   return block_sum<NT>(v, sh);
 }
 
-// One warp per block row.  Lanes 8r..8r+7 own output component r (lanes
-// 24..31 idle): lane q of group r multiplies row r of blocks q, q+8, q+16,
-// q+24 with x, so each stored value takes exactly one FMA (FP64 issue is the
-// scarce resource on this GPU), all loads are issued before the products, and
-// the group sum is three xor-shuffles.  The row's values are contiguous, so
-// the group's loads stay inside a few L1 lines.
-__device__ __forceinline__ void spmv_row(const int32_t *__restrict__ rp,
-                                         const int32_t *__restrict__ col,
-                                         const double *__restrict__ val,
-                                         const double *__restrict__ x, int row, int lane,
-                                         double &y0, double &y1, double &y2) {
-  const int base = rp[row];
-  const int nb = rp[row + 1] - base;
-  const int r = lane >> 3, q = lane & 7;
-  double acc = 0.0;
-  if (r < 3) {
-    double vv[12], xx[12];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int b = q + 8 * k;
-      if (b < nb) {
-        const double *vb = val + 9 * (size_t)(base + b) + 3 * r;
-        const double *xb = x + 3 * __ldg(col + base + b);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          vv[3 * k + c] = __ldg(vb + c);
-          xx[3 * k + c] = __ldg(xb + c);
-        }
-      } else {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) vv[3 * k + c] = xx[3 * k + c] = 0.0;
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < 12; ++k) acc = fma(vv[k], xx[k], acc);
+// One lane per matrix row: lanes 3i..3i+2 of a warp hold the three rows of
+// block row 10g + i (i < 10; lanes 30, 31 idle), so every stored value takes
+// exactly one FMA and no sum crosses lanes -- FP64 issue, not bandwidth, is the
+// scarce resource on this GPU, and a shuffle reduction costs FP64 adds.  The
+// three lanes of a block row read the three rows of the same 72-byte blocks
+// and the same x entries, so their loads share L1 lines; results are written
+// to 30 consecutive entries of y.
+constexpr int kRowsPerWarp = 10;
+
+__device__ __forceinline__ double spmv_lane_row(const int32_t *__restrict__ rp,
+                                                const int32_t *__restrict__ col,
+                                                const double *__restrict__ val,
+                                                const double *__restrict__ x, int node, int r) {
+  const int base = rp[node];
+  const int nb = rp[node + 1] - base;
+  const double *v = val + 9 * (size_t)base + 3 * r;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+#pragma unroll 9
+  for (int b = 0; b < nb; ++b) {
+    const double *xb = x + 3 * __ldg(col + base + b);
+    a0 = fma(__ldg(v + 9 * b), __ldg(xb), a0);
+    a1 = fma(__ldg(v + 9 * b + 1), __ldg(xb + 1), a1);
+    a2 = fma(__ldg(v + 9 * b + 2), __ldg(xb + 2), a2);
   }
-  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-  acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-  y0 = __shfl_sync(0xffffffffu, acc, 0);
-  y1 = __shfl_sync(0xffffffffu, acc, 8);
-  y2 = __shfl_sync(0xffffffffu, acc, 16);
+  return (a0 + a1) + a2;
 }
 
 __global__ void __launch_bounds__(256) k_spmv(int nnode, const int32_t *__restrict__ rp,
@@ -83,17 +66,13 @@ __global__ void __launch_bounds__(256) k_spmv(int nnode, const int32_t *__restri
                                               const double *__restrict__ val,
                                               const double *__restrict__ x,
                                               double *__restrict__ y) {
-  int lane = threadIdx.x & 31;
-  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int row = warp; row < nnode; row += nw) {
-    double y0, y1, y2;
-    spmv_row(rp, col, val, x, row, lane, y0, y1, y2);
-    if (lane == 0) {
-      y[3 * row] = y0;
-      y[3 * row + 1] = y1;
-      y[3 * row + 2] = y2;
-    }
+  const int lane = threadIdx.x & 31, i = lane / 3, r = lane - 3 * i;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int g = warp; g * kRowsPerWarp < nnode; g += nw) {
+    const int node = g * kRowsPerWarp + i;
+    if (lane < 3 * kRowsPerWarp && node < nnode)
+      y[3 * node + r] = spmv_lane_row(rp, col, val, x, node, r);
   }
 }
 
@@ -109,14 +88,13 @@ __global__ void __launch_bounds__(NT) k_cg_spmv_pq(int nnode, const int32_t *__r
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int nw = (gridDim.x * blockDim.x) >> 5;
   double acc = 0.0;
-  for (int row = warp; row < nnode; row += nw) {
-    double y0, y1, y2;
-    spmv_row(rp, col, val, p, row, lane, y0, y1, y2);
-    if (lane == 0) {
-      q[3 * row] = y0;
-      q[3 * row + 1] = y1;
-      q[3 * row + 2] = y2;
-      acc += p[3 * row] * y0 + p[3 * row + 1] * y1 + p[3 * row + 2] * y2;
+  const int i = lane / 3, r = lane - 3 * i;
+  for (int g = warp; g * kRowsPerWarp < nnode; g += nw) {
+    const int node = g * kRowsPerWarp + i;
+    if (lane < 3 * kRowsPerWarp && node < nnode) {
+      const double yv = spmv_lane_row(rp, col, val, p, node, r);
+      q[3 * node + r] = yv;
+      acc = fma(p[3 * node + r], yv, acc);
     }
   }
   double s = block_sum<NT>(acc, sh);

@@ -55,6 +55,7 @@ struct Precond {
   int eig_cycles = 0;
   double eig_tol = 1e-8;          // Ritz residual <= eig_tol * theta (bounds the eigenvalue error)
   double *Vt = nullptr;           // restart scratch [nsub][npad][kkeep]
+  int *gate = nullptr;            // per subdomain: second re-orthogonalisation pass needed
   double *V = nullptr;            // Lanczos basis [nsub][npad_neu][kdim + p] row-major
   double *W = nullptr;            // [nsub][npad_neu][p]
   double *T1 = nullptr;           // work block [nsub][npad_neu][p]

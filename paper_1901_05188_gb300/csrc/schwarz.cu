@@ -277,6 +277,194 @@ __device__ void cluster_sweep(const cg::cluster_group &cluster, const T *__restr
   }
 }
 
+// Look-ahead sweep.  Warps 4..15 multiply the far tiles (distance >= 2) of row
+// I+1, which need only rows <= I-1, while warps 0..3 finish row I: they reduce
+// and exchange the far partials of row I (computed in the previous step),
+// arrive at the cluster barrier, multiply the coupling tile L(I, I-1) (every
+// CTA redundantly), wait, and apply the inverted diagonal block.  One split
+// cluster barrier and one block barrier per row; the chain overlaps the far
+// work.  Far tiles d = 2 + c + tC belong to CTA c.
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+template <typename T, int C>
+__device__ void cluster_sweep_la(const cg::cluster_group &cluster, const T *__restrict__ pool,
+                                 const BandLayout &L, T *y, T *red, T *chn, T *part,
+                                 bool backward) {
+  constexpr int kFar = kClWarps - kChain;
+  constexpr int B = sizeof(T) == 8 ? 2 : 4;
+  constexpr int kLinesPerUnit = 8 * 32 * (int)sizeof(T) / 128;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = (int)cluster.block_rank();
+  const int nt = L.nt, w = L.w;
+  auto row = [&](int q) { return backward ? nt - 1 - q : q; };
+  auto dmax = [&](int I) { return backward ? min(w, nt - 1 - I) : min(w, I); };
+  auto ycol = [&](int I, int d) { return backward ? I + d : I - d; };
+  // far units of row I for this CTA: d = 2 + c + t*C, 4 column groups per tile
+  auto nfar = [&](int I) {
+    const int dm = dmax(I), d0 = 2 + c;
+    return dm >= d0 ? ((dm - d0) / C + 1) * kGroups : 0;
+  };
+  int buf = 0;
+  T dv[8], nv[8];                                 // chain: this warp's 8 columns
+  if (warp < kChain && nt > 0) {
+    const T *D = tile_at(pool, L, row(0), 0) + warp * 256;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      dv[k] = __ldg(D + k * 32 + lane);
+      nv[k] = T(0);                               // row 0 has no coupling
+    }
+  }
+  for (int q = 0; q < nt; ++q) {
+    const int I = row(q);
+    const int par = q & 1;
+    if (warp >= kChain) {
+      const int cw = warp - kChain;
+      cluster_arrive();
+      T a0 = T(0), a1 = T(0);
+      if (q + 1 < nt) {
+        const int In = row(q + 1), nu = nfar(In);
+        if (q + 2 < nt) {                         // L2 prefetch of the next step's units
+          const int I2 = row(q + 2), nu2 = nfar(I2);
+          for (int u = cw; u < nu2; u += kFar)
+            if (lane < kLinesPerUnit)
+              prefetch_l2(tile_at(pool, L, I2, 2 + c + (u / kGroups) * C) + (u % kGroups) * 256 +
+                          lane * (128 / sizeof(T)));
+        }
+        for (int u0 = cw; u0 < nu; u0 += B * kFar) {
+          T v[B][8];
+#pragma unroll
+          for (int b = 0; b < B; ++b) {
+            const int u = u0 + b * kFar;
+            if (u < nu) {
+              const T *t = tile_at(pool, L, In, 2 + c + (u / kGroups) * C) + (u % kGroups) * 256;
+#pragma unroll
+              for (int e = 0; e < 8; ++e) v[b][e] = __ldg(t + e * 32 + lane);
+            }
+          }
+#pragma unroll
+          for (int b = 0; b < B; ++b) {
+            const int u = u0 + b * kFar;
+            if (u < nu) {
+              const int d = 2 + c + (u / kGroups) * C;
+              const T *yJ = y + ycol(In, d) * 32 + (u % kGroups) * 8;
+#pragma unroll
+              for (int e = 0; e < 8; e += 2) {
+                a0 += v[b][e] * yJ[e];
+                a1 += v[b][e + 1] * yJ[e + 1];
+              }
+            }
+          }
+        }
+      }
+      red[(par ^ 1) * kFar * 32 + cw * 32 + lane] = a0 + a1;
+      cluster_wait();
+    } else {
+      // far partials of row I: CTA sum, pushed to every CTA of the cluster
+      if (q > 0) {
+        T sp = T(0);
+#pragma unroll
+        for (int k = warp; k < kFar; k += kChain) sp += red[par * kFar * 32 + k * 32 + lane];
+        T *cb = chn + (buf & 1) * (kChain * 32);
+        cb[warp * 32 + lane] = sp;
+        chain_bar();
+        ++buf;
+        const T tot = ((cb[lane] + cb[32 + lane]) + cb[64 + lane]) + cb[96 + lane];
+        for (int dst = warp; dst < C; dst += kChain) {
+          T *pp = cluster.map_shared_rank(part, dst);
+          pp[(par * C + c) * 32 + lane] = tot;
+        }
+      }
+      cluster_arrive();
+      // coupling to the previous row, split by columns
+      T p0 = T(0), p1 = T(0);
+      if (q > 0) {
+        const T *yJ = y + ycol(I, 1) * 32 + warp * 8;
+#pragma unroll
+        for (int k = 0; k < 8; k += 2) {
+          p0 += nv[k] * yJ[k];
+          p1 += nv[k + 1] * yJ[k + 1];
+        }
+      }
+      T *cb = chn + (buf & 1) * (kChain * 32);
+      cb[warp * 32 + lane] = p0 + p1;
+      chain_bar();
+      ++buf;
+      T sv = y[I * 32 + lane] - (((cb[lane] + cb[32 + lane]) + cb[64 + lane]) + cb[96 + lane]);
+      cluster_wait();
+      if (q > 0) {
+#pragma unroll
+        for (int qq = 0; qq < C; ++qq) sv -= part[(par * C + qq) * 32 + lane];
+      }
+      T o0 = T(0), o1 = T(0);
+#pragma unroll
+      for (int k = 0; k < 8; k += 2) {
+        o0 += dv[k] * __shfl_sync(0xffffffffu, sv, warp * 8 + k);
+        o1 += dv[k + 1] * __shfl_sync(0xffffffffu, sv, warp * 8 + k + 1);
+      }
+      cb = chn + (buf & 1) * (kChain * 32);
+      cb[warp * 32 + lane] = o0 + o1;
+      chain_bar();
+      ++buf;
+      const T yI = ((cb[lane] + cb[32 + lane]) + cb[64 + lane]) + cb[96 + lane];
+      if (warp == 0) y[I * 32 + lane] = yI;
+      if (q + 1 < nt) {                           // next row's chain tiles, in flight over the barrier
+        const int In = row(q + 1);
+        const T *D = tile_at(pool, L, In, 0) + warp * 256;
+        const bool has1 = dmax(In) >= 1;
+        const T *N = tile_at(pool, L, In, has1 ? 1 : 0) + warp * 256;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          dv[k] = __ldg(D + k * 32 + lane);
+          nv[k] = has1 ? __ldg(N + k * 32 + lane) : T(0);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int C>
+__global__ void __launch_bounds__(kClWarps * 32)
+    k_schwarz_cluster_la(const SubDesc *subs, const BandLayout *lay, int nnx, int nny,
+                         const T *poolL, const T *poolU, const double *__restrict__ r,
+                         T *__restrict__ xloc, const CGScalars *cgs) {
+  if (cgs && cgs->done) return;           // the same for every CTA of the cluster
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *red = reinterpret_cast<T *>(smraw);  // [2][kClWarps - kChain][32]
+  T *chn = red + 2 * (kClWarps - kChain) * 32;   // [2][kChain][32]
+  T *part = chn + 2 * kChain * 32;        // [2][C][32]
+  T *y = part + 2 * C * 32;               // [npad]
+  const int j = blockIdx.x / C;
+  const SubDesc &S = subs[j];
+  const BandLayout L = lay[j];
+  const int n = S.n_int, npad = L.nt * 32;
+  for (int l = threadIdx.x; l < npad; l += blockDim.x) {
+    T v = T(0);
+    if (l < n) {
+      int node = l / 3, comp = l - 3 * node;
+      int gi, gj, gk;
+      S.ibox.global(node, gi, gj, gk);
+      v = T(r[3 * (gi + nnx * (gj + nny * gk)) + comp]);
+    }
+    y[l] = v;
+  }
+  cluster.sync();                          // every CTA's shared memory is live
+  cluster_sweep_la<T, C>(cluster, poolL, L, y, red, chn, part, false);
+  cluster.sync();                          // the partial buffers are reused by the second sweep
+  cluster_sweep_la<T, C>(cluster, poolU, L, y, red, chn, part, true);
+  if (cluster.block_rank() == 0) {
+    T *out = xloc + S.v_int;
+    for (int l = threadIdx.x; l < n; l += blockDim.x) out[l] = y[l];
+  }
+  cluster.sync();                          // no CTA leaves while others may still write to it
+}
+
 template <typename T, int C, int R>
 __global__ void __launch_bounds__(kClWarps * 32)
     k_schwarz_cluster(const SubDesc *subs, const BandLayout *lay, int nnx, int nny,
@@ -315,6 +503,7 @@ __global__ void __launch_bounds__(kClWarps * 32)
 
 template <typename T>
 int smem_bytes(int npad, int C, int R) {
+  if (R == 0) return ((2 * (kClWarps - kChain) + 2 * kChain + 2 * C) * 32 + npad) * (int)sizeof(T);
   return ((kClWarps + 2 * kChain + 2 * C) * R * 32 + npad) * (int)sizeof(T);
 }
 
@@ -334,8 +523,13 @@ int launch_cr(const SubDesc *d_subs, const BandLayout *d_lay, int nsub, int npad
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_schwarz_cluster<T, C, R>, d_subs, d_lay, nnx, nny,
-                                    poolL, poolU, r, xloc, cgs));
+  if constexpr (R == 0) {
+    GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_schwarz_cluster_la<T, C>, d_subs, d_lay, nnx, nny,
+                                      poolL, poolU, r, xloc, cgs));
+  } else {
+    GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_schwarz_cluster<T, C, R>, d_subs, d_lay, nnx, nny,
+                                      poolL, poolU, r, xloc, cgs));
+  }
   GENEO_COUNT_LAUNCH();
   return GENEO_OK;
 }
@@ -345,6 +539,7 @@ int launch_c(int rows, const SubDesc *d_subs, const BandLayout *d_lay, int nsub,
              int nnx, int nny, const T *poolL, const T *poolU, const double *r, T *xloc,
              const CGScalars *cgs, cudaStream_t s) {
   switch (rows) {
+    case 0: return launch_cr<T, C, 0>(d_subs, d_lay, nsub, npad_max, nnx, nny, poolL, poolU, r, xloc, cgs, s);
     case 4: return launch_cr<T, C, 4>(d_subs, d_lay, nsub, npad_max, nnx, nny, poolL, poolU, r, xloc, cgs, s);
     case 2: return launch_cr<T, C, 2>(d_subs, d_lay, nsub, npad_max, nnx, nny, poolL, poolU, r, xloc, cgs, s);
     default: return launch_cr<T, C, 1>(d_subs, d_lay, nsub, npad_max, nnx, nny, poolL, poolU, r, xloc, cgs, s);
@@ -356,6 +551,7 @@ int prepare_c(int npad_max) {
   int st;
   if ((st = ensure_smem(k_schwarz_cluster<T, C, 1>, smem_bytes<T>(npad_max, C, 1)))) return st;
   if ((st = ensure_smem(k_schwarz_cluster<T, C, 2>, smem_bytes<T>(npad_max, C, 2)))) return st;
+  if ((st = ensure_smem(k_schwarz_cluster_la<T, C>, smem_bytes<T>(npad_max, C, 0)))) return st;
   return ensure_smem(k_schwarz_cluster<T, C, 4>, smem_bytes<T>(npad_max, C, 4));
 }
 

@@ -1,0 +1,88 @@
+"""Every launch shape of the Schwarz local solves against the oracle.
+
+The set-up autotuner picks one of the launch shapes by timing; each must give
+the one-level additive Schwarz application of the oracle (Sec. 3.1), so each
+is pinned here through GENEO_SCHWARZ_CLUSTER / GENEO_SCHWARZ_ROWS (rows 0 is
+the look-ahead sweep), and compared with the oracle and with the reference
+shape (one CTA per subdomain, one row per barrier); repeated applications
+must be bit-identical (no race between the warps or CTAs of a sweep).
+
+FP64 factors: 1e-9 relative to the oracle, 1e-12 to the reference shape, and
+the same iteration count within 1.  FP32 factors: the local matrices of these
+layered blocks have condition numbers up to 4e5, so an FP32 solve may lose up
+to kappa * 2^-24 ~ 2e-2 relative (LAPACK's FP32 Cholesky loses 7e-5 on this
+data, the tile factor with explicitly inverted diagonal blocks 8e-4 for every
+shape); the shapes then differ only by rounding, measured at 2e-7, bounded
+here by 1e-5.  Iteration counts are not compared across FP32 shapes: without
+a coarse space, flexible CG with an FP32 preconditioner is sensitive to the
+rounding pattern (measured 67-79 iterations on the 12x8x6 block, 85-114 on
+the 8x8x8 block, against 64 and 78 in FP64); only convergence is required,
+within 1.6x the FP64 count.
+"""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import decomp, fem, krylov
+
+from gpu_common import rel, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    return require_gpu()
+
+
+_REF = {}
+
+
+def _reference(pkg, monkeypatch, name, prec, r):
+    """(iterations, M^-1 r) of the reference launch shape (C = 1, R = 1)."""
+    key = (name, prec)
+    if key not in _REF:
+        with monkeypatch.context() as m:
+            m.setenv("GENEO_SCHWARZ_CLUSTER", "1")
+            m.setenv("GENEO_SCHWARZ_ROWS", "1")
+            p = workloads.config(name)
+            s = pkg.GeneoSolver()
+            s.assemble(p)
+            s.setup(p, prec, pkg.GENEO_AS, pkg.GENEO_COARSE_NONE)
+            z = s.apply_preconditioner(r)
+            _REF[key] = (s.solve(tol=1e-8, max_it=3000)[1]["iterations"], z)
+            s.close()
+    return _REF[key]
+
+
+@pytest.mark.parametrize("name", ["small", "c1"])
+@pytest.mark.parametrize("cluster", [1, 2, 4])
+@pytest.mark.parametrize("rows", [0, 1, 2, 4])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_schwarz_launch_shapes(pkg, monkeypatch, name, cluster, rows, prec):
+    if prec == 0 and rows == 4:
+        pytest.skip("four rows per barrier are offered for FP32 factors only")
+    p = workloads.config(name)
+    A, _ = fem.assemble_system(p)
+    M = krylov.OneLevelAS(A, decomp.partition(p))
+    r = np.random.default_rng(5).normal(size=A.shape[0])
+    r[p["dirichlet_dofs"]] = 0.0
+    it64, _ = _reference(pkg, monkeypatch, name, 0, r)
+    itref, zref = _reference(pkg, monkeypatch, name, prec, r)
+    monkeypatch.setenv("GENEO_SCHWARZ_CLUSTER", str(cluster))
+    monkeypatch.setenv("GENEO_SCHWARZ_ROWS", str(rows))
+    s = pkg.GeneoSolver()
+    s.assemble(p)
+    s.setup(p, prec, pkg.GENEO_AS, pkg.GENEO_COARSE_NONE)
+    z = s.apply_preconditioner(r)
+    assert np.array_equal(z, s.apply_preconditioner(r))
+    assert rel(z, M(r)) <= (1e-9 if prec == 0 else 5e-3)
+    assert rel(z, zref) <= (1e-12 if prec == 0 else 1e-5)
+    u, st = s.solve(tol=1e-8, max_it=3000)
+    assert (st["schwarz_cluster"], st["schwarz_rows"]) == (cluster, rows)
+    assert st["rel_res_true"] <= 2e-8
+    if prec == 0:
+        assert abs(st["iterations"] - it64) <= 1
+    else:
+        assert st["iterations"] <= 1.6 * it64
+    s.close()
