@@ -360,8 +360,7 @@ def run_ours(args):
     cand.append((ms_k * n_schwarz, hbm))
     if st["n_coarse"] > 0:
         ms_l, by_l, fl_l = pkg.geneo_profile(s.ctx, 3, 5)
-        ksteps, kkeep = 16, 64
-        n_lanczos = 2 * (ksteps + (st["eig_cycles"] - 1) * (ksteps - kkeep // 8)) + 1
+        n_lanczos = 2 * st["lanczos_steps"] + 1   # two sweeps per block step + the Ritz vectors
         alu = dict(bound="alu", kernel="k_band_solve_dense (GenEO shift-invert band solves, FP64, "
                                        "8 right-hand sides)",
                    achieved=fl_l / (ms_l * 1e-3) / 1e12, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",

@@ -122,6 +122,7 @@ typedef struct {
   int failed_subdomain;           /* subdomain of a GENEO_ERR_NOT_SPD, else -1 */
   int flexible;                   /* 1 if flexible CG was used */
   int eig_cycles;                 /* block-Lanczos restart cycles of the last set-up */
+  int lanczos_steps;              /* block-Lanczos steps of the last set-up (two band sweeps each) */
   int schwarz_cluster;            /* CTAs per subdomain chosen for the local solves */
   int schwarz_rows;               /* tile rows per cluster barrier chosen for them */
 } geneo_stats;

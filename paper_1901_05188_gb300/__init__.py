@@ -63,6 +63,7 @@ class geneo_stats(C.Structure):
                 ("ms_solve", C.c_float), ("bytes_per_iter", C.c_double),
                 ("eig_max_residual", C.c_double), ("failed_subdomain", C.c_int),
                 ("flexible", C.c_int), ("eig_cycles", C.c_int),
+                ("lanczos_steps", C.c_int),
                 ("schwarz_cluster", C.c_int), ("schwarz_rows", C.c_int)]
 
     def as_dict(self):

@@ -503,6 +503,23 @@ int build_plan(geneo_ctx *c, const geneo_partition *part, const geneo_modes *mod
     return fail(GENEO_ERR_INVALID_ARG, "bad mode options (modes <= 32, shift < 0)");
   int n[3] = {c->nx, c->ny, c->nz};
   int p[3] = {part->px, part->py, part->pz};
+  // block-Lanczos options: block steps per restart cycle (basis p * steps) and
+  // the Ritz residual tolerance relative to the Ritz value.  A residual of
+  // 1e-6 theta bounds the eigenvalue error by about (1e-6)^2 / gap and the
+  // angle of an eigenvector by 1e-6 / gap, far below what the coarse space
+  // needs; 12 steps reach it in two cycles on the laminate workloads.
+  // GENEO_LANCZOS_STEPS (8..16, the projected eigensolver holds up to 128
+  // columns) and GENEO_EIG_TOL (1e-12..1e-4) override the defaults.
+  c->pc.ksteps = 12;
+  c->pc.eig_tol = 1e-6;
+  if (const char *e = std::getenv("GENEO_LANCZOS_STEPS")) {
+    const int v = std::atoi(e);
+    if (v >= 8 && v <= 16) c->pc.ksteps = v;
+  }
+  if (const char *e = std::getenv("GENEO_EIG_TOL")) {
+    const double v = std::atof(e);
+    if (v >= 1e-12 && v <= 1e-4) c->pc.eig_tol = v;
+  }
   AxisPart ax[3];
   int st;
   for (int d = 0; d < 3; ++d)
@@ -774,6 +791,7 @@ static int setup_coarse_zem(geneo_ctx *c, SetupPlan &P, cudaStream_t s) {
   pc.lambdas.assign((size_t)nsub * mcap, INFINITY);
   pc.eig_max_res = 0.0;
   pc.eig_cycles = 0;
+  pc.lanczos_steps = 0;
   int coff = 0;
   long long zoff = 0, yoff = 0;
   std::vector<long long> yoffs(nsub);
@@ -839,7 +857,9 @@ static int setup_coarse(geneo_ctx *c, SetupPlan &P, cudaStream_t s) {
   std::vector<double> ev((size_t)nsub * kdim), er((size_t)nsub * kdim);
   int first_block = 0;
   pc.eig_cycles = 0;
+  pc.lanczos_steps = 0;
   for (int cycle = 0; cycle < pc.max_cycles; ++cycle) {
+    pc.lanczos_steps += pc.ksteps - first_block;
     for (int k = first_block; k < pc.ksteps; ++k) {
       // W = L^-1 B L^-T V_k
       if ((st = launch_band_solve_dense(pc.d_lay_neu, nsub, npad, pc.neuL, pc.neuU, pc.V + k * p,
@@ -1513,6 +1533,7 @@ extern "C" int geneo_solve(geneo_ctx *c, double tol, int max_it, double *u, gene
   out.failed_subdomain = -1;
   out.flexible = flexible ? 1 : 0;
   out.eig_cycles = pc.eig_cycles;
+  out.lanczos_steps = pc.lanczos_steps;
   out.schwarz_cluster = pc.cluster;
   out.schwarz_rows = pc.rows;
   if (!flexible && h.it > 0) {

@@ -48,12 +48,13 @@ struct Precond {
   double *neuL = nullptr, *neuU = nullptr;   // factor of S = A - sigma B
   double *Bloc = nullptr;         // 27-slot local BSR of B (9 doubles per block)
   double *Xneu = nullptr;         // PoU on Neumann dofs
-  int ksteps = 16;                // Lanczos block steps per cycle (basis size kdim = p * ksteps)
+  int ksteps = 12;                // Lanczos block steps per cycle (basis size kdim = p * ksteps)
   int kdim = 0;                   // p * ksteps
   int kkeep = 0;                  // Ritz vectors kept at a thick restart
   int max_cycles = 12;            // restart cycles
+  int lanczos_steps = 0;          // block steps of the last eigensolve (two band sweeps each)
   int eig_cycles = 0;
-  double eig_tol = 1e-8;          // Ritz residual <= eig_tol * theta (bounds the eigenvalue error)
+  double eig_tol = 1e-6;          // Ritz residual <= eig_tol * theta (bounds the eigenvalue error)
   double *Vt = nullptr;           // restart scratch [nsub][npad][kkeep]
   int *gate = nullptr;            // per subdomain: second re-orthogonalisation pass needed
   double *V = nullptr;            // Lanczos basis [nsub][npad_neu][kdim + p] row-major
