@@ -190,6 +190,16 @@ int geneo_assemble(geneo_ctx *ctx, const geneo_mesh *mesh, int n_mat,
  * solves with the new b.  Errors: GENEO_ERR_STATE before geneo_assemble. */
 int geneo_set_load(geneo_ctx *ctx, const double *nodal_load, double top_pressure);
 
+/* Stress recovery (Sec. 2 constitutive law; the stresses the paper derives
+ * from the displacements for its failure analysis, Sec. 5): for every element
+ * sigma = C_e B(centre) u_e, the rotated ply stiffness times the strain of the
+ * trilinear element at its centre (its element-average strain).
+ *   u     : 3*n_nodes doubles (host or device), e.g. from geneo_solve
+ *   sigma : 6*n_elements doubles (host or device), element e at 6e, Voigt
+ *           order (xx, yy, zz, yz, xz, xy), element e = ex + nx*(ey + ny*ez)
+ * Errors: GENEO_ERR_STATE before geneo_assemble. */
+int geneo_element_stress(geneo_ctx *ctx, const double *u, double *sigma);
+
 /* Sizes of the assembled system: nodes and stored 3x3 blocks. */
 int geneo_system_info(geneo_ctx *ctx, int *n_nodes, int *nnz_blocks);
 

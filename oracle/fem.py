@@ -202,3 +202,26 @@ def assemble_system(p):
     A = assemble_stiffness(p)
     b = top_pressure_load(p)
     return apply_dirichlet(A, b, p["dirichlet_dofs"], p["dirichlet_values"])
+
+
+def element_stresses(p, u):
+    """Stress recovery: sigma_e = C_e B(centroid) u_e at every element (nel, 6).
+
+    Voigt order (xx, yy, zz, yz, xz, xy); C_e is the rotated ply stiffness of
+    the element (Sec. 2 constitutive law), B the strain-displacement matrix of
+    the trilinear element at its centre (engineering shear strains).  The
+    paper recovers stresses from the displacement solution for its failure
+    analysis (Sec. 5); the centroid is the one point where the Q1 strain of a
+    box element is the element average.
+    """
+    Cv = element_voigt_all(p)
+    ex, ey, ez = element_coords(p)
+    x, y, z = np.asarray(p["x"]), np.asarray(p["y"]), np.asarray(p["z"])
+    g0 = shape_grad_ref(0.0, 0.0, 0.0)
+    out = np.zeros((ex.size, 6))
+    for e in range(ex.size):
+        h = np.array([x[ex[e] + 1] - x[ex[e]], y[ey[e] + 1] - y[ey[e]], z[ez[e] + 1] - z[ez[e]]])
+        B = strain_displacement(g0 * (2.0 / h))
+        eps = B @ u[element_dofs(p["nx"], p["ny"], ex[e], ey[e], ez[e])]
+        out[e] = Cv[e] @ eps
+    return out

@@ -93,6 +93,7 @@ _SIGS = {
     "geneo_assemble": [_P, C.POINTER(geneo_mesh), C.c_int, _P, _P, _P, _P,
                        C.POINTER(geneo_dirichlet), _P, C.c_double],
     "geneo_set_load": [_P, _P, C.c_double],
+    "geneo_element_stress": [_P, _P, _P],
     "geneo_system_info": [_P, C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "geneo_get_system": [_P, _P, _P, _P, _P],
     "geneo_spmv": [_P, _P, _P],
@@ -207,6 +208,10 @@ def geneo_assemble(ctx, mesh, mats, elem_mat, elem_theta, elem_phi, dirichlet, n
 
 def geneo_set_load(ctx, nodal_load, top_pressure):
     _check(load().geneo_set_load(ctx, _ptr(nodal_load), float(top_pressure)))
+
+
+def geneo_element_stress(ctx, u, sigma):
+    _check(load().geneo_element_stress(ctx, _ptr(u), _ptr(sigma)))
 
 
 def geneo_system_info(ctx):
@@ -335,6 +340,7 @@ class GeneoSolver:
         geneo_assemble(self.ctx, mesh, mats, emat, th, ph, dirichlet, nl, p["top_pressure"])
         self.nnode, self.nnzb = geneo_system_info(self.ctx)
         self.ndof = 3 * self.nnode
+        self.nx, self.ny, self.nz = int(p["nx"]), int(p["ny"]), int(p["nz"])
 
     def set_load(self, nodal_load=None, top_pressure=0.0):
         """New load on the resident system (matrix and preconditioner unchanged)."""
@@ -347,6 +353,21 @@ class GeneoSolver:
             if not isinstance(nodal_load, np.ndarray) and nodal_load.dtype != self.torch.float64:
                 raise TypeError("nodal_load must be float64")
         geneo_set_load(self.ctx, nodal_load, top_pressure)
+
+    def element_stress(self, u):
+        """Stresses at the element centres, (n_elements, 6) in Voigt order."""
+        nel = self.nx * self.ny * self.nz
+        if isinstance(u, np.ndarray):
+            u = np.ascontiguousarray(u, dtype=np.float64)
+            n = u.size
+            out = np.zeros((nel, 6))
+        else:
+            n = u.numel()
+            out = self.torch.empty((nel, 6), dtype=self.torch.float64, device=u.device)
+        if n != self.ndof:
+            raise ValueError(f"u has {n} entries, the system {self.ndof}")
+        geneo_element_stress(self.ctx, u, out)
+        return out
 
     @staticmethod
     def partition_of(p):

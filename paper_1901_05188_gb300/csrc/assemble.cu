@@ -245,6 +245,48 @@ int launch_assembly(const AssemblyArgs &a, cudaStream_t s) {
   return GENEO_OK;
 }
 
+// Stress recovery at the element centres: sigma_e = C_e B(0) u_e (Voigt order
+// 11, 22, 33, 23, 13, 12; engineering shear strains).  At the centre of a box
+// element dN_a/dx_d = s_d / (4 h_d) with the corner sign s_d = +-1.
+__global__ void k_element_stress(int nx, int ny, int nz, const double *__restrict__ X,
+                                 const double *__restrict__ Y, const double *__restrict__ Z,
+                                 const double *__restrict__ Cel, const double *__restrict__ u,
+                                 double *__restrict__ sig) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nx * ny * nz) return;
+  const int ex = e % nx, ey = (e / nx) % ny, ez = e / (nx * ny);
+  const int nnx = nx + 1, nny = ny + 1;
+  const double ih[3] = {0.25 / (X[ex + 1] - X[ex]), 0.25 / (Y[ey + 1] - Y[ey]),
+                        0.25 / (Z[ez + 1] - Z[ez])};
+  double du[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};   // du_i / dx_d
+  for (int a = 0; a < 8; ++a) {
+    const int ia = a & 1, ja = (a >> 1) & 1, ka = (a >> 2) & 1;
+    const long long n = (ex + ia) + (long long)nnx * ((ey + ja) + (long long)nny * (ez + ka));
+    const double g[3] = {(2 * ia - 1) * ih[0], (2 * ja - 1) * ih[1], (2 * ka - 1) * ih[2]};
+    for (int i = 0; i < 3; ++i) {
+      const double ui = u[3 * n + i];
+      for (int d = 0; d < 3; ++d) du[i][d] += g[d] * ui;
+    }
+  }
+  const double eps[6] = {du[0][0], du[1][1], du[2][2], du[1][2] + du[2][1], du[0][2] + du[2][0],
+                         du[0][1] + du[1][0]};
+  const double *C = Cel + 36 * (size_t)e;
+  for (int r = 0; r < 6; ++r) {
+    double s = 0.0;
+    for (int c = 0; c < 6; ++c) s += C[6 * r + c] * eps[c];
+    sig[6 * (size_t)e + r] = s;
+  }
+}
+
+int launch_element_stress(int nx, int ny, int nz, const double *X, const double *Y,
+                          const double *Z, const double *Cel, const double *u, double *sig,
+                          cudaStream_t s) {
+  const int nel = nx * ny * nz, T = 256;
+  k_element_stress<<<(nel + T - 1) / T, T, 0, s>>>(nx, ny, nz, X, Y, Z, Cel, u, sig); GENEO_COUNT_LAUNCH();
+  GENEO_CUDA_TRY(cudaGetLastError());
+  return GENEO_OK;
+}
+
 int launch_load(const AssemblyArgs &a, cudaStream_t s) {
   const int T = 256;
   int nnode = (a.nx + 1) * (a.ny + 1) * (a.nz + 1);

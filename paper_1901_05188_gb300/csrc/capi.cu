@@ -130,6 +130,7 @@ void plan_assemble(Arena &A, geneo_ctx *c, int nx, int ny, int nz, int n_mat, in
   c->b = A.take<double>(3 * (size_t)nnode);
   c->g = A.take<double>(3 * (size_t)nnode);
   c->lift = A.take<double>(3 * (size_t)nnode);
+  c->sig = A.take<double>(6 * (size_t)nel);
   c->mask = A.take<uint8_t>(3 * (size_t)nnode);
   c->status = A.take<DevStatus>(1);
   c->mats = A.take<geneo_ortho>(std::max(n_mat, 1));
@@ -431,6 +432,24 @@ int geneo_set_load(geneo_ctx *c, const double *nodal_load, double top_pressure) 
   a.lift = c->lift;
   a.mask = c->mask;
   if ((st = launch_load(a, s))) return st;
+  return GENEO_OK;
+}
+
+int geneo_element_stress(geneo_ctx *c, const double *u, double *sigma) {
+  if (!c || !c->assembled) return fail(GENEO_ERR_STATE, "not assembled");
+  if (!u || !sigma) return fail(GENEO_ERR_INVALID_ARG, "null vector");
+  cudaStream_t s = c->stream;
+  int st;
+  // u is staged into the phase-0 scratch vector g (needed only during assembly)
+  const double *du = u;
+  if (!is_device_ptr(u)) {
+    if ((st = stage(c->g, u, c->ndof, s))) return st;
+    du = c->g;
+  }
+  double *ds = is_device_ptr(sigma) ? sigma : c->sig;
+  if ((st = launch_element_stress(c->nx, c->ny, c->nz, c->X, c->Y, c->Z, c->Cel, du, ds, s))) return st;
+  if (ds != sigma) return unstage(sigma, ds, 6 * (size_t)c->nel, s);
+  GENEO_CUDA_TRY(cudaStreamSynchronize(s));
   return GENEO_OK;
 }
 

@@ -30,6 +30,7 @@ struct geneo_ctx {
   int32_t *row_ptr = nullptr, *col = nullptr, *cnt = nullptr;
   double *val = nullptr, *b = nullptr, *g = nullptr;
   double *lift = nullptr;                  // Dirichlet lifting (kept for new loads)
+  double *sig = nullptr;                   // element stresses (6 per element), output staging
   int n_dir = 0;
   uint8_t *mask = nullptr;
   geneo::DevStatus *status = nullptr;

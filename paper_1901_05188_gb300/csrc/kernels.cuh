@@ -25,6 +25,10 @@ struct AssemblyArgs {
 int launch_assembly(const AssemblyArgs &a, cudaStream_t s);
 // Right-hand side only (load kernel + stored lifting): b = mask ? lift : f + lift.
 int launch_load(const AssemblyArgs &a, cudaStream_t s);
+// Element stresses at the centres (6 per element, Voigt order) from u.
+int launch_element_stress(int nx, int ny, int nz, const double *X, const double *Y,
+                          const double *Z, const double *Cel, const double *u, double *sig,
+                          cudaStream_t s);
 
 // Scalars of one (F)PCG solve, resident on the device.
 struct CGScalars {
