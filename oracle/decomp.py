@@ -57,8 +57,13 @@ def _box_elems(p, lo, hi):
     return np.sort((I + nx * (J + ny * K)).reshape(-1))
 
 
-def dofs_of(nodes):
-    return (3 * nodes[:, None] + np.arange(3)[None, :]).reshape(-1)
+def ncomp(p):
+    """Unknowns per node: 1 for the scalar Darcy problem, 3 for elasticity."""
+    return 1 if p.get("kind") == "darcy" else 3
+
+
+def dofs_of(nodes, nc=3):
+    return (nc * nodes[:, None] + np.arange(nc)[None, :]).reshape(-1)
 
 
 def partition(p):
@@ -82,8 +87,8 @@ def partition(p):
                 s = Subdomain(index=len(subs), owned=owned, ebox=ebox,
                               elems=_box_elems(p, elo, ehi),
                               neu_nodes=neu, int_nodes=intn)
-                s.neu_dofs = dofs_of(neu)
-                s.int_dofs = dofs_of(intn)
+                s.neu_dofs = dofs_of(neu, ncomp(p))
+                s.int_dofs = dofs_of(intn, ncomp(p))
                 subs.append(s)
     _pou(p, subs)
     _overlap(p, subs)
@@ -92,7 +97,7 @@ def partition(p):
 
 def _pou(p, subs):
     """Standard PoU (Sec. 3.3.1): 1/multiplicity on V_{h,0}(Omega_j) dofs."""
-    ndof = 3 * (p["nx"] + 1) * (p["ny"] + 1) * (p["nz"] + 1)
+    ndof = ncomp(p) * (p["nx"] + 1) * (p["ny"] + 1) * (p["nz"] + 1)
     mult = np.zeros(ndof)
     for s in subs:
         mult[s.int_dofs] += 1.0
@@ -118,7 +123,7 @@ def _overlap(p, subs):
 
 def pou_sum(p, subs):
     """sum_j R_j^T X_j R_j 1 (Def. Partition of Unity, applied to v = 1)."""
-    ndof = 3 * (p["nx"] + 1) * (p["ny"] + 1) * (p["nz"] + 1)
+    ndof = ncomp(p) * (p["nx"] + 1) * (p["ny"] + 1) * (p["nz"] + 1)
     v = np.zeros(ndof)
     for s in subs:
         v[s.neu_dofs] += s.X

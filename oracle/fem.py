@@ -198,7 +198,11 @@ def apply_dirichlet(A, b, dofs, values, diag=1.0):
 
 
 def assemble_system(p):
-    """Global A (CSR, Dirichlet eliminated) and load b (eqn:fe_matrix_system)."""
+    """Global A (CSR, Dirichlet eliminated) and load b (eqn:fe_matrix_system);
+    the scalar Darcy problem (eq-fe-darcy) when p["kind"] == "darcy"."""
+    if p.get("kind") == "darcy":
+        from . import darcy
+        return darcy.assemble_system(p)
     A = assemble_stiffness(p)
     b = top_pressure_load(p)
     return apply_dirichlet(A, b, p["dirichlet_dofs"], p["dirichlet_values"])

@@ -31,7 +31,7 @@ import scipy.linalg as sla
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from . import fem
+from . import decomp, fem
 
 DENSE_LIMIT = 3000
 INF_MU_RTOL = 1e-12    # mu below this times 1/|sigma| means lambda = infinity
@@ -51,12 +51,18 @@ def local_matrices(p, s):
     """
     nm = local_node_map(p, s.neu_nodes)
     nloc = s.neu_nodes.size
-    A = fem.assemble_stiffness(p, s.elems, nm, nloc)
-    if s.ovl_elems.size:
-        Ao = fem.assemble_stiffness(p, s.ovl_elems, nm, nloc)
+    nc = decomp.ncomp(p)
+    if nc == 1:
+        from . import darcy
+        assemble = darcy.assemble_matrix
     else:
-        Ao = sp.csr_matrix((3 * nloc, 3 * nloc))
-    dmask = np.zeros(3 * ((p["nx"] + 1) * (p["ny"] + 1) * (p["nz"] + 1)), bool)
+        assemble = fem.assemble_stiffness
+    A = assemble(p, s.elems, nm, nloc)
+    if s.ovl_elems.size:
+        Ao = assemble(p, s.ovl_elems, nm, nloc)
+    else:
+        Ao = sp.csr_matrix((nc * nloc, nc * nloc))
+    dmask = np.zeros(nc * ((p["nx"] + 1) * (p["ny"] + 1) * (p["nz"] + 1)), bool)
     dmask[np.asarray(p["dirichlet_dofs"], np.int64)] = True
     ld = np.nonzero(dmask[s.neu_dofs])[0]
     zeros = np.zeros(ld.size)
@@ -209,11 +215,15 @@ def zem_space(p, subs, A):
     dmask = np.zeros(ndof, bool)
     dmask[np.asarray(p["dirichlet_dofs"], np.int64)] = True
     cols, info = [], []
+    nc = decomp.ncomp(p)
     for s in subs:
         floating = not dmask[s.neu_dofs].any()
-        m = 6 if floating else 0
+        m = (6 if nc == 3 else 1) if floating else 0
         if m:
-            R = rigid_body_modes(p, s.neu_nodes)
+            # the kernel of the Neumann problem: rigid displacements, or the
+            # constants for the scalar problem
+            R = (rigid_body_modes(p, s.neu_nodes) if nc == 3
+                 else np.full((s.neu_nodes.size, 1), 1.0 / np.sqrt(s.neu_nodes.size)))
             for k in range(m):
                 phi = np.zeros(ndof)
                 phi[s.neu_dofs] = s.X * R[:, k]
