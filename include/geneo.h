@@ -151,10 +151,14 @@ int geneo_setup_workspace_bytes(geneo_ctx *ctx, const geneo_partition *part,
 
 /* Host-only estimate of both workspaces (assemble, setup + solve) for a
  * problem that has not been assembled yet; used to admit requests by device
- * memory.  Either output may be NULL.  Touches no device state. */
-int geneo_estimate_workspace_bytes(const geneo_mesh *mesh, const geneo_partition *part,
-                                   const geneo_modes *modes, geneo_precision prec,
-                                   size_t *assemble_bytes, size_t *setup_bytes);
+ * memory.  unknowns_per_node: 3 for elasticity (geneo_assemble), 1 for the
+ * Darcy problem (geneo_assemble_darcy); the assemble figure is the
+ * elasticity one, an upper bound for Darcy.  Either output may be NULL.
+ * Touches no device state. */
+int geneo_estimate_workspace_bytes(const geneo_mesh *mesh, int unknowns_per_node,
+                                   const geneo_partition *part, const geneo_modes *modes,
+                                   geneo_precision prec, size_t *assemble_bytes,
+                                   size_t *setup_bytes);
 
 /* Bind caller-owned device memory (e.g. allocated by PyTorch) as the
  * workspace of phase 0 (assemble) or phase 1 (setup + solve).  It must stay
@@ -180,6 +184,22 @@ int geneo_assemble(geneo_ctx *ctx, const geneo_mesh *mesh, int n_mat,
                    const double *elem_theta, const double *elem_phi,
                    const geneo_dirichlet *dirichlet, const double *nodal_load,
                    double top_pressure);
+
+/* Assemble the scalar Darcy problem of the paper's subsurface application
+ * (the section on the SPE10 benchmark, eqn:Darcy and eq-fe-darcy):
+ * -div(K grad u) = f with K = diag(Kx, Ky, Kz) constant per element, Q1
+ * elements with 2x2x2 Gauss integration, one unknown per node (dof = node),
+ * 1x1 blocks in the same 27-point BSR pattern, symmetric elimination of the
+ * Dirichlet set.  Everything after it -- geneo_setup (GenEO, ZEM or none,
+ * FP64 or mixed), geneo_solve, geneo_set_load (its scalar is the source f) --
+ * works on this system as on the elasticity one; geneo_element_stress does not.
+ *   perm      : 3*n_elements doubles (Kx, Ky, Kz) per element (host or device)
+ *   dirichlet : node ids and values (e.g. the face z = 0 with u = 0)
+ *   nodal_load: n_nodes doubles added to the right-hand side, may be NULL
+ *   source    : uniform f, applied as int f N_a dx */
+int geneo_assemble_darcy(geneo_ctx *ctx, const geneo_mesh *mesh, const double *perm,
+                         const geneo_dirichlet *dirichlet, const double *nodal_load,
+                         double source);
 
 /* Replace the load of the assembled system (Sec. 2, the right-hand side of
  * eqn:fe_matrix_system) without touching the matrix, the preconditioner or

@@ -87,9 +87,11 @@ _SIGS = {
     "geneo_setup_workspace_bytes": [_P, C.POINTER(geneo_partition), C.POINTER(geneo_modes),
                                     C.c_int, C.POINTER(C.c_size_t)],
     "geneo_bind_workspace": [_P, C.c_int, _P, C.c_size_t],
-    "geneo_estimate_workspace_bytes": [C.POINTER(geneo_mesh), C.POINTER(geneo_partition),
+    "geneo_estimate_workspace_bytes": [C.POINTER(geneo_mesh), C.c_int, C.POINTER(geneo_partition),
                                        C.POINTER(geneo_modes), C.c_int, C.POINTER(C.c_size_t),
                                        C.POINTER(C.c_size_t)],
+    "geneo_assemble_darcy": [_P, C.POINTER(geneo_mesh), _P, C.POINTER(geneo_dirichlet), _P,
+                             C.c_double],
     "geneo_assemble": [_P, C.POINTER(geneo_mesh), C.c_int, _P, _P, _P, _P,
                        C.POINTER(geneo_dirichlet), _P, C.c_double],
     "geneo_set_load": [_P, _P, C.c_double],
@@ -188,11 +190,17 @@ def geneo_setup_workspace_bytes(ctx, part, modes, prec):
     return n.value
 
 
-def geneo_estimate_workspace_bytes(mesh, part, modes, prec):
+def geneo_estimate_workspace_bytes(mesh, part, modes, prec, unknowns_per_node=3):
     a, s = C.c_size_t(), C.c_size_t()
-    _check(load().geneo_estimate_workspace_bytes(C.byref(mesh), C.byref(part), C.byref(modes),
-                                                 prec, C.byref(a), C.byref(s)))
+    _check(load().geneo_estimate_workspace_bytes(C.byref(mesh), int(unknowns_per_node),
+                                                 C.byref(part), C.byref(modes), prec,
+                                                 C.byref(a), C.byref(s)))
     return a.value, s.value
+
+
+def geneo_assemble_darcy(ctx, mesh, perm, dirichlet, nodal_load, source):
+    _check(load().geneo_assemble_darcy(ctx, C.byref(mesh), _ptr(perm), C.byref(dirichlet),
+                                       _ptr(nodal_load), float(source)))
 
 
 def geneo_bind_workspace(ctx, phase, ptr, nbytes):
@@ -320,10 +328,30 @@ class GeneoSolver:
         keep.extend(xs)
         return geneo_mesh(p["nx"], p["ny"], p["nz"], _ptr(xs[0]), _ptr(xs[1]), _ptr(xs[2]))
 
+    @staticmethod
+    def unknowns_per_node(p):
+        return 1 if p.get("kind") == "darcy" else 3
+
     def assemble(self, p):
+        """Assemble the elasticity system, or the Darcy one for p["kind"] == "darcy"."""
         keep = []
         mesh = self.mesh_of(p, keep)
         self._bind(0, geneo_assemble_workspace_bytes(mesh))
+        conv = lambda a, dt: (np.ascontiguousarray(a, dtype=dt) if isinstance(a, np.ndarray) else a)
+        if self.unknowns_per_node(p) == 1:
+            perm = conv(p["perm"], np.float64)
+            dd = conv(p["dirichlet_dofs"], np.int32)
+            dv = conv(p["dirichlet_values"], np.float64)
+            nl = p.get("nodal_load")
+            nl = conv(nl, np.float64) if nl is not None else None
+            keep += [perm, dd, dv, nl]
+            dirichlet = geneo_dirichlet(int(len(dd)), _ptr(dd), _ptr(dv))
+            geneo_assemble_darcy(self.ctx, mesh, perm, dirichlet, nl, p["source"])
+            self.nnode, self.nnzb = geneo_system_info(self.ctx)
+            self.nc = 1
+            self.ndof = self.nnode
+            self.nx, self.ny, self.nz = int(p["nx"]), int(p["ny"]), int(p["nz"])
+            return
         mats_np = np.asarray(p["materials"], dtype=np.float64)
         mats = (geneo_ortho * len(mats_np))(*[geneo_ortho(*row) for row in mats_np])
         conv = lambda a, dt: (np.ascontiguousarray(a, dtype=dt) if isinstance(a, np.ndarray) else a)
@@ -339,6 +367,7 @@ class GeneoSolver:
         dirichlet = geneo_dirichlet(int(len(dd)), _ptr(dd), _ptr(dv))
         geneo_assemble(self.ctx, mesh, mats, emat, th, ph, dirichlet, nl, p["top_pressure"])
         self.nnode, self.nnzb = geneo_system_info(self.ctx)
+        self.nc = 3
         self.ndof = 3 * self.nnode
         self.nx, self.ny, self.nz = int(p["nx"]), int(p["ny"]), int(p["nz"])
 
@@ -395,10 +424,11 @@ class GeneoSolver:
     def system(self):
         rp = np.zeros(self.nnode + 1, np.int32)
         col = np.zeros(self.nnzb, np.int32)
-        val = np.zeros(9 * self.nnzb)
+        nc = getattr(self, "nc", 3)
+        val = np.zeros(nc * nc * self.nnzb)
         b = np.zeros(self.ndof)
         geneo_get_system(self.ctx, rp, col, val, b)
-        return rp, col, val.reshape(-1, 3, 3), b
+        return rp, col, val.reshape(-1, nc, nc), b
 
     def spmv(self, x):
         y = np.zeros(self.ndof) if isinstance(x, np.ndarray) else self.torch.empty_like(x)

@@ -166,13 +166,13 @@ __global__ void k_dirichlet_mark(int nd, const int32_t *__restrict__ dofs,
 // Lifting of the Dirichlet data (Sec. 2, u = g on the clamped face):
 // lift_i = -sum_{c in D} A_ic g_c on free rows, lift_i = g_i on Dirichlet rows.
 // It is kept so that a new load reuses it without the eliminated columns.
-__global__ void k_dirichlet_lift(int nnode, const int32_t *__restrict__ row_ptr,
+__global__ void k_dirichlet_lift(int nnode, int nc, const int32_t *__restrict__ row_ptr,
                                  const int32_t *__restrict__ col, const double *__restrict__ val,
                                  const uint8_t *__restrict__ mask, const double *__restrict__ g,
                                  double *__restrict__ lift) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 3 * nnode) return;
-  int n = t / 3, r = t % 3;
+  if (t >= nc * nnode) return;
+  int n = t / nc, r = t % nc;
   if (mask[t]) {
     lift[t] = g[t];
     return;
@@ -180,8 +180,8 @@ __global__ void k_dirichlet_lift(int nnode, const int32_t *__restrict__ row_ptr,
   double s = 0.0;
   for (int p = row_ptr[n]; p < row_ptr[n + 1]; ++p) {
     int cn = col[p];
-    for (int c = 0; c < 3; ++c)
-      if (mask[3 * cn + c]) s += val[9 * (size_t)p + 3 * r + c] * g[3 * cn + c];
+    for (int c = 0; c < nc; ++c)
+      if (mask[nc * cn + c]) s += val[(size_t)nc * nc * p + nc * r + c] * g[nc * cn + c];
   }
   lift[t] = -s;
 }
@@ -194,23 +194,75 @@ __global__ void k_apply_lift(int n3, const uint8_t *__restrict__ mask,
   b[t] = mask[t] ? lift[t] : b[t] + lift[t];
 }
 
-// Zero Dirichlet rows and columns, unit diagonal.
-__global__ void k_dirichlet_eliminate(int nnode, const int32_t *__restrict__ row_ptr,
+// Zero Dirichlet rows and columns, unit diagonal (nc unknowns per node).
+__global__ void k_dirichlet_eliminate(int nnode, int nc, const int32_t *__restrict__ row_ptr,
                                       const int32_t *__restrict__ col,
                                       const uint8_t *__restrict__ mask,
                                       double *__restrict__ val) {
   int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nnode) return;
-  bool anyrow = mask[3 * n] | mask[3 * n + 1] | mask[3 * n + 2];
+  bool anyrow = false;
+  for (int r = 0; r < nc; ++r) anyrow |= mask[nc * n + r] != 0;
   for (int p = row_ptr[n]; p < row_ptr[n + 1]; ++p) {
     int cn = col[p];
-    bool anycol = mask[3 * cn] | mask[3 * cn + 1] | mask[3 * cn + 2];
+    bool anycol = false;
+    for (int c = 0; c < nc; ++c) anycol |= mask[nc * cn + c] != 0;
     if (!anyrow && !anycol) continue;
-    for (int r = 0; r < 3; ++r)
-      for (int c = 0; c < 3; ++c)
-        if (mask[3 * n + r] || mask[3 * cn + c])
-          val[9 * (size_t)p + 3 * r + c] = (cn == n && r == c) ? 1.0 : 0.0;
+    for (int r = 0; r < nc; ++r)
+      for (int c = 0; c < nc; ++c)
+        if (mask[nc * n + r] || mask[nc * cn + c])
+          val[(size_t)nc * nc * p + nc * r + c] = (cn == n && r == c) ? 1.0 : 0.0;
   }
+}
+
+// ---- scalar Darcy problem (eqn:Darcy, eq-fe-darcy): one unknown per node ----
+
+// One thread per (node, neighbour slot), gathered from the shared elements.
+__global__ void k_assemble_values_darcy(int nx, int ny, int nz, const double *__restrict__ X,
+                                        const double *__restrict__ Y,
+                                        const double *__restrict__ Z,
+                                        const double *__restrict__ perm,
+                                        const int32_t *__restrict__ row_ptr,
+                                        double *__restrict__ val) {
+  int nnx = nx + 1, nny = ny + 1, nnz = nz + 1;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)nnx * nny * nnz * 27) return;
+  int n = (int)(t / 27), s = (int)(t % 27);
+  int i, j, k;
+  node_ijk(n, nnx, nny, i, j, k);
+  if (!slot_valid(s, i, j, k, nnx, nny, nnz)) return;
+  int pos = row_ptr[n];
+  for (int q = 0; q < s; ++q) pos += slot_valid(q, i, j, k, nnx, nny, nnz);
+  int i2 = i + s % 3 - 1, j2 = j + (s / 3) % 3 - 1, k2 = k + s / 9 - 1;
+  double acc = 0.0;
+  for (int ez = max(max(k, k2) - 1, 0); ez <= min(min(k, k2), nz - 1); ++ez)
+    for (int ey = max(max(j, j2) - 1, 0); ey <= min(min(j, j2), ny - 1); ++ey)
+      for (int ex = max(max(i, i2) - 1, 0); ex <= min(min(i, i2), nx - 1); ++ex) {
+        int e = ex + nx * (ey + ny * ez);
+        int a = (i - ex) + 2 * (j - ey) + 4 * (k - ez);
+        int b = (i2 - ex) + 2 * (j2 - ey) + 4 * (k2 - ez);
+        acc += darcy_entry(perm + 3 * (size_t)e, X[ex + 1] - X[ex], Y[ey + 1] - Y[ey],
+                           Z[ez + 1] - Z[ez], a, b);
+      }
+  val[pos] = acc;
+}
+
+// b_n = int f N_n dx = sum over the elements of node n of f V_e / 8, plus nodal.
+__global__ void k_load_darcy(int nx, int ny, int nz, const double *__restrict__ X,
+                             const double *__restrict__ Y, const double *__restrict__ Z,
+                             double f, const double *__restrict__ nodal, double *__restrict__ b) {
+  int nnx = nx + 1, nny = ny + 1;
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nnx * nny * (nz + 1)) return;
+  int i, j, k;
+  node_ijk(n, nnx, nny, i, j, k);
+  double v = 0.0;
+  if (f != 0.0)
+    for (int ez = max(k - 1, 0); ez <= min(k, nz - 1); ++ez)
+      for (int ey = max(j - 1, 0); ey <= min(j, ny - 1); ++ey)
+        for (int ex = max(i - 1, 0); ex <= min(i, nx - 1); ++ex)
+          v += f * (X[ex + 1] - X[ex]) * (Y[ey + 1] - Y[ey]) * (Z[ez + 1] - Z[ez]) * 0.125;
+  b[n] = v + (nodal ? nodal[n] : 0.0);
 }
 
 // ---------------------------------------------------------------------------
@@ -235,10 +287,10 @@ int launch_assembly(const AssemblyArgs &a, cudaStream_t s) {
   if (a.n_dir > 0) {
     k_dirichlet_mark<<<(a.n_dir + T - 1) / T, T, 0, s>>>(a.n_dir, a.dir_dofs, a.dir_vals,
                                                          3 * nnode, a.mask, a.g, a.status); GENEO_COUNT_LAUNCH();
-    k_dirichlet_lift<<<(3 * nnode + T - 1) / T, T, 0, s>>>(nnode, a.row_ptr, a.col, a.val,
+    k_dirichlet_lift<<<(3 * nnode + T - 1) / T, T, 0, s>>>(nnode, 3, a.row_ptr, a.col, a.val,
                                                            a.mask, a.g, a.lift); GENEO_COUNT_LAUNCH();
     k_apply_lift<<<(3 * nnode + T - 1) / T, T, 0, s>>>(3 * nnode, a.mask, a.lift, a.b); GENEO_COUNT_LAUNCH();
-    k_dirichlet_eliminate<<<(nnode + T - 1) / T, T, 0, s>>>(nnode, a.row_ptr, a.col, a.mask,
+    k_dirichlet_eliminate<<<(nnode + T - 1) / T, T, 0, s>>>(nnode, 3, a.row_ptr, a.col, a.mask,
                                                             a.val); GENEO_COUNT_LAUNCH();
   }
   GENEO_CUDA_TRY(cudaGetLastError());
@@ -290,10 +342,43 @@ int launch_element_stress(int nx, int ny, int nz, const double *X, const double 
 int launch_load(const AssemblyArgs &a, cudaStream_t s) {
   const int T = 256;
   int nnode = (a.nx + 1) * (a.ny + 1) * (a.nz + 1);
-  k_load<<<(nnode + T - 1) / T, T, 0, s>>>(a.nx, a.ny, a.nz, a.X, a.Y, a.top_pressure,
-                                           a.nodal, a.b); GENEO_COUNT_LAUNCH();
+  const int nc = a.nc == 1 ? 1 : 3;
+  if (nc == 1) {
+    k_load_darcy<<<(nnode + T - 1) / T, T, 0, s>>>(a.nx, a.ny, a.nz, a.X, a.Y, a.Z, a.top_pressure,
+                                                   a.nodal, a.b); GENEO_COUNT_LAUNCH();
+  } else {
+    k_load<<<(nnode + T - 1) / T, T, 0, s>>>(a.nx, a.ny, a.nz, a.X, a.Y, a.top_pressure,
+                                             a.nodal, a.b); GENEO_COUNT_LAUNCH();
+  }
   if (a.n_dir > 0) {
-    k_apply_lift<<<(3 * nnode + T - 1) / T, T, 0, s>>>(3 * nnode, a.mask, a.lift, a.b); GENEO_COUNT_LAUNCH();
+    k_apply_lift<<<(nc * nnode + T - 1) / T, T, 0, s>>>(nc * nnode, a.mask, a.lift, a.b); GENEO_COUNT_LAUNCH();
+  }
+  GENEO_CUDA_TRY(cudaGetLastError());
+  return GENEO_OK;
+}
+
+int launch_assembly_darcy(const AssemblyArgs &a, cudaStream_t s) {
+  const int T = 256;
+  int nnx = a.nx + 1, nny = a.ny + 1, nnz = a.nz + 1;
+  int nnode = nnx * nny * nnz;
+  k_bsr_count<<<(nnode + T - 1) / T, T, 0, s>>>(nnx, nny, nnz, a.cnt); GENEO_COUNT_LAUNCH();
+  k_scan_single<<<1, 1024, 0, s>>>(nnode, a.cnt, a.row_ptr); GENEO_COUNT_LAUNCH();
+  k_bsr_fill<<<(nnode + T - 1) / T, T, 0, s>>>(nnx, nny, nnz, a.row_ptr, a.col); GENEO_COUNT_LAUNCH();
+  long long nt = (long long)nnode * 27;
+  k_assemble_values_darcy<<<(unsigned)((nt + 127) / 128), 128, 0, s>>>(
+      a.nx, a.ny, a.nz, a.X, a.Y, a.Z, a.perm, a.row_ptr, a.val); GENEO_COUNT_LAUNCH();
+  k_load_darcy<<<(nnode + T - 1) / T, T, 0, s>>>(a.nx, a.ny, a.nz, a.X, a.Y, a.Z, a.top_pressure,
+                                                 a.nodal, a.b); GENEO_COUNT_LAUNCH();
+  GENEO_CUDA_TRY(cudaMemsetAsync(a.mask, 0, (size_t)nnode, s));
+  GENEO_CUDA_TRY(cudaMemsetAsync(a.g, 0, (size_t)nnode * sizeof(double), s));
+  if (a.n_dir > 0) {
+    k_dirichlet_mark<<<(a.n_dir + T - 1) / T, T, 0, s>>>(a.n_dir, a.dir_dofs, a.dir_vals, nnode,
+                                                         a.mask, a.g, a.status); GENEO_COUNT_LAUNCH();
+    k_dirichlet_lift<<<(nnode + T - 1) / T, T, 0, s>>>(nnode, 1, a.row_ptr, a.col, a.val, a.mask,
+                                                       a.g, a.lift); GENEO_COUNT_LAUNCH();
+    k_apply_lift<<<(nnode + T - 1) / T, T, 0, s>>>(nnode, a.mask, a.lift, a.b); GENEO_COUNT_LAUNCH();
+    k_dirichlet_eliminate<<<(nnode + T - 1) / T, T, 0, s>>>(nnode, 1, a.row_ptr, a.col, a.mask,
+                                                            a.val); GENEO_COUNT_LAUNCH();
   }
   GENEO_CUDA_TRY(cudaGetLastError());
   return GENEO_OK;

@@ -308,13 +308,14 @@ __global__ void k_extract_interior(const SubDesc *subs, const BandLayout *lay, i
     pos += ((unsigned)qi < (unsigned)nnx && (unsigned)qj < (unsigned)nny &&
             (unsigned)qk < (unsigned)nnz);
   }
-  const double *blk = val + 9 * (size_t)pos;
-  for (int rr = 0; rr < 3; ++rr)
-    for (int cc = 0; cc < 3; ++cc) {
-      int R = 3 * l + rr, C = 3 * l2 + cc;
+  const int nc = S.nc;
+  const double *blk = val + (size_t)nc * nc * pos;
+  for (int rr = 0; rr < nc; ++rr)
+    for (int cc = 0; cc < nc; ++cc) {
+      int R = nc * l + rr, C = nc * l2 + cc;
       if (R < C) continue;
       int I = R >> 5, J = C >> 5;
-      tile_ptr(pool, L, I, I - J)[(C & 31) * 32 + (R & 31)] = T(blk[3 * rr + cc]);
+      tile_ptr(pool, L, I, I - J)[(C & 31) * 32 + (R & 31)] = T(blk[nc * rr + cc]);
     }
 }
 
@@ -339,6 +340,7 @@ __global__ void k_schwarz_gather(int nnx, int nny, int nnz, int px, int py,
   while (ncj < kMaxCand && cj[ncj] >= 0) ++ncj;
   while (nck < kMaxCand && ck[nck] >= 0) ++nck;
   double wgt = pou ? 1.0 / double(nci * ncj * nck) : 1.0;
+  const int nc = subs[0].nc;
   double o[3] = {0.0, 0.0, 0.0};
   for (int c = 0; c < nck; ++c)
     for (int b = 0; b < ncj; ++b)
@@ -347,21 +349,19 @@ __global__ void k_schwarz_gather(int nnx, int nny, int nnz, int px, int py,
         const SubDesc &S = subs[j];
         int l = S.ibox.local(i, jj, k);
         if (l < 0) continue;
-        const T *xs = xloc + S.v_int + 3 * l;
-        for (int comp = 0; comp < 3; ++comp) {
+        const T *xs = xloc + S.v_int + nc * l;
+        for (int comp = 0; comp < nc; ++comp) {
           double v = double(xs[comp]);
-          if (pou) v *= mask[3 * n + comp] ? 0.0 : wgt;
+          if (pou) v *= mask[nc * n + comp] ? 0.0 : wgt;
           if (S.m > 0 && yH) {
-            const double *zr = Zp + S.z_off + (long long)(3 * l + comp) * S.m;
+            const double *zr = Zp + S.z_off + (long long)(nc * l + comp) * S.m;
             const double *yy = yH + S.coff;
             for (int q = 0; q < S.m; ++q) v += zr[q] * yy[q];
           }
           o[comp] += v;
         }
       }
-  z[3 * n] = o[0];
-  z[3 * n + 1] = o[1];
-  z[3 * n + 2] = o[2];
+  for (int comp = 0; comp < nc; ++comp) z[nc * n + comp] = o[comp];
 }
 
 // partial w_{j,k} over a chunk of interior rows: thread (k = t % 32, row group t / 32)
@@ -383,10 +383,10 @@ __global__ void __launch_bounds__(256) k_coarse_restrict(const SubDesc *subs, in
   double s = 0.0;
   if (k < m) {
     for (int l = l0 + grp; l < l1; l += 8) {
-      int node = l / 3, c = l - 3 * node;
+      int node = l / S.nc, c = l - S.nc * node;
       int gi, gj, gk;
       S.ibox.global(node, gi, gj, gk);
-      s += Zp[S.z_off + (long long)l * m + k] * r[3 * (gi + nnx * (gj + nny * gk)) + c];
+      s += Zp[S.z_off + (long long)l * m + k] * r[S.nc * (gi + nnx * (gj + nny * gk)) + c];
     }
   }
   acc[grp][k] = s;

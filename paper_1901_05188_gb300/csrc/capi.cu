@@ -113,33 +113,36 @@ int check_status(geneo_ctx *c, int *where = nullptr) {
 }
 
 // ---- phase 0 layout --------------------------------------------------------
-void plan_assemble(Arena &A, geneo_ctx *c, int nx, int ny, int nz, int n_mat, int n_dir) {
+void plan_assemble(Arena &A, geneo_ctx *c, int nx, int ny, int nz, int n_mat, int n_dir,
+                   int nc = 3) {
   int nnode = (nx + 1) * (ny + 1) * (nz + 1);
   long long nel = (long long)nx * ny * nz;
   // nnzb upper bound: 27 per node
   long long nnzb = 27LL * nnode;
+  const bool elastic = nc == 3;
   c->X = A.take<double>(nx + 1);
   c->Y = A.take<double>(ny + 1);
   c->Z = A.take<double>(nz + 1);
-  c->C0 = A.take<double>(36 * (size_t)std::max(n_mat, 1));
-  c->Cel = A.take<double>(36 * (size_t)nel);
+  c->C0 = elastic ? A.take<double>(36 * (size_t)std::max(n_mat, 1)) : nullptr;
+  c->Cel = elastic ? A.take<double>(36 * (size_t)nel) : nullptr;
   c->cnt = A.take<int32_t>(nnode);
   c->row_ptr = A.take<int32_t>(nnode + 1);
   c->col = A.take<int32_t>(nnzb);
-  c->val = A.take<double>(9 * (size_t)nnzb);
-  c->b = A.take<double>(3 * (size_t)nnode);
-  c->g = A.take<double>(3 * (size_t)nnode);
-  c->lift = A.take<double>(3 * (size_t)nnode);
-  c->sig = A.take<double>(6 * (size_t)nel);
-  c->mask = A.take<uint8_t>(3 * (size_t)nnode);
+  c->val = A.take<double>((size_t)nc * nc * nnzb);
+  c->b = A.take<double>((size_t)nc * nnode);
+  c->g = A.take<double>((size_t)nc * nnode);
+  c->lift = A.take<double>((size_t)nc * nnode);
+  c->sig = elastic ? A.take<double>(6 * (size_t)nel) : nullptr;
+  c->mask = A.take<uint8_t>((size_t)nc * nnode);
   c->status = A.take<DevStatus>(1);
-  c->mats = A.take<geneo_ortho>(std::max(n_mat, 1));
-  c->emat = A.take<int32_t>(nel);
-  c->theta = A.take<double>(nel);
-  c->phi = A.take<double>(nel);
+  c->mats = elastic ? A.take<geneo_ortho>(std::max(n_mat, 1)) : nullptr;
+  c->emat = elastic ? A.take<int32_t>(nel) : nullptr;
+  c->theta = elastic ? A.take<double>(nel) : nullptr;
+  c->phi = elastic ? A.take<double>(nel) : nullptr;
+  c->perm = elastic ? nullptr : A.take<double>(3 * (size_t)nel);
   c->dir_dofs = A.take<int32_t>(std::max(n_dir, 1));
   c->dir_vals = A.take<double>(std::max(n_dir, 1));
-  c->nodal = A.take<double>(3 * (size_t)nnode);
+  c->nodal = A.take<double>((size_t)nc * nnode);
 }
 
 // ---- box partition (host integer logic) -----------------------------------
@@ -296,26 +299,28 @@ int geneo_bind_workspace(geneo_ctx *c, int phase, void *ptr, size_t bytes) {
   return GENEO_OK;
 }
 
-int geneo_assemble(geneo_ctx *c, const geneo_mesh *mesh, int n_mat, const geneo_ortho *mats,
-                   const int32_t *elem_mat, const double *elem_theta, const double *elem_phi,
-                   const geneo_dirichlet *dir, const double *nodal_load, double top_pressure) {
-  if (!c || !mesh || !mats || !elem_mat || !elem_theta || n_mat < 1)
-    return fail(GENEO_ERR_INVALID_ARG, "null argument");
+}  // extern "C"
+
+// Shared start of both assemblies: mesh checks, host copies of the axes, the
+// phase-0 workspace laid out for nc unknowns per node, axes and Dirichlet data
+// staged on the device.
+static int begin_assembly(geneo_ctx *c, const geneo_mesh *mesh, int n_mat, const geneo_dirichlet *dir,
+                          int nc, int &n_dir) {
   if (mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1 || !mesh->x || !mesh->y || !mesh->z)
     return fail(GENEO_ERR_INVALID_ARG, "bad mesh");
   long long nnode_ll = (long long)(mesh->nx + 1) * (mesh->ny + 1) * (mesh->nz + 1);
   if (nnode_ll * 27 > 0x7fffffffLL) return fail(GENEO_ERR_INVALID_ARG, "mesh too large for int32 BSR");
-  int n_dir = dir ? dir->n : 0;
+  n_dir = dir ? dir->n : 0;
   if (n_dir < 0 || (n_dir > 0 && !dir->dof)) return fail(GENEO_ERR_INVALID_ARG, "bad Dirichlet set");
   cudaStream_t s = c->stream;
   release_setup(c);
   c->assembled = false;
-  // host copies of coordinates (validation + partition geometry)
+  c->nc = nc;
   c->nx = mesh->nx;
   c->ny = mesh->ny;
   c->nz = mesh->nz;
   c->nnode = (int)nnode_ll;
-  c->ndof = 3 * c->nnode;
+  c->ndof = nc * c->nnode;
   c->nel = c->nx * c->ny * c->nz;
   const double *axes[3] = {mesh->x, mesh->y, mesh->z};
   std::vector<double> *hv[3] = {&c->hx, &c->hy, &c->hz};
@@ -330,11 +335,9 @@ int geneo_assemble(geneo_ctx *c, const geneo_mesh *mesh, int n_mat, const geneo_
     for (int i = 1; i < na[d]; ++i)
       if (!((*hv[d])[i] > (*hv[d])[i - 1])) return fail(GENEO_ERR_INVALID_ARG, "coordinates not increasing");
   }
-  // workspace
   Arena A;
-  plan_assemble(A, c, c->nx, c->ny, c->nz, n_mat, n_dir);
+  plan_assemble(A, c, c->nx, c->ny, c->nz, n_mat, n_dir, nc);
   size_t need = A.off + 256;
-  char *base;
   if (c->ws0_bound) {
     if (c->ws0_bound_bytes < need) return fail(GENEO_ERR_WORKSPACE_TOO_SMALL, "assemble workspace too small");
     if (c->ws0_owned && c->ws0) cudaFree(c->ws0);
@@ -347,62 +350,29 @@ int geneo_assemble(geneo_ctx *c, const geneo_mesh *mesh, int n_mat, const geneo_
     c->ws0_owned = true;
     c->ws0_bytes = need;
   }
-  base = (char *)c->ws0;
   Arena B;
-  B.base = base;
+  B.base = (char *)c->ws0;
   B.cap = c->ws0_bytes;
-  plan_assemble(B, c, c->nx, c->ny, c->nz, n_mat, n_dir);
-  cudaEvent_t e0, e1;
-  GENEO_CUDA_TRY(cudaEventCreate(&e0));
-  GENEO_CUDA_TRY(cudaEventCreate(&e1));
-  GENEO_CUDA_TRY(cudaEventRecord(e0, s));
+  plan_assemble(B, c, c->nx, c->ny, c->nz, n_mat, n_dir, nc);
   GENEO_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(DevStatus), s));
   int st;
   if ((st = stage(c->X, mesh->x, c->nx + 1, s))) return st;
   if ((st = stage(c->Y, mesh->y, c->ny + 1, s))) return st;
   if ((st = stage(c->Z, mesh->z, c->nz + 1, s))) return st;
-  if ((st = stage(c->mats, mats, n_mat, s))) return st;
-  if ((st = stage(c->emat, elem_mat, c->nel, s))) return st;
-  if ((st = stage(c->theta, elem_theta, c->nel, s))) return st;
-  if (elem_phi && (st = stage(c->phi, elem_phi, c->nel, s))) return st;
   if (n_dir > 0) {
     if ((st = stage(c->dir_dofs, dir->dof, n_dir, s))) return st;
     if (dir->value && (st = stage(c->dir_vals, dir->value, n_dir, s))) return st;
   }
-  if (nodal_load && (st = stage(c->nodal, nodal_load, c->ndof, s))) return st;
-  AssemblyArgs a{};
-  a.nx = c->nx;
-  a.ny = c->ny;
-  a.nz = c->nz;
-  a.n_mat = n_mat;
-  a.n_dir = n_dir;
-  a.X = c->X;
-  a.Y = c->Y;
-  a.Z = c->Z;
-  a.mats = c->mats;
-  a.emat = c->emat;
-  a.theta = c->theta;
-  a.phi = elem_phi ? c->phi : nullptr;
-  a.dir_dofs = c->dir_dofs;
-  a.dir_vals = (n_dir > 0 && dir->value) ? c->dir_vals : nullptr;
-  a.nodal = nodal_load ? c->nodal : nullptr;
-  a.top_pressure = top_pressure;
-  a.C0 = c->C0;
-  a.Cel = c->Cel;
-  a.cnt = c->cnt;
-  a.row_ptr = c->row_ptr;
-  a.col = c->col;
-  a.val = c->val;
-  a.b = c->b;
-  a.g = c->g;
-  a.lift = c->lift;
-  a.mask = c->mask;
-  a.status = c->status;
   c->n_dir = n_dir;
-  if ((st = launch_assembly(a, s))) return st;
-  GENEO_CUDA_TRY(cudaEventRecord(e1, s));
+  return GENEO_OK;
+}
+
+// Shared end: number of stored blocks, device status, host copy of the mask.
+static int finish_assembly(geneo_ctx *c, cudaEvent_t e0, cudaEvent_t e1) {
+  cudaStream_t s = c->stream;
   int32_t nnzb;
   GENEO_CUDA_TRY(cudaMemcpyAsync(&nnzb, c->row_ptr + c->nnode, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  int st;
   if ((st = check_status(c))) return st;
   GENEO_CUDA_TRY(cudaEventElapsedTime(&c->ms_assemble, e0, e1));
   cudaEventDestroy(e0);
@@ -412,6 +382,84 @@ int geneo_assemble(geneo_ctx *c, const geneo_mesh *mesh, int n_mat, const geneo_
   GENEO_CUDA_TRY(copy_sync(c, c->hmask.data(), c->mask, c->ndof, cudaMemcpyDeviceToHost));
   c->assembled = true;
   return GENEO_OK;
+}
+
+static void fill_common_args(geneo_ctx *c, AssemblyArgs &a, int n_dir, const geneo_dirichlet *dir,
+                             const double *nodal_load, double scalar) {
+  a.nx = c->nx;
+  a.ny = c->ny;
+  a.nz = c->nz;
+  a.n_dir = n_dir;
+  a.nc = c->nc;
+  a.X = c->X;
+  a.Y = c->Y;
+  a.Z = c->Z;
+  a.dir_dofs = c->dir_dofs;
+  a.dir_vals = (n_dir > 0 && dir->value) ? c->dir_vals : nullptr;
+  a.nodal = nodal_load ? c->nodal : nullptr;
+  a.top_pressure = scalar;
+  a.cnt = c->cnt;
+  a.row_ptr = c->row_ptr;
+  a.col = c->col;
+  a.val = c->val;
+  a.b = c->b;
+  a.g = c->g;
+  a.lift = c->lift;
+  a.mask = c->mask;
+  a.status = c->status;
+}
+
+extern "C" {
+
+int geneo_assemble(geneo_ctx *c, const geneo_mesh *mesh, int n_mat, const geneo_ortho *mats,
+                   const int32_t *elem_mat, const double *elem_theta, const double *elem_phi,
+                   const geneo_dirichlet *dir, const double *nodal_load, double top_pressure) {
+  if (!c || !mesh || !mats || !elem_mat || !elem_theta || n_mat < 1)
+    return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  int n_dir = 0, st;
+  if ((st = begin_assembly(c, mesh, n_mat, dir, 3, n_dir))) return st;
+  cudaStream_t s = c->stream;
+  cudaEvent_t e0, e1;
+  GENEO_CUDA_TRY(cudaEventCreate(&e0));
+  GENEO_CUDA_TRY(cudaEventCreate(&e1));
+  GENEO_CUDA_TRY(cudaEventRecord(e0, s));
+  if ((st = stage(c->mats, mats, n_mat, s))) return st;
+  if ((st = stage(c->emat, elem_mat, c->nel, s))) return st;
+  if ((st = stage(c->theta, elem_theta, c->nel, s))) return st;
+  if (elem_phi && (st = stage(c->phi, elem_phi, c->nel, s))) return st;
+  if (nodal_load && (st = stage(c->nodal, nodal_load, c->ndof, s))) return st;
+  AssemblyArgs a{};
+  fill_common_args(c, a, n_dir, dir, nodal_load, top_pressure);
+  a.n_mat = n_mat;
+  a.mats = c->mats;
+  a.emat = c->emat;
+  a.theta = c->theta;
+  a.phi = elem_phi ? c->phi : nullptr;
+  a.C0 = c->C0;
+  a.Cel = c->Cel;
+  if ((st = launch_assembly(a, s))) return st;
+  GENEO_CUDA_TRY(cudaEventRecord(e1, s));
+  return finish_assembly(c, e0, e1);
+}
+
+int geneo_assemble_darcy(geneo_ctx *c, const geneo_mesh *mesh, const double *perm,
+                         const geneo_dirichlet *dir, const double *nodal_load, double source) {
+  if (!c || !mesh || !perm) return fail(GENEO_ERR_INVALID_ARG, "null argument");
+  int n_dir = 0, st;
+  if ((st = begin_assembly(c, mesh, 1, dir, 1, n_dir))) return st;
+  cudaStream_t s = c->stream;
+  cudaEvent_t e0, e1;
+  GENEO_CUDA_TRY(cudaEventCreate(&e0));
+  GENEO_CUDA_TRY(cudaEventCreate(&e1));
+  GENEO_CUDA_TRY(cudaEventRecord(e0, s));
+  if ((st = stage(c->perm, perm, 3 * (size_t)c->nel, s))) return st;
+  if (nodal_load && (st = stage(c->nodal, nodal_load, c->ndof, s))) return st;
+  AssemblyArgs a{};
+  fill_common_args(c, a, n_dir, dir, nodal_load, source);
+  a.perm = c->perm;
+  if ((st = launch_assembly_darcy(a, s))) return st;
+  GENEO_CUDA_TRY(cudaEventRecord(e1, s));
+  return finish_assembly(c, e0, e1);
 }
 
 int geneo_set_load(geneo_ctx *c, const double *nodal_load, double top_pressure) {
@@ -424,8 +472,10 @@ int geneo_set_load(geneo_ctx *c, const double *nodal_load, double top_pressure) 
   a.ny = c->ny;
   a.nz = c->nz;
   a.n_dir = c->n_dir;
+  a.nc = c->nc;
   a.X = c->X;
   a.Y = c->Y;
+  a.Z = c->Z;
   a.nodal = nodal_load ? c->nodal : nullptr;
   a.top_pressure = top_pressure;
   a.b = c->b;
@@ -437,6 +487,7 @@ int geneo_set_load(geneo_ctx *c, const double *nodal_load, double top_pressure) 
 
 int geneo_element_stress(geneo_ctx *c, const double *u, double *sigma) {
   if (!c || !c->assembled) return fail(GENEO_ERR_STATE, "not assembled");
+  if (c->nc != 3) return fail(GENEO_ERR_INVALID_ARG, "stresses exist for the elasticity system only");
   if (!u || !sigma) return fail(GENEO_ERR_INVALID_ARG, "null vector");
   cudaStream_t s = c->stream;
   int st;
@@ -465,7 +516,7 @@ int geneo_get_system(geneo_ctx *c, int32_t *row_ptr, int32_t *col, double *val, 
   int st;
   if ((st = unstage(row_ptr, c->row_ptr, c->nnode + 1, c->stream))) return st;
   if ((st = unstage(col, c->col, c->nnzb, c->stream))) return st;
-  if ((st = unstage(val, c->val, 9 * (size_t)c->nnzb, c->stream))) return st;
+  if ((st = unstage(val, c->val, (size_t)c->nc * c->nc * c->nnzb, c->stream))) return st;
   if ((st = unstage(b, c->b, c->ndof, c->stream))) return st;
   return GENEO_OK;
 }
@@ -490,7 +541,7 @@ int geneo_spmv(geneo_ctx *c, const double *x, double *y) {
     dx = scratch;
   }
   if (!yd) dy = scratch + c->ndof;
-  BSR A{c->nnode, c->row_ptr, c->col, c->val};
+  BSR A{c->nnode, c->row_ptr, c->col, c->val, c->nc};
   launch_spmv(A, dx, dy, s);
   GENEO_CUDA_TRY(cudaGetLastError());
   if (!yd) GENEO_CUDA_TRY(cudaMemcpyAsync(y, dy, c->ndof * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -595,10 +646,11 @@ int build_plan(geneo_ctx *c, const geneo_partition *part, const geneo_modes *mod
           return next[u] < next[v] || (next[u] == next[v] && u < v);
         });
         for (int d = 0; d < 3; ++d) S.nbox.perm[d] = S.ibox.perm[d] = perm[d];
-        S.n_int = 3 * S.ibox.count();
-        S.n_neu = 3 * S.nbox.count();
-        BandLayout Li = make_layout(S.n_int, S.ibox.half_band_dofs(), f_int);
-        BandLayout Ln = make_layout(S.n_neu, S.nbox.half_band_dofs(), f_neu);
+        S.nc = c->nc;
+        S.n_int = c->nc * S.ibox.count();
+        S.n_neu = c->nc * S.nbox.count();
+        BandLayout Li = make_layout(S.n_int, S.ibox.half_band_dofs(c->nc), f_int);
+        BandLayout Ln = make_layout(S.n_neu, S.nbox.half_band_dofs(c->nc), f_neu);
         S.nt_int = Li.nt;
         S.w_int = Li.w;
         S.f_int = f_int;
@@ -679,7 +731,7 @@ void plan_setup(Arena &A, geneo_ctx *c, const SetupPlan &P) {
     if (eig) {   // shift-invert block Lanczos of the GenEO eigenproblems
       pc.neuL = A.take<double>(pc.fac_neu_elems);
       pc.neuU = A.take<double>(pc.fac_neu_elems);
-      pc.Bloc = A.take<double>(9 * (size_t)pc.bloc_blocks);
+      pc.Bloc = A.take<double>((size_t)c->nc * c->nc * pc.bloc_blocks);
       pc.V = A.take<double>((size_t)nsub * npad * (pc.kdim + p));
       pc.Vt = A.take<double>((size_t)nsub * npad * pc.kkeep);
       pc.W = A.take<double>((size_t)nsub * npad * p);
@@ -821,9 +873,9 @@ static int setup_coarse_zem(geneo_ctx *c, SetupPlan &P, cudaStream_t s) {
       int gi, gj, gk;
       S.nbox.global(l, gi, gj, gk);
       const long long n = gi + (long long)nnx * (gj + (long long)nny * gk);
-      floating = !(c->hmask[3 * n] | c->hmask[3 * n + 1] | c->hmask[3 * n + 2]);
+      for (int comp = 0; comp < c->nc; ++comp) floating = floating && !c->hmask[c->nc * n + comp];
     }
-    const int m = floating ? 6 : 0;
+    const int m = floating ? (c->nc == 3 ? 6 : 1) : 0;
     for (int i = 0; i < m; ++i) pc.lambdas[(size_t)j * mcap + i] = 0.0;
     S.m = m;
     S.coff = coff;
@@ -851,8 +903,8 @@ static int setup_coarse(geneo_ctx *c, SetupPlan &P, cudaStream_t s) {
                      pc.Xneu, s);
   if ((st = launch_band_clear<double>(pc.d_lay_neu, nsub, pc.neuL, pc.fac_neu_elems, s))) return st;
   launch_neumann_assemble(pc.d_subs, pc.d_lay_neu, nsub, P.max_nodes_neu, c->nx, c->ny, c->nz,
-                          c->X, c->Y, c->Z, c->Cel, pc.d_ecnt, pc.ecnt_off, c->mask, pc.Xneu,
-                          sigma, pc.neuL, pc.Bloc, s);
+                          c->X, c->Y, c->Z, c->Cel, c->perm, pc.d_ecnt, pc.ecnt_off, c->mask,
+                          pc.Xneu, sigma, pc.neuL, pc.Bloc, s);
   if ((st = launch_band_cholesky<double>(pc.d_lay_neu, nsub, pc.nt_neu_max, pc.w_neu_max,
                                          pc.neuL, pc.neuU, c->status, s, c->side_stream)))
     return st;
@@ -1076,9 +1128,12 @@ int geneo_setup_workspace_bytes(geneo_ctx *c, const geneo_partition *part,
   return GENEO_OK;
 }
 
-int geneo_estimate_workspace_bytes(const geneo_mesh *mesh, const geneo_partition *part,
-                                   const geneo_modes *modes, geneo_precision prec,
-                                   size_t *assemble_bytes, size_t *setup_bytes) {
+int geneo_estimate_workspace_bytes(const geneo_mesh *mesh, int unknowns_per_node,
+                                   const geneo_partition *part, const geneo_modes *modes,
+                                   geneo_precision prec, size_t *assemble_bytes,
+                                   size_t *setup_bytes) {
+  if (unknowns_per_node != 1 && unknowns_per_node != 3)
+    return fail(GENEO_ERR_INVALID_ARG, "unknowns per node must be 1 or 3");
   if (!mesh || mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1)
     return fail(GENEO_ERR_INVALID_ARG, "bad mesh");
   int st;
@@ -1089,7 +1144,8 @@ int geneo_estimate_workspace_bytes(const geneo_mesh *mesh, const geneo_partition
   tmp.ny = mesh->ny;
   tmp.nz = mesh->nz;
   tmp.nnode = (mesh->nx + 1) * (mesh->ny + 1) * (mesh->nz + 1);
-  tmp.ndof = 3 * tmp.nnode;
+  tmp.nc = unknowns_per_node;
+  tmp.ndof = tmp.nc * tmp.nnode;
   tmp.pc.prec = prec;
   SetupPlan P;
   if ((st = build_plan(&tmp, part, modes, P))) return st;
@@ -1378,9 +1434,9 @@ int geneo_get_coarse(geneo_ctx *c, double *Phi, double *AH) {
     const int nnx = c->nx + 1, nny = c->ny + 1;
     for (const SubDesc &S : pc.subs) {
       for (int l = 0; l < S.n_int; ++l) {
-        int node = l / 3, comp = l % 3, gi, gj, gk;
+        int node = l / c->nc, comp = l % c->nc, gi, gj, gk;
         S.ibox.global(node, gi, gj, gk);
-        long long dof = 3LL * (gi + nnx * (gj + nny * gk)) + comp;
+        long long dof = (long long)c->nc * (gi + nnx * (gj + nny * gk)) + comp;
         for (int k = 0; k < S.m; ++k)
           out[(size_t)(S.coff + k) * c->ndof + dof] = z[S.z_off + (long long)l * S.m + k];
       }
@@ -1444,7 +1500,7 @@ double kappa_from_cg(const std::vector<double> &al, const std::vector<double> &b
 }
 
 int enqueue_iterations(geneo_ctx *c, int iters, cudaStream_t s) {
-  BSR A{c->nnode, c->row_ptr, c->col, c->val};
+  BSR A{c->nnode, c->row_ptr, c->col, c->val, c->nc};
   const int n = c->ndof;
   int st;
   for (int it = 0; it < iters; ++it) {
@@ -1524,7 +1580,7 @@ extern "C" int geneo_solve(geneo_ctx *c, double tol, int max_it, double *u, gene
   GENEO_CUDA_TRY(cudaEventRecord(e1, s));
   h = *c->cg_host;
   // true residual ||b - A x|| / ||b||
-  BSR A{c->nnode, c->row_ptr, c->col, c->val};
+  BSR A{c->nnode, c->row_ptr, c->col, c->val, c->nc};
   launch_spmv(A, c->x, c->tmp, s);
   launch_sub(n, c->b, c->tmp, c->tmp, s);
   launch_norm2(n, c->tmp, c->scal, c->part, &c->cg->counter, s);
@@ -1583,20 +1639,21 @@ extern "C" int geneo_debug_local_matrix(geneo_ctx *c, int sub, int kind, double 
   const bool factor = kind >= 3;
   const int base_kind = kind == 3 ? 0 : (kind == 4 ? 1 : kind);
   const NodeBox &box = base_kind == 0 ? S.ibox : S.nbox;
-  const int n = 3 * box.count();
+  const int nc = c->nc;
+  const int n = nc * box.count();
   const int nnx = c->nx + 1, nny = c->ny + 1, nnz = c->nz + 1;
   if (gdof) {
     for (int l = 0; l < box.count(); ++l) {
       int gi, gj, gk;
       box.global(l, gi, gj, gk);
-      for (int comp = 0; comp < 3; ++comp) gdof[3 * l + comp] = 3 * (gi + nnx * (gj + nny * gk)) + comp;
+      for (int comp = 0; comp < nc; ++comp) gdof[nc * l + comp] = nc * (gi + nnx * (gj + nny * gk)) + comp;
     }
   }
   if (!dense) return GENEO_OK;
   std::vector<double> out((size_t)n * n, 0.0);
   if (kind == 2) {
-    std::vector<double> bl((size_t)27 * 9 * box.count());
-    GENEO_CUDA_TRY(cudaMemcpyAsync(bl.data(), pc.Bloc + S.b_neu * 9, bl.size() * sizeof(double),
+    std::vector<double> bl((size_t)27 * nc * nc * box.count());
+    GENEO_CUDA_TRY(cudaMemcpyAsync(bl.data(), pc.Bloc + S.b_neu * nc * nc, bl.size() * sizeof(double),
                                    cudaMemcpyDeviceToHost, s));
     GENEO_CUDA_TRY(cudaStreamSynchronize(s));
     for (int l = 0; l < box.count(); ++l) {
@@ -1605,13 +1662,14 @@ extern "C" int geneo_debug_local_matrix(geneo_ctx *c, int sub, int kind, double 
       for (int q = 0; q < 27; ++q) {
         int l2 = box.local(gi + q % 3 - 1, gj + (q / 3) % 3 - 1, gk + q / 9 - 1);
         if (l2 < 0) continue;
-        for (int r = 0; r < 3; ++r)
-          for (int cc = 0; cc < 3; ++cc)
-            out[(size_t)(3 * l + r) * n + 3 * l2 + cc] = bl[((size_t)l * 27 + q) * 9 + 3 * r + cc];
+        for (int r = 0; r < nc; ++r)
+          for (int cc = 0; cc < nc; ++cc)
+            out[(size_t)(nc * l + r) * n + nc * l2 + cc] =
+                bl[((size_t)l * 27 + q) * nc * nc + nc * r + cc];
       }
     }
   } else {
-    BandLayout L = make_layout(n, box.half_band_dofs(), 0);
+    BandLayout L = make_layout(n, box.half_band_dofs(nc), 0);
     long long el = layout_elems(L);
     double *tmp = nullptr;
     BandLayout *dl = nullptr;
@@ -1627,8 +1685,8 @@ extern "C" int geneo_debug_local_matrix(geneo_ctx *c, int sub, int kind, double 
                                              c->row_ptr, c->val, tmp, s);
       else
         launch_neumann_assemble(pc.d_subs + sub, dl, 1, box.count(), c->nx, c->ny, c->nz, c->X,
-                                c->Y, c->Z, c->Cel, pc.d_ecnt, pc.ecnt_off, c->mask, pc.Xneu,
-                                pc.modes.shift, tmp, pc.Bloc, s);
+                                c->Y, c->Z, c->Cel, c->perm, pc.d_ecnt, pc.ecnt_off, c->mask,
+                                pc.Xneu, pc.modes.shift, tmp, pc.Bloc, s);
     }
     if (!st && factor) {
       GENEO_CUDA_TRY(cudaMemsetAsync(c->status, 0, sizeof(DevStatus), s));
@@ -1686,7 +1744,7 @@ extern "C" int geneo_profile(geneo_ctx *c, int what, int reps, double *ms_per_la
   const double esz = f32 ? 4.0 : 8.0;
   double by = 0.0, fl = 0.0;
   for (const SubDesc &S : pc.subs) {
-    const double n = S.n_int, hb = S.ibox.half_band_dofs();
+    const double n = S.n_int, hb = S.ibox.half_band_dofs(c->nc);
     const double band = n * (hb + 1) - hb * (hb + 1) / 2;     // entries of L_j
     if (what != 1) {
       by += 2.0 * band * esz + n * (8.0 + esz);
@@ -1694,8 +1752,8 @@ extern "C" int geneo_profile(geneo_ctx *c, int what, int reps, double *ms_per_la
     }
   }
   if (what == 1) {
-    by = (double)c->nnzb * (72.0 + 4.0) + 4.0 * (c->nnode + 1) + 16.0 * c->ndof;
-    fl = 18.0 * c->nnzb;
+    by = (double)c->nnzb * (8.0 * c->nc * c->nc + 4.0) + 4.0 * (c->nnode + 1) + 16.0 * c->ndof;
+    fl = 2.0 * c->nc * c->nc * c->nnzb;
   }
   if (what == 2) {
     by += 8.0 * c->ndof + (double)pc.nH * pc.nH * 8.0;
@@ -1704,14 +1762,14 @@ extern "C" int geneo_profile(geneo_ctx *c, int what, int reps, double *ms_per_la
   if (what == 3) {
     by = fl = 0.0;
     for (const SubDesc &S : pc.subs) {
-      const double n = S.n_neu, hb = S.nbox.half_band_dofs();
+      const double n = S.n_neu, hb = S.nbox.half_band_dofs(c->nc);
       const double band = n * (hb + 1) - hb * (hb + 1) / 2;
       by += band * 8.0 + 2.0 * n * kLanczosBlock * 8.0;
       fl += 2.0 * kLanczosBlock * band;
     }
   }
   // a deterministic, non-trivial residual to work on
-  BSR A{c->nnode, c->row_ptr, c->col, c->val};
+  BSR A{c->nnode, c->row_ptr, c->col, c->val, c->nc};
   launch_spmv(A, c->b, c->r, s);
   cudaEvent_t e0, e1;
   GENEO_CUDA_TRY(cudaEventCreate(&e0));

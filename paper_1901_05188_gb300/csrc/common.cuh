@@ -103,16 +103,18 @@ struct NodeBox {
     j = lo[1] + c[1];
     k = lo[2] + c[2];
   }
-  // half bandwidth in dofs of a 27-point coupling in this numbering
-  __host__ __device__ int half_band_dofs() const {
+  // half bandwidth in dofs of a 27-point coupling in this numbering with nc
+  // unknowns per node
+  __host__ __device__ int half_band_dofs(int nc = 3) const {
     int nf = n[perm[0]], nm = n[perm[1]], ns = n[perm[2]];
     int dn = (nf > 1 ? 1 : 0) + (nm > 1 ? nf : 0) + (ns > 1 ? nf * nm : 0);
-    return 3 * dn + 2;
+    return nc * dn + nc - 1;
   }
 };
 
 // Per-subdomain descriptor (host and device).
 struct SubDesc {
+  int nc;          // unknowns per node: 3 elasticity, 1 Darcy
   NodeBox ibox;    // nodes of V_{h,0}(Omega_j) (interior)
   NodeBox nbox;    // all nodes of Omega_j (Neumann set)
   int elo[3], ehi[3];   // element box of Omega_j, half-open

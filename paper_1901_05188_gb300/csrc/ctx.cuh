@@ -18,6 +18,7 @@ struct geneo_ctx {
   // ---- mesh / assembled system (phase 0)
   bool assembled = false;
   int nx = 0, ny = 0, nz = 0, nnode = 0, ndof = 0, nel = 0, nnzb = 0;
+  int nc = 3;                              // unknowns per node: 3 elasticity, 1 Darcy
   std::vector<double> hx, hy, hz;          // host copies of node coordinates
   std::vector<uint8_t> hmask;              // host copy of the Dirichlet mask
   void *ws0 = nullptr;
@@ -38,6 +39,7 @@ struct geneo_ctx {
   geneo_ortho *mats = nullptr;
   int32_t *emat = nullptr, *dir_dofs = nullptr;
   double *theta = nullptr, *phi = nullptr, *dir_vals = nullptr, *nodal = nullptr;
+  double *perm = nullptr;                  // Darcy: (Kx, Ky, Kz) per element
 
   // ---- preconditioner + Krylov state (phase 1)
   bool setup_done = false;

@@ -127,4 +127,29 @@ __device__ inline void element_block(const double *__restrict__ C, double hx, do
     }
 }
 
+// int K grad N_a . grad N_b over an hx x hy x hz box with K = diag(kd),
+// 2x2x2 Gauss points (local node a at corner (a & 1, (a >> 1) & 1, a >> 2)).
+__device__ inline double darcy_entry(const double *__restrict__ kd, double hx, double hy,
+                                     double hz, int a, int b) {
+  const double g = 0.57735026918962576451;  // 1/sqrt(3)
+  const double sa[3] = {double(2 * (a & 1) - 1), double(2 * ((a >> 1) & 1) - 1),
+                        double(2 * ((a >> 2) & 1) - 1)};
+  const double sb[3] = {double(2 * (b & 1) - 1), double(2 * ((b >> 1) & 1) - 1),
+                        double(2 * ((b >> 2) & 1) - 1)};
+  const double h[3] = {hx, hy, hz};
+  double G[3] = {0.0, 0.0, 0.0};
+  for (int q = 0; q < 8; ++q) {
+    const double t[3] = {(q & 1) ? g : -g, (q & 2) ? g : -g, (q & 4) ? g : -g};
+    double fa[3], fb[3];
+    for (int d = 0; d < 3; ++d) {
+      fa[d] = 0.5 * (1.0 + sa[d] * t[d]);
+      fb[d] = 0.5 * (1.0 + sb[d] * t[d]);
+    }
+    G[0] += (sa[0] / h[0] * fa[1] * fa[2]) * (sb[0] / h[0] * fb[1] * fb[2]);
+    G[1] += (sa[1] / h[1] * fa[0] * fa[2]) * (sb[1] / h[1] * fb[0] * fb[2]);
+    G[2] += (sa[2] / h[2] * fa[0] * fa[1]) * (sb[2] / h[2] * fb[0] * fb[1]);
+  }
+  return (kd[0] * G[0] + kd[1] * G[1] + kd[2] * G[2]) * (hx * hy * hz * 0.125);
+}
+
 }  // namespace geneo

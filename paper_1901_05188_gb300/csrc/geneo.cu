@@ -30,9 +30,10 @@ __global__ void k_pou_neumann(const SubDesc *subs, const int *cand, int co0, int
                               const uint8_t *mask, int nnx, int nny, double *Xneu) {
   const int j = blockIdx.y;
   const SubDesc &S = subs[j];
+  const int nc = S.nc;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 3 * S.nbox.count()) return;
-  int l = t / 3, comp = t - 3 * l;
+  if (t >= nc * S.nbox.count()) return;
+  int l = t / nc, comp = t - nc * l;
   int gi, gj, gk;
   S.nbox.global(l, gi, gj, gk);
   double x = 0.0;
@@ -40,7 +41,7 @@ __global__ void k_pou_neumann(const SubDesc *subs, const int *cand, int co0, int
     int mu = cand_count(cand + (co0 + gi) * kMaxCand) * cand_count(cand + (co1 + gj) * kMaxCand) *
              cand_count(cand + (co2 + gk) * kMaxCand);
     x = 1.0 / double(mu);
-    if (mask[3 * (gi + nnx * (gj + nny * gk)) + comp]) x = 0.0;
+    if (mask[nc * (gi + nnx * (gj + nny * gk)) + comp]) x = 0.0;
   }
   Xneu[S.x_neu + t] = x;
 }
@@ -49,6 +50,7 @@ __global__ void __launch_bounds__(128)
     k_neumann_assemble(const SubDesc *subs, const BandLayout *lay, int nx, int ny, int nz,
                        const double *__restrict__ X, const double *__restrict__ Y,
                        const double *__restrict__ Z, const double *__restrict__ Cel,
+                       const double *__restrict__ perm,
                        const int *__restrict__ ecnt, int eo0, int eo1, int eo2,
                        const uint8_t *__restrict__ mask, const double *__restrict__ Xneu,
                        double sigma, double *poolS, double *Bloc) {
@@ -62,9 +64,10 @@ __global__ void __launch_bounds__(128)
   S.nbox.global(l, gi, gj, gk);
   const int i2 = gi + s % 3 - 1, j2 = gj + (s / 3) % 3 - 1, k2 = gk + s / 9 - 1;
   const int l2 = S.nbox.local(i2, j2, k2);
-  double *bl = Bloc + (S.b_neu + (long long)l * 27 + s) * 9;
+  const int nc = S.nc, nc2 = nc * nc;
+  double *bl = Bloc + (S.b_neu + (long long)l * 27 + s) * nc2;
   if (l2 < 0) {
-    for (int q = 0; q < 9; ++q) bl[q] = 0.0;
+    for (int q = 0; q < nc2; ++q) bl[q] = 0.0;
     return;
   }
   double KA[9], KO[9];
@@ -76,10 +79,14 @@ __global__ void __launch_bounds__(128)
         int a = (gi - ex) + 2 * (gj - ey) + 4 * (gk - ez);
         int b = (i2 - ex) + 2 * (j2 - ey) + 4 * (k2 - ez);
         double Kb[9];
-        element_block(Cel + 36 * (size_t)e, X[ex + 1] - X[ex], Y[ey + 1] - Y[ey], Z[ez + 1] - Z[ez],
-                      a, b, Kb);
+        if (nc == 3)
+          element_block(Cel + 36 * (size_t)e, X[ex + 1] - X[ex], Y[ey + 1] - Y[ey],
+                        Z[ez + 1] - Z[ez], a, b, Kb);
+        else
+          Kb[0] = darcy_entry(perm + 3 * (size_t)e, X[ex + 1] - X[ex], Y[ey + 1] - Y[ey],
+                              Z[ez + 1] - Z[ez], a, b);
         bool ov = ecnt[eo0 + ex] * ecnt[eo1 + ey] * ecnt[eo2 + ez] >= 2;
-        for (int q = 0; q < 9; ++q) {
+        for (int q = 0; q < nc2; ++q) {
           KA[q] += Kb[q];
           if (ov) KO[q] += Kb[q];
         }
@@ -87,17 +94,17 @@ __global__ void __launch_bounds__(128)
   const int nnx = nx + 1, nny = ny + 1;
   const int g = gi + nnx * (gj + nny * gk), g2 = i2 + nnx * (j2 + nny * k2);
   const BandLayout L = lay[j];
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 3; ++c) {
-      int rd = 3 * g + r, cd = 3 * g2 + c;
-      double a = KA[3 * r + c], o = KO[3 * r + c];
+  for (int r = 0; r < nc; ++r)
+    for (int c = 0; c < nc; ++c) {
+      int rd = nc * g + r, cd = nc * g2 + c;
+      double a = KA[nc * r + c], o = KO[nc * r + c];
       if (mask[rd] || mask[cd]) {
         a = (rd == cd) ? 1.0 : 0.0;
         o = 0.0;
       }
-      double bv = Xneu[S.x_neu + 3 * l + r] * o * Xneu[S.x_neu + 3 * l2 + c];
-      bl[3 * r + c] = bv;
-      int R = 3 * l + r, C = 3 * l2 + c;
+      double bv = Xneu[S.x_neu + nc * l + r] * o * Xneu[S.x_neu + nc * l2 + c];
+      bl[nc * r + c] = bv;
+      int R = nc * l + r, C = nc * l2 + c;
       if (R >= C) tile_at(poolS, L, R >> 5, (R >> 5) - (C >> 5))[(C & 31) * 32 + (R & 31)] = a - sigma * bv;
     }
 }
@@ -107,9 +114,10 @@ __global__ void k_bloc_mv(const SubDesc *subs, const double *__restrict__ Bloc,
                           long long stride, int p) {
   const int j = blockIdx.y;
   const SubDesc &S = subs[j];
+  const int nc = S.nc;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 3 * S.nbox.count()) return;
-  int l = t / 3, r = t - 3 * l;
+  if (t >= nc * S.nbox.count()) return;
+  int l = t / nc, r = t - nc * l;
   int gi, gj, gk;
   S.nbox.global(l, gi, gj, gk);
   double acc[kLanczosBlock];
@@ -119,11 +127,11 @@ __global__ void k_bloc_mv(const SubDesc *subs, const double *__restrict__ Bloc,
   for (int s = 0; s < 27; ++s) {
     int l2 = S.nbox.local(gi + s % 3 - 1, gj + (s / 3) % 3 - 1, gk + s / 9 - 1);
     if (l2 < 0) continue;
-    const double *bl = Bloc + (S.b_neu + (long long)l * 27 + s) * 9 + 3 * r;
-    for (int c = 0; c < 3; ++c) {
+    const double *bl = Bloc + (S.b_neu + (long long)l * 27 + s) * (nc * nc) + nc * r;
+    for (int c = 0; c < nc; ++c) {
       double bv = bl[c];
       if (bv == 0.0) continue;
-      const double *tr = Tj + (long long)(3 * l2 + c) * p;
+      const double *tr = Tj + (long long)(nc * l2 + c) * p;
 #pragma unroll
       for (int q = 0; q < kLanczosBlock; ++q)
         if (q < p) acc[q] += bv * tr[q];
@@ -670,11 +678,12 @@ __global__ void k_build_Z(const SubDesc *subs, const double *P, int ldp, long lo
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)S.n_int * S.m) return;
   int row = (int)(t / S.m), k = (int)(t - (long long)row * S.m);
-  int node = row / 3, comp = row - 3 * node;
+  const int nc = S.nc;
+  int node = row / nc, comp = row - nc * node;
   int gi, gj, gk;
   S.ibox.global(node, gi, gj, gk);
   int ln = S.nbox.local(gi, gj, gk);
-  int nd = 3 * ln + comp;
+  int nd = nc * ln + comp;
   Zp[S.z_off + t] = Xneu[S.x_neu + nd] * P[j * sp + (long long)nd * ldp + k];
 }
 
@@ -685,9 +694,10 @@ __global__ void k_AZ(const SubDesc *subs, int nnx, int nny, int nnz, const int32
   const SubDesc &S = subs[j];
   const int m = S.m;
   if (m == 0) return;
+  const int nc = S.nc;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 3 * S.nbox.count()) return;
-  int l = t / 3, r = t - 3 * l;
+  if (t >= nc * S.nbox.count()) return;
+  int l = t / nc, r = t - nc * l;
   int gi, gj, gk;
   S.nbox.global(l, gi, gj, gk);
   int g = gi + nnx * (gj + nny * gk);
@@ -699,9 +709,9 @@ __global__ void k_AZ(const SubDesc *subs, int nnx, int nny, int nnz, const int32
     int i2 = g2 % nnx, rr = g2 / nnx, j2 = rr % nny, k2 = rr / nny;
     int l2 = S.ibox.local(i2, j2, k2);
     if (l2 < 0) continue;
-    for (int c = 0; c < 3; ++c) {
-      double a = val[9 * (size_t)pidx + 3 * r + c];
-      const double *zr = Zp + S.z_off + (long long)(3 * l2 + c) * m;
+    for (int c = 0; c < nc; ++c) {
+      double a = val[(size_t)nc * nc * pidx + nc * r + c];
+      const double *zr = Zp + S.z_off + (long long)(nc * l2 + c) * m;
 #pragma unroll
       for (int q = 0; q < kMaxModes; ++q)
         if (q < m) acc[q] += a * zr[q];
@@ -734,9 +744,9 @@ __global__ void __launch_bounds__(256)
       for (int q = 0; q < ex * ey * ez; ++q) {
         int ii = lo[0] + q % ex, rr = q / ex, jj = lo[1] + rr % ey, kk = lo[2] + rr / ey;
         int lj = Sj.ibox.local(ii, jj, kk), lk = Sk.nbox.local(ii, jj, kk);
-        for (int c = 0; c < 3; ++c)
-          s += Zp[Sj.z_off + (long long)(3 * lj + c) * mj + a] *
-               Yp[yoff[pr.y] + (long long)(3 * lk + c) * mk + b];
+        for (int c = 0; c < Sj.nc; ++c)
+          s += Zp[Sj.z_off + (long long)(Sj.nc * lj + c) * mj + a] *
+               Yp[yoff[pr.y] + (long long)(Sj.nc * lk + c) * mk + b];
       }
     }
     AH[(long long)(Sj.coff + a) * nH + Sk.coff + b] = s;
@@ -799,7 +809,9 @@ __global__ void k_rigid_modes(const SubDesc *subs, int npad, const double *__res
   if (t >= (long long)npad * ld) return;
   const int row = (int)(t / ld), k = (int)(t - (long long)row * ld);
   double v = 0.0;
-  if (row < S.n_neu && k < 6) {
+  if (S.nc == 1) {                // scalar problem: the constants
+    v = (row < S.n_neu && k == 0) ? 1.0 : 0.0;
+  } else if (row < S.n_neu && k < 6) {
     const int node = row / 3, comp = row - 3 * node;
     int gi, gj, gk;
     S.nbox.global(node, gi, gj, gk);
@@ -841,12 +853,13 @@ void launch_pou_neumann(const SubDesc *d_subs, int nsub, int max_nodes, const in
 void launch_neumann_assemble(const SubDesc *d_subs, const BandLayout *d_lay, int nsub,
                              int max_nodes, int nx, int ny, int nz, const double *X,
                              const double *Y, const double *Z, const double *Cel,
+                             const double *perm,
                              const int *ecnt, const int ecnt_off[3], const uint8_t *mask,
                              const double *Xneu, double sigma, double *poolS, double *Bloc,
                              cudaStream_t s) {
   long long tot = (long long)max_nodes * 27;
   dim3 g((unsigned)((tot + 127) / 128), nsub);
-  k_neumann_assemble<<<g, 128, 0, s>>>(d_subs, d_lay, nx, ny, nz, X, Y, Z, Cel, ecnt,
+  k_neumann_assemble<<<g, 128, 0, s>>>(d_subs, d_lay, nx, ny, nz, X, Y, Z, Cel, perm, ecnt,
                                        ecnt_off[0], ecnt_off[1], ecnt_off[2], mask, Xneu, sigma,
                                        poolS, Bloc); GENEO_COUNT_LAUNCH();
 }

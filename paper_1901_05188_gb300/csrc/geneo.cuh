@@ -16,6 +16,7 @@ void launch_pou_neumann(const SubDesc *d_subs, int nsub, int max_nodes, const in
 void launch_neumann_assemble(const SubDesc *d_subs, const BandLayout *d_lay, int nsub,
                              int max_nodes, int nx, int ny, int nz, const double *X,
                              const double *Y, const double *Z, const double *Cel,
+                             const double *perm,
                              const int *ecnt, const int ecnt_off[3], const uint8_t *mask,
                              const double *Xneu, double sigma, double *poolS, double *Bloc,
                              cudaStream_t s);

@@ -7,6 +7,8 @@ namespace geneo {
 
 struct AssemblyArgs {
   int nx, ny, nz, n_mat, n_dir;
+  int nc;                           // unknowns per node: 3 elasticity, 1 Darcy
+  const double *perm;               // Darcy: (Kx, Ky, Kz) per element (device)
   const double *X, *Y, *Z;          // node coordinates (device)
   const geneo_ortho *mats;          // device
   const int32_t *emat;              // device
@@ -14,7 +16,7 @@ struct AssemblyArgs {
   const int32_t *dir_dofs;          // device
   const double *dir_vals;           // device (may be null)
   const double *nodal;              // device (may be null)
-  double top_pressure;
+  double top_pressure;              // elasticity: top traction; Darcy: the uniform source f
   double *C0, *Cel;                 // per-material / per-element Voigt stiffness
   int32_t *cnt, *row_ptr, *col;
   double *val, *b, *g;
@@ -23,6 +25,8 @@ struct AssemblyArgs {
   DevStatus *status;
 };
 int launch_assembly(const AssemblyArgs &a, cudaStream_t s);
+// The scalar Darcy system (one unknown per node, 1x1 blocks in the same pattern).
+int launch_assembly_darcy(const AssemblyArgs &a, cudaStream_t s);
 // Right-hand side only (load kernel + stored lifting): b = mask ? lift : f + lift.
 int launch_load(const AssemblyArgs &a, cudaStream_t s);
 // Element stresses at the centres (6 per element, Voigt order) from u.
@@ -43,6 +47,7 @@ struct BSR {
   int nnode;
   const int32_t *row_ptr, *col;
   const double *val;
+  int nc = 3;                        // block size: unknowns per node (3 or 1)
 };
 
 // y = A x (FP64, warp per block row).

@@ -34,48 +34,59 @@ __device__ __forceinline__ double sum_partials(const double *part, int n, double
   return block_sum<NT>(v, sh);
 }
 
-// One lane per matrix row: lanes 3i..3i+2 of a warp hold the three rows of
-// block row 10g + i (i < 10; lanes 30, 31 idle), so every stored value takes
-// exactly one FMA and no sum crosses lanes -- FP64 issue, not bandwidth, is the
-// scarce resource on this GPU, and a shuffle reduction costs FP64 adds.  The
-// three lanes of a block row read the three rows of the same 72-byte blocks
-// and the same x entries, so their loads share L1 lines; results are written
-// to 30 consecutive entries of y.
-constexpr int kRowsPerWarp = 10;
+// One lane per matrix row: for 3x3 blocks lanes 3i..3i+2 of a warp hold the
+// three rows of block row 10g + i (i < 10; lanes 30, 31 idle), for the scalar
+// problem lane i holds row 32g + i; every stored value takes exactly one FMA
+// and no sum crosses lanes -- FP64 issue, not bandwidth, is the scarce
+// resource on this GPU, and a shuffle reduction costs FP64 adds.  The lanes of
+// a block row read the rows of the same blocks and the same x entries, so
+// their loads share L1 lines; results go to consecutive entries of y.
+template <int NC>
+struct RowMap {
+  static constexpr int kNodes = 32 / NC;          // block rows per warp
+};
 
+template <int NC>
 __device__ __forceinline__ double spmv_lane_row(const int32_t *__restrict__ rp,
                                                 const int32_t *__restrict__ col,
                                                 const double *__restrict__ val,
                                                 const double *__restrict__ x, int node, int r) {
   const int base = rp[node];
   const int nb = rp[node + 1] - base;
-  const double *v = val + 9 * (size_t)base + 3 * r;
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+  const double *v = val + (size_t)NC * NC * base + NC * r;
+  double a[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) a[c] = 0.0;
 #pragma unroll 9
   for (int b = 0; b < nb; ++b) {
-    const double *xb = x + 3 * __ldg(col + base + b);
-    a0 = fma(__ldg(v + 9 * b), __ldg(xb), a0);
-    a1 = fma(__ldg(v + 9 * b + 1), __ldg(xb + 1), a1);
-    a2 = fma(__ldg(v + 9 * b + 2), __ldg(xb + 2), a2);
+    const double *xb = x + NC * __ldg(col + base + b);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) a[c] = fma(__ldg(v + NC * NC * b + c), __ldg(xb + c), a[c]);
   }
-  return (a0 + a1) + a2;
+  double s = a[0];
+#pragma unroll
+  for (int c = 1; c < NC; ++c) s += a[c];
+  return s;
 }
 
+template <int NC>
 __global__ void __launch_bounds__(256) k_spmv(int nnode, const int32_t *__restrict__ rp,
                                               const int32_t *__restrict__ col,
                                               const double *__restrict__ val,
                                               const double *__restrict__ x,
                                               double *__restrict__ y) {
-  const int lane = threadIdx.x & 31, i = lane / 3, r = lane - 3 * i;
+  constexpr int kN = RowMap<NC>::kNodes;
+  const int lane = threadIdx.x & 31, i = lane / NC, r = lane - NC * i;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int g = warp; g * kRowsPerWarp < nnode; g += nw) {
-    const int node = g * kRowsPerWarp + i;
-    if (lane < 3 * kRowsPerWarp && node < nnode)
-      y[3 * node + r] = spmv_lane_row(rp, col, val, x, node, r);
+  for (int g = warp; g * kN < nnode; g += nw) {
+    const int node = g * kN + i;
+    if (lane < NC * kN && node < nnode)
+      y[NC * node + r] = spmv_lane_row<NC>(rp, col, val, x, node, r);
   }
 }
 
+template <int NC>
 __global__ void __launch_bounds__(NT) k_cg_spmv_pq(int nnode, const int32_t *__restrict__ rp,
                                                    const int32_t *__restrict__ col,
                                                    const double *__restrict__ val,
@@ -88,13 +99,14 @@ __global__ void __launch_bounds__(NT) k_cg_spmv_pq(int nnode, const int32_t *__r
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int nw = (gridDim.x * blockDim.x) >> 5;
   double acc = 0.0;
-  const int i = lane / 3, r = lane - 3 * i;
-  for (int g = warp; g * kRowsPerWarp < nnode; g += nw) {
-    const int node = g * kRowsPerWarp + i;
-    if (lane < 3 * kRowsPerWarp && node < nnode) {
-      const double yv = spmv_lane_row(rp, col, val, p, node, r);
-      q[3 * node + r] = yv;
-      acc = fma(p[3 * node + r], yv, acc);
+  constexpr int kN = RowMap<NC>::kNodes;
+  const int i = lane / NC, r = lane - NC * i;
+  for (int g = warp; g * kN < nnode; g += nw) {
+    const int node = g * kN + i;
+    if (lane < NC * kN && node < nnode) {
+      const double yv = spmv_lane_row<NC>(rp, col, val, p, node, r);
+      q[NC * node + r] = yv;
+      acc = fma(p[NC * node + r], yv, acc);
     }
   }
   double s = block_sum<NT>(acc, sh);
@@ -267,7 +279,11 @@ __global__ void k_sub(int n, const double *__restrict__ a, const double *__restr
 }  // namespace
 
 void launch_spmv(const BSR &A, const double *x, double *y, cudaStream_t s) {
-  k_spmv<<<NB * 4, 256, 0, s>>>(A.nnode, A.row_ptr, A.col, A.val, x, y); GENEO_COUNT_LAUNCH();
+  if (A.nc == 1) {
+    k_spmv<1><<<NB * 4, 256, 0, s>>>(A.nnode, A.row_ptr, A.col, A.val, x, y); GENEO_COUNT_LAUNCH();
+  } else {
+    k_spmv<3><<<NB * 4, 256, 0, s>>>(A.nnode, A.row_ptr, A.col, A.val, x, y); GENEO_COUNT_LAUNCH();
+  }
 }
 void launch_cg_init(int n, const double *b, double *x, double *r, CGScalars *cg, double *part,
                     cudaStream_t s) {
@@ -279,7 +295,11 @@ void launch_cg_init2(int n, const double *r, const double *z, double *p, CGScala
 }
 void launch_cg_spmv_pq(const BSR &A, const double *p, double *q, CGScalars *cg, double *part,
                        cudaStream_t s) {
-  k_cg_spmv_pq<<<NB * 4, NT, 0, s>>>(A.nnode, A.row_ptr, A.col, A.val, p, q, cg, part); GENEO_COUNT_LAUNCH();
+  if (A.nc == 1) {
+    k_cg_spmv_pq<1><<<NB * 4, NT, 0, s>>>(A.nnode, A.row_ptr, A.col, A.val, p, q, cg, part); GENEO_COUNT_LAUNCH();
+  } else {
+    k_cg_spmv_pq<3><<<NB * 4, NT, 0, s>>>(A.nnode, A.row_ptr, A.col, A.val, p, q, cg, part); GENEO_COUNT_LAUNCH();
+  }
 }
 void launch_cg_update_xr(int n, const double *p, const double *q, double *x, double *r,
                          CGScalars *cg, double *part, double *alphas, cudaStream_t s) {

@@ -447,10 +447,11 @@ __global__ void __launch_bounds__(kClWarps * 32)
   for (int l = threadIdx.x; l < npad; l += blockDim.x) {
     T v = T(0);
     if (l < n) {
-      int node = l / 3, comp = l - 3 * node;
+      const int nc = S.nc;
+      int node = l / nc, comp = l - nc * node;
       int gi, gj, gk;
       S.ibox.global(node, gi, gj, gk);
-      v = T(r[3 * (gi + nnx * (gj + nny * gk)) + comp]);
+      v = T(r[nc * (gi + nnx * (gj + nny * gk)) + comp]);
     }
     y[l] = v;
   }
@@ -484,10 +485,11 @@ __global__ void __launch_bounds__(kClWarps * 32)
   for (int l = threadIdx.x; l < npad; l += blockDim.x) {
     T v = T(0);
     if (l < n) {
-      int node = l / 3, comp = l - 3 * node;
+      const int nc = S.nc;
+      int node = l / nc, comp = l - nc * node;
       int gi, gj, gk;
       S.ibox.global(node, gi, gj, gk);
-      v = T(r[3 * (gi + nnx * (gj + nny * gk)) + comp]);
+      v = T(r[nc * (gi + nnx * (gj + nny * gk)) + comp]);
     }
     y[l] = v;
   }

@@ -61,7 +61,8 @@ def request_memory(problem, prec):
     keep = []
     mesh = GeneoSolver.mesh_of(problem, keep)
     a, s = geneo_estimate_workspace_bytes(mesh, GeneoSolver.partition_of(problem),
-                                          GeneoSolver.modes_of(problem), prec)
+                                          GeneoSolver.modes_of(problem), prec,
+                                          GeneoSolver.unknowns_per_node(problem))
     return int(a + s)
 
 
@@ -96,7 +97,8 @@ class GpuSlotExecutor:
         s = self._slot(slot)
         with torch.cuda.stream(self.streams[slot]):
             if reuse:
-                s.set_load(req.problem.get("nodal_load"), req.problem["top_pressure"])
+                scalar = req.problem["source" if req.problem.get("kind") == "darcy" else "top_pressure"]
+                s.set_load(req.problem.get("nodal_load"), scalar)
             else:
                 s.assemble(req.problem)
                 s.setup(req.problem, req.prec)
@@ -309,7 +311,7 @@ def run_poisson(server, problems, rate_hz, seed=0, prec=0, tol=1e-8, keys=None):
 
 
 def serve_benchmark(n=10, seed=4, prec=1, slots=4, rate_factors=(None, 0.5), tol=1e-8,
-                    dof_lo=2e4, dof_hi=2e6, warmup=True):
+                    dof_lo=2e4, dof_hi=2e6, warmup=True, darcy_frac=0.0):
     """Serve a seeded request stream; one summary per arrival pattern.
 
     rate_factors: None = every request arrives at t = 0 (a burst, which gives
@@ -318,7 +320,7 @@ def serve_benchmark(n=10, seed=4, prec=1, slots=4, rate_factors=(None, 0.5), tol
     summaries.
     """
     from workloads.serving import dofs_of, request_stream
-    base = request_stream(n, seed=seed, dof_lo=dof_lo, dof_hi=dof_hi)
+    base = request_stream(n, seed=seed, dof_lo=dof_lo, dof_hi=dof_hi, darcy_frac=darcy_frac)
     if warmup:   # load the library and build every kernel variant once
         from workloads import config
         w = GeneoServer(slots=1)
@@ -326,6 +328,7 @@ def serve_benchmark(n=10, seed=4, prec=1, slots=4, rate_factors=(None, 0.5), tol
         w.close()
     out = dict(requests=n, seed=seed, slots=slots, precision="mixed" if prec else "fp64",
                dofs=[dofs_of(p) for _, p, _ in base],
+               darcy=sum(1 for _, p, _ in base if p.get("kind") == "darcy"),
                repeats=sum(1 for i, (k, _, _) in enumerate(base)
                            if any(k == kk for kk, _, _ in base[:i])),
                runs=[])

@@ -13,13 +13,12 @@ def require_gpu():
     return pkg
 
 
-def bsr_to_csr(rp, col, val, n):
-    """Expand the library's 3x3 BSR into a scipy CSR matrix."""
-    nb = len(col)
+def bsr_to_csr(rp, col, val, n, nc=3):
+    """Expand the library's nc x nc block BSR into a scipy CSR matrix."""
     rows = np.repeat(np.arange(n), np.diff(rp))
-    R = (3 * rows[:, None, None] + np.arange(3)[None, :, None]).repeat(3, axis=2)
-    Cc = (3 * col[:, None, None] + np.arange(3)[None, None, :]).repeat(3, axis=1)
-    return sp.csr_matrix((val.reshape(-1), (R.reshape(-1), Cc.reshape(-1))), shape=(3 * n, 3 * n))
+    R = (nc * rows[:, None, None] + np.arange(nc)[None, :, None]).repeat(nc, axis=2)
+    Cc = (nc * col[:, None, None] + np.arange(nc)[None, None, :]).repeat(nc, axis=1)
+    return sp.csr_matrix((val.reshape(-1), (R.reshape(-1), Cc.reshape(-1))), shape=(nc * n, nc * n))
 
 
 def rel(a, b):

@@ -7,8 +7,12 @@ sequence of {0, +-45, 90} plies of two elements each, and the partition gives
 subdomains of about 16 x 8 x 12 elements (the size of the 64x32x24 workload's
 subdomains) with overlap 1 and the threshold mode rule capped at 20.  A share
 of the requests repeats an earlier structure with a new load (another top
-pressure), which the server can answer from resident factors.  Arrival times
-are a Poisson process.
+pressure), which the server can answer from resident factors.  With
+`darcy_frac` > 0 that share of the new structures is instead a scalar Darcy
+block (one unknown per node) with the layered permeability of
+`workloads.darcy`, the same log-uniform unknown count, SPE10-like 60:220:85
+proportions and an in-plane decomposition over the full height (about 10 x 12
+cells per subdomain, which keeps a subdomain's local vector in shared memory).  Arrival times are a Poisson process.
 """
 from __future__ import annotations
 
@@ -16,6 +20,7 @@ import math
 
 import numpy as np
 
+from .darcy import make_darcy
 from .laminate import make_block
 
 SUB_ELEMS = (16, 8, 12)
@@ -34,7 +39,16 @@ def block_for_dofs(dofs, rng, name):
     return make_block(nx, ny, nz, ang, partition=part, modes=modes, name=name)
 
 
-def request_stream(n, seed=4, dof_lo=2e4, dof_hi=2e6, repeat_frac=0.25, rate_hz=None):
+def darcy_for_dofs(dofs, rng, name):
+    """A Darcy block with about `dofs` unknowns in SPE10's 60:220:85 proportions."""
+    a = max((dofs / (60.0 * 220.0 * 85.0)) ** (1.0 / 3.0), 0.05)
+    nx, ny, nz = max(4, round(60 * a)), max(4, round(220 * a)), max(3, round(85 * a))
+    part = (max(1, min(nx // 2, math.ceil(nx / 10))), max(1, min(ny // 2, math.ceil(ny / 12))), 1, 1)
+    return make_darcy(nx, ny, nz, seed=int(rng.integers(1 << 30)), partition=part, name=name)
+
+
+def request_stream(n, seed=4, dof_lo=2e4, dof_hi=2e6, repeat_frac=0.25, rate_hz=None,
+                   darcy_frac=0.0):
     """n requests as (key, problem, arrival_offset_s).
 
     Without a rate every offset is 0 (a burst); with one, offsets are the
@@ -48,13 +62,17 @@ def request_stream(n, seed=4, dof_lo=2e4, dof_hi=2e6, repeat_frac=0.25, rate_hz=
         if structures and rng.random() < repeat_frac:
             key, base = structures[int(rng.integers(len(structures)))]
             p = dict(base)
-            p["top_pressure"] = float(rng.uniform(0.5, 2.0))
+            p["source" if p.get("kind") == "darcy" else "top_pressure"] = float(rng.uniform(0.5, 2.0))
             p["name"] = f"{key}+load{i}"
         else:
             dofs = math.exp(rng.uniform(math.log(dof_lo), math.log(dof_hi)))
             key = f"s{i}"
-            p = block_for_dofs(dofs, rng, key)
-            p["top_pressure"] = float(rng.uniform(0.5, 2.0))
+            if darcy_frac > 0 and rng.random() < darcy_frac:
+                p = darcy_for_dofs(dofs, rng, key)
+                p["source"] = float(rng.uniform(0.5, 2.0))
+            else:
+                p = block_for_dofs(dofs, rng, key)
+                p["top_pressure"] = float(rng.uniform(0.5, 2.0))
             structures.append((key, p))
         out.append((key, p, t))
         if rate_hz:
@@ -63,4 +81,5 @@ def request_stream(n, seed=4, dof_lo=2e4, dof_hi=2e6, repeat_frac=0.25, rate_hz=
 
 
 def dofs_of(p):
-    return 3 * (p["nx"] + 1) * (p["ny"] + 1) * (p["nz"] + 1)
+    nc = 1 if p.get("kind") == "darcy" else 3
+    return nc * (p["nx"] + 1) * (p["ny"] + 1) * (p["nz"] + 1)
