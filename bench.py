@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-darcy", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=10,
                     help="requests of the serving sample (uneven laminate blocks)")
     return ap.parse_args()
@@ -413,15 +414,38 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_serve and args.serve_requests > 0:
         from paper_1901_05188_gb300.serve import serve_benchmark
         sv = serve_benchmark(n=args.serve_requests, seed=4, prec=pkg.GENEO_MIXED_FP32, slots=4,
-                             rate_factors=(None, 0.5))
-        serving = dict(workload=f"{sv['requests']} laminate blocks, {min(sv['dofs'])}-"
-                                f"{max(sv['dofs'])} dofs (log-uniform 2e4-2e6, seed 4), "
-                                f"{sv['repeats']} repeated structures with new loads",
+                             rate_factors=(None, 0.5), darcy_frac=0.3)
+        serving = dict(workload=f"{sv['requests']} requests: {sv['requests'] - sv['darcy']} laminate "
+                                f"blocks and {sv['darcy']} Darcy blocks (layered permeability), "
+                                f"{min(sv['dofs'])}-{max(sv['dofs'])} unknowns (log-uniform 2e4-2e6, "
+                                f"seed 4), {sv['repeats']} repeated structures with new loads",
                        precision=sv["precision"], slots=sv["slots"],
                        runs=[{k: r[k] for k in ("arrivals", "n", "p50_ms", "p99_ms", "mean_ms",
                                                 "solves_per_s", "reused", "peak_inflight",
                                                 "peak_mem_gb", "failed") if k in r}
                              for r in sv["runs"]])
+
+    # the paper's second application at its full grid: Darcy on SPE10's 60x220x85
+    # cells with a synthetic layered permeability (contrast 1.4e10), FP64
+    darcy = None
+    if rank == 0 and world == 1 and not args.no_darcy:
+        from workloads.darcy import darcy_config
+        pdz = darcy_config("d-spe10")
+        sd = pkg.GeneoSolver()
+        for _ in range(2):                       # warm-up, then one timed solve
+            e0.record(stream)
+            sd.assemble(pdz)
+            sd.setup(pdz, pkg.GENEO_FP64)
+            _, std = sd.solve(tol=TOL, max_it=5000)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+        darcy = dict(workload="Darcy, 60x220x85 cells (1,159,366 unknowns), 6x18 subdomains, "
+                              "synthetic layered log-normal permeability, f = 1",
+                     ms_per_solve=e0.elapsed_time(e1), iterations=std["iterations"],
+                     n_coarse=std["n_coarse"], rel_res_true=std["rel_res_true"],
+                     phases_ms=dict(assemble=std["ms_assemble"], setup_eig_coarse=std["ms_setup_eig"],
+                                    setup_factor=std["ms_setup_factor"], solve=std["ms_solve"]))
+        sd.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -442,7 +466,8 @@ def run_ours(args):
                     bytes_per_iter=st["bytes_per_iter"], kernels=kernels,
                     schwarz_launch=dict(cluster=st["schwarz_cluster"], rows=st["schwarz_rows"],
                                         chosen_by="set-up autotuner"),
-                    accuracy_vs_oracle=acc, mixed_precision=mixed, serving=serving)
+                    accuracy_vs_oracle=acc, mixed_precision=mixed, serving=serving,
+                    darcy_spe10=darcy)
         print(json.dumps(line))
     s.close()
     if world > 1:
