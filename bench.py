@@ -413,12 +413,12 @@ def run_ours(args):
     serving = None
     if rank == 0 and world == 1 and not args.no_serve and args.serve_requests > 0:
         from paper_1901_05188_gb300.serve import serve_benchmark
-        sv = serve_benchmark(n=args.serve_requests, seed=4, prec=pkg.GENEO_MIXED_FP32, slots=4,
+        sv = serve_benchmark(n=args.serve_requests, seed=6, prec=pkg.GENEO_MIXED_FP32, slots=4,
                              rate_factors=(None, 0.5), darcy_frac=0.3)
         serving = dict(workload=f"{sv['requests']} requests: {sv['requests'] - sv['darcy']} laminate "
                                 f"blocks and {sv['darcy']} Darcy blocks (layered permeability), "
                                 f"{min(sv['dofs'])}-{max(sv['dofs'])} unknowns (log-uniform 2e4-2e6, "
-                                f"seed 4), {sv['repeats']} repeated structures with new loads",
+                                f"seed 6), {sv['repeats']} repeated structures with new loads",
                        precision=sv["precision"], slots=sv["slots"],
                        runs=[{k: r[k] for k in ("arrivals", "n", "p50_ms", "p99_ms", "mean_ms",
                                                 "solves_per_s", "reused", "peak_inflight",

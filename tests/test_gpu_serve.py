@@ -12,6 +12,7 @@ import pytest
 
 from gpu_common import require_gpu
 from workloads import config, make_block
+from workloads.darcy import darcy_config
 
 pytestmark = pytest.mark.gpu
 
@@ -27,6 +28,7 @@ def _problems():
         ("tiny", config("tiny")),
         ("wr", make_block(16, 12, 8, [0, 90, 90, 0], partition=(2, 3, 2, 1),
                           modes=thr, wrinkle=(10.0, 4.0), name="wr")),
+        ("darcy", darcy_config("d-small")),
     ]
 
 
