@@ -401,8 +401,11 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         mixed = dict(ms_per_solve=e0.elapsed_time(e1) / args.steps, iterations=stm["iterations"],
-                     rel_res_true=stm["rel_res_true"], ms_setup=stm["ms_setup_eig"] + stm["ms_setup_factor"],
-                     ms_solve=stm["ms_solve"])
+                     rel_res_true=stm["rel_res_true"],
+                     phases_ms=dict(setup_eig_coarse=stm["ms_setup_eig"],
+                                    setup_factor=stm["ms_setup_factor"], solve=stm["ms_solve"]),
+                     schwarz_launch=dict(cluster=stm["schwarz_cluster"], rows=stm["schwarz_rows"],
+                                         staged=stm["schwarz_staged"]))
         if acc is not None:
             u = u_dev.cpu().numpy()
             us = u[::g["sample_stride"]][:len(g["u_samples"])]
@@ -465,6 +468,7 @@ def run_ours(args):
                                    setup_factor=st["ms_setup_factor"], solve=st["ms_solve"]),
                     bytes_per_iter=st["bytes_per_iter"], kernels=kernels,
                     schwarz_launch=dict(cluster=st["schwarz_cluster"], rows=st["schwarz_rows"],
+                                        staged=st["schwarz_staged"],
                                         chosen_by="set-up autotuner"),
                     accuracy_vs_oracle=acc, mixed_precision=mixed, serving=serving,
                     darcy_spe10=darcy)

@@ -125,6 +125,7 @@ typedef struct {
   int lanczos_steps;              /* block-Lanczos steps of the last set-up (two band sweeps each) */
   int schwarz_cluster;            /* CTAs per subdomain chosen for the local solves */
   int schwarz_rows;               /* tile rows per cluster barrier chosen for them */
+  int schwarz_staged;             /* 1 if their tiles are staged in shared memory by bulk copies */
 } geneo_stats;
 
 /* Create a context whose work runs on `cuda_stream` (a cudaStream_t; NULL =

@@ -64,7 +64,8 @@ class geneo_stats(C.Structure):
                 ("eig_max_residual", C.c_double), ("failed_subdomain", C.c_int),
                 ("flexible", C.c_int), ("eig_cycles", C.c_int),
                 ("lanczos_steps", C.c_int),
-                ("schwarz_cluster", C.c_int), ("schwarz_rows", C.c_int)]
+                ("schwarz_cluster", C.c_int), ("schwarz_rows", C.c_int),
+                ("schwarz_staged", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

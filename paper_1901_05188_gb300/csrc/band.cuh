@@ -47,19 +47,26 @@ int launch_extract_interior(const SubDesc *d_subs, const BandLayout *d_lay, int 
                             int max_nodes, int nnx, int nny, int nnz, const int32_t *rp,
                             const double *val, T *pool, cudaStream_t s);
 
-// Opt in to the shared memory the Schwarz solve needs (call before capture).
+// Opt in to the shared memory the Schwarz solve needs (call before capture);
+// w_max is the largest tile half-bandwidth of the local factors.
 template <typename T>
-int prepare_schwarz_solve(int npad_max);
+int prepare_schwarz_solve(int npad_max, int w_max);
 
 // One-level Schwarz local solves: x_j = A_j^-1 R_j r for every subdomain, one
 // thread-block cluster of `cluster` CTAs (1, 2, 4 or 8) per subdomain, `rows`
 // tile rows (1, 2 or 4) per cluster barrier, or rows = 0 for the look-ahead
-// sweep (the next row's far tiles overlap the current row's chain).
+// sweep (the next row's far tiles overlap the current row's chain).  With
+// staged = 1 (rows 1 or 2 only) every step's tiles are copied into shared
+// memory a step ahead by bulk asynchronous copies; a copy that does not land
+// within about a second sets GENEO_ERR_TIMEOUT in *status.
 template <typename T>
 int launch_schwarz_solve(const SubDesc *d_subs, const BandLayout *d_lay, int nsub,
-                         int npad_max, int nnx, int nny, const T *poolL, const T *poolU,
-                         const double *r, T *xloc, const CGScalars *cg, int cluster, int rows,
-                         DevStatus *status, cudaStream_t s);
+                         int npad_max, int w_max, int nnx, int nny, const T *poolL,
+                         const T *poolU, const double *r, T *xloc, const CGScalars *cg,
+                         int cluster, int rows, int staged, DevStatus *status, cudaStream_t s);
+// True when the staged launch (cluster, rows) fits in shared memory.
+template <typename T>
+bool schwarz_staged_fits(int npad_max, int w_max, int cluster, int rows);
 // Cluster size that fills the GPU: the largest power of two <= 8 with
 // 2 * nsub * size <= number of SMs (at least 1).
 int schwarz_cluster_size(int nsub, int sm_count);

@@ -807,6 +807,23 @@ double default_threshold(geneo_ctx *c, const SubDesc &S, int O) {
 }  // namespace
 
 // Apply the preconditioner z = M^-1 r on stream s (device vectors).
+// The local solves x_j = A_j^-1 R_j r of every subdomain in launch shape
+// (cluster, rows, staged).
+static int schwarz_local_solves(geneo_ctx *c, const double *r, const CGScalars *cg, int cluster,
+                                int rows, int staged, cudaStream_t s) {
+  Precond &pc = c->pc;
+  const int nnx = c->nx + 1, nny = c->ny + 1;
+  if (pc.prec == GENEO_MIXED_FP32)
+    return launch_schwarz_solve<float>(pc.d_subs, pc.d_lay_int, pc.nsub, pc.npad_int_max,
+                                       pc.w_int_max, nnx, nny, (const float *)pc.facL,
+                                       (const float *)pc.facU, r, (float *)pc.xloc, cg, cluster,
+                                       rows, staged, c->status, s);
+  return launch_schwarz_solve<double>(pc.d_subs, pc.d_lay_int, pc.nsub, pc.npad_int_max,
+                                      pc.w_int_max, nnx, nny, (const double *)pc.facL,
+                                      (const double *)pc.facU, r, (double *)pc.xloc, cg, cluster,
+                                      rows, staged, c->status, s);
+}
+
 static int precond_apply(geneo_ctx *c, const double *r, double *z, const CGScalars *cg,
                          cudaStream_t s) {
   Precond &pc = c->pc;
@@ -817,20 +834,12 @@ static int precond_apply(geneo_ctx *c, const double *r, double *z, const CGScala
                         pc.AHinv, pc.nH, pc.mcap, cg, s);
   int st;
   const int pou = pc.schwarz == GENEO_AS_POU;
+  if ((st = schwarz_local_solves(c, r, cg, pc.cluster, pc.rows, pc.staged, s))) return st;
   if (pc.prec == GENEO_MIXED_FP32) {
-    if ((st = launch_schwarz_solve<float>(pc.d_subs, pc.d_lay_int, pc.nsub, pc.npad_int_max, nnx,
-                                          nny, (const float *)pc.facL, (const float *)pc.facU, r,
-                                          (float *)pc.xloc, cg, pc.cluster, pc.rows, c->status, s)))
-      return st;
     launch_schwarz_gather<float>(c->nx, c->ny, c->nz, pc.part.px, pc.part.py, pc.d_cand,
                                  pc.cand_off, pc.d_subs, (const float *)pc.xloc, pc.Zp,
                                  coarse ? pc.yH : nullptr, pou, c->mask, z, cg, s);
   } else {
-    if ((st = launch_schwarz_solve<double>(pc.d_subs, pc.d_lay_int, pc.nsub, pc.npad_int_max,
-                                           nnx, nny, (const double *)pc.facL,
-                                           (const double *)pc.facU, r, (double *)pc.xloc, cg,
-                                           pc.cluster, pc.rows, c->status, s)))
-      return st;
     launch_schwarz_gather<double>(c->nx, c->ny, c->nz, pc.part.px, pc.part.py, pc.d_cand,
                                   pc.cand_off, pc.d_subs, (const double *)pc.xloc, pc.Zp,
                                   coarse ? pc.yH : nullptr, pou, c->mask, z, cg, s);
@@ -1164,39 +1173,41 @@ int geneo_estimate_workspace_bytes(const geneo_mesh *mesh, int unknowns_per_node
 
 // ---- autotuning of the Schwarz local-solve launch ---------------------------
 // The launch shape of the local solves (CTAs per subdomain, tile rows per
-// cluster barrier) is chosen by timing the candidates on the factors just
-// built; the choice is cached for the process, keyed by precision, subdomain
-// count, largest padded subdomain, largest band width and SM count, so a
-// repeated set-up of the same shape does not tune again.  GENEO_SCHWARZ_CLUSTER
-// and GENEO_SCHWARZ_ROWS (0 = the look-ahead sweep) fix either dimension.
+// cluster barrier, tiles staged in shared memory or read from global memory)
+// is chosen by timing the candidates on the factors just built; the choice is
+// cached for the process, keyed by precision, subdomain count, largest padded
+// subdomain, largest band width and SM count, so a repeated set-up of the same
+// shape does not tune again.  GENEO_SCHWARZ_CLUSTER, GENEO_SCHWARZ_ROWS
+// (0 = the look-ahead sweep) and GENEO_SCHWARZ_STAGED (0 or 1) fix a
+// dimension each.
 struct TuneKey {
   int prec, nsub, npad, w, sms;
   bool operator<(const TuneKey &o) const {
     return std::tie(prec, nsub, npad, w, sms) < std::tie(o.prec, o.nsub, o.npad, o.w, o.sms);
   }
 };
+struct TuneChoice {
+  int cluster, rows, staged;
+};
 static std::mutex g_tune_mu;
-static std::map<TuneKey, std::pair<int, int>> g_tune;
+static std::map<TuneKey, TuneChoice> g_tune;
 
+// Value of an environment variable if it is one of `allowed`, else -1.
 static int env_choice(const char *name, std::initializer_list<int> allowed) {
   const char *e = std::getenv(name);
-  if (!e) return 0;
-  int v = std::atoi(e);
+  if (!e || !e[0]) return -1;
+  char *end = nullptr;
+  long v = std::strtol(e, &end, 10);
+  if (*end) return -1;
   for (int a : allowed)
-    if (a == v) return v;
-  return 0;
+    if (a == v) return (int)v;
+  return -1;
 }
 
-static int schwarz_once(geneo_ctx *c, int cluster, int rows, cudaStream_t s) {
-  Precond &pc = c->pc;
-  const int nnx = c->nx + 1, nny = c->ny + 1;
-  if (pc.prec == GENEO_MIXED_FP32)
-    return launch_schwarz_solve<float>(pc.d_subs, pc.d_lay_int, pc.nsub, pc.npad_int_max, nnx, nny,
-                                       (const float *)pc.facL, (const float *)pc.facU, c->b,
-                                       (float *)pc.xloc, nullptr, cluster, rows, c->status, s);
-  return launch_schwarz_solve<double>(pc.d_subs, pc.d_lay_int, pc.nsub, pc.npad_int_max, nnx, nny,
-                                      (const double *)pc.facL, (const double *)pc.facU, c->b,
-                                      (double *)pc.xloc, nullptr, cluster, rows, c->status, s);
+static bool staged_fits(const Precond &pc, int C, int R) {
+  return pc.prec == GENEO_MIXED_FP32
+             ? schwarz_staged_fits<float>(pc.npad_int_max, pc.w_int_max, C, R)
+             : schwarz_staged_fits<double>(pc.npad_int_max, pc.w_int_max, C, R);
 }
 
 static int tune_schwarz(geneo_ctx *c, const SetupPlan &P, cudaStream_t s) {
@@ -1204,59 +1215,62 @@ static int tune_schwarz(geneo_ctx *c, const SetupPlan &P, cudaStream_t s) {
   const TuneKey key{(int)pc.prec, P.nsub, pc.npad_int_max, pc.w_int_max, pc.sms};
   const int fc = env_choice("GENEO_SCHWARZ_CLUSTER", {1, 2, 4, 8});
   const int fr = env_choice("GENEO_SCHWARZ_ROWS", {0, 1, 2, 4});
-  const char *fr_env = std::getenv("GENEO_SCHWARZ_ROWS");
-  const bool fr_set = fr_env && (fr || fr_env[0] == '0');
-  {
+  const int fs = env_choice("GENEO_SCHWARZ_STAGED", {0, 1});
+  const bool pinned = fc >= 0 || fr >= 0 || fs >= 0;
+  if (!pinned) {
     std::lock_guard<std::mutex> g(g_tune_mu);
     auto it = g_tune.find(key);
-    if (it != g_tune.end() && !fc && !fr_set) {
-      pc.cluster = it->second.first;
-      pc.rows = it->second.second;
+    if (it != g_tune.end()) {
+      pc.cluster = it->second.cluster;
+      pc.rows = it->second.rows;
+      pc.staged = it->second.staged;
       return GENEO_OK;
     }
   }
-  std::vector<int> cs, rs;
-  if (fc) {
-    cs = {fc};
-  } else {
-    // one wave of clusters: nsub * C CTAs on distinct SMs
-    for (int C : {1, 2, 4, 8})
-      if (C == 1 || P.nsub * C <= pc.sms) cs.push_back(C);
+  std::vector<TuneChoice> cand;
+  for (int C : {1, 2, 4, 8}) {
+    if (fc >= 0 ? C != fc : (C > 1 && P.nsub * C > pc.sms)) continue;   // one wave of clusters
+    for (int R : {0, 1, 2, 4}) {
+      if (fr >= 0 ? R != fr : (R == 4 && pc.prec != GENEO_MIXED_FP32)) continue;
+      for (int St : {0, 1}) {
+        if (fs >= 0 && St != fs) continue;
+        if (St && !staged_fits(pc, C, R)) continue;
+        cand.push_back({C, R, St});
+      }
+    }
   }
-  if (fr_set) rs = {fr};
-  else if (pc.prec == GENEO_MIXED_FP32) rs = {0, 1, 2, 4};
-  else rs = {0, 1, 2};
-  if (cs.size() * rs.size() == 1) {
-    pc.cluster = cs[0];
-    pc.rows = rs[0];
-    return GENEO_OK;
-  }
+  if (cand.empty()) return fail(GENEO_ERR_INVALID_ARG, "no Schwarz launch shape fits the pinned choice");
+  pc.cluster = cand[0].cluster;
+  pc.rows = cand[0].rows;
+  pc.staged = cand[0].staged;
+  if (cand.size() == 1) return GENEO_OK;
   cudaEvent_t e0, e1;
   GENEO_CUDA_TRY(cudaEventCreate(&e0));
   GENEO_CUDA_TRY(cudaEventCreate(&e1));
   float best = 1e30f;
   int st;
-  for (int C : cs)
-    for (int R : rs) {
-      if ((st = schwarz_once(c, C, R, s))) return st;          // warm-up
-      GENEO_CUDA_TRY(cudaEventRecord(e0, s));
-      for (int k = 0; k < 2; ++k)
-        if ((st = schwarz_once(c, C, R, s))) return st;
-      GENEO_CUDA_TRY(cudaEventRecord(e1, s));
-      GENEO_CUDA_TRY(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      GENEO_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-      if (ms < best) {
-        best = ms;
-        pc.cluster = C;
-        pc.rows = R;
-      }
+  for (const TuneChoice &t : cand) {
+    if ((st = schwarz_local_solves(c, c->b, nullptr, t.cluster, t.rows, t.staged, s))) return st;
+    GENEO_CUDA_TRY(cudaEventRecord(e0, s));
+    for (int k = 0; k < 2; ++k)
+      if ((st = schwarz_local_solves(c, c->b, nullptr, t.cluster, t.rows, t.staged, s))) return st;
+    GENEO_CUDA_TRY(cudaEventRecord(e1, s));
+    GENEO_CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    GENEO_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      pc.cluster = t.cluster;
+      pc.rows = t.rows;
+      pc.staged = t.staged;
     }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (!fc && !fr_set) {
+  if ((st = check_status(c))) return st;
+  if (!pinned) {
     std::lock_guard<std::mutex> g(g_tune_mu);
-    g_tune[key] = {pc.cluster, pc.rows};
+    g_tune[key] = {pc.cluster, pc.rows, pc.staged};
   }
   return GENEO_OK;
 }
@@ -1303,11 +1317,12 @@ int geneo_setup(geneo_ctx *c, const geneo_partition *part, const geneo_modes *mo
   GENEO_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
   pc.cluster = schwarz_cluster_size(P.nsub, sms);
   pc.rows = 1;
+  pc.staged = 0;
   pc.sms = sms;
   if (f32) {
-    if ((st = prepare_schwarz_solve<float>(pc.npad_int_max))) return fail(st, "subdomain too large for shared memory");
+    if ((st = prepare_schwarz_solve<float>(pc.npad_int_max, pc.w_int_max))) return fail(st, "subdomain too large for shared memory");
   } else {
-    if ((st = prepare_schwarz_solve<double>(pc.npad_int_max))) return fail(st, "subdomain too large for shared memory");
+    if ((st = prepare_schwarz_solve<double>(pc.npad_int_max, pc.w_int_max))) return fail(st, "subdomain too large for shared memory");
   }
   if (pc.coarse == GENEO_COARSE_GENEO && pc.mcap > 1 && pc.npad_neu_max * 8 + 16 * 32 * 8 > 227 * 1024)
     return fail(GENEO_ERR_INVALID_ARG, "subdomain too large for the eigensolver's shared memory");
@@ -1611,6 +1626,7 @@ extern "C" int geneo_solve(geneo_ctx *c, double tol, int max_it, double *u, gene
   out.lanczos_steps = pc.lanczos_steps;
   out.schwarz_cluster = pc.cluster;
   out.schwarz_rows = pc.rows;
+  out.schwarz_staged = pc.staged;
   if (!flexible && h.it > 0) {
     int k = std::min(h.it, kHistCap);
     std::vector<double> al(k), be(std::max(k - 1, 0));
@@ -1774,20 +1790,12 @@ extern "C" int geneo_profile(geneo_ctx *c, int what, int reps, double *ms_per_la
   cudaEvent_t e0, e1;
   GENEO_CUDA_TRY(cudaEventCreate(&e0));
   GENEO_CUDA_TRY(cudaEventCreate(&e1));
-  const int nnx = c->nx + 1, nny = c->ny + 1;
   int st = 0;
   for (int pass = 0; pass < 2 && !st; ++pass) {      // pass 0 warms up
     GENEO_CUDA_TRY(cudaEventRecord(e0, s));
     for (int i = 0; i < (pass ? reps : 1) && !st; ++i) {
       if (what == 0) {
-        st = f32 ? launch_schwarz_solve<float>(pc.d_subs, pc.d_lay_int, pc.nsub, pc.npad_int_max,
-                                               nnx, nny, (const float *)pc.facL,
-                                               (const float *)pc.facU, c->r, (float *)pc.xloc,
-                                               nullptr, pc.cluster, pc.rows, c->status, s)
-                 : launch_schwarz_solve<double>(pc.d_subs, pc.d_lay_int, pc.nsub,
-                                                pc.npad_int_max, nnx, nny,
-                                                (const double *)pc.facL, (const double *)pc.facU,
-                                                c->r, (double *)pc.xloc, nullptr, pc.cluster, pc.rows, c->status, s);
+        st = schwarz_local_solves(c, c->r, nullptr, pc.cluster, pc.rows, pc.staged, s);
       } else if (what == 1) {
         launch_spmv(A, c->r, c->q, s);
       } else if (what == 3) {

@@ -27,6 +27,7 @@ struct Precond {
   int nsub = 0;
   int cluster = 1;                // CTAs per subdomain in the Schwarz local solves
   int rows = 1;                   // tile rows per cluster barrier in the Schwarz local solves
+  int staged = 0;                 // Schwarz tiles staged in shared memory by bulk copies
   int sms = 0;                    // SM count of the device
   std::vector<SubDesc> subs;
   SubDesc *d_subs = nullptr;

@@ -53,6 +53,7 @@ __device__ __forceinline__ void far_tiles(int r, int dmax, int c, int &t0, int &
 
 template <typename T, int C, int R>
 struct Sweep {
+  static constexpr int kNearSlots = R > 1 ? R * (R - 1) / 2 : 1;
   const T *pool;
   BandLayout L;
   int c, nt, w;
@@ -88,16 +89,98 @@ struct Sweep {
   }
 };
 
+// Second half of a step, shared by the sweeps that load their tiles from
+// global memory and from shared-memory stages: per-CTA partials of the far
+// products to every CTA of the cluster, one cluster barrier, then the chain
+// warps finish the R rows (partials, couplings inside the group, inverted
+// diagonal block) and write y_I.
+template <typename T, int C, int R>
+__device__ __forceinline__ void step_tail(const cg::cluster_group &cluster,
+                                          const Sweep<T, C, R> &S, int step, T (&acc)[R][2],
+                                          const T (&dv)[R][8],
+                                          const T (&nv)[Sweep<T, C, R>::kNearSlots][8], T *y,
+                                          T *red, T *chn, T *part, int &buf) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = S.c, par = step & 1;
+#pragma unroll
+  for (int q = 0; q < R; ++q) red[(warp * R + q) * 32 + lane] = acc[q][0] + acc[q][1];
+  __syncthreads();
+  if (warp < kChain) {
+    // CTA partial of each row: warps w, w+4, w+8, w+12, then the four sums
+    T *cb = chn + (buf & 1) * (kChain * R * 32);
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      T s = red[(warp * R + q) * 32 + lane];
+#pragma unroll
+      for (int k = warp + kChain; k < kClWarps; k += kChain) s += red[(k * R + q) * 32 + lane];
+      cb[(warp * R + q) * 32 + lane] = s;
+    }
+    chain_bar();
+    ++buf;
+    T tot[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      tot[q] = cb[q * 32 + lane];
+#pragma unroll
+      for (int k = 1; k < kChain; ++k) tot[q] += cb[(k * R + q) * 32 + lane];
+    }
+    for (int dst = warp; dst < C; dst += kChain) {
+      T *p = cluster.map_shared_rank(part, dst);
+#pragma unroll
+      for (int q = 0; q < R; ++q) p[((par * R + q) * C + c) * 32 + lane] = tot[q];
+    }
+  }
+  cluster.sync();
+  if (warp < kChain) {
+    T yr[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (!S.valid(step, r)) break;
+      const int I = S.row(step, r);
+      T s = y[I * 32 + lane];
+#pragma unroll
+      for (int q = 0; q < C; ++q) s -= part[((par * R + r) * C + q) * 32 + lane];
+      if (r > 0) {                            // couplings to the rows solved in this step
+        T pn0 = T(0), pn1 = T(0);
+#pragma unroll
+        for (int d = 1; d <= r; ++d)
+#pragma unroll
+          for (int k = 0; k < 8; k += 2) {
+            pn0 += nv[r * (r - 1) / 2 + d - 1][k] * __shfl_sync(0xffffffffu, yr[r - d], warp * 8 + k);
+            pn1 += nv[r * (r - 1) / 2 + d - 1][k + 1] *
+                   __shfl_sync(0xffffffffu, yr[r - d], warp * 8 + k + 1);
+          }
+        T *cb = chn + (buf & 1) * (kChain * R * 32);
+        cb[warp * 32 + lane] = pn0 + pn1;
+        chain_bar();
+        ++buf;
+        s -= ((cb[lane] + cb[32 + lane]) + cb[64 + lane]) + cb[96 + lane];
+      }
+      T po0 = T(0), po1 = T(0);
+#pragma unroll
+      for (int k = 0; k < 8; k += 2) {
+        po0 += dv[r][k] * __shfl_sync(0xffffffffu, s, warp * 8 + k);
+        po1 += dv[r][k + 1] * __shfl_sync(0xffffffffu, s, warp * 8 + k + 1);
+      }
+      T *cb = chn + (buf & 1) * (kChain * R * 32);
+      cb[warp * 32 + lane] = po0 + po1;
+      chain_bar();
+      ++buf;
+      yr[r] = ((cb[lane] + cb[32 + lane]) + cb[64 + lane]) + cb[96 + lane];
+      if (warp == 0) y[I * 32 + lane] = yr[r];
+    }
+  }
+  __syncthreads();
+}
+
 template <typename T, int C, int R>
 __device__ void cluster_sweep(const cg::cluster_group &cluster, const T *__restrict__ pool,
                               const BandLayout &L, T *y, T *red, T *chn, T *part,
                               bool backward) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   Sweep<T, C, R> S{pool, L, (int)cluster.block_rank(), L.nt, L.w, backward};
-  const int c = S.c;
   const int nsteps = (S.nt + R - 1) / R;
   constexpr int kLinesPerUnit = 8 * 32 * (int)sizeof(T) / 128;
-  constexpr int kNear = R * (R - 1) / 2;       // couplings inside a group of R rows
   T nx[8];                                      // register copy of this warp's next first unit
   bool have_nx = false;
   {
@@ -111,11 +194,10 @@ __device__ void cluster_sweep(const cg::cluster_group &cluster, const T *__restr
   }
   int buf = 0;                                  // rotating chain buffer
   for (int step = 0; step < nsteps; ++step) {
-    const int par = step & 1;
     // chain tiles of this step: columns 8*warp..8*warp+7 of every inverted
     // diagonal block and every coupling inside the group
     T dv[R][8];
-    T nv[kNear > 0 ? kNear : 1][8];
+    T nv[Sweep<T, C, R>::kNearSlots][8];
     if (warp < kChain) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
@@ -205,76 +287,168 @@ __device__ void cluster_sweep(const cg::cluster_group &cluster, const T *__restr
         have_nx = true;
       }
     }
+    step_tail<T, C, R>(cluster, S, step, acc, dv, nv, y, red, chn, part, buf);
+  }
+}
+
+// ---- sweep with its tiles staged in shared memory ---------------------------
+// The same step as above, but the tiles a CTA reads in a step (its R inverted
+// diagonal blocks, the couplings inside the group and its far tiles) are
+// copied into a shared-memory stage by bulk asynchronous copies
+// (cp.async.bulk, completed on an mbarrier) that one thread issues a step
+// ahead, so neither the far products nor the chain wait on L2 or HBM.  A
+// stage holds R * (1 + ceil(w / C)) + R (R - 1) / 2 tiles; every tile of the
+// pool is a contiguous, 4 KB aligned block, so each copy is one tile.
+constexpr int kStages = 2;
+
+__device__ __forceinline__ uint32_t sm_addr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for phase `parity` of an mbarrier; false after about a second.
+__device__ __forceinline__ bool mbar_wait(uint64_t *m, uint32_t parity) {
+  const uint32_t a = sm_addr(m);
+  uint32_t done = 0;
+  const uint64_t t0 = global_ns();
+  for (int it = 0; !done; ++it) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (!done && (it & 255) == 255 && global_ns() - t0 > 1000000000ull) break;
+  }
+  return done != 0;
+}
+
+__device__ __forceinline__ void bulk_tile(void *dst, const void *src, uint32_t bytes,
+                                          uint64_t *m) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(sm_addr(dst)), "l"(src), "r"(bytes), "r"(sm_addr(m))
+      : "memory");
+}
+
+// Tiles per stage for half-bandwidth w (host and device).
+__host__ __device__ __forceinline__ int stage_tiles(int w, int C, int R) {
+  return R * (1 + (w + C - 1) / C) + R * (R - 1) / 2;
+}
+
+// Issue the copies of one step into stage `st` (one thread).
+template <typename T, int C, int R>
+__device__ void stage_step(const Sweep<T, C, R> &S, int step, T *st, uint64_t *m) {
+  constexpr uint32_t kTile = 1024 * sizeof(T);
+  constexpr int kFar0 = R + (R * (R - 1)) / 2;  // first far slot
+  int ntiles = 0;
 #pragma unroll
-    for (int q = 0; q < R; ++q) red[(warp * R + q) * 32 + lane] = acc[q][0] + acc[q][1];
-    __syncthreads();
-    if (warp < kChain) {
-      // CTA partial of each row: warps w, w+4, w+8, w+12, then the four sums
-      T *cb = chn + (buf & 1) * (kChain * R * 32);
+  for (int q = 0; q < R; ++q) {
+    if (!S.valid(step, q)) break;
+    int t0, n;
+    far_tiles<C>(q, S.dmax(S.row(step, q)), S.c, t0, n);
+    ntiles += 1 + min(q, S.w) + n;
+  }
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+               ::"r"(sm_addr(m)), "r"(ntiles * kTile)
+               : "memory");
+  int slot = kFar0;
 #pragma unroll
-      for (int q = 0; q < R; ++q) {
-        T s = red[(warp * R + q) * 32 + lane];
-#pragma unroll
-        for (int k = warp + kChain; k < kClWarps; k += kChain) s += red[(k * R + q) * 32 + lane];
-        cb[(warp * R + q) * 32 + lane] = s;
-      }
-      chain_bar();
-      ++buf;
-      T tot[R];
-#pragma unroll
-      for (int q = 0; q < R; ++q) {
-        tot[q] = cb[q * 32 + lane];
-#pragma unroll
-        for (int k = 1; k < kChain; ++k) tot[q] += cb[(k * R + q) * 32 + lane];
-      }
-      for (int dst = warp; dst < C; dst += kChain) {
-        T *p = cluster.map_shared_rank(part, dst);
-#pragma unroll
-        for (int q = 0; q < R; ++q) p[((par * R + q) * C + c) * 32 + lane] = tot[q];
+  for (int q = 0; q < R; ++q) {
+    if (!S.valid(step, q)) break;
+    const int I = S.row(step, q);
+    bulk_tile(st + q * 1024, tile_at(S.pool, S.L, I, 0), kTile, m);
+    for (int d = 1; d <= q && d <= S.w; ++d)
+      bulk_tile(st + (R + q * (q - 1) / 2 + d - 1) * 1024, tile_at(S.pool, S.L, I, d), kTile, m);
+    int t0, n;
+    far_tiles<C>(q, S.dmax(I), S.c, t0, n);
+    for (int t = 0; t < n; ++t, ++slot)
+      bulk_tile(st + slot * 1024, tile_at(S.pool, S.L, I, 1 + S.c + (t0 + t) * C), kTile, m);
+  }
+}
+
+template <typename T, int C, int R>
+__device__ void cluster_sweep_staged(const cg::cluster_group &cluster, const T *__restrict__ pool,
+                                     const BandLayout &L, T *y, T *red, T *chn, T *part,
+                                     bool backward, T *stages, int stride, uint64_t *mbar,
+                                     uint32_t &seq, bool &dead, DevStatus *status, int sys) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  Sweep<T, C, R> S{pool, L, (int)cluster.block_rank(), L.nt, L.w, backward};
+  const int nsteps = (S.nt + R - 1) / R;
+  constexpr int kFar0 = R + (R * (R - 1)) / 2;
+  int issued = 0;                               // steps staged (thread 0)
+  if (threadIdx.x == 0 && !dead)
+    for (; issued < kStages - 1 && issued < nsteps; ++issued) {
+      const uint32_t q = seq + issued;
+      stage_step(S, issued, stages + (q % kStages) * stride, mbar + q % kStages);
+    }
+  int buf = 0;
+  for (int step = 0; step < nsteps; ++step) {
+    const uint32_t q = seq + step;
+    // the stage of step + kStages - 1 was last read in the previous step,
+    // which every warp has left (block barrier at the end of a step)
+    if (threadIdx.x == 0 && !dead && step + kStages - 1 < nsteps) {
+      const uint32_t qn = q + kStages - 1;
+      stage_step(S, step + kStages - 1, stages + (qn % kStages) * stride, mbar + qn % kStages);
+      issued = step + kStages;
+    }
+    if (!dead && !mbar_wait(mbar + q % kStages, (q / kStages) & 1u)) {
+      dead = true;
+      if (lane == 0 && atomicCAS(&status->code, 0, GENEO_ERR_TIMEOUT) == 0) {
+        status->where = sys;
+        status->detail = step;
       }
     }
-    cluster.sync();
+    const T *st = stages + (q % kStages) * stride;
+    T dv[R][8];
+    T nv[Sweep<T, C, R>::kNearSlots][8];
     if (warp < kChain) {
-      T yr[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         if (!S.valid(step, r)) break;
-        const int I = S.row(step, r);
-        T s = y[I * 32 + lane];
 #pragma unroll
-        for (int q = 0; q < C; ++q) s -= part[((par * R + r) * C + q) * 32 + lane];
-        if (r > 0) {                            // couplings to the rows solved in this step
-          T pn0 = T(0), pn1 = T(0);
+        for (int k = 0; k < 8; ++k) dv[r][k] = st[r * 1024 + warp * 256 + k * 32 + lane];
 #pragma unroll
-          for (int d = 1; d <= r; ++d)
+        for (int d = 1; d <= r; ++d)            // zero outside the band (d > w)
 #pragma unroll
-            for (int k = 0; k < 8; k += 2) {
-              pn0 += nv[r * (r - 1) / 2 + d - 1][k] * __shfl_sync(0xffffffffu, yr[r - d], warp * 8 + k);
-              pn1 += nv[r * (r - 1) / 2 + d - 1][k + 1] *
-                     __shfl_sync(0xffffffffu, yr[r - d], warp * 8 + k + 1);
-            }
-          T *cb = chn + (buf & 1) * (kChain * R * 32);
-          cb[warp * 32 + lane] = pn0 + pn1;
-          chain_bar();
-          ++buf;
-          s -= ((cb[lane] + cb[32 + lane]) + cb[64 + lane]) + cb[96 + lane];
-        }
-        T po0 = T(0), po1 = T(0);
-#pragma unroll
-        for (int k = 0; k < 8; k += 2) {
-          po0 += dv[r][k] * __shfl_sync(0xffffffffu, s, warp * 8 + k);
-          po1 += dv[r][k + 1] * __shfl_sync(0xffffffffu, s, warp * 8 + k + 1);
-        }
-        T *cb = chn + (buf & 1) * (kChain * R * 32);
-        cb[warp * 32 + lane] = po0 + po1;
-        chain_bar();
-        ++buf;
-        yr[r] = ((cb[lane] + cb[32 + lane]) + cb[64 + lane]) + cb[96 + lane];
-        if (warp == 0) y[I * 32 + lane] = yr[r];
+          for (int k = 0; k < 8; ++k)
+            nv[r * (r - 1) / 2 + d - 1][k] =
+                d <= S.w ? st[(R + r * (r - 1) / 2 + d - 1) * 1024 + warp * 256 + k * 32 + lane]
+                         : T(0);
       }
     }
-    __syncthreads();
+    T acc[R][2];
+#pragma unroll
+    for (int q2 = 0; q2 < R; ++q2) acc[q2][0] = acc[q2][1] = T(0);
+    int r, d, g;
+    for (int u = warp; S.unit(step, u, r, d, g); u += kClWarps) {
+      const T *t = st + (kFar0 + u / kGroups) * 1024 + g * 256;
+      const int I = S.row(step, r);
+      const T *yJ = y + (backward ? (I + d) : (I - d)) * 32 + g * 8;
+      T a0 = T(0), a1 = T(0);
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) {
+        a0 += t[e * 32 + lane] * yJ[e];
+        a1 += t[(e + 1) * 32 + lane] * yJ[e + 1];
+      }
+#pragma unroll
+      for (int q2 = 0; q2 < R; ++q2)
+        if (q2 == r) {
+          acc[q2][0] += a0;
+          acc[q2][1] += a1;
+        }
+    }
+    step_tail<T, C, R>(cluster, S, step, acc, dv, nv, y, red, chn, part, buf);
   }
+  if (threadIdx.x == 0 && dead)                 // copies still in flight land before the exit
+    for (int s = max(0, issued - kStages); s < issued; ++s)
+      mbar_wait(mbar + (seq + s) % kStages, ((seq + s) / kStages) & 1u);
+  seq += nsteps;
 }
 
 // Look-ahead sweep.  Warps 4..15 multiply the far tiles (distance >= 2) of row
@@ -503,16 +677,73 @@ __global__ void __launch_bounds__(kClWarps * 32)
   cluster.sync();                          // no CTA leaves while others may still write to it
 }
 
+template <typename T, int C, int R>
+__global__ void __launch_bounds__(kClWarps * 32)
+    k_schwarz_cluster_staged(const SubDesc *subs, const BandLayout *lay, int nnx, int nny,
+                             const T *poolL, const T *poolU, const double *__restrict__ r,
+                             T *__restrict__ xloc, const CGScalars *cgs, int stride,
+                             DevStatus *status) {
+  if (cgs && cgs->done) return;           // the same for every CTA of the cluster
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *stages = reinterpret_cast<T *>(smraw);                        // [kStages][stride]
+  uint64_t *mbar = reinterpret_cast<uint64_t *>(stages + kStages * stride);   // [kStages]
+  T *red = reinterpret_cast<T *>(mbar + kStages);  // [kClWarps][R][32]
+  T *chn = red + kClWarps * R * 32;       // [2][kChain][R][32]
+  T *part = chn + 2 * kChain * R * 32;    // [2][R][C][32]
+  T *y = part + 2 * R * C * 32;           // [npad]
+  const int j = blockIdx.x / C;
+  const SubDesc &S = subs[j];
+  const BandLayout L = lay[j];
+  const int n = S.n_int, npad = L.nt * 32;
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < kStages; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_addr(mbar + b)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int l = threadIdx.x; l < npad; l += blockDim.x) {
+    T v = T(0);
+    if (l < n) {
+      const int nc = S.nc;
+      int node = l / nc, comp = l - nc * node;
+      int gi, gj, gk;
+      S.ibox.global(node, gi, gj, gk);
+      v = T(r[nc * (gi + nnx * (gj + nny * gk)) + comp]);
+    }
+    y[l] = v;
+  }
+  cluster.sync();                          // shared memory and mbarriers live in every CTA
+  uint32_t seq = 0;
+  bool dead = false;
+  cluster_sweep_staged<T, C, R>(cluster, poolL, L, y, red, chn, part, false, stages, stride, mbar,
+                                seq, dead, status, j);
+  cluster_sweep_staged<T, C, R>(cluster, poolU, L, y, red, chn, part, true, stages, stride, mbar,
+                                seq, dead, status, j);
+  if (cluster.block_rank() == 0) {
+    T *out = xloc + S.v_int;
+    for (int l = threadIdx.x; l < n; l += blockDim.x) out[l] = y[l];
+  }
+  cluster.sync();                          // no CTA leaves while others may still write to it
+}
+
 template <typename T>
 int smem_bytes(int npad, int C, int R) {
   if (R == 0) return ((2 * (kClWarps - kChain) + 2 * kChain + 2 * C) * 32 + npad) * (int)sizeof(T);
   return ((kClWarps + 2 * kChain + 2 * C) * R * 32 + npad) * (int)sizeof(T);
 }
 
+template <typename T>
+long long smem_bytes_staged(int npad, int w, int C, int R) {
+  return (long long)kStages * stage_tiles(w, C, R) * 1024 * sizeof(T) + kStages * 8 +
+         smem_bytes<T>(npad, C, R);
+}
+
+constexpr long long kSmemMax = 227 * 1024;
+
 template <typename T, int C, int R>
-int launch_cr(const SubDesc *d_subs, const BandLayout *d_lay, int nsub, int npad_max, int nnx,
-              int nny, const T *poolL, const T *poolU, const double *r, T *xloc,
-              const CGScalars *cgs, cudaStream_t s) {
+int launch_cr(const SubDesc *d_subs, const BandLayout *d_lay, int nsub, int npad_max, int w_max,
+              int staged, int nnx, int nny, const T *poolL, const T *poolU, const double *r,
+              T *xloc, const CGScalars *cgs, DevStatus *status, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nsub * C);
   cfg.blockDim = dim3(kClWarps * 32);
@@ -528,7 +759,20 @@ int launch_cr(const SubDesc *d_subs, const BandLayout *d_lay, int nsub, int npad
   if constexpr (R == 0) {
     GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_schwarz_cluster_la<T, C>, d_subs, d_lay, nnx, nny,
                                       poolL, poolU, r, xloc, cgs));
+  } else if constexpr (R <= 2) {
+    if (staged) {
+      const long long sm = smem_bytes_staged<T>(npad_max, w_max, C, R);
+      if (sm > kSmemMax) return GENEO_ERR_INVALID_ARG;
+      cfg.dynamicSmemBytes = (size_t)sm;
+      const int stride = stage_tiles(w_max, C, R) * 1024;
+      GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_schwarz_cluster_staged<T, C, R>, d_subs, d_lay,
+                                        nnx, nny, poolL, poolU, r, xloc, cgs, stride, status));
+    } else {
+      GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_schwarz_cluster<T, C, R>, d_subs, d_lay, nnx, nny,
+                                        poolL, poolU, r, xloc, cgs));
+    }
   } else {
+    if (staged) return GENEO_ERR_INVALID_ARG;
     GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_schwarz_cluster<T, C, R>, d_subs, d_lay, nnx, nny,
                                       poolL, poolU, r, xloc, cgs));
   }
@@ -537,24 +781,29 @@ int launch_cr(const SubDesc *d_subs, const BandLayout *d_lay, int nsub, int npad
 }
 
 template <typename T, int C>
-int launch_c(int rows, const SubDesc *d_subs, const BandLayout *d_lay, int nsub, int npad_max,
-             int nnx, int nny, const T *poolL, const T *poolU, const double *r, T *xloc,
-             const CGScalars *cgs, cudaStream_t s) {
+int launch_c(int rows, int staged, const SubDesc *d_subs, const BandLayout *d_lay, int nsub,
+             int npad_max, int w_max, int nnx, int nny, const T *poolL, const T *poolU,
+             const double *r, T *xloc, const CGScalars *cgs, DevStatus *status, cudaStream_t s) {
   switch (rows) {
-    case 0: return launch_cr<T, C, 0>(d_subs, d_lay, nsub, npad_max, nnx, nny, poolL, poolU, r, xloc, cgs, s);
-    case 4: return launch_cr<T, C, 4>(d_subs, d_lay, nsub, npad_max, nnx, nny, poolL, poolU, r, xloc, cgs, s);
-    case 2: return launch_cr<T, C, 2>(d_subs, d_lay, nsub, npad_max, nnx, nny, poolL, poolU, r, xloc, cgs, s);
-    default: return launch_cr<T, C, 1>(d_subs, d_lay, nsub, npad_max, nnx, nny, poolL, poolU, r, xloc, cgs, s);
+    case 0: return launch_cr<T, C, 0>(d_subs, d_lay, nsub, npad_max, w_max, staged, nnx, nny, poolL, poolU, r, xloc, cgs, status, s);
+    case 4: return launch_cr<T, C, 4>(d_subs, d_lay, nsub, npad_max, w_max, staged, nnx, nny, poolL, poolU, r, xloc, cgs, status, s);
+    case 2: return launch_cr<T, C, 2>(d_subs, d_lay, nsub, npad_max, w_max, staged, nnx, nny, poolL, poolU, r, xloc, cgs, status, s);
+    default: return launch_cr<T, C, 1>(d_subs, d_lay, nsub, npad_max, w_max, staged, nnx, nny, poolL, poolU, r, xloc, cgs, status, s);
   }
 }
 
 template <typename T, int C>
-int prepare_c(int npad_max) {
+int prepare_c(int npad_max, int w_max) {
   int st;
   if ((st = ensure_smem(k_schwarz_cluster<T, C, 1>, smem_bytes<T>(npad_max, C, 1)))) return st;
   if ((st = ensure_smem(k_schwarz_cluster<T, C, 2>, smem_bytes<T>(npad_max, C, 2)))) return st;
   if ((st = ensure_smem(k_schwarz_cluster_la<T, C>, smem_bytes<T>(npad_max, C, 0)))) return st;
-  return ensure_smem(k_schwarz_cluster<T, C, 4>, smem_bytes<T>(npad_max, C, 4));
+  if ((st = ensure_smem(k_schwarz_cluster<T, C, 4>, smem_bytes<T>(npad_max, C, 4)))) return st;
+  const long long s1 = smem_bytes_staged<T>(npad_max, w_max, C, 1);
+  const long long s2 = smem_bytes_staged<T>(npad_max, w_max, C, 2);
+  if (s1 <= kSmemMax && (st = ensure_smem(k_schwarz_cluster_staged<T, C, 1>, (int)s1))) return st;
+  if (s2 <= kSmemMax && (st = ensure_smem(k_schwarz_cluster_staged<T, C, 2>, (int)s2))) return st;
+  return GENEO_OK;
 }
 
 }  // namespace
@@ -568,37 +817,44 @@ int schwarz_cluster_size(int nsub, int sm_count) {
 }
 
 template <typename T>
-int prepare_schwarz_solve(int npad_max) {
-  if (smem_bytes<T>(npad_max, 8, 4) > 227 * 1024) return GENEO_ERR_INVALID_ARG;
+int prepare_schwarz_solve(int npad_max, int w_max) {
+  if (smem_bytes<T>(npad_max, 8, 4) > kSmemMax) return GENEO_ERR_INVALID_ARG;
   int st;
-  if ((st = prepare_c<T, 1>(npad_max))) return st;
-  if ((st = prepare_c<T, 2>(npad_max))) return st;
-  if ((st = prepare_c<T, 4>(npad_max))) return st;
-  return prepare_c<T, 8>(npad_max);
+  if ((st = prepare_c<T, 1>(npad_max, w_max))) return st;
+  if ((st = prepare_c<T, 2>(npad_max, w_max))) return st;
+  if ((st = prepare_c<T, 4>(npad_max, w_max))) return st;
+  return prepare_c<T, 8>(npad_max, w_max);
+}
+
+template <typename T>
+bool schwarz_staged_fits(int npad_max, int w_max, int cluster, int rows) {
+  return (rows == 1 || rows == 2) && smem_bytes_staged<T>(npad_max, w_max, cluster, rows) <= kSmemMax;
 }
 
 template <typename T>
 int launch_schwarz_solve(const SubDesc *d_subs, const BandLayout *d_lay, int nsub, int npad_max,
-                         int nnx, int nny, const T *poolL, const T *poolU, const double *r,
-                         T *xloc, const CGScalars *cgs, int cluster, int rows,
-                         DevStatus *status, cudaStream_t s) {
-  (void)status;
+                         int w_max, int nnx, int nny, const T *poolL, const T *poolU,
+                         const double *r, T *xloc, const CGScalars *cgs, int cluster, int rows,
+                         int staged, DevStatus *status, cudaStream_t s) {
   switch (cluster) {
-    case 8: return launch_c<T, 8>(rows, d_subs, d_lay, nsub, npad_max, nnx, nny, poolL, poolU, r, xloc, cgs, s);
-    case 4: return launch_c<T, 4>(rows, d_subs, d_lay, nsub, npad_max, nnx, nny, poolL, poolU, r, xloc, cgs, s);
-    case 2: return launch_c<T, 2>(rows, d_subs, d_lay, nsub, npad_max, nnx, nny, poolL, poolU, r, xloc, cgs, s);
-    default: return launch_c<T, 1>(rows, d_subs, d_lay, nsub, npad_max, nnx, nny, poolL, poolU, r, xloc, cgs, s);
+    case 8: return launch_c<T, 8>(rows, staged, d_subs, d_lay, nsub, npad_max, w_max, nnx, nny, poolL, poolU, r, xloc, cgs, status, s);
+    case 4: return launch_c<T, 4>(rows, staged, d_subs, d_lay, nsub, npad_max, w_max, nnx, nny, poolL, poolU, r, xloc, cgs, status, s);
+    case 2: return launch_c<T, 2>(rows, staged, d_subs, d_lay, nsub, npad_max, w_max, nnx, nny, poolL, poolU, r, xloc, cgs, status, s);
+    default: return launch_c<T, 1>(rows, staged, d_subs, d_lay, nsub, npad_max, w_max, nnx, nny, poolL, poolU, r, xloc, cgs, status, s);
   }
 }
 
-template int prepare_schwarz_solve<double>(int);
-template int prepare_schwarz_solve<float>(int);
+template int prepare_schwarz_solve<double>(int, int);
+template int prepare_schwarz_solve<float>(int, int);
+template bool schwarz_staged_fits<double>(int, int, int, int);
+template bool schwarz_staged_fits<float>(int, int, int, int);
 template int launch_schwarz_solve<double>(const SubDesc *, const BandLayout *, int, int, int, int,
-                                          const double *, const double *, const double *,
-                                          double *, const CGScalars *, int, int, DevStatus *,
+                                          int, const double *, const double *, const double *,
+                                          double *, const CGScalars *, int, int, int, DevStatus *,
                                           cudaStream_t);
 template int launch_schwarz_solve<float>(const SubDesc *, const BandLayout *, int, int, int, int,
-                                         const float *, const float *, const double *, float *,
-                                         const CGScalars *, int, int, DevStatus *, cudaStream_t);
+                                         int, const float *, const float *, const double *,
+                                         float *, const CGScalars *, int, int, int, DevStatus *,
+                                         cudaStream_t);
 
 }  // namespace geneo
