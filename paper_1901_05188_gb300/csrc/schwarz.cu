@@ -372,13 +372,151 @@ __device__ void stage_step(const Sweep<T, C, R> &S, int step, T *st, uint64_t *m
   }
 }
 
+// Exchange of the per-CTA far partials without a cluster barrier: the chain
+// warps of every CTA store their partials straight into each CTA's buffer
+// with st.async, whose bytes complete a transaction count on the receiving
+// CTA's mbarrier (armed by its thread 0 for the step); the receiving chain
+// warps wait on that barrier alone, and the far warps never wait on the
+// cluster.  Buffer and barrier alternate with the step parity; a CTA cannot
+// send the partials of step s + 2 before every CTA has consumed those of step
+// s (it needs their step s + 1 partials first).
+__device__ __forceinline__ uint32_t cluster_addr(const void *p, int rank) {
+  uint32_t a;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(sm_addr(p)), "r"(rank));
+  return a;
+}
+
+__device__ __forceinline__ void st_async(uint32_t addr, float v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];"
+               ::"r"(addr), "r"(__float_as_uint(v)), "r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void st_async(uint32_t addr, double v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];"
+               ::"r"(addr), "l"(__double_as_longlong(v)), "r"(bar)
+               : "memory");
+}
+
+// Wait for phase `parity` with cluster-scope acquire (remote writes visible);
+// false after about a second.
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t *m, uint32_t parity) {
+  const uint32_t a = sm_addr(m);
+  uint32_t done = 0;
+  const uint64_t t0 = global_ns();
+  for (int it = 0; !done; ++it) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (!done && (it & 255) == 255 && global_ns() - t0 > 1000000000ull) break;
+  }
+  return done != 0;
+}
+
 template <typename T, int C, int R>
-__device__ void cluster_sweep_staged(const cg::cluster_group &cluster, const T *__restrict__ pool,
-                                     const BandLayout &L, T *y, T *red, T *chn, T *part,
-                                     bool backward, T *stages, int stride, uint64_t *mbar,
-                                     uint32_t &seq, bool &dead, DevStatus *status, int sys) {
+__device__ __forceinline__ void step_tail_async(const Sweep<T, C, R> &S, int step, uint32_t gstep,
+                                                T (&acc)[R][2], const T (&dv)[R][8],
+                                                const T (&nv)[Sweep<T, C, R>::kNearSlots][8],
+                                                T *y, T *red, T *chn, T *part, uint64_t *mbx,
+                                                int &buf, bool &dead, DevStatus *status, int sys) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  Sweep<T, C, R> S{pool, L, (int)cluster.block_rank(), L.nt, L.w, backward};
+  const int c = S.c, par = gstep & 1;
+#pragma unroll
+  for (int q = 0; q < R; ++q) red[(warp * R + q) * 32 + lane] = acc[q][0] + acc[q][1];
+  __syncthreads();
+  if (warp < kChain) {
+    // CTA partial of each row: warps w, w+4, w+8, w+12, then the four sums
+    T *cb = chn + (buf & 1) * (kChain * R * 32);
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      T s = red[(warp * R + q) * 32 + lane];
+#pragma unroll
+      for (int k = warp + kChain; k < kClWarps; k += kChain) s += red[(k * R + q) * 32 + lane];
+      cb[(warp * R + q) * 32 + lane] = s;
+    }
+    chain_bar();
+    ++buf;
+    T tot[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      tot[q] = cb[q * 32 + lane];
+#pragma unroll
+      for (int k = 1; k < kChain; ++k) tot[q] += cb[(k * R + q) * 32 + lane];
+    }
+    if constexpr (C > 1) {
+      if (threadIdx.x == 0)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                     ::"r"(sm_addr(mbx + par)), "r"((uint32_t)(C * R * 32 * sizeof(T)))
+                     : "memory");
+      for (int dst = warp; dst < C; dst += kChain) {
+        const uint32_t bar = cluster_addr(mbx + par, dst);
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+          st_async(cluster_addr(part + ((par * R + q) * C + c) * 32 + lane, dst), tot[q], bar);
+      }
+      if (!dead && !mbar_wait_cluster(mbx + par, (gstep >> 1) & 1u)) {
+        dead = true;
+        if (lane == 0 && atomicCAS(&status->code, 0, GENEO_ERR_TIMEOUT) == 0) {
+          status->where = sys;
+          status->detail = -1 - step;
+        }
+      }
+    }
+    T yr[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (!S.valid(step, r)) break;
+      const int I = S.row(step, r);
+      T s = y[I * 32 + lane];
+      if constexpr (C > 1) {
+#pragma unroll
+        for (int q = 0; q < C; ++q) s -= part[((par * R + r) * C + q) * 32 + lane];
+      } else {
+        s -= tot[r];
+      }
+      if (r > 0) {                            // couplings to the rows solved in this step
+        T pn0 = T(0), pn1 = T(0);
+#pragma unroll
+        for (int d = 1; d <= r; ++d)
+#pragma unroll
+          for (int k = 0; k < 8; k += 2) {
+            pn0 += nv[r * (r - 1) / 2 + d - 1][k] * __shfl_sync(0xffffffffu, yr[r - d], warp * 8 + k);
+            pn1 += nv[r * (r - 1) / 2 + d - 1][k + 1] *
+                   __shfl_sync(0xffffffffu, yr[r - d], warp * 8 + k + 1);
+          }
+        T *cb = chn + (buf & 1) * (kChain * R * 32);
+        cb[warp * 32 + lane] = pn0 + pn1;
+        chain_bar();
+        ++buf;
+        s -= ((cb[lane] + cb[32 + lane]) + cb[64 + lane]) + cb[96 + lane];
+      }
+      T po0 = T(0), po1 = T(0);
+#pragma unroll
+      for (int k = 0; k < 8; k += 2) {
+        po0 += dv[r][k] * __shfl_sync(0xffffffffu, s, warp * 8 + k);
+        po1 += dv[r][k + 1] * __shfl_sync(0xffffffffu, s, warp * 8 + k + 1);
+      }
+      T *cb = chn + (buf & 1) * (kChain * R * 32);
+      cb[warp * 32 + lane] = po0 + po1;
+      chain_bar();
+      ++buf;
+      yr[r] = ((cb[lane] + cb[32 + lane]) + cb[64 + lane]) + cb[96 + lane];
+      if (warp == 0) y[I * 32 + lane] = yr[r];
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T, int C, int R>
+__device__ void cluster_sweep_staged(const T *__restrict__ pool, int c, const BandLayout &L, T *y,
+                                     T *red, T *chn, T *part, bool backward, T *stages,
+                                     int stride, uint64_t *mbar, uint64_t *mbx, uint32_t &seq,
+                                     bool &dead, DevStatus *status, int sys) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  Sweep<T, C, R> S{pool, L, c, L.nt, L.w, backward};
   const int nsteps = (S.nt + R - 1) / R;
   constexpr int kFar0 = R + (R * (R - 1)) / 2;
   int issued = 0;                               // steps staged (thread 0)
@@ -422,28 +560,34 @@ __device__ void cluster_sweep_staged(const cg::cluster_group &cluster, const T *
                          : T(0);
       }
     }
+    // far products, row by row: units u = warp, warp + 16, ... of the step,
+    // accumulated straight into the row's two accumulators
     T acc[R][2];
+    int ubase = 0;                              // first unit of row r
 #pragma unroll
-    for (int q2 = 0; q2 < R; ++q2) acc[q2][0] = acc[q2][1] = T(0);
-    int r, d, g;
-    for (int u = warp; S.unit(step, u, r, d, g); u += kClWarps) {
-      const T *t = st + (kFar0 + u / kGroups) * 1024 + g * 256;
+    for (int r = 0; r < R; ++r) {
+      acc[r][0] = acc[r][1] = T(0);
+      if (!S.valid(step, r)) continue;
       const int I = S.row(step, r);
-      const T *yJ = y + (backward ? (I + d) : (I - d)) * 32 + g * 8;
-      T a0 = T(0), a1 = T(0);
+      int t0, n;
+      far_tiles<C>(r, S.dmax(I), c, t0, n);
+      const int uend = ubase + kGroups * n;
+      for (int u = ubase + ((warp - ubase) % kClWarps + kClWarps) % kClWarps; u < uend;
+           u += kClWarps) {
+        const int lu = u - ubase, g = lu % kGroups;
+        const int d = 1 + c + (t0 + lu / kGroups) * C;
+        const T *t = st + (kFar0 + u / kGroups) * 1024 + g * 256;
+        const T *yJ = y + (backward ? (I + d) : (I - d)) * 32 + g * 8;
 #pragma unroll
-      for (int e = 0; e < 8; e += 2) {
-        a0 += t[e * 32 + lane] * yJ[e];
-        a1 += t[(e + 1) * 32 + lane] * yJ[e + 1];
-      }
-#pragma unroll
-      for (int q2 = 0; q2 < R; ++q2)
-        if (q2 == r) {
-          acc[q2][0] += a0;
-          acc[q2][1] += a1;
+        for (int e = 0; e < 8; e += 2) {
+          acc[r][0] = fma(t[e * 32 + lane], yJ[e], acc[r][0]);
+          acc[r][1] = fma(t[(e + 1) * 32 + lane], yJ[e + 1], acc[r][1]);
         }
+      }
+      ubase = uend;
     }
-    step_tail<T, C, R>(cluster, S, step, acc, dv, nv, y, red, chn, part, buf);
+    step_tail_async<T, C, R>(S, step, q, acc, dv, nv, y, red, chn, part, mbx, buf, dead, status,
+                             sys);
   }
   if (threadIdx.x == 0 && dead)                 // copies still in flight land before the exit
     for (int s = max(0, issued - kStages); s < issued; ++s)
@@ -688,7 +832,8 @@ __global__ void __launch_bounds__(kClWarps * 32)
   extern __shared__ __align__(16) unsigned char smraw[];
   T *stages = reinterpret_cast<T *>(smraw);                        // [kStages][stride]
   uint64_t *mbar = reinterpret_cast<uint64_t *>(stages + kStages * stride);   // [kStages]
-  T *red = reinterpret_cast<T *>(mbar + kStages);  // [kClWarps][R][32]
+  uint64_t *mbx = mbar + kStages;         // [2] partial exchange, by step parity
+  T *red = reinterpret_cast<T *>(mbx + 2);  // [kClWarps][R][32]
   T *chn = red + kClWarps * R * 32;       // [2][kChain][R][32]
   T *part = chn + 2 * kChain * R * 32;    // [2][R][C][32]
   T *y = part + 2 * R * C * 32;           // [npad]
@@ -697,7 +842,7 @@ __global__ void __launch_bounds__(kClWarps * 32)
   const BandLayout L = lay[j];
   const int n = S.n_int, npad = L.nt * 32;
   if (threadIdx.x == 0) {
-    for (int b = 0; b < kStages; ++b)
+    for (int b = 0; b < kStages + 2; ++b)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_addr(mbar + b)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -715,9 +860,10 @@ __global__ void __launch_bounds__(kClWarps * 32)
   cluster.sync();                          // shared memory and mbarriers live in every CTA
   uint32_t seq = 0;
   bool dead = false;
-  cluster_sweep_staged<T, C, R>(cluster, poolL, L, y, red, chn, part, false, stages, stride, mbar,
+  const int c = (int)cluster.block_rank();
+  cluster_sweep_staged<T, C, R>(poolL, c, L, y, red, chn, part, false, stages, stride, mbar, mbx,
                                 seq, dead, status, j);
-  cluster_sweep_staged<T, C, R>(cluster, poolU, L, y, red, chn, part, true, stages, stride, mbar,
+  cluster_sweep_staged<T, C, R>(poolU, c, L, y, red, chn, part, true, stages, stride, mbar, mbx,
                                 seq, dead, status, j);
   if (cluster.block_rank() == 0) {
     T *out = xloc + S.v_int;
@@ -734,7 +880,7 @@ int smem_bytes(int npad, int C, int R) {
 
 template <typename T>
 long long smem_bytes_staged(int npad, int w, int C, int R) {
-  return (long long)kStages * stage_tiles(w, C, R) * 1024 * sizeof(T) + kStages * 8 +
+  return (long long)kStages * stage_tiles(w, C, R) * 1024 * sizeof(T) + (kStages + 2) * 8 +
          smem_bytes<T>(npad, C, R);
 }
 
