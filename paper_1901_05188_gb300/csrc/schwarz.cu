@@ -416,16 +416,113 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint64_t *m, uint32_t parity) 
   return done != 0;
 }
 
+// Second half of a staged step with FP64 factors, where the issue rate of
+// FP64 instructions bounds a step.  Chain warp w owns rows 8w..8w+7 of the
+// step's tile rows; lane 4i + k works on row 8w + i and column group k (8
+// columns), so every sum over warps, CTAs or columns is a 4-term sum per lane
+// and two butterfly shuffles, with no sum repeated by the four warps:
+//   1. the CTA partial of each row from the 16 far-warp partials;
+//   2. the partials to every CTA (st.async, lane k to CTAs k, k + 4), wait;
+//   3. s = y_I - (sum of the C partials) - couplings inside the group;
+//   4. s to shared memory, then y_I = D^-1 s from this warp's 8 rows of the
+//      inverted diagonal block.
 template <typename T, int C, int R>
 __device__ __forceinline__ void step_tail_async(const Sweep<T, C, R> &S, int step, uint32_t gstep,
-                                                T (&acc)[R][2], const T (&dv)[R][8],
+                                                const T (&acc)[R], const T (&dv)[R][8],
                                                 const T (&nv)[Sweep<T, C, R>::kNearSlots][8],
-                                                T *y, T *red, T *chn, T *part, uint64_t *mbx,
-                                                int &buf, bool &dead, DevStatus *status, int sys) {
+                                                T *y, T *red, T *sb, T *part, uint64_t *mbx,
+                                                bool &dead, DevStatus *status, int sys) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = S.c, par = gstep & 1;
 #pragma unroll
-  for (int q = 0; q < R; ++q) red[(warp * R + q) * 32 + lane] = acc[q][0] + acc[q][1];
+  for (int q = 0; q < R; ++q) red[(warp * R + q) * 32 + lane] = acc[q];
+  __syncthreads();
+  if (warp < kChain) {
+    const int i = lane >> 2, k = lane & 3, row = warp * 8 + i;
+    T tot[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      T p = ((red[((4 * k) * R + q) * 32 + row] + red[((4 * k + 1) * R + q) * 32 + row]) +
+             red[((4 * k + 2) * R + q) * 32 + row]) +
+            red[((4 * k + 3) * R + q) * 32 + row];
+      p += __shfl_xor_sync(0xffffffffu, p, 1);
+      p += __shfl_xor_sync(0xffffffffu, p, 2);
+      tot[q] = p;
+    }
+    if constexpr (C > 1) {
+      if (threadIdx.x == 0)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                     ::"r"(sm_addr(mbx + par)), "r"((uint32_t)(C * R * 32 * sizeof(T)))
+                     : "memory");
+      for (int dst = k; dst < C; dst += 4) {
+        const uint32_t bar = cluster_addr(mbx + par, dst);
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+          st_async(cluster_addr(part + ((par * R + q) * C + c) * 32 + row, dst), tot[q], bar);
+      }
+      if (!dead && !mbar_wait_cluster(mbx + par, (gstep >> 1) & 1u)) {
+        dead = true;
+        if (lane == 0 && atomicCAS(&status->code, 0, GENEO_ERR_TIMEOUT) == 0) {
+          status->where = sys;
+          status->detail = -1 - step;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        T t = T(0);
+#pragma unroll
+        for (int src = k; src < C; src += 4) t += part[((par * R + q) * C + src) * 32 + row];
+        t += __shfl_xor_sync(0xffffffffu, t, 1);
+        t += __shfl_xor_sync(0xffffffffu, t, 2);
+        tot[q] = t;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (!S.valid(step, r)) break;
+      const int I = S.row(step, r);
+      T s = y[I * 32 + row] - tot[r];
+      if (r > 0) {                            // couplings to the rows solved in this step
+        chain_bar();                          // their y, written by every chain warp
+        T pn = T(0);
+#pragma unroll
+        for (int d = 1; d <= r; ++d) {
+          const T *yp = y + (S.backward ? I + d : I - d) * 32 + 8 * k;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) pn = fma(nv[r * (r - 1) / 2 + d - 1][e], yp[e], pn);
+        }
+        pn += __shfl_xor_sync(0xffffffffu, pn, 1);
+        pn += __shfl_xor_sync(0xffffffffu, pn, 2);
+        s -= pn;
+      }
+      if (k == 0) sb[r * 32 + row] = s;
+      chain_bar();
+      T po = T(0);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) po = fma(dv[r][e], sb[r * 32 + 8 * k + e], po);
+      po += __shfl_xor_sync(0xffffffffu, po, 1);
+      po += __shfl_xor_sync(0xffffffffu, po, 2);
+      if (k == 0) y[I * 32 + row] = po;
+    }
+  }
+  __syncthreads();
+}
+
+// FP32 variant of the chain: the four chain warps each take 8 columns of
+// every chain tile for all 32 rows (the sums over warps are repeated in each
+// of them), which keeps the dependent steps of a row short; with FP32 the
+// row latency, not the arithmetic, bounds a step.
+template <typename T, int C, int R>
+__device__ __forceinline__ void step_tail_async_lat(const Sweep<T, C, R> &S, int step, uint32_t gstep,
+                                                const T (&acc)[R], const T (&dv)[R][8],
+                                                const T (&nv)[Sweep<T, C, R>::kNearSlots][8],
+                                                T *y, T *red, T *chn, T *part, uint64_t *mbx,
+                                                bool &dead, DevStatus *status, int sys) {
+  int buf = 0;                                  // rotating chain buffer
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = S.c, par = gstep & 1;
+#pragma unroll
+  for (int q = 0; q < R; ++q) red[(warp * R + q) * 32 + lane] = acc[q];
   __syncthreads();
   if (warp < kChain) {
     // CTA partial of each row: warps w, w+4, w+8, w+12, then the four sums
@@ -525,7 +622,6 @@ __device__ void cluster_sweep_staged(const T *__restrict__ pool, int c, const Ba
       const uint32_t q = seq + issued;
       stage_step(S, issued, stages + (q % kStages) * stride, mbar + q % kStages);
     }
-  int buf = 0;
   for (int step = 0; step < nsteps; ++step) {
     const uint32_t q = seq + step;
     // the stage of step + kStages - 1 was last read in the previous step,
@@ -543,30 +639,33 @@ __device__ void cluster_sweep_staged(const T *__restrict__ pool, int c, const Ba
       }
     }
     const T *st = stages + (q % kStages) * stride;
+    // chain tiles: FP64 row 8 * warp + lane / 4, columns 8 * (lane % 4) + e;
+    // FP32 row lane, columns 8 * warp + e
     T dv[R][8];
     T nv[Sweep<T, C, R>::kNearSlots][8];
     if (warp < kChain) {
+      const int el = sizeof(T) == 8 ? (8 * (lane & 3)) * 32 + warp * 8 + (lane >> 2)
+                                    : (8 * warp) * 32 + lane;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         if (!S.valid(step, r)) break;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) dv[r][k] = st[r * 1024 + warp * 256 + k * 32 + lane];
+        for (int e = 0; e < 8; ++e) dv[r][e] = st[r * 1024 + el + e * 32];
 #pragma unroll
         for (int d = 1; d <= r; ++d)            // zero outside the band (d > w)
 #pragma unroll
-          for (int k = 0; k < 8; ++k)
-            nv[r * (r - 1) / 2 + d - 1][k] =
-                d <= S.w ? st[(R + r * (r - 1) / 2 + d - 1) * 1024 + warp * 256 + k * 32 + lane]
-                         : T(0);
+          for (int e = 0; e < 8; ++e)
+            nv[r * (r - 1) / 2 + d - 1][e] =
+                d <= S.w ? st[(R + r * (r - 1) / 2 + d - 1) * 1024 + el + e * 32] : T(0);
       }
     }
     // far products, row by row: units u = warp, warp + 16, ... of the step,
-    // accumulated straight into the row's two accumulators
-    T acc[R][2];
+    // accumulated straight into the row's accumulator
+    T acc[R];
     int ubase = 0;                              // first unit of row r
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      acc[r][0] = acc[r][1] = T(0);
+      acc[r] = T(0);
       if (!S.valid(step, r)) continue;
       const int I = S.row(step, r);
       int t0, n;
@@ -579,15 +678,15 @@ __device__ void cluster_sweep_staged(const T *__restrict__ pool, int c, const Ba
         const T *t = st + (kFar0 + u / kGroups) * 1024 + g * 256;
         const T *yJ = y + (backward ? (I + d) : (I - d)) * 32 + g * 8;
 #pragma unroll
-        for (int e = 0; e < 8; e += 2) {
-          acc[r][0] = fma(t[e * 32 + lane], yJ[e], acc[r][0]);
-          acc[r][1] = fma(t[(e + 1) * 32 + lane], yJ[e + 1], acc[r][1]);
-        }
+        for (int e = 0; e < 8; ++e) acc[r] = fma(t[e * 32 + lane], yJ[e], acc[r]);
       }
       ubase = uend;
     }
-    step_tail_async<T, C, R>(S, step, q, acc, dv, nv, y, red, chn, part, mbx, buf, dead, status,
-                             sys);
+    if constexpr (sizeof(T) == 8)
+      step_tail_async<T, C, R>(S, step, q, acc, dv, nv, y, red, chn, part, mbx, dead, status, sys);
+    else
+      step_tail_async_lat<T, C, R>(S, step, q, acc, dv, nv, y, red, chn, part, mbx, dead, status,
+                                   sys);
   }
   if (threadIdx.x == 0 && dead)                 // copies still in flight land before the exit
     for (int s = max(0, issued - kStages); s < issued; ++s)
