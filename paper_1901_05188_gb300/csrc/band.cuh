@@ -56,9 +56,11 @@ int prepare_schwarz_solve(int npad_max, int w_max);
 // thread-block cluster of `cluster` CTAs (1, 2, 4 or 8) per subdomain, `rows`
 // tile rows (1, 2 or 4) per cluster barrier, or rows = 0 for the look-ahead
 // sweep (the next row's far tiles overlap the current row's chain).  With
-// staged = 1 (rows 1 or 2 only) every step's tiles are copied into shared
-// memory a step ahead by bulk asynchronous copies; a copy that does not land
-// within about a second sets GENEO_ERR_TIMEOUT in *status.
+// staged = 1 (rows 0, 1 or 2) every step's tiles are copied into shared
+// memory a step ahead by bulk asynchronous copies and the per-CTA partials
+// are exchanged by st.async on mbarriers instead of cluster barriers; a copy
+// or partial that does not land within about a second sets GENEO_ERR_TIMEOUT
+// in *status.
 template <typename T>
 int launch_schwarz_solve(const SubDesc *d_subs, const BandLayout *d_lay, int nsub,
                          int npad_max, int w_max, int nnx, int nny, const T *poolL,

@@ -300,6 +300,8 @@ __device__ void cluster_sweep(const cg::cluster_group &cluster, const T *__restr
 // stage holds R * (1 + ceil(w / C)) + R (R - 1) / 2 tiles; every tile of the
 // pool is a contiguous, 4 KB aligned block, so each copy is one tile.
 constexpr int kStages = 2;
+constexpr int kXBuf = 4;                        // partial-exchange buffers (and mbarriers)
+constexpr int kIssuer = kClWarps * 32 - 32;     // lane 0 of the last warp issues the copies
 
 __device__ __forceinline__ uint32_t sm_addr(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -616,8 +618,8 @@ __device__ void cluster_sweep_staged(const T *__restrict__ pool, int c, const Ba
   Sweep<T, C, R> S{pool, L, c, L.nt, L.w, backward};
   const int nsteps = (S.nt + R - 1) / R;
   constexpr int kFar0 = R + (R * (R - 1)) / 2;
-  int issued = 0;                               // steps staged (thread 0)
-  if (threadIdx.x == 0 && !dead)
+  int issued = 0;                               // steps staged (issuing thread)
+  if (threadIdx.x == kIssuer && !dead)
     for (; issued < kStages - 1 && issued < nsteps; ++issued) {
       const uint32_t q = seq + issued;
       stage_step(S, issued, stages + (q % kStages) * stride, mbar + q % kStages);
@@ -626,7 +628,7 @@ __device__ void cluster_sweep_staged(const T *__restrict__ pool, int c, const Ba
     const uint32_t q = seq + step;
     // the stage of step + kStages - 1 was last read in the previous step,
     // which every warp has left (block barrier at the end of a step)
-    if (threadIdx.x == 0 && !dead && step + kStages - 1 < nsteps) {
+    if (threadIdx.x == kIssuer && !dead && step + kStages - 1 < nsteps) {
       const uint32_t qn = q + kStages - 1;
       stage_step(S, step + kStages - 1, stages + (qn % kStages) * stride, mbar + qn % kStages);
       issued = step + kStages;
@@ -688,10 +690,160 @@ __device__ void cluster_sweep_staged(const T *__restrict__ pool, int c, const Ba
       step_tail_async_lat<T, C, R>(S, step, q, acc, dv, nv, y, red, chn, part, mbx, dead, status,
                                    sys);
   }
-  if (threadIdx.x == 0 && dead)                 // copies still in flight land before the exit
+  if (threadIdx.x == kIssuer && dead)           // copies still in flight land before the exit
     for (int s = max(0, issued - kStages); s < issued; ++s)
       mbar_wait(mbar + (seq + s) % kStages, ((seq + s) / kStages) & 1u);
   seq += nsteps;
+}
+
+// Staged look-ahead sweep (one tile row per step).  At step q the 12 far
+// warps multiply the far tiles (distance >= 2, d = 2 + c + tC) of row I_{q+1},
+// which need only rows solved before step q, sum their partials and push the
+// CTA partial of row I_{q+1} into every CTA's exchange buffer (st.async,
+// completed on that CTA's mbarrier); meanwhile the four chain warps finish row
+// I_q: the coupling L(I_q, I_q - 1) y_{I_q - 1}, the wait for the C partials
+// of row I_q (pushed during step q - 1), and the inverted diagonal block.  A
+// step's stage holds D^-1(I_q), L(I_q, I_q - 1) and the far tiles of I_{q+1}.
+// Exchange buffers rotate over four rows: a CTA can push the partials of row
+// q + 3 while another still reads those of row q, but not of row q + 4.
+
+__device__ __forceinline__ void far_bar() {
+  asm volatile("bar.sync 2, %0;" ::"n"((kClWarps - kChain) * 32) : "memory");
+}
+
+__host__ __device__ __forceinline__ int stage_tiles_la(int w, int C) {
+  return 2 + (w > 1 ? (w - 1 + C - 1) / C : 0);
+}
+
+template <typename T, int C>
+__device__ void cluster_sweep_staged_la(const T *__restrict__ pool, int c, const BandLayout &L,
+                                        T *y, T *red, T *chn, T *part, bool backward, T *stages,
+                                        int stride, uint64_t *mbar, uint64_t *mbx, uint32_t &seq,
+                                        bool &dead, DevStatus *status, int sys) {
+  constexpr int kFarW = kClWarps - kChain;
+  constexpr uint32_t kTile = 1024 * sizeof(T);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nt = L.nt, w = L.w;
+  auto row = [&](int q) { return backward ? nt - 1 - q : q; };
+  auto dmax = [&](int I) { return backward ? min(w, nt - 1 - I) : min(w, I); };
+  auto nfar = [&](int I) {
+    const int dm = dmax(I), d0 = 2 + c;
+    return dm >= d0 ? (dm - d0) / C + 1 : 0;
+  };
+  auto stage = [&](int q) {                     // one thread: copies of step q
+    const uint32_t g = seq + q;
+    T *st = stages + (g % kStages) * stride;
+    uint64_t *m = mbar + g % kStages;
+    const int I = row(q);
+    const int has1 = dmax(I) >= 1 ? 1 : 0;
+    const int nf = q + 1 < nt ? nfar(row(q + 1)) : 0;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(sm_addr(m)), "r"((uint32_t)(1 + has1 + nf) * kTile)
+                 : "memory");
+    bulk_tile(st, tile_at(pool, L, I, 0), kTile, m);
+    if (has1) bulk_tile(st + 1024, tile_at(pool, L, I, 1), kTile, m);
+    for (int t = 0; t < nf; ++t)
+      bulk_tile(st + (2 + t) * 1024, tile_at(pool, L, row(q + 1), 2 + c + t * C), kTile, m);
+  };
+  // push the CTA partial `v` of the row with sequence number g (far warps 0..C-1)
+  auto push = [&](uint32_t g, int fw, T v) {
+    if constexpr (C > 1) {
+      st_async(cluster_addr(part + ((g % kXBuf) * C + c) * 32 + lane, fw), v,
+               cluster_addr(mbx + g % kXBuf, fw));
+    } else {
+      part[(g % kXBuf) * 32 + lane] = v;
+    }
+  };
+  int issued = 0;
+  if (threadIdx.x == kIssuer && !dead && nt > 0) {
+    stage(0);
+    issued = 1;
+  }
+  // row 0 has no far tiles: its partials are zero
+  if (warp >= kChain && warp - kChain < C && nt > 0) push(seq, warp - kChain, T(0));
+  __syncthreads();
+  int buf = 0;
+  for (int q = 0; q < nt; ++q) {
+    const uint32_t g = seq + q;
+    if (threadIdx.x == kIssuer && !dead && q + 1 < nt) {   // the stage step q - 1 used is free
+      stage(q + 1);
+      issued = q + 2;
+    }
+    if (!dead && !mbar_wait(mbar + g % kStages, (g / kStages) & 1u)) {
+      dead = true;
+      if (lane == 0 && atomicCAS(&status->code, 0, GENEO_ERR_TIMEOUT) == 0) {
+        status->where = sys;
+        status->detail = q;
+      }
+    }
+    const T *st = stages + (g % kStages) * stride;
+    const int I = row(q);
+    if (warp < kChain) {
+      if (C > 1 && threadIdx.x == 0)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                     ::"r"(sm_addr(mbx + g % kXBuf)), "r"((uint32_t)(C * 32 * sizeof(T)))
+                     : "memory");
+      const bool has1 = dmax(I) >= 1;
+      T p = T(0);
+      if (has1) {
+        const T *yp = y + (backward ? I + 1 : I - 1) * 32 + 8 * warp;
+        const T *t1 = st + 1024 + (8 * warp) * 32 + lane;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) p = fma(t1[e * 32], yp[e], p);
+      }
+      T *cb = chn + (buf & 1) * (kChain * 32);
+      cb[warp * 32 + lane] = p;
+      chain_bar();
+      ++buf;
+      T s = y[I * 32 + lane] - (((cb[lane] + cb[32 + lane]) + cb[64 + lane]) + cb[96 + lane]);
+      if constexpr (C > 1) {
+        if (!dead && !mbar_wait_cluster(mbx + g % kXBuf, (g / kXBuf) & 1u)) {
+          dead = true;
+          if (lane == 0 && atomicCAS(&status->code, 0, GENEO_ERR_TIMEOUT) == 0) {
+            status->where = sys;
+            status->detail = -1 - q;
+          }
+        }
+#pragma unroll
+        for (int src = 0; src < C; ++src) s -= part[((g % kXBuf) * C + src) * 32 + lane];
+      } else {
+        s -= part[(g % kXBuf) * 32 + lane];
+      }
+      const T *t0 = st + (8 * warp) * 32 + lane;
+      T po = T(0);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) po = fma(t0[e * 32], __shfl_sync(0xffffffffu, s, 8 * warp + e), po);
+      cb = chn + (buf & 1) * (kChain * 32);
+      cb[warp * 32 + lane] = po;
+      chain_bar();
+      ++buf;
+      if (warp == 0) y[I * 32 + lane] = ((cb[lane] + cb[32 + lane]) + cb[64 + lane]) + cb[96 + lane];
+    } else if (q + 1 < nt) {
+      const int fw = warp - kChain;
+      const int In = row(q + 1), nu = kGroups * nfar(In);
+      T a = T(0);
+      for (int u = fw; u < nu; u += kFarW) {
+        const int d = 2 + c + (u / kGroups) * C, gq = u % kGroups;
+        const T *t = st + (2 + u / kGroups) * 1024 + gq * 256 + lane;
+        const T *yJ = y + (backward ? In + d : In - d) * 32 + gq * 8;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) a = fma(t[e * 32], yJ[e], a);
+      }
+      red[fw * 32 + lane] = a;
+      far_bar();
+      if (fw < C) {
+        T tot = red[lane];
+#pragma unroll
+        for (int k = 1; k < kFarW; ++k) tot += red[k * 32 + lane];
+        push(g + 1, fw, tot);
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == kIssuer && dead)           // copies still in flight land before the exit
+    for (int s = max(0, issued - kStages); s < issued; ++s)
+      mbar_wait(mbar + (seq + s) % kStages, ((seq + s) / kStages) & 1u);
+  seq += nt;
 }
 
 // Look-ahead sweep.  Warps 4..15 multiply the far tiles (distance >= 2) of row
@@ -929,19 +1081,20 @@ __global__ void __launch_bounds__(kClWarps * 32)
   if (cgs && cgs->done) return;           // the same for every CTA of the cluster
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int RR = R > 0 ? R : 1;
   T *stages = reinterpret_cast<T *>(smraw);                        // [kStages][stride]
   uint64_t *mbar = reinterpret_cast<uint64_t *>(stages + kStages * stride);   // [kStages]
-  uint64_t *mbx = mbar + kStages;         // [2] partial exchange, by step parity
-  T *red = reinterpret_cast<T *>(mbx + 2);  // [kClWarps][R][32]
-  T *chn = red + kClWarps * R * 32;       // [2][kChain][R][32]
-  T *part = chn + 2 * kChain * R * 32;    // [2][R][C][32]
-  T *y = part + 2 * R * C * 32;           // [npad]
+  uint64_t *mbx = mbar + kStages;         // [kXBuf] partial exchange
+  T *red = reinterpret_cast<T *>(mbx + kXBuf);   // [kClWarps][R][32] ([12][32] for R = 0)
+  T *chn = red + kClWarps * RR * 32;      // [2][kChain][R][32]
+  T *part = chn + 2 * kChain * RR * 32;   // [2][R][C][32] ([kXBuf][C][32] for R = 0)
+  T *y = part + kXBuf * RR * C * 32;      // [npad]
   const int j = blockIdx.x / C;
   const SubDesc &S = subs[j];
   const BandLayout L = lay[j];
   const int n = S.n_int, npad = L.nt * 32;
   if (threadIdx.x == 0) {
-    for (int b = 0; b < kStages + 2; ++b)
+    for (int b = 0; b < kStages + kXBuf; ++b)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_addr(mbar + b)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -960,10 +1113,17 @@ __global__ void __launch_bounds__(kClWarps * 32)
   uint32_t seq = 0;
   bool dead = false;
   const int c = (int)cluster.block_rank();
-  cluster_sweep_staged<T, C, R>(poolL, c, L, y, red, chn, part, false, stages, stride, mbar, mbx,
-                                seq, dead, status, j);
-  cluster_sweep_staged<T, C, R>(poolU, c, L, y, red, chn, part, true, stages, stride, mbar, mbx,
-                                seq, dead, status, j);
+  if constexpr (R == 0) {
+    cluster_sweep_staged_la<T, C>(poolL, c, L, y, red, chn, part, false, stages, stride, mbar, mbx,
+                                  seq, dead, status, j);
+    cluster_sweep_staged_la<T, C>(poolU, c, L, y, red, chn, part, true, stages, stride, mbar, mbx,
+                                  seq, dead, status, j);
+  } else {
+    cluster_sweep_staged<T, C, R>(poolL, c, L, y, red, chn, part, false, stages, stride, mbar, mbx,
+                                  seq, dead, status, j);
+    cluster_sweep_staged<T, C, R>(poolU, c, L, y, red, chn, part, true, stages, stride, mbar, mbx,
+                                  seq, dead, status, j);
+  }
   if (cluster.block_rank() == 0) {
     T *out = xloc + S.v_int;
     for (int l = threadIdx.x; l < n; l += blockDim.x) out[l] = y[l];
@@ -979,8 +1139,10 @@ int smem_bytes(int npad, int C, int R) {
 
 template <typename T>
 long long smem_bytes_staged(int npad, int w, int C, int R) {
-  return (long long)kStages * stage_tiles(w, C, R) * 1024 * sizeof(T) + (kStages + 2) * 8 +
-         smem_bytes<T>(npad, C, R);
+  const int RR = R > 0 ? R : 1;
+  const int tiles = R > 0 ? stage_tiles(w, C, R) : stage_tiles_la(w, C);
+  return (long long)kStages * tiles * 1024 * sizeof(T) + (kStages + kXBuf) * 8 +
+         ((long long)(kClWarps + 2 * kChain + kXBuf * C) * RR * 32 + npad) * sizeof(T);
 }
 
 constexpr long long kSmemMax = 227 * 1024;
@@ -1001,17 +1163,17 @@ int launch_cr(const SubDesc *d_subs, const BandLayout *d_lay, int nsub, int npad
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  if constexpr (R == 0) {
-    GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_schwarz_cluster_la<T, C>, d_subs, d_lay, nnx, nny,
-                                      poolL, poolU, r, xloc, cgs));
-  } else if constexpr (R <= 2) {
+  if constexpr (R <= 2) {
     if (staged) {
       const long long sm = smem_bytes_staged<T>(npad_max, w_max, C, R);
       if (sm > kSmemMax) return GENEO_ERR_INVALID_ARG;
       cfg.dynamicSmemBytes = (size_t)sm;
-      const int stride = stage_tiles(w_max, C, R) * 1024;
+      const int stride = (R > 0 ? stage_tiles(w_max, C, R) : stage_tiles_la(w_max, C)) * 1024;
       GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_schwarz_cluster_staged<T, C, R>, d_subs, d_lay,
                                         nnx, nny, poolL, poolU, r, xloc, cgs, stride, status));
+    } else if constexpr (R == 0) {
+      GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_schwarz_cluster_la<T, C>, d_subs, d_lay, nnx, nny,
+                                        poolL, poolU, r, xloc, cgs));
     } else {
       GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_schwarz_cluster<T, C, R>, d_subs, d_lay, nnx, nny,
                                         poolL, poolU, r, xloc, cgs));
@@ -1044,8 +1206,10 @@ int prepare_c(int npad_max, int w_max) {
   if ((st = ensure_smem(k_schwarz_cluster<T, C, 2>, smem_bytes<T>(npad_max, C, 2)))) return st;
   if ((st = ensure_smem(k_schwarz_cluster_la<T, C>, smem_bytes<T>(npad_max, C, 0)))) return st;
   if ((st = ensure_smem(k_schwarz_cluster<T, C, 4>, smem_bytes<T>(npad_max, C, 4)))) return st;
+  const long long s0 = smem_bytes_staged<T>(npad_max, w_max, C, 0);
   const long long s1 = smem_bytes_staged<T>(npad_max, w_max, C, 1);
   const long long s2 = smem_bytes_staged<T>(npad_max, w_max, C, 2);
+  if (s0 <= kSmemMax && (st = ensure_smem(k_schwarz_cluster_staged<T, C, 0>, (int)s0))) return st;
   if (s1 <= kSmemMax && (st = ensure_smem(k_schwarz_cluster_staged<T, C, 1>, (int)s1))) return st;
   if (s2 <= kSmemMax && (st = ensure_smem(k_schwarz_cluster_staged<T, C, 2>, (int)s2))) return st;
   return GENEO_OK;
@@ -1073,7 +1237,7 @@ int prepare_schwarz_solve(int npad_max, int w_max) {
 
 template <typename T>
 bool schwarz_staged_fits(int npad_max, int w_max, int cluster, int rows) {
-  return (rows == 1 || rows == 2) && smem_bytes_staged<T>(npad_max, w_max, cluster, rows) <= kSmemMax;
+  return rows >= 0 && rows <= 2 && smem_bytes_staged<T>(npad_max, w_max, cluster, rows) <= kSmemMax;
 }
 
 template <typename T>

@@ -4,7 +4,8 @@ The set-up autotuner picks one of the launch shapes by timing; each must give
 the one-level additive Schwarz application of the oracle (Sec. 3.1), so each
 is pinned here through GENEO_SCHWARZ_CLUSTER / GENEO_SCHWARZ_ROWS (rows 0 is
 the look-ahead sweep) / GENEO_SCHWARZ_STAGED (tiles copied into shared memory
-by bulk asynchronous copies, rows 1 and 2), and compared with the oracle and
+by bulk asynchronous copies and partials exchanged by st.async, rows 0, 1 and
+2), and compared with the oracle and
 with the reference shape (one CTA per subdomain, one row per barrier, tiles
 read from global memory); repeated applications must be bit-identical (no
 race between the warps or CTAs of a sweep, or between a stage's copies and
@@ -67,8 +68,8 @@ def _reference(pkg, monkeypatch, name, prec, r):
 def test_schwarz_launch_shapes(pkg, monkeypatch, name, cluster, rows, prec, staged):
     if prec == 0 and rows == 4:
         pytest.skip("four rows per barrier are offered for FP32 factors only")
-    if staged and rows not in (1, 2):
-        pytest.skip("the staged sweep takes one or two rows per barrier")
+    if staged and rows not in (0, 1, 2):
+        pytest.skip("the staged sweeps take zero (look-ahead), one or two rows per step")
     p = workloads.config(name)
     A, _ = fem.assemble_system(p)
     M = krylov.OneLevelAS(A, decomp.partition(p))
