@@ -703,7 +703,10 @@ __device__ void cluster_sweep_staged(const T *__restrict__ pool, int c, const Ba
 // completed on that CTA's mbarrier); meanwhile the four chain warps finish row
 // I_q: the coupling L(I_q, I_q - 1) y_{I_q - 1}, the wait for the C partials
 // of row I_q (pushed during step q - 1), and the inverted diagonal block.  A
-// step's stage holds D^-1(I_q), L(I_q, I_q - 1) and the far tiles of I_{q+1}.
+// step's stage holds the far tiles of I_{q+1} and, when shared memory allows
+// (stage_chain), the chain's two tiles of I_q; otherwise the chain warps load
+// those into registers at the end of the previous step, in flight over the
+// block barrier.
 // Exchange buffers rotate over four rows: a CTA can push the partials of row
 // q + 3 while another still reads those of row q, but not of row q + 4.
 
@@ -712,14 +715,15 @@ __device__ __forceinline__ void far_bar() {
 }
 
 __host__ __device__ __forceinline__ int stage_tiles_la(int w, int C) {
-  return 2 + (w > 1 ? (w - 1 + C - 1) / C : 0);
+  return w > 1 ? (w - 1 + C - 1) / C : 1;
 }
 
-template <typename T, int C>
+template <typename T, int C, bool kSC>
 __device__ void cluster_sweep_staged_la(const T *__restrict__ pool, int c, const BandLayout &L,
                                         T *y, T *red, T *chn, T *part, bool backward, T *stages,
                                         int stride, uint64_t *mbar, uint64_t *mbx, uint32_t &seq,
                                         bool &dead, DevStatus *status, int sys) {
+  constexpr int stage_chain = kSC ? 1 : 0;
   constexpr int kFarW = kClWarps - kChain;
   constexpr uint32_t kTile = 1024 * sizeof(T);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -734,17 +738,33 @@ __device__ void cluster_sweep_staged_la(const T *__restrict__ pool, int c, const
     const uint32_t g = seq + q;
     T *st = stages + (g % kStages) * stride;
     uint64_t *m = mbar + g % kStages;
-    const int I = row(q);
-    const int has1 = dmax(I) >= 1 ? 1 : 0;
     const int nf = q + 1 < nt ? nfar(row(q + 1)) : 0;
+    const int I = row(q), has1 = stage_chain && dmax(I) >= 1 ? 1 : 0;
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                 ::"r"(sm_addr(m)), "r"((uint32_t)(1 + has1 + nf) * kTile)
+                 ::"r"(sm_addr(m)), "r"((uint32_t)(nf + (stage_chain ? 1 + has1 : 0)) * kTile)
                  : "memory");
-    bulk_tile(st, tile_at(pool, L, I, 0), kTile, m);
-    if (has1) bulk_tile(st + 1024, tile_at(pool, L, I, 1), kTile, m);
+    if (stage_chain) {
+      bulk_tile(st, tile_at(pool, L, I, 0), kTile, m);
+      if (has1) bulk_tile(st + 1024, tile_at(pool, L, I, 1), kTile, m);
+    }
+    T *sf = st + (stage_chain ? 2 : 0) * 1024;
     for (int t = 0; t < nf; ++t)
-      bulk_tile(st + (2 + t) * 1024, tile_at(pool, L, row(q + 1), 2 + c + t * C), kTile, m);
+      bulk_tile(sf + t * 1024, tile_at(pool, L, row(q + 1), 2 + c + t * C), kTile, m);
   };
+  // chain tiles of row I_q, columns 8 * warp + e: D^-1 and L(I_q, I_q - 1)
+  T dv[8], nv[8];
+  auto chain_tiles = [&](int q) {
+    const int I = row(q);
+    const T *D = tile_at(pool, L, I, 0) + (8 * warp) * 32 + lane;
+    const bool has1 = dmax(I) >= 1;
+    const T *N = tile_at(pool, L, I, has1 ? 1 : 0) + (8 * warp) * 32 + lane;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      dv[e] = __ldg(D + e * 32);
+      nv[e] = has1 ? __ldg(N + e * 32) : T(0);
+    }
+  };
+  if (!stage_chain && warp < kChain && nt > 0) chain_tiles(0);
   // push the CTA partial `v` of the row with sequence number g (far warps 0..C-1)
   auto push = [&](uint32_t g, int fw, T v) {
     if constexpr (C > 1) {
@@ -769,7 +789,8 @@ __device__ void cluster_sweep_staged_la(const T *__restrict__ pool, int c, const
       stage(q + 1);
       issued = q + 2;
     }
-    if (!dead && !mbar_wait(mbar + g % kStages, (g / kStages) & 1u)) {
+    if ((warp >= kChain || stage_chain) && !dead &&
+        !mbar_wait(mbar + g % kStages, (g / kStages) & 1u)) {
       dead = true;
       if (lane == 0 && atomicCAS(&status->code, 0, GENEO_ERR_TIMEOUT) == 0) {
         status->where = sys;
@@ -783,13 +804,12 @@ __device__ void cluster_sweep_staged_la(const T *__restrict__ pool, int c, const
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                      ::"r"(sm_addr(mbx + g % kXBuf)), "r"((uint32_t)(C * 32 * sizeof(T)))
                      : "memory");
-      const bool has1 = dmax(I) >= 1;
       T p = T(0);
-      if (has1) {
+      if (dmax(I) >= 1) {
         const T *yp = y + (backward ? I + 1 : I - 1) * 32 + 8 * warp;
         const T *t1 = st + 1024 + (8 * warp) * 32 + lane;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) p = fma(t1[e * 32], yp[e], p);
+        for (int e = 0; e < 8; ++e) p = fma(kSC ? t1[e * 32] : nv[e], yp[e], p);
       }
       T *cb = chn + (buf & 1) * (kChain * 32);
       cb[warp * 32 + lane] = p;
@@ -812,19 +832,21 @@ __device__ void cluster_sweep_staged_la(const T *__restrict__ pool, int c, const
       const T *t0 = st + (8 * warp) * 32 + lane;
       T po = T(0);
 #pragma unroll
-      for (int e = 0; e < 8; ++e) po = fma(t0[e * 32], __shfl_sync(0xffffffffu, s, 8 * warp + e), po);
+      for (int e = 0; e < 8; ++e)
+        po = fma(kSC ? t0[e * 32] : dv[e], __shfl_sync(0xffffffffu, s, 8 * warp + e), po);
       cb = chn + (buf & 1) * (kChain * 32);
       cb[warp * 32 + lane] = po;
       chain_bar();
       ++buf;
       if (warp == 0) y[I * 32 + lane] = ((cb[lane] + cb[32 + lane]) + cb[64 + lane]) + cb[96 + lane];
+      if (!stage_chain && q + 1 < nt) chain_tiles(q + 1);   // in flight over the block barrier
     } else if (q + 1 < nt) {
       const int fw = warp - kChain;
       const int In = row(q + 1), nu = kGroups * nfar(In);
       T a = T(0);
       for (int u = fw; u < nu; u += kFarW) {
         const int d = 2 + c + (u / kGroups) * C, gq = u % kGroups;
-        const T *t = st + (2 + u / kGroups) * 1024 + gq * 256 + lane;
+        const T *t = st + (u / kGroups + (stage_chain ? 2 : 0)) * 1024 + gq * 256 + lane;
         const T *yJ = y + (backward ? In + d : In - d) * 32 + gq * 8;
 #pragma unroll
         for (int e = 0; e < 8; ++e) a = fma(t[e * 32], yJ[e], a);
@@ -1072,8 +1094,8 @@ __global__ void __launch_bounds__(kClWarps * 32)
   cluster.sync();                          // no CTA leaves while others may still write to it
 }
 
-template <typename T, int C, int R>
-__global__ void __launch_bounds__(kClWarps * 32)
+template <typename T, int C, int R, bool kSC>
+__global__ void __launch_bounds__(kClWarps * 32, 1)
     k_schwarz_cluster_staged(const SubDesc *subs, const BandLayout *lay, int nnx, int nny,
                              const T *poolL, const T *poolU, const double *__restrict__ r,
                              T *__restrict__ xloc, const CGScalars *cgs, int stride,
@@ -1114,10 +1136,10 @@ __global__ void __launch_bounds__(kClWarps * 32)
   bool dead = false;
   const int c = (int)cluster.block_rank();
   if constexpr (R == 0) {
-    cluster_sweep_staged_la<T, C>(poolL, c, L, y, red, chn, part, false, stages, stride, mbar, mbx,
-                                  seq, dead, status, j);
-    cluster_sweep_staged_la<T, C>(poolU, c, L, y, red, chn, part, true, stages, stride, mbar, mbx,
-                                  seq, dead, status, j);
+    cluster_sweep_staged_la<T, C, kSC>(poolL, c, L, y, red, chn, part, false, stages, stride,
+                                       mbar, mbx, seq, dead, status, j);
+    cluster_sweep_staged_la<T, C, kSC>(poolU, c, L, y, red, chn, part, true, stages, stride,
+                                       mbar, mbx, seq, dead, status, j);
   } else {
     cluster_sweep_staged<T, C, R>(poolL, c, L, y, red, chn, part, false, stages, stride, mbar, mbx,
                                   seq, dead, status, j);
@@ -1137,15 +1159,34 @@ int smem_bytes(int npad, int C, int R) {
   return ((kClWarps + 2 * kChain + 2 * C) * R * 32 + npad) * (int)sizeof(T);
 }
 
+// Tiles per stage of a staged launch; for the look-ahead sweep (R = 0) the two
+// chain tiles are staged too when the whole launch then fits.
 template <typename T>
-long long smem_bytes_staged(int npad, int w, int C, int R) {
+long long smem_bytes_staged_t(int npad, int tiles, int C, int R) {
   const int RR = R > 0 ? R : 1;
-  const int tiles = R > 0 ? stage_tiles(w, C, R) : stage_tiles_la(w, C);
   return (long long)kStages * tiles * 1024 * sizeof(T) + (kStages + kXBuf) * 8 +
          ((long long)(kClWarps + 2 * kChain + kXBuf * C) * RR * 32 + npad) * sizeof(T);
 }
 
 constexpr long long kSmemMax = 227 * 1024;
+
+template <typename T>
+int staged_tiles(int npad, int w, int C, int R, int *stage_chain) {
+  *stage_chain = 0;
+  if (R > 0) return stage_tiles(w, C, R);
+  const int t = stage_tiles_la(w, C);
+  if (smem_bytes_staged_t<T>(npad, t + 2, C, 0) <= kSmemMax) {
+    *stage_chain = 1;
+    return t + 2;
+  }
+  return t;
+}
+
+template <typename T>
+long long smem_bytes_staged(int npad, int w, int C, int R) {
+  int sc;
+  return smem_bytes_staged_t<T>(npad, staged_tiles<T>(npad, w, C, R, &sc), C, R);
+}
 
 template <typename T, int C, int R>
 int launch_cr(const SubDesc *d_subs, const BandLayout *d_lay, int nsub, int npad_max, int w_max,
@@ -1168,9 +1209,17 @@ int launch_cr(const SubDesc *d_subs, const BandLayout *d_lay, int nsub, int npad
       const long long sm = smem_bytes_staged<T>(npad_max, w_max, C, R);
       if (sm > kSmemMax) return GENEO_ERR_INVALID_ARG;
       cfg.dynamicSmemBytes = (size_t)sm;
-      const int stride = (R > 0 ? stage_tiles(w_max, C, R) : stage_tiles_la(w_max, C)) * 1024;
-      GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_schwarz_cluster_staged<T, C, R>, d_subs, d_lay,
-                                        nnx, nny, poolL, poolU, r, xloc, cgs, stride, status));
+      int stage_chain;
+      const int stride = staged_tiles<T>(npad_max, w_max, C, R, &stage_chain) * 1024;
+      if (R == 0 && stage_chain) {
+        GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_schwarz_cluster_staged<T, C, 0, true>, d_subs,
+                                          d_lay, nnx, nny, poolL, poolU, r, xloc, cgs, stride,
+                                          status));
+      } else {
+        GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_schwarz_cluster_staged<T, C, R, false>, d_subs,
+                                          d_lay, nnx, nny, poolL, poolU, r, xloc, cgs, stride,
+                                          status));
+      }
     } else if constexpr (R == 0) {
       GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_schwarz_cluster_la<T, C>, d_subs, d_lay, nnx, nny,
                                         poolL, poolU, r, xloc, cgs));
@@ -1209,9 +1258,12 @@ int prepare_c(int npad_max, int w_max) {
   const long long s0 = smem_bytes_staged<T>(npad_max, w_max, C, 0);
   const long long s1 = smem_bytes_staged<T>(npad_max, w_max, C, 1);
   const long long s2 = smem_bytes_staged<T>(npad_max, w_max, C, 2);
-  if (s0 <= kSmemMax && (st = ensure_smem(k_schwarz_cluster_staged<T, C, 0>, (int)s0))) return st;
-  if (s1 <= kSmemMax && (st = ensure_smem(k_schwarz_cluster_staged<T, C, 1>, (int)s1))) return st;
-  if (s2 <= kSmemMax && (st = ensure_smem(k_schwarz_cluster_staged<T, C, 2>, (int)s2))) return st;
+  if (s0 <= kSmemMax) {
+    if ((st = ensure_smem(k_schwarz_cluster_staged<T, C, 0, false>, (int)s0))) return st;
+    if ((st = ensure_smem(k_schwarz_cluster_staged<T, C, 0, true>, (int)s0))) return st;
+  }
+  if (s1 <= kSmemMax && (st = ensure_smem(k_schwarz_cluster_staged<T, C, 1, false>, (int)s1))) return st;
+  if (s2 <= kSmemMax && (st = ensure_smem(k_schwarz_cluster_staged<T, C, 2, false>, (int)s2))) return st;
   return GENEO_OK;
 }
 
