@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-darcy", action="store_true")
+    ap.add_argument("--no-c3", action="store_true",
+                    help="skip the 128x64x48 mixed-precision leg")
     ap.add_argument("--serve-requests", type=int, default=10,
                     help="requests of the serving sample (uneven laminate blocks)")
     return ap.parse_args()
@@ -450,6 +452,38 @@ def run_ours(args):
                                     setup_factor=std["ms_setup_factor"], solve=std["ms_solve"]))
         sd.close()
 
+    # the 1.2M-dof wrinkled laminate (128x64x48, 8x4x4 subdomains): time to
+    # 1e-8 with the FP32-factor preconditioner against the all-FP64 one, and the
+    # HBM fraction of its Schwarz local solves
+    c3 = None
+    if rank == 0 and world == 1 and not args.no_c3 and args.config != "c3":
+        p3 = workloads.config("c3")
+        pd3 = device_problem(p3, torch, dev)
+        s3 = pkg.GeneoSolver()
+        n3 = 3 * (p3["nx"] + 1) * (p3["ny"] + 1) * (p3["nz"] + 1)
+        u3 = torch.empty(n3, dtype=torch.float64, device=dev)
+        c3 = dict(workload=f"c3: 128x64x48 Q1 hex laminate with a fibre wrinkle, {n3} dofs, "
+                           "8x4x4 subdomains")
+        for key, pr in (("mixed", pkg.GENEO_MIXED_FP32), ("fp64", pkg.GENEO_FP64)):
+            for _ in range(2):                   # warm-up (and tuning), then one timed solve
+                e0.record(stream)
+                st3 = one_solve(pkg, s3, pd3, pr, u3)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+            leg = dict(ms_per_solve=e0.elapsed_time(e1), iterations=st3["iterations"],
+                       rel_res_true=st3["rel_res_true"], n_coarse=st3["n_coarse"],
+                       phases_ms=dict(assemble=st3["ms_assemble"],
+                                      setup_eig_coarse=st3["ms_setup_eig"],
+                                      setup_factor=st3["ms_setup_factor"], solve=st3["ms_solve"]),
+                       schwarz_launch=dict(cluster=st3["schwarz_cluster"], rows=st3["schwarz_rows"],
+                                           staged=st3["schwarz_staged"]))
+            ms3, by3, _ = pkg.geneo_profile(s3.ctx, 0, 10)
+            leg["schwarz_apply"] = dict(ms=ms3, gbs=by3 / (ms3 * 1e-3) / 1e9,
+                                        frac_of_measured_hbm=by3 / (ms3 * 1e-3) / 1e9 / peak)
+            c3[key] = leg
+        s3.close()
+        del pd3, u3
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ms_cpu, sample, threads = oracle_sample(p, st["iterations"])
@@ -471,7 +505,7 @@ def run_ours(args):
                                         staged=st["schwarz_staged"],
                                         chosen_by="set-up autotuner"),
                     accuracy_vs_oracle=acc, mixed_precision=mixed, serving=serving,
-                    darcy_spe10=darcy)
+                    darcy_spe10=darcy, c3_mixed_vs_fp64=c3)
         print(json.dumps(line))
     s.close()
     if world > 1:
