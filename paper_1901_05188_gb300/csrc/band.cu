@@ -325,9 +325,9 @@ template <typename T>
 __global__ void k_schwarz_gather(int nnx, int nny, int nnz, int px, int py,
                                  const int *__restrict__ cand, int co0, int co1, int co2,
                                  const SubDesc *subs, const T *__restrict__ xloc,
-                                 const double *__restrict__ Zp, const double *__restrict__ yH,
-                                 int pou, const uint8_t *__restrict__ mask,
-                                 double *__restrict__ z, const CGScalars *cg) {
+                                 const double *__restrict__ zy, int pou,
+                                 const uint8_t *__restrict__ mask, double *__restrict__ z,
+                                 const CGScalars *cg) {
   if (cg && cg->done) return;
   int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nnx * nny * nnz) return;
@@ -353,18 +353,15 @@ __global__ void k_schwarz_gather(int nnx, int nny, int nnz, int px, int py,
         for (int comp = 0; comp < nc; ++comp) {
           double v = double(xs[comp]);
           if (pou) v *= mask[nc * n + comp] ? 0.0 : wgt;
-          if (S.m > 0 && yH) {
-            const double *zr = Zp + S.z_off + (long long)(nc * l + comp) * S.m;
-            const double *yy = yH + S.coff;
-            for (int q = 0; q < S.m; ++q) v += zr[q] * yy[q];
-          }
+          if (zy) v += zy[S.v_int + nc * l + comp];
           o[comp] += v;
         }
       }
   for (int comp = 0; comp < nc; ++comp) z[nc * n + comp] = o[comp];
 }
 
-// partial w_{j,k} over a chunk of interior rows: thread (k = t % 32, row group t / 32)
+// partial w_{j,k} over a chunk of interior rows: thread (k = t % 32, row group t / 32),
+// two rows per iteration on independent accumulators (the loads of both in flight)
 __global__ void __launch_bounds__(256) k_coarse_restrict(const SubDesc *subs, int nnx, int nny,
                                                          const double *__restrict__ Zp,
                                                          const double *__restrict__ r,
@@ -376,26 +373,66 @@ __global__ void __launch_bounds__(256) k_coarse_restrict(const SubDesc *subs, in
   const int m = S.m;
   __shared__ double acc[8][32];
   if (m == 0) return;
-  const int n = S.n_int;
+  const int n = S.n_int, nc = S.nc;
   const int per = (n + kRestrictChunks - 1) / kRestrictChunks;
   const int l0 = ch * per, l1 = min(n, l0 + per);
   const int k = threadIdx.x & 31, grp = threadIdx.x >> 5;
-  double s = 0.0;
+  auto rv = [&](int l) {
+    const int node = l / nc, c = l - nc * node;
+    int gi, gj, gk;
+    S.ibox.global(node, gi, gj, gk);
+    return __ldg(r + nc * (gi + nnx * (gj + nny * gk)) + c);
+  };
+  double s0 = 0.0, s1 = 0.0;
   if (k < m) {
-    for (int l = l0 + grp; l < l1; l += 8) {
-      int node = l / S.nc, c = l - S.nc * node;
-      int gi, gj, gk;
-      S.ibox.global(node, gi, gj, gk);
-      s += Zp[S.z_off + (long long)l * m + k] * r[S.nc * (gi + nnx * (gj + nny * gk)) + c];
+    const double *Z = Zp + S.z_off + k;
+    int l = l0 + grp;
+    for (; l + 8 < l1; l += 16) {
+      const double z0 = __ldg(Z + (long long)l * m), z1 = __ldg(Z + (long long)(l + 8) * m);
+      const double r0 = rv(l), r1 = rv(l + 8);
+      s0 = fma(z0, r0, s0);
+      s1 = fma(z1, r1, s1);
     }
+    if (l < l1) s0 = fma(__ldg(Z + (long long)l * m), rv(l), s0);
   }
-  acc[grp][k] = s;
+  acc[grp][k] = s0 + s1;
   __syncthreads();
   if (threadIdx.x < 32 && k < m) {
     double t = 0.0;
     for (int g = 0; g < 8; ++g) t += acc[g][k];
     wpart[((long long)j * kRestrictChunks + ch) * mcap + k] = t;
   }
+}
+
+// zy_j = Z_j y_j on the interior dofs of subdomain j (row-major Z_j: a warp's
+// rows are one contiguous block, each thread consumes its row of m values)
+__global__ void __launch_bounds__(256) k_coarse_prolong(const SubDesc *subs,
+                                                        const double *__restrict__ Zp,
+                                                        const double *__restrict__ yH,
+                                                        double *__restrict__ zy,
+                                                        const CGScalars *cg) {
+  if (cg && cg->done) return;
+  const int j = blockIdx.y;
+  const SubDesc &S = subs[j];
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = S.m;
+  __shared__ double yj[kMaxModes];
+  if (threadIdx.x < m) yj[threadIdx.x] = yH[S.coff + threadIdx.x];
+  __syncthreads();
+  if (l >= S.n_int) return;
+  double v = 0.0;
+  if (m > 0) {
+    const double *zr = Zp + S.z_off + (long long)l * m;
+    double v1 = 0.0;
+    int q = 0;
+    for (; q + 1 < m; q += 2) {
+      v = fma(__ldg(zr + q), yj[q], v);
+      v1 = fma(__ldg(zr + q + 1), yj[q + 1], v1);
+    }
+    if (q < m) v = fma(__ldg(zr + q), yj[q], v);
+    v += v1;
+  }
+  zy[S.v_int + l] = v;
 }
 
 __global__ void k_coarse_reduce(const SubDesc *subs, const double *__restrict__ wpart,
@@ -528,24 +565,23 @@ int launch_extract_interior(const SubDesc *d_subs, const BandLayout *d_lay, int 
 template <typename T>
 void launch_schwarz_gather(int nx, int ny, int nz, int px, int py, const int *cand,
                            const int cand_off[3], const SubDesc *d_subs, const T *xloc,
-                           const double *Zp, const double *yH, int pou,
-                           const uint8_t *mask, double *z, const CGScalars *cg,
-                           cudaStream_t s) {
+                           const double *zy, int pou, const uint8_t *mask, double *z,
+                           const CGScalars *cg, cudaStream_t s) {
   int nn = (nx + 1) * (ny + 1) * (nz + 1);
   k_schwarz_gather<T><<<(nn + 255) / 256, 256, 0, s>>>(nx + 1, ny + 1, nz + 1, px, py, cand,
                                                       cand_off[0], cand_off[1], cand_off[2],
-                                                      d_subs, xloc, Zp, yH, pou, mask, z, cg); GENEO_COUNT_LAUNCH();
+                                                      d_subs, xloc, zy, pou, mask, z, cg); GENEO_COUNT_LAUNCH();
 }
 
 void launch_coarse_apply(const SubDesc *d_subs, int nsub, int max_nint, int nnx, int nny,
                          const double *Zp, const double *r, double *wpart, double *wH,
-                         double *yH, const double *AHinv, int nH, int mcap,
+                         double *yH, double *zy, const double *AHinv, int nH, int mcap,
                          const CGScalars *cg, cudaStream_t s) {
-  (void)max_nint;
   k_coarse_restrict<<<dim3(nsub, kRestrictChunks), 256, 0, s>>>(d_subs, nnx, nny, Zp, r, wpart,
                                                                mcap, cg); GENEO_COUNT_LAUNCH();
   k_coarse_reduce<<<nsub, 32, 0, s>>>(d_subs, wpart, wH, mcap, cg); GENEO_COUNT_LAUNCH();
   k_coarse_gemv<<<(nH * 32 + 255) / 256, 256, 0, s>>>(nH, AHinv, wH, yH, cg); GENEO_COUNT_LAUNCH();
+  k_coarse_prolong<<<dim3((max_nint + 255) / 256, nsub), 256, 0, s>>>(d_subs, Zp, yH, zy, cg); GENEO_COUNT_LAUNCH();
 }
 
 template int launch_band_clear<double>(const BandLayout *, int, double *, long long, cudaStream_t);
@@ -561,12 +597,12 @@ template int launch_extract_interior<float>(const SubDesc *, const BandLayout *,
                                             int, int, const int32_t *, const double *, float *,
                                             cudaStream_t);
 template void launch_schwarz_gather<double>(int, int, int, int, int, const int *, const int[3],
-                                            const SubDesc *, const double *, const double *,
-                                            const double *, int, const uint8_t *, double *,
-                                            const CGScalars *, cudaStream_t);
+                                            const SubDesc *, const double *, const double *, int,
+                                            const uint8_t *, double *, const CGScalars *,
+                                            cudaStream_t);
 template void launch_schwarz_gather<float>(int, int, int, int, int, const int *, const int[3],
-                                           const SubDesc *, const float *, const double *,
-                                           const double *, int, const uint8_t *, double *,
-                                           const CGScalars *, cudaStream_t);
+                                           const SubDesc *, const float *, const double *, int,
+                                           const uint8_t *, double *, const CGScalars *,
+                                           cudaStream_t);
 
 }  // namespace geneo

@@ -677,6 +677,7 @@ int build_plan(geneo_ctx *c, const geneo_partition *part, const geneo_modes *mod
   Precond &pc = c->pc;
   pc.fac_int_elems = f_int;
   pc.xloc_elems = v_int;
+  pc.max_nint = P.max_nint;
   pc.fac_neu_elems = f_neu;
   pc.bloc_blocks = b_neu;
   pc.xneu_elems = x_neu;
@@ -769,12 +770,13 @@ void plan_setup(Arena &A, geneo_ctx *c, const SetupPlan &P) {
     pc.wpart = A.take<double>((size_t)nsub * kRestrictChunks * pc.mcap);
     pc.wH = A.take<double>(pc.nH_cap);
     pc.yH = A.take<double>(pc.nH_cap);
+    pc.zy = A.take<double>(pc.xloc_elems);
   } else {
     pc.neuL = pc.neuU = pc.Bloc = pc.Xneu = pc.V = pc.Vt = pc.W = pc.T1 = pc.Hm = pc.Hpart = nullptr;
     pc.Hs = pc.G = pc.Racc = nullptr;
     pc.Rblk = pc.Evec = pc.Eval = pc.Eres = pc.P = pc.Zp = pc.Yp = nullptr;
     pc.gate = nullptr;
-    pc.AH = pc.AHinv = pc.AHL = pc.AHU = pc.wpart = pc.wH = pc.yH = nullptr;
+    pc.AH = pc.AHinv = pc.AHL = pc.AHU = pc.wpart = pc.wH = pc.yH = pc.zy = nullptr;
     pc.nH_cap = 0;
     pc.z_elems = 0;
   }
@@ -830,19 +832,19 @@ static int precond_apply(geneo_ctx *c, const double *r, double *z, const CGScala
   const int nnx = c->nx + 1, nny = c->ny + 1;
   const bool coarse = pc.nH > 0;
   if (coarse)
-    launch_coarse_apply(pc.d_subs, pc.nsub, 0, nnx, nny, pc.Zp, r, pc.wpart, pc.wH, pc.yH,
-                        pc.AHinv, pc.nH, pc.mcap, cg, s);
+    launch_coarse_apply(pc.d_subs, pc.nsub, pc.max_nint, nnx, nny, pc.Zp, r, pc.wpart, pc.wH,
+                        pc.yH, pc.zy, pc.AHinv, pc.nH, pc.mcap, cg, s);
   int st;
   const int pou = pc.schwarz == GENEO_AS_POU;
   if ((st = schwarz_local_solves(c, r, cg, pc.cluster, pc.rows, pc.staged, s))) return st;
   if (pc.prec == GENEO_MIXED_FP32) {
     launch_schwarz_gather<float>(c->nx, c->ny, c->nz, pc.part.px, pc.part.py, pc.d_cand,
-                                 pc.cand_off, pc.d_subs, (const float *)pc.xloc, pc.Zp,
-                                 coarse ? pc.yH : nullptr, pou, c->mask, z, cg, s);
+                                 pc.cand_off, pc.d_subs, (const float *)pc.xloc,
+                                 coarse ? pc.zy : nullptr, pou, c->mask, z, cg, s);
   } else {
     launch_schwarz_gather<double>(c->nx, c->ny, c->nz, pc.part.px, pc.part.py, pc.d_cand,
-                                  pc.cand_off, pc.d_subs, (const double *)pc.xloc, pc.Zp,
-                                  coarse ? pc.yH : nullptr, pou, c->mask, z, cg, s);
+                                  pc.cand_off, pc.d_subs, (const double *)pc.xloc,
+                                  coarse ? pc.zy : nullptr, pou, c->mask, z, cg, s);
   }
   GENEO_CUDA_TRY(cudaGetLastError());
   return GENEO_OK;

@@ -79,6 +79,8 @@ struct Precond {
   double *AHL = nullptr, *AHU = nullptr;    // tiles of the coarse factor
   double *wpart = nullptr;        // restriction partials [nsub][kChunks][mcap]
   double *wH = nullptr, *yH = nullptr;
+  double *zy = nullptr;           // coarse correction Z_j y_j per interior dof [sum n_int]
+  int max_nint = 0;               // largest interior dof count of a subdomain
   std::vector<int> m;
   std::vector<double> lambdas;    // [nsub][mcap]
   double eig_max_res = 0.0;
