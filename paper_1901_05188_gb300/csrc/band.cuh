@@ -73,17 +73,27 @@ bool schwarz_staged_fits(int npad_max, int w_max, int cluster, int rows);
 // 2 * nsub * size <= number of SMs (at least 1).
 int schwarz_cluster_size(int nsub, int sm_count);
 
-// z = sum_j R_j^T (D_j x_j + (Z y)_j): deterministic gather over subdomains;
-// zy holds Z_j y_j per interior dof (from launch_coarse_apply) or is null.
+// Per node: offsets into the local solutions of the subdomains whose interior
+// holds it (8 slots, -1 padded) and the number of overlapping subdomains
+// containing it (0xFF: more than 8 interior subdomains, visited directly).
+void launch_gather_map(int nx, int ny, int nz, int px, int py, const int *cand,
+                       const int cand_off[3], const SubDesc *d_subs, int *gmap, uint8_t *gcnt,
+                       cudaStream_t s);
+
+// z = sum_j R_j^T (D_j x_j + (Z y)_j): deterministic gather over subdomains
+// through the gather map; zy holds Z_j y_j per interior dof (from
+// launch_coarse_apply) or is null.
 template <typename T>
 void launch_schwarz_gather(int nx, int ny, int nz, int px, int py, const int *cand,
-                           const int cand_off[3], const SubDesc *d_subs, const T *xloc,
-                           const double *zy, int pou, const uint8_t *mask, double *z,
-                           const CGScalars *cg, cudaStream_t s);
+                           const int cand_off[3], const SubDesc *d_subs, const int *gmap,
+                           const uint8_t *gcnt, const T *xloc, const double *zy, int pou,
+                           const uint8_t *mask, double *z, const CGScalars *cg, cudaStream_t s);
 
-// Coarse restriction w = Z^T r (partials over row chunks), reduction,
-// y = A_H^-1 w and the prolongation zy_j = Z_j y_j per interior dof.
-constexpr int kRestrictChunks = 32;
+// Coarse restriction w = Z^T r (partials over blocks of kZRows rows),
+// reduction, y = A_H^-1 w and the prolongation zy_j = Z_j y_j per interior
+// dof.  wpart holds nsub * restrict_chunks(max_nint) * mcap doubles.
+constexpr int kZRows = 128;
+inline int restrict_chunks(int max_nint) { return (max_nint + kZRows - 1) / kZRows; }
 void launch_coarse_apply(const SubDesc *d_subs, int nsub, int max_nint, int nnx, int nny,
                          const double *Zp, const double *r, double *wpart, double *wH,
                          double *yH, double *zy, const double *AHinv, int nH, int mcap,

@@ -711,6 +711,8 @@ void plan_setup(Arena &A, geneo_ctx *c, const SetupPlan &P) {
   pc.d_lay_neu = A.take<BandLayout>(nsub);
   pc.d_lay_H = A.take<BandLayout>(1);
   pc.d_cand = A.take<int>(P.cand.size());
+  pc.gmap = A.take<int>((size_t)c->nnode * 8);
+  pc.gcnt = A.take<uint8_t>((size_t)c->nnode);
   pc.d_ecnt = A.take<int>(P.ecnt.size());
   pc.d_yoff = A.take<long long>(nsub);
   pc.d_pairs = A.take<int2>((size_t)nsub * nsub);
@@ -767,7 +769,7 @@ void plan_setup(Arena &A, geneo_ctx *c, const SetupPlan &P) {
     pc.AHinv = A.take<double>((size_t)pc.nH_cap * pc.nH_cap);
     pc.AHL = A.take<double>((size_t)ntH * ntH * 1024);
     pc.AHU = A.take<double>((size_t)ntH * ntH * 1024);
-    pc.wpart = A.take<double>((size_t)nsub * kRestrictChunks * pc.mcap);
+    pc.wpart = A.take<double>((size_t)nsub * restrict_chunks(P.max_nint) * pc.mcap);
     pc.wH = A.take<double>(pc.nH_cap);
     pc.yH = A.take<double>(pc.nH_cap);
     pc.zy = A.take<double>(pc.xloc_elems);
@@ -839,12 +841,14 @@ static int precond_apply(geneo_ctx *c, const double *r, double *z, const CGScala
   if ((st = schwarz_local_solves(c, r, cg, pc.cluster, pc.rows, pc.staged, s))) return st;
   if (pc.prec == GENEO_MIXED_FP32) {
     launch_schwarz_gather<float>(c->nx, c->ny, c->nz, pc.part.px, pc.part.py, pc.d_cand,
-                                 pc.cand_off, pc.d_subs, (const float *)pc.xloc,
-                                 coarse ? pc.zy : nullptr, pou, c->mask, z, cg, s);
+                                 pc.cand_off, pc.d_subs, pc.gmap, pc.gcnt,
+                                 (const float *)pc.xloc, coarse ? pc.zy : nullptr, pou, c->mask,
+                                 z, cg, s);
   } else {
     launch_schwarz_gather<double>(c->nx, c->ny, c->nz, pc.part.px, pc.part.py, pc.d_cand,
-                                  pc.cand_off, pc.d_subs, (const double *)pc.xloc,
-                                  coarse ? pc.zy : nullptr, pou, c->mask, z, cg, s);
+                                  pc.cand_off, pc.d_subs, pc.gmap, pc.gcnt,
+                                  (const double *)pc.xloc, coarse ? pc.zy : nullptr, pou,
+                                  c->mask, z, cg, s);
   }
   GENEO_CUDA_TRY(cudaGetLastError());
   return GENEO_OK;
@@ -1337,6 +1341,8 @@ int geneo_setup(geneo_ctx *c, const geneo_partition *part, const geneo_modes *mo
   GENEO_CUDA_TRY(cudaMemcpyAsync(pc.d_lay_neu, P.lay_neu.data(), P.nsub * sizeof(BandLayout), cudaMemcpyHostToDevice, s));
   GENEO_CUDA_TRY(cudaMemcpyAsync(pc.d_cand, P.cand.data(), P.cand.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   GENEO_CUDA_TRY(cudaMemcpyAsync(pc.d_ecnt, P.ecnt.data(), P.ecnt.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+  launch_gather_map(c->nx, c->ny, c->nz, pc.part.px, pc.part.py, pc.d_cand, pc.cand_off,
+                    pc.d_subs, pc.gmap, pc.gcnt, s);
   pc.subs = P.subs;
   pc.m.assign(P.nsub, 0);
   pc.lambdas.assign((size_t)P.nsub * pc.mcap, INFINITY);

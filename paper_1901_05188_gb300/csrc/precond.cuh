@@ -35,6 +35,8 @@ struct Precond {
   long long *d_yoff = nullptr;
   int2 *d_pairs = nullptr;
   double *Hs = nullptr, *G = nullptr, *Racc = nullptr;
+  int *gmap = nullptr;            // gather map [nnode][8]: local-solution offsets, -1 padded
+  uint8_t *gcnt = nullptr;        // [nnode] overlapping-subdomain count (0xFF: map full)
   int *d_cand = nullptr;          // [nnx + nny + nnz][kMaxCand] subdomain axis index or -1
   int *d_ecnt = nullptr;          // [nx + ny + nz] subdomains containing the element, per axis
   int cand_off[3] = {0, 0, 0}, ecnt_off[3] = {0, 0, 0};
@@ -77,7 +79,7 @@ struct Precond {
   double *Yp = nullptr;           // A Z_j on Neumann dofs, [nsub] x n_neu x m_j
   double *AH = nullptr, *AHinv = nullptr;   // dense nH x nH
   double *AHL = nullptr, *AHU = nullptr;    // tiles of the coarse factor
-  double *wpart = nullptr;        // restriction partials [nsub][kChunks][mcap]
+  double *wpart = nullptr;        // restriction partials [nsub][row blocks][mcap]
   double *wH = nullptr, *yH = nullptr;
   double *zy = nullptr;           // coarse correction Z_j y_j per interior dof [sum n_int]
   int max_nint = 0;               // largest interior dof count of a subdomain
