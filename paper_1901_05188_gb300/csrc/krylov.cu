@@ -34,17 +34,13 @@ __device__ __forceinline__ double sum_partials(const double *part, int n, double
   return block_sum<NT>(v, sh);
 }
 
-// One lane per matrix row: for 3x3 blocks lanes 3i..3i+2 of a warp hold the
-// three rows of block row 10g + i (i < 10; lanes 30, 31 idle), for the scalar
-// problem lane i holds row 32g + i; every stored value takes exactly one FMA
-// and no sum crosses lanes -- FP64 issue, not bandwidth, is the scarce
-// resource on this GPU, and a shuffle reduction costs FP64 adds.  The lanes of
-// a block row read the rows of the same blocks and the same x entries, so
-// their loads share L1 lines; results go to consecutive entries of y.
-template <int NC>
-struct RowMap {
-  static constexpr int kNodes = 32 / NC;          // block rows per warp
-};
+// One lane per matrix row: lane i of warp group g holds scalar row 32g + i
+// (block row (32g + i) / NC, component (32g + i) % NC), so no lane idles; every
+// stored value takes exactly one FMA and no sum crosses lanes -- FP64 issue,
+// not bandwidth, is the scarce resource on this GPU, and a shuffle reduction
+// costs FP64 adds.  The lanes of a block row read the rows of the same blocks
+// and the same x entries, so their loads share L1 lines; results go to
+// consecutive entries of y.
 
 template <int NC>
 __device__ __forceinline__ double spmv_lane_row(const int32_t *__restrict__ rp,
@@ -75,14 +71,16 @@ __global__ void __launch_bounds__(256) k_spmv(int nnode, const int32_t *__restri
                                               const double *__restrict__ val,
                                               const double *__restrict__ x,
                                               double *__restrict__ y) {
-  constexpr int kN = RowMap<NC>::kNodes;
-  const int lane = threadIdx.x & 31, i = lane / NC, r = lane - NC * i;
+  const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
-  for (int g = warp; g * kN < nnode; g += nw) {
-    const int node = g * kN + i;
-    if (lane < NC * kN && node < nnode)
-      y[NC * node + r] = spmv_lane_row<NC>(rp, col, val, x, node, r);
+  const int nrow = NC * nnode;
+  for (int g = warp; g * 32 < nrow; g += nw) {
+    const int row = g * 32 + lane;
+    if (row < nrow) {
+      const int node = row / NC;
+      y[row] = spmv_lane_row<NC>(rp, col, val, x, node, row - NC * node);
+    }
   }
 }
 
@@ -99,14 +97,14 @@ __global__ void __launch_bounds__(NT) k_cg_spmv_pq(int nnode, const int32_t *__r
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int nw = (gridDim.x * blockDim.x) >> 5;
   double acc = 0.0;
-  constexpr int kN = RowMap<NC>::kNodes;
-  const int i = lane / NC, r = lane - NC * i;
-  for (int g = warp; g * kN < nnode; g += nw) {
-    const int node = g * kN + i;
-    if (lane < NC * kN && node < nnode) {
-      const double yv = spmv_lane_row<NC>(rp, col, val, p, node, r);
-      q[NC * node + r] = yv;
-      acc = fma(p[NC * node + r], yv, acc);
+  const int nrow = NC * nnode;
+  for (int g = warp; g * 32 < nrow; g += nw) {
+    const int row = g * 32 + lane;
+    if (row < nrow) {
+      const int node = row / NC;
+      const double yv = spmv_lane_row<NC>(rp, col, val, p, node, row - NC * node);
+      q[row] = yv;
+      acc = fma(p[row], yv, acc);
     }
   }
   double s = block_sum<NT>(acc, sh);
