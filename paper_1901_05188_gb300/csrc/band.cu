@@ -1,6 +1,9 @@
-// Band-tiled Cholesky factors and the fused subdomain solves of the one-level
-// additive Schwarz term  sum_j R_j^T D_j A_j^-1 R_j  (Sec. 3.1, eqn:onelevelAS)
-// and the coarse correction Z A_H^-1 Z^T (Sec. 3.1, Sec. 3.3.3).
+// Band-tiled Cholesky factors of the one-level additive Schwarz term
+// sum_j R_j^T D_j A_j^-1 R_j  (Sec. 3.1, eqn:onelevelAS) and of the GenEO
+// shift-invert operators, their multi-right-hand-side sweeps, and the
+// extraction of A_j from the global matrix.  The coarse correction and the
+// gather are in coarse.cu, the cluster sweeps of the local solves in
+// schwarz.cu.
 //
 // The paper factors A_j with a sparse direct solver (UMFPack).  Here each
 // A_j is a band matrix in a box numbering whose longest axis runs slowest, held
@@ -319,228 +322,6 @@ __global__ void k_extract_interior(const SubDesc *subs, const BandLayout *lay, i
     }
 }
 
-// ---- gather / coarse --------------------------------------------------------
-
-// Subdomains of node n (global node coordinates i, jj, k): the per-axis
-// candidate lists give the overlapping subdomains containing the node (their
-// count is the partition-of-unity denominator); `visit(S, l)` is called, in a
-// fixed order, for those whose interior holds it (l = local node index).
-template <typename F>
-__device__ __forceinline__ int for_node_subdomains(int i, int jj, int k, int px, int py,
-                                                   const int *__restrict__ cand, int co0, int co1,
-                                                   int co2, const SubDesc *subs, F visit) {
-  const int *ci = cand + (co0 + i) * kMaxCand;
-  const int *cj = cand + (co1 + jj) * kMaxCand;
-  const int *ck = cand + (co2 + k) * kMaxCand;
-  int nci = 0, ncj = 0, nck = 0;
-  while (nci < kMaxCand && ci[nci] >= 0) ++nci;
-  while (ncj < kMaxCand && cj[ncj] >= 0) ++ncj;
-  while (nck < kMaxCand && ck[nck] >= 0) ++nck;
-  for (int c = 0; c < nck; ++c)
-    for (int b = 0; b < ncj; ++b)
-      for (int a = 0; a < nci; ++a) {
-        const SubDesc &S = subs[ci[a] + px * (cj[b] + py * ck[c])];
-        const int l = S.ibox.local(i, jj, k);
-        if (l >= 0) visit(S, l);
-      }
-  return nci * ncj * nck;
-}
-
-// Gather map: per node the xloc offsets (v_int + nc l) of the subdomains whose
-// interior holds it, in the order above (-1 after the last), and the number of
-// overlapping subdomains containing it; kMapFull marks a node with more than
-// kMapSlots interior subdomains, which the gather then visits directly.
-constexpr int kMapSlots = 8;
-constexpr uint8_t kMapFull = 0xFF;
-
-__global__ void k_gather_map(int nnx, int nny, int nnz, int px, int py,
-                             const int *__restrict__ cand, int co0, int co1, int co2,
-                             const SubDesc *subs, int *__restrict__ gmap,
-                             uint8_t *__restrict__ gcnt) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= nnx * nny * nnz) return;
-  const int i = n % nnx, r = n / nnx, jj = r % nny, k = r / nny;
-  int e = 0;
-  bool full = false;
-  const int cnt = for_node_subdomains(i, jj, k, px, py, cand, co0, co1, co2, subs,
-                                      [&](const SubDesc &S, int l) {
-                                        if (e < kMapSlots) gmap[n * kMapSlots + e++] = S.v_int + S.nc * l;
-                                        else full = true;
-                                      });
-  for (; e < kMapSlots; ++e) gmap[n * kMapSlots + e] = -1;
-  gcnt[n] = full ? kMapFull : (uint8_t)cnt;
-}
-
-// z = sum_j R_j^T (D_j x_j + (Z y)_j), one thread per node, deterministic order.
-template <typename T>
-__global__ void __launch_bounds__(256)
-    k_schwarz_gather(int nnx, int nny, int nnz, int px, int py, const int *__restrict__ cand,
-                     int co0, int co1, int co2, const SubDesc *subs,
-                     const int *__restrict__ gmap, const uint8_t *__restrict__ gcnt,
-                     const T *__restrict__ xloc, const double *__restrict__ zy, int pou,
-                     const uint8_t *__restrict__ mask, double *__restrict__ z,
-                     const CGScalars *cg) {
-  if (cg && cg->done) return;
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= nnx * nny * nnz) return;
-  const int nc = subs[0].nc;
-  double o[3] = {0.0, 0.0, 0.0};
-  const int cnt = gcnt[n];
-  auto add = [&](int off, double wgt) {
-    for (int comp = 0; comp < nc; ++comp) {
-      double v = double(xloc[off + comp]);
-      if (pou) v *= mask[nc * n + comp] ? 0.0 : wgt;
-      if (zy) v += zy[off + comp];
-      o[comp] += v;
-    }
-  };
-  if (cnt != kMapFull) {
-    const int4 a = reinterpret_cast<const int4 *>(gmap)[2 * n];
-    const int4 b = reinterpret_cast<const int4 *>(gmap)[2 * n + 1];
-    const int off[kMapSlots] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-    const double wgt = pou ? 1.0 / double(cnt) : 1.0;
-#pragma unroll
-    for (int e = 0; e < kMapSlots; ++e) {
-      if (off[e] < 0) break;
-      add(off[e], wgt);
-    }
-  } else {
-    const int i = n % nnx, r = n / nnx, jj = r % nny, k = r / nny;
-    const int count = for_node_subdomains(i, jj, k, px, py, cand, co0, co1, co2, subs,
-                                          [](const SubDesc &, int) {});
-    const double wgt = pou ? 1.0 / double(count) : 1.0;
-    for_node_subdomains(i, jj, k, px, py, cand, co0, co1, co2, subs,
-                        [&](const SubDesc &S, int l) { add(S.v_int + nc * l, wgt); });
-  }
-  for (int comp = 0; comp < nc; ++comp) z[nc * n + comp] = o[comp];
-}
-
-// Coarse restriction and prolongation stream Z_j (row-major n_int x m_j) in
-// blocks of kZRows rows: the block's m_j * kZRows contiguous values are loaded
-// with coalesced loads, all in flight at once, into shared memory.
-__device__ __forceinline__ double restrict_r(const SubDesc &S, const double *__restrict__ r,
-                                             int nnx, int nny, int l) {
-  const int nc = S.nc, node = l / nc, c = l - nc * node;
-  int gi, gj, gk;
-  S.ibox.global(node, gi, gj, gk);
-  return __ldg(r + nc * (gi + nnx * (gj + nny * gk)) + c);
-}
-
-// partial w_{j,k} over rows [kZRows b, kZRows (b + 1)): warp g takes rows g, g + 8, ..., lane k
-__global__ void __launch_bounds__(256) k_coarse_restrict(const SubDesc *subs, int nnx, int nny,
-                                                         const double *__restrict__ Zp,
-                                                         const double *__restrict__ r,
-                                                         double *__restrict__ wpart, int nchunk,
-                                                         int mcap, const CGScalars *cg) {
-  if (cg && cg->done) return;
-  const int j = blockIdx.y, b = blockIdx.x;
-  const SubDesc &S = subs[j];
-  const int m = S.m, l0 = b * kZRows;
-  if (m == 0 || l0 >= S.n_int) return;
-  const int rows = min(kZRows, S.n_int - l0), cnt = rows * m;
-  __shared__ double zs[kZRows * kMaxModes];
-  __shared__ double rs[kZRows];
-  __shared__ double acc[8][32];
-  const double *Z = Zp + S.z_off + (long long)l0 * m;
-#pragma unroll 4
-  for (int e = threadIdx.x; e < cnt; e += 256) zs[e] = __ldg(Z + e);
-  if (threadIdx.x < rows) rs[threadIdx.x] = restrict_r(S, r, nnx, nny, l0 + threadIdx.x);
-  __syncthreads();
-  const int k = threadIdx.x & 31, g = threadIdx.x >> 5;
-  double s = 0.0;
-  if (k < m)
-    for (int t = g; t < rows; t += 8) s = fma(zs[t * m + k], rs[t], s);
-  acc[g][k] = s;
-  __syncthreads();
-  if (threadIdx.x < m) {
-    double t = 0.0;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) t += acc[q][k];
-    wpart[((long long)j * nchunk + b) * mcap + k] = t;
-  }
-}
-
-// zy_j = Z_j y_j on rows [kZRows b, kZRows (b + 1)) of subdomain j (rows padded
-// to m + 1 values in shared memory against bank conflicts)
-__global__ void __launch_bounds__(256) k_coarse_prolong(const SubDesc *subs,
-                                                        const double *__restrict__ Zp,
-                                                        const double *__restrict__ yH,
-                                                        double *__restrict__ zy,
-                                                        const CGScalars *cg) {
-  if (cg && cg->done) return;
-  const int j = blockIdx.y;
-  const SubDesc &S = subs[j];
-  const int m = S.m, l0 = blockIdx.x * kZRows;
-  if (l0 >= S.n_int) return;
-  const int rows = min(kZRows, S.n_int - l0);
-  if (m == 0) {
-    if (threadIdx.x < rows) zy[S.v_int + l0 + threadIdx.x] = 0.0;
-    return;
-  }
-  __shared__ double zs[kZRows * (kMaxModes + 1)];
-  __shared__ double yj[kMaxModes];
-  if (threadIdx.x < m) yj[threadIdx.x] = yH[S.coff + threadIdx.x];
-  const double *Z = Zp + S.z_off + (long long)l0 * m;
-  const int cnt = rows * m;
-#pragma unroll 4
-  for (int e = threadIdx.x; e < cnt; e += 256) {
-    const int t = e / m;
-    zs[e + t] = __ldg(Z + e);                   // row t at t * (m + 1)
-  }
-  __syncthreads();
-  if (threadIdx.x < rows) {
-    const double *zr = zs + threadIdx.x * (m + 1);
-    double v0 = 0.0, v1 = 0.0;
-    int q = 0;
-    for (; q + 1 < m; q += 2) {
-      v0 = fma(zr[q], yj[q], v0);
-      v1 = fma(zr[q + 1], yj[q + 1], v1);
-    }
-    if (q < m) v0 = fma(zr[q], yj[q], v0);
-    zy[S.v_int + l0 + threadIdx.x] = v0 + v1;
-  }
-}
-
-// w_{j,k} = sum of the row-block partials: warp g adds blocks g, g + 8, ...
-__global__ void __launch_bounds__(256) k_coarse_reduce(const SubDesc *subs,
-                                                       const double *__restrict__ wpart,
-                                                       double *__restrict__ wH, int nchunk,
-                                                       int mcap, const CGScalars *cg) {
-  if (cg && cg->done) return;
-  const int j = blockIdx.x;
-  const SubDesc &S = subs[j];
-  const int k = threadIdx.x & 31, g = threadIdx.x >> 5, m = S.m;
-  __shared__ double acc[8][32];
-  if (m == 0) return;
-  const int nb = (S.n_int + kZRows - 1) / kZRows;
-  double t = 0.0;
-  if (k < m)
-    for (int ch = g; ch < nb; ch += 8) t += wpart[((long long)j * nchunk + ch) * mcap + k];
-  acc[g][k] = t;
-  __syncthreads();
-  if (threadIdx.x < m) {
-    double u = 0.0;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) u += acc[q][k];
-    wH[S.coff + k] = u;
-  }
-}
-
-// y = AHinv w, one warp per row (AHinv symmetric, row-major)
-__global__ void k_coarse_gemv(int nH, const double *__restrict__ Ainv,
-                              const double *__restrict__ w, double *__restrict__ y,
-                              const CGScalars *cg) {
-  if (cg && cg->done) return;
-  int lane = threadIdx.x & 31;
-  int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (row >= nH) return;
-  const double *a = Ainv + (long long)row * nH;
-  double s = 0.0;
-  for (int c = lane; c < nH; c += 32) s += a[c] * w[c];
-  s = warp_sum(s);
-  if (lane == 0) y[row] = s;
-}
-
 }  // namespace
 
 // ---- launchers ----------------------------------------------------------------
@@ -640,39 +421,6 @@ int launch_extract_interior(const SubDesc *d_subs, const BandLayout *d_lay, int 
   return GENEO_OK;
 }
 
-void launch_gather_map(int nx, int ny, int nz, int px, int py, const int *cand,
-                       const int cand_off[3], const SubDesc *d_subs, int *gmap, uint8_t *gcnt,
-                       cudaStream_t s) {
-  int nn = (nx + 1) * (ny + 1) * (nz + 1);
-  k_gather_map<<<(nn + 255) / 256, 256, 0, s>>>(nx + 1, ny + 1, nz + 1, px, py, cand,
-                                                cand_off[0], cand_off[1], cand_off[2], d_subs,
-                                                gmap, gcnt); GENEO_COUNT_LAUNCH();
-}
-
-template <typename T>
-void launch_schwarz_gather(int nx, int ny, int nz, int px, int py, const int *cand,
-                           const int cand_off[3], const SubDesc *d_subs, const int *gmap,
-                           const uint8_t *gcnt, const T *xloc, const double *zy, int pou,
-                           const uint8_t *mask, double *z, const CGScalars *cg, cudaStream_t s) {
-  int nn = (nx + 1) * (ny + 1) * (nz + 1);
-  k_schwarz_gather<T><<<(nn + 255) / 256, 256, 0, s>>>(nx + 1, ny + 1, nz + 1, px, py, cand,
-                                                      cand_off[0], cand_off[1], cand_off[2],
-                                                      d_subs, gmap, gcnt, xloc, zy, pou, mask,
-                                                      z, cg); GENEO_COUNT_LAUNCH();
-}
-
-void launch_coarse_apply(const SubDesc *d_subs, int nsub, int max_nint, int nnx, int nny,
-                         const double *Zp, const double *r, double *wpart, double *wH,
-                         double *yH, double *zy, const double *AHinv, int nH, int mcap,
-                         const CGScalars *cg, cudaStream_t s) {
-  const int nchunk = restrict_chunks(max_nint);
-  k_coarse_restrict<<<dim3(nchunk, nsub), 256, 0, s>>>(d_subs, nnx, nny, Zp, r, wpart, nchunk,
-                                                      mcap, cg); GENEO_COUNT_LAUNCH();
-  k_coarse_reduce<<<nsub, 256, 0, s>>>(d_subs, wpart, wH, nchunk, mcap, cg); GENEO_COUNT_LAUNCH();
-  k_coarse_gemv<<<(nH * 32 + 255) / 256, 256, 0, s>>>(nH, AHinv, wH, yH, cg); GENEO_COUNT_LAUNCH();
-  k_coarse_prolong<<<dim3(nchunk, nsub), 256, 0, s>>>(d_subs, Zp, yH, zy, cg); GENEO_COUNT_LAUNCH();
-}
-
 template int launch_band_clear<double>(const BandLayout *, int, double *, long long, cudaStream_t);
 template int launch_band_clear<float>(const BandLayout *, int, float *, long long, cudaStream_t);
 template int launch_band_cholesky<double>(const BandLayout *, int, int, int, double *, double *,
@@ -685,13 +433,4 @@ template int launch_extract_interior<double>(const SubDesc *, const BandLayout *
 template int launch_extract_interior<float>(const SubDesc *, const BandLayout *, int, int, int,
                                             int, int, const int32_t *, const double *, float *,
                                             cudaStream_t);
-template void launch_schwarz_gather<double>(int, int, int, int, int, const int *, const int[3],
-                                            const SubDesc *, const int *, const uint8_t *,
-                                            const double *, const double *, int, const uint8_t *,
-                                            double *, const CGScalars *, cudaStream_t);
-template void launch_schwarz_gather<float>(int, int, int, int, int, const int *, const int[3],
-                                           const SubDesc *, const int *, const uint8_t *,
-                                           const float *, const double *, int, const uint8_t *,
-                                           double *, const CGScalars *, cudaStream_t);
-
 }  // namespace geneo
