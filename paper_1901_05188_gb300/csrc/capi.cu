@@ -243,7 +243,12 @@ int geneo_create(geneo_ctx **out, void *cuda_stream) {
   GENEO_CUDA_TRY(cudaGetDevice(&c->device));
   GENEO_CUDA_TRY(cudaMallocHost(&c->cg_host, sizeof(CGScalars)));
   GENEO_CUDA_TRY(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
-  GENEO_CUDA_TRY(cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking));
+  // The eigensolve is the set-up's critical path; the subdomain factorisation
+  // that overlaps it runs at the default priority and fills the SMs it leaves.
+  int least = 0, greatest = 0;
+  GENEO_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  GENEO_CUDA_TRY(cudaStreamCreateWithPriority(&c->eig_stream, cudaStreamNonBlocking, greatest));
+  GENEO_CUDA_TRY(cudaStreamCreateWithPriority(&c->side_stream, cudaStreamNonBlocking, greatest));
   GENEO_CUDA_TRY(cudaStreamCreateWithFlags(&c->fac_stream, cudaStreamNonBlocking));
   GENEO_CUDA_TRY(cudaStreamCreateWithFlags(&c->fac_side, cudaStreamNonBlocking));
   *out = c;
@@ -269,6 +274,7 @@ int geneo_destroy(geneo_ctx *c) {
   if (c->ws0_owned && c->ws0) cudaFree(c->ws0);
   if (c->cg_host) cudaFreeHost(c->cg_host);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->eig_stream) cudaStreamDestroy(c->eig_stream);
   if (c->side_stream) cudaStreamDestroy(c->side_stream);
   if (c->fac_stream) cudaStreamDestroy(c->fac_stream);
   if (c->fac_side) cudaStreamDestroy(c->fac_side);
@@ -1381,11 +1387,13 @@ int geneo_setup(geneo_ctx *c, const geneo_partition *part, const geneo_modes *mo
       return st;
   }
   GENEO_CUDA_TRY(cudaEventRecord(ev[2], fs));
-  GENEO_CUDA_TRY(cudaStreamWaitEvent(s, e_extracted, 0));
+  cudaStream_t es = c->eig_stream;
+  GENEO_CUDA_TRY(cudaStreamWaitEvent(es, e_extracted, 0));
   if (pc.mcap > 1) {
-    if ((st = setup_coarse(c, P, s))) return st;
+    if ((st = setup_coarse(c, P, es))) return st;
   }
-  GENEO_CUDA_TRY(cudaEventRecord(ev[3], s));
+  GENEO_CUDA_TRY(cudaEventRecord(ev[3], es));
+  GENEO_CUDA_TRY(cudaStreamWaitEvent(s, ev[3], 0));
   GENEO_CUDA_TRY(cudaStreamWaitEvent(s, ev[2], 0));
   cudaEventDestroy(e_ready);
   cudaEventDestroy(e_extracted);
