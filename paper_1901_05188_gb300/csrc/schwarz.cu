@@ -15,6 +15,16 @@
 // warp's dependent FP64 instructions are the critical path.  Tiles of the next
 // step are loaded into registers during the barrier phase and the step after
 // that is prefetched into L2.
+//
+// Three other forms of the same sweep follow, all chosen among by the set-up
+// autotuner: the look-ahead sweep (far warps multiply row I+1 while the chain
+// finishes row I, one split cluster barrier per row); and the staged forms,
+// where one thread copies each step's tiles into shared memory a step ahead
+// (cp.async.bulk completed on an mbarrier) and the per-CTA partials travel by
+// st.async into every CTA's buffer, completing a transaction count on that
+// CTA's mbarrier, so no cluster barrier remains inside a sweep (R rows per
+// step, or the look-ahead order where the far warps push row I+1's partial
+// while the chain finishes row I).
 #include <cooperative_groups.h>
 
 #include "band.cuh"
