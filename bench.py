@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-darcy", action="store_true")
     ap.add_argument("--no-c3", action="store_true",
                     help="skip the 128x64x48 mixed-precision leg")
+    ap.add_argument("--batch-blocks", type=int, default=32,
+                    help="blocks of the uneven batched-solve workload to run (0 skips it)")
     ap.add_argument("--serve-requests", type=int, default=10,
                     help="requests of the serving sample (uneven laminate blocks)")
     return ap.parse_args()
@@ -430,6 +432,35 @@ def run_ours(args):
                                                 "peak_mem_gb", "failed") if k in r}
                              for r in sv["runs"]])
 
+    # batched uneven solves: the first blocks of the seeded batch (8e3-1e5
+    # elements, 4-24 plies, 2-64 subdomains), all submitted at once to the
+    # concurrent-slot server (mixed precision), throughput and latency
+    batch = None
+    if rank == 0 and world == 1 and args.batch_blocks > 0:
+        from paper_1901_05188_gb300.serve import GeneoServer, latency_summary
+        from workloads.batch import batch_blocks
+        blocks = batch_blocks(args.batch_blocks, seed=3)
+        srv = GeneoServer(slots=4)
+        try:
+            t0 = time.perf_counter()
+            reqs = [srv.submit(pb, prec=pkg.GENEO_MIXED_FP32, tol=TOL, key=pb["name"], arrival=t0)
+                    for pb in blocks]
+            for rq in reqs:
+                rq.wait()
+            wall = time.perf_counter() - t0
+        finally:
+            srv.close()
+        summ = latency_summary(reqs)
+        dofs = [3 * (pb["nx"] + 1) * (pb["ny"] + 1) * (pb["nz"] + 1) for pb in blocks]
+        parts = [pb["partition"][0] * pb["partition"][1] * pb["partition"][2] for pb in blocks]
+        batch = dict(workload=f"first {len(blocks)} blocks of the seeded batch (seed 3): "
+                              f"{min(dofs)}-{max(dofs)} dofs, {min(parts)}-{max(parts)} subdomains, "
+                              "4-24 plies, burst of independent solves",
+                     precision="mixed", slots=4, wall_s=wall,
+                     solves_per_s=len(blocks) / wall, dofs_per_s=sum(dofs) / wall,
+                     p50_ms=summ.get("p50_ms"), p99_ms=summ.get("p99_ms"),
+                     failed=summ.get("failed", len(blocks)))
+
     # the paper's second application at its full grid: Darcy on SPE10's 60x220x85
     # cells with a synthetic layered permeability (contrast 1.4e10), FP64
     darcy = None
@@ -505,7 +536,7 @@ def run_ours(args):
                                         staged=st["schwarz_staged"],
                                         chosen_by="set-up autotuner"),
                     accuracy_vs_oracle=acc, mixed_precision=mixed, serving=serving,
-                    darcy_spe10=darcy, c3_mixed_vs_fp64=c3)
+                    darcy_spe10=darcy, c3_mixed_vs_fp64=c3, batched_uneven=batch)
         print(json.dumps(line))
     s.close()
     if world > 1:
