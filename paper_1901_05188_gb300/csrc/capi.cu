@@ -248,6 +248,7 @@ int geneo_create(geneo_ctx **out, void *cuda_stream) {
   int least = 0, greatest = 0;
   GENEO_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
   GENEO_CUDA_TRY(cudaStreamCreateWithPriority(&c->eig_stream, cudaStreamNonBlocking, greatest));
+  GENEO_CUDA_TRY(cudaStreamCreateWithPriority(&c->eig_stream2, cudaStreamNonBlocking, greatest));
   GENEO_CUDA_TRY(cudaStreamCreateWithPriority(&c->side_stream, cudaStreamNonBlocking, greatest));
   GENEO_CUDA_TRY(cudaStreamCreateWithFlags(&c->fac_stream, cudaStreamNonBlocking));
   GENEO_CUDA_TRY(cudaStreamCreateWithFlags(&c->fac_side, cudaStreamNonBlocking));
@@ -275,6 +276,7 @@ int geneo_destroy(geneo_ctx *c) {
   if (c->cg_host) cudaFreeHost(c->cg_host);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->eig_stream) cudaStreamDestroy(c->eig_stream);
+  if (c->eig_stream2) cudaStreamDestroy(c->eig_stream2);
   if (c->side_stream) cudaStreamDestroy(c->side_stream);
   if (c->fac_stream) cudaStreamDestroy(c->fac_stream);
   if (c->fac_side) cudaStreamDestroy(c->fac_side);
@@ -940,60 +942,107 @@ static int setup_coarse(geneo_ctx *c, SetupPlan &P, cudaStream_t s) {
   GENEO_CUDA_TRY(cudaMemsetAsync(pc.W, 0, (size_t)nsub * sW * sizeof(double), s));
   GENEO_CUDA_TRY(cudaMemsetAsync(pc.T1, 0, (size_t)nsub * sW * sizeof(double), s));
   launch_random_block(pc.d_subs, nsub, npad, pc.W, p, sW, p, 0x5eed1234ull, s);
+  double *const Rinv = pc.Racc + (long long)nsub * p * p;   // second half of Racc's buffer
   for (int pass = 0; pass < 2; ++pass) {
     launch_tsdots(pc.d_subs, nsub, npad, pc.W, p, sW, p, pc.W, p, sW, p, pc.Hpart, kDotChunks,
                   pc.G, (long long)p * p, s);
-    launch_cholqr(pc.d_subs, nsub, npad, pc.G, pc.W, p, pc.Racc, pass == 0, 0.0, s);
+    launch_cholqr(pc.d_subs, nsub, npad, pc.G, pc.W, p, pc.Racc, Rinv, pass == 0, 0.0, s);
   }
   launch_copy_block(pc.d_subs, nsub, npad, pc.W, p, sW, pc.V, ldv, sV, p, s);
   std::vector<double> ev((size_t)nsub * kdim), er((size_t)nsub * kdim);
+  // The iterations run on two groups of subdomains, each on its own stream, so
+  // that one group's re-orthogonalisation and small kernels fill the SMs the
+  // other group's band sweeps leave.  The groups share no buffer: every array
+  // below is offset by the group's first subdomain (per-subdomain strides;
+  // the scratch of the projections at its largest stride).
+  struct Group {
+    int j0, n;
+    cudaStream_t st;
+  };
+  const int ngrp = nsub >= 2 ? 2 : 1;
+  const int half = (nsub + 1) / 2;
+  const Group grp[2] = {{0, ngrp == 2 ? half : nsub, s}, {half, nsub - half, c->eig_stream2}};
+  const long long nout = std::max((long long)kdim * p, (long long)mcap * mcap);
+  struct EventPair {             // destroyed on every return path
+    cudaEvent_t fork = nullptr, join = nullptr;
+    ~EventPair() {
+      if (fork) cudaEventDestroy(fork);
+      if (join) cudaEventDestroy(join);
+    }
+  } ev2;
+  GENEO_CUDA_TRY(cudaEventCreateWithFlags(&ev2.fork, cudaEventDisableTiming));
+  GENEO_CUDA_TRY(cudaEventCreateWithFlags(&ev2.join, cudaEventDisableTiming));
+  cudaEvent_t e_fork = ev2.fork, e_join = ev2.join;
+  GENEO_CUDA_TRY(cudaEventRecord(e_fork, s));
+  if (ngrp == 2) GENEO_CUDA_TRY(cudaStreamWaitEvent(grp[1].st, e_fork, 0));
+  auto lanczos_step = [&](const Group &g, int k) -> int {
+    const long long j0 = g.j0;
+    const int n = g.n;
+    cudaStream_t gs = g.st;
+    const SubDesc *subs = pc.d_subs + j0;
+    const BandLayout *lay = pc.d_lay_neu + j0;
+    double *V = pc.V + j0 * sV, *W = pc.W + j0 * sW, *T1 = pc.T1 + j0 * sW;
+    double *Hm = pc.Hm + j0 * kdim * kdim, *Hs = pc.Hs + j0 * nout;
+    double *Hpart = pc.Hpart + j0 * kDotChunks * nout, *G = pc.G + j0 * p * p;
+    double *Racc = pc.Racc + j0 * p * p, *Ri = Rinv + j0 * p * p, *Rblk = pc.Rblk + j0 * p * p;
+    int *gate = pc.gate + j0;
+    int r;
+    // W = L^-1 B L^-T V_k
+    if ((r = launch_band_solve_dense(lay, n, npad, pc.neuL, pc.neuU, V + k * p, sV, ldv, T1, sW,
+                                     p, p, 2, gs)))
+      return r;
+    launch_bloc_mv(subs, n, P.max_nodes_neu, pc.Bloc, T1, W, sW, p, gs);
+    if ((r = launch_band_solve_dense(lay, n, npad, pc.neuL, pc.neuU, W, sW, p, W, sW, p, p, 1, gs)))
+      return r;
+    const int na = (k + 1) * p;
+    // full re-orthogonalisation against V: a second pass only for the
+    // subdomains where the first one removed most of a column
+    for (int pass = 0; pass < 2; ++pass) {
+      const int *gt = pass == 0 ? nullptr : gate;
+      if (pass == 1) {
+        launch_tsdots(subs, n, npad, W, p, sW, p, W, p, sW, p, Hpart, kDotChunks, G,
+                      (long long)p * p, gs);
+        launch_reorth_gate(n, G, p, Hs, na, (long long)na * p, gate, gs);
+      }
+      launch_tsdots(subs, n, npad, V, ldv, sV, na, W, p, sW, p, Hpart, kDotChunks, Hs,
+                    (long long)na * p, gs, gt);
+      launch_hm_accum(n, Hm, kdim, Hs, na, k, p, gs);
+      launch_tsgemm(subs, n, npad, V, ldv, sV, na, Hs, p, (long long)na * p, W, p, sW, p, -1.0,
+                    1.0, gs, gt);
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+      launch_tsdots(subs, n, npad, W, p, sW, p, W, p, sW, p, Hpart, kDotChunks, G,
+                    (long long)p * p, gs);
+      launch_cholqr(subs, n, npad, G, W, p, Racc, Ri, pass == 0, abs_tiny, gs);
+    }
+    launch_hm_subdiag(n, Hm, kdim, Racc, k, p, Rblk, gs);
+    if (k + 1 < pc.ksteps) launch_copy_block(subs, n, npad, W, p, sW, V + (k + 1) * p, ldv, sV, p, gs);
+    return GENEO_OK;
+  };
   int first_block = 0;
   pc.eig_cycles = 0;
   pc.lanczos_steps = 0;
   for (int cycle = 0; cycle < pc.max_cycles; ++cycle) {
     pc.lanczos_steps += pc.ksteps - first_block;
-    for (int k = first_block; k < pc.ksteps; ++k) {
-      // W = L^-1 B L^-T V_k
-      if ((st = launch_band_solve_dense(pc.d_lay_neu, nsub, npad, pc.neuL, pc.neuU, pc.V + k * p,
-                                        sV, ldv, pc.T1, sW, p, p, 2, s)))
-        return st;
-      launch_bloc_mv(pc.d_subs, nsub, P.max_nodes_neu, pc.Bloc, pc.T1, pc.W, sW, p, s);
-      if ((st = launch_band_solve_dense(pc.d_lay_neu, nsub, npad, pc.neuL, pc.neuU, pc.W, sW, p,
-                                        pc.W, sW, p, p, 1, s)))
-        return st;
-      const int na = (k + 1) * p;
-      // full re-orthogonalisation against V: a second pass only for the
-      // subdomains where the first one removed most of a column
-      for (int pass = 0; pass < 2; ++pass) {
-        const int *gate = pass == 0 ? nullptr : pc.gate;
-        if (pass == 1) {
-          launch_tsdots(pc.d_subs, nsub, npad, pc.W, p, sW, p, pc.W, p, sW, p, pc.Hpart,
-                        kDotChunks, pc.G, (long long)p * p, s);
-          launch_reorth_gate(nsub, pc.G, p, pc.Hs, na, (long long)na * p, pc.gate, s);
-        }
-        launch_tsdots(pc.d_subs, nsub, npad, pc.V, ldv, sV, na, pc.W, p, sW, p, pc.Hpart,
-                      kDotChunks, pc.Hs, (long long)na * p, s, gate);
-        launch_hm_accum(nsub, pc.Hm, kdim, pc.Hs, na, k, p, s);
-        launch_tsgemm(pc.d_subs, nsub, npad, pc.V, ldv, sV, na, pc.Hs, p, (long long)na * p,
-                      pc.W, p, sW, p, -1.0, 1.0, s, gate);
-      }
-      for (int pass = 0; pass < 2; ++pass) {
-        launch_tsdots(pc.d_subs, nsub, npad, pc.W, p, sW, p, pc.W, p, sW, p, pc.Hpart,
-                      kDotChunks, pc.G, (long long)p * p, s);
-        launch_cholqr(pc.d_subs, nsub, npad, pc.G, pc.W, p, pc.Racc, pass == 0, abs_tiny, s);
-      }
-      launch_hm_subdiag(nsub, pc.Hm, kdim, pc.Racc, k, p, pc.Rblk, s);
-      if (k + 1 < pc.ksteps)
-        launch_copy_block(pc.d_subs, nsub, npad, pc.W, p, sW, pc.V + (k + 1) * p, ldv, sV, p, s);
-    }
+    for (int k = first_block; k < pc.ksteps; ++k)
+      for (int g = 0; g < ngrp; ++g)
+        if ((st = lanczos_step(grp[g], k))) return st;
     GENEO_CUDA_TRY(cudaGetLastError());
-    if ((st = launch_ritz_eig(nsub, pc.Hm, kdim, std::max(kk, mcap), p, pc.Rblk, pc.Eval, pc.Evec,
-                              pc.Eres, s)))
-      return st;
+    for (int g = 0; g < ngrp; ++g) {
+      const long long j0 = grp[g].j0;
+      if ((st = launch_ritz_eig(grp[g].n, pc.Hm + j0 * kdim * kdim, kdim, std::max(kk, mcap), p,
+                                pc.Rblk + j0 * p * p, pc.Eval + j0 * kdim,
+                                pc.Evec + j0 * kdim * kdim, pc.Eres + j0 * kdim, grp[g].st)))
+        return st;
+      GENEO_CUDA_TRY(cudaMemcpyAsync(ev.data() + j0 * kdim, pc.Eval + j0 * kdim,
+                                     (size_t)grp[g].n * kdim * sizeof(double),
+                                     cudaMemcpyDeviceToHost, grp[g].st));
+      GENEO_CUDA_TRY(cudaMemcpyAsync(er.data() + j0 * kdim, pc.Eres + j0 * kdim,
+                                     (size_t)grp[g].n * kdim * sizeof(double),
+                                     cudaMemcpyDeviceToHost, grp[g].st));
+    }
     ++pc.eig_cycles;
-    GENEO_CUDA_TRY(cudaMemcpyAsync(ev.data(), pc.Eval, ev.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-    GENEO_CUDA_TRY(cudaMemcpyAsync(er.data(), pc.Eres, er.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-    GENEO_CUDA_TRY(cudaStreamSynchronize(s));
+    for (int g = 0; g < ngrp; ++g) GENEO_CUDA_TRY(cudaStreamSynchronize(grp[g].st));
     // converged when every wanted Ritz pair has residual <= tol * theta
     bool conv = true;
     for (int j = 0; j < nsub && conv; ++j)
@@ -1007,13 +1056,25 @@ static int setup_coarse(geneo_ctx *c, SetupPlan &P, cudaStream_t s) {
       }
     if (conv || cycle + 1 == pc.max_cycles) break;
     // restart: V[:, :kk] = V S[:, :kk], V[:, kk:kk+p] = next Lanczos block
-    launch_tsgemm(pc.d_subs, nsub, npad, pc.V, ldv, sV, kdim, pc.Evec, kdim,
-                  (long long)kdim * kdim, pc.Vt, kk, sT, kk, 1.0, 0.0, s);
-    for (int b = 0; b < kk / p; ++b)
-      launch_copy_block(pc.d_subs, nsub, npad, pc.Vt + b * p, kk, sT, pc.V + b * p, ldv, sV, p, s);
-    launch_copy_block(pc.d_subs, nsub, npad, pc.W, p, sW, pc.V + kk, ldv, sV, p, s);
-    launch_restart_hm(nsub, pc.Hm, kdim, pc.Eval, pc.Evec, pc.Rblk, kk, p, s);
+    for (int g = 0; g < ngrp; ++g) {
+      const long long j0 = grp[g].j0;
+      const int n = grp[g].n;
+      cudaStream_t gs = grp[g].st;
+      const SubDesc *subs = pc.d_subs + j0;
+      double *V = pc.V + j0 * sV, *Vt = pc.Vt + j0 * sT;
+      launch_tsgemm(subs, n, npad, V, ldv, sV, kdim, pc.Evec + j0 * kdim * kdim, kdim,
+                    (long long)kdim * kdim, Vt, kk, sT, kk, 1.0, 0.0, gs);
+      for (int b = 0; b < kk / p; ++b)
+        launch_copy_block(subs, n, npad, Vt + b * p, kk, sT, V + b * p, ldv, sV, p, gs);
+      launch_copy_block(subs, n, npad, pc.W + j0 * sW, p, sW, V + kk, ldv, sV, p, gs);
+      launch_restart_hm(n, pc.Hm + j0 * kdim * kdim, kdim, pc.Eval + j0 * kdim,
+                        pc.Evec + j0 * kdim * kdim, pc.Rblk + j0 * p * p, kk, p, gs);
+    }
     first_block = kk / p;
+  }
+  if (ngrp == 2) {
+    GENEO_CUDA_TRY(cudaEventRecord(e_join, grp[1].st));
+    GENEO_CUDA_TRY(cudaStreamWaitEvent(s, e_join, 0));
   }
   // Ritz vectors y = V s, then p = L^-T y, normalised to ||p||_2 = 1
   const long long sP = (long long)npad * mcap;

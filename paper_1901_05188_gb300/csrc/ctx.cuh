@@ -11,6 +11,7 @@ struct geneo_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;        // private stream used only to capture graphs
   cudaStream_t eig_stream = nullptr;        // GenEO eigensolve and coarse space (highest priority)
+  cudaStream_t eig_stream2 = nullptr;       // second group of the Lanczos iterations (same)
   cudaStream_t side_stream = nullptr;       // its look-ahead factorisation (highest priority)
   cudaStream_t fac_stream = nullptr;        // subdomain factorisation, overlapping the eigensolve
   cudaStream_t fac_side = nullptr;          // its look-ahead stream

@@ -906,9 +906,7 @@ void launch_tsgemm(const SubDesc *d_subs, int nsub, int npad, const double *A, i
 }
 
 void launch_cholqr(const SubDesc *d_subs, int nsub, int npad, const double *G, double *W,
-                   int p, double *Racc, int first, double abs_tiny, cudaStream_t s) {
-  // Rinv stored right after Racc's nsub*p*p entries
-  double *Rinv = Racc + (long long)nsub * p * p;
+                   int p, double *Racc, double *Rinv, int first, double abs_tiny, cudaStream_t s) {
   k_cholqr_small<<<nsub, 32, 0, s>>>(G, p, Rinv, Racc, first, abs_tiny); GENEO_COUNT_LAUNCH();
   dim3 g((npad + 255) / 256, nsub);
   k_rowmul<<<g, 256, 0, s>>>(d_subs, npad, W, p, Rinv); GENEO_COUNT_LAUNCH();

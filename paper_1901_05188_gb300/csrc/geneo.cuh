@@ -52,9 +52,9 @@ void launch_tsgemm(const SubDesc *d_subs, int nsub, int npad, const double *A, i
                    const int *gate = nullptr);
 
 // Cholesky-QR step on p x p Gram matrices: R = chol(G), W <- W R^-1 (columns
-// with a vanishing pivot are zeroed); Racc <- R Racc.
+// with a vanishing pivot are zeroed); Racc <- R Racc.  Rinv: nsub p x p scratch.
 void launch_cholqr(const SubDesc *d_subs, int nsub, int npad, const double *G, double *W,
-                   int p, double *Racc, int first, double abs_tiny, cudaStream_t s);
+                   int p, double *Racc, double *Rinv, int first, double abs_tiny, cudaStream_t s);
 // Thick restart: Hm <- diag(theta_0..kk-1) with the coupling block R_s S[last p rows, :kk].
 void launch_restart_hm(int nsub, double *Hm, int kdim, const double *Eval, const double *Evec,
                        const double *Rblk, int kk, int p, cudaStream_t s);
