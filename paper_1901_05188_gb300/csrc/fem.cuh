@@ -86,70 +86,68 @@ __device__ inline void rotate_voigt(const double C[36], double theta, double phi
     }
 }
 
+// Integral over the box element of d_j N_a * d_l N_b (trilinear N, axis-aligned
+// box of sides h): a product over the axes of 1D integrals of the linear
+// factors, with s = +-1 the slope sign of a factor and 1/h its derivative's
+// size: int f_a f_b = h/3 (same side) or h/6, int f_a' f_b = s_a/2,
+// int f_a f_b' = s_b/2, int f_a' f_b' = s_a s_b / h.  The 2x2x2 Gauss rule is
+// exact for these products, so this equals the quadrature to rounding.
+__device__ __forceinline__ double box_grad_integral(const double sa[3], const double sb[3],
+                                                    const double h[3], const double ih[3],
+                                                    int j, int l) {
+  double v = 1.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double f;
+    if (d == j && d == l) f = sa[d] * sb[d] * ih[d];
+    else if (d == j) f = 0.5 * sa[d];
+    else if (d == l) f = 0.5 * sb[d];
+    else f = (sa[d] == sb[d] ? (1.0 / 3.0) : (1.0 / 6.0)) * h[d];
+    v *= f;
+  }
+  return v;
+}
+
 // 3x3 block K_ab of the Q1 element stiffness of an hx x hy x hz box with
 // global-frame Voigt stiffness C (row-major 6x6):
 //   K_ab[i][k] = sum_{j,l} C_ijkl G_ab[j][l],  G_ab[j][l] = int dN_a/dx_j dN_b/dx_l,
-// the integral taken with the 2x2x2 Gauss-Legendre rule (Sec. 2).
+// the integrals in closed form, equal to the 2x2x2 Gauss-Legendre rule (Sec. 2).
 // Local node a sits at corner (a & 1, (a >> 1) & 1, (a >> 2) & 1).
 __device__ inline void element_block(const double *__restrict__ C, double hx, double hy,
                                      double hz, int a, int b, double K[9]) {
-  const double g = 0.57735026918962576451;  // 1/sqrt(3)
-  double sa[3] = {double(2 * (a & 1) - 1), double(2 * ((a >> 1) & 1) - 1),
-                  double(2 * ((a >> 2) & 1) - 1)};
-  double sb[3] = {double(2 * (b & 1) - 1), double(2 * ((b >> 1) & 1) - 1),
-                  double(2 * ((b >> 2) & 1) - 1)};
-  double h[3] = {hx, hy, hz};
-  double detJ = hx * hy * hz * 0.125;
-  double G[3][3];
-  for (int j = 0; j < 3; ++j)
-    for (int l = 0; l < 3; ++l) G[j][l] = 0.0;
-  for (int q = 0; q < 8; ++q) {
-    double t[3] = {(q & 1) ? g : -g, (q & 2) ? g : -g, (q & 4) ? g : -g};
-    double fa[3], fb[3];
-    for (int d = 0; d < 3; ++d) {
-      fa[d] = 0.5 * (1.0 + sa[d] * t[d]);
-      fb[d] = 0.5 * (1.0 + sb[d] * t[d]);
-    }
-    // dN/dx_d = (s_d / h_d) * prod_{e != d} f_e
-    double ga[3] = {sa[0] / h[0] * fa[1] * fa[2], sa[1] / h[1] * fa[0] * fa[2],
-                    sa[2] / h[2] * fa[0] * fa[1]};
-    double gb[3] = {sb[0] / h[0] * fb[1] * fb[2], sb[1] / h[1] * fb[0] * fb[2],
-                    sb[2] / h[2] * fb[0] * fb[1]};
-    for (int j = 0; j < 3; ++j)
-      for (int l = 0; l < 3; ++l) G[j][l] += ga[j] * gb[l];
-  }
-  for (int i = 0; i < 3; ++i)
-    for (int k = 0; k < 3; ++k) {
-      double s = 0.0;
-      for (int j = 0; j < 3; ++j)
-        for (int l = 0; l < 3; ++l) s += C[6 * voigt(i, j) + voigt(k, l)] * G[j][l];
-      K[3 * i + k] = s * detJ;
-    }
-}
-
-// int K grad N_a . grad N_b over an hx x hy x hz box with K = diag(kd),
-// 2x2x2 Gauss points (local node a at corner (a & 1, (a >> 1) & 1, a >> 2)).
-__device__ inline double darcy_entry(const double *__restrict__ kd, double hx, double hy,
-                                     double hz, int a, int b) {
-  const double g = 0.57735026918962576451;  // 1/sqrt(3)
   const double sa[3] = {double(2 * (a & 1) - 1), double(2 * ((a >> 1) & 1) - 1),
                         double(2 * ((a >> 2) & 1) - 1)};
   const double sb[3] = {double(2 * (b & 1) - 1), double(2 * ((b >> 1) & 1) - 1),
                         double(2 * ((b >> 2) & 1) - 1)};
   const double h[3] = {hx, hy, hz};
-  double G[3] = {0.0, 0.0, 0.0};
-  for (int q = 0; q < 8; ++q) {
-    const double t[3] = {(q & 1) ? g : -g, (q & 2) ? g : -g, (q & 4) ? g : -g};
-    double fa[3], fb[3];
-    for (int d = 0; d < 3; ++d) {
-      fa[d] = 0.5 * (1.0 + sa[d] * t[d]);
-      fb[d] = 0.5 * (1.0 + sb[d] * t[d]);
+  const double ih[3] = {1.0 / hx, 1.0 / hy, 1.0 / hz};
+  double G[3][3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+#pragma unroll
+    for (int l = 0; l < 3; ++l) G[j][l] = box_grad_integral(sa, sb, h, ih, j, l);
+  for (int i = 0; i < 3; ++i)
+    for (int k = 0; k < 3; ++k) {
+      double s = 0.0;
+      for (int j = 0; j < 3; ++j)
+        for (int l = 0; l < 3; ++l) s += C[6 * voigt(i, j) + voigt(k, l)] * G[j][l];
+      K[3 * i + k] = s;
     }
-    G[0] += (sa[0] / h[0] * fa[1] * fa[2]) * (sb[0] / h[0] * fb[1] * fb[2]);
-    G[1] += (sa[1] / h[1] * fa[0] * fa[2]) * (sb[1] / h[1] * fb[0] * fb[2]);
-    G[2] += (sa[2] / h[2] * fa[0] * fa[1]) * (sb[2] / h[2] * fb[0] * fb[1]);
-  }
-  return (kd[0] * G[0] + kd[1] * G[1] + kd[2] * G[2]) * (hx * hy * hz * 0.125);
+}
+
+// int K grad N_a . grad N_b over an hx x hy x hz box with K = diag(kd), in closed
+// form, equal to 2x2x2 Gauss points (local node a at corner (a & 1, (a >> 1) & 1, a >> 2)).
+__device__ inline double darcy_entry(const double *__restrict__ kd, double hx, double hy,
+                                     double hz, int a, int b) {
+  const double sa[3] = {double(2 * (a & 1) - 1), double(2 * ((a >> 1) & 1) - 1),
+                        double(2 * ((a >> 2) & 1) - 1)};
+  const double sb[3] = {double(2 * (b & 1) - 1), double(2 * ((b >> 1) & 1) - 1),
+                        double(2 * ((b >> 2) & 1) - 1)};
+  const double h[3] = {hx, hy, hz};
+  const double ih[3] = {1.0 / hx, 1.0 / hy, 1.0 / hz};
+  return kd[0] * box_grad_integral(sa, sb, h, ih, 0, 0) +
+         kd[1] * box_grad_integral(sa, sb, h, ih, 1, 1) +
+         kd[2] * box_grad_integral(sa, sb, h, ih, 2, 2);
 }
 
 }  // namespace geneo
