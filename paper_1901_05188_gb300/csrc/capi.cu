@@ -1019,16 +1019,20 @@ static int setup_coarse(geneo_ctx *c, SetupPlan &P, cudaStream_t s) {
     if (k + 1 < pc.ksteps) launch_copy_block(subs, n, npad, W, p, sW, V + (k + 1) * p, ldv, sV, p, gs);
     return GENEO_OK;
   };
+  // Each group restarts until every wanted Ritz pair of its own subdomains has
+  // converged; a converged group keeps the Ritz vectors of that cycle.
   int first_block = 0;
+  bool done[2] = {false, false};
   pc.eig_cycles = 0;
   pc.lanczos_steps = 0;
   for (int cycle = 0; cycle < pc.max_cycles; ++cycle) {
     pc.lanczos_steps += pc.ksteps - first_block;
     for (int k = first_block; k < pc.ksteps; ++k)
       for (int g = 0; g < ngrp; ++g)
-        if ((st = lanczos_step(grp[g], k))) return st;
+        if (!done[g] && (st = lanczos_step(grp[g], k))) return st;
     GENEO_CUDA_TRY(cudaGetLastError());
     for (int g = 0; g < ngrp; ++g) {
+      if (done[g]) continue;
       const long long j0 = grp[g].j0;
       if ((st = launch_ritz_eig(grp[g].n, pc.Hm + j0 * kdim * kdim, kdim, std::max(kk, mcap), p,
                                 pc.Rblk + j0 * p * p, pc.Eval + j0 * kdim,
@@ -1044,19 +1048,26 @@ static int setup_coarse(geneo_ctx *c, SetupPlan &P, cudaStream_t s) {
     ++pc.eig_cycles;
     for (int g = 0; g < ngrp; ++g) GENEO_CUDA_TRY(cudaStreamSynchronize(grp[g].st));
     // converged when every wanted Ritz pair has residual <= tol * theta
-    bool conv = true;
-    for (int j = 0; j < nsub && conv; ++j)
-      for (int i = 0; i < mcap; ++i) {
-        double th = ev[(size_t)j * kdim + i];
-        if (!(th > 1e-12 / std::fabs(sigma))) break;      // infinite eigenvalues follow
-        if (!(er[(size_t)j * kdim + i] <= pc.eig_tol * th)) {
-          conv = false;
-          break;
+    bool all = true;
+    for (int g = 0; g < ngrp; ++g) {
+      if (done[g]) continue;
+      bool conv = true;
+      for (int j = grp[g].j0; j < grp[g].j0 + grp[g].n && conv; ++j)
+        for (int i = 0; i < mcap; ++i) {
+          double th = ev[(size_t)j * kdim + i];
+          if (!(th > 1e-12 / std::fabs(sigma))) break;      // infinite eigenvalues follow
+          if (!(er[(size_t)j * kdim + i] <= pc.eig_tol * th)) {
+            conv = false;
+            break;
+          }
         }
-      }
-    if (conv || cycle + 1 == pc.max_cycles) break;
+      done[g] = conv || cycle + 1 == pc.max_cycles;
+      all = all && done[g];
+    }
+    if (all) break;
     // restart: V[:, :kk] = V S[:, :kk], V[:, kk:kk+p] = next Lanczos block
     for (int g = 0; g < ngrp; ++g) {
+      if (done[g]) continue;
       const long long j0 = grp[g].j0;
       const int n = grp[g].n;
       cudaStream_t gs = grp[g].st;
