@@ -13,19 +13,21 @@ import numpy as np
 from . import decomp, fem, geneo, krylov
 
 
-def setup(p, precond="geneo", weight="none", eig_method="auto", A=None, b=None):
+def setup(p, precond="geneo", weight="none", eig_method="auto", A=None, b=None,
+          coarse="direct", coarse_tol=1e-2):
     t0 = time.perf_counter()
     if A is None:
         A, b = fem.assemble_system(p)
     t1 = time.perf_counter()
     subs = decomp.partition(p)
     info = None
-    if precond == "geneo":
-        Z, info = geneo.coarse_space(p, subs, A, eig_method)
-        M = krylov.TwoLevelAS(A, subs, Z, weight)
-    elif precond == "zem":
-        Z, info = geneo.zem_space(p, subs, A)
-        M = krylov.TwoLevelAS(A, subs, Z, weight)
+    if precond in ("geneo", "zem"):
+        if precond == "geneo":
+            Z, info = geneo.coarse_space(p, subs, A, eig_method)
+        else:
+            Z, info = geneo.zem_space(p, subs, A)
+        M = krylov.TwoLevelAS(A, subs, Z, weight, coarse=coarse, coarse_tol=coarse_tol,
+                              block_sizes=[d["m"] for d in info])
     elif precond == "as":
         M = krylov.OneLevelAS(A, subs, weight)
     elif precond == "none":
@@ -38,11 +40,14 @@ def setup(p, precond="geneo", weight="none", eig_method="auto", A=None, b=None):
 
 
 def solve(p, precond="geneo", tol=1e-8, maxit=2000, flexible=None,
-          weight="none", eig_method="auto"):
-    """Returns dict(u, iterations, rel_res, true_rel_res, kappa, n_coarse, ...)."""
-    st = setup(p, precond, weight, eig_method)
+          weight="none", eig_method="auto", coarse="direct", coarse_tol=1e-2):
+    """Returns dict(u, iterations, rel_res, true_rel_res, kappa, n_coarse, ...).
+
+    coarse="cg" solves the coarse problem by block-Jacobi PCG to coarse_tol
+    (an inexact coarse solve: flexible CG outside, Sec. 3.3.3)."""
+    st = setup(p, precond, weight, eig_method, coarse=coarse, coarse_tol=coarse_tol)
     if flexible is None:
-        flexible = weight != "none"
+        flexible = weight != "none" or coarse != "direct"
     t0 = time.perf_counter()
     u, it = krylov.pcg(st["A"], st["b"], st["M"], tol=tol, maxit=maxit,
                        flexible=flexible)
