@@ -1257,8 +1257,8 @@ int geneo_estimate_workspace_bytes(const geneo_mesh *mesh, int unknowns_per_node
 
 // ---- autotuning of the Schwarz local-solve launch ---------------------------
 // The launch shape of the local solves (CTAs per subdomain, tile rows per
-// cluster barrier, tiles staged in shared memory or read from global memory)
-// is chosen by timing the candidates on the factors just built; the choice is
+// step, tiles staged in shared memory or read from global memory) is chosen
+// by timing the candidates on the factors just built; the choice is
 // cached for the process, keyed by precision, subdomain count, largest padded
 // subdomain, largest band width and SM count, so a repeated set-up of the same
 // shape does not tune again.  GENEO_SCHWARZ_CLUSTER, GENEO_SCHWARZ_ROWS
@@ -1311,14 +1311,18 @@ static int tune_schwarz(geneo_ctx *c, const SetupPlan &P, cudaStream_t s) {
       return GENEO_OK;
     }
   }
+  // Unpinned, the tuner skips the shapes that never won on the measured
+  // workloads: four rows per step, and the global-memory form of a shape whose
+  // staged form fits in shared memory.
   std::vector<TuneChoice> cand;
   for (int C : {1, 2, 4, 8}) {
     if (fc >= 0 ? C != fc : (C > 1 && P.nsub * C > pc.sms)) continue;   // one wave of clusters
     for (int R : {0, 1, 2, 4}) {
-      if (fr >= 0 ? R != fr : (R == 4 && pc.prec != GENEO_MIXED_FP32)) continue;
+      if (fr >= 0 ? R != fr : R == 4) continue;
+      const bool fits = staged_fits(pc, C, R);
       for (int St : {0, 1}) {
-        if (fs >= 0 && St != fs) continue;
-        if (St && !staged_fits(pc, C, R)) continue;
+        if (fs >= 0 ? St != fs : (St == 0 && fits)) continue;
+        if (St && !fits) continue;
         cand.push_back({C, R, St});
       }
     }
