@@ -168,3 +168,60 @@ def assemble_stiffness(p):
                       shape=(n, n)).tocsr()
     A.sum_duplicates()
     return A
+
+
+def face_shape(xi, eta):
+    """The eight serendipity functions of a face (the element's z = +1 face
+    restricted to it), in the order corners (as the element's 4 top corners)
+    then mid-edges along x (eta = -1, +1) and along y (xi = -1, +1)."""
+    s = np.array([(-1, -1), (1, -1), (-1, 1), (1, 1)], dtype=np.float64)
+    N = np.empty(8)
+    for a, (s1, s2) in enumerate(s):
+        N[a] = (1 + s1 * xi) * (1 + s2 * eta) * (s1 * xi + s2 * eta - 1) / 4.0
+    N[4] = (1 - xi ** 2) * (1 - eta) / 2.0
+    N[5] = (1 - xi ** 2) * (1 + eta) / 2.0
+    N[6] = (1 - xi) * (1 - eta ** 2) / 2.0
+    N[7] = (1 + xi) * (1 - eta ** 2) / 2.0
+    return N
+
+
+# element-local nodes of the z = +1 face in face_shape's order
+TOP_FACE = [4, 5, 6, 7, 10, 11, 14, 15]
+
+
+def top_pressure_load(p):
+    """Consistent nodal load of traction (0, 0, -q) on z = z_max: int_face N_a t dA
+    with the 8-node face functions, 3 x 3 Gauss points (corners get -1/12 and
+    mid-edges 1/3 of the face's force)."""
+    nx, ny, nz = p["nx"], p["ny"], p["nz"]
+    ids, nn = node_map(nx, ny, nz)
+    x, y = np.asarray(p["x"], dtype=np.float64), np.asarray(p["y"], dtype=np.float64)
+    q = p["top_pressure"]
+    pts, wts = GAUSS3
+    fN = np.zeros(8)
+    for j, eta in enumerate(pts):
+        for i, xi in enumerate(pts):
+            fN += wts[i] * wts[j] * face_shape(xi, eta) / 4.0     # int over the unit face
+    b = np.zeros(3 * nn)
+    for ey in range(ny):
+        for ex in range(nx):
+            area = (x[ex + 1] - x[ex]) * (y[ey + 1] - y[ey])
+            nodes = element_nodes(ids, ex, ey, nz - 1)[TOP_FACE]
+            np.add.at(b, 3 * nodes + 2, -q * area * fN)
+    return b
+
+
+def clamp_dofs(p):
+    """Dofs of the nodes on x = 0 (the cantilever's clamp)."""
+    nodes = np.flatnonzero(node_coordinates(p)[:, 0] == np.asarray(p["x"])[0])
+    return (3 * nodes[:, None] + np.arange(3)).reshape(-1)
+
+
+def assemble_system(p):
+    """Clamped at x = 0, loaded on the top face: (A, b) with the Dirichlet rows
+    eliminated symmetrically as for the trilinear element."""
+    from .fem import apply_dirichlet
+    A = assemble_stiffness(p)
+    b = top_pressure_load(p)
+    D = clamp_dofs(p)
+    return apply_dirichlet(A, b, D, np.zeros(len(D)))

@@ -156,3 +156,40 @@ def test_quadratic_element_beats_trilinear_on_a_coarse_cantilever():
     ref = ser(beam(32, 2, 4))
     coarse = beam(8, 1, 1)
     assert abs(ser(coarse) - ref) < 0.5 * abs(q1(coarse) - ref)
+
+
+def test_face_functions_are_the_element_functions_on_the_face():
+    rng = np.random.default_rng(4)
+    others = [a for a in range(20) if a not in sd.TOP_FACE]
+    for _ in range(10):
+        xi, eta = rng.uniform(-1, 1, 2)
+        N = sd.shape(xi, eta, 1.0)
+        assert np.allclose(N[sd.TOP_FACE], sd.face_shape(xi, eta), atol=1e-14)
+        assert np.abs(N[others]).max() <= 1e-14
+
+
+def test_top_load_total_and_pattern():
+    p = make_block(3, 2, 2, [0.0, 90.0], partition=(1, 1, 1, 1))
+    b = sd.top_pressure_load(p)
+    Lx, Ly = p["x"][-1] - p["x"][0], p["y"][-1] - p["y"][0]
+    assert abs(b.sum() + p["top_pressure"] * Lx * Ly) <= 1e-12 * Lx * Ly
+    assert np.all(b[0::3] == 0.0) and np.all(b[1::3] == 0.0)
+    xyz = sd.node_coordinates(p)
+    top = np.abs(xyz[:, 2] - xyz[:, 2].max()) < 1e-12
+    assert np.all(b[2::3][~top] == 0.0)
+    # a corner of the top face lies in one element and takes -1/12 of its face's downward
+    # force -q * hx * hy: +q * hx * hy / 12
+    hx, hy = p["x"][1] - p["x"][0], p["y"][1] - p["y"][0]
+    corner = np.flatnonzero(top & (xyz[:, 0] == p["x"][0]) & (xyz[:, 1] == p["y"][0]))[0]
+    assert abs(b[3 * corner + 2] - p["top_pressure"] * hx * hy / 12.0) <= 1e-15
+
+
+def test_clamped_system_is_spd_and_solves():
+    p = make_block(3, 2, 2, [0.0, 90.0], partition=(1, 1, 1, 1))
+    A, b = sd.assemble_system(p)
+    Ad = A.toarray()
+    assert np.allclose(Ad, Ad.T, atol=1e-12 * abs(Ad).max())
+    np.linalg.cholesky(Ad)
+    u = np.linalg.solve(Ad, b)
+    D = sd.clamp_dofs(p)
+    assert np.all(u[D] == 0.0) and u[2::3].min() < 0.0       # clamped, and the block bends down
