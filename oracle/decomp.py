@@ -62,6 +62,18 @@ def ncomp(p):
     return 1 if p.get("kind") == "darcy" else 3
 
 
+def serendipity(p):
+    return p.get("element") == "serendipity"
+
+
+def nnodes(p):
+    """Mesh nodes: the trilinear grid, or the 20-node serendipity mesh."""
+    if serendipity(p):
+        from . import serendipity as sd
+        return sd.nnodes(p)
+    return (p["nx"] + 1) * (p["ny"] + 1) * (p["nz"] + 1)
+
+
 def dofs_of(nodes, nc=3):
     return (nc * nodes[:, None] + np.arange(nc)[None, :]).reshape(-1)
 
@@ -80,10 +92,19 @@ def partition(p):
                              for d, (a, b) in enumerate(owned))
                 elo = [e[0] for e in ebox]
                 ehi = [e[1] for e in ebox]
-                neu = _box_nodes(p, elo, ehi)
-                ilo = [elo[d] + (1 if elo[d] > 0 else 0) for d in range(3)]
-                ihi = [ehi[d] - (1 if ehi[d] < n[d] else 0) for d in range(3)]
-                intn = _box_nodes(p, ilo, ihi)
+                if serendipity(p):
+                    # nodes in doubled-grid coordinates: V_{h,0} keeps the edge
+                    # midpoints of the first layer, drops those on the boundary
+                    from . import serendipity as sd
+                    neu = sd.box_nodes(p, [2 * e for e in elo], [2 * e for e in ehi])
+                    dlo = [2 * elo[d] + (1 if elo[d] > 0 else 0) for d in range(3)]
+                    dhi = [2 * ehi[d] - (1 if ehi[d] < n[d] else 0) for d in range(3)]
+                    intn = sd.box_nodes(p, dlo, dhi)
+                else:
+                    neu = _box_nodes(p, elo, ehi)
+                    ilo = [elo[d] + (1 if elo[d] > 0 else 0) for d in range(3)]
+                    ihi = [ehi[d] - (1 if ehi[d] < n[d] else 0) for d in range(3)]
+                    intn = _box_nodes(p, ilo, ihi)
                 s = Subdomain(index=len(subs), owned=owned, ebox=ebox,
                               elems=_box_elems(p, elo, ehi),
                               neu_nodes=neu, int_nodes=intn)
@@ -97,7 +118,7 @@ def partition(p):
 
 def _pou(p, subs):
     """Standard PoU (Sec. 3.3.1): 1/multiplicity on V_{h,0}(Omega_j) dofs."""
-    ndof = ncomp(p) * (p["nx"] + 1) * (p["ny"] + 1) * (p["nz"] + 1)
+    ndof = ncomp(p) * nnodes(p)
     mult = np.zeros(ndof)
     for s in subs:
         mult[s.int_dofs] += 1.0
@@ -123,7 +144,7 @@ def _overlap(p, subs):
 
 def pou_sum(p, subs):
     """sum_j R_j^T X_j R_j 1 (Def. Partition of Unity, applied to v = 1)."""
-    ndof = ncomp(p) * (p["nx"] + 1) * (p["ny"] + 1) * (p["nz"] + 1)
+    ndof = ncomp(p) * nnodes(p)
     v = np.zeros(ndof)
     for s in subs:
         v[s.neu_dofs] += s.X

@@ -203,6 +203,9 @@ def assemble_system(p):
     if p.get("kind") == "darcy":
         from . import darcy
         return darcy.assemble_system(p)
+    if p.get("element") == "serendipity":
+        from . import serendipity
+        return serendipity.assemble_system(p)
     A = assemble_stiffness(p)
     b = top_pressure_load(p)
     return apply_dirichlet(A, b, p["dirichlet_dofs"], p["dirichlet_values"])

@@ -38,8 +38,7 @@ INF_MU_RTOL = 1e-12    # mu below this times 1/|sigma| means lambda = infinity
 
 
 def local_node_map(p, nodes):
-    nn = (p["nx"] + 1) * (p["ny"] + 1) * (p["nz"] + 1)
-    m = -np.ones(nn, np.int64)
+    m = -np.ones(decomp.nnodes(p), np.int64)
     m[nodes] = np.arange(nodes.size)
     return m
 
@@ -55,6 +54,9 @@ def local_matrices(p, s):
     if nc == 1:
         from . import darcy
         assemble = darcy.assemble_matrix
+    elif decomp.serendipity(p):
+        from . import serendipity
+        assemble = serendipity.assemble_stiffness_on
     else:
         assemble = fem.assemble_stiffness
     A = assemble(p, s.elems, nm, nloc)
@@ -62,7 +64,7 @@ def local_matrices(p, s):
         Ao = assemble(p, s.ovl_elems, nm, nloc)
     else:
         Ao = sp.csr_matrix((nc * nloc, nc * nloc))
-    dmask = np.zeros(nc * ((p["nx"] + 1) * (p["ny"] + 1) * (p["nz"] + 1)), bool)
+    dmask = np.zeros(nc * decomp.nnodes(p), bool)
     dmask[np.asarray(p["dirichlet_dofs"], np.int64)] = True
     ld = np.nonzero(dmask[s.neu_dofs])[0]
     zeros = np.zeros(ld.size)
@@ -186,11 +188,15 @@ def rigid_body_modes(p, nodes):
     Columns: translations along x, y, z; rotations about the x, y and z axes
     through the centre of the nodes' bounding box (u = omega x (X - c)).
     """
-    nnx, nny = p["nx"] + 1, p["ny"] + 1
-    i = nodes % nnx
-    j = (nodes // nnx) % nny
-    k = nodes // (nnx * nny)
-    X = np.stack([np.asarray(p["x"])[i], np.asarray(p["y"])[j], np.asarray(p["z"])[k]], axis=1)
+    if decomp.serendipity(p):
+        from . import serendipity
+        X = serendipity.node_coordinates(p)[nodes]
+    else:
+        nnx, nny = p["nx"] + 1, p["ny"] + 1
+        i = nodes % nnx
+        j = (nodes // nnx) % nny
+        k = nodes // (nnx * nny)
+        X = np.stack([np.asarray(p["x"])[i], np.asarray(p["y"])[j], np.asarray(p["z"])[k]], axis=1)
     c = 0.5 * (X.min(axis=0) + X.max(axis=0))
     d = X - c
     n = nodes.size

@@ -145,29 +145,9 @@ def node_coordinates(p):
 def assemble_stiffness(p):
     """Unconstrained global stiffness (CSR, 3 nnodes square) of problem p's block
     meshed with serendipity elements and its per-element materials."""
-    nx, ny, nz = p["nx"], p["ny"], p["nz"]
-    ids, nn = node_map(nx, ny, nz)
-    Cv = element_voigt_all(p)
-    x, y, z = (np.asarray(p[k], dtype=np.float64) for k in ("x", "y", "z"))
-    rows, cols, vals = [], [], []
-    cache = {}
-    for e in range(nx * ny * nz):
-        ex, ey, ez = e % nx, (e // nx) % ny, e // (nx * ny)
-        h = (x[ex + 1] - x[ex], y[ey + 1] - y[ey], z[ez + 1] - z[ez])
-        key = (Cv[e].tobytes(), h)
-        Ke = cache.get(key)
-        if Ke is None:
-            Ke = element_stiffness(Cv[e], *h)
-            cache[key] = Ke
-        dofs = (3 * element_nodes(ids, ex, ey, ez)[:, None] + np.arange(3)).reshape(-1)
-        rows.append(np.repeat(dofs, 60))
-        cols.append(np.tile(dofs, 60))
-        vals.append(Ke.reshape(-1))
-    n = 3 * nn
-    A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
-                      shape=(n, n)).tocsr()
-    A.sum_duplicates()
-    return A
+    nn = nnodes(p)
+    return assemble_stiffness_on(p, np.arange(p["nx"] * p["ny"] * p["nz"]),
+                                 np.arange(nn), nn)
 
 
 def face_shape(xi, eta):
@@ -218,10 +198,69 @@ def clamp_dofs(p):
 
 
 def assemble_system(p):
-    """Clamped at x = 0, loaded on the top face: (A, b) with the Dirichlet rows
-    eliminated symmetrically as for the trilinear element."""
+    """Loaded on the top face, with the Dirichlet rows eliminated symmetrically as
+    for the trilinear element: p's serendipity-numbered Dirichlet dofs when p is
+    a serendipity problem, else the clamp at x = 0."""
     from .fem import apply_dirichlet
     A = assemble_stiffness(p)
     b = top_pressure_load(p)
-    D = clamp_dofs(p)
-    return apply_dirichlet(A, b, D, np.zeros(len(D)))
+    if p.get("element") == "serendipity":
+        D = np.asarray(p["dirichlet_dofs"], np.int64)
+        g = np.asarray(p["dirichlet_values"], np.float64)
+    else:
+        D = clamp_dofs(p)
+        g = np.zeros(len(D))
+    return apply_dirichlet(A, b, D, g)
+
+
+def nnodes(p):
+    return node_map(p["nx"], p["ny"], p["nz"])[1]
+
+
+def box_nodes(p, dlo, dhi):
+    """Sorted ids of the nodes whose doubled-grid coordinates lie in [dlo, dhi]."""
+    ids, _ = node_map(p["nx"], p["ny"], p["nz"])
+    sub = ids[dlo[0]:dhi[0] + 1, dlo[1]:dhi[1] + 1, dlo[2]:dhi[2] + 1]
+    return np.sort(sub[sub >= 0].reshape(-1))
+
+
+def assemble_stiffness_on(p, elems, node_map_local, n_local_nodes):
+    """sum_e K_e over `elems` on a local node set (global node -> local id)."""
+    nx, ny, nz = p["nx"], p["ny"], p["nz"]
+    ids, _ = node_map(nx, ny, nz)
+    Cv = element_voigt_all(p)
+    x, y, z = (np.asarray(p[k], dtype=np.float64) for k in ("x", "y", "z"))
+    rows, cols, vals = [], [], []
+    cache = {}
+    for e in np.asarray(elems):
+        ex, ey, ez = e % nx, (e // nx) % ny, e // (nx * ny)
+        h = (x[ex + 1] - x[ex], y[ey + 1] - y[ey], z[ez + 1] - z[ez])
+        key = (Cv[e].tobytes(), h)
+        Ke = cache.get(key)
+        if Ke is None:
+            Ke = element_stiffness(Cv[e], *h)
+            cache[key] = Ke
+        loc = node_map_local[element_nodes(ids, ex, ey, ez)]
+        dofs = (3 * loc[:, None] + np.arange(3)).reshape(-1)
+        rows.append(np.repeat(dofs, 60))
+        cols.append(np.tile(dofs, 60))
+        vals.append(Ke.reshape(-1))
+    n = 3 * n_local_nodes
+    if not rows:
+        return sp.csr_matrix((n, n))
+    A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(n, n)).tocsr()
+    A.sum_duplicates()
+    return A
+
+
+def problem(p):
+    """A copy of the block problem p meshed with serendipity elements: the same
+    geometry, materials, partition and load, with the clamp on x = 0 numbered on
+    the serendipity mesh."""
+    q = dict(p)
+    q["element"] = "serendipity"
+    D = clamp_dofs(q)
+    q["dirichlet_dofs"] = D.astype(np.int32)
+    q["dirichlet_values"] = np.zeros(len(D))
+    return q
