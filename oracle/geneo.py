@@ -12,8 +12,12 @@ The eigenpairs come from the shift-and-invert transformation with a small
 negative shift sigma (Sec. 3.3.2): with S = A - sigma B (SPD for sigma < 0),
     B p = mu S p,  lambda = sigma + 1 / mu,
 so the smallest lambda are the largest mu.  Small problems use a dense
-symmetric-definite solver on (B, S); large ones use ARPACK's shift-invert
-mode on (A, B, sigma), the method the paper uses.
+symmetric-definite solver on (B, S); large ones use ARPACK (the paper's
+eigensolver) on the same pencil, with S as the inner-product matrix and a
+sparse LU of S for its inverse.  B is only semi-definite, so handing it to
+ARPACK as the inner-product matrix (its shift-invert mode on (A, B, sigma))
+would make the returned vectors orthogonal only modulo ker B: with clustered
+eigenvalues two of them can coincide on the support of X_j.
 
 Coarse basis (Sec. 3.3.2): Phi_{i(j,k)} = R_j^T X_j p_k^j; coarse matrix
 (Sec. 3.3.3) A_H = Phi^T A Phi with the fully assembled global A.
@@ -94,10 +98,20 @@ def eigenpairs(A, B, nev, sigma, method="auto"):
         lam = np.full(mu.shape, np.inf)
         lam[finite] = sigma + 1.0 / mu[finite]
     elif method == "arpack":
-        lam, V = spla.eigsh(A.tocsc(), k=nev, M=B.tocsc(), sigma=sigma,
-                            which="LM", tol=1e-12, maxiter=20000)
-        order = np.argsort(lam)
-        lam, V = lam[order], V[:, order]
+        # the same shift-invert pencil as the dense branch, B v = mu S v with
+        # S = A - sigma B SPD as the inner-product matrix (B is only
+        # semi-definite, so it cannot serve as one: vectors would be
+        # orthogonal only modulo ker B)
+        S = (A - sigma * B).tocsc()
+        lu = spla.splu(S)
+        Sinv = spla.LinearOperator(S.shape, matvec=lu.solve, dtype=np.float64)
+        mu, V = spla.eigsh(B.tocsc(), k=nev, M=S, Minv=Sinv, which="LA",
+                           tol=1e-12, maxiter=20000)
+        order = np.argsort(mu)[::-1]
+        mu, V = mu[order], V[:, order]
+        finite = mu > INF_MU_RTOL / abs(sigma)
+        lam = np.full(mu.shape, np.inf)
+        lam[finite] = sigma + 1.0 / mu[finite]
     else:
         raise ValueError(method)
     V = V / np.linalg.norm(V, axis=0, keepdims=True)

@@ -69,3 +69,31 @@ def test_table1_zem_dimension(n):
     assert Z.shape[1] == GOLD["table1_zem_dim"][str(n)]
     touching = sum(1 for s in subs if s.ebox[0][0] == 0)
     assert [d["m"] for d in info].count(0) == touching
+
+
+def test_clustered_spectrum_sparse_eigensolver():
+    # Threshold rule with the cap of 20 on the 2x2 plate: a subdomain larger than
+    # the dense limit, whose wanted GenEO eigenvalues crowd towards the bottom of
+    # the overlap-localised modes.  The sparse branch must give the dense branch's
+    # eigenvalues and S-orthogonal vectors (S = A - sigma B), so that the coarse
+    # columns X_j p_k stay independent and A_H is SPD.
+    import scipy.linalg as sla
+    import scipy.sparse as sp
+    p = _plate((2, 2, 1, 1))
+    p["modes"] = dict(fixed_modes=0, threshold=0.0, max_modes=20, shift=-0.01)
+    subs = decomp.partition(p)
+    s = subs[0]
+    A, Ao = geneo.local_matrices(p, s)
+    assert A.shape[0] > geneo.DENSE_LIMIT
+    Xd = sp.diags(s.X)
+    B = (Xd @ Ao @ Xd).tocsr()
+    sig = p["modes"]["shift"]
+    la, Pa = geneo.eigenpairs(A, B, 21, sig, "arpack")
+    ld, _ = geneo.eigenpairs(A, B, 21, sig, "dense")
+    assert np.allclose(la, ld, rtol=1e-9, atol=1e-12)
+    G = Pa.T @ ((A - sig * B) @ Pa)
+    assert np.abs(G - np.diag(np.diag(G))).max() <= 1e-9 * np.abs(np.diag(G)).max()
+    Ag, _ = fem.assemble_system(p)
+    Z, info = geneo.coarse_space(p, subs, Ag)
+    assert all(d["m"] == 20 for d in info)
+    sla.cho_factor((Z.T @ (Ag @ Z)).toarray(), lower=True)
