@@ -333,8 +333,17 @@ class GeneoSolver:
     def unknowns_per_node(p):
         return 1 if p.get("kind") == "darcy" else 3
 
+    @staticmethod
+    def check_element(p):
+        """The library meshes every problem with trilinear 8-node hexahedra; a
+        problem that asks for another element is refused, not re-meshed."""
+        el = p.get("element", "trilinear")
+        if el != "trilinear":
+            raise ValueError(f"element {el!r}: the library assembles trilinear hexahedra only")
+
     def assemble(self, p):
         """Assemble the elasticity system, or the Darcy one for p["kind"] == "darcy"."""
+        self.check_element(p)
         keep = []
         mesh = self.mesh_of(p, keep)
         self._bind(0, geneo_assemble_workspace_bytes(mesh))

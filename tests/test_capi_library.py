@@ -60,3 +60,15 @@ def test_workspace_size_query_is_host_only(lib):
     n = pkg.geneo_assemble_workspace_bytes(m)
     # BSR values alone take 27 * 729 * 9 doubles
     assert n > 27 * 729 * 9 * 8
+
+
+def test_binding_refuses_other_elements():
+    # the library meshes with trilinear hexahedra only: a 20-node problem (which
+    # the oracle can build) is refused before anything reaches the GPU
+    import paper_1901_05188_gb300 as pkg
+    from workloads.laminate import make_block
+    p = make_block(2, 2, 2, [0.0, 90.0], partition=(1, 1, 1, 1))
+    pkg.GeneoSolver.check_element(p)
+    q = dict(p, element="serendipity")
+    with pytest.raises(ValueError, match="trilinear"):
+        pkg.GeneoSolver.check_element(q)
