@@ -111,9 +111,64 @@ def partition(p):
                 s.neu_dofs = dofs_of(neu, ncomp(p))
                 s.int_dofs = dofs_of(intn, ncomp(p))
                 subs.append(s)
-    _pou(p, subs)
+    if p.get("pou", "standard") == "sarkis":
+        _pou_sarkis(p, subs)
+    else:
+        _pou(p, subs)
     _overlap(p, subs)
     return subs
+
+
+def node_layers(p):
+    """(nnodes, 3) node positions in element layers along each axis: the grid
+    index of a trilinear node, half the doubled-grid index of a serendipity
+    node (edge midpoints sit half a layer in)."""
+    if serendipity(p):
+        from . import serendipity as sd
+        ids, nn = sd.node_map(p["nx"], p["ny"], p["nz"])
+        out = np.empty((nn, 3))
+        I, J, K = np.nonzero(ids >= 0)
+        out[ids[I, J, K]] = 0.5 * np.stack([I, J, K], axis=1)
+        return out
+    nnx, nny = p["nx"] + 1, p["ny"] + 1
+    m = np.arange(nnodes(p))
+    return np.stack([m % nnx, (m // nnx) % nny, m // (nnx * nny)], axis=1).astype(np.float64)
+
+
+def _pou_sarkis(p, subs):
+    """Sarkis's PoU (Sec. 3.2 and Sec. 3.3.1 offer it beside the standard one):
+    X_j(n) = d_j(n) / sum_k d_k(n), d_j the distance from node n to the
+    artificial boundary of Omega_j (the part of its boundary inside the
+    domain), counted in element layers, so that the weight ramps linearly
+    across the overlap on any element grading.  For a box and a point inside
+    it the distance to a face is the distance to the face's plane, so d_j is
+    the least over the artificial faces.  Zero on the artificial boundary and
+    on global Dirichlet dofs; with one layer of overlap it equals the standard
+    PoU."""
+    n = (p["nx"], p["ny"], p["nz"])
+    pos = node_layers(p)
+    nc = ncomp(p)
+    dist = []
+    for s in subs:
+        c = pos[s.neu_nodes]
+        d = np.full(s.neu_nodes.size, np.inf)
+        for a in range(3):
+            lo, hi = s.ebox[a]
+            if lo > 0:
+                d = np.minimum(d, c[:, a] - lo)
+            if hi < n[a]:
+                d = np.minimum(d, hi - c[:, a])
+        d[~np.isfinite(d)] = 1.0               # no artificial face: the whole domain
+        dist.append(d)
+    total = np.zeros(nnodes(p))
+    for s, d in zip(subs, dist):
+        total[s.neu_nodes] += d
+    dir_mask = np.zeros(nc * nnodes(p), bool)
+    dir_mask[np.asarray(p["dirichlet_dofs"], np.int64)] = True
+    for s, d in zip(subs, dist):
+        X = np.repeat(d / total[s.neu_nodes], nc)
+        X[dir_mask[s.neu_dofs]] = 0.0
+        s.X = X
 
 
 def _pou(p, subs):
