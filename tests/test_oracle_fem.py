@@ -141,3 +141,35 @@ def test_top_pressure_total_load_and_symmetry():
     assert np.allclose(bz, bz[:, ::-1, :])
     # only top-face nodes are loaded
     assert np.all(bz[:-1] == 0)
+
+
+def _fibre_strain(Cv, d):
+    """Normal strain along unit d under the uniaxial stress d (x) d."""
+    sig = np.array([d[0] ** 2, d[1] ** 2, d[2] ** 2, d[1] * d[2], d[0] * d[2], d[0] * d[1]])
+    e = np.linalg.solve(Cv, sig)                     # engineering shear strains
+    return (d[0] ** 2 * e[0] + d[1] ** 2 * e[1] + d[2] ** 2 * e[2]
+            + d[1] * d[2] * e[3] + d[0] * d[2] * e[4] + d[0] * d[1] * e[5])
+
+
+def test_element_material_follows_the_fibre():
+    # Every ply element of a wrinkled block is stiff (E1) along its fibre
+    # (cos t cos f, sin t cos f, -sin f) for its own ply angle t and wrinkle
+    # angle f: the element stiffness takes the angles with their signs.
+    p = workloads.config("small", wrinkle=(8.0, 3.0))
+    Cv = fem.element_voigt_all(p)
+    E1 = p["materials"][0][0]
+    ply = np.flatnonzero(p["elem_mat"] == 0)
+    assert np.abs(p["elem_phi"][ply]).max() > 0.05 and np.ptp(p["elem_theta"][ply]) > 0.5
+    for e in ply[:: max(1, ply.size // 40)]:
+        t, f = p["elem_theta"][e], p["elem_phi"][e]
+        d = np.array([np.cos(t) * np.cos(f), np.sin(t) * np.cos(f), -np.sin(f)])
+        assert _fibre_strain(Cv[e], d) == pytest.approx(1.0 / E1, rel=1e-10)
+    # and the element stiffness matrices are built from those same C_e
+    x, y, z = p["x"], p["y"], p["z"]
+    nx, ny = p["nx"], p["ny"]
+    Ku, inv, elems = fem.element_stiffness_all(p)
+    for e in ply[:: max(1, ply.size // 10)]:
+        ex, ey, ez = e % nx, (e // nx) % ny, e // (nx * ny)
+        Ke = fem.element_stiffness(Cv[e], x[ex + 1] - x[ex], y[ey + 1] - y[ey], z[ez + 1] - z[ez])
+        got = Ku[inv[np.flatnonzero(elems == e)[0]]]
+        assert np.abs(got - Ke).max() <= 1e-12 * np.abs(Ke).max()

@@ -87,6 +87,33 @@ def test_select_modes_rules():
     assert geneo.select_modes(lam, 0, 0.3, 1) == 0      # cut inside the zero pair
     assert geneo.select_modes(lam, 2, 0.0, 20) == 2
     assert geneo.select_modes(lam, 0, 10.0, 20) == 7
+    # neighbours 1e-3 apart (relative) are distinct eigenvalues, not a cluster
+    near = np.array([0.1, 0.2, 0.3, 0.3003, 0.9])
+    assert geneo.select_modes(near, 0, 10.0, 3) == 3
+    assert geneo.select_modes(near, 3, 0.0, 20) == 3
+
+
+def test_cap_inside_a_degenerate_pair_drops_it():
+    # The middle subdomain of a 3 x 3 in-plane split of a square isotropic block
+    # is symmetric under quarter turns about z, so past its six rigid modes
+    # GenEO eigenvalues come in equal pairs; a cap or a fixed count that would
+    # split a pair keeps neither of the two (the kept span must be unique).
+    import scipy.sparse as sp
+    from workloads.laminate import RESIN, make_block
+    p = make_block(6, 6, 2, [0.0], partition=(3, 3, 1, 1), clamp="none")
+    p["materials"] = np.array([RESIN, RESIN], dtype=np.float64)
+    p["x"], p["y"], p["z"] = np.linspace(0, 6, 7), np.linspace(0, 6, 7), np.linspace(0, 2, 3)
+    subs = decomp.partition(p)
+    mid = subs[4]
+    A, Ao = geneo.local_matrices(p, mid)
+    Xd = sp.diags(mid.X)
+    lam, _ = geneo.eigenpairs(A, (Xd @ Ao @ Xd).tocsr(), 12, -0.01, "dense")
+    assert abs(lam[8] - lam[9]) <= 1e-10 * lam[9] and lam[9] < lam[10] * (1 - 1e-3)
+    Ag = fem.assemble_stiffness(p)
+    for rule, want in (((0, 1e9, 9), 8), ((0, 1e9, 10), 10), ((9, 0.0, 20), 8)):
+        p["modes"] = dict(fixed_modes=rule[0], threshold=rule[1], max_modes=rule[2], shift=-0.01)
+        _, info = geneo.coarse_space(p, subs, Ag, "dense")
+        assert info[4]["m"] == want, (rule, info[4]["m"])
 
 
 def test_threshold_closed_form():

@@ -97,6 +97,26 @@ def test_pou_weighted_schwarz_with_flexible_cg_converges():
     assert np.linalg.norm(r["u"] - u) <= 1e-6 * np.linalg.norm(u)
 
 
+def test_pou_weighted_one_level_is_the_plain_one_over_multiplicity():
+    # With the standard PoU every subdomain holding a free dof in its interior
+    # weighs it by 1/multiplicity, so sum_j R_j^T X_j A_j^-1 R_j r is the plain
+    # one-level sum divided by the multiplicity, dof by dof.
+    p = workloads.config("small")
+    A, _ = fem.assemble_system(p)
+    subs = decomp.partition(p)
+    mult = np.zeros(A.shape[0])
+    for s in subs:
+        mult[s.int_dofs] += 1.0
+    free = np.ones(A.shape[0], bool)
+    free[p["dirichlet_dofs"]] = False
+    assert mult[free].max() >= 4
+    r = np.random.default_rng(5).normal(size=A.shape[0])
+    plain = krylov.OneLevelAS(A, subs, "none")(r)
+    weighted = krylov.OneLevelAS(A, subs, "pou")(r)
+    assert np.abs(weighted[free] * mult[free] - plain[free]).max() <= 1e-12 * np.abs(plain).max()
+    assert np.all(weighted[~free] == 0.0)
+
+
 def test_geneo_condition_insensitive_to_contrast():
     # Sec. 3.2 bound: kappa stays bounded as the layer stiffness contrast grows.
     md = dict(fixed_modes=0, threshold=0.0, max_modes=20, shift=-0.01)

@@ -31,6 +31,31 @@ def test_uniaxial_stress_engineering_constants():
         assert np.allclose(np.delete(eps, k), 0, atol=1e-20)
 
 
+def test_uniaxial_stress_general_orthotropic():
+    # Nine distinct constants (E2 != E3, G13 != G12, ...), so that an engineering
+    # constant divided by the wrong modulus cannot hide behind the ply's
+    # transverse isotropy: sigma_kk = 1 gives eps_kk = 1/E_k and, for i != k,
+    # eps_ii = -nu_ki / E_k with nu_ki = nu_ik E_k / E_i for i < k.
+    E1, E2, E3 = 140000.0, 9000.0, 6000.0
+    G12, G13, G23 = 4800.0, 4100.0, 2700.0
+    nu12, nu13, nu23 = 0.31, 0.27, 0.45
+    mat = (E1, E2, E3, G12, G13, G23, nu12, nu13, nu23)
+    C = M.stiffness_voigt(mat)
+    E = (E1, E2, E3)
+    nu = {(0, 1): nu12, (0, 2): nu13, (1, 2): nu23}
+    for k in range(3):
+        sig = np.zeros(6)
+        sig[k] = 1.0
+        eps = np.linalg.solve(C, sig)
+        want = np.zeros(6)
+        want[k] = 1.0 / E[k]
+        for i in range(3):
+            if i != k:
+                nu_ki = nu[(k, i)] if k < i else nu[(i, k)] * E[k] / E[i]
+                want[i] = -nu_ki / E[k]
+        assert np.allclose(eps, want, rtol=1e-12, atol=1e-22), k
+
+
 def test_isotropic_two_routes_agree():
     E, nu = 10000.0, 0.35
     G = E / (2 * (1 + nu))

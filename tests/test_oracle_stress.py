@@ -52,3 +52,22 @@ def test_pure_shear_excites_its_component():
     Gm = workloads.RESIN[3]
     assert np.allclose(sig[:, 4], Gm * a, rtol=1e-12, atol=0)
     assert np.abs(np.delete(sig, 4, axis=1)).max() <= 1e-12 * Gm * a
+
+
+def test_centroid_value_of_a_varying_strain():
+    # u = (a x y, b y z, c z x) lies in the trilinear space, so it is
+    # interpolated exactly; its strain varies linearly across each element and
+    # the recovered stress is C_e times the strain at the element's centre
+    # (eps_xx = a y, eps_yy = b z, eps_zz = c x, gamma_xy = a x,
+    # gamma_yz = b y, gamma_xz = c z there).
+    p = workloads.config("small", wrinkle=(8.0, 3.0))
+    X = _nodes(p)
+    a, b, c = 0.004, -0.003, 0.002
+    u = np.stack([a * X[:, 0] * X[:, 1], b * X[:, 1] * X[:, 2], c * X[:, 2] * X[:, 0]], 1).reshape(-1)
+    ex, ey, ez = fem.element_coords(p)
+    x, y, z = (np.asarray(p[k]) for k in ("x", "y", "z"))
+    xc, yc, zc = 0.5 * (x[ex] + x[ex + 1]), 0.5 * (y[ey] + y[ey + 1]), 0.5 * (z[ez] + z[ez + 1])
+    eps = np.stack([a * yc, b * zc, c * xc, b * yc, c * zc, a * xc], axis=1)
+    ref = np.einsum("eij,ej->ei", fem.element_voigt_all(p), eps)
+    sig = fem.element_stresses(p, u)
+    assert np.abs(sig - ref).max() <= 1e-11 * np.abs(ref).max()
