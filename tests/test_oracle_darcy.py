@@ -93,3 +93,26 @@ def test_iterations_as_greater_than_geneo():
     p = darcy_config("d-small")
     it = {k: solver.solve(p, precond=k, tol=1e-8)["iterations"] for k in ("as", "geneo")}
     assert it["as"] > it["geneo"], it
+
+
+def test_global_energy_of_linear_field_heterogeneous():
+    # On the unconstrained matrix the energy of a linear field g.x is
+    # sum_e V_e sum_d K_{e,d} g_d^2 exactly, for a per-cell K and a graded mesh
+    # with different spacings per axis: it ties every cell to its own K
+    # components and its own edge lengths.
+    p = make_darcy(5, 4, 3, seed=2)
+    p["x"] = np.cumsum(np.r_[0.0, [1.0, 1.5, 0.7, 2.0, 1.1]])
+    p["y"] = np.cumsum(np.r_[0.0, [0.4, 0.9, 0.6, 1.3]])
+    p["z"] = np.cumsum(np.r_[0.0, [0.2, 0.05, 0.3]])
+    Zc, Yc, Xc = np.meshgrid(p["z"], p["y"], p["x"], indexing="ij")
+    g = np.array([0.8, -1.7, 2.3])
+    u = np.stack([Xc.ravel(), Yc.ravel(), Zc.ravel()], 1) @ g
+    nx, ny = p["nx"], p["ny"]
+    e = np.arange(nx * ny * p["nz"])
+    ex, ey, ez = e % nx, (e // nx) % ny, e // (nx * ny)
+    vol = np.diff(p["x"])[ex] * np.diff(p["y"])[ey] * np.diff(p["z"])[ez]
+    K = np.random.default_rng(9).uniform(0.1, 10.0, size=(e.size, 3))   # Kx, Ky, Kz all distinct
+    p["perm"] = K
+    A = darcy.assemble_matrix(p)
+    want = np.sum(vol * (K @ (g * g)))
+    assert abs(u @ (A @ u) - want) <= 1e-12 * want

@@ -7,6 +7,7 @@ ZEM coarse space PCG must need fewer iterations than one-level AS and more
 than GenEO, the ordering of Table 1.
 """
 import numpy as np
+import pytest
 import scipy.linalg as sla
 import scipy.sparse as sp
 
@@ -71,3 +72,32 @@ def test_iterations_as_greater_than_zem_greater_than_geneo():
     p = workloads.config("small")
     it = {k: solver.solve(p, precond=k, tol=1e-8)["iterations"] for k in ("as", "zem", "geneo")}
     assert it["as"] > it["zem"] > it["geneo"], it
+
+
+def test_rotation_columns_are_centred():
+    # rotations are taken about the centre of the node set's bounding box, so
+    # on a box node set they are orthogonal to the three translations
+    p = workloads.config("c1")
+    subs = decomp.partition(p)
+    R = geneo.rigid_body_modes(p, subs[0].neu_nodes)
+    assert np.abs(R[:, :3].T @ R[:, 3:]).max() <= 1e-13
+
+
+@pytest.mark.parametrize("coarse", ["zem", "geneo"])
+def test_global_rigid_modes_lie_in_the_coarse_space(coarse):
+    # Unclamped block: every subdomain floats and keeps its six rigid modes,
+    # weighted by its PoU; summed over the subdomains the PoU rebuilds each
+    # global rigid displacement (sum_j R_j^T X_j R_j = I), so the coarse space
+    # must contain all six.
+    from oracle import fem
+    p = workloads.config("small", clamp="none")
+    p["modes"] = dict(fixed_modes=6, threshold=0.0, max_modes=20, shift=-0.01)
+    subs = decomp.partition(p)
+    A = fem.assemble_stiffness(p)
+    if coarse == "zem":
+        Z, _ = geneo.zem_space(p, subs, A)
+    else:
+        Z, _ = geneo.coarse_space(p, subs, A)
+    allnodes = np.arange(A.shape[0] // 3)
+    Rg = geneo.rigid_body_modes(p, allnodes)
+    assert sla.subspace_angles(Z.toarray(), Rg).max() < 1e-8
