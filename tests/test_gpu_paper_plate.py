@@ -9,7 +9,10 @@ oracle's sparse eigensolver pin covers.  Same tolerances as the other parity
 tests: eigenvalues 1e-7 relative, coarse span angles 1e-5, solution 1e-6
 relative L2 with iterations within +-2 (FP64), and 1e-6 for the mixed
 precision solve at a tolerance of 1e-10; the true residual within twice the
-oracle's, which sits at the FP64 floor of b - A u for this system.
+oracle's, which sits at the FP64 floor of b - A u for this system.  With the
+zero-energy-mode coarse space the GPU reaches Table 1's printed coarse
+dimensions for 4, 8, 16 and 32 subdomains (in-plane grids 2x2, 8x1, 8x2, 8x4),
+and its 32-subdomain ZEM solve matches the oracle's.
 """
 import json
 import os
@@ -33,12 +36,12 @@ def pkg():
     return require_gpu()
 
 
-def plate():
+def plate(grid=(2, 2)):
     m = GOLD["base_mesh"]
     nply = len(GOLD["stacking_deg"])
     nz = m["elements_per_ply"] * nply + m["elements_per_resin"] * GOLD["resin_layers"]
     p = make_block(m["nx"], m["ny"], nz, GOLD["stacking_deg"], resin_between=True,
-                   partition=(2, 2, 1, 1),
+                   partition=(grid[0], grid[1], 1, 1),
                    modes=dict(fixed_modes=0, threshold=0.0, max_modes=20, shift=-0.01))
     lx, ly = GOLD["plate_mm"]
     p["x"] = np.linspace(0.0, lx, m["nx"] + 1)
@@ -82,5 +85,27 @@ def test_plate_solve_matches_oracle(pkg, prec):
     assert st["rel_res_true"] <= max(2 * tol, 2 * ref["true_rel_res"]), \
         (st["rel_res_true"], ref["true_rel_res"])
     if prec == "fp64":
+        assert abs(st["iterations"] - ref["iterations"]) <= 2, (st["iterations"], ref["iterations"])
+    s.close()
+
+
+GRIDS = {4: (2, 2), 8: (8, 1), 16: (8, 2), 32: (8, 4)}
+
+
+@pytest.mark.parametrize("n", sorted(GRIDS))
+def test_plate_table1_zem_dimension(pkg, n):
+    p = plate(GRIDS[n])
+    s = pkg.GeneoSolver()
+    s.assemble(p)
+    s.setup(p, pkg.GENEO_FP64, pkg.GENEO_AS, pkg.GENEO_COARSE_ZEM)
+    modes, _, nh = s.coarse_info()
+    assert len(modes) == n
+    assert nh == GOLD["table1_zem_dim"][str(n)]
+    if n == 32:
+        tol = GOLD["table1_residual_reduction"]
+        u, st = s.solve(tol=tol, max_it=2000)
+        ref = osolver.solve(p, precond="zem", tol=tol)
+        assert st["n_coarse"] == ref["n_coarse"] == nh
+        assert rel(u, ref["u"]) <= 1e-4
         assert abs(st["iterations"] - ref["iterations"]) <= 2, (st["iterations"], ref["iterations"])
     s.close()
