@@ -41,3 +41,32 @@ def test_reference_line_has_the_contract_keys():
 
 def test_reference_arm_is_silent_off_rank_zero():
     assert _run({"RANK": "1", "WORLD_SIZE": "2"}) == []
+
+
+class _Done:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def test_clock_record_median_max_and_reasons(tmp_path):
+    # nvidia-smi's CSV (noheader, nounits) in the order of ClockSampler.FIELDS:
+    # the record keeps the median SM clock under load, the largest maximum, and
+    # every throttle reason seen active in any sample.
+    sys.path.insert(0, ROOT)
+    import bench
+    rows = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 1980, 2070, 1390.5, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 2055, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "garbage line",
+            "0, N/A, 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    path = tmp_path / "clocks.csv"
+    path.write_text("\n".join(rows) + "\n")
+    cs = bench.ClockSampler(0)
+    cs.path, cs.proc = str(path), _Done()
+    rec = cs.stop()
+    assert rec["sm_mhz"] == 2055.0 and rec["sm_max_mhz"] == 2070.0 and rec["samples"] == 3
+    assert rec["reasons"] == ["sw_power_cap"]
+    assert not path.exists()
