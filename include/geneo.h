@@ -161,6 +161,27 @@ int geneo_estimate_workspace_bytes(const geneo_mesh *mesh, int unknowns_per_node
                                    geneo_precision prec, size_t *assemble_bytes,
                                    size_t *setup_bytes);
 
+/* Host-only view of the subdomain plan geneo_setup builds for this mesh and
+ * box partition (Sec. 3.1: parts of each axis with n elements and p parts
+ * own [floor(k n / p), floor((k + 1) n / p)); Omega_j adds `overlap` element
+ * layers per side, clipped to the mesh; V_{h,0}(Omega_j) keeps the nodes of
+ * Omega_j not on its boundary inside the domain).  Subdomain j = kx + px (ky
+ * + py kz) fills GENEO_PLAN_INTS int32 at plan[GENEO_PLAN_INTS * j]: element
+ * box lo (x, y, z) and hi (exclusive), interior node box lo and hi (inclusive),
+ * then the interior unknown count n_j and the half-bandwidth of its band
+ * factor in 32-row tiles, and the same two for the Neumann set (all nodes of
+ * Omega_j).  *n_subdomains = px py pz; with plan NULL only the count is
+ * returned; max_subs below the count is GENEO_ERR_INVALID_ARG.  The
+ * partition is refused (GENEO_ERR_INVALID_ARG) exactly when geneo_setup
+ * would refuse it: parts outside [1, elements] on an axis, an empty interior,
+ * or an overlap so wide that a node lies in the interiors of more than four
+ * parts of one axis (the gather's candidate lists hold four).  Touches no
+ * device state. */
+#define GENEO_PLAN_INTS 16
+int geneo_plan_subdomains(const geneo_mesh *mesh, int unknowns_per_node,
+                          const geneo_partition *part, int max_subs, int32_t *plan,
+                          int *n_subdomains);
+
 /* Bind caller-owned device memory (e.g. allocated by PyTorch) as the
  * workspace of phase 0 (assemble) or phase 1 (setup + solve).  It must stay
  * alive until the context is destroyed or rebound; alignment >= 256 bytes.

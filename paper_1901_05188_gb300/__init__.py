@@ -91,6 +91,8 @@ _SIGS = {
     "geneo_estimate_workspace_bytes": [C.POINTER(geneo_mesh), C.c_int, C.POINTER(geneo_partition),
                                        C.POINTER(geneo_modes), C.c_int, C.POINTER(C.c_size_t),
                                        C.POINTER(C.c_size_t)],
+    "geneo_plan_subdomains": [C.POINTER(geneo_mesh), C.c_int, C.POINTER(geneo_partition), C.c_int,
+                              _P, C.POINTER(C.c_int)],
     "geneo_assemble_darcy": [_P, C.POINTER(geneo_mesh), _P, C.POINTER(geneo_dirichlet), _P,
                              C.c_double],
     "geneo_assemble": [_P, C.POINTER(geneo_mesh), C.c_int, _P, _P, _P, _P,
@@ -197,6 +199,24 @@ def geneo_estimate_workspace_bytes(mesh, part, modes, prec, unknowns_per_node=3)
                                                  C.byref(part), C.byref(modes), prec,
                                                  C.byref(a), C.byref(s)))
     return a.value, s.value
+
+
+PLAN_INTS = 16
+
+
+def geneo_plan_subdomains(mesh, part, unknowns_per_node=3):
+    """The subdomain plan of geneo_setup (host-only): an int32 array (nsub, 16)
+    of element box lo, hi (exclusive), interior node box lo, hi (inclusive),
+    interior unknowns and band half-width in tiles, Neumann unknowns and
+    half-width."""
+    lib = load()
+    n = C.c_int()
+    _check(lib.geneo_plan_subdomains(C.byref(mesh), int(unknowns_per_node), C.byref(part), 0,
+                                     None, C.byref(n)))
+    out = np.zeros((n.value, PLAN_INTS), dtype=np.int32)
+    _check(lib.geneo_plan_subdomains(C.byref(mesh), int(unknowns_per_node), C.byref(part),
+                                     n.value, out.ctypes.data, C.byref(n)))
+    return out
 
 
 def geneo_assemble_darcy(ctx, mesh, perm, dirichlet, nodal_load, source):

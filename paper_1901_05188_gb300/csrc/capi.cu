@@ -1253,6 +1253,46 @@ int geneo_estimate_workspace_bytes(const geneo_mesh *mesh, int unknowns_per_node
   return GENEO_OK;
 }
 
+int geneo_plan_subdomains(const geneo_mesh *mesh, int unknowns_per_node,
+                          const geneo_partition *part, int max_subs, int32_t *plan,
+                          int *n_subdomains) {
+  if (unknowns_per_node != 1 && unknowns_per_node != 3)
+    return fail(GENEO_ERR_INVALID_ARG, "unknowns per node must be 1 or 3");
+  if (!mesh || mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1)
+    return fail(GENEO_ERR_INVALID_ARG, "bad mesh");
+  if (!n_subdomains) return fail(GENEO_ERR_INVALID_ARG, "null n_subdomains");
+  geneo_ctx tmp;                       // host-only: the integer plan, no device state
+  tmp.nx = mesh->nx;
+  tmp.ny = mesh->ny;
+  tmp.nz = mesh->nz;
+  tmp.nnode = (mesh->nx + 1) * (mesh->ny + 1) * (mesh->nz + 1);
+  tmp.nc = unknowns_per_node;
+  tmp.ndof = tmp.nc * tmp.nnode;
+  tmp.pc.prec = GENEO_FP64;
+  const geneo_modes modes{6, 0.0, 20, -0.01};   // the plan does not depend on them
+  SetupPlan P;
+  int st;
+  if ((st = build_plan(&tmp, part, &modes, P))) return st;
+  *n_subdomains = P.nsub;
+  if (!plan) return GENEO_OK;
+  if (max_subs < P.nsub) return fail(GENEO_ERR_INVALID_ARG, "plan buffer too small");
+  for (int j = 0; j < P.nsub; ++j) {
+    const SubDesc &S = P.subs[j];
+    int32_t *r = plan + (size_t)GENEO_PLAN_INTS * j;
+    for (int d = 0; d < 3; ++d) {
+      r[d] = S.elo[d];
+      r[3 + d] = S.ehi[d];
+      r[6 + d] = S.ibox.lo[d];
+      r[9 + d] = S.ibox.lo[d] + S.ibox.n[d] - 1;
+    }
+    r[12] = S.n_int;
+    r[13] = P.lay_int[j].w;
+    r[14] = S.n_neu;
+    r[15] = P.lay_neu[j].w;
+  }
+  return GENEO_OK;
+}
+
 }  // extern "C"
 
 // ---- autotuning of the Schwarz local-solve launch ---------------------------
