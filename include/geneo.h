@@ -324,6 +324,15 @@ int geneo_spmv_dot_noalloc(int n_nodes, const int32_t *row_ptr, const int32_t *c
                            const double *val, const double *x, double *y, double *xy,
                            void *cuda_stream);
 
+/* The condition estimate geneo_solve reports (stats.kappa_est), from the CG
+ * coefficients alpha_0..alpha_{k-1} and beta_0..beta_{k-2} of a plain PCG run
+ * (host arrays): the ratio of the extreme eigenvalues of the Lanczos
+ * tridiagonal T with T_ii = 1/alpha_i + beta_{i-1}/alpha_{i-1} and
+ * T_{i,i+1} = sqrt(beta_i)/alpha_i (the estimate of Sec. 5, Tables 1-2),
+ * found by Sturm-sequence bisection.  0 when k = 0 or the smallest
+ * eigenvalue is not positive.  Host-only. */
+int geneo_kappa_from_cg(const double *alphas, const double *betas, int k, double *kappa);
+
 /* Solve A u = b by PCG (FP64 precision, GENEO_AS) or flexible CG (mixed
  * precision or GENEO_AS_POU) from u0 = 0 until ||r_k|| <= tol ||b|| or max_it
  * iterations (Sec. 3.1).  u: 3*n_nodes doubles.  stats may be NULL. */

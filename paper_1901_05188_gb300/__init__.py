@@ -91,6 +91,7 @@ _SIGS = {
     "geneo_estimate_workspace_bytes": [C.POINTER(geneo_mesh), C.c_int, C.POINTER(geneo_partition),
                                        C.POINTER(geneo_modes), C.c_int, C.POINTER(C.c_size_t),
                                        C.POINTER(C.c_size_t)],
+    "geneo_kappa_from_cg": [_P, _P, C.c_int, C.POINTER(C.c_double)],
     "geneo_plan_subdomains": [C.POINTER(geneo_mesh), C.c_int, C.POINTER(geneo_partition), C.c_int,
                               _P, C.POINTER(C.c_int)],
     "geneo_assemble_darcy": [_P, C.POINTER(geneo_mesh), _P, C.POINTER(geneo_dirichlet), _P,
@@ -217,6 +218,17 @@ def geneo_plan_subdomains(mesh, part, unknowns_per_node=3):
     _check(lib.geneo_plan_subdomains(C.byref(mesh), int(unknowns_per_node), C.byref(part),
                                      n.value, out.ctypes.data, C.byref(n)))
     return out
+
+
+def geneo_kappa_from_cg(alphas, betas):
+    """stats.kappa_est's estimate from PCG coefficients (host-only)."""
+    a = np.ascontiguousarray(alphas, dtype=np.float64)
+    b = np.ascontiguousarray(betas, dtype=np.float64)
+    out = C.c_double()
+    _check(load().geneo_kappa_from_cg(a.ctypes.data if a.size else None,
+                                      b.ctypes.data if b.size else None, int(a.size),
+                                      C.byref(out)))
+    return out.value
 
 
 def geneo_assemble_darcy(ctx, mesh, perm, dirichlet, nodal_load, source):

@@ -1667,6 +1667,17 @@ int enqueue_iterations(geneo_ctx *c, int iters, cudaStream_t s) {
 
 }  // namespace
 
+extern "C" int geneo_kappa_from_cg(const double *alphas, const double *betas, int k,
+                                   double *kappa) {
+  if (k < 0 || !kappa || (k > 0 && !alphas) || (k > 1 && !betas))
+    return fail(GENEO_ERR_INVALID_ARG, "bad CG coefficients");
+  std::vector<double> al(alphas, alphas + k);
+  std::vector<double> be;
+  if (k > 1) be.assign(betas, betas + (k - 1));
+  *kappa = kappa_from_cg(al, be);
+  return GENEO_OK;
+}
+
 extern "C" int geneo_solve(geneo_ctx *c, double tol, int max_it, double *u, geneo_stats *stats) {
   if (!c || !c->assembled) return fail(GENEO_ERR_STATE, "not assembled");
   if (!c->setup_done) return fail(GENEO_ERR_STATE, "call geneo_setup first");
