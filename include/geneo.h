@@ -324,6 +324,23 @@ int geneo_spmv_dot_noalloc(int n_nodes, const int32_t *row_ptr, const int32_t *c
                            const double *val, const double *x, double *y, double *xy,
                            void *cuda_stream);
 
+/* The set-up's mode-selection rule (Sec. 3.2), host-only: given n eigenvalues
+ * in ascending order (INFINITY for infinite ones), *m = modes->fixed_modes
+ * when that is > 0 (at most the finite ones), else the number of eigenvalues
+ * <= tau capped at modes->max_modes; then, while the cut falls inside a
+ * cluster (neighbours equal to 1e-6 relative plus 1e-9), one fewer, so the
+ * kept span is unique. */
+int geneo_select_modes(const double *lambdas, int n, const geneo_modes *modes, double tau,
+                       int *m);
+
+/* The set-up's default eigenvalue thresholds (Sec. 3.2 and its footnote, read
+ * for a 3D box): per subdomain, half the diagonal of Omega_j's box over
+ * overlap times its smallest element edge.  The mesh coordinates are host
+ * arrays here.  *n_subdomains as for geneo_plan_subdomains; tau may be NULL.
+ * Host-only. */
+int geneo_default_thresholds(const geneo_mesh *mesh, const geneo_partition *part, int max_subs,
+                             double *tau, int *n_subdomains);
+
 /* The condition estimate geneo_solve reports (stats.kappa_est), from the CG
  * coefficients alpha_0..alpha_{k-1} and beta_0..beta_{k-2} of a plain PCG run
  * (host arrays): the ratio of the extreme eigenvalues of the Lanczos

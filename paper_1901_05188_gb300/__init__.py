@@ -92,6 +92,9 @@ _SIGS = {
                                        C.POINTER(geneo_modes), C.c_int, C.POINTER(C.c_size_t),
                                        C.POINTER(C.c_size_t)],
     "geneo_kappa_from_cg": [_P, _P, C.c_int, C.POINTER(C.c_double)],
+    "geneo_select_modes": [_P, C.c_int, C.POINTER(geneo_modes), C.c_double, C.POINTER(C.c_int)],
+    "geneo_default_thresholds": [C.POINTER(geneo_mesh), C.POINTER(geneo_partition), C.c_int, _P,
+                                 C.POINTER(C.c_int)],
     "geneo_plan_subdomains": [C.POINTER(geneo_mesh), C.c_int, C.POINTER(geneo_partition), C.c_int,
                               _P, C.POINTER(C.c_int)],
     "geneo_assemble_darcy": [_P, C.POINTER(geneo_mesh), _P, C.POINTER(geneo_dirichlet), _P,
@@ -217,6 +220,26 @@ def geneo_plan_subdomains(mesh, part, unknowns_per_node=3):
     out = np.zeros((n.value, PLAN_INTS), dtype=np.int32)
     _check(lib.geneo_plan_subdomains(C.byref(mesh), int(unknowns_per_node), C.byref(part),
                                      n.value, out.ctypes.data, C.byref(n)))
+    return out
+
+
+def geneo_select_modes(lambdas, modes, tau):
+    """The set-up's mode count for ascending eigenvalues (host-only)."""
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    m = C.c_int()
+    _check(load().geneo_select_modes(lam.ctypes.data if lam.size else None, int(lam.size),
+                                     C.byref(modes), float(tau), C.byref(m)))
+    return m.value
+
+
+def geneo_default_thresholds(mesh, part):
+    """The set-up's default threshold per subdomain (host-only; host coordinates)."""
+    lib = load()
+    n = C.c_int()
+    _check(lib.geneo_default_thresholds(C.byref(mesh), C.byref(part), 0, None, C.byref(n)))
+    out = np.zeros(n.value)
+    _check(lib.geneo_default_thresholds(C.byref(mesh), C.byref(part), n.value, out.ctypes.data,
+                                        C.byref(n)))
     return out
 
 

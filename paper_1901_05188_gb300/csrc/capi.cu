@@ -1667,6 +1667,42 @@ int enqueue_iterations(geneo_ctx *c, int iters, cudaStream_t s) {
 
 }  // namespace
 
+extern "C" int geneo_select_modes(const double *lambdas, int n, const geneo_modes *modes,
+                                  double tau, int *m) {
+  if (n < 0 || !m || !modes || (n > 0 && !lambdas))
+    return fail(GENEO_ERR_INVALID_ARG, "bad eigenvalue list");
+  std::vector<double> lam(lambdas, lambdas + n);
+  *m = select_modes(lam, modes->fixed_modes, tau, modes->max_modes);
+  return GENEO_OK;
+}
+
+extern "C" int geneo_default_thresholds(const geneo_mesh *mesh, const geneo_partition *part,
+                                        int max_subs, double *tau, int *n_subdomains) {
+  if (!mesh || mesh->nx < 1 || mesh->ny < 1 || mesh->nz < 1 || !mesh->x || !mesh->y || !mesh->z)
+    return fail(GENEO_ERR_INVALID_ARG, "bad mesh");
+  if (!n_subdomains) return fail(GENEO_ERR_INVALID_ARG, "null n_subdomains");
+  geneo_ctx tmp;                       // host-only: coordinates are host arrays here
+  tmp.nx = mesh->nx;
+  tmp.ny = mesh->ny;
+  tmp.nz = mesh->nz;
+  tmp.nnode = (mesh->nx + 1) * (mesh->ny + 1) * (mesh->nz + 1);
+  tmp.nc = 3;
+  tmp.ndof = 3 * tmp.nnode;
+  tmp.pc.prec = GENEO_FP64;
+  tmp.hx.assign(mesh->x, mesh->x + mesh->nx + 1);
+  tmp.hy.assign(mesh->y, mesh->y + mesh->ny + 1);
+  tmp.hz.assign(mesh->z, mesh->z + mesh->nz + 1);
+  const geneo_modes modes{0, 0.0, 20, -0.01};
+  SetupPlan P;
+  int st;
+  if ((st = build_plan(&tmp, part, &modes, P))) return st;
+  *n_subdomains = P.nsub;
+  if (!tau) return GENEO_OK;
+  if (max_subs < P.nsub) return fail(GENEO_ERR_INVALID_ARG, "threshold buffer too small");
+  for (int j = 0; j < P.nsub; ++j) tau[j] = default_threshold(&tmp, P.subs[j], part->overlap);
+  return GENEO_OK;
+}
+
 extern "C" int geneo_kappa_from_cg(const double *alphas, const double *betas, int k,
                                    double *kappa) {
   if (k < 0 || !kappa || (k > 0 && !alphas) || (k > 1 && !betas))
