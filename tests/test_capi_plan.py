@@ -105,3 +105,22 @@ def test_plan_of_random_partitions(case):
         assert ei.value.status == 1
     else:
         _check(p)
+
+
+@pytest.mark.parametrize("name", ["small", "c1", "c2"])
+def test_setup_estimate_covers_the_planned_factors(name):
+    # The host-only set-up estimate (used to admit requests by device memory)
+    # must hold at least the band factor pools of the plan: per subdomain
+    # nt (w + 1) tiles of 32 x 32 for L and for L^T, interior factors in the
+    # chosen precision, the Neumann factors of the GenEO eigensolve in FP64.
+    p = workloads.config(name)
+    plan = _plan(p)
+    keep = []
+    mesh = pkg.GeneoSolver.mesh_of(p, keep)
+    tiles = lambda n, w: ((n + 31) // 32) * (w + 1) * 1024
+    int_elems = sum(tiles(int(r[12]), int(r[13])) for r in plan)
+    neu_elems = sum(tiles(int(r[14]), int(r[15])) for r in plan)
+    for prec, size in ((pkg.GENEO_FP64, 8), (pkg.GENEO_MIXED_FP32, 4)):
+        _, setup = pkg.geneo_estimate_workspace_bytes(mesh, pkg.GeneoSolver.partition_of(p),
+                                                      pkg.GeneoSolver.modes_of(p), prec)
+        assert setup >= 2 * int_elems * size + 2 * neu_elems * 8, (prec, setup)
