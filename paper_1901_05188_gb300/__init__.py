@@ -247,6 +247,8 @@ def geneo_kappa_from_cg(alphas, betas):
     """stats.kappa_est's estimate from PCG coefficients (host-only)."""
     a = np.ascontiguousarray(alphas, dtype=np.float64)
     b = np.ascontiguousarray(betas, dtype=np.float64)
+    if b.size < max(a.size - 1, 0):
+        raise ValueError("need one beta fewer than alphas")
     out = C.c_double()
     _check(load().geneo_kappa_from_cg(a.ctypes.data if a.size else None,
                                       b.ctypes.data if b.size else None, int(a.size),

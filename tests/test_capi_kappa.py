@@ -45,3 +45,8 @@ def test_kappa_of_random_sequences():
 
 def test_kappa_without_coefficients():
     assert pkg.geneo_kappa_from_cg([], []) == 0.0
+
+
+def test_too_few_betas_is_refused():
+    with pytest.raises(ValueError):
+        pkg.geneo_kappa_from_cg([1.0, 2.0, 3.0], [0.5])
