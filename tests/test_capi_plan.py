@@ -124,3 +124,25 @@ def test_setup_estimate_covers_the_planned_factors(name):
         _, setup = pkg.geneo_estimate_workspace_bytes(mesh, pkg.GeneoSolver.partition_of(p),
                                                       pkg.GeneoSolver.modes_of(p), prec)
         assert setup >= 2 * int_elems * size + 2 * neu_elems * 8, (prec, setup)
+
+
+@pytest.mark.parametrize("case", _random(10, 32))
+def test_plan_of_random_darcy_partitions(case):
+    # one unknown per node: the same boxes, unknown counts and band widths in
+    # scalar unknowns
+    from workloads.darcy import make_darcy
+    ne, parts, O = case
+    p = make_darcy(*ne, seed=1, partition=(*parts, O))
+    try:
+        _check(p)
+    except pkg.GeneoError as e:
+        assert e.status == 1
+        for n, k in zip(ne, parts):
+            cnt = np.zeros(n + 1, int)
+            for lo, hi in decomp.axis_split(n, k):
+                elo, ehi = max(0, lo - O), min(n, hi + O)
+                cnt[elo + (elo > 0): ehi - (ehi < n) + 1] += 1
+            if cnt.max() > 4:
+                break
+        else:
+            raise
