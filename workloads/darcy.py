@@ -32,7 +32,8 @@ def permeability(nx, ny, nz, seed=5, mean=-1.0, std=1.5, ell_xy=20.0, ell_z=2.0)
     rng = np.random.default_rng(seed)
     g = rng.standard_normal((nz, ny, nx))
     g = _smooth(_smooth(_smooth(g, 2, ell_xy), 1, ell_xy), 0, ell_z)
-    g = (g - g.mean()) / g.std()
+    sd = g.std()
+    g = (g - g.mean()) / sd if sd > 0 else np.zeros_like(g)     # one cell: the mean field
     logk = mean + std * g
     # channelised layers: every third layer, a meandering channel of width 4
     xs = np.arange(nx)
