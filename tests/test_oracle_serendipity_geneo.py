@@ -9,7 +9,8 @@ sum_j R_j^T X_j R_j 1 = 1 on free dofs.  GenEO: on a floating subdomain the
 generalised eigenproblem has exactly six zero eigenvalues and their
 eigenspace is the rigid displacements of the subdomain's nodes.  Solver: PCG
 with the GenEO preconditioner equals a dense direct solve, and the clamp
-makes the serendipity system SPD.
+makes the serendipity system SPD; on an unclamped block both the ZEM and the
+GenEO coarse spaces contain the six global rigid displacements.
 """
 import numpy as np
 import pytest
@@ -90,3 +91,18 @@ def test_system_spd_and_pcg_matches_direct_solve():
     u_d = np.linalg.solve(Ad, b)
     r = solver.solve(q, precond="geneo", tol=1e-12)
     assert np.linalg.norm(r["u"] - u_d) <= 1e-9 * np.linalg.norm(u_d)
+
+
+@pytest.mark.parametrize("coarse", ["zem", "geneo"])
+def test_global_rigid_modes_lie_in_the_coarse_space(coarse):
+    # unclamped 20-node block: every subdomain floats, its six rigid modes
+    # weighted by the PoU rebuild the six global ones
+    p = make_block(4, 2, 4, [0.0, 90.0], partition=(2, 1, 2, 1), clamp="none",
+                   modes=dict(fixed_modes=6, threshold=0.0, max_modes=20, shift=-0.01))
+    q = dict(p, element="serendipity", dirichlet_dofs=np.zeros(0, np.int32),
+             dirichlet_values=np.zeros(0))
+    subs = decomp.partition(q)
+    A = sd.assemble_stiffness(q)
+    Z, _ = (geneo.zem_space(q, subs, A) if coarse == "zem" else geneo.coarse_space(q, subs, A))
+    Rg = geneo.rigid_body_modes(q, np.arange(sd.nnodes(q)))
+    assert sla.subspace_angles(Z.toarray(), Rg).max() < 1e-8
