@@ -83,8 +83,9 @@ def test_rotation_columns_are_centred():
     assert np.abs(R[:, :3].T @ R[:, 3:]).max() <= 1e-13
 
 
+@pytest.mark.parametrize("pou", ["standard", "sarkis"])
 @pytest.mark.parametrize("coarse", ["zem", "geneo"])
-def test_global_rigid_modes_lie_in_the_coarse_space(coarse):
+def test_global_rigid_modes_lie_in_the_coarse_space(coarse, pou):
     # Unclamped block: every subdomain floats and keeps its six rigid modes,
     # weighted by its PoU; summed over the subdomains the PoU rebuilds each
     # global rigid displacement (sum_j R_j^T X_j R_j = I), so the coarse space
@@ -92,6 +93,8 @@ def test_global_rigid_modes_lie_in_the_coarse_space(coarse):
     from oracle import fem
     p = workloads.config("small", clamp="none")
     p["modes"] = dict(fixed_modes=6, threshold=0.0, max_modes=20, shift=-0.01)
+    p["pou"] = pou
+    p["partition"] = tuple(p["partition"][:3]) + (2,)       # Sarkis differs from 1/multiplicity
     subs = decomp.partition(p)
     A = fem.assemble_stiffness(p)
     if coarse == "zem":
