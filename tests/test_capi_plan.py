@@ -107,13 +107,17 @@ def test_plan_of_random_partitions(case):
         _check(p)
 
 
-@pytest.mark.parametrize("name", ["small", "c1", "c2"])
+@pytest.mark.parametrize("name", ["small", "c1", "c2", "d-small"])
 def test_setup_estimate_covers_the_planned_factors(name):
     # The host-only set-up estimate (used to admit requests by device memory)
     # must hold at least the band factor pools of the plan: per subdomain
     # nt (w + 1) tiles of 32 x 32 for L and for L^T, interior factors in the
     # chosen precision, the Neumann factors of the GenEO eigensolve in FP64.
-    p = workloads.config(name)
+    if name.startswith("d-"):
+        from workloads.darcy import darcy_config
+        p = darcy_config(name)
+    else:
+        p = workloads.config(name)
     plan = _plan(p)
     keep = []
     mesh = pkg.GeneoSolver.mesh_of(p, keep)
@@ -122,7 +126,8 @@ def test_setup_estimate_covers_the_planned_factors(name):
     neu_elems = sum(tiles(int(r[14]), int(r[15])) for r in plan)
     for prec, size in ((pkg.GENEO_FP64, 8), (pkg.GENEO_MIXED_FP32, 4)):
         _, setup = pkg.geneo_estimate_workspace_bytes(mesh, pkg.GeneoSolver.partition_of(p),
-                                                      pkg.GeneoSolver.modes_of(p), prec)
+                                                      pkg.GeneoSolver.modes_of(p), prec,
+                                                      pkg.GeneoSolver.unknowns_per_node(p))
         assert setup >= 2 * int_elems * size + 2 * neu_elems * 8, (prec, setup)
 
 
