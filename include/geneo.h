@@ -312,8 +312,9 @@ int geneo_profile(geneo_ctx *ctx, int what, int reps, double *ms_per_launch, dou
  * (512 KiB, held by every GPU that loads the library until exit), so n_nodes
  * may be at most 524,288 block rows; larger inputs return
  * GENEO_ERR_WORKSPACE_TOO_SMALL.  All pointers are device memory owned by the
- * caller: row_ptr[n_nodes+1], col[nnzb], val[9*nnzb] (row-major blocks),
- * x and y [3*n_nodes], xy [1].  Work is enqueued on cuda_stream (NULL = legacy
+ * caller: row_ptr[n_nodes+1], col[nnzb], val[9*nnzb] (row-major blocks;
+ * rows may hold any number of blocks), x and y [3*n_nodes], xy [1].  x and y
+ * must not overlap (GENEO_ERR_INVALID_ARG otherwise).  Work is enqueued on cuda_stream (NULL = legacy
  * default stream); the call does not synchronise.  The first call on each
  * device looks up the scratch array's device address (cudaGetSymbolAddress)
  * with that device current, so make that first call before any stream

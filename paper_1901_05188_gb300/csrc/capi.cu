@@ -1671,6 +1671,10 @@ extern "C" int geneo_select_modes(const double *lambdas, int n, const geneo_mode
                                   double tau, int *m) {
   if (n < 0 || !m || !modes || (n > 0 && !lambdas))
     return fail(GENEO_ERR_INVALID_ARG, "bad eigenvalue list");
+  if (modes->fixed_modes < 0 || modes->fixed_modes > kMaxModes ||
+      (modes->fixed_modes == 0 && (modes->max_modes < 1 || modes->max_modes > kMaxModes)))
+    return fail(GENEO_ERR_INVALID_ARG, "bad mode options (fixed_modes 0..32; max_modes 1..32 "
+                                       "when fixed_modes is 0)");
   std::vector<double> lam(lambdas, lambdas + n);
   *m = select_modes(lam, modes->fixed_modes, tau, modes->max_modes);
   return GENEO_OK;

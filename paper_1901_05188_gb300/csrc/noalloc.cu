@@ -48,9 +48,9 @@ __global__ void __launch_bounds__(256)
     const double *v = val + 9 * (size_t)base;
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
     for (int e = lane; e < ne; e += 32) {
-      int blk = (e * 57) >> 9;      // e / 9 for e < 256
-      int rc = e - 9 * blk;
-      int r = (rc * 11) >> 5;       // rc / 3 for rc < 9
+      const int blk = e / 9;        // exact for any row length
+      const int rc = e - 9 * blk;
+      const int r = rc / 3;
       double prod = v[e] * x[3 * col[base + blk] + rc - 3 * r];
       if (r == 0) a0 += prod;
       else if (r == 1) a1 += prod;
@@ -111,10 +111,27 @@ extern "C" int geneo_spmv_dot_noalloc(int n_nodes, const int32_t *row_ptr, const
                            "524288 block rows");
     return GENEO_ERR_WORKSPACE_TOO_SMALL;
   }
+  {
+    // y is written while other warps still read x: the two must not overlap
+    const char *xb = reinterpret_cast<const char *>(x);
+    const char *yb = reinterpret_cast<const char *>(y);
+    const size_t len = 3 * sizeof(double) * (size_t)n_nodes;
+    if (xb < yb + len && yb < xb + len) {
+      geneo_set_last_message("geneo_spmv_dot_noalloc: x and y overlap (in-place calls are not "
+                             "supported)");
+      return GENEO_ERR_INVALID_ARG;
+    }
+  }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return GENEO_ERR_CUDA;
-  if (dev < 0 || dev >= kNaMaxDevices) return GENEO_ERR_INVALID_ARG;
+  if (e != cudaSuccess) {
+    geneo_set_last_cuda_error(e, "cudaGetDevice", __FILE__, __LINE__);
+    return GENEO_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= kNaMaxDevices) {
+    geneo_set_last_message("geneo_spmv_dot_noalloc: device ordinal above 63");
+    return GENEO_ERR_INVALID_ARG;
+  }
   // once per device, with that device current: device address of the scratch
   NaSetup &S = g_na[dev];
   std::call_once(S.once, [&S]() {
@@ -127,10 +144,17 @@ extern "C" int geneo_spmv_dot_noalloc(int n_nodes, const int32_t *row_ptr, const
   cudaStream_t s = (cudaStream_t)cuda_stream;
   // the ticket counter must start at zero (a previous call may have been cut short)
   e = cudaMemsetAsync(S.ptr + kNaMaxPartials, 0, sizeof(unsigned int), s);
-  if (e != cudaSuccess) return GENEO_ERR_CUDA;
+  if (e != cudaSuccess) {
+    geneo_set_last_cuda_error(e, "cudaMemsetAsync(scratch counter)", __FILE__, __LINE__);
+    return GENEO_ERR_CUDA;
+  }
   const int blocks = (n_nodes + kNaRowsPerBlock - 1) / kNaRowsPerBlock;
   k_spmv_dot_noalloc<<<blocks, 256, 0, s>>>(n_nodes, row_ptr, col, val, x, y, xy, S.ptr);
   GENEO_COUNT_LAUNCH();
   e = cudaGetLastError();
-  return e == cudaSuccess ? GENEO_OK : GENEO_ERR_CUDA;
+  if (e != cudaSuccess) {
+    geneo_set_last_cuda_error(e, "k_spmv_dot_noalloc launch", __FILE__, __LINE__);
+    return GENEO_ERR_CUDA;
+  }
+  return GENEO_OK;
 }

@@ -3,8 +3,10 @@
 Calls only the FP64 CPU oracle (oracle/) on the seeded inputs of `workloads`.
 Output: tests/golden/<name>_oracle.json with the PCG iteration count, the
 Lanczos condition estimate, the coarse dimension, per-subdomain mode counts
-and eigenvalues, and the displacement at a fixed sample of dofs (every
-stride-th dof) plus its 2-norm.  Usage: python tests/golden/make_golden.py c2
+and eigenvalues, the displacement at a fixed sample of dofs (every
+stride-th dof), its 2-norm, and the 2-norm of every consecutive chunk of
+CHUNK dofs (so a comparison touches every dof, not only the samples).
+Usage: python tests/golden/make_golden.py c2 [nsamples]
 """
 import json
 import os
@@ -20,6 +22,9 @@ import workloads  # noqa: E402
 from oracle import solver  # noqa: E402
 
 
+CHUNK = 1024
+
+
 def main(name, nsamples=600):
     p = workloads.config(name)
     t = time.time()
@@ -33,6 +38,9 @@ def main(name, nsamples=600):
                lambdas=[[float(v) for v in lam[:21]] for lam in r["lambdas"]],
                u_norm=float(np.linalg.norm(u)), u_min_z=float(u[2::3].min()),
                sample_stride=int(stride), u_samples=[float(v) for v in u[idx]],
+               chunk=CHUNK,
+               u_chunk_norms=[float(np.linalg.norm(u[i:i + CHUNK]))
+                              for i in range(0, u.size, CHUNK)],
                rel_res_true=float(r["true_rel_res"]),
                oracle_seconds=dict(assemble=r["t_assemble"], setup=r["t_setup"],
                                    solve=r["t_solve"], total=time.time() - t))
@@ -43,4 +51,5 @@ def main(name, nsamples=600):
 
 
 if __name__ == "__main__":
-    main(sys.argv[1] if len(sys.argv) > 1 else "c2")
+    main(sys.argv[1] if len(sys.argv) > 1 else "c2",
+         int(sys.argv[2]) if len(sys.argv) > 2 else 600)

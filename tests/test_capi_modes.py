@@ -72,3 +72,13 @@ def test_select_modes(seed):
         modes = pkg.geneo_modes(fixed, 0.0, cap, -0.01)
         assert pkg.geneo_select_modes(lam, modes, tau) == geneo.select_modes(lam, fixed, tau, cap), \
             (lam, fixed, tau, cap)
+
+
+def test_select_modes_refuses_bad_caps():
+    lam = np.array([0.0, 0.1, 0.2, 0.3])
+    for fixed, cap in ((0, 0), (0, -3), (0, 33), (-1, 20), (33, 20)):
+        with pytest.raises(pkg.GeneoError) as e:
+            pkg.geneo_select_modes(lam, pkg.geneo_modes(fixed, 0.0, cap, -0.01), 1.0)
+        assert e.value.status == 1, (fixed, cap)
+    # a fixed count ignores the cap
+    assert pkg.geneo_select_modes(lam, pkg.geneo_modes(2, 0.0, 0, -0.01), 1.0) == 2
