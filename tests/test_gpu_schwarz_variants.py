@@ -11,6 +11,15 @@ read from global memory); repeated applications must be bit-identical (no
 race between the warps or CTAs of a sweep, or between a stage's copies and
 its readers).
 
+Besides the small and c1 blocks (narrow bands: every staged shape also stages
+its chain tiles), two wide-band blocks reach the forms the larger workloads
+use: "wide" (14x14x28 elements, 1x1x2 subdomains, half-bandwidth 23 tiles,
+like the 128x64x48 workload's) takes the look-ahead sweep with chain tiles in
+registers (stage without the chain tiles) for FP32 at one CTA per subdomain,
+and only the unstaged sweeps fit for FP64 at one and two CTAs; "wide15"
+(15x15x30, 26 tiles) takes the register-chain form for FP64 at four CTAs.
+Clusters of 1, 2, 4 and 8 CTAs are pinned on every block.
+
 FP64 factors: 1e-9 relative to the oracle, 1e-12 to the reference shape, and
 the same iteration count within 1.  FP32 factors: the local matrices of these
 layered blocks have condition numbers up to 4e5, so an FP32 solve may lose up
@@ -28,6 +37,7 @@ import pytest
 
 import workloads
 from oracle import decomp, fem, krylov
+from workloads.laminate import make_block
 
 from gpu_common import rel, require_gpu
 
@@ -40,6 +50,32 @@ def pkg():
 
 
 _REF = {}
+_WIDE = {"wide": (14, 14, 28), "wide15": (15, 15, 30)}
+
+
+def _problem(name):
+    if name in _WIDE:
+        return make_block(*_WIDE[name], [0.0, 90.0, 90.0, 0.0], partition=(1, 1, 2, 1))
+    return workloads.config(name)
+
+
+def _staged_form(pkg, p, prec, cluster):
+    """'chain' / 'no-chain' / None: how the staged look-ahead sweep of this
+    block stages its tiles (the library's shared-memory rule: two stages of
+    far tiles, plus the two chain tiles when the launch still fits in 227 KB)."""
+    keep = []
+    plan = pkg.geneo_plan_subdomains(pkg.GeneoSolver.mesh_of(p, keep),
+                                     pkg.GeneoSolver.partition_of(p))
+    npad = 32 * ((int(plan[:, 12].max()) + 31) // 32)
+    w = int(plan[:, 13].max())
+    size = 8 if prec == 0 else 4
+    t = (w - 1 + cluster - 1) // cluster if w > 1 else 1
+
+    def smem(tiles):
+        return 2 * tiles * 1024 * size + 6 * 8 + ((16 + 8 + 4 * cluster) * 32 + npad) * size
+    if smem(t + 2) <= 227 * 1024:
+        return "chain"
+    return "no-chain" if smem(t) <= 227 * 1024 else None
 
 
 def _reference(pkg, monkeypatch, name, prec, r):
@@ -50,7 +86,7 @@ def _reference(pkg, monkeypatch, name, prec, r):
             m.setenv("GENEO_SCHWARZ_CLUSTER", "1")
             m.setenv("GENEO_SCHWARZ_ROWS", "1")
             m.setenv("GENEO_SCHWARZ_STAGED", "0")
-            p = workloads.config(name)
+            p = _problem(name)
             s = pkg.GeneoSolver()
             s.assemble(p)
             s.setup(p, prec, pkg.GENEO_AS, pkg.GENEO_COARSE_NONE)
@@ -60,8 +96,19 @@ def _reference(pkg, monkeypatch, name, prec, r):
     return _REF[key]
 
 
-@pytest.mark.parametrize("name", ["small", "c1"])
-@pytest.mark.parametrize("cluster", [1, 2, 4])
+def test_wide_blocks_reach_the_register_chain_forms():
+    pkg = require_gpu()
+    assert _staged_form(pkg, _problem("wide"), 1, 1) == "no-chain"
+    assert _staged_form(pkg, _problem("wide"), 0, 1) is None
+    assert _staged_form(pkg, _problem("wide"), 0, 2) is None
+    assert _staged_form(pkg, _problem("wide15"), 0, 4) == "no-chain"
+    assert _staged_form(pkg, workloads.config("c3"), 1, 1) == "no-chain"
+    for name in ("small", "c1"):
+        assert _staged_form(pkg, workloads.config(name), 0, 1) == "chain"
+
+
+@pytest.mark.parametrize("name", ["small", "c1", "wide", "wide15"])
+@pytest.mark.parametrize("cluster", [1, 2, 4, 8])
 @pytest.mark.parametrize("rows", [0, 1, 2, 4])
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("staged", [0, 1])
@@ -70,7 +117,9 @@ def test_schwarz_launch_shapes(pkg, monkeypatch, name, cluster, rows, prec, stag
         pytest.skip("four rows per barrier are offered for FP32 factors only")
     if staged and rows not in (0, 1, 2):
         pytest.skip("the staged sweeps take zero (look-ahead), one or two rows per step")
-    p = workloads.config(name)
+    if name == "wide15" and not (prec == 0 and cluster == 4):
+        pytest.skip("wide15 is here for the FP64 register-chain form at four CTAs")
+    p = _problem(name)
     A, _ = fem.assemble_system(p)
     M = krylov.OneLevelAS(A, decomp.partition(p))
     r = np.random.default_rng(5).normal(size=A.shape[0])
