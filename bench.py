@@ -1,25 +1,34 @@
 #!/usr/bin/env python
 """GenEO-PCG time-to-solution benchmark on GB300.
 
-Workload (default): the 64x32x24-element laminated block (160,875 dofs,
-12 plies drawn from {0, +-45, 90} with 11 one-element resin interlayers),
-clamped at x = 0 under 1 MPa top pressure, 4x4x2 subdomains with overlap 1,
-GenEO threshold rule capped at 20 modes per subdomain, PCG to ||r||/||b|| <= 1e-8.
+Workload (default): the 128x64x48-element laminated block with a fibre
+wrinkle (1,232,595 dofs, 24 plies of a seeded random stacking, out-of-plane
+Gaussian wrinkle of 8 degrees and width 10 elements), clamped at x = 0 under
+1 MPa top pressure, 8x4x4 subdomains with overlap 1, GenEO threshold rule
+capped at 20 modes per subdomain, (F)PCG to ||r||/||b|| <= 1e-8.  `value` is
+the mixed-precision path (FP32 subdomain factors with 3xTF32 tensor-core
+updates inside FP64 flexible CG); the all-FP64 path is timed beside it
+(`fp64`), and both carry their error against the FP64 oracle's stored
+solution (tests/golden/c3_oracle.json).
 
 One step = the whole method on one synthetic problem: assembly of A u = b,
 the GenEO set-up (eigenproblems, coarse space, subdomain factors) and the
 (F)PCG solve, all on the GPU through the library's C ABI.  `value` times
 steps whose inputs already sit in device memory; `e2e` times the same step
 from host arrays with the host<->device copies inside the timed region.
+Secondary legs: the 64x32x24 laminate (160,875 dofs) with GenEO in FP64 and
+mixed precision, one-level additive Schwarz and unpreconditioned CG; Darcy
+flow on SPE10's 60x220x85 grid; a batch of uneven blocks; a serving stream.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--config c2] [--precision fp64|mixed]
+                  [--config c3] [--precision mixed|fp64]
 
 Multi-GPU: the path does not shard (one GPU per problem, no collectives), so
 N ranks run N independent replicas (weak scaling); value = max-over-ranks time
 divided by the solves all ranks completed.
 `--impl reference` times the FP64 CPU oracle on a bounded sample of the same
-workload and extrapolates to one full solve.
+workload per step (one subdomain's share of every stage) and reports the
+extrapolation to one full solve, labelled as such.
 """
 from __future__ import annotations
 
@@ -48,15 +57,19 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--config", default="c3")
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--other-steps", type=int, default=5,
+                    help="timed solves of the other precision (at most --steps)")
+    ap.add_argument("--no-other", action="store_true", help="skip the other precision's leg")
+    ap.add_argument("--no-c2", action="store_true",
+                    help="skip the 64x32x24 legs (GenEO FP64/mixed, one-level AS, plain CG)")
+    ap.add_argument("--no-profile", action="store_true", help="skip the per-kernel rooflines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-darcy", action="store_true")
-    ap.add_argument("--no-c3", action="store_true",
-                    help="skip the 128x64x48 mixed-precision leg")
     ap.add_argument("--batch-blocks", type=int, default=32,
                     help="blocks of the uneven batched-solve workload to run (0 skips it)")
     ap.add_argument("--serve-requests", type=int, default=10,
@@ -65,7 +78,8 @@ def parse():
 
 
 def workload_config(p, prec):
-    s = dict(workload=f"{p['name']}: {p['nx']}x{p['ny']}x{p['nz']} Q1 hex laminate, "
+    wr = " with a fibre wrinkle" if np.any(np.asarray(p.get("elem_phi", 0.0)) != 0) else ""
+    s = dict(workload=f"{p['name']}: {p['nx']}x{p['ny']}x{p['nz']} Q1 hex laminate{wr}, "
                       f"{3 * (p['nx'] + 1) * (p['ny'] + 1) * (p['nz'] + 1)} dofs",
              partition="x".join(str(v) for v in p["partition"][:3]) + f", overlap {p['partition'][3]}",
              modes=("fixed %d" % p["modes"]["fixed_modes"] if p["modes"]["fixed_modes"]
@@ -126,6 +140,8 @@ class ClockSampler:
 
 
 FP64_PEAK_TFLOPS = 1.25
+FP64_PEAK_SOURCE = ("nominal FP64 1.25 TFLOP/s (152 SMs x 2 FMA/clk x 2.07 GHz); "
+                    "torch DGEMM measured 1.10")
 
 
 def profiled_traffic(kernel, args):
@@ -162,60 +178,87 @@ def measured_peaks():
 # ---------------------------------------------------------------------------
 # CPU oracle sample (the baseline arm)
 
-def oracle_sample(p, gpu_iterations):
-    """Time a bounded sample of the oracle on this workload and extrapolate to
-    one full solve: 1/8 of the element assembly (x8), one of the GenEO
-    eigensolves (x subdomains), four subdomain factorisations (x subdomains/4),
-    and per iteration an SpMV on the sampled rows (x8) plus the four subdomain
-    solves (x subdomains/4), times the iteration count.
-    Returns (ms, sample description, threads used)."""
-    import contextlib
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [d.get("num_threads") for d in threadpool_info() if d.get("user_api") == "blas"]
+        if n:
+            return int(max(n)), "threadpoolctl"
+    except ImportError:
+        pass
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(k):
+            return int(os.environ[k]), k
+    return os.cpu_count() or 1, "library default (all cores)"
+
+
+def oracle_sample(p, A, subs, gpu_iterations, step=0):
+    """Time one subdomain's share of the oracle's whole solve on this workload:
+    1/nsub of the element assembly, the GenEO eigensolve and the subdomain
+    factorisation (sparse LU of A_j = R_j A R_j^T, as the oracle's one-level
+    term builds it) of one subdomain (rotating with `step`), and per iteration
+    an SpMV over 1/nsub of the elements plus that subdomain's solve.  A is the
+    oracle's assembled global matrix (built once, outside the samples).
+    Returns (measured ms of the sample, ms extrapolated to one full solve
+    (x nsub), sample description).  The coarse space and the vector updates
+    are not sampled."""
     import scipy.sparse as sp
     import scipy.sparse.linalg as spla
-    from oracle import decomp, fem, geneo
-    try:
-        from threadpoolctl import threadpool_limits
-        ctx, threads = threadpool_limits(limits=1), 1
-    except ImportError:           # BLAS keeps its default; the sparse kernels are serial
-        ctx, threads = contextlib.nullcontext(), os.cpu_count() or 1
-    with ctx:
-        nel = p["nx"] * p["ny"] * p["nz"]
-        t0 = time.perf_counter()
-        A8 = fem.assemble_stiffness(p, np.arange(0, nel, 8))
-        t_asm = (time.perf_counter() - t0) * 8
-        subs = decomp.partition(p)
-        ns = len(subs)
-        j = min(ns - 1, ns // 2 + 1)
-        m = p["modes"]
-        nev = (m["fixed_modes"] if m["fixed_modes"] > 0 else m["max_modes"]) + 1
-        t0 = time.perf_counter()
-        Aj, Aoj = geneo.local_matrices(p, subs[j])
-        Xd = sp.diags(subs[j].X)
-        geneo.eigenpairs(Aj, (Xd @ Aoj @ Xd).tocsr(), nev, m["shift"])
-        t_eig = (time.perf_counter() - t0) * ns
-        idx = sorted({min(ns - 1, k * ns // 4) for k in range(4)})
-        t0 = time.perf_counter()
-        lus = []
-        for k in idx:
-            Ak, _ = geneo.local_matrices(p, subs[k])
-            lus.append((spla.splu(Ak.tocsc()), Ak.shape[0]))
-        t_fac = (time.perf_counter() - t0) * ns / len(idx)
-        x = np.ones(A8.shape[0])
-        t0 = time.perf_counter()
-        for _ in range(3):
-            A8 @ x
-        t_spmv = (time.perf_counter() - t0) / 3 * 8
-        t0 = time.perf_counter()
-        for _ in range(3):
-            for lu, n in lus:
-                lu.solve(np.ones(n))
-        t_sub = (time.perf_counter() - t0) / 3 * ns / len(idx)
-        total = t_asm + t_eig + t_fac + gpu_iterations * (t_spmv + t_sub)
-    sample = (f"FP64 oracle sample: assembly of 1/8 of the elements (x8), 1 of {ns} GenEO "
-              f"eigensolves (x{ns}), {len(idx)} of {ns} subdomain factorisations, per-iteration "
-              f"SpMV on 1/8 of the elements (x8) + {len(idx)} subdomain solves, "
-              f"x {gpu_iterations} iterations")
-    return total * 1000.0, sample, threads
+    from oracle import fem, geneo
+    t_start = time.perf_counter()
+    ns = len(subs)
+    nel = p["nx"] * p["ny"] * p["nz"]
+    t0 = time.perf_counter()
+    Ae = fem.assemble_stiffness(p, np.arange(step % ns, nel, ns)).tocsr()
+    t_asm = time.perf_counter() - t0
+    j = (ns // 2 + 1 + step) % ns
+    m = p["modes"]
+    nev = (m["fixed_modes"] if m["fixed_modes"] > 0 else m["max_modes"]) + 1
+    t0 = time.perf_counter()
+    Aj, Aoj = geneo.local_matrices(p, subs[j])
+    Xd = sp.diags(subs[j].X)
+    geneo.eigenpairs(Aj, (Xd @ Aoj @ Xd).tocsr(), nev, m["shift"])
+    t_eig = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    d = subs[j].int_dofs
+    lu = spla.splu(A[d][:, d].tocsc())
+    t_fac = time.perf_counter() - t0
+    x = np.ones(Ae.shape[0])
+    rj = np.ones(d.size)
+    t0 = time.perf_counter()
+    for _ in range(gpu_iterations):
+        Ae @ x
+        lu.solve(rj)
+    t_it = time.perf_counter() - t0
+    measured = time.perf_counter() - t_start
+    full = (t_asm + t_eig + t_fac + t_it) * ns
+    sample = (f"one subdomain's share of the FP64 oracle: 1/{ns} of the element assembly, "
+              f"subdomain {j}'s GenEO eigensolve (ARPACK shift-invert) and sparse LU, "
+              f"{gpu_iterations} iterations of an SpMV over 1/{ns} of the elements plus its local "
+              f"solve; extrapolated x{ns}; coarse space and vector updates not sampled")
+    return measured * 1000.0, full * 1000.0, sample
+
+
+def golden(config):
+    path = os.path.join(ROOT, "tests", "golden", f"{config}_oracle.json")
+    return json.load(open(path)) if os.path.exists(path) else None
 
 
 def run_reference(args):
@@ -223,24 +266,39 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    from oracle import decomp, fem
     p = workloads.config(args.config)
-    iters = 103 if args.config == "c2" else 60
-    gold = os.path.join(ROOT, "tests", "golden", f"{args.config}_oracle.json")
-    if os.path.exists(gold):
-        iters = json.load(open(gold))["iterations"]
-    for _ in range(args.warmup):
-        oracle_sample(p, iters)
-    times = []
-    sample, threads = "", 1
-    for _ in range(args.steps):
-        ms, sample, threads = oracle_sample(p, iters)
-        times.append(ms)
-    v = statistics.mean(times)
+    g = golden(args.config)
+    iters = g["iterations"] if g else 100
+    A, _ = fem.assemble_system(p)
+    A = A.tocsr()
+    subs = decomp.partition(p)
+    for w in range(args.warmup):
+        oracle_sample(p, A, subs, iters, step=w)
+    meas, full = [], []
+    sample = ""
+    for k in range(args.steps):
+        ms, est, sample = oracle_sample(p, A, subs, iters, step=args.warmup + k)
+        meas.append(ms)
+        full.append(est)
+    v = statistics.mean(full)
+    threads, how = blas_threads()
+    cpu = dict(value=v, unit=UNIT, cores=os.cpu_count() or 1, kind="oracle", sample=sample,
+               estimate="extrapolated from the sample, not a timed full solve",
+               cpu_model=cpu_model(), blas_threads=threads, blas_threads_set_by=how,
+               sparse_lu_threads=1)
+    if g and "oracle_seconds" in g:
+        cpu["full_solve_recorded_s"] = g["oracle_seconds"].get("total")
+        cpu["full_solve_recorded_on"] = "the machine that wrote tests/golden (x86, 8 cores)"
     line = dict(metric=METRIC, value=v, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
-                warmup=args.warmup, ms_per_step=v, higher_is_better=False, scaling="weak",
-                vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
-                config=workload_config(p, "fp64"),
-                cpu_baseline=dict(value=v, unit=UNIT, cores=threads, kind="oracle", sample=sample),
+                warmup=args.warmup, ms_per_step=statistics.mean(meas), higher_is_better=False,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
+                config=workload_config(p, "fp64"), cpu_baseline=cpu,
+                extrapolation=dict(ms_per_step_measured=statistics.mean(meas),
+                                   factor=int(p["partition"][0] * p["partition"][1] *
+                                              p["partition"][2]),
+                                   note="value = one full solve extrapolated from each step's "
+                                        "sample; ms_per_step = the sample actually timed"),
                 e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line))
 
@@ -278,11 +336,108 @@ def job_ms_per_solve(ms_local, steps, world, device="cpu"):
     return ms_step, ms_step / world
 
 
-def one_solve(pkg, s, p, prec, out):
+def one_solve(pkg, s, p, prec, out, schwarz=0, coarse=0, max_it=5000):
     s.assemble(p)
-    s.setup(p, prec)
-    u, st = s.solve(tol=TOL, max_it=5000, out=out)
+    s.setup(p, prec, schwarz, coarse)
+    u, st = s.solve(tol=TOL, max_it=max_it, out=out, raise_on_nonconvergence=False)
     return st
+
+
+def oracle_error(u, g):
+    """Error of the displacement u against the FP64 oracle's stored solution:
+    relative L2 over the stored samples, the norm of u, and the largest
+    deviation of the per-chunk norms (every dof is in one chunk) relative to
+    the largest chunk norm."""
+    if g is None:
+        return None
+    us = u[::g["sample_stride"]][:len(g["u_samples"])]
+    ref = np.asarray(g["u_samples"])
+    out = dict(rel_l2_err_samples=float(np.linalg.norm(us - ref) / np.linalg.norm(ref)),
+               n_samples=int(ref.size),
+               rel_err_u_norm=float(abs(np.linalg.norm(u) - g["u_norm"]) / g["u_norm"]),
+               oracle_iterations=g["iterations"])
+    if "u_chunk_norms" in g:
+        ch = int(g["chunk"])
+        cn = np.sqrt(np.add.reduceat(u * u, np.arange(0, u.size, ch)))
+        rc = np.asarray(g["u_chunk_norms"])
+        out["max_dev_chunk_norms"] = float(np.max(np.abs(cn - rc)) / np.max(rc))
+    return out
+
+
+def leg_summary(st):
+    return dict(iterations=st["iterations"], rel_res_true=st["rel_res_true"],
+                n_coarse=st["n_coarse"], kappa_est=st["kappa_est"],
+                phases_ms=dict(assemble=st["ms_assemble"], setup_eig_coarse=st["ms_setup_eig"],
+                               setup_factor=st["ms_setup_factor"], solve=st["ms_solve"]),
+                schwarz_launch=dict(cluster=st["schwarz_cluster"], rows=st["schwarz_rows"],
+                                    staged=st["schwarz_staged"]))
+
+
+def tf32_peak():
+    """Dense TF32 tensor peak: the measured bf16 burst peak times the nominal
+    TF32 / bf16 ratio (1.1 / 2.25 PFLOP/s)."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["bf16_tflops"]) * 1.1 / 2.25, "measured bf16 x nominal TF32/bf16"
+    except Exception:
+        return 1900.0 * 1.1 / 2.25, "fallback bf16 x nominal TF32/bf16"
+
+
+def rooflines(pkg, s, st, args, peak, peak_kind):
+    """Per-kernel rooflines of one solve of the resident set-up, each with its
+    time share: (ms per solve, record) for the Schwarz local solves, the SpMV,
+    the eigensolver's band solves, the Cholesky of the shifted Neumann
+    matrices and the subdomain factorisation."""
+    mixed = args.precision == "mixed"
+    cand = []
+    n_it = st["iterations"] + 1
+    ms, by, fl = pkg.geneo_profile(s.ctx, 0, 10)
+    cand.append((ms * n_it, dict(
+        bound="hbm", kernel="k_schwarz_cluster* (one-level local band solves, "
+                            f"{'FP32' if mixed else 'FP64'})",
+        achieved=by / (ms * 1e-3) / 1e9, peak=peak, unit="GB/s", peak_source=f"{peak_kind} hbm_gbs",
+        ms_per_launch=ms, algorithmic_bytes=by, launches_per_solve=n_it)))
+    ms, by, fl = pkg.geneo_profile(s.ctx, 1, 50)
+    cand.append((ms * n_it, dict(
+        bound="hbm", kernel="k_cg_spmv_pq / k_spmv (3x3 BSR SpMV, FP64)",
+        achieved=by / (ms * 1e-3) / 1e9, peak=peak, unit="GB/s", peak_source=f"{peak_kind} hbm_gbs",
+        ms_per_launch=ms, algorithmic_bytes=by, launches_per_solve=n_it)))
+    if st["n_coarse"] > 0 and st["lanczos_steps"] > 0:
+        n_l = 2 * st["lanczos_steps"] + 1     # two sweeps per block step + the Ritz vectors
+        ms, by, fl = pkg.geneo_profile(s.ctx, 3, 5)
+        cand.append((ms * n_l, dict(
+            bound="alu", kernel="k_band_solve_dense (GenEO shift-invert band solves, FP64, "
+                                "8 right-hand sides)",
+            achieved=fl / (ms * 1e-3) / 1e12, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+            peak_source=FP64_PEAK_SOURCE, ms_per_launch=ms, algorithmic_flops=fl,
+            algorithmic_bytes=by, launches_per_solve=n_l)))
+        ms, by, fl = pkg.geneo_profile(s.ctx, 4, 2)
+        cand.append((ms, dict(
+            bound="alu", kernel="band Cholesky of S_j = A_j - sigma B_j (k_chol_diag/trsm/"
+                                "update<double>, FP64)",
+            achieved=fl / (ms * 1e-3) / 1e12, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+            peak_source=FP64_PEAK_SOURCE, ms_per_launch=ms, algorithmic_flops=fl,
+            algorithmic_bytes=by, launches_per_solve=1)))
+    ms, by, fl = pkg.geneo_profile(s.ctx, 5, 2)
+    if mixed:
+        tp, tsrc = tf32_peak()
+        rec = dict(bound="tensor", kernel="band Cholesky of A_j, FP32 with 3xTF32 tcgen05 trailing "
+                                          "updates (k_chol_update_tc)",
+                   achieved=3 * fl / (ms * 1e-3) / 1e12, peak=tp, unit="TFLOP/s",
+                   peak_source=tsrc, ms_per_launch=ms, algorithmic_flops=fl,
+                   tensor_flops=3 * fl, launches_per_solve=1,
+                   note="runs beside the GenEO eigensolve on its own streams")
+    else:
+        rec = dict(bound="alu", kernel="band Cholesky of A_j (k_chol_*<double>, FP64)",
+                   achieved=fl / (ms * 1e-3) / 1e12, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                   peak_source=FP64_PEAK_SOURCE, ms_per_launch=ms, algorithmic_flops=fl,
+                   launches_per_solve=1, note="runs beside the GenEO eigensolve on its own streams")
+    cand.append((ms, rec))
+    for t, r in cand:
+        r["frac"] = r["achieved"] / r["peak"]
+        r["ms_per_solve"] = t
+    cand.sort(key=lambda t: -t[0])
+    return cand
 
 
 def run_ours(args):
@@ -299,18 +454,34 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
     pkg.load(build_if_missing=True)
-    prec = pkg.GENEO_FP64 if args.precision == "fp64" else pkg.GENEO_MIXED_FP32
+    mixed = args.precision == "mixed"
+    prec = pkg.GENEO_MIXED_FP32 if mixed else pkg.GENEO_FP64
+    other = pkg.GENEO_FP64 if mixed else pkg.GENEO_MIXED_FP32
     p = workloads.config(args.config)
+    g = golden(args.config)
     pd = device_problem(p, torch, dev)
     s = pkg.GeneoSolver()
     ndof = 3 * (p["nx"] + 1) * (p["ny"] + 1) * (p["nz"] + 1)
     u_dev = torch.empty(ndof, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize(dev)
+
+    def timed(prob, pr, out, steps, warm, **kw):
+        for _ in range(warm):
+            st = one_solve(pkg, s, prob, pr, out, **kw)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(steps):
+            st = one_solve(pkg, s, prob, pr, out, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / steps, st
 
     for _ in range(args.warmup):
         st = one_solve(pkg, s, pd, prec, u_dev)
@@ -318,8 +489,6 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     l0 = pkg.geneo_launch_count()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     stats = []
     for _ in range(args.steps):
@@ -331,6 +500,7 @@ def run_ours(args):
     ms_total = e0.elapsed_time(e1)
     ms_step, value = job_ms_per_solve(ms_total, args.steps, world, dev)
     st = stats[-1]
+    acc = oracle_error(u_dev.cpu().numpy(), g)
 
     # end-to-end through the C ABI from host arrays (copies inside the region)
     e2e = None
@@ -346,74 +516,55 @@ def run_ours(args):
         barrier()
         wall = (time.perf_counter() - t0) * 1000.0
         _, e2e_ms = job_ms_per_solve(max(e0.elapsed_time(e1), wall), args.steps, world, dev)
-        e2e = dict(value=e2e_ms, unit=UNIT,
+        e2e = dict(value=e2e_ms, unit=UNIT, steps=args.steps,
                    h2d_bytes_per_step=host_bytes(p), d2h_bytes_per_step=8 * ndof)
 
-    # roofline of the dominant kernel: the larger of the Schwarz local solves
-    # (per iteration) and the eigensolver's FP64 band solves (per Lanczos step)
+    # rooflines of the resident set-up's kernels; the headline object is the
+    # kernel with the largest share of one solve
     peak, peak_kind = measured_peaks()
-    ms_k, by_k, fl_k = pkg.geneo_profile(s.ctx, 0, 20)
-    n_schwarz = st["iterations"] + 1
-    cand = []
-    hbm = dict(bound="hbm", kernel="k_schwarz_cluster (one-level local band solves, "
-                                   f"{'FP64' if args.precision == 'fp64' else 'FP32'})",
-               achieved=by_k / (ms_k * 1e-3) / 1e9, peak=peak, unit="GB/s",
-               peak_source=f"{peak_kind} hbm_gbs", ms_per_launch=ms_k,
-               algorithmic_bytes=by_k, launches_per_solve=n_schwarz)
-    hbm["frac"] = hbm["achieved"] / peak
-    hbm["traffic"] = profiled_traffic("k_schwarz_cluster", args)
-    cand.append((ms_k * n_schwarz, hbm))
-    if st["n_coarse"] > 0:
-        ms_l, by_l, fl_l = pkg.geneo_profile(s.ctx, 3, 5)
-        n_lanczos = 2 * st["lanczos_steps"] + 1   # two sweeps per block step + the Ritz vectors
-        alu = dict(bound="alu", kernel="k_band_solve_dense (GenEO shift-invert band solves, FP64, "
-                                       "8 right-hand sides)",
-                   achieved=fl_l / (ms_l * 1e-3) / 1e12, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
-                   peak_source="nominal FP64 1.25 TFLOP/s (152 SMs x 2 FMA/clk x 2.07 GHz); "
-                               "torch DGEMM measured 1.10",
-                   ms_per_launch=ms_l, algorithmic_flops=fl_l, launches_per_solve=n_lanczos)
-        alu["frac"] = alu["achieved"] / FP64_PEAK_TFLOPS
-        alu["traffic"] = profiled_traffic("k_band_solve_dense", args)
-        cand.append((ms_l * n_lanczos, alu))
-    cand.sort(key=lambda t: -t[0])
-    roof = cand[0][1]
-    ms_sp, by_sp, _ = pkg.geneo_profile(s.ctx, 1, 50)
-    ms_pc, by_pc, _ = pkg.geneo_profile(s.ctx, 2, 20)
-    kernels = dict(spmv=dict(ms=ms_sp, gbs=by_sp / (ms_sp * 1e-3) / 1e9),
-                   precond_apply=dict(ms=ms_pc, gbs=by_pc / (ms_pc * 1e-3) / 1e9),
-                   other_roofline=[c[1] for c in cand[1:]])
+    roof, kernels = None, None
+    if not args.no_profile:
+        cand = rooflines(pkg, s, st, args, peak, peak_kind)
+        roof = dict(cand[0][1])
+        for k in ("k_band_solve_dense", "k_schwarz_cluster"):
+            if roof["kernel"].startswith(k):
+                roof["traffic"] = profiled_traffic(k, args)
+        roof.setdefault("traffic", None)
+        ms_pc, by_pc, _ = pkg.geneo_profile(s.ctx, 2, 10)
+        kernels = dict(precond_apply=dict(ms=ms_pc, gbs=by_pc / (ms_pc * 1e-3) / 1e9),
+                       other_rooflines=[c[1] for c in cand[1:]])
 
-    # accuracy against the oracle's stored summary (sampled displacements)
-    acc = None
-    gold = os.path.join(ROOT, "tests", "golden", f"{args.config}_oracle.json")
-    if os.path.exists(gold):
-        g = json.load(open(gold))
-        u = u_dev.cpu().numpy()
-        us = u[::g["sample_stride"]][:len(g["u_samples"])]
-        ref = np.asarray(g["u_samples"])
-        acc = dict(rel_err_samples=float(np.linalg.norm(us - ref) / np.linalg.norm(ref)),
-                   oracle_iterations=g["iterations"])
+    # the other precision on the same workload, at equal accuracy
+    other_leg = None
+    if rank == 0 and world == 1 and not args.no_other:
+        k = max(1, min(args.steps, args.other_steps))
+        ms_o, st_o = timed(pd, other, u_dev, k, 1)
+        other_leg = dict(precision="fp64" if mixed else "mixed", ms_per_solve=ms_o, steps=k,
+                         **leg_summary(st_o), oracle_error=oracle_error(u_dev.cpu().numpy(), g))
+        other_leg["speedup_of_mixed"] = (ms_o / value) if mixed else (value / ms_o)
 
-    mixed = None
-    if not args.no_mixed and args.precision == "fp64":
-        for _ in range(2):
-            stm = one_solve(pkg, s, pd, pkg.GENEO_MIXED_FP32, u_dev)
-        torch.cuda.synchronize(dev)
-        e0.record(stream)
-        for _ in range(args.steps):
-            stm = one_solve(pkg, s, pd, pkg.GENEO_MIXED_FP32, u_dev)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        mixed = dict(ms_per_solve=e0.elapsed_time(e1) / args.steps, iterations=stm["iterations"],
-                     rel_res_true=stm["rel_res_true"],
-                     phases_ms=dict(setup_eig_coarse=stm["ms_setup_eig"],
-                                    setup_factor=stm["ms_setup_factor"], solve=stm["ms_solve"]),
-                     schwarz_launch=dict(cluster=stm["schwarz_cluster"], rows=stm["schwarz_rows"],
-                                         staged=stm["schwarz_staged"]))
-        if acc is not None:
-            u = u_dev.cpu().numpy()
-            us = u[::g["sample_stride"]][:len(g["u_samples"])]
-            mixed["rel_err_samples"] = float(np.linalg.norm(us - ref) / np.linalg.norm(ref))
+    # the 64x32x24 laminate: GenEO in both precisions against one-level
+    # additive Schwarz and unpreconditioned CG
+    c2 = None
+    if rank == 0 and world == 1 and not args.no_c2 and args.config != "c2":
+        p2 = workloads.config("c2")
+        g2 = golden("c2")
+        pd2 = device_problem(p2, torch, dev)
+        n2 = 3 * (p2["nx"] + 1) * (p2["ny"] + 1) * (p2["nz"] + 1)
+        u2 = torch.empty(n2, dtype=torch.float64, device=dev)
+        c2 = dict(workload=workload_config(p2, "fp64")["workload"],
+                  partition=workload_config(p2, "fp64")["partition"])
+        k2 = max(1, min(args.steps, 3))
+        for key, pr, sw, co, mi in (("geneo_fp64", pkg.GENEO_FP64, pkg.GENEO_AS, 0, 5000),
+                                    ("geneo_mixed", pkg.GENEO_MIXED_FP32, pkg.GENEO_AS, 0, 5000),
+                                    ("one_level_as_fp64", pkg.GENEO_FP64, pkg.GENEO_AS,
+                                     pkg.GENEO_COARSE_NONE, 20000),
+                                    ("plain_cg", pkg.GENEO_FP64, pkg.GENEO_NO_PRECOND, 0, 20000)):
+            kk = k2 if key.startswith("geneo") else 1
+            ms2, st2 = timed(pd2, pr, u2, kk, 1, schwarz=sw, coarse=co, max_it=mi)
+            c2[key] = dict(ms_per_solve=ms2, steps=kk, converged=st2["rel_res_recursive"] <= TOL,
+                           **leg_summary(st2), oracle_error=oracle_error(u2.cpu().numpy(), g2))
+        del pd2, u2
 
     # serving: a seeded stream of uneven solve requests through the
     # continuous-batching server (burst, then Poisson at half its throughput)
@@ -483,42 +634,20 @@ def run_ours(args):
                                     setup_factor=std["ms_setup_factor"], solve=std["ms_solve"]))
         sd.close()
 
-    # the 1.2M-dof wrinkled laminate (128x64x48, 8x4x4 subdomains): time to
-    # 1e-8 with the FP32-factor preconditioner against the all-FP64 one, and the
-    # HBM fraction of its Schwarz local solves
-    c3 = None
-    if rank == 0 and world == 1 and not args.no_c3 and args.config != "c3":
-        p3 = workloads.config("c3")
-        pd3 = device_problem(p3, torch, dev)
-        s3 = pkg.GeneoSolver()
-        n3 = 3 * (p3["nx"] + 1) * (p3["ny"] + 1) * (p3["nz"] + 1)
-        u3 = torch.empty(n3, dtype=torch.float64, device=dev)
-        c3 = dict(workload=f"c3: 128x64x48 Q1 hex laminate with a fibre wrinkle, {n3} dofs, "
-                           "8x4x4 subdomains")
-        for key, pr in (("mixed", pkg.GENEO_MIXED_FP32), ("fp64", pkg.GENEO_FP64)):
-            for _ in range(2):                   # warm-up (and tuning), then one timed solve
-                e0.record(stream)
-                st3 = one_solve(pkg, s3, pd3, pr, u3)
-                e1.record(stream)
-                torch.cuda.synchronize(dev)
-            leg = dict(ms_per_solve=e0.elapsed_time(e1), iterations=st3["iterations"],
-                       rel_res_true=st3["rel_res_true"], n_coarse=st3["n_coarse"],
-                       phases_ms=dict(assemble=st3["ms_assemble"],
-                                      setup_eig_coarse=st3["ms_setup_eig"],
-                                      setup_factor=st3["ms_setup_factor"], solve=st3["ms_solve"]),
-                       schwarz_launch=dict(cluster=st3["schwarz_cluster"], rows=st3["schwarz_rows"],
-                                           staged=st3["schwarz_staged"]))
-            ms3, by3, _ = pkg.geneo_profile(s3.ctx, 0, 10)
-            leg["schwarz_apply"] = dict(ms=ms3, gbs=by3 / (ms3 * 1e-3) / 1e9,
-                                        frac_of_measured_hbm=by3 / (ms3 * 1e-3) / 1e9 / peak)
-            c3[key] = leg
-        s3.close()
-        del pd3, u3
-
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ms_cpu, sample, threads = oracle_sample(p, st["iterations"])
-        cpu = dict(value=ms_cpu, unit=UNIT, cores=threads, kind="oracle", sample=sample)
+        from oracle import decomp, fem
+        A, _ = fem.assemble_system(p)
+        ms_s, ms_cpu, sample = oracle_sample(p, A.tocsr(), decomp.partition(p), st["iterations"])
+        threads, how = blas_threads()
+        cpu = dict(value=ms_cpu, unit=UNIT, cores=os.cpu_count() or 1, kind="oracle",
+                   sample=sample, sample_ms=ms_s,
+                   estimate="extrapolated from the sample, not a timed full solve",
+                   cpu_model=cpu_model(), blas_threads=threads, blas_threads_set_by=how,
+                   sparse_lu_threads=1)
+        if g and "oracle_seconds" in g:
+            cpu["full_solve_recorded_s"] = g["oracle_seconds"].get("total")
+            cpu["full_solve_recorded_on"] = "the machine that wrote tests/golden (x86, 8 cores)"
 
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps,
@@ -527,16 +656,11 @@ def run_ours(args):
                     dtype="f64" if args.precision == "fp64" else "f64+f32",
                     data="synthetic", config=workload_config(p, args.precision),
                     roofline=roof, cpu_baseline=cpu, e2e=e2e, gpu_launches=int(launches),
-                    clocks=clk, iterations=st["iterations"], rel_res_true=st["rel_res_true"],
-                    n_coarse=st["n_coarse"], kappa_est=st["kappa_est"],
-                    phases_ms=dict(assemble=st["ms_assemble"], setup_eig_coarse=st["ms_setup_eig"],
-                                   setup_factor=st["ms_setup_factor"], solve=st["ms_solve"]),
-                    bytes_per_iter=st["bytes_per_iter"], kernels=kernels,
-                    schwarz_launch=dict(cluster=st["schwarz_cluster"], rows=st["schwarz_rows"],
-                                        staged=st["schwarz_staged"],
-                                        chosen_by="set-up autotuner"),
-                    accuracy_vs_oracle=acc, mixed_precision=mixed, serving=serving,
-                    darcy_spe10=darcy, c3_mixed_vs_fp64=c3, batched_uneven=batch)
+                    clocks=clk, **leg_summary(st), bytes_per_iter=st["bytes_per_iter"],
+                    oracle_error=acc, kernels=kernels,
+                    **{("fp64" if mixed else "mixed"): other_leg},
+                    c2=c2, serving=serving, darcy_spe10=darcy, batched_uneven=batch)
+        line["schwarz_launch"]["chosen_by"] = "set-up autotuner"
         print(json.dumps(line))
     s.close()
     if world > 1:

@@ -58,8 +58,11 @@ typedef enum { GENEO_FP64 = 0, GENEO_MIXED_FP32 = 1 } geneo_precision;
 /* One-level term weight D_j in  M^-1 = sum_j R_j^T D_j A_j^-1 R_j + Z A_H^-1 Z^T.
  * GENEO_AS: D_j = I, the symmetric operator of Sec. 3.1 (eqn:onelevelAS).
  * GENEO_AS_POU: D_j = X_j (partition of unity); not symmetric, so solve()
- *   then always uses flexible CG. */
-typedef enum { GENEO_AS = 0, GENEO_AS_POU = 1 } geneo_schwarz;
+ *   then always uses flexible CG.
+ * GENEO_NO_PRECOND: M = I, plain CG (Sec. 3.1 with no preconditioner; the
+ *   unpreconditioned baseline the preconditioners are compared with).  The
+ *   partition, modes, precision and coarse arguments are then ignored. */
+typedef enum { GENEO_AS = 0, GENEO_AS_POU = 1, GENEO_NO_PRECOND = 2 } geneo_schwarz;
 
 /* Coarse space kind. GENEO_COARSE_GENEO: GenEO eigenvectors (Sec. 3.2);
  * GENEO_COARSE_NONE: one-level additive Schwarz only (Sec. 3.1);
@@ -296,7 +299,12 @@ int geneo_debug_local_matrix(geneo_ctx *ctx, int sub, int kind, double *dense, i
  * eqn:onelevelAS: gather, forward and backward band sweeps, both factor
  * streams), 1 = the BSR SpMV, 2 = the whole preconditioner application,
  * 3 = one FP64 backward sweep of the GenEO eigensolver's band solves with 8
- * right-hand sides per subdomain (Sec. 3.3.2 shift-and-invert operator).
+ * right-hand sides per subdomain (Sec. 3.3.2 shift-and-invert operator),
+ * 4 = the band Cholesky factorisation of the shifted Neumann matrices
+ * S_j = A_Omega_j - sigma B_j (FP64, re-assembled first; Sec. 3.3.2),
+ * 5 = the band Cholesky factorisation of the subdomain matrices A_j in the
+ * set-up's precision (re-extracted first; Sec. 3.1 local solves).  Kinds 4
+ * and 5 rebuild the factors they time, with the same result.
  * Outputs (any may be NULL): mean ms per launch, bytes and flops per launch.
  * Needs geneo_setup; overwrites the solver's internal work vectors. */
 int geneo_profile(geneo_ctx *ctx, int what, int reps, double *ms_per_launch, double *bytes,

@@ -22,7 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgeneo.so")
 
 GENEO_FP64, GENEO_MIXED_FP32 = 0, 1
-GENEO_AS, GENEO_AS_POU = 0, 1
+GENEO_AS, GENEO_AS_POU, GENEO_NO_PRECOND = 0, 1, 2
 GENEO_COARSE_GENEO, GENEO_COARSE_NONE, GENEO_COARSE_ZEM = 0, 1, 2
 
 STATUS = {0: "GENEO_OK", 1: "GENEO_ERR_INVALID_ARG", 2: "GENEO_ERR_WORKSPACE_TOO_SMALL",

@@ -709,6 +709,22 @@ int build_plan(geneo_ctx *c, const geneo_partition *part, const geneo_modes *mod
 }
 
 // Lay out the phase-1 workspace (a pass with A.base == nullptr only measures).
+// The Krylov vectors and scalars of geneo_solve.
+void take_cg_vectors(Arena &A, geneo_ctx *c) {
+  const int n = c->ndof;
+  c->x = A.take<double>(n);
+  c->r = A.take<double>(n);
+  c->p = A.take<double>(n);
+  c->q = A.take<double>(n);
+  c->z = A.take<double>(n);
+  c->tmp = A.take<double>(n);
+  c->part = A.take<double>(8 * kRedBlocks);   // the fused SpMV-dot kernel runs 4 x kRedBlocks blocks
+  c->alphas = A.take<double>(kHistCap);
+  c->betas = A.take<double>(kHistCap);
+  c->scal = A.take<double>(4);
+  c->cg = A.take<CGScalars>(1);
+}
+
 void plan_setup(Arena &A, geneo_ctx *c, const SetupPlan &P) {
   Precond &pc = c->pc;
   const int nsub = P.nsub, p = kLanczosBlock;
@@ -790,18 +806,7 @@ void plan_setup(Arena &A, geneo_ctx *c, const SetupPlan &P) {
     pc.nH_cap = 0;
     pc.z_elems = 0;
   }
-  const int n = c->ndof;
-  c->x = A.take<double>(n);
-  c->r = A.take<double>(n);
-  c->p = A.take<double>(n);
-  c->q = A.take<double>(n);
-  c->z = A.take<double>(n);
-  c->tmp = A.take<double>(n);
-  c->part = A.take<double>(8 * kRedBlocks);   // the fused SpMV-dot kernel runs 4 x kRedBlocks blocks
-  c->alphas = A.take<double>(kHistCap);
-  c->betas = A.take<double>(kHistCap);
-  c->scal = A.take<double>(4);
-  c->cg = A.take<CGScalars>(1);
+  take_cg_vectors(A, c);
 }
 
 double default_threshold(geneo_ctx *c, const SubDesc &S, int O) {
@@ -839,6 +844,13 @@ static int schwarz_local_solves(geneo_ctx *c, const double *r, const CGScalars *
 static int precond_apply(geneo_ctx *c, const double *r, double *z, const CGScalars *cg,
                          cudaStream_t s) {
   Precond &pc = c->pc;
+  if (pc.schwarz == GENEO_NO_PRECOND) {          // M = I: plain CG
+    if (cg)
+      launch_copy_if_running(c->ndof, r, z, cg, s);
+    else
+      GENEO_CUDA_TRY(cudaMemcpyAsync(z, r, sizeof(double) * c->ndof, cudaMemcpyDeviceToDevice, s));
+    return GENEO_OK;
+  }
   const int nnx = c->nx + 1, nny = c->ny + 1;
   const bool coarse = pc.nH > 0;
   if (coarse)
@@ -1403,13 +1415,53 @@ static int tune_schwarz(geneo_ctx *c, const SetupPlan &P, cudaStream_t s) {
   return GENEO_OK;
 }
 
+// Plain CG (M = I, the unpreconditioned comparison): only the Krylov vectors.
+static int setup_no_precond(geneo_ctx *c) {
+  release_setup(c);
+  Precond &pc = c->pc;
+  pc.prec = GENEO_FP64;
+  pc.schwarz = GENEO_NO_PRECOND;
+  pc.coarse = GENEO_COARSE_NONE;
+  pc.nH = 0;
+  pc.nsub = 0;
+  pc.eig_done = false;
+  pc.m.clear();
+  pc.lambdas.clear();
+  pc.ms_eig = pc.ms_factor = pc.ms_coarse = 0.f;
+  pc.eig_max_res = 0.0;
+  pc.eig_cycles = pc.lanczos_steps = 0;
+  pc.cluster = pc.rows = pc.staged = 0;
+  Arena M;
+  take_cg_vectors(M, c);
+  const size_t need = M.off + 256;
+  if (c->ws1_bound) {
+    if (c->ws1_bound_bytes < need) return fail(GENEO_ERR_WORKSPACE_TOO_SMALL, "setup workspace too small");
+    c->ws1 = c->ws1_bound;
+    c->ws1_bytes = c->ws1_bound_bytes;
+    c->ws1_owned = false;
+  } else {
+    GENEO_CUDA_TRY(cudaMalloc(&c->ws1, need));
+    c->ws1_bytes = need;
+    c->ws1_owned = true;
+  }
+  Arena B;
+  B.base = (char *)c->ws1;
+  B.cap = c->ws1_bytes;
+  take_cg_vectors(B, c);
+  pc.bytes_per_apply = 16.0 * c->ndof;
+  c->setup_done = true;
+  return GENEO_OK;
+}
+
 extern "C" {
 
 int geneo_setup(geneo_ctx *c, const geneo_partition *part, const geneo_modes *modes,
                 geneo_precision prec, geneo_schwarz schwarz, geneo_coarse coarse) {
   if (!c || !c->assembled) return fail(GENEO_ERR_STATE, "not assembled");
   if (prec != GENEO_FP64 && prec != GENEO_MIXED_FP32) return fail(GENEO_ERR_INVALID_ARG, "bad precision");
-  if (schwarz != GENEO_AS && schwarz != GENEO_AS_POU) return fail(GENEO_ERR_INVALID_ARG, "bad schwarz");
+  if (schwarz != GENEO_AS && schwarz != GENEO_AS_POU && schwarz != GENEO_NO_PRECOND)
+    return fail(GENEO_ERR_INVALID_ARG, "bad schwarz");
+  if (schwarz == GENEO_NO_PRECOND) return setup_no_precond(c);
   if (coarse != GENEO_COARSE_GENEO && coarse != GENEO_COARSE_NONE && coarse != GENEO_COARSE_ZEM)
     return fail(GENEO_ERR_INVALID_ARG, "bad coarse");
   cudaStream_t s = c->stream;
@@ -1466,6 +1518,8 @@ int geneo_setup(geneo_ctx *c, const geneo_partition *part, const geneo_modes *mo
   launch_gather_map(c->nx, c->ny, c->nz, pc.part.px, pc.part.py, pc.d_cand, pc.cand_off,
                     pc.d_subs, pc.gmap, pc.gcnt, s);
   pc.subs = P.subs;
+  pc.max_nodes_int = P.max_nodes_int;
+  pc.max_nodes_neu = P.max_nodes_neu;
   pc.m.assign(P.nsub, 0);
   pc.lambdas.assign((size_t)P.nsub * pc.mcap, INFINITY);
   pc.eig_max_res = 0.0;
@@ -1936,8 +1990,10 @@ extern "C" int geneo_profile(geneo_ctx *c, int what, int reps, double *ms_per_la
                              double *bytes, double *flops) {
   if (!c || !c->setup_done) return fail(GENEO_ERR_STATE, "no preconditioner set up");
   Precond &pc = c->pc;
-  if (reps < 1 || what < 0 || what > 3) return fail(GENEO_ERR_INVALID_ARG, "bad profile request");
-  if (what == 3 && !pc.neuL) return fail(GENEO_ERR_STATE, "no GenEO eigensolver data");
+  if (reps < 1 || what < 0 || what > 5) return fail(GENEO_ERR_INVALID_ARG, "bad profile request");
+  if ((what == 3 || what == 4) && !pc.neuL) return fail(GENEO_ERR_STATE, "no GenEO eigensolver data");
+  if (what != 1 && pc.schwarz == GENEO_NO_PRECOND)
+    return fail(GENEO_ERR_STATE, "plain CG has no preconditioner to profile");
   cudaStream_t s = c->stream;
   const bool f32 = pc.prec == GENEO_MIXED_FP32;
   const double esz = f32 ? 4.0 : 8.0;
@@ -1967,6 +2023,22 @@ extern "C" int geneo_profile(geneo_ctx *c, int what, int reps, double *ms_per_la
       fl += 2.0 * kLanczosBlock * band;
     }
   }
+  if (what == 4 || what == 5) {
+    // band Cholesky: column k updates the trailing triangle of its band,
+    // min(hb, n-1-k)^2 / 2 multiply-adds; bytes: the band written once and
+    // read once (the factor stays resident in the tiles)
+    by = fl = 0.0;
+    for (const SubDesc &S : pc.subs) {
+      const bool neu = what == 4;
+      const double n = neu ? S.n_neu : S.n_int;
+      const double hb = neu ? S.nbox.half_band_dofs(c->nc) : S.ibox.half_band_dofs(c->nc);
+      const double band = n * (hb + 1) - hb * (hb + 1) / 2;
+      const double e = neu ? 8.0 : esz;
+      by += 2.0 * band * e;
+      const double full = std::max(0.0, n - hb);          // columns with a full band below
+      fl += full * hb * hb + (hb * (hb - 1) * (2 * hb - 1)) / 6.0;
+    }
+  }
   // a deterministic, non-trivial residual to work on
   BSR A{c->nnode, c->row_ptr, c->col, c->val, c->nc};
   launch_spmv(A, c->b, c->r, s);
@@ -1986,6 +2058,35 @@ extern "C" int geneo_profile(geneo_ctx *c, int what, int reps, double *ms_per_la
         st = launch_band_solve_dense(pc.d_lay_neu, pc.nsub, npad, pc.neuL, pc.neuU, pc.V,
                                      (long long)npad * ldv, ldv, pc.T1, (long long)npad * p, p, p,
                                      2, s);
+      } else if (what == 4) {
+        // re-assemble S_j = A_j - sigma B_j and factor it again (same result)
+        if (!(st = launch_band_clear<double>(pc.d_lay_neu, pc.nsub, pc.neuL, pc.fac_neu_elems, s))) {
+          launch_neumann_assemble(pc.d_subs, pc.d_lay_neu, pc.nsub, pc.max_nodes_neu, c->nx, c->ny,
+                                  c->nz, c->X, c->Y, c->Z, c->Cel, c->perm, pc.d_ecnt, pc.ecnt_off,
+                                  c->mask, pc.Xneu, pc.modes.shift, pc.neuL, pc.Bloc, s);
+          st = launch_band_cholesky<double>(pc.d_lay_neu, pc.nsub, pc.nt_neu_max, pc.w_neu_max,
+                                            pc.neuL, pc.neuU, c->status, s, c->side_stream);
+        }
+      } else if (what == 5) {
+        // re-extract A_j and factor it again in the set-up's precision
+        const int nnx = c->nx + 1, nny = c->ny + 1, nnz = c->nz + 1;
+        if (f32) {
+          float *L = (float *)pc.facL, *U = (float *)pc.facU;
+          if (!(st = launch_band_clear<float>(pc.d_lay_int, pc.nsub, L, pc.fac_int_elems, s)) &&
+              !(st = launch_extract_interior<float>(pc.d_subs, pc.d_lay_int, pc.nsub,
+                                                    pc.max_nodes_int, nnx, nny, nnz, c->row_ptr,
+                                                    c->val, L, s)))
+            st = launch_band_cholesky<float>(pc.d_lay_int, pc.nsub, pc.nt_int_max, pc.w_int_max, L,
+                                             U, c->status, s, c->side_stream);
+        } else {
+          double *L = (double *)pc.facL, *U = (double *)pc.facU;
+          if (!(st = launch_band_clear<double>(pc.d_lay_int, pc.nsub, L, pc.fac_int_elems, s)) &&
+              !(st = launch_extract_interior<double>(pc.d_subs, pc.d_lay_int, pc.nsub,
+                                                     pc.max_nodes_int, nnx, nny, nnz, c->row_ptr,
+                                                     c->val, L, s)))
+            st = launch_band_cholesky<double>(pc.d_lay_int, pc.nsub, pc.nt_int_max, pc.w_int_max,
+                                              L, U, c->status, s, c->side_stream);
+        }
       } else {
         st = precond_apply(c, c->r, c->z, nullptr, s);
       }

@@ -83,6 +83,7 @@ struct Precond {
   double *wH = nullptr, *yH = nullptr;
   double *zy = nullptr;           // coarse correction Z_j y_j per interior dof [sum n_int]
   int max_nint = 0;               // largest interior dof count of a subdomain
+  int max_nodes_int = 0, max_nodes_neu = 0;   // largest interior / Neumann node count
   std::vector<int> m;
   std::vector<double> lambdas;    // [nsub][mcap]
   double eig_max_res = 0.0;
