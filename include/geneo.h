@@ -72,6 +72,32 @@ typedef enum { GENEO_AS = 0, GENEO_AS_POU = 1, GENEO_NO_PRECOND = 2 } geneo_schw
  * of unity; the mode options other than the shift are ignored. */
 typedef enum { GENEO_COARSE_GENEO = 0, GENEO_COARSE_NONE = 1, GENEO_COARSE_ZEM = 2 } geneo_coarse;
 
+/* Partition of unity X_j (Def. Partition of Unity, Sec. 3.2; Sec. 3.3.1),
+ * used in B_j = X_j A_{Omega_j^o} X_j, in the coarse basis R_j^T X_j p and in
+ * the one-level weight D_j = X_j of GENEO_AS_POU.
+ * GENEO_POU_MULTIPLICITY: 1 / (number of subdomains whose V_{h,0} holds the
+ *   node), Sec. 3.3.1 (the default).
+ * GENEO_POU_SARKIS: d_j / sum_k d_k, d_j the node's distance to the
+ *   artificial boundary of Omega_j counted in element layers (the least
+ *   distance to a face of Omega_j's box that lies inside the domain; 1 when
+ *   there is none), the sum over the subdomains whose V_{h,0} holds the
+ *   node: Sarkis's smoother partition of unity, Sec. 3.2.  Equal to the
+ *   multiplicity one at overlap 1.
+ * Both are zero on global Dirichlet dofs and on Omega_j's artificial
+ * boundary. */
+typedef enum { GENEO_POU_MULTIPLICITY = 0, GENEO_POU_SARKIS = 1 } geneo_pou;
+
+/* Solver of the coarse problem A_H y = w (Sec. 3.3.3).
+ * GENEO_COARSE_DIRECT: Cholesky factor of A_H at set-up, its explicit inverse
+ *   applied as a matrix-vector product (the default).
+ * GENEO_COARSE_ITERATIVE: the inexact solve the paper uses for very large
+ *   coarse spaces: CG on A_H from y = 0, preconditioned by the inverses of
+ *   A_H's diagonal blocks (one block per subdomain's modes), stopped at
+ *   ||w - A_H y|| <= tol ||w|| or after max_it steps; the outer Krylov method
+ *   is then flexible CG.  The paper preconditions this inner CG with an
+ *   algebraic multigrid (BoomerAMG); block Jacobi stands in for it here. */
+typedef enum { GENEO_COARSE_DIRECT = 0, GENEO_COARSE_ITERATIVE = 1 } geneo_coarse_solver;
+
 typedef struct {
   int nx, ny, nz;                 /* elements per axis, each >= 1 */
   const double *x, *y, *z;        /* node coordinates, lengths nx+1, ny+1, nz+1 */
@@ -129,6 +155,8 @@ typedef struct {
   int schwarz_cluster;            /* CTAs per subdomain chosen for the local solves */
   int schwarz_rows;               /* tile rows per cluster barrier chosen for them */
   int schwarz_staged;             /* 1 if their tiles are staged in shared memory by bulk copies */
+  int coarse_inner_iterations;    /* inner PCG steps of the iterative coarse solve, summed over
+                                     the solve's preconditioner applications (0 if direct) */
 } geneo_stats;
 
 /* Create a context whose work runs on `cuda_stream` (a cudaStream_t; NULL =
@@ -264,6 +292,19 @@ int geneo_spmv(geneo_ctx *ctx, const double *x, double *y);
 int geneo_setup(geneo_ctx *ctx, const geneo_partition *part,
                 const geneo_modes *modes, geneo_precision prec,
                 geneo_schwarz schwarz, geneo_coarse coarse);
+
+/* Partition of unity of the next geneo_setup calls on this context
+ * (geneo_pou; the default is GENEO_POU_MULTIPLICITY).  Host-only; returns
+ * GENEO_ERR_INVALID_ARG for an unknown kind. */
+int geneo_set_partition_of_unity(geneo_ctx *ctx, int kind);
+
+/* Coarse solver of the next geneo_setup calls on this context
+ * (geneo_coarse_solver; tol and max_it are read for GENEO_COARSE_ITERATIVE
+ * only: 0 < tol < 1, max_it >= 1).  Host-only; GENEO_ERR_INVALID_ARG
+ * otherwise.  The iterative solve runs as one cooperative launch per
+ * application: its blocks wait for one another at a grid barrier (bounded:
+ * after about a second the solve fails with GENEO_ERR_TIMEOUT). */
+int geneo_set_coarse_solver(geneo_ctx *ctx, int kind, double tol, int max_it);
 
 /* z = M^-1 r with the preconditioner of the last geneo_setup. */
 int geneo_apply_preconditioner(geneo_ctx *ctx, const double *r, double *z);

@@ -23,6 +23,8 @@ LIB_PATH = os.path.join(_HERE, "libgeneo.so")
 
 GENEO_FP64, GENEO_MIXED_FP32 = 0, 1
 GENEO_AS, GENEO_AS_POU, GENEO_NO_PRECOND = 0, 1, 2
+GENEO_POU_MULTIPLICITY, GENEO_POU_SARKIS = 0, 1
+GENEO_COARSE_DIRECT, GENEO_COARSE_ITERATIVE = 0, 1
 GENEO_COARSE_GENEO, GENEO_COARSE_NONE, GENEO_COARSE_ZEM = 0, 1, 2
 
 STATUS = {0: "GENEO_OK", 1: "GENEO_ERR_INVALID_ARG", 2: "GENEO_ERR_WORKSPACE_TOO_SMALL",
@@ -65,7 +67,7 @@ class geneo_stats(C.Structure):
                 ("flexible", C.c_int), ("eig_cycles", C.c_int),
                 ("lanczos_steps", C.c_int),
                 ("schwarz_cluster", C.c_int), ("schwarz_rows", C.c_int),
-                ("schwarz_staged", C.c_int)]
+                ("schwarz_staged", C.c_int), ("coarse_inner_iterations", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -114,6 +116,8 @@ _SIGS = {
     "geneo_solve": [_P, C.c_double, C.c_int, _P, C.POINTER(geneo_stats)],
     "geneo_debug_local_matrix": [_P, C.c_int, C.c_int, _P, _P],
     "geneo_spmv_dot_noalloc": [C.c_int, _P, _P, _P, _P, _P, _P, _P],
+    "geneo_set_partition_of_unity": [_P, C.c_int],
+    "geneo_set_coarse_solver": [_P, C.c_int, C.c_double, C.c_int],
     "geneo_profile": [_P, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                       C.POINTER(C.c_double)],
 }
@@ -316,6 +320,14 @@ def geneo_debug_local_matrix(ctx, sub, kind, dense=None, gdof=None):
     _check(load().geneo_debug_local_matrix(ctx, sub, kind, _ptr(dense), _ptr(gdof)))
 
 
+def geneo_set_partition_of_unity(ctx, kind):
+    _check(load().geneo_set_partition_of_unity(ctx, int(kind)))
+
+
+def geneo_set_coarse_solver(ctx, kind, tol=1e-2, max_it=200):
+    _check(load().geneo_set_coarse_solver(ctx, int(kind), float(tol), int(max_it)))
+
+
 def geneo_spmv_dot_noalloc(n_nodes, row_ptr, col, val, x, y, xy, stream=None):
     """y = A x and xy[0] = x . y on device tensors; allocates nothing."""
     _check(load().geneo_spmv_dot_noalloc(int(n_nodes), _ptr(row_ptr), _ptr(col), _ptr(val),
@@ -477,7 +489,18 @@ class GeneoSolver:
                            float(m["shift"]))
 
     def setup(self, p, prec=GENEO_FP64, schwarz=GENEO_AS, coarse=GENEO_COARSE_GENEO):
+        """p["pou"] = "sarkis" selects Sarkis's partition of unity."""
         part, modes = self.partition_of(p), self.modes_of(p)
+        pou = p.get("pou", "standard")
+        if pou not in ("standard", "sarkis"):
+            raise ValueError(f"partition of unity {pou!r}")
+        geneo_set_partition_of_unity(self.ctx, GENEO_POU_SARKIS if pou == "sarkis"
+                                     else GENEO_POU_MULTIPLICITY)
+        cs = p.get("coarse_solver", "direct")
+        if cs not in ("direct", "cg"):
+            raise ValueError(f"coarse solver {cs!r}")
+        geneo_set_coarse_solver(self.ctx, GENEO_COARSE_ITERATIVE if cs == "cg" else GENEO_COARSE_DIRECT,
+                                float(p.get("coarse_tol", 1e-2)), int(p.get("coarse_maxit", 200)))
         self._bind(1, geneo_setup_workspace_bytes(self.ctx, part, modes, prec))
         geneo_setup(self.ctx, part, modes, prec, schwarz, coarse)
         self.part, self.modes, self.prec = part, modes, prec

@@ -82,12 +82,14 @@ void launch_gather_map(int nx, int ny, int nz, int px, int py, const int *cand,
 
 // z = sum_j R_j^T (D_j x_j + (Z y)_j): deterministic gather over subdomains
 // through the gather map; zy holds Z_j y_j per interior dof (from
-// launch_coarse_apply) or is null.
+// launch_coarse_apply) or is null.  With pou, D_j = X_j: the weights wloc
+// (laid out like the local solutions) when given, else 1 / multiplicity.
 template <typename T>
 void launch_schwarz_gather(int nx, int ny, int nz, int px, int py, const int *cand,
                            const int cand_off[3], const SubDesc *d_subs, const int *gmap,
                            const uint8_t *gcnt, const T *xloc, const double *zy, int pou,
-                           const uint8_t *mask, double *z, const CGScalars *cg, cudaStream_t s);
+                           const double *wloc, const uint8_t *mask, double *z,
+                           const CGScalars *cg, cudaStream_t s);
 
 // Coarse restriction w = Z^T r (partials over blocks of kZRows rows),
 // reduction, y = A_H^-1 w and the prolongation zy_j = Z_j y_j per interior
@@ -98,5 +100,21 @@ void launch_coarse_apply(const SubDesc *d_subs, int nsub, int max_nint, int nnx,
                          const double *Zp, const double *r, double *wpart, double *wH,
                          double *yH, double *zy, const double *AHinv, int nH, int mcap,
                          const CGScalars *cg, cudaStream_t s);
+
+// Inexact coarse solve (Sec. 3.3.3): BJ[j] = inverse of subdomain j's
+// diagonal block of A_H (m_j x m_j, stride mcap), then per application the
+// restriction, block-Jacobi PCG on A_H y = w to ||w - A_H y|| <= tol ||w|| or
+// maxit steps in one cooperative launch (work: 4 nH + 4 * coarse_pcg_blocks()
+// doubles; bar: two barrier words, zero before the first launch), and the
+// prolongation.  inner_its (or null) accumulates the inner steps taken.
+void launch_coarse_bj_inverse(const SubDesc *d_subs, int nsub, int nH, const double *AH,
+                              double *BJ, int mcap, cudaStream_t s);
+int coarse_pcg_blocks();
+int launch_coarse_apply_iterative(const SubDesc *d_subs, int nsub, int max_nint, int nnx,
+                                  int nny, const double *Zp, const double *r, double *wpart,
+                                  double *wH, double *yH, double *zy, const double *AH,
+                                  const double *BJ, int nH, int mcap, double *work,
+                                  unsigned int *bar, double tol, int maxit, const CGScalars *cg,
+                                  DevStatus *st, int *inner_its, cudaStream_t s);
 
 }  // namespace geneo

@@ -743,6 +743,7 @@ void plan_setup(Arena &A, geneo_ctx *c, const SetupPlan &P) {
   pc.facL = A.take<char>(pc.fac_int_elems * esz);
   pc.facU = A.take<char>(pc.fac_int_elems * esz);
   pc.xloc = A.take<char>(pc.xloc_elems * esz);
+  pc.wloc = pc.pou == GENEO_POU_SARKIS ? A.take<double>(pc.xloc_elems) : nullptr;
   int cap = pc.modes.fixed_modes > 0 ? pc.modes.fixed_modes : pc.modes.max_modes;
   if (pc.coarse == GENEO_COARSE_NONE) cap = 0;
   if (pc.coarse == GENEO_COARSE_ZEM) cap = 6;     // the rigid displacements
@@ -797,7 +798,14 @@ void plan_setup(Arena &A, geneo_ctx *c, const SetupPlan &P) {
     pc.wH = A.take<double>(pc.nH_cap);
     pc.yH = A.take<double>(pc.nH_cap);
     pc.zy = A.take<double>(pc.xloc_elems);
+    pc.BJ = A.take<double>((size_t)nsub * pc.mcap * pc.mcap);
+    pc.cwork = A.take<double>(4 * (size_t)pc.nH_cap + 4 * 1024);
+    pc.cbar = A.take<unsigned int>(2);
+    pc.c_inner = A.take<int>(1);
   } else {
+    pc.BJ = pc.cwork = nullptr;
+    pc.cbar = nullptr;
+    pc.c_inner = nullptr;
     pc.neuL = pc.neuU = pc.Bloc = pc.Xneu = pc.V = pc.Vt = pc.W = pc.T1 = pc.Hm = pc.Hpart = nullptr;
     pc.Hs = pc.G = pc.Racc = nullptr;
     pc.Rblk = pc.Evec = pc.Eval = pc.Eres = pc.P = pc.Zp = pc.Yp = nullptr;
@@ -853,22 +861,31 @@ static int precond_apply(geneo_ctx *c, const double *r, double *z, const CGScala
   }
   const int nnx = c->nx + 1, nny = c->ny + 1;
   const bool coarse = pc.nH > 0;
-  if (coarse)
+  int st;
+  if (coarse && pc.csolver == GENEO_COARSE_ITERATIVE) {
+    if ((st = launch_coarse_apply_iterative(pc.d_subs, pc.nsub, pc.max_nint, nnx, nny, pc.Zp, r,
+                                            pc.wpart, pc.wH, pc.yH, pc.zy, pc.AH, pc.BJ, pc.nH,
+                                            pc.mcap, pc.cwork, pc.cbar, pc.ctol, pc.cmaxit, cg,
+                                            c->status, pc.c_inner, s)))
+      return st;
+  } else if (coarse) {
     launch_coarse_apply(pc.d_subs, pc.nsub, pc.max_nint, nnx, nny, pc.Zp, r, pc.wpart, pc.wH,
                         pc.yH, pc.zy, pc.AHinv, pc.nH, pc.mcap, cg, s);
-  int st;
+  }
   const int pou = pc.schwarz == GENEO_AS_POU;
   if ((st = schwarz_local_solves(c, r, cg, pc.cluster, pc.rows, pc.staged, s))) return st;
   if (pc.prec == GENEO_MIXED_FP32) {
     launch_schwarz_gather<float>(c->nx, c->ny, c->nz, pc.part.px, pc.part.py, pc.d_cand,
                                  pc.cand_off, pc.d_subs, pc.gmap, pc.gcnt,
-                                 (const float *)pc.xloc, coarse ? pc.zy : nullptr, pou, c->mask,
-                                 z, cg, s);
+                                 (const float *)pc.xloc, coarse ? pc.zy : nullptr, pou,
+                                 pc.pou == GENEO_POU_SARKIS ? pc.wloc : nullptr, c->mask, z, cg,
+                                 s);
   } else {
     launch_schwarz_gather<double>(c->nx, c->ny, c->nz, pc.part.px, pc.part.py, pc.d_cand,
                                   pc.cand_off, pc.d_subs, pc.gmap, pc.gcnt,
                                   (const double *)pc.xloc, coarse ? pc.zy : nullptr, pou,
-                                  c->mask, z, cg, s);
+                                  pc.pou == GENEO_POU_SARKIS ? pc.wloc : nullptr, c->mask, z,
+                                  cg, s);
   }
   GENEO_CUDA_TRY(cudaGetLastError());
   return GENEO_OK;
@@ -887,7 +904,7 @@ static int setup_coarse_zem(geneo_ctx *c, SetupPlan &P, cudaStream_t s) {
   const int nnx = c->nx + 1, nny = c->ny + 1;
   const long long sP = (long long)npad * mcap;
   launch_pou_neumann(pc.d_subs, nsub, P.max_nodes_neu, pc.d_cand, pc.cand_off, c->mask, nnx, nny,
-                     pc.Xneu, s);
+                     c->nz + 1, pc.part.px, pc.part.py, pc.pou, pc.Xneu, s);
   launch_rigid_modes(pc.d_subs, nsub, npad, c->X, c->Y, c->Z, pc.P, mcap, sP, s);
   launch_tsdots(pc.d_subs, nsub, npad, pc.P, mcap, sP, mcap, pc.P, mcap, sP, mcap, pc.Hpart,
                 kDotChunks, pc.G, (long long)mcap * mcap, s);
@@ -935,7 +952,7 @@ static int setup_coarse(geneo_ctx *c, SetupPlan &P, cudaStream_t s) {
   int st;
   // PoU, S = A - sigma B into band tiles, B into a local BSR
   launch_pou_neumann(pc.d_subs, nsub, P.max_nodes_neu, pc.d_cand, pc.cand_off, c->mask, nnx, nny,
-                     pc.Xneu, s);
+                     c->nz + 1, pc.part.px, pc.part.py, pc.pou, pc.Xneu, s);
   if ((st = launch_band_clear<double>(pc.d_lay_neu, nsub, pc.neuL, pc.fac_neu_elems, s))) return st;
   launch_neumann_assemble(pc.d_subs, pc.d_lay_neu, nsub, P.max_nodes_neu, c->nx, c->ny, c->nz,
                           c->X, c->Y, c->Z, c->Cel, c->perm, pc.d_ecnt, pc.ecnt_off, c->mask,
@@ -1185,6 +1202,16 @@ static int build_coarse_operator(geneo_ctx *c, SetupPlan &P, const std::vector<l
   GENEO_CUDA_TRY(cudaMemsetAsync(pc.AH, 0, (size_t)nH * nH * sizeof(double), s));
   launch_coarse_blocks(pc.d_subs, pc.d_pairs, (int)pairs.size(), pc.Zp, pc.Yp, pc.d_yoff, pc.AH, nH, s);
   launch_symmetrize(pc.AH, nH, s);
+  if (pc.csolver == GENEO_COARSE_ITERATIVE) {
+    // inexact coarse solve: block-Jacobi inverses, no factor of A_H
+    if (4 * 1024 < 4 * coarse_pcg_blocks())
+      return fail(GENEO_ERR_INVALID_ARG, "too many blocks for the coarse PCG partials");
+    launch_coarse_bj_inverse(pc.d_subs, nsub, nH, pc.AH, pc.BJ, mcap, s);
+    GENEO_CUDA_TRY(cudaMemsetAsync(pc.cbar, 0, 2 * sizeof(unsigned int), s));
+    GENEO_CUDA_TRY(cudaMemsetAsync(pc.c_inner, 0, sizeof(int), s));
+    GENEO_CUDA_TRY(cudaGetLastError());
+    return GENEO_OK;
+  }
   // dense Cholesky of A_H (a band system of full width) and its inverse
   BandLayout LH;
   LH.n = nH;
@@ -1214,6 +1241,7 @@ int geneo_setup_workspace_bytes(geneo_ctx *c, const geneo_partition *part,
   Precond saved = c->pc;
   SetupPlan P;
   c->pc.prec = prec;
+  c->pc.pou = c->pou_kind;
   c->pc.coarse = GENEO_COARSE_GENEO;
   int st = build_plan(c, part, modes, P);
   if (st) {
@@ -1252,6 +1280,7 @@ int geneo_estimate_workspace_bytes(const geneo_mesh *mesh, int unknowns_per_node
   tmp.nc = unknowns_per_node;
   tmp.ndof = tmp.nc * tmp.nnode;
   tmp.pc.prec = prec;
+  tmp.pc.pou = GENEO_POU_SARKIS;          // the larger of the two layouts
   SetupPlan P;
   if ((st = build_plan(&tmp, part, modes, P))) return st;
   size_t most = 0;
@@ -1415,6 +1444,28 @@ static int tune_schwarz(geneo_ctx *c, const SetupPlan &P, cudaStream_t s) {
   return GENEO_OK;
 }
 
+extern "C" int geneo_set_partition_of_unity(geneo_ctx *c, int kind) {
+  if (!c) return fail(GENEO_ERR_INVALID_ARG, "null context");
+  if (kind != GENEO_POU_MULTIPLICITY && kind != GENEO_POU_SARKIS)
+    return fail(GENEO_ERR_INVALID_ARG, "unknown partition of unity");
+  c->pou_kind = kind;
+  return GENEO_OK;
+}
+
+extern "C" int geneo_set_coarse_solver(geneo_ctx *c, int kind, double tol, int max_it) {
+  if (!c) return fail(GENEO_ERR_INVALID_ARG, "null context");
+  if (kind != GENEO_COARSE_DIRECT && kind != GENEO_COARSE_ITERATIVE)
+    return fail(GENEO_ERR_INVALID_ARG, "unknown coarse solver");
+  if (kind == GENEO_COARSE_ITERATIVE && (!(tol > 0.0 && tol < 1.0) || max_it < 1))
+    return fail(GENEO_ERR_INVALID_ARG, "iterative coarse solve needs 0 < tol < 1 and max_it >= 1");
+  c->csolver = kind;
+  if (kind == GENEO_COARSE_ITERATIVE) {
+    c->ctol = tol;
+    c->cmaxit = max_it;
+  }
+  return GENEO_OK;
+}
+
 // Plain CG (M = I, the unpreconditioned comparison): only the Krylov vectors.
 static int setup_no_precond(geneo_ctx *c) {
   release_setup(c);
@@ -1470,6 +1521,10 @@ int geneo_setup(geneo_ctx *c, const geneo_partition *part, const geneo_modes *mo
   pc.prec = prec;
   pc.schwarz = schwarz;
   pc.coarse = coarse;
+  pc.pou = c->pou_kind;
+  pc.csolver = c->csolver;
+  pc.ctol = c->ctol;
+  pc.cmaxit = c->cmaxit;
   pc.nH = 0;
   pc.eig_done = false;
   SetupPlan P;
@@ -1517,6 +1572,10 @@ int geneo_setup(geneo_ctx *c, const geneo_partition *part, const geneo_modes *mo
   GENEO_CUDA_TRY(cudaMemcpyAsync(pc.d_ecnt, P.ecnt.data(), P.ecnt.size() * sizeof(int), cudaMemcpyHostToDevice, s));
   launch_gather_map(c->nx, c->ny, c->nz, pc.part.px, pc.part.py, pc.d_cand, pc.cand_off,
                     pc.d_subs, pc.gmap, pc.gcnt, s);
+  if (pc.pou == GENEO_POU_SARKIS)
+    launch_pou_interior(pc.d_subs, P.nsub, P.max_nodes_int, pc.d_cand, pc.cand_off, c->mask,
+                        c->nx + 1, c->ny + 1, c->nz + 1, pc.part.px, pc.part.py, pc.pou, pc.wloc,
+                        s);
   pc.subs = P.subs;
   pc.max_nodes_int = P.max_nodes_int;
   pc.max_nodes_neu = P.max_nodes_neu;
@@ -1779,7 +1838,9 @@ extern "C" int geneo_solve(geneo_ctx *c, double tol, int max_it, double *u, gene
   cudaStream_t s = c->stream;
   const int n = c->ndof;
   const Precond &pc = c->pc;
-  const bool flexible = pc.prec == GENEO_MIXED_FP32 || pc.schwarz == GENEO_AS_POU;
+  const bool flexible = pc.prec == GENEO_MIXED_FP32 || pc.schwarz == GENEO_AS_POU ||
+                        (pc.nH > 0 && pc.csolver == GENEO_COARSE_ITERATIVE);
+  if (pc.c_inner) GENEO_CUDA_TRY(cudaMemsetAsync(pc.c_inner, 0, sizeof(int), s));
   CGScalars h{};
   h.tol2 = tol * tol;
   h.maxit = std::min(max_it, kHistCap);
@@ -1864,6 +1925,10 @@ extern "C" int geneo_solve(geneo_ctx *c, double tol, int max_it, double *u, gene
   out.schwarz_cluster = pc.cluster;
   out.schwarz_rows = pc.rows;
   out.schwarz_staged = pc.staged;
+  out.coarse_inner_iterations = 0;
+  if (pc.nH > 0 && pc.csolver == GENEO_COARSE_ITERATIVE && pc.c_inner)
+    GENEO_CUDA_TRY(copy_sync(c, &out.coarse_inner_iterations, pc.c_inner, sizeof(int),
+                             cudaMemcpyDeviceToHost));
   if (!flexible && h.it > 0) {
     int k = std::min(h.it, kHistCap);
     std::vector<double> al(k), be(std::max(k - 1, 0));

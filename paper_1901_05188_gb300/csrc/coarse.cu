@@ -3,6 +3,8 @@
 // restriction w = Z^T r, y = A_H^-1 w, the prolongation Z_j y_j, and the
 // deterministic gather of the local solutions over the subdomains containing
 // each node.
+#include <algorithm>
+
 #include "band.cuh"
 
 namespace geneo {
@@ -68,8 +70,8 @@ __global__ void __launch_bounds__(256)
                      int co0, int co1, int co2, const SubDesc *subs,
                      const int *__restrict__ gmap, const uint8_t *__restrict__ gcnt,
                      const T *__restrict__ xloc, const double *__restrict__ zy, int pou,
-                     const uint8_t *__restrict__ mask, double *__restrict__ z,
-                     const CGScalars *cg) {
+                     const double *__restrict__ wloc, const uint8_t *__restrict__ mask,
+                     double *__restrict__ z, const CGScalars *cg) {
   if (cg && cg->done) return;
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nnx * nny * nnz) return;
@@ -79,7 +81,7 @@ __global__ void __launch_bounds__(256)
   auto add = [&](int off, double wgt) {
     for (int comp = 0; comp < nc; ++comp) {
       double v = double(xloc[off + comp]);
-      if (pou) v *= mask[nc * n + comp] ? 0.0 : wgt;
+      if (pou) v *= wloc ? wloc[off + comp] : (mask[nc * n + comp] ? 0.0 : wgt);
       if (zy) v += zy[off + comp];
       o[comp] += v;
     }
@@ -231,7 +233,250 @@ __global__ void k_coarse_gemv(int nH, const double *__restrict__ Ainv,
   if (lane == 0) y[row] = s;
 }
 
+// ---- inexact coarse solve (Sec. 3.3.3) -------------------------------------
+// For large coarse spaces the paper solves A_H y = w by preconditioned CG and
+// makes the outer Krylov method flexible.  Here: CG preconditioned by the
+// inverses of A_H's diagonal blocks (one block per subdomain's modes), run to
+// ||w - A_H y|| <= tol ||w|| or max_it steps, inside one cooperative launch
+// whose blocks meet at a grid barrier with bounded waits.
+
+// Inverse of subdomain j's diagonal block of A_H (m_j x m_j, SPD) by
+// Gauss-Jordan elimination on [B | I] in shared memory; one CTA per subdomain.
+__global__ void __launch_bounds__(1024) k_coarse_bj_inverse(const SubDesc *subs, int nH,
+                                                            const double *__restrict__ AH,
+                                                            double *__restrict__ BJ, int mcap) {
+  const int j = blockIdx.x;
+  const SubDesc &S = subs[j];
+  const int m = S.m, o = S.coff;
+  if (m == 0) return;
+  __shared__ double G[32][65];
+  const int r = threadIdx.x >> 5, c = threadIdx.x & 31;
+  G[r][c] = (r < m && c < m) ? AH[(long long)(o + r) * nH + o + c] : (r == c ? 1.0 : 0.0);
+  G[r][32 + c] = r == c ? 1.0 : 0.0;
+  __syncthreads();
+  for (int k = 0; k < m; ++k) {
+    const double piv = G[k][k];
+    const double f0 = G[r][k];
+    __syncthreads();
+    if (r == k) {
+      G[k][c] /= piv;
+      G[k][32 + c] /= piv;
+    }
+    __syncthreads();
+    if (r != k) {
+      G[r][c] -= f0 * G[k][c];
+      G[r][32 + c] -= f0 * G[k][32 + c];
+    }
+    __syncthreads();
+  }
+  if (r < m && c < m) BJ[(long long)j * mcap * mcap + r * mcap + c] = G[r][32 + c];
+}
+
+__device__ __forceinline__ uint64_t coarse_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid barrier over the co-resident blocks of a cooperative launch: arrival
+// counter and generation word in global memory; a block that waits more than
+// about a second records GENEO_ERR_TIMEOUT and returns false.
+__device__ bool coarse_grid_barrier(unsigned int *bar, DevStatus *st) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned int *gen = bar + 1;
+    const unsigned int g = *gen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(bar, 1u);
+    if (arrived == gridDim.x - 1) {
+      bar[0] = 0;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const uint64_t t0 = coarse_ns();
+      while (*gen == g) {
+        if (coarse_ns() - t0 > 1000000000ull) {
+          atomicCAS(&st->code, 0, (int)GENEO_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Sum of the per-block partials part[b * 4 + k], the same order in every block.
+__device__ __forceinline__ double coarse_sum_partials(const double *part, int k) {
+  double s = 0.0;
+  for (int b = 0; b < (int)gridDim.x; ++b) s += ((volatile const double *)part)[b * 4 + k];
+  return s;
+}
+
+__device__ __forceinline__ void coarse_block_partials(double *part, double a, double b,
+                                                      double c) {
+  __shared__ double red[8][3];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  a = warp_sum(a);
+  b = warp_sum(b);
+  c = warp_sum(c);
+  if (lane == 0) {
+    red[warp][0] = a;
+    red[warp][1] = b;
+    red[warp][2] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w][threadIdx.x];
+    part[blockIdx.x * 4 + threadIdx.x] = t;
+  }
+  __syncthreads();
+}
+
+// Block-Jacobi PCG on A_H y = w from y = 0.  work: r, z, p, q [nH each] then
+// the per-block partials [gridDim.x][4]; bar: the barrier words.  One warp per
+// subdomain block for the vector updates and the block-Jacobi product, one
+// warp per row for A_H p.
+__global__ void __launch_bounds__(256)
+    k_coarse_pcg(const SubDesc *subs, int nsub, int nH, int mcap, const double *__restrict__ AH,
+                 const double *__restrict__ BJ, const double *__restrict__ w,
+                 double *__restrict__ y, double *work, unsigned int *bar, double tol2, int maxit,
+                 const CGScalars *cg, DevStatus *st, int *inner_its) {
+  if (cg && cg->done) return;
+  double *r = work, *z = r + nH, *p = z + nH, *q = p + nH, *part = q + nH;
+  const int lane = threadIdx.x & 31;
+  const int gwarp = blockIdx.x * 8 + (threadIdx.x >> 5), nwarps = gridDim.x * 8;
+  // r = w, y = 0, z = BJ r, p = z; partials r.z and r.r
+  double a0 = 0.0, a1 = 0.0;
+  for (int j = gwarp; j < nsub; j += nwarps) {
+    const int m = subs[j].m, o = subs[j].coff;
+    if (m == 0) continue;
+    const double rv = lane < m ? w[o + lane] : 0.0;
+    double zv = 0.0;
+    for (int k = 0; k < m; ++k)
+      zv += (lane < m ? BJ[(long long)j * mcap * mcap + lane * mcap + k] : 0.0) *
+            __shfl_sync(0xffffffffu, rv, k);
+    if (lane < m) {
+      r[o + lane] = rv;
+      y[o + lane] = 0.0;
+      z[o + lane] = zv;
+      p[o + lane] = zv;
+      a0 += rv * zv;
+      a1 += rv * rv;
+    }
+  }
+  coarse_block_partials(part, a0, a1, 0.0);
+  if (!coarse_grid_barrier(bar, st)) return;
+  double rz = coarse_sum_partials(part, 0), rr = coarse_sum_partials(part, 1);
+  const double ww = rr;
+  int it = 0;
+  for (; it < maxit && rr > tol2 * ww; ++it) {
+    if (!coarse_grid_barrier(bar, st)) return;     // every block has read the partials
+    // q = A_H p and p.q
+    double pq = 0.0;
+    for (int row = gwarp; row < nH; row += nwarps) {
+      const double *a = AH + (long long)row * nH;
+      double sum = 0.0;
+      for (int c = lane; c < nH; c += 32) sum += a[c] * p[c];
+      sum = warp_sum(sum);
+      if (lane == 0) {
+        q[row] = sum;
+        pq += p[row] * sum;
+      }
+    }
+    coarse_block_partials(part, pq, 0.0, 0.0);
+    if (!coarse_grid_barrier(bar, st)) return;
+    const double alpha = rz / coarse_sum_partials(part, 0);
+    if (!coarse_grid_barrier(bar, st)) return;     // partials read before they are rewritten
+    // y += alpha p, r -= alpha q, z = BJ r; partials r.z, r.r
+    a0 = a1 = 0.0;
+    for (int j = gwarp; j < nsub; j += nwarps) {
+      const int m = subs[j].m, o = subs[j].coff;
+      if (m == 0) continue;
+      double rv = 0.0;
+      if (lane < m) {
+        y[o + lane] += alpha * p[o + lane];
+        rv = r[o + lane] - alpha * q[o + lane];
+        r[o + lane] = rv;
+      }
+      double zv = 0.0;
+      for (int k = 0; k < m; ++k)
+        zv += (lane < m ? BJ[(long long)j * mcap * mcap + lane * mcap + k] : 0.0) *
+              __shfl_sync(0xffffffffu, rv, k);
+      if (lane < m) {
+        z[o + lane] = zv;
+        a0 += rv * zv;
+        a1 += rv * rv;
+      }
+    }
+    coarse_block_partials(part, a0, a1, 0.0);
+    if (!coarse_grid_barrier(bar, st)) return;
+    const double rz_new = coarse_sum_partials(part, 0);
+    rr = coarse_sum_partials(part, 1);
+    const double beta = rz_new / rz;
+    rz = rz_new;
+    for (int j = gwarp; j < nsub; j += nwarps) {
+      const int m = subs[j].m, o = subs[j].coff;
+      if (lane < m) p[o + lane] = z[o + lane] + beta * p[o + lane];
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && inner_its) atomicAdd(inner_its, it);
+}
+
 }  // namespace
+
+void launch_coarse_bj_inverse(const SubDesc *d_subs, int nsub, int nH, const double *AH,
+                              double *BJ, int mcap, cudaStream_t s) {
+  k_coarse_bj_inverse<<<nsub, 1024, 0, s>>>(d_subs, nH, AH, BJ, mcap); GENEO_COUNT_LAUNCH();
+}
+
+int coarse_pcg_blocks() {
+  static int blocks = 0;
+  if (blocks == 0) {
+    int dev = 0, sms = 0, per = 0;
+    GENEO_CUDA_TRY(cudaGetDevice(&dev));
+    GENEO_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    GENEO_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_coarse_pcg, 256, 0));
+    blocks = sms * std::max(1, std::min(per, 2));
+  }
+  return blocks;
+}
+
+int launch_coarse_apply_iterative(const SubDesc *d_subs, int nsub, int max_nint, int nnx,
+                                  int nny, const double *Zp, const double *r, double *wpart,
+                                  double *wH, double *yH, double *zy, const double *AH,
+                                  const double *BJ, int nH, int mcap, double *work,
+                                  unsigned int *bar, double tol, int maxit, const CGScalars *cg,
+                                  DevStatus *st, int *inner_its, cudaStream_t s) {
+  const int nchunk = restrict_chunks(max_nint);
+  k_coarse_restrict<<<dim3(nchunk, nsub), 256, 0, s>>>(d_subs, nnx, nny, Zp, r, wpart, nchunk,
+                                                      mcap, cg); GENEO_COUNT_LAUNCH();
+  k_coarse_reduce<<<nsub, 256, 0, s>>>(d_subs, wpart, wH, nchunk, mcap, cg); GENEO_COUNT_LAUNCH();
+  const int blocks = coarse_pcg_blocks();
+  if (blocks <= 0) return GENEO_ERR_CUDA;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;     // every block resident: the barrier can complete
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const double tol2 = tol * tol;
+  GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_coarse_pcg, d_subs, nsub, nH, mcap, AH, BJ,
+                                    (const double *)wH, yH, work, bar, tol2, maxit, cg, st,
+                                    inner_its));
+  GENEO_COUNT_LAUNCH();
+  k_coarse_prolong<<<dim3(nchunk, nsub), 256, 0, s>>>(d_subs, Zp, yH, zy, cg); GENEO_COUNT_LAUNCH();
+  return GENEO_OK;
+}
 
 void launch_gather_map(int nx, int ny, int nz, int px, int py, const int *cand,
                        const int cand_off[3], const SubDesc *d_subs, int *gmap, uint8_t *gcnt,
@@ -246,12 +491,13 @@ template <typename T>
 void launch_schwarz_gather(int nx, int ny, int nz, int px, int py, const int *cand,
                            const int cand_off[3], const SubDesc *d_subs, const int *gmap,
                            const uint8_t *gcnt, const T *xloc, const double *zy, int pou,
-                           const uint8_t *mask, double *z, const CGScalars *cg, cudaStream_t s) {
+                           const double *wloc, const uint8_t *mask, double *z,
+                           const CGScalars *cg, cudaStream_t s) {
   int nn = (nx + 1) * (ny + 1) * (nz + 1);
   k_schwarz_gather<T><<<(nn + 255) / 256, 256, 0, s>>>(nx + 1, ny + 1, nz + 1, px, py, cand,
                                                       cand_off[0], cand_off[1], cand_off[2],
-                                                      d_subs, gmap, gcnt, xloc, zy, pou, mask,
-                                                      z, cg); GENEO_COUNT_LAUNCH();
+                                                      d_subs, gmap, gcnt, xloc, zy, pou, wloc,
+                                                      mask, z, cg); GENEO_COUNT_LAUNCH();
 }
 
 void launch_coarse_apply(const SubDesc *d_subs, int nsub, int max_nint, int nnx, int nny,
@@ -268,11 +514,13 @@ void launch_coarse_apply(const SubDesc *d_subs, int nsub, int max_nint, int nnx,
 
 template void launch_schwarz_gather<double>(int, int, int, int, int, const int *, const int[3],
                                             const SubDesc *, const int *, const uint8_t *,
-                                            const double *, const double *, int, const uint8_t *,
-                                            double *, const CGScalars *, cudaStream_t);
+                                            const double *, const double *, int, const double *,
+                                            const uint8_t *, double *, const CGScalars *,
+                                            cudaStream_t);
 template void launch_schwarz_gather<float>(int, int, int, int, int, const int *, const int[3],
                                            const SubDesc *, const int *, const uint8_t *,
-                                           const float *, const double *, int, const uint8_t *,
-                                           double *, const CGScalars *, cudaStream_t);
+                                           const float *, const double *, int, const double *,
+                                           const uint8_t *, double *, const CGScalars *,
+                                           cudaStream_t);
 
 }  // namespace geneo

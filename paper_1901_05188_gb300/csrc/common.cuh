@@ -133,6 +133,23 @@ struct SubDesc {
   long long z_off;      // offset of Z_j (n_int x m, row-major) in the Z pool
 };
 
+// Distance of node (i, j, k) to the artificial boundary of Omega_j (the faces
+// of its element box that lie inside the domain of nx x ny x nz elements),
+// counted in element layers: the least distance to such a face's plane; 1
+// when Omega_j has no artificial face (the whole domain).  The weight of the
+// Sarkis partition of unity (Sec. 3.2, Sec. 3.3.1) is this distance over its
+// sum across the subdomains whose interior holds the node.
+__host__ __device__ __forceinline__ int artificial_distance(const SubDesc &S, int i, int j, int k,
+                                                            int nx, int ny, int nz) {
+  const int pos[3] = {i, j, k}, ne[3] = {nx, ny, nz};
+  int d = 0x7fffffff;
+  for (int a = 0; a < 3; ++a) {
+    if (S.elo[a] > 0) d = min(d, pos[a] - S.elo[a]);
+    if (S.ehi[a] < ne[a]) d = min(d, S.ehi[a] - pos[a]);
+  }
+  return d == 0x7fffffff ? 1 : d;
+}
+
 // ---------------------------------------------------------------------------
 // Deterministic block reduction helpers.
 __device__ __forceinline__ double warp_sum(double v) {

@@ -16,6 +16,10 @@ struct geneo_ctx {
   cudaStream_t fac_stream = nullptr;        // subdomain factorisation, overlapping the eigensolve
   cudaStream_t fac_side = nullptr;          // its look-ahead stream
   int device = 0;
+  int pou_kind = 0;                          // partition of unity of the next geneo_setup
+  int csolver = 0;                           // coarse solver of the next geneo_setup
+  double ctol = 1e-2;                        // its inner tolerance (iterative)
+  int cmaxit = 200;                          // its inner step limit (iterative)
 
   // ---- mesh / assembled system (phase 0)
   bool assembled = false;

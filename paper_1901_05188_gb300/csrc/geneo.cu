@@ -26,8 +26,29 @@ __device__ __forceinline__ int cand_count(const int *c) {
   return n;
 }
 
+// Partition-of-unity weight X_j at node (gi, gj, gk) of subdomain j's
+// interior: 1 / multiplicity (Sec. 3.3.1), or Sarkis's d_j / sum_k d_k with
+// d the distance to each interior subdomain's artificial boundary in element
+// layers (Sec. 3.2).  The caller zeroes it on global Dirichlet dofs.
+__device__ double pou_weight(const SubDesc *subs, int j, int gi, int gj, int gk, const int *cand,
+                             int co0, int co1, int co2, int px, int py, int nx, int ny, int nz,
+                             int kind) {
+  const int *ci = cand + (co0 + gi) * kMaxCand;
+  const int *cj = cand + (co1 + gj) * kMaxCand;
+  const int *ck = cand + (co2 + gk) * kMaxCand;
+  const int nci = cand_count(ci), ncj = cand_count(cj), nck = cand_count(ck);
+  if (kind == 0) return 1.0 / double(nci * ncj * nck);
+  int sum = 0;
+  for (int c = 0; c < nck; ++c)
+    for (int b = 0; b < ncj; ++b)
+      for (int a = 0; a < nci; ++a)
+        sum += artificial_distance(subs[ci[a] + px * (cj[b] + py * ck[c])], gi, gj, gk, nx, ny, nz);
+  return double(artificial_distance(subs[j], gi, gj, gk, nx, ny, nz)) / double(sum);
+}
+
 __global__ void k_pou_neumann(const SubDesc *subs, const int *cand, int co0, int co1, int co2,
-                              const uint8_t *mask, int nnx, int nny, double *Xneu) {
+                              const uint8_t *mask, int nnx, int nny, int nnz, int px, int py,
+                              int kind, double *Xneu) {
   const int j = blockIdx.y;
   const SubDesc &S = subs[j];
   const int nc = S.nc;
@@ -38,12 +59,30 @@ __global__ void k_pou_neumann(const SubDesc *subs, const int *cand, int co0, int
   S.nbox.global(l, gi, gj, gk);
   double x = 0.0;
   if (S.ibox.local(gi, gj, gk) >= 0) {
-    int mu = cand_count(cand + (co0 + gi) * kMaxCand) * cand_count(cand + (co1 + gj) * kMaxCand) *
-             cand_count(cand + (co2 + gk) * kMaxCand);
-    x = 1.0 / double(mu);
+    x = pou_weight(subs, j, gi, gj, gk, cand, co0, co1, co2, px, py, nnx - 1, nny - 1, nnz - 1,
+                   kind);
     if (mask[nc * (gi + nnx * (gj + nny * gk)) + comp]) x = 0.0;
   }
   Xneu[S.x_neu + t] = x;
+}
+
+// The same weights on the interior dofs, laid out like the local solutions
+// (offset v_int): the one-level weight D_j = X_j of the gather.
+__global__ void k_pou_interior(const SubDesc *subs, const int *cand, int co0, int co1, int co2,
+                               const uint8_t *mask, int nnx, int nny, int nnz, int px, int py,
+                               int kind, double *wloc) {
+  const int j = blockIdx.y;
+  const SubDesc &S = subs[j];
+  const int nc = S.nc;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nc * S.ibox.count()) return;
+  int l = t / nc, comp = t - nc * l;
+  int gi, gj, gk;
+  S.ibox.global(l, gi, gj, gk);
+  double x = pou_weight(subs, j, gi, gj, gk, cand, co0, co1, co2, px, py, nnx - 1, nny - 1,
+                        nnz - 1, kind);
+  if (mask[nc * (gi + nnx * (gj + nny * gk)) + comp]) x = 0.0;
+  wloc[S.v_int + t] = x;
 }
 
 __global__ void __launch_bounds__(128)
@@ -843,11 +882,19 @@ void launch_rigid_modes(const SubDesc *d_subs, int nsub, int npad, const double 
 }
 
 void launch_pou_neumann(const SubDesc *d_subs, int nsub, int max_nodes, const int *cand,
-                        const int cand_off[3], const uint8_t *mask, int nnx, int nny,
-                        double *Xneu, cudaStream_t s) {
+                        const int cand_off[3], const uint8_t *mask, int nnx, int nny, int nnz,
+                        int px, int py, int kind, double *Xneu, cudaStream_t s) {
   dim3 g((3 * max_nodes + 255) / 256, nsub);
   k_pou_neumann<<<g, 256, 0, s>>>(d_subs, cand, cand_off[0], cand_off[1], cand_off[2], mask, nnx,
-                                  nny, Xneu); GENEO_COUNT_LAUNCH();
+                                  nny, nnz, px, py, kind, Xneu); GENEO_COUNT_LAUNCH();
+}
+
+void launch_pou_interior(const SubDesc *d_subs, int nsub, int max_nodes, const int *cand,
+                         const int cand_off[3], const uint8_t *mask, int nnx, int nny, int nnz,
+                         int px, int py, int kind, double *wloc, cudaStream_t s) {
+  dim3 g((3 * max_nodes + 255) / 256, nsub);
+  k_pou_interior<<<g, 256, 0, s>>>(d_subs, cand, cand_off[0], cand_off[1], cand_off[2], mask,
+                                   nnx, nny, nnz, px, py, kind, wloc); GENEO_COUNT_LAUNCH();
 }
 
 void launch_neumann_assemble(const SubDesc *d_subs, const BandLayout *d_lay, int nsub,

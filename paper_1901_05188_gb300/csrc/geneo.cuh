@@ -5,11 +5,16 @@
 
 namespace geneo {
 
-// X_j on Neumann dofs (Sec. 3.3.1 standard PoU): 1/multiplicity on the dofs of
-// V_{h,0}(Omega_j), zero on the artificial boundary and on Dirichlet dofs.
+// Partition of unity (kind 0: 1 / multiplicity, Sec. 3.3.1; kind 1: Sarkis's
+// distance-weighted one, Sec. 3.2) on every subdomain's Neumann dofs (Xneu,
+// offset x_neu), or on its interior dofs laid out like the local solutions
+// (wloc, offset v_int); zero on global Dirichlet dofs.
 void launch_pou_neumann(const SubDesc *d_subs, int nsub, int max_nodes, const int *cand,
-                        const int cand_off[3], const uint8_t *mask, int nnx, int nny,
-                        double *Xneu, cudaStream_t s);
+                        const int cand_off[3], const uint8_t *mask, int nnx, int nny, int nnz,
+                        int px, int py, int kind, double *Xneu, cudaStream_t s);
+void launch_pou_interior(const SubDesc *d_subs, int nsub, int max_nodes, const int *cand,
+                         const int cand_off[3], const uint8_t *mask, int nnx, int nny, int nnz,
+                         int px, int py, int kind, double *wloc, cudaStream_t s);
 
 // S_j = A_{Omega_j} - sigma X_j A_{Omega_j^o} X_j into band tiles (lower part)
 // and B_j = X_j A_{Omega_j^o} X_j into a 27-slot local BSR.

@@ -47,6 +47,8 @@ struct Precond {
   // interior factors (T = double or float), L and U copies
   void *facL = nullptr, *facU = nullptr;
   void *xloc = nullptr;           // per-subdomain local solutions
+  int pou = 0;                    // partition of unity: GENEO_POU_MULTIPLICITY or _SARKIS
+  double *wloc = nullptr;         // Sarkis weights X_j on interior dofs (like xloc), or null
   // GenEO eigenproblem data (FP64)
   double *neuL = nullptr, *neuU = nullptr;   // factor of S = A - sigma B
   double *Bloc = nullptr;         // 27-slot local BSR of B (9 doubles per block)
@@ -82,6 +84,13 @@ struct Precond {
   double *wpart = nullptr;        // restriction partials [nsub][row blocks][mcap]
   double *wH = nullptr, *yH = nullptr;
   double *zy = nullptr;           // coarse correction Z_j y_j per interior dof [sum n_int]
+  int csolver = 0;                // GENEO_COARSE_DIRECT or GENEO_COARSE_ITERATIVE
+  double ctol = 1e-2;             // inner relative residual of the iterative coarse solve
+  int cmaxit = 200;               // its step limit
+  double *BJ = nullptr;           // block-Jacobi inverses [nsub][mcap][mcap]
+  double *cwork = nullptr;        // inner PCG vectors and partials
+  unsigned int *cbar = nullptr;   // grid-barrier words of the inner PCG
+  int *c_inner = nullptr;         // inner steps accumulated over the applications
   int max_nint = 0;               // largest interior dof count of a subdomain
   int max_nodes_int = 0, max_nodes_neu = 0;   // largest interior / Neumann node count
   std::vector<int> m;

@@ -23,3 +23,36 @@ def bsr_to_csr(rp, col, val, n, nc=3):
 
 def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def check_against_golden(u, st, gold, coarse=None, u_tol=1e-6):
+    """Compare a GPU solve with an oracle summary written by make_golden.py:
+    the displacement at the stored samples (relative L2), the norm of every
+    consecutive chunk of dofs (largest deviation relative to the largest
+    chunk norm, so every dof is covered), the norm of u, the iteration count
+    (+-2) and, given coarse = (modes, lambdas, n_coarse), the coarse
+    dimension, the per-subdomain mode counts and eigenvalues (1e-7 relative,
+    floor 1e-2)."""
+    ref = np.asarray(gold["u_samples"])
+    us = u[::gold["sample_stride"]][:ref.size]
+    err = np.linalg.norm(us - ref) / np.linalg.norm(ref)
+    assert err <= u_tol, ("samples", err)
+    assert abs(np.linalg.norm(u) - gold["u_norm"]) <= u_tol * gold["u_norm"]
+    if "u_chunk_norms" in gold:
+        ch = int(gold["chunk"])
+        cn = np.sqrt(np.add.reduceat(u * u, np.arange(0, u.size, ch)))
+        rc = np.asarray(gold["u_chunk_norms"])
+        assert cn.size == rc.size
+        dev = np.max(np.abs(cn - rc)) / np.max(rc)
+        assert dev <= u_tol, ("chunk norms", dev)
+    assert abs(st["iterations"] - gold["iterations"]) <= 2, (st["iterations"], gold["iterations"])
+    if coarse is not None:
+        modes, lam, nh = coarse
+        assert nh == gold["n_coarse"]
+        assert list(modes) == gold["modes"]
+        for j, lref in enumerate(gold["lambdas"]):
+            lref = np.asarray(lref)
+            k = min(len(lref), modes[j] + 1)
+            got = lam[j, :k]
+            assert np.all(np.abs(got - lref[:k]) <= 1e-7 * np.maximum(np.abs(lref[:k]), 1e-2)), j
+    return err

@@ -12,7 +12,7 @@ import pytest
 
 import workloads
 
-from gpu_common import require_gpu
+from gpu_common import check_against_golden, require_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -51,6 +51,7 @@ def test_c2_fp64_matches_oracle(pkg, gold):
     ref = np.asarray(gold["u_samples"])
     assert np.linalg.norm(samples(u, gold) - ref) <= 1e-6 * np.linalg.norm(ref)
     assert abs(np.linalg.norm(u) - gold["u_norm"]) <= 1e-6 * gold["u_norm"]
+    check_against_golden(u, st, gold)
     assert st["rel_res_true"] <= 2e-8
     s.close()
 
@@ -64,6 +65,7 @@ def test_c2_mixed_precision_matches_oracle(pkg, gold):
     ref = np.asarray(gold["u_samples"])
     err = np.linalg.norm(samples(u, gold) - ref) / np.linalg.norm(ref)
     assert err <= 1e-6, err
+    check_against_golden(u, st, gold, s.coarse_info())
     assert st["rel_res_true"] <= 2e-8
     assert st["flexible"] == 1
     s.close()
