@@ -564,6 +564,25 @@ def run_ours(args):
             ms2, st2 = timed(pd2, pr, u2, kk, 1, schwarz=sw, coarse=co, max_it=mi)
             c2[key] = dict(ms_per_solve=ms2, steps=kk, converged=st2["rel_res_recursive"] <= TOL,
                            **leg_summary(st2), oracle_error=oracle_error(u2.cpu().numpy(), g2))
+        # threshold scaling (Sec. 3.2: the eigenvalue threshold trades coarse
+        # dimension and set-up time against iterations): absolute thresholds
+        # at multiples of the median default threshold, cap 32 modes
+        keep = []
+        taus = pkg.geneo_default_thresholds(pkg.GeneoSolver.mesh_of(p2, keep),
+                                            pkg.GeneoSolver.partition_of(p2))
+        tau0 = float(np.median(taus))
+        sweep = []
+        for f in (0.25, 0.5, 1.0, 2.0, 4.0):
+            q = dict(p2, modes=dict(fixed_modes=0, threshold=f * tau0, max_modes=32, shift=-0.01))
+            ms_t, st_t = timed(device_problem(q, torch, dev), pkg.GENEO_FP64, u2, 1, 1)
+            sweep.append(dict(threshold_factor=f, threshold=f * tau0, ms_per_solve=ms_t,
+                              n_coarse=st_t["n_coarse"], iterations=st_t["iterations"],
+                              kappa_est=st_t["kappa_est"],
+                              setup_ms=st_t["ms_setup_eig"], solve_ms=st_t["ms_solve"],
+                              oracle_error=oracle_error(u2.cpu().numpy(), g2) if f == 1.0
+                              else None))
+        c2["threshold_sweep"] = dict(default_threshold_median=tau0, cap=32, precision="fp64",
+                                     runs=sweep)
         del pd2, u2
 
     # serving: a seeded stream of uneven solve requests through the
