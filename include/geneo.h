@@ -400,6 +400,38 @@ int geneo_default_thresholds(const geneo_mesh *mesh, const geneo_partition *part
  * eigenvalue is not positive.  Host-only. */
 int geneo_kappa_from_cg(const double *alphas, const double *betas, int k, double *kappa);
 
+/* Batched solves (the many-instance form of geneo_solve, for a stream of
+ * independent problems of uneven sizes; Sec. 3.3's batched local solves
+ * carried across instances).  A batch is built from n contexts that are each
+ * assembled and set up (same device, same precision, the direct coarse
+ * solve); it keeps their matrices, factors and coarse spaces where they are
+ * and owns only the concatenated Krylov vectors and its work tables.  Every
+ * kernel launch of an iteration covers every instance; each instance keeps
+ * its own (F)PCG scalars and stops on its own criterion; the one-level local
+ * solves of all instances run in one persistent launch whose CTAs take
+ * (instance, subdomain) items from a device work queue, largest first, in a
+ * launch shape chosen by timing at creation (GENEO_SCHWARZ_ROWS /
+ * GENEO_SCHWARZ_STAGED pin it); the iterations are captured in a CUDA graph.
+ * While a batch exists its contexts must not run other work (it uses their
+ * buffers).  Work goes to cuda_stream (NULL = legacy default stream).
+ * Returns GENEO_ERR_STATE for a context that is not set up,
+ * GENEO_ERR_INVALID_ARG for mixed precisions or devices or a repeated
+ * context. */
+typedef struct geneo_batch geneo_batch;
+int geneo_batch_create(geneo_batch **out, geneo_ctx *const *ctxs, int n, void *cuda_stream);
+
+/* Solve every instance of the batch from u0 = 0 to ||r_k|| <= tol ||b_k||
+ * or max_it iterations (Sec. 3.1), each with its context's current
+ * right-hand side (geneo_set_load may change it between solves).  u[i] (host or device, 3*n_nodes or n_nodes
+ * doubles; NULL entries skipped) receives instance i's solution; stats[i]
+ * (may be NULL) its statistics, ms_solve being the whole batch's time.
+ * Returns GENEO_ERR_NOT_CONVERGED / GENEO_ERR_CG_BREAKDOWN if any instance
+ * did not converge (the others' results are still written). */
+int geneo_batch_solve(geneo_batch *batch, double tol, int max_it, double *const *u,
+                      geneo_stats *stats);
+
+int geneo_batch_destroy(geneo_batch *batch);
+
 /* Solve A u = b by PCG (FP64 precision, GENEO_AS) or flexible CG (mixed
  * precision or GENEO_AS_POU) from u0 = 0 until ||r_k|| <= tol ||b|| or max_it
  * iterations (Sec. 3.1).  u: 3*n_nodes doubles.  stats may be NULL. */

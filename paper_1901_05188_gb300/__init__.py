@@ -118,6 +118,9 @@ _SIGS = {
     "geneo_spmv_dot_noalloc": [C.c_int, _P, _P, _P, _P, _P, _P, _P],
     "geneo_set_partition_of_unity": [_P, C.c_int],
     "geneo_set_coarse_solver": [_P, C.c_int, C.c_double, C.c_int],
+    "geneo_batch_create": [C.POINTER(_P), C.POINTER(_P), C.c_int, _P],
+    "geneo_batch_solve": [_P, C.c_double, C.c_int, C.POINTER(_P), C.POINTER(geneo_stats)],
+    "geneo_batch_destroy": [_P],
     "geneo_profile": [_P, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                       C.POINTER(C.c_double)],
 }
@@ -348,6 +351,27 @@ def geneo_solve(ctx, tol, max_it, u, raise_on_nonconvergence=True):
     return st, status
 
 
+def geneo_batch_create(ctxs, stream=None):
+    arr = (_P * len(ctxs))(*[C.cast(c, _P) if not isinstance(c, int) else c for c in ctxs])
+    out = _P()
+    _check(load().geneo_batch_create(C.byref(out), arr, len(ctxs), stream))
+    return out
+
+
+def geneo_batch_solve(batch, tol, max_it, us, raise_on_nonconvergence=True):
+    n = len(us)
+    arr = (_P * n)(*[_ptr(u) for u in us])
+    st = (geneo_stats * n)()
+    status = load().geneo_batch_solve(batch, float(tol), int(max_it), arr, st)
+    if status != 0 and (raise_on_nonconvergence or status not in (7,)):
+        _check(status)
+    return [s.as_dict() for s in st], status
+
+
+def geneo_batch_destroy(batch):
+    _check(load().geneo_batch_destroy(batch))
+
+
 # ---- convenience driver -------------------------------------------------------------
 
 class GeneoSolver:
@@ -554,3 +578,34 @@ class GeneoSolver:
         if nh:
             geneo_get_coarse(self.ctx, Phi, AH)
         return Phi.T, AH
+
+
+class GeneoBatch:
+    """Batched solves of several set-up GeneoSolver instances (same device and
+    precision): every iteration step is one launch over all of them, the
+    local solves one persistent work-queue launch (geneo_batch_*)."""
+
+    def __init__(self, solvers, stream=None):
+        import torch
+        self.solvers = list(solvers)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.solvers[0].device).cuda_stream
+        self.batch = geneo_batch_create([s.ctx for s in self.solvers],
+                                        C.c_void_p(stream) if stream else None)
+
+    def solve(self, tol=1e-8, max_it=2000, outs=None, raise_on_nonconvergence=True):
+        if outs is None:
+            outs = [np.zeros(s.ndof) for s in self.solvers]
+        stats, _ = geneo_batch_solve(self.batch, tol, max_it, outs, raise_on_nonconvergence)
+        return outs, stats
+
+    def close(self):
+        if self.batch is not None:
+            geneo_batch_destroy(self.batch)
+            self.batch = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

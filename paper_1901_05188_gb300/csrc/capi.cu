@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "ctx.cuh"
+#include "batch.cuh"
 #include "geneo.cuh"
 
 using namespace geneo;
@@ -2167,5 +2168,438 @@ extern "C" int geneo_profile(geneo_ctx *c, int what, int reps, double *ms_per_la
   if (ms_per_launch) *ms_per_launch = ms / reps;
   if (bytes) *bytes = by;
   if (flops) *flops = fl;
+  return GENEO_OK;
+}
+
+// ============================================================================
+// Batched solves of many independent instances (one launch per step over all
+// instances, the local solves in one persistent work-queue launch).
+struct geneo_batch {
+  int n = 0;
+  std::vector<geneo_ctx *> ctx;
+  cudaStream_t stream = nullptr, cap = nullptr;
+  bool f32 = false;
+  void *mem = nullptr;
+  std::vector<BatchInst> inst;
+  BatchInst *d_inst = nullptr;
+  BatchTables T{};
+  std::vector<long long> vbase;
+  long long ntot = 0;
+  double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+  double *tpart = nullptr, *alphas = nullptr, *betas = nullptr, *rt2 = nullptr;
+  int hist = 0;
+  CGScalars *cg = nullptr, *cg_host = nullptr;
+  int *heads = nullptr;
+  DevStatus *status = nullptr;
+  int npad_max = 0, w_max = 0, rows = 0, staged = 0, blocks = 0;
+  bool any_coarse = false;
+  cudaGraphExec_t graph = nullptr;
+  long long graph_kernels = 0;
+  float ms_tune = 0.f;
+};
+
+namespace {
+
+constexpr int kBatchHist = 4096;   // Krylov coefficients kept per instance (condition estimate)
+
+int batch_precond(geneo_batch *B, const double *r, double *z, int head, cudaStream_t s) {
+  int st;
+  if (B->any_coarse) launch_batch_coarse(B->d_inst, B->T, B->cg, r, s);
+  GENEO_CUDA_TRY(cudaMemsetAsync(B->heads + head, 0, sizeof(int), s));
+  if (B->f32)
+    st = launch_batch_schwarz<float>(B->d_inst, B->cg, B->T.sub_items, B->T.nsub_items,
+                                     B->heads + head, r, B->npad_max, B->w_max, B->rows,
+                                     B->staged, B->blocks, B->status, s);
+  else
+    st = launch_batch_schwarz<double>(B->d_inst, B->cg, B->T.sub_items, B->T.nsub_items,
+                                      B->heads + head, r, B->npad_max, B->w_max, B->rows,
+                                      B->staged, B->blocks, B->status, s);
+  if (st) return st;
+  launch_batch_gather(B->d_inst, B->T, B->cg, B->f32, z, s);
+  GENEO_CUDA_TRY(cudaGetLastError());
+  return GENEO_OK;
+}
+
+int batch_iterations(geneo_batch *B, int iters, cudaStream_t s) {
+  int st;
+  for (int it = 0; it < iters; ++it) {
+    launch_batch_spmv_pq(B->d_inst, B->T, B->cg, B->p, B->q, B->tpart, s);
+    launch_batch_reduce(B->d_inst, B->T, B->cg, B->tpart, 2, nullptr, nullptr, 0, nullptr, s);
+    launch_batch_update_xr(B->d_inst, B->T, B->cg, B->p, B->q, B->x, B->r, B->tpart, s);
+    launch_batch_reduce(B->d_inst, B->T, B->cg, B->tpart, 3, B->alphas, nullptr, B->hist,
+                        nullptr, s);
+    if ((st = batch_precond(B, B->r, B->z, it, s))) return st;
+    launch_batch_dots(B->d_inst, B->T, B->cg, B->r, B->z, B->q, B->tpart, s);
+    launch_batch_reduce(B->d_inst, B->T, B->cg, B->tpart, 4, nullptr, B->betas, B->hist,
+                        nullptr, s);
+    launch_batch_update_p(B->d_inst, B->T, B->cg, B->z, B->p, s);
+  }
+  GENEO_CUDA_TRY(cudaGetLastError());
+  return GENEO_OK;
+}
+
+int batch_check_status(geneo_batch *B) {
+  DevStatus h{};
+  GENEO_CUDA_TRY(cudaMemcpyAsync(&h, B->status, sizeof(h), cudaMemcpyDeviceToHost, B->stream));
+  GENEO_CUDA_TRY(cudaStreamSynchronize(B->stream));
+  if (h.code != 0) {
+    GENEO_CUDA_TRY(cudaMemsetAsync(B->status, 0, sizeof(DevStatus), B->stream));
+    g_last_error = "device status " + std::to_string(h.code) + " at index " +
+                   std::to_string(h.where) + " detail " + std::to_string(h.detail);
+  }
+  return h.code;
+}
+
+void batch_free(geneo_batch *B) {
+  if (!B) return;
+  if (B->stream) cudaStreamSynchronize(B->stream);
+  if (B->graph) cudaGraphExecDestroy(B->graph);
+  if (B->mem) cudaFree(B->mem);
+  if (B->cg_host) cudaFreeHost(B->cg_host);
+  if (B->cap) cudaStreamDestroy(B->cap);
+  delete B;
+}
+
+}  // namespace
+
+extern "C" int geneo_batch_create(geneo_batch **out, geneo_ctx *const *ctxs, int n,
+                                  void *cuda_stream) {
+  if (!out || !ctxs || n < 1) return fail(GENEO_ERR_INVALID_ARG, "null batch arguments");
+  *out = nullptr;
+  int dev = -1;
+  bool f32 = false;
+  for (int i = 0; i < n; ++i) {
+    geneo_ctx *c = ctxs[i];
+    if (!c || !c->assembled || !c->setup_done)
+      return fail(GENEO_ERR_STATE, "every context of a batch must be assembled and set up");
+    const Precond &pc = c->pc;
+    if (pc.schwarz == GENEO_NO_PRECOND)
+      return fail(GENEO_ERR_INVALID_ARG, "a batch needs the Schwarz preconditioner");
+    if (pc.nH > 0 && pc.csolver != GENEO_COARSE_DIRECT)
+      return fail(GENEO_ERR_INVALID_ARG, "a batch uses the direct coarse solve");
+    const bool fi = pc.prec == GENEO_MIXED_FP32;
+    if (i == 0) {
+      dev = c->device;
+      f32 = fi;
+    } else if (c->device != dev || fi != f32) {
+      return fail(GENEO_ERR_INVALID_ARG, "the contexts of a batch share one device and precision");
+    }
+    for (int k = 0; k < i; ++k)
+      if (ctxs[k] == c) return fail(GENEO_ERR_INVALID_ARG, "a context appears twice in the batch");
+  }
+  int cur = -1;
+  GENEO_CUDA_TRY(cudaGetDevice(&cur));
+  if (cur != dev) return fail(GENEO_ERR_INVALID_ARG, "the batch's device is not current");
+  geneo_batch *B = new (std::nothrow) geneo_batch;
+  if (!B) return fail(GENEO_ERR_INVALID_ARG, "out of host memory");
+  struct Guard {
+    geneo_batch *b;
+    ~Guard() { batch_free(b); }
+  } guard{B};
+  B->n = n;
+  B->ctx.assign(ctxs, ctxs + n);
+  B->stream = (cudaStream_t)cuda_stream;
+  B->f32 = f32;
+  GENEO_CUDA_TRY(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
+  for (geneo_ctx *c : B->ctx) GENEO_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  // instances and work tables (host)
+  std::vector<long long> task_off(n + 1, 0), node_off(n + 1, 0);
+  std::vector<int2> sub_items, row_items;
+  std::vector<int4> chunk_items;
+  std::vector<std::pair<long long, int2>> cost;
+  B->inst.resize(n);
+  B->vbase.resize(n);
+  long long v = 0;
+  for (int i = 0; i < n; ++i) {
+    geneo_ctx *c = B->ctx[i];
+    Precond &pc = c->pc;
+    BatchInst &I = B->inst[i];
+    I = BatchInst{};
+    I.vbase = v;
+    B->vbase[i] = v;
+    I.nnode = c->nnode;
+    I.nc = c->nc;
+    I.ndof = c->ndof;
+    I.row_ptr = c->row_ptr;
+    I.col = c->col;
+    I.val = c->val;
+    I.mask = c->mask;
+    I.flexible = (pc.prec == GENEO_MIXED_FP32 || pc.schwarz == GENEO_AS_POU) ? 1 : 0;
+    I.nsub = pc.nsub;
+    I.nnx = c->nx + 1;
+    I.nny = c->ny + 1;
+    I.nnz = c->nz + 1;
+    I.px = pc.part.px;
+    I.py = pc.part.py;
+    I.subs = pc.d_subs;
+    I.lay = pc.d_lay_int;
+    I.facL = pc.facL;
+    I.facU = pc.facU;
+    I.xloc = pc.xloc;
+    I.cand = pc.d_cand;
+    I.co0 = pc.cand_off[0];
+    I.co1 = pc.cand_off[1];
+    I.co2 = pc.cand_off[2];
+    I.gmap = pc.gmap;
+    I.gcnt = pc.gcnt;
+    I.pou = pc.schwarz == GENEO_AS_POU ? 1 : 0;
+    I.wloc = pc.pou == GENEO_POU_SARKIS ? pc.wloc : nullptr;
+    I.nH = pc.nH;
+    I.mcap = pc.mcap;
+    I.nchunk = restrict_chunks(pc.max_nint);
+    I.Zp = pc.Zp;
+    I.AHinv = pc.AHinv;
+    I.wpart = pc.wpart;
+    I.wH = pc.wH;
+    I.yH = pc.yH;
+    I.zy = pc.zy;
+    v += c->ndof;
+    task_off[i + 1] = task_off[i] + (c->ndof + 31) / 32;
+    node_off[i + 1] = node_off[i] + (c->nnode + 255) / 256;
+    for (int j = 0; j < pc.nsub; ++j) {
+      const SubDesc &S = pc.subs[j];
+      cost.push_back({(long long)S.nt_int * (S.w_int + 1), make_int2(i, j)});
+      B->npad_max = std::max(B->npad_max, S.nt_int * 32);
+      B->w_max = std::max(B->w_max, S.w_int);
+      if (pc.nH > 0)
+        for (int b = 0; b < (S.n_int + kZRows - 1) / kZRows; ++b)
+          chunk_items.push_back(make_int4(i, j, b, 0));
+    }
+    for (int k = 0; k < pc.nH; ++k) row_items.push_back(make_int2(i, k));
+    if (pc.nH > 0) B->any_coarse = true;
+  }
+  std::stable_sort(cost.begin(), cost.end(),
+                   [](const std::pair<long long, int2> &a, const std::pair<long long, int2> &b) {
+                     return a.first > b.first;
+                   });
+  for (auto &e : cost) sub_items.push_back(e.second);
+  B->ntot = v;
+  B->hist = kBatchHist;
+  // one device allocation for everything the batch owns
+  Arena A;
+  auto layout = [&](Arena &a) {
+    B->d_inst = a.take<BatchInst>(n);
+    B->T.task_off = a.take<long long>(n + 1);
+    B->T.node_off = a.take<long long>(n + 1);
+    B->T.sub_items = a.take<int2>(sub_items.size());
+    B->T.chunk_items = a.take<int4>(std::max<size_t>(1, chunk_items.size()));
+    B->T.row_items = a.take<int2>(std::max<size_t>(1, row_items.size()));
+    B->b = a.take<double>(v);
+    B->x = a.take<double>(v);
+    B->r = a.take<double>(v);
+    B->z = a.take<double>(v);
+    B->p = a.take<double>(v);
+    B->q = a.take<double>(v);
+    B->tpart = a.take<double>(2 * task_off[n]);
+    B->alphas = a.take<double>((size_t)n * B->hist);
+    B->betas = a.take<double>((size_t)n * B->hist);
+    B->rt2 = a.take<double>(n);
+    B->cg = a.take<CGScalars>(n);
+    B->heads = a.take<int>(kGraphIters + 8);
+    B->status = a.take<DevStatus>(1);
+  };
+  layout(A);
+  GENEO_CUDA_TRY(cudaMalloc(&B->mem, A.off + 256));
+  Arena D;
+  D.base = (char *)B->mem;
+  D.cap = A.off + 256;
+  layout(D);
+  B->T.n = n;
+  B->T.ntask = task_off[n];
+  B->T.nnodeblk = node_off[n];
+  B->T.nsub_items = (int)sub_items.size();
+  B->T.nchunk_items = (int)chunk_items.size();
+  B->T.nrow_items = (int)row_items.size();
+  cudaStream_t s = B->stream;
+  GENEO_CUDA_TRY(cudaMemcpyAsync(B->d_inst, B->inst.data(), n * sizeof(BatchInst), cudaMemcpyHostToDevice, s));
+  GENEO_CUDA_TRY(cudaMemcpyAsync((void *)B->T.task_off, task_off.data(), (n + 1) * sizeof(long long), cudaMemcpyHostToDevice, s));
+  GENEO_CUDA_TRY(cudaMemcpyAsync((void *)B->T.node_off, node_off.data(), (n + 1) * sizeof(long long), cudaMemcpyHostToDevice, s));
+  GENEO_CUDA_TRY(cudaMemcpyAsync((void *)B->T.sub_items, sub_items.data(), sub_items.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+  if (!chunk_items.empty())
+    GENEO_CUDA_TRY(cudaMemcpyAsync((void *)B->T.chunk_items, chunk_items.data(), chunk_items.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+  if (!row_items.empty())
+    GENEO_CUDA_TRY(cudaMemcpyAsync((void *)B->T.row_items, row_items.data(), row_items.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+  for (int i = 0; i < n; ++i)                 // the tuner's right-hand sides
+    GENEO_CUDA_TRY(cudaMemcpyAsync(B->b + B->vbase[i], B->ctx[i]->b, B->ctx[i]->ndof * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  GENEO_CUDA_TRY(cudaMemsetAsync(B->status, 0, sizeof(DevStatus), s));
+  GENEO_CUDA_TRY(cudaMemsetAsync(B->cg, 0, n * sizeof(CGScalars), s));
+  GENEO_CUDA_TRY(cudaMallocHost(&B->cg_host, n * sizeof(CGScalars)));
+  int st;
+  if (f32) {
+    if ((st = prepare_batch_schwarz<float>(B->npad_max, B->w_max))) return st;
+  } else {
+    if ((st = prepare_batch_schwarz<double>(B->npad_max, B->w_max))) return st;
+  }
+  int sms = 0;
+  GENEO_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  B->blocks = std::max(1, std::min(sms, B->T.nsub_items));
+  // batch autotuner: the one-CTA launch shapes of the local solves, timed on
+  // the batch's own items (rhs = b, every instance running); GENEO_SCHWARZ_ROWS
+  // and GENEO_SCHWARZ_STAGED pin a dimension
+  const int fr = env_choice("GENEO_SCHWARZ_ROWS", {0, 1});
+  const int fs = env_choice("GENEO_SCHWARZ_STAGED", {0, 1});
+  std::vector<std::pair<int, int>> cand;
+  for (int R : {0, 1})
+    for (int Sg : {1, 0}) {
+      if ((fr >= 0 && R != fr) || (fs >= 0 && Sg != fs)) continue;
+      const bool fits = f32 ? batch_schwarz_fits<float>(B->npad_max, B->w_max, R, Sg)
+                            : batch_schwarz_fits<double>(B->npad_max, B->w_max, R, Sg);
+      if (fits) cand.push_back({R, Sg});
+    }
+  if (cand.empty()) return fail(GENEO_ERR_INVALID_ARG, "no batched local-solve shape fits");
+  B->rows = cand[0].first;
+  B->staged = cand[0].second;
+  if (cand.size() > 1) {
+    cudaEvent_t e0, e1;
+    GENEO_CUDA_TRY(cudaEventCreate(&e0));
+    GENEO_CUDA_TRY(cudaEventCreate(&e1));
+    float best = 1e30f;
+    std::pair<int, int> pick = cand[0];
+    for (const auto &cd : cand) {
+      B->rows = cd.first;
+      B->staged = cd.second;
+      for (int rep = 0; rep < 3; ++rep) {         // one warm-up, two timed applications
+        if (rep == 1) GENEO_CUDA_TRY(cudaEventRecord(e0, s));
+        if ((st = batch_precond(B, B->b, B->z, kGraphIters, s))) return st;
+      }
+      GENEO_CUDA_TRY(cudaEventRecord(e1, s));
+      GENEO_CUDA_TRY(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      GENEO_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      B->ms_tune += ms;
+      if (ms < best) {
+        best = ms;
+        pick = cd;
+      }
+    }
+    B->rows = pick.first;
+    B->staged = pick.second;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if ((st = batch_check_status(B))) return st;
+  }
+  guard.b = nullptr;
+  *out = B;
+  return GENEO_OK;
+}
+
+extern "C" int geneo_batch_solve(geneo_batch *B, double tol, int max_it, double *const *u,
+                                 geneo_stats *stats) {
+  if (!B) return fail(GENEO_ERR_INVALID_ARG, "null batch");
+  if (!(tol > 0.0) || max_it < 1) return fail(GENEO_ERR_INVALID_ARG, "bad solve arguments");
+  cudaStream_t s = B->stream;
+  const int n = B->n;
+  for (int i = 0; i < n; ++i) {
+    CGScalars h{};
+    h.tol2 = tol * tol;
+    h.maxit = std::min(max_it, kHistCap);
+    h.flexible = B->inst[i].flexible;
+    B->cg_host[i] = h;
+  }
+  cudaEvent_t e0, e1;
+  GENEO_CUDA_TRY(cudaEventCreate(&e0));
+  GENEO_CUDA_TRY(cudaEventCreate(&e1));
+  GENEO_CUDA_TRY(cudaEventRecord(e0, s));
+  for (int i = 0; i < n; ++i) {               // each context's current right-hand side
+    GENEO_CUDA_TRY(cudaStreamSynchronize(B->ctx[i]->stream));
+    GENEO_CUDA_TRY(cudaMemcpyAsync(B->b + B->vbase[i], B->ctx[i]->b, B->ctx[i]->ndof * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  GENEO_CUDA_TRY(cudaMemcpyAsync(B->cg, B->cg_host, n * sizeof(CGScalars), cudaMemcpyHostToDevice, s));
+  launch_batch_init(B->d_inst, B->T, B->b, B->x, B->r, B->tpart, s);
+  launch_batch_reduce(B->d_inst, B->T, B->cg, B->tpart, 0, nullptr, nullptr, 0, nullptr, s);
+  int st;
+  if ((st = batch_precond(B, B->r, B->z, kGraphIters, s))) return st;
+  launch_batch_init2(B->d_inst, B->T, B->cg, B->r, B->z, B->p, B->tpart, s);
+  launch_batch_reduce(B->d_inst, B->T, B->cg, B->tpart, 1, nullptr, nullptr, 0, nullptr, s);
+  GENEO_CUDA_TRY(cudaGetLastError());
+  if (!B->graph) {
+    cudaGraph_t g;
+    GENEO_CUDA_TRY(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal));
+    g_counting = false;
+    const long long before = g_thread_launches;
+    st = batch_iterations(B, kGraphIters, B->cap);
+    B->graph_kernels = g_thread_launches - before;
+    g_counting = true;
+    cudaError_t ce = cudaStreamEndCapture(B->cap, &g);
+    if (st) return st;
+    if (ce != cudaSuccess) {
+      geneo_set_last_cuda_error(ce, "cudaStreamEndCapture", __FILE__, __LINE__);
+      return GENEO_ERR_CUDA;
+    }
+    GENEO_CUDA_TRY(cudaGraphInstantiate(&B->graph, g, 0));
+    cudaGraphDestroy(g);
+  }
+  int launched = 0, maxit = std::min(max_it, kHistCap);
+  for (;;) {
+    GENEO_CUDA_TRY(cudaGraphLaunch(B->graph, s));
+    g_launch_count.fetch_add(B->graph_kernels);
+    launched += kGraphIters;
+    GENEO_CUDA_TRY(cudaMemcpyAsync(B->cg_host, B->cg, n * sizeof(CGScalars), cudaMemcpyDeviceToHost, s));
+    GENEO_CUDA_TRY(cudaStreamSynchronize(s));
+    bool all = true;
+    for (int i = 0; i < n && all; ++i) all = B->cg_host[i].done != 0;
+    if (all || launched > maxit + 2 * kGraphIters) break;
+    if ((st = batch_check_status(B))) return fail(st, "device status set during the batched iteration");
+  }
+  if ((st = batch_check_status(B))) return fail(st, "device status set during the batched iteration");
+  GENEO_CUDA_TRY(cudaEventRecord(e1, s));
+  // true residuals ||b - A x|| per instance
+  launch_batch_residual(B->d_inst, B->T, B->x, B->b, B->tpart, s);
+  launch_batch_reduce(B->d_inst, B->T, B->cg, B->tpart, 5, nullptr, nullptr, 0, B->rt2, s);
+  std::vector<double> rt2(n);
+  GENEO_CUDA_TRY(cudaMemcpyAsync(rt2.data(), B->rt2, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  GENEO_CUDA_TRY(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  GENEO_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int worst = GENEO_OK;
+  for (int i = 0; i < n; ++i) {
+    geneo_ctx *c = B->ctx[i];
+    if (u && u[i]) {
+      cudaMemcpyKind k = is_device_ptr(u[i]) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+      GENEO_CUDA_TRY(cudaMemcpyAsync(u[i], B->x + B->vbase[i], c->ndof * sizeof(double), k, s));
+    }
+    const CGScalars &h = B->cg_host[i];
+    geneo_stats o{};
+    o.iterations = h.it;
+    o.rel_res_recursive = h.bb > 0 ? std::sqrt(h.rr / h.bb) : 0.0;
+    o.rel_res_true = h.bb > 0 ? std::sqrt(rt2[i] / h.bb) : 0.0;
+    o.n_coarse = c->pc.nH;
+    o.n_subdomains = c->pc.nsub;
+    o.ms_assemble = c->ms_assemble;
+    o.ms_setup_eig = c->pc.ms_eig;
+    o.ms_setup_coarse = c->pc.ms_coarse;
+    o.ms_setup_factor = c->pc.ms_factor;
+    o.ms_solve = ms;
+    o.failed_subdomain = -1;
+    o.flexible = B->inst[i].flexible;
+    o.eig_cycles = c->pc.eig_cycles;
+    o.lanczos_steps = c->pc.lanczos_steps;
+    o.schwarz_cluster = 1;
+    o.schwarz_rows = B->rows;
+    o.schwarz_staged = B->staged;
+    if (!o.flexible && h.it > 0) {
+      const int k = std::min(h.it, B->hist);
+      std::vector<double> al(k), be(std::max(k - 1, 0));
+      GENEO_CUDA_TRY(cudaMemcpyAsync(al.data(), B->alphas + (size_t)i * B->hist, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+      if (k > 1)
+        GENEO_CUDA_TRY(cudaMemcpyAsync(be.data(), B->betas + (size_t)i * B->hist, (k - 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+      GENEO_CUDA_TRY(cudaStreamSynchronize(s));
+      o.kappa_est = kappa_from_cg(al, be);
+    }
+    if (stats) stats[i] = o;
+    const int code = h.done == 1 ? GENEO_OK
+                     : h.done == 2 ? GENEO_ERR_CG_BREAKDOWN : GENEO_ERR_NOT_CONVERGED;
+    if (code && !worst) worst = code;
+  }
+  GENEO_CUDA_TRY(cudaStreamSynchronize(s));
+  if (worst) return fail(worst, worst == GENEO_ERR_CG_BREAKDOWN ? "CG breakdown in an instance"
+                                                                : "max_it reached by an instance");
+  return GENEO_OK;
+}
+
+extern "C" int geneo_batch_destroy(geneo_batch *B) {
+  batch_free(B);
   return GENEO_OK;
 }

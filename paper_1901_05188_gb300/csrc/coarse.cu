@@ -6,6 +6,7 @@
 #include <algorithm>
 
 #include "band.cuh"
+#include "batch.cuh"
 
 namespace geneo {
 
@@ -65,16 +66,16 @@ __global__ void k_gather_map(int nnx, int nny, int nnz, int px, int py,
 
 // z = sum_j R_j^T (D_j x_j + (Z y)_j), one thread per node, deterministic order.
 template <typename T>
-__global__ void __launch_bounds__(256)
-    k_schwarz_gather(int nnx, int nny, int nnz, int px, int py, const int *__restrict__ cand,
-                     int co0, int co1, int co2, const SubDesc *subs,
-                     const int *__restrict__ gmap, const uint8_t *__restrict__ gcnt,
-                     const T *__restrict__ xloc, const double *__restrict__ zy, int pou,
-                     const double *__restrict__ wloc, const uint8_t *__restrict__ mask,
-                     double *__restrict__ z, const CGScalars *cg) {
-  if (cg && cg->done) return;
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= nnx * nny * nnz) return;
+__device__ __forceinline__ void gather_node(int n, int nnx, int nny, int px, int py,
+                                            const int *__restrict__ cand, int co0, int co1,
+                                            int co2, const SubDesc *subs,
+                                            const int *__restrict__ gmap,
+                                            const uint8_t *__restrict__ gcnt,
+                                            const T *__restrict__ xloc,
+                                            const double *__restrict__ zy, int pou,
+                                            const double *__restrict__ wloc,
+                                            const uint8_t *__restrict__ mask,
+                                            double *__restrict__ z) {
   const int nc = subs[0].nc;
   double o[3] = {0.0, 0.0, 0.0};
   const int cnt = gcnt[n];
@@ -107,6 +108,21 @@ __global__ void __launch_bounds__(256)
   for (int comp = 0; comp < nc; ++comp) z[nc * n + comp] = o[comp];
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_schwarz_gather(int nnx, int nny, int nnz, int px, int py, const int *__restrict__ cand,
+                     int co0, int co1, int co2, const SubDesc *subs,
+                     const int *__restrict__ gmap, const uint8_t *__restrict__ gcnt,
+                     const T *__restrict__ xloc, const double *__restrict__ zy, int pou,
+                     const double *__restrict__ wloc, const uint8_t *__restrict__ mask,
+                     double *__restrict__ z, const CGScalars *cg) {
+  if (cg && cg->done) return;
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nnx * nny * nnz) return;
+  gather_node<T>(n, nnx, nny, px, py, cand, co0, co1, co2, subs, gmap, gcnt, xloc, zy, pou,
+                 wloc, mask, z);
+}
+
 // Coarse restriction and prolongation stream Z_j (row-major n_int x m_j) in
 // blocks of kZRows rows: the block's m_j * kZRows contiguous values are loaded
 // with coalesced loads, all in flight at once, into shared memory.
@@ -119,13 +135,11 @@ __device__ __forceinline__ double restrict_r(const SubDesc &S, const double *__r
 }
 
 // partial w_{j,k} over rows [kZRows b, kZRows (b + 1)): warp g takes rows g, g + 8, ..., lane k
-__global__ void __launch_bounds__(256) k_coarse_restrict(const SubDesc *subs, int nnx, int nny,
-                                                         const double *__restrict__ Zp,
-                                                         const double *__restrict__ r,
-                                                         double *__restrict__ wpart, int nchunk,
-                                                         int mcap, const CGScalars *cg) {
-  if (cg && cg->done) return;
-  const int j = blockIdx.y, b = blockIdx.x;
+__device__ __forceinline__ void coarse_restrict_block(const SubDesc *subs, int j, int b, int nnx,
+                                                      int nny, const double *__restrict__ Zp,
+                                                      const double *__restrict__ r,
+                                                      double *__restrict__ wpart, int nchunk,
+                                                      int mcap) {
   const SubDesc &S = subs[j];
   const int m = S.m, l0 = b * kZRows;
   if (m == 0 || l0 >= S.n_int) return;
@@ -152,17 +166,23 @@ __global__ void __launch_bounds__(256) k_coarse_restrict(const SubDesc *subs, in
   }
 }
 
+__global__ void __launch_bounds__(256) k_coarse_restrict(const SubDesc *subs, int nnx, int nny,
+                                                         const double *__restrict__ Zp,
+                                                         const double *__restrict__ r,
+                                                         double *__restrict__ wpart, int nchunk,
+                                                         int mcap, const CGScalars *cg) {
+  if (cg && cg->done) return;
+  coarse_restrict_block(subs, blockIdx.y, blockIdx.x, nnx, nny, Zp, r, wpart, nchunk, mcap);
+}
+
 // zy_j = Z_j y_j on rows [kZRows b, kZRows (b + 1)) of subdomain j (rows padded
 // to m + 1 values in shared memory against bank conflicts)
-__global__ void __launch_bounds__(256) k_coarse_prolong(const SubDesc *subs,
-                                                        const double *__restrict__ Zp,
-                                                        const double *__restrict__ yH,
-                                                        double *__restrict__ zy,
-                                                        const CGScalars *cg) {
-  if (cg && cg->done) return;
-  const int j = blockIdx.y;
+__device__ __forceinline__ void coarse_prolong_block(const SubDesc *subs, int j, int b,
+                                                     const double *__restrict__ Zp,
+                                                     const double *__restrict__ yH,
+                                                     double *__restrict__ zy) {
   const SubDesc &S = subs[j];
-  const int m = S.m, l0 = blockIdx.x * kZRows;
+  const int m = S.m, l0 = b * kZRows;
   if (l0 >= S.n_int) return;
   const int rows = min(kZRows, S.n_int - l0);
   if (m == 0) {
@@ -193,13 +213,20 @@ __global__ void __launch_bounds__(256) k_coarse_prolong(const SubDesc *subs,
   }
 }
 
-// w_{j,k} = sum of the row-block partials: warp g adds blocks g, g + 8, ...
-__global__ void __launch_bounds__(256) k_coarse_reduce(const SubDesc *subs,
-                                                       const double *__restrict__ wpart,
-                                                       double *__restrict__ wH, int nchunk,
-                                                       int mcap, const CGScalars *cg) {
+__global__ void __launch_bounds__(256) k_coarse_prolong(const SubDesc *subs,
+                                                        const double *__restrict__ Zp,
+                                                        const double *__restrict__ yH,
+                                                        double *__restrict__ zy,
+                                                        const CGScalars *cg) {
   if (cg && cg->done) return;
-  const int j = blockIdx.x;
+  coarse_prolong_block(subs, blockIdx.y, blockIdx.x, Zp, yH, zy);
+}
+
+// w_{j,k} = sum of the row-block partials: warp g adds blocks g, g + 8, ...
+__device__ __forceinline__ void coarse_reduce_block(const SubDesc *subs, int j,
+                                                    const double *__restrict__ wpart,
+                                                    double *__restrict__ wH, int nchunk,
+                                                    int mcap) {
   const SubDesc &S = subs[j];
   const int k = threadIdx.x & 31, g = threadIdx.x >> 5, m = S.m;
   __shared__ double acc[8][32];
@@ -216,6 +243,79 @@ __global__ void __launch_bounds__(256) k_coarse_reduce(const SubDesc *subs,
     for (int q = 0; q < 8; ++q) u += acc[q][k];
     wH[S.coff + k] = u;
   }
+}
+
+__global__ void __launch_bounds__(256) k_coarse_reduce(const SubDesc *subs,
+                                                       const double *__restrict__ wpart,
+                                                       double *__restrict__ wH, int nchunk,
+                                                       int mcap, const CGScalars *cg) {
+  if (cg && cg->done) return;
+  coarse_reduce_block(subs, blockIdx.x, wpart, wH, nchunk, mcap);
+}
+
+// ---- the same steps over the instances of a batch ------------------------------
+__global__ void __launch_bounds__(256) k_batch_restrict(const BatchInst *inst, const int4 *items,
+                                                        const CGScalars *cg,
+                                                        const double *__restrict__ r) {
+  const int4 it = items[blockIdx.x];
+  if (cg[it.x].done) return;
+  const BatchInst &B = inst[it.x];
+  coarse_restrict_block(B.subs, it.y, it.z, B.nnx, B.nny, B.Zp, r + B.vbase, B.wpart, B.nchunk,
+                        B.mcap);
+}
+
+__global__ void __launch_bounds__(256) k_batch_reduce_w(const BatchInst *inst, const int2 *items,
+                                                        const CGScalars *cg) {
+  const int2 it = items[blockIdx.x];
+  const BatchInst &B = inst[it.x];
+  if (cg[it.x].done || B.nH == 0) return;
+  coarse_reduce_block(B.subs, it.y, B.wpart, B.wH, B.nchunk, B.mcap);
+}
+
+// y = A_H^-1 w per instance, one warp per coarse row
+__global__ void __launch_bounds__(256) k_batch_gemv(const BatchInst *inst, const int2 *items,
+                                                    int nitems, const CGScalars *cg) {
+  const int lane = threadIdx.x & 31;
+  const int wi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (wi >= nitems) return;
+  const int2 it = items[wi];
+  if (cg[it.x].done) return;
+  const BatchInst &B = inst[it.x];
+  const double *a = B.AHinv + (long long)it.y * B.nH;
+  double s = 0.0;
+  for (int c = lane; c < B.nH; c += 32) s += a[c] * B.wH[c];
+  s = warp_sum(s);
+  if (lane == 0) B.yH[it.y] = s;
+}
+
+__global__ void __launch_bounds__(256) k_batch_prolong(const BatchInst *inst, const int4 *items,
+                                                       const CGScalars *cg) {
+  const int4 it = items[blockIdx.x];
+  if (cg[it.x].done) return;
+  const BatchInst &B = inst[it.x];
+  coarse_prolong_block(B.subs, it.y, it.z, B.Zp, B.yH, B.zy);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_batch_gather(const BatchInst *inst, const long long *off,
+                                                      int n, const CGScalars *cg,
+                                                      double *__restrict__ z) {
+  // block b covers nodes [256 (b - off[i]), ...) of the instance i it belongs to
+  const long long b = blockIdx.x;
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  const int i = lo;
+  if (cg[i].done) return;
+  const BatchInst &B = inst[i];
+  const int node = (int)(b - off[i]) * 256 + threadIdx.x;
+  if (node >= B.nnode) return;
+  gather_node<T>(node, B.nnx, B.nny, B.px, B.py, B.cand, B.co0, B.co1, B.co2, B.subs, B.gmap,
+                 B.gcnt, (const T *)B.xloc, B.nH > 0 ? B.zy : nullptr, B.pou, B.wloc, B.mask,
+                 z + B.vbase);
 }
 
 // y = AHinv w, one warp per row (AHinv symmetric, row-major)
@@ -476,6 +576,25 @@ int launch_coarse_apply_iterative(const SubDesc *d_subs, int nsub, int max_nint,
   GENEO_COUNT_LAUNCH();
   k_coarse_prolong<<<dim3(nchunk, nsub), 256, 0, s>>>(d_subs, Zp, yH, zy, cg); GENEO_COUNT_LAUNCH();
   return GENEO_OK;
+}
+
+void launch_batch_coarse(const BatchInst *inst, const BatchTables &T, const CGScalars *cg,
+                         const double *r, cudaStream_t s) {
+  if (T.nchunk_items == 0) return;
+  k_batch_restrict<<<T.nchunk_items, 256, 0, s>>>(inst, T.chunk_items, cg, r); GENEO_COUNT_LAUNCH();
+  k_batch_reduce_w<<<T.nsub_items, 256, 0, s>>>(inst, T.sub_items, cg); GENEO_COUNT_LAUNCH();
+  k_batch_gemv<<<(T.nrow_items * 32 + 255) / 256, 256, 0, s>>>(inst, T.row_items, T.nrow_items,
+                                                               cg); GENEO_COUNT_LAUNCH();
+  k_batch_prolong<<<T.nchunk_items, 256, 0, s>>>(inst, T.chunk_items, cg); GENEO_COUNT_LAUNCH();
+}
+
+void launch_batch_gather(const BatchInst *inst, const BatchTables &T, const CGScalars *cg,
+                         bool f32, double *z, cudaStream_t s) {
+  if (f32) {
+    k_batch_gather<float><<<(unsigned)T.nnodeblk, 256, 0, s>>>(inst, T.node_off, T.n, cg, z); GENEO_COUNT_LAUNCH();
+  } else {
+    k_batch_gather<double><<<(unsigned)T.nnodeblk, 256, 0, s>>>(inst, T.node_off, T.n, cg, z); GENEO_COUNT_LAUNCH();
+  }
 }
 
 void launch_gather_map(int nx, int ny, int nz, int px, int py, const int *cand,

@@ -4,6 +4,9 @@
 // partial sum, and the last block to finish (ticket counter) adds the
 // partials in a fixed order and updates the CG scalars on the device, so the
 // iteration runs without host round trips and can be captured in a graph.
+#include <algorithm>
+
+#include "batch.cuh"
 #include "kernels.cuh"
 
 namespace geneo {
@@ -274,7 +277,253 @@ __global__ void k_sub(int n, const double *__restrict__ a, const double *__restr
   for (int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT) out[i] = a[i] - b[i];
 }
 
+// ---- batched steps over many instances ---------------------------------------
+// A warp task is 32 consecutive scalar rows of one instance; task t belongs to
+// the instance i with task_off[i] <= t < task_off[i + 1].  Every lane of a
+// warp shares the task, so the instance and its `done` flag are warp-uniform.
+// The per-task partial sums are added per instance by k_batch_reduce in a
+// fixed order.
+
+__device__ __forceinline__ int find_inst(const long long *off, int n, long long t) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= t) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Calls f(B, i, row, global index) for this warp's rows; writes the two warp
+// sums of the values f returns (a, b) as the task's partials.
+template <bool SkipDone, typename F>
+__device__ __forceinline__ void batch_rows(const BatchInst *inst, const long long *off, int n,
+                                           long long ntask, const CGScalars *cg, double *tpart,
+                                           F f) {
+  const int lane = threadIdx.x & 31;
+  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long t = w0; t < ntask; t += nw) {
+    const int i = find_inst(off, n, t);
+    if (SkipDone && cg[i].done) continue;
+    const BatchInst &B = inst[i];
+    const int row = (int)(t - off[i]) * 32 + lane;
+    double a = 0.0, b = 0.0;
+    if (row < B.ndof) f(B, i, row, B.vbase + row, a, b);
+    a = warp_sum(a);
+    b = warp_sum(b);
+    if (tpart && lane == 0) {
+      tpart[2 * t] = a;
+      tpart[2 * t + 1] = b;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_batch_init(const BatchInst *inst, const long long *off,
+                                                    int n, long long ntask,
+                                                    const double *__restrict__ b,
+                                                    double *__restrict__ x,
+                                                    double *__restrict__ r, double *tpart) {
+  batch_rows<false>(inst, off, n, ntask, nullptr, tpart,
+                    [&](const BatchInst &, int, int, long long g, double &a, double &) {
+                      const double bi = b[g];
+                      x[g] = 0.0;
+                      r[g] = bi;
+                      a = bi * bi;
+                    });
+}
+
+__global__ void __launch_bounds__(256) k_batch_init2(const BatchInst *inst, const long long *off,
+                                                     int n, long long ntask, const CGScalars *cg,
+                                                     const double *__restrict__ r,
+                                                     const double *__restrict__ z,
+                                                     double *__restrict__ p, double *tpart) {
+  batch_rows<true>(inst, off, n, ntask, cg, tpart,
+                   [&](const BatchInst &, int, int, long long g, double &a, double &) {
+                     const double zi = z[g];
+                     p[g] = zi;
+                     a = r[g] * zi;
+                   });
+}
+
+__global__ void __launch_bounds__(256) k_batch_spmv_pq(const BatchInst *inst, const long long *off,
+                                                       int n, long long ntask,
+                                                       const CGScalars *cg,
+                                                       const double *__restrict__ p,
+                                                       double *__restrict__ q, double *tpart) {
+  batch_rows<true>(inst, off, n, ntask, cg, tpart,
+                   [&](const BatchInst &B, int, int row, long long g, double &a, double &) {
+                     const double *pb = p + B.vbase;
+                     double y;
+                     if (B.nc == 3) {
+                       const int node = row / 3;
+                       y = spmv_lane_row<3>(B.row_ptr, B.col, B.val, pb, node, row - 3 * node);
+                     } else {
+                       y = spmv_lane_row<1>(B.row_ptr, B.col, B.val, pb, row, 0);
+                     }
+                     q[g] = y;
+                     a = pb[row] * y;
+                   });
+}
+
+__global__ void __launch_bounds__(256) k_batch_residual(const BatchInst *inst,
+                                                        const long long *off, int n,
+                                                        long long ntask,
+                                                        const double *__restrict__ x,
+                                                        const double *__restrict__ bv,
+                                                        double *tpart) {
+  batch_rows<false>(inst, off, n, ntask, nullptr, tpart,
+                    [&](const BatchInst &B, int, int row, long long g, double &a, double &) {
+                      const double *xb = x + B.vbase;
+                      double y;
+                      if (B.nc == 3) {
+                        const int node = row / 3;
+                        y = spmv_lane_row<3>(B.row_ptr, B.col, B.val, xb, node, row - 3 * node);
+                      } else {
+                        y = spmv_lane_row<1>(B.row_ptr, B.col, B.val, xb, row, 0);
+                      }
+                      const double d = bv[g] - y;
+                      a = d * d;
+                    });
+}
+
+__global__ void __launch_bounds__(256) k_batch_update_xr(const BatchInst *inst,
+                                                         const long long *off, int n,
+                                                         long long ntask, const CGScalars *cg,
+                                                         const double *__restrict__ p,
+                                                         const double *__restrict__ q,
+                                                         double *__restrict__ x,
+                                                         double *__restrict__ r, double *tpart) {
+  batch_rows<true>(inst, off, n, ntask, cg, tpart,
+                   [&](const BatchInst &, int i, int, long long g, double &a, double &) {
+                     const double alpha = cg[i].alpha;
+                     x[g] += alpha * p[g];
+                     const double ri = r[g] - alpha * q[g];
+                     r[g] = ri;
+                     a = ri * ri;
+                   });
+}
+
+__global__ void __launch_bounds__(256) k_batch_dots(const BatchInst *inst, const long long *off,
+                                                    int n, long long ntask, const CGScalars *cg,
+                                                    const double *__restrict__ r,
+                                                    const double *__restrict__ z,
+                                                    const double *__restrict__ q,
+                                                    double *tpart) {
+  batch_rows<true>(inst, off, n, ntask, cg, tpart,
+                   [&](const BatchInst &, int, int, long long g, double &a, double &b) {
+                     const double zi = z[g];
+                     a = r[g] * zi;
+                     b = zi * q[g];
+                   });
+}
+
+__global__ void __launch_bounds__(256) k_batch_update_p(const BatchInst *inst,
+                                                        const long long *off, int n,
+                                                        long long ntask, const CGScalars *cg,
+                                                        const double *__restrict__ z,
+                                                        double *__restrict__ p) {
+  batch_rows<true>(inst, off, n, ntask, cg, nullptr,
+                   [&](const BatchInst &, int i, int, long long g, double &, double &) {
+                     p[g] = z[g] + cg[i].beta * p[g];
+                   });
+}
+
+// One block per instance: the instance's task partials in a fixed order,
+// then the scalar update of the step (the same rules as the single-system
+// kernels above).
+__global__ void __launch_bounds__(NT) k_batch_reduce(const long long *off, CGScalars *cgs,
+                                                     const double *tpart, int kind,
+                                                     double *alphas, double *betas, int hist,
+                                                     double *out) {
+  __shared__ double sh[32];
+  const int i = blockIdx.x;
+  CGScalars *cg = cgs + i;
+  if (kind >= 1 && kind <= 4 && cg->done) return;
+  double a = 0.0, b = 0.0;
+  for (long long t = off[i] + threadIdx.x; t < off[i + 1]; t += NT) {
+    a += tpart[2 * t];
+    b += tpart[2 * t + 1];
+  }
+  a = block_sum<NT>(a, sh);
+  b = block_sum<NT>(b, sh);
+  if (threadIdx.x != 0) return;
+  if (kind == 0) {
+    cg->bb = a;
+    cg->rr = a;
+    cg->it = 0;
+    cg->done = (a == 0.0) ? 1 : 0;
+  } else if (kind == 1) {
+    cg->rz = a;
+    if (!(a == a)) cg->done = 2;
+  } else if (kind == 2) {
+    cg->pq = a;
+    if (!(a > 0.0)) cg->done = 2;
+    else cg->alpha = cg->rz / a;
+  } else if (kind == 3) {
+    cg->rr = a;
+    const int it = cg->it;
+    if (alphas && it < hist) alphas[(long long)i * hist + it] = cg->alpha;
+    cg->it = it + 1;
+    if (!(a == a)) cg->done = 2;
+    else if (a <= cg->tol2 * cg->bb) cg->done = 1;
+    else if (it + 1 >= cg->maxit) cg->done = 3;
+  } else if (kind == 4) {
+    const double beta = cg->flexible ? -b / cg->pq : a / cg->rz;
+    if (!(beta == beta) || !(a == a)) cg->done = 2;
+    cg->beta = beta;
+    cg->zq = b;
+    if (betas && cg->it - 1 < hist) betas[(long long)i * hist + cg->it - 1] = beta;
+    cg->rz = a;
+  } else if (out) {
+    out[i] = a;
+  }
+}
+
 }  // namespace
+
+static unsigned batch_grid(long long ntask) {
+  const long long blocks = (ntask + 7) / 8;          // 8 warps per block, one task each
+  return (unsigned)std::max(1LL, std::min(blocks, (long long)NB * 8));
+}
+
+void launch_batch_init(const BatchInst *inst, const BatchTables &T, const double *b, double *x,
+                       double *r, double *tpart, cudaStream_t s) {
+  k_batch_init<<<batch_grid(T.ntask), 256, 0, s>>>(inst, T.task_off, T.n, T.ntask, b, x, r, tpart); GENEO_COUNT_LAUNCH();
+}
+void launch_batch_init2(const BatchInst *inst, const BatchTables &T, const CGScalars *cg,
+                        const double *r, const double *z, double *p, double *tpart,
+                        cudaStream_t s) {
+  k_batch_init2<<<batch_grid(T.ntask), 256, 0, s>>>(inst, T.task_off, T.n, T.ntask, cg, r, z, p, tpart); GENEO_COUNT_LAUNCH();
+}
+void launch_batch_spmv_pq(const BatchInst *inst, const BatchTables &T, const CGScalars *cg,
+                          const double *p, double *q, double *tpart, cudaStream_t s) {
+  k_batch_spmv_pq<<<batch_grid(T.ntask), 256, 0, s>>>(inst, T.task_off, T.n, T.ntask, cg, p, q, tpart); GENEO_COUNT_LAUNCH();
+}
+void launch_batch_update_xr(const BatchInst *inst, const BatchTables &T, const CGScalars *cg,
+                            const double *p, const double *q, double *x, double *r,
+                            double *tpart, cudaStream_t s) {
+  k_batch_update_xr<<<batch_grid(T.ntask), 256, 0, s>>>(inst, T.task_off, T.n, T.ntask, cg, p, q, x, r, tpart); GENEO_COUNT_LAUNCH();
+}
+void launch_batch_dots(const BatchInst *inst, const BatchTables &T, const CGScalars *cg,
+                       const double *r, const double *z, const double *q, double *tpart,
+                       cudaStream_t s) {
+  k_batch_dots<<<batch_grid(T.ntask), 256, 0, s>>>(inst, T.task_off, T.n, T.ntask, cg, r, z, q, tpart); GENEO_COUNT_LAUNCH();
+}
+void launch_batch_update_p(const BatchInst *inst, const BatchTables &T, const CGScalars *cg,
+                           const double *z, double *p, cudaStream_t s) {
+  k_batch_update_p<<<batch_grid(T.ntask), 256, 0, s>>>(inst, T.task_off, T.n, T.ntask, cg, z, p); GENEO_COUNT_LAUNCH();
+}
+void launch_batch_residual(const BatchInst *inst, const BatchTables &T, const double *x,
+                           const double *a, double *tpart, cudaStream_t s) {
+  k_batch_residual<<<batch_grid(T.ntask), 256, 0, s>>>(inst, T.task_off, T.n, T.ntask, x, a, tpart); GENEO_COUNT_LAUNCH();
+}
+void launch_batch_reduce(const BatchInst *inst, const BatchTables &T, CGScalars *cg,
+                         const double *tpart, int kind, double *alphas, double *betas,
+                         int hist, double *out, cudaStream_t s) {
+  (void)inst;
+  k_batch_reduce<<<T.n, NT, 0, s>>>(T.task_off, cg, tpart, kind, alphas, betas, hist, out); GENEO_COUNT_LAUNCH();
+}
 
 void launch_spmv(const BSR &A, const double *x, double *y, cudaStream_t s) {
   if (A.nc == 1) {

@@ -28,6 +28,7 @@
 #include <cooperative_groups.h>
 
 #include "band.cuh"
+#include "batch.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -1163,6 +1164,103 @@ __global__ void __launch_bounds__(kClWarps * 32, 1)
   cluster.sync();                          // no CTA leaves while others may still write to it
 }
 
+// ---- local solves of a batch of instances: one persistent launch ---------------
+// Every CTA takes (instance, subdomain) items from a device work queue (the
+// items are ordered largest local solve first, so the long ones start early
+// and the short ones fill the tail) and runs the one-CTA form of the sweep the
+// batch autotuner chose: look-ahead (R = 0) or one row per step (R = 1),
+// tiles from global memory or staged in shared memory by bulk copies (St).
+// The mbarriers of the staged forms are initialised once per CTA and their
+// phase count carries over from item to item, as from the forward to the
+// backward sweep.
+template <typename T, int R, int St, bool kSC>
+__global__ void __launch_bounds__(kClWarps * 32, 1)
+    k_schwarz_batch(const BatchInst *inst, const CGScalars *cgs, const int2 *items, int nitems,
+                    int *head, const double *__restrict__ r, int stride, DevStatus *status) {
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int RR = R > 0 ? R : 1;
+  __shared__ int s_item;
+  T *stages = nullptr, *red, *chn, *part, *y;
+  uint64_t *mbar = nullptr, *mbx = nullptr;
+  if constexpr (St) {
+    stages = reinterpret_cast<T *>(smraw);
+    mbar = reinterpret_cast<uint64_t *>(stages + kStages * stride);
+    mbx = mbar + kStages;
+    red = reinterpret_cast<T *>(mbx + kXBuf);
+    chn = red + kClWarps * RR * 32;
+    part = chn + 2 * kChain * RR * 32;
+    y = part + kXBuf * RR * 32;
+    if (threadIdx.x == 0) {
+      for (int b = 0; b < kStages + kXBuf; ++b)
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_addr(mbar + b)) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+  } else if constexpr (R == 0) {
+    red = reinterpret_cast<T *>(smraw);   // [2][kClWarps - kChain][32]
+    chn = red + 2 * (kClWarps - kChain) * 32;
+    part = chn + 2 * kChain * 32;
+    y = part + 2 * 32;
+  } else {
+    red = reinterpret_cast<T *>(smraw);   // [kClWarps][R][32]
+    chn = red + kClWarps * R * 32;
+    part = chn + 2 * kChain * R * 32;
+    y = part + 2 * R * 32;
+  }
+  cluster.sync();
+  uint32_t seq = 0;
+  bool dead = false;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(head, 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();                       // every thread has read the item before the next fetch
+    if (it >= nitems) break;
+    const int2 w = items[it];
+    if (cgs[w.x].done) continue;
+    const BatchInst &B = inst[w.x];
+    const SubDesc &S = B.subs[w.y];
+    const BandLayout L = B.lay[w.y];
+    const T *poolL = static_cast<const T *>(B.facL), *poolU = static_cast<const T *>(B.facU);
+    const double *rb = r + B.vbase;
+    const int n = S.n_int, npad = L.nt * 32, nc = S.nc;
+    for (int l = threadIdx.x; l < npad; l += blockDim.x) {
+      T v = T(0);
+      if (l < n) {
+        const int node = l / nc, comp = l - nc * node;
+        int gi, gj, gk;
+        S.ibox.global(node, gi, gj, gk);
+        v = T(rb[nc * (gi + B.nnx * (gj + B.nny * gk)) + comp]);
+      }
+      y[l] = v;
+    }
+    cluster.sync();
+    if constexpr (St) {
+      if constexpr (R == 0) {
+        cluster_sweep_staged_la<T, 1, kSC>(poolL, 0, L, y, red, chn, part, false, stages, stride,
+                                           mbar, mbx, seq, dead, status, w.y);
+        cluster_sweep_staged_la<T, 1, kSC>(poolU, 0, L, y, red, chn, part, true, stages, stride,
+                                           mbar, mbx, seq, dead, status, w.y);
+      } else {
+        cluster_sweep_staged<T, 1, R>(poolL, 0, L, y, red, chn, part, false, stages, stride, mbar,
+                                      mbx, seq, dead, status, w.y);
+        cluster_sweep_staged<T, 1, R>(poolU, 0, L, y, red, chn, part, true, stages, stride, mbar,
+                                      mbx, seq, dead, status, w.y);
+      }
+    } else if constexpr (R == 0) {
+      cluster_sweep_la<T, 1>(cluster, poolL, L, y, red, chn, part, false);
+      cluster.sync();
+      cluster_sweep_la<T, 1>(cluster, poolU, L, y, red, chn, part, true);
+    } else {
+      cluster_sweep<T, 1, R>(cluster, poolL, L, y, red, chn, part, false);
+      cluster_sweep<T, 1, R>(cluster, poolU, L, y, red, chn, part, true);
+    }
+    T *out = static_cast<T *>(B.xloc) + S.v_int;
+    for (int l = threadIdx.x; l < n; l += blockDim.x) out[l] = y[l];
+    cluster.sync();                        // y and the buffers are reused by the next item
+  }
+}
+
 template <typename T>
 int smem_bytes(int npad, int C, int R) {
   if (R == 0) return ((2 * (kClWarps - kChain) + 2 * kChain + 2 * C) * 32 + npad) * (int)sizeof(T);
@@ -1314,6 +1412,97 @@ int launch_schwarz_solve(const SubDesc *d_subs, const BandLayout *d_lay, int nsu
     default: return launch_c<T, 1>(rows, staged, d_subs, d_lay, nsub, npad_max, w_max, nnx, nny, poolL, poolU, r, xloc, cgs, status, s);
   }
 }
+
+// ---- batch launchers -----------------------------------------------------------
+template <typename T>
+static long long batch_smem(int npad_max, int w_max, int rows, int staged, int *stride,
+                            int *stage_chain) {
+  *stride = 0;
+  *stage_chain = 0;
+  if (!staged) return smem_bytes<T>(npad_max, 1, rows);
+  const int tiles = staged_tiles<T>(npad_max, w_max, 1, rows, stage_chain);
+  *stride = tiles * 1024;
+  return smem_bytes_staged_t<T>(npad_max, tiles, 1, rows);
+}
+
+template <typename T>
+bool batch_schwarz_fits(int npad_max, int w_max, int rows, int staged) {
+  if (rows < 0 || rows > 1) return false;
+  int st, sc;
+  return batch_smem<T>(npad_max, w_max, rows, staged, &st, &sc) <= kSmemMax;
+}
+
+template <typename T>
+int prepare_batch_schwarz(int npad_max, int w_max) {
+  int st, stride, sc;
+  long long b;
+  if ((b = batch_smem<T>(npad_max, w_max, 0, 0, &stride, &sc)) <= kSmemMax &&
+      (st = ensure_smem(k_schwarz_batch<T, 0, 0, false>, (int)b)))
+    return st;
+  if ((b = batch_smem<T>(npad_max, w_max, 1, 0, &stride, &sc)) <= kSmemMax &&
+      (st = ensure_smem(k_schwarz_batch<T, 1, 0, false>, (int)b)))
+    return st;
+  if ((b = batch_smem<T>(npad_max, w_max, 0, 1, &stride, &sc)) <= kSmemMax) {
+    if ((st = ensure_smem(k_schwarz_batch<T, 0, 1, false>, (int)b))) return st;
+    if ((st = ensure_smem(k_schwarz_batch<T, 0, 1, true>, (int)b))) return st;
+  }
+  if ((b = batch_smem<T>(npad_max, w_max, 1, 1, &stride, &sc)) <= kSmemMax &&
+      (st = ensure_smem(k_schwarz_batch<T, 1, 1, false>, (int)b)))
+    return st;
+  return GENEO_OK;
+}
+
+template <typename T>
+int launch_batch_schwarz(const BatchInst *inst, const CGScalars *cg, const int2 *items,
+                         int nitems, int *head, const double *r, int npad_max, int w_max,
+                         int rows, int staged, int blocks, DevStatus *status, cudaStream_t s) {
+  int stride, sc;
+  const long long sm = batch_smem<T>(npad_max, w_max, rows, staged, &stride, &sc);
+  if (sm > kSmemMax || rows < 0 || rows > 1) return GENEO_ERR_INVALID_ARG;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(kClWarps * 32);
+  cfg.dynamicSmemBytes = (size_t)sm;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 1;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (staged) {
+    if (rows == 0 && sc) {
+      GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_schwarz_batch<T, 0, 1, true>, inst, cg, items,
+                                        nitems, head, r, stride, status));
+    } else if (rows == 0) {
+      GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_schwarz_batch<T, 0, 1, false>, inst, cg, items,
+                                        nitems, head, r, stride, status));
+    } else {
+      GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_schwarz_batch<T, 1, 1, false>, inst, cg, items,
+                                        nitems, head, r, stride, status));
+    }
+  } else if (rows == 0) {
+    GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_schwarz_batch<T, 0, 0, false>, inst, cg, items,
+                                      nitems, head, r, stride, status));
+  } else {
+    GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_schwarz_batch<T, 1, 0, false>, inst, cg, items,
+                                      nitems, head, r, stride, status));
+  }
+  GENEO_COUNT_LAUNCH();
+  return GENEO_OK;
+}
+
+template bool batch_schwarz_fits<double>(int, int, int, int);
+template bool batch_schwarz_fits<float>(int, int, int, int);
+template int prepare_batch_schwarz<double>(int, int);
+template int prepare_batch_schwarz<float>(int, int);
+template int launch_batch_schwarz<double>(const BatchInst *, const CGScalars *, const int2 *, int,
+                                          int *, const double *, int, int, int, int, int,
+                                          DevStatus *, cudaStream_t);
+template int launch_batch_schwarz<float>(const BatchInst *, const CGScalars *, const int2 *, int,
+                                         int *, const double *, int, int, int, int, int,
+                                         DevStatus *, cudaStream_t);
 
 template int prepare_schwarz_solve<double>(int, int);
 template int prepare_schwarz_solve<float>(int, int);
