@@ -70,10 +70,17 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-darcy", action="store_true")
-    ap.add_argument("--batch-blocks", type=int, default=32,
+    ap.add_argument("--batch-blocks", type=int, default=256,
                     help="blocks of the uneven batched-solve workload to run (0 skips it)")
     ap.add_argument("--serve-requests", type=int, default=10,
                     help="requests of the serving sample (uneven laminate blocks)")
+    ap.add_argument("--serve-rates", default="0.5,0.8",
+                    help="Poisson arrival rates of the serving runs after the burst, as "
+                         "fractions of the burst's solves/s (comma-separated)")
+    ap.add_argument("--serve-darcy-grid", default=None, choices=[None, "spe10"],
+                    help="spe10: the stream's Darcy requests are the 60x220x85 SPE10 grid")
+    ap.add_argument("--serve-only", action="store_true",
+                    help="run only the serving stream and print its summary")
     return ap.parse_args()
 
 
@@ -440,6 +447,100 @@ def rooflines(pkg, s, st, args, peak, peak_kind):
     return cand
 
 
+def serving_leg(pkg, args):
+    """The continuous-batching server on a seeded stream of uneven requests:
+    a burst (saturated throughput), then Poisson arrivals at the given
+    fractions of the burst's solves/s; errors against the oracle's stored
+    solutions of the stream's small requests where they exist."""
+    from paper_1901_05188_gb300.serve import serve_benchmark
+    gpath = os.path.join(ROOT, "tests", "golden", "serving_oracle.json")
+    golden = None
+    if os.path.exists(gpath):
+        g = json.load(open(gpath))
+        if (g["n"], g["seed"], g["darcy_grid"]) == (args.serve_requests, 6, args.serve_darcy_grid):
+            golden = g["requests"]
+    rates = tuple(float(x) for x in args.serve_rates.split(",") if x.strip())
+    sv = serve_benchmark(n=args.serve_requests, seed=6, prec=pkg.GENEO_MIXED_FP32, slots=4,
+                         rate_factors=(None,) + rates, darcy_frac=0.3,
+                         darcy_grid=args.serve_darcy_grid, golden=golden)
+    dgrid = "the 60x220x85 SPE10 grid" if args.serve_darcy_grid == "spe10" else "SPE10 proportions"
+    return dict(workload=f"{sv['requests']} requests: {sv['requests'] - sv['darcy']} laminate "
+                         f"blocks and {sv['darcy']} Darcy problems (layered permeability, {dgrid}), "
+                         f"{min(sv['dofs'])}-{max(sv['dofs'])} unknowns (laminates log-uniform "
+                         f"2e4-2e6, seed 6), {sv['repeats']} repeated structures with new loads",
+                precision=sv["precision"], slots=sv["slots"],
+                runs=[{k: r[k] for k in ("arrivals", "n", "p50_ms", "p99_ms", "mean_ms",
+                                         "solves_per_s", "reused", "peak_inflight",
+                                         "peak_mem_gb", "failed", "oracle_checked",
+                                         "max_rel_err_vs_oracle") if k in r}
+                      for r in sv["runs"]])
+
+
+def batched_uneven(pkg, torch, dev, nblocks):
+    import concurrent.futures as cf
+    from paper_1901_05188_gb300.serve import request_memory
+    from workloads.batch import batch_blocks
+    prec = pkg.GENEO_MIXED_FP32
+    blocks = batch_blocks(nblocks, seed=3)
+    est = [request_memory(pb, prec) for pb in blocks]
+    budget = 0.5 * torch.cuda.mem_get_info(dev)[0]
+    waves, cur, used = [], [], 0
+    for k, e in enumerate(est):
+        if cur and used + e > budget:
+            waves.append(cur)
+            cur, used = [], 0
+        cur.append(k)
+        used += e
+    waves.append(cur)
+    streams = [torch.cuda.Stream(dev) for _ in range(4)]
+
+    def build(k, st):
+        with torch.cuda.stream(st):
+            sv = pkg.GeneoSolver(stream=st.cuda_stream, device=dev.index)
+            sv.assemble(blocks[k])
+            sv.setup(blocks[k], prec)
+        return sv
+
+    iters, failed, t_setup, t_solve, shapes = [], 0, 0.0, 0.0, set()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(4) as ex:
+        for wv in waves:
+            ta = time.perf_counter()
+            futs = [ex.submit(build, k, streams[i % 4]) for i, k in enumerate(wv)]
+            solvers = [f.result() for f in futs]
+            for st in streams:
+                st.synchronize()
+            tb = time.perf_counter()
+            bt = pkg.GeneoBatch(solvers)
+            outs = [torch.empty(sv.ndof, dtype=torch.float64, device=dev) for sv in solvers]
+            _, stats = bt.solve(tol=TOL, max_it=5000, outs=outs, raise_on_nonconvergence=False)
+            torch.cuda.synchronize(dev)
+            tc = time.perf_counter()
+            bt.close()
+            for sv in solvers:
+                sv.close()
+            t_setup += tb - ta
+            t_solve += tc - tb
+            iters += [st["iterations"] for st in stats]
+            failed += sum(1 for st in stats if not st["rel_res_recursive"] <= TOL)
+            shapes.add((stats[0]["schwarz_rows"], stats[0]["schwarz_staged"]))
+    wall = time.perf_counter() - t0
+    dofs = [3 * (pb["nx"] + 1) * (pb["ny"] + 1) * (pb["nz"] + 1) for pb in blocks]
+    parts = [pb["partition"][0] * pb["partition"][1] * pb["partition"][2] for pb in blocks]
+    return dict(workload=f"{len(blocks)} blocks of the seeded batch (seed 3): {min(dofs)}-{max(dofs)} "
+                         f"dofs ({sum(dofs)} in all), {min(parts)}-{max(parts)} subdomains "
+                         f"({sum(parts)} in all), 4-24 plies",
+                precision="mixed", waves=len(waves), wave_sizes=[len(w) for w in waves],
+                memory_budget_gb=budget / 1e9, wall_s=wall, setup_s=t_setup, batched_solve_s=t_solve,
+                solves_per_s=len(blocks) / wall, dofs_per_s=sum(dofs) / wall,
+                iterations=dict(min=min(iters), max=max(iters),
+                                mean=float(np.mean(iters))),
+                local_solve_shapes=sorted([dict(rows=r, staged=st) for r, st in shapes],
+                                          key=lambda d: (d["rows"], d["staged"])),
+                setup="four concurrent contexts", failed=failed)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -589,47 +690,17 @@ def run_ours(args):
     # continuous-batching server (burst, then Poisson at half its throughput)
     serving = None
     if rank == 0 and world == 1 and not args.no_serve and args.serve_requests > 0:
-        from paper_1901_05188_gb300.serve import serve_benchmark
-        sv = serve_benchmark(n=args.serve_requests, seed=6, prec=pkg.GENEO_MIXED_FP32, slots=4,
-                             rate_factors=(None, 0.5), darcy_frac=0.3)
-        serving = dict(workload=f"{sv['requests']} requests: {sv['requests'] - sv['darcy']} laminate "
-                                f"blocks and {sv['darcy']} Darcy blocks (layered permeability), "
-                                f"{min(sv['dofs'])}-{max(sv['dofs'])} unknowns (log-uniform 2e4-2e6, "
-                                f"seed 6), {sv['repeats']} repeated structures with new loads",
-                       precision=sv["precision"], slots=sv["slots"],
-                       runs=[{k: r[k] for k in ("arrivals", "n", "p50_ms", "p99_ms", "mean_ms",
-                                                "solves_per_s", "reused", "peak_inflight",
-                                                "peak_mem_gb", "failed") if k in r}
-                             for r in sv["runs"]])
+        serving = serving_leg(pkg, args)
 
-    # batched uneven solves: the first blocks of the seeded batch (8e3-1e5
-    # elements, 4-24 plies, 2-64 subdomains), all submitted at once to the
-    # concurrent-slot server (mixed precision), throughput and latency
+    # batched uneven solves: the seeded batch of laminated blocks (8e3-1e5
+    # elements, 4-24 plies, 2-64 subdomains), in waves that fit the device
+    # memory: each wave's instances are assembled and set up by four
+    # concurrent contexts, then solved together by one batched FCG (one
+    # launch per step over the wave, local solves in one persistent
+    # work-queue launch, iterations in a CUDA graph)
     batch = None
     if rank == 0 and world == 1 and args.batch_blocks > 0:
-        from paper_1901_05188_gb300.serve import GeneoServer, latency_summary
-        from workloads.batch import batch_blocks
-        blocks = batch_blocks(args.batch_blocks, seed=3)
-        srv = GeneoServer(slots=4)
-        try:
-            t0 = time.perf_counter()
-            reqs = [srv.submit(pb, prec=pkg.GENEO_MIXED_FP32, tol=TOL, key=pb["name"], arrival=t0)
-                    for pb in blocks]
-            for rq in reqs:
-                rq.wait()
-            wall = time.perf_counter() - t0
-        finally:
-            srv.close()
-        summ = latency_summary(reqs)
-        dofs = [3 * (pb["nx"] + 1) * (pb["ny"] + 1) * (pb["nz"] + 1) for pb in blocks]
-        parts = [pb["partition"][0] * pb["partition"][1] * pb["partition"][2] for pb in blocks]
-        batch = dict(workload=f"first {len(blocks)} blocks of the seeded batch (seed 3): "
-                              f"{min(dofs)}-{max(dofs)} dofs, {min(parts)}-{max(parts)} subdomains, "
-                              "4-24 plies, burst of independent solves",
-                     precision="mixed", slots=4, wall_s=wall,
-                     solves_per_s=len(blocks) / wall, dofs_per_s=sum(dofs) / wall,
-                     p50_ms=summ.get("p50_ms"), p99_ms=summ.get("p99_ms"),
-                     failed=summ.get("failed", len(blocks)))
+        batch = batched_uneven(pkg, torch, dev, args.batch_blocks)
 
     # the paper's second application at its full grid: Darcy on SPE10's 60x220x85
     # cells with a synthetic layered permeability (contrast 1.4e10), FP64
@@ -688,6 +759,13 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.serve_only:
+        import torch
+        import paper_1901_05188_gb300 as pkg
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        pkg.load(build_if_missing=True)
+        print(json.dumps(dict(serving=serving_leg(pkg, args))))
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -311,16 +311,20 @@ def run_poisson(server, problems, rate_hz, seed=0, prec=0, tol=1e-8, keys=None):
 
 
 def serve_benchmark(n=10, seed=4, prec=1, slots=4, rate_factors=(None, 0.5), tol=1e-8,
-                    dof_lo=2e4, dof_hi=2e6, warmup=True, darcy_frac=0.0):
+                    dof_lo=2e4, dof_hi=2e6, warmup=True, darcy_frac=0.0, darcy_grid=None,
+                    golden=None):
     """Serve a seeded request stream; one summary per arrival pattern.
 
     rate_factors: None = every request arrives at t = 0 (a burst, which gives
     the saturated throughput); a number f = Poisson arrivals at f times the
-    burst's solves/s.  Returns a dict with the stream description and the
-    summaries.
+    burst's solves/s.  golden: stored reference solutions of some requests of
+    this stream ({request index: summary with sample_stride, u_samples,
+    u_norm}); every run reports the largest relative error of those requests.
+    Returns a dict with the stream description and the summaries.
     """
     from workloads.serving import dofs_of, request_stream
-    base = request_stream(n, seed=seed, dof_lo=dof_lo, dof_hi=dof_hi, darcy_frac=darcy_frac)
+    base = request_stream(n, seed=seed, dof_lo=dof_lo, dof_hi=dof_hi, darcy_frac=darcy_frac,
+                          darcy_grid=darcy_grid)
     if warmup:   # load the library and build every kernel variant once
         from workloads import config
         w = GeneoServer(slots=1)
@@ -363,6 +367,19 @@ def serve_benchmark(n=10, seed=4, prec=1, slots=4, rate_factors=(None, 0.5), tol
         s["peak_inflight"] = srv.peak_inflight
         s["peak_mem_gb"] = srv.peak_mem / 1e9
         s["iterations"] = [int(r.stats.get("iterations", -1)) for r in reqs]
+        if golden:
+            errs = []
+            for i, r in enumerate(reqs):
+                g = golden.get(str(i))
+                if g is None or r.u is None:
+                    continue
+                ref = np.asarray(g["u_samples"])
+                us = np.asarray(r.u)[::g["sample_stride"]][:ref.size]
+                errs.append(float(np.linalg.norm(us - ref) / np.linalg.norm(ref)))
+            s["oracle_checked"] = len(errs)
+            s["max_rel_err_vs_oracle"] = max(errs) if errs else None
+        for r in reqs:
+            r.u = None                                   # results are not kept
         errs = [r.error for r in reqs if r.error]
         if errs:
             s["errors"] = errs[:3]

@@ -12,7 +12,10 @@ pressure), which the server can answer from resident factors.  With
 block (one unknown per node) with the layered permeability of
 `workloads.darcy`, the same log-uniform unknown count, SPE10-like 60:220:85
 proportions and an in-plane decomposition over the full height (about 10 x 12
-cells per subdomain, which keeps a subdomain's local vector in shared memory).  Arrival times are a Poisson process.
+cells per subdomain, which keeps a subdomain's local vector in shared memory);
+with `darcy_grid="spe10"` every new Darcy structure is instead the full
+60 x 220 x 85-cell SPE10 grid (1,159,366 unknowns, 6 x 18 subdomains) with its
+own seeded permeability.  Arrival times are a Poisson process.
 """
 from __future__ import annotations
 
@@ -48,7 +51,7 @@ def darcy_for_dofs(dofs, rng, name):
 
 
 def request_stream(n, seed=4, dof_lo=2e4, dof_hi=2e6, repeat_frac=0.25, rate_hz=None,
-                   darcy_frac=0.0):
+                   darcy_frac=0.0, darcy_grid=None):
     """n requests as (key, problem, arrival_offset_s).
 
     Without a rate every offset is 0 (a burst); with one, offsets are the
@@ -68,7 +71,11 @@ def request_stream(n, seed=4, dof_lo=2e4, dof_hi=2e6, repeat_frac=0.25, rate_hz=
             dofs = math.exp(rng.uniform(math.log(dof_lo), math.log(dof_hi)))
             key = f"s{i}"
             if darcy_frac > 0 and rng.random() < darcy_frac:
-                p = darcy_for_dofs(dofs, rng, key)
+                if darcy_grid == "spe10":
+                    p = make_darcy(60, 220, 85, seed=int(rng.integers(1 << 30)),
+                                   partition=(6, 18, 1, 1), name=key)
+                else:
+                    p = darcy_for_dofs(dofs, rng, key)
                 p["source"] = float(rng.uniform(0.5, 2.0))
             else:
                 p = block_for_dofs(dofs, rng, key)
