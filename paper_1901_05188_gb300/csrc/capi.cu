@@ -744,7 +744,7 @@ void plan_setup(Arena &A, geneo_ctx *c, const SetupPlan &P) {
   pc.facL = A.take<char>(pc.fac_int_elems * esz);
   pc.facU = A.take<char>(pc.fac_int_elems * esz);
   pc.xloc = A.take<char>(pc.xloc_elems * esz);
-  pc.wloc = pc.pou == GENEO_POU_SARKIS ? A.take<double>(pc.xloc_elems) : nullptr;
+  pc.wloc = A.take<double>(pc.xloc_elems);     // Sarkis weights (filled for that PoU only)
   int cap = pc.modes.fixed_modes > 0 ? pc.modes.fixed_modes : pc.modes.max_modes;
   if (pc.coarse == GENEO_COARSE_NONE) cap = 0;
   if (pc.coarse == GENEO_COARSE_ZEM) cap = 6;     // the rigid displacements
@@ -1281,7 +1281,6 @@ int geneo_estimate_workspace_bytes(const geneo_mesh *mesh, int unknowns_per_node
   tmp.nc = unknowns_per_node;
   tmp.ndof = tmp.nc * tmp.nnode;
   tmp.pc.prec = prec;
-  tmp.pc.pou = GENEO_POU_SARKIS;          // the larger of the two layouts
   SetupPlan P;
   if ((st = build_plan(&tmp, part, modes, P))) return st;
   size_t most = 0;
