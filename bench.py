@@ -462,7 +462,10 @@ def serving_leg(pkg, args):
     rates = tuple(float(x) for x in args.serve_rates.split(",") if x.strip())
     sv = serve_benchmark(n=args.serve_requests, seed=6, prec=pkg.GENEO_MIXED_FP32, slots=4,
                          rate_factors=(None,) + rates, darcy_frac=0.3,
-                         darcy_grid=args.serve_darcy_grid, golden=golden)
+                         darcy_grid=args.serve_darcy_grid, golden=golden,
+                         progress=lambda r: print(json.dumps({k: v for k, v in r.items()
+                                                              if k != "iterations"}),
+                                                  file=sys.stderr, flush=True))
     dgrid = "the 60x220x85 SPE10 grid" if args.serve_darcy_grid == "spe10" else "SPE10 proportions"
     return dict(workload=f"{sv['requests']} requests: {sv['requests'] - sv['darcy']} laminate "
                          f"blocks and {sv['darcy']} Darcy problems (layered permeability, {dgrid}), "

@@ -105,10 +105,20 @@ class GpuSlotExecutor:
             u, st = s.solve(tol=req.tol, max_it=5000)
         req.u, req.stats = u, st
 
+    def release(self, slot):
+        """Release the slot's resident problem and workspaces (the slot is idle)."""
+        s = self.solvers.pop(slot, None)
+        if s is not None:
+            self.streams[slot].synchronize()
+            s.close()
+            self.torch.cuda.empty_cache()
+
     def close(self):
-        for s in self.solvers.values():
+        for slot, s in self.solvers.items():
+            self.streams[slot].synchronize()
             s.close()
         self.solvers.clear()
+        self.torch.cuda.empty_cache()       # the next server sees the memory as free
 
 
 class GeneoServer:
@@ -147,6 +157,7 @@ class GeneoServer:
         self.peak_mem = 0
         self.peak_inflight = 0
         self.inflight = 0
+        self.evictions = 0
         self.dispatcher = threading.Thread(target=self._dispatch, daemon=True)
         self.dispatcher.start()
 
@@ -182,14 +193,21 @@ class GeneoServer:
         return True
 
     def _place(self, req):
-        """(slot, reuse) for the queue head, or None if it must wait.  Lock held."""
+        """(slot, reuse, evict) for the queue head, or None if it must wait.  Lock held.
+
+        evict lists idle slots whose resident workspaces must be released
+        first.  Without eviction a slot only grows to the request's size; when
+        that fits nowhere, the idle slots are released one at a time, the
+        largest first (the slot the request runs on is released first when
+        its own memory is not enough), until the request fits; when even
+        releasing every idle slot is not enough it waits for a busy slot."""
         idle = [s for s in range(self.nslots) if self.idle[s]]
         if not idle:
             return None
         if req.key is not None:
             for s in idle:
                 if self.slot_key[s] == (req.key, req.prec) and self.slot_mem[s] >= req.mem:
-                    return s, True
+                    return s, True, []
         total = self.mem_in_use
         best = None
         for s in idle:
@@ -198,9 +216,21 @@ class GeneoServer:
             rank = (self.slot_key[s] is not None, t, s)
             if t <= self.mem_budget and (best is None or rank < best[0]):
                 best = (rank, s)
-        if best is None:
+        if best is not None:
+            return best[1], False, []
+        # release idle slots, largest first, until the request fits on one of them
+        order = sorted(idle, key=lambda s: (-self.slot_mem[s], s))
+        target = order[0]
+        evict = [target]
+        t = total - self.slot_mem[target] + req.mem
+        for s in order[1:]:
+            if t <= self.mem_budget:
+                break
+            evict.append(s)
+            t -= self.slot_mem[s]
+        if t > self.mem_budget:
             return None
-        return best[1], False
+        return target, False, evict
 
     def _next(self):
         """(request, slot, reuse) to start now, or None.  Lock held.
@@ -233,8 +263,14 @@ class GeneoServer:
                     self.lock.wait(0.05)
                 if nxt is None:
                     return
-                req, slot, reuse = nxt
+                req, slot, reuse, evict = nxt
                 self.queue.remove(req)
+                for e in evict:                      # idle slots: nothing runs on them
+                    if hasattr(self.executor, "release"):
+                        self.executor.release(e)
+                    self.slot_mem[e] = 0
+                    self.slot_key[e] = None
+                    self.evictions += 1
                 self.idle[slot] = False
                 self.slot_mem[slot] = max(self.slot_mem[slot], req.mem)
                 self.slot_key[slot] = None if req.key is None else (req.key, req.prec)
@@ -312,12 +348,13 @@ def run_poisson(server, problems, rate_hz, seed=0, prec=0, tol=1e-8, keys=None):
 
 def serve_benchmark(n=10, seed=4, prec=1, slots=4, rate_factors=(None, 0.5), tol=1e-8,
                     dof_lo=2e4, dof_hi=2e6, warmup=True, darcy_frac=0.0, darcy_grid=None,
-                    golden=None):
+                    golden=None, progress=None):
     """Serve a seeded request stream; one summary per arrival pattern.
 
     rate_factors: None = every request arrives at t = 0 (a burst, which gives
     the saturated throughput); a number f = Poisson arrivals at f times the
-    burst's solves/s.  golden: stored reference solutions of some requests of
+    burst's solves/s; progress(summary) is called after every run.  golden:
+    stored reference solutions of some requests of
     this stream ({request index: summary with sample_stride, u_samples,
     u_norm}); every run reports the largest relative error of those requests.
     Returns a dict with the stream description and the summaries.
@@ -364,6 +401,7 @@ def serve_benchmark(n=10, seed=4, prec=1, slots=4, rate_factors=(None, 0.5), tol
         s = latency_summary(reqs)
         s["arrivals"] = "burst" if f is None else f"poisson {rate:.3g}/s"
         s["reused"] = sum(1 for r in reqs if r.reused)
+        s["evictions"] = srv.evictions
         s["peak_inflight"] = srv.peak_inflight
         s["peak_mem_gb"] = srv.peak_mem / 1e9
         s["iterations"] = [int(r.stats.get("iterations", -1)) for r in reqs]
@@ -386,6 +424,8 @@ def serve_benchmark(n=10, seed=4, prec=1, slots=4, rate_factors=(None, 0.5), tol
         if f is None:
             burst_rate = s.get("solves_per_s")
         out["runs"].append(s)
+        if progress:
+            progress(s)
     return out
 
 

@@ -3,7 +3,9 @@
 The executor records which requests overlap in time; the tests check FIFO
 admission, the device-memory budget (slots keep their largest workspace),
 reuse of a slot's resident problem by key, rejection of oversized requests,
-error isolation, and that a request is admitted while others still run.
+error isolation, that a request is admitted while others still run, and that
+idle slots' resident workspaces are released when a larger request would
+otherwise never fit (no deadlock once every slot has grown).
 """
 import threading
 import time
@@ -21,6 +23,7 @@ class FakeExecutor:
         self.running = set()
         self.overlaps = []          # (rid, set of rids running when it started)
         self.calls = []             # (slot, rid, reuse)
+        self.released = []          # (slot, rids running at the time)
 
     def __call__(self, slot, req, reuse):
         with self.lock:
@@ -35,6 +38,11 @@ class FakeExecutor:
             raise RuntimeError("planted failure")
         req.u = ("solution", req.problem["id"])
         req.stats = {"iterations": 1}
+
+
+    def release(self, slot):
+        with self.lock:
+            self.released.append((slot, set(self.running)))
 
 
 def mem_of(req):
@@ -176,3 +184,42 @@ def test_repeated_key_waits_for_its_resident_slot():
     assert a2.reused and a2.slot == a1.slot
     assert b.slot != a1.slot and not b.reused
     assert b.t_start < a2.t_start          # B went ahead of the waiting A
+
+
+def test_idle_slots_released_for_a_larger_request():
+    srv, ex = make_server(slots=2, budget=100)
+    first = [srv.submit({"id": i, "mem": 45}) for i in range(2)]
+    for r in first:
+        r.wait(5)
+    big = srv.submit({"id": 2, "mem": 70})      # 45 + 45 resident: fits only after releasing both
+    big.wait(5)
+    srv.close()
+    assert big.error is None
+    assert srv.evictions == 2
+    assert sorted(sl for sl, _ in ex.released) == [0, 1]
+    assert all(not running for _, running in ex.released)   # nothing ran on a released slot
+
+
+def test_no_deadlock_once_every_slot_has_grown():
+    srv, ex = make_server(slots=4, budget=100, duration=0.01)
+    sizes = [24, 24, 24, 24, 60, 24, 90, 30, 24, 50]
+    reqs = [srv.submit({"id": i, "mem": m}) for i, m in enumerate(sizes)]
+    for r in reqs:
+        r.wait(5)
+    srv.close()
+    assert all(r.error is None for r in reqs)
+    starts = [rid for rid, _ in ex.overlaps]
+    assert starts == sorted(starts)                      # still FIFO
+    assert srv.peak_mem <= 100
+
+
+def test_release_waits_for_busy_slots():
+    srv, ex = make_server(slots=2, budget=100, duration=0.2)
+    a = srv.submit({"id": 0, "mem": 60})
+    time.sleep(0.05)
+    b = srv.submit({"id": 1, "mem": 60})            # cannot start while a holds 60
+    for r in (a, b):
+        r.wait(5)
+    srv.close()
+    assert a.error is None and b.error is None
+    assert 1 not in ex.overlaps[0][1] and 0 not in ex.overlaps[1][1]
