@@ -159,7 +159,8 @@ def profiled_traffic(kernel, args):
     path = os.path.join(ROOT, "profiles", f"dram_{args.config}_{args.precision}.md")
     if not os.path.exists(path):
         return None
-    srcs = {"k_schwarz_cluster": "schwarz.cu", "k_band_solve_dense": "band.cu"}
+    srcs = {"k_schwarz_cluster": "schwarz.cu", "k_band_solve_dense": "band.cu",
+            "band_cholesky_neumann": "band.cu"}
     src = os.path.join(ROOT, "paper_1901_05188_gb300", "csrc", srcs.get(kernel, ""))
     h = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12] if os.path.isfile(src) else None
     for line in open(path):
@@ -635,6 +636,8 @@ def run_ours(args):
         for k in ("k_band_solve_dense", "k_schwarz_cluster"):
             if roof["kernel"].startswith(k):
                 roof["traffic"] = profiled_traffic(k, args)
+        if roof["kernel"].startswith("band Cholesky of S_j"):
+            roof["traffic"] = profiled_traffic("band_cholesky_neumann", args)
         roof.setdefault("traffic", None)
         ms_pc, by_pc, _ = pkg.geneo_profile(s.ctx, 2, 10)
         kernels = dict(precond_apply=dict(ms=ms_pc, gbs=by_pc / (ms_pc * 1e-3) / 1e9),
