@@ -498,7 +498,8 @@ def batched_uneven(pkg, torch, dev, nblocks):
         cur.append(k)
         used += e
     waves.append(cur)
-    streams = [torch.cuda.Stream(dev) for _ in range(4)]
+    nconc = 8
+    streams = [torch.cuda.Stream(dev) for _ in range(nconc)]
 
     def build(k, st):
         with torch.cuda.stream(st):
@@ -510,10 +511,10 @@ def batched_uneven(pkg, torch, dev, nblocks):
     iters, failed, t_setup, t_solve, shapes = [], 0, 0.0, 0.0, set()
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    with cf.ThreadPoolExecutor(4) as ex:
+    with cf.ThreadPoolExecutor(nconc) as ex:
         for wv in waves:
             ta = time.perf_counter()
-            futs = [ex.submit(build, k, streams[i % 4]) for i, k in enumerate(wv)]
+            futs = [ex.submit(build, k, streams[i % nconc]) for i, k in enumerate(wv)]
             solvers = [f.result() for f in futs]
             for st in streams:
                 st.synchronize()
@@ -544,7 +545,7 @@ def batched_uneven(pkg, torch, dev, nblocks):
                                 mean=float(np.mean(iters))),
                 local_solve_shapes=sorted([dict(rows=r, staged=st) for r, st in shapes],
                                           key=lambda d: (d["rows"], d["staged"])),
-                setup="four concurrent contexts", failed=failed)
+                setup=f"{nconc} concurrent contexts", failed=failed)
 
 
 def run_ours(args):
@@ -701,7 +702,7 @@ def run_ours(args):
 
     # batched uneven solves: the seeded batch of laminated blocks (8e3-1e5
     # elements, 4-24 plies, 2-64 subdomains), in waves that fit the device
-    # memory: each wave's instances are assembled and set up by four
+    # memory: each wave's instances are assembled and set up by eight
     # concurrent contexts, then solved together by one batched FCG (one
     # launch per step over the wave, local solves in one persistent
     # work-queue launch, iterations in a CUDA graph)
