@@ -81,6 +81,11 @@ def parse():
                     help="spe10: the stream's Darcy requests are the 60x220x85 SPE10 grid")
     ap.add_argument("--serve-only", action="store_true",
                     help="run only the serving stream and print its summary")
+    ap.add_argument("--profile-case", default=None, choices=["schwarz", "chol"],
+                    help="the small case the DRAM captures under profiles/ use: a 32x32x24 "
+                         "laminate in 2x2x2 subdomains of the 128x64x48 workload's size, set up "
+                         "in mixed precision, then the local solves (schwarz) or the band "
+                         "Cholesky of the shifted Neumann matrices (chol) through geneo_profile")
     return ap.parse_args()
 
 
@@ -765,8 +770,32 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def profile_case(args):
+    import paper_1901_05188_gb300 as pkg
+    from workloads.laminate import make_block
+    pkg.load(build_if_missing=True)
+    thr = dict(fixed_modes=0, threshold=0.0, max_modes=20, shift=-0.01)
+    p = make_block(32, 32, 24, [0.0, 45.0, -45.0, 90.0] * 3, partition=(2, 2, 2, 1), modes=thr,
+                   name="c3-subdomains-8")
+    s = pkg.GeneoSolver()
+    s.assemble(p)
+    s.setup(p, pkg.GENEO_MIXED_FP32)
+    out = {}
+    if args.profile_case == "schwarz":
+        ms, by, _ = pkg.geneo_profile(s.ctx, 0, 3)
+        out["schwarz"] = dict(ms=ms, bytes=by)
+    else:
+        ms, by, fl = pkg.geneo_profile(s.ctx, 4, 1)
+        out["chol_neumann"] = dict(ms=ms, bytes=by, flops=fl)
+    s.close()
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        profile_case(args)
+        return
     if args.serve_only:
         import torch
         import paper_1901_05188_gb300 as pkg
