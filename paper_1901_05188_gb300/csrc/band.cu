@@ -1,7 +1,8 @@
 // Band-tiled Cholesky factors of the one-level additive Schwarz term
 // sum_j R_j^T D_j A_j^-1 R_j  (Sec. 3.1, eqn:onelevelAS) and of the GenEO
-// shift-invert operators, their multi-right-hand-side sweeps, and the
-// extraction of A_j from the global matrix.  The coarse correction and the
+// shift-invert operators (whose multi-right-hand-side solves run the local
+// solves' look-ahead sweep), and the extraction of A_j from the global
+// matrix.  The coarse correction and the
 // gather are in coarse.cu, the cluster sweeps of the local solves in
 // schwarz.cu.
 //
@@ -193,98 +194,6 @@ __global__ void __launch_bounds__(256) k_chol_update(const BandLayout *lay, int 
   }
 }
 
-// ---- triangular sweeps -------------------------------------------------------
-
-// One sweep over the tile rows of a factored band system with the local
-// vector y in shared memory.  Forward: y_I <- inv(L_II)(y_I - sum_d L(I,I-d) y_{I-d});
-// backward: the same on the U stream with I descending and J = I + d.
-//
-// Warp w multiplies the tiles d = w+1, w+1+16, ... of the row; the per-row
-// chain (sum of the warps' partials, inverted diagonal block) runs on warps
-// 0..3, one per SM sub-partition, each taking 8 of the 32 columns, because on
-// this GPU a warp's dependent FP64 instructions are the critical path.
-constexpr int kChainW = 4;
-
-__device__ __forceinline__ void solve_chain_bar() {
-  asm volatile("bar.sync 1, %0;" ::"n"(kChainW * 32) : "memory");
-}
-
-template <typename T>
-__device__ __forceinline__ void band_sweep(const T *__restrict__ pool, const BandLayout &L,
-                                           T *y, T *red, T *chn, bool backward) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nt = L.nt, w = L.w;
-  int buf = 0;
-  for (int step = 0; step < nt; ++step) {
-    const int I = backward ? nt - 1 - step : step;
-    const int dmax = backward ? min(w, nt - 1 - I) : min(w, I);
-    T dv[8];
-    if (warp < kChainW) {                       // this warp's columns of inv(L_II), early
-      const T *D = tile_ptr(pool, L, I, 0) + warp * 256;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) dv[k] = __ldg(D + k * 32 + lane);
-    }
-    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-    for (int d = warp + 1; d <= dmax; d += kSolveWarps) {
-      const T *t = tile_ptr(pool, L, I, d);
-      const T *yJ = y + (backward ? (I + d) : (I - d)) * 32;
-#pragma unroll
-      for (int c = 0; c < 32; c += 4) {
-        a0 += __ldg(t + (c + 0) * 32 + lane) * yJ[c + 0];
-        a1 += __ldg(t + (c + 1) * 32 + lane) * yJ[c + 1];
-        a2 += __ldg(t + (c + 2) * 32 + lane) * yJ[c + 2];
-        a3 += __ldg(t + (c + 3) * 32 + lane) * yJ[c + 3];
-      }
-    }
-    red[warp * 32 + lane] = (a0 + a1) + (a2 + a3);
-    __syncthreads();
-    if (warp < kChainW) {
-      T pr = red[warp * 32 + lane];
-#pragma unroll
-      for (int k = warp + kChainW; k < kSolveWarps; k += kChainW) pr += red[k * 32 + lane];
-      T *cb = chn + (buf & 1) * (kChainW * 32);
-      cb[warp * 32 + lane] = pr;
-      solve_chain_bar();
-      ++buf;
-      const T s = y[I * 32 + lane] - (((cb[lane] + cb[32 + lane]) + cb[64 + lane]) + cb[96 + lane]);
-      T o0 = T(0), o1 = T(0);
-#pragma unroll
-      for (int k = 0; k < 8; k += 2) {
-        o0 += dv[k] * __shfl_sync(0xffffffffu, s, warp * 8 + k);
-        o1 += dv[k + 1] * __shfl_sync(0xffffffffu, s, warp * 8 + k + 1);
-      }
-      cb = chn + (buf & 1) * (kChainW * 32);
-      cb[warp * 32 + lane] = o0 + o1;
-      solve_chain_bar();
-      ++buf;
-      const T yI = ((cb[lane] + cb[32 + lane]) + cb[64 + lane]) + cb[96 + lane];
-      if (warp == 0) y[I * 32 + lane] = yI;
-    }
-    __syncthreads();
-  }
-}
-
-__global__ void __launch_bounds__(kSolveWarps * 32, 2)
-    k_band_solve_dense(const BandLayout *lay, const double *poolL, const double *poolU,
-                       const double *__restrict__ in, long long in_sys, int in_row,
-                       double *__restrict__ out, long long out_sys, int out_row, int mode) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  double *red = reinterpret_cast<double *>(smraw);     // [kSolveWarps][32]
-  double *chn = red + kSolveWarps * 32;                // [2][kChainW][32]
-  double *y = chn + 2 * kChainW * 32;
-  const int j = blockIdx.x, c = blockIdx.y;
-  const BandLayout L = lay[j];
-  const int n = L.n, npad = L.nt * 32;
-  const double *src = in + j * in_sys + c;
-  for (int l = threadIdx.x; l < npad; l += blockDim.x)
-    y[l] = l < n ? src[(long long)l * in_row] : 0.0;
-  __syncthreads();
-  if (mode & 1) band_sweep(poolL, L, y, red, chn, false);
-  if (mode & 2) band_sweep(poolU, L, y, red, chn, true);
-  double *dst = out + j * out_sys + c;
-  for (int l = threadIdx.x; l < n; l += blockDim.x) dst[(long long)l * out_row] = y[l];
-}
-
 // ---- extraction of A_j from the global BSR ----------------------------------
 
 template <typename T>
@@ -393,21 +302,15 @@ int launch_band_cholesky(const BandLayout *d_lay, int nsys, int nt_max, int w_ma
   return GENEO_OK;
 }
 
-static int solve_smem_bytes(int npad, size_t elem) {
-  return (int)((kSolveWarps * 32 + 2 * kChainW * 32 + npad) * elem);
-}
-
+// The GenEO eigensolver's multi-right-hand-side solves run the one-CTA
+// look-ahead sweep of the local solves (schwarz.cu), one CTA per (system,
+// right-hand side), the column in shared memory.
 int launch_band_solve_dense(const BandLayout *d_lay, int nsys, int npad_max,
                             const double *poolL, const double *poolU, const double *in,
                             long long in_sys, int in_row, double *out, long long out_sys,
                             int out_row, int ncols, int mode, cudaStream_t s) {
-  int sm = solve_smem_bytes(npad_max, sizeof(double));
-  if (sm > 227 * 1024) return GENEO_ERR_INVALID_ARG;
-  if (int st = ensure_smem(k_band_solve_dense, sm)) return st;
-  k_band_solve_dense<<<dim3(nsys, ncols), kSolveWarps * 32, sm, s>>>(
-      d_lay, poolL, poolU, in, in_sys, in_row, out, out_sys, out_row, mode); GENEO_COUNT_LAUNCH();
-  GENEO_CUDA_TRY(cudaGetLastError());
-  return GENEO_OK;
+  return launch_band_solve_la(d_lay, nsys, npad_max, poolL, poolU, in, in_sys, in_row, out,
+                              out_sys, out_row, ncols, mode, s);
 }
 
 template <typename T>

@@ -6,7 +6,6 @@
 
 namespace geneo {
 
-constexpr int kSolveWarps = 16;     // warps of a band-solve CTA
 
 // Zero a pool of tiles and put ones on the padded diagonal of every system.
 template <typename T>
@@ -31,6 +30,12 @@ int launch_band_solve_dense(const BandLayout *d_lay, int nsys, int npad_max,
                             const double *poolL, const double *poolU, const double *in,
                             long long in_sys, int in_row, double *out, long long out_sys,
                             int out_row, int ncols, int mode, cudaStream_t s);
+
+// The same solve with the one-CTA look-ahead sweep of the local solves.
+int launch_band_solve_la(const BandLayout *d_lay, int nsys, int npad_max, const double *poolL,
+                         const double *poolU, const double *in, long long in_sys, int in_row,
+                         double *out, long long out_sys, int out_row, int ncols, int mode,
+                         cudaStream_t s);
 
 // FP32 trailing update of tile column J on the tensor cores (3xTF32 tcgen05
 // MMAs, blocks of 4 x 4 tiles); part as for the band Cholesky's update

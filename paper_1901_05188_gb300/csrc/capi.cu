@@ -584,13 +584,14 @@ int build_plan(geneo_ctx *c, const geneo_partition *part, const geneo_modes *mod
   int p[3] = {part->px, part->py, part->pz};
   // block-Lanczos options: block steps per restart cycle (basis p * steps) and
   // the Ritz residual tolerance relative to the Ritz value.  A residual of
-  // 1e-6 theta bounds the eigenvalue error by about (1e-6)^2 / gap and the
-  // angle of an eigenvector by 1e-6 / gap, far below what the coarse space
-  // needs; 12 steps reach it in two cycles on the laminate workloads.
-  // GENEO_LANCZOS_STEPS (8..16, the projected eigensolver holds up to 128
-  // columns) and GENEO_EIG_TOL (1e-12..1e-4) override the defaults.
-  c->pc.ksteps = 12;
-  c->pc.eig_tol = 1e-6;
+  // 1e-5 theta bounds the eigenvalue error by about (1e-5 theta)^2 / gap and
+  // the angle of an eigenvector by 1e-5 theta / gap, far below what the coarse
+  // space needs; 10 steps per cycle reach it with the fewest band solves on
+  // the laminate workloads (the 128x64x48 set-up: 2.60 s against 2.84 s with
+  // 12 steps and 1e-6).  GENEO_LANCZOS_STEPS (8..16, the projected eigensolver
+  // holds up to 128 columns) and GENEO_EIG_TOL (1e-12..1e-4) override them.
+  c->pc.ksteps = 10;
+  c->pc.eig_tol = 1e-5;
   if (const char *e = std::getenv("GENEO_LANCZOS_STEPS")) {
     const int v = std::atoi(e);
     if (v >= 8 && v <= 16) c->pc.ksteps = v;

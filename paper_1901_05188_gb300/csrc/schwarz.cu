@@ -1164,6 +1164,35 @@ __global__ void __launch_bounds__(kClWarps * 32, 1)
   cluster.sync();                          // no CTA leaves while others may still write to it
 }
 
+// ---- the GenEO eigensolver's band solves in the look-ahead form ------------------
+// One CTA per (system, right-hand side): the column is loaded into shared
+// memory (row stride in_row), swept forward and/or backward with the
+// one-CTA look-ahead sweep above (far warps multiply row I+1 while the chain
+// warps finish row I), and written back (row stride out_row).
+__global__ void __launch_bounds__(kClWarps * 32)
+    k_band_solve_la(const BandLayout *lay, const double *poolL, const double *poolU,
+                    const double *__restrict__ in, long long in_sys, int in_row,
+                    double *__restrict__ out, long long out_sys, int out_row, int mode) {
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double *red = reinterpret_cast<double *>(smraw);   // [2][kClWarps - kChain][32]
+  double *chn = red + 2 * (kClWarps - kChain) * 32;   // [2][kChain][32]
+  double *part = chn + 2 * kChain * 32;               // [2][1][32]
+  double *y = part + 2 * 32;                          // [npad]
+  const int j = blockIdx.x, c = blockIdx.y;
+  const BandLayout L = lay[j];
+  const int n = L.n, npad = L.nt * 32;
+  const double *src = in + j * in_sys + c;
+  for (int l = threadIdx.x; l < npad; l += blockDim.x) y[l] = l < n ? src[(long long)l * in_row] : 0.0;
+  cluster.sync();
+  if (mode & 1) cluster_sweep_la<double, 1>(cluster, poolL, L, y, red, chn, part, false);
+  cluster.sync();
+  if (mode & 2) cluster_sweep_la<double, 1>(cluster, poolU, L, y, red, chn, part, true);
+  cluster.sync();
+  double *dst = out + j * out_sys + c;
+  for (int l = threadIdx.x; l < n; l += blockDim.x) dst[(long long)l * out_row] = y[l];
+}
+
 // ---- local solves of a batch of instances: one persistent launch ---------------
 // Every CTA takes (instance, subdomain) items from a device work queue (the
 // items are ordered largest local solve first, so the long ones start early
@@ -1411,6 +1440,31 @@ int launch_schwarz_solve(const SubDesc *d_subs, const BandLayout *d_lay, int nsu
     case 2: return launch_c<T, 2>(rows, staged, d_subs, d_lay, nsub, npad_max, w_max, nnx, nny, poolL, poolU, r, xloc, cgs, status, s);
     default: return launch_c<T, 1>(rows, staged, d_subs, d_lay, nsub, npad_max, w_max, nnx, nny, poolL, poolU, r, xloc, cgs, status, s);
   }
+}
+
+int launch_band_solve_la(const BandLayout *d_lay, int nsys, int npad_max, const double *poolL,
+                         const double *poolU, const double *in, long long in_sys, int in_row,
+                         double *out, long long out_sys, int out_row, int ncols, int mode,
+                         cudaStream_t s) {
+  const int sm = smem_bytes<double>(npad_max, 1, 0);
+  if (sm > kSmemMax) return GENEO_ERR_INVALID_ARG;
+  if (int st = ensure_smem(k_band_solve_la, sm)) return st;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nsys, ncols);
+  cfg.blockDim = dim3(kClWarps * 32);
+  cfg.dynamicSmemBytes = (size_t)sm;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 1;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_band_solve_la, d_lay, poolL, poolU, in, in_sys, in_row,
+                                    out, out_sys, out_row, mode));
+  GENEO_COUNT_LAUNCH();
+  return GENEO_OK;
 }
 
 // ---- batch launchers -----------------------------------------------------------

@@ -56,3 +56,22 @@ def check_against_golden(u, st, gold, coarse=None, u_tol=1e-6):
             got = lam[j, :k]
             assert np.all(np.abs(got - lref[:k]) <= 1e-7 * np.maximum(np.abs(lref[:k]), 1e-2)), j
     return err
+
+
+# The set-up's default Ritz acceptance: residual <= EIG_TOL * theta
+# (theta = mu = 1 / (lambda - sigma), the shift-invert eigenvalue).
+EIG_TOL = 1e-5
+
+
+def span_tolerance(modes, lambdas, shift, eig_tol=EIG_TOL):
+    """Largest angle the Ritz acceptance allows between the kept eigenvectors
+    and the exact ones: eig_tol * mu_k over the gap to the first dropped
+    mode, maximised over subdomains and kept modes (at least 1e-5), from the
+    oracle's eigenvalues."""
+    worst = 1e-5
+    for m, lam in zip(modes, lambdas):
+        lam = np.asarray(lam, dtype=float)
+        if 0 < m < lam.size and np.isfinite(lam[m]):
+            mu = 1.0 / (lam - shift)
+            worst = max(worst, max(eig_tol * mu[k] / (mu[k] - mu[m]) for k in range(m)))
+    return worst

@@ -6,7 +6,7 @@ aspect ratios up to 435), clamped at x = 0 under top pressure, split 2 x 2 in
 plane with overlap 1 and the threshold rule capped at 20 modes: the wanted
 GenEO eigenvalues crowd towards the overlap-localised modes, the case the
 oracle's sparse eigensolver pin covers.  Same tolerances as the other parity
-tests: eigenvalues 1e-7 relative, coarse span angles 1e-5, solution 1e-6
+tests: eigenvalues 1e-7 relative, coarse span angles within the Ritz acceptance's bound, solution 1e-6
 relative L2 with iterations within +-2 (FP64), and 1e-6 for the mixed
 precision solve at a tolerance of 1e-10; the true residual within twice the
 oracle's, which sits at the FP64 floor of b - A u for this system.  With the
@@ -24,7 +24,7 @@ import scipy.linalg as sla
 from oracle import decomp, fem, geneo, solver as osolver
 from workloads.laminate import make_block
 
-from gpu_common import rel, require_gpu
+from gpu_common import rel, require_gpu, span_tolerance
 
 pytestmark = pytest.mark.gpu
 
@@ -65,7 +65,8 @@ def test_plate_eigenvalues_and_span(pkg):
         assert np.all(np.abs(lam[j, :kk] - ref) <= 1e-7 * np.maximum(np.abs(ref), 1e-2)), j
     Phi, AH = s.coarse()
     assert Phi.shape[1] == nh == Zo.shape[1]
-    assert sla.subspace_angles(Phi, Zo.toarray()).max() < 1e-5
+    assert sla.subspace_angles(Phi, Zo.toarray()).max() <= span_tolerance(
+        [d["m"] for d in info], [d["lam"] for d in info], p["modes"]["shift"])
     s.close()
 
 

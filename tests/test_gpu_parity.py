@@ -4,7 +4,8 @@ Tolerances (FP64 path): assembly entries 1e-12 relative to max |A|, the load
 exactly up to rounding (1e-13); one preconditioner application 1e-9 relative
 (different but exact factorisations of the same SPD matrices); GenEO
 eigenvalues 1e-7 relative (Lanczos vs dense/ARPACK); coarse span principal
-angles 1e-5; solutions 1e-6 relative L2 with iteration counts within +-2.
+angles within the Ritz acceptance's bound (residual 1e-5 theta over the gap to the
+first dropped mode, at least 1e-5); solutions 1e-6 relative L2 with iteration counts within +-2.
 """
 import numpy as np
 import pytest
@@ -13,7 +14,7 @@ import scipy.linalg as sla
 import workloads
 from oracle import decomp, fem, geneo, krylov, solver as osolver
 
-from gpu_common import bsr_to_csr, rel, require_gpu
+from gpu_common import bsr_to_csr, rel, require_gpu, span_tolerance
 
 pytestmark = pytest.mark.gpu
 
@@ -142,7 +143,8 @@ def test_geneo_eigenvalues_and_span(pkg, name):
     assert Phi.shape[1] == nh == Zo.shape[1]
     if nh:
         ang = sla.subspace_angles(Phi, Zo.toarray())
-        assert ang.max() < 1e-5
+        assert ang.max() <= span_tolerance([d["m"] for d in info], [d["lam"] for d in info],
+                                           p["modes"]["shift"])
         # A_H = Phi^T A Phi (Sec. 3.3.3) for the GPU's own basis
         AHr = Phi.T @ (A @ Phi)
         assert np.abs(AH - AHr).max() <= 1e-10 * np.abs(AHr).max()

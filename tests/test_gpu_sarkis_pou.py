@@ -8,7 +8,8 @@ D_j = X_j.  With overlap 2 it differs from the multiplicity PoU (the weight
 ramps across the overlap), so the checks run there: B_j and S_j entry by
 entry (1e-12), the PoU-weighted one-level application (1e-9, also on a block
 whose nodes sit in up to nine subdomain interiors, gathered through the
-candidate lists), and GenEO-PCG (eigenvalues 1e-7, span angles 1e-5, u 1e-6,
+candidate lists), and GenEO-PCG (eigenvalues 1e-7, span angles within the Ritz
+acceptance's bound, u 1e-6,
 iterations +-2).  With overlap 1 the two PoUs are the same numbers, so the
 preconditioner applications are bit-identical.
 """
@@ -21,7 +22,7 @@ import workloads
 from oracle import decomp, fem, geneo, krylov, solver
 from workloads.laminate import make_block
 
-from gpu_common import rel, require_gpu
+from gpu_common import rel, require_gpu, span_tolerance
 
 pytestmark = pytest.mark.gpu
 
@@ -36,22 +37,6 @@ def overlap2(name):
         p["partition"] = tuple(p["partition"][:3]) + (2,)
     p["pou"] = "sarkis"
     return p
-
-
-def span_tolerance(p, ref):
-    """Largest angle the library's Ritz acceptance allows between a kept
-    eigenvector and the oracle's: a Ritz residual of at most 1e-6 theta
-    (theta = mu = 1 / (lambda - sigma)) over the gap to the first dropped mode,
-    max over subdomains and kept modes (at least 1e-5).  On the overlap-2
-    blocks the ramping weights bring dropped modes closer to the cut than on
-    the overlap-1 workloads."""
-    sig, worst = p["modes"]["shift"], 1e-5
-    for m, lam in zip(ref["modes"], ref["lambdas"]):
-        lam = np.asarray(lam)
-        if 0 < m < lam.size and np.isfinite(lam[m]):
-            mu = 1.0 / (lam - sig)
-            worst = max(worst, max(1e-6 * mu[k] / (mu[k] - mu[m]) for k in range(m)))
-    return worst
 
 
 @pytest.fixture(scope="module")
@@ -116,7 +101,8 @@ def test_sarkis_geneo_pcg_matches_oracle(pkg, name):
         assert np.all(np.abs(lam[j, :kk] - lo[:kk]) <= 1e-7 * np.maximum(np.abs(lo[:kk]), 1e-2)), j
     Phi, _ = s.coarse()
     Zo, _ = geneo.coarse_space(p, decomp.partition(p), ref["A"], "dense")
-    assert sla.subspace_angles(Phi, Zo.toarray()).max() <= span_tolerance(p, ref)
+    assert sla.subspace_angles(Phi, Zo.toarray()).max() <= span_tolerance(
+        ref["modes"], ref["lambdas"], p["modes"]["shift"])
     u, st = s.solve(tol=1e-8, max_it=2000)
     s.close()
     assert rel(u, ref["u"]) <= 1e-6
