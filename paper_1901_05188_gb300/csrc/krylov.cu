@@ -38,10 +38,10 @@ __device__ __forceinline__ double sum_partials(const double *part, int n, double
   return block_sum<NT>(v, sh);
 }
 
-// One lane per matrix row (the loop over a row's blocks unrolled three times and
-// the kernels limited to 32 registers so that 64 warps per SM keep loads in
-// flight: 1.46x faster than nine-fold unrolling at 40 registers on the
-// 128x64x48 workload; the few spilled registers stay in L1).
+// One lane per matrix row (the loop over a row's blocks not unrolled and the
+// kernels limited to 32 registers, so that 64 warps per SM keep the loads in
+// flight; measured on the 128x64x48 workload: 0.187 ms against 0.211 ms
+// unrolled three times and 0.308 ms unrolled nine times at 40 registers).
 // Lane i of warp group g holds scalar row 32g + i
 // (block row (32g + i) / NC, component (32g + i) % NC), so no lane idles; every
 // stored value takes exactly one FMA and no sum crosses lanes -- FP64 issue,
@@ -50,7 +50,7 @@ __device__ __forceinline__ double sum_partials(const double *part, int n, double
 // and the same x entries, so their loads share L1 lines; results go to
 // consecutive entries of y.
 
-template <int NC, int U = 3>
+template <int NC, int U = 1>
 __device__ __forceinline__ double spmv_lane_row(const int32_t *__restrict__ rp,
                                                 const int32_t *__restrict__ col,
                                                 const double *__restrict__ val,
