@@ -81,11 +81,12 @@ def parse():
                     help="spe10: the stream's Darcy requests are the 60x220x85 SPE10 grid")
     ap.add_argument("--serve-only", action="store_true",
                     help="run only the serving stream and print its summary")
-    ap.add_argument("--profile-case", default=None, choices=["schwarz", "chol"],
-                    help="the small case the DRAM captures under profiles/ use: a 32x32x24 "
+    ap.add_argument("--profile-case", default=None, choices=["schwarz", "chol", "spmv"],
+                    help="the small cases the ncu captures under profiles/ use: a 32x32x24 "
                          "laminate in 2x2x2 subdomains of the 128x64x48 workload's size, set up "
                          "in mixed precision, then the local solves (schwarz) or the band "
-                         "Cholesky of the shifted Neumann matrices (chol) through geneo_profile")
+                         "Cholesky of the shifted Neumann matrices (chol) through geneo_profile; "
+                         "spmv: five SpMVs of a 96x48x36 laminate (361 MB of BSR, above L2)")
     return ap.parse_args()
 
 
@@ -774,6 +775,21 @@ def profile_case(args):
     import paper_1901_05188_gb300 as pkg
     from workloads.laminate import make_block
     pkg.load(build_if_missing=True)
+    if args.profile_case == "spmv":
+        import torch
+        p = make_block(96, 48, 36, [0.0, 45.0, -45.0, 90.0] * 3, partition=(1, 1, 1, 1),
+                       name="spmv-96x48x36")
+        s = pkg.GeneoSolver()
+        s.assemble(p)
+        x = torch.ones(s.ndof, dtype=torch.float64, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(5):
+            pkg.geneo_spmv(s.ctx, x, y)
+        torch.cuda.synchronize()
+        print(json.dumps(dict(spmv_nnzb=s.nnzb, ndof=s.ndof,
+                              bsr_bytes=s.nnzb * 76 + 4 * (s.nnode + 1))))
+        s.close()
+        return
     thr = dict(fixed_modes=0, threshold=0.0, max_modes=20, shift=-0.01)
     p = make_block(32, 32, 24, [0.0, 45.0, -45.0, 90.0] * 3, partition=(2, 2, 2, 1), modes=thr,
                    name="c3-subdomains-8")
