@@ -2198,6 +2198,7 @@ struct geneo_batch {
   cudaGraphExec_t graph = nullptr;
   long long graph_kernels = 0;
   float ms_tune = 0.f;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;   // timing of a batched solve
 };
 
 namespace {
@@ -2256,6 +2257,8 @@ void batch_free(geneo_batch *B) {
   if (!B) return;
   if (B->stream) cudaStreamSynchronize(B->stream);
   if (B->graph) cudaGraphExecDestroy(B->graph);
+  if (B->ev0) cudaEventDestroy(B->ev0);
+  if (B->ev1) cudaEventDestroy(B->ev1);
   if (B->mem) cudaFree(B->mem);
   if (B->cg_host) cudaFreeHost(B->cg_host);
   if (B->cap) cudaStreamDestroy(B->cap);
@@ -2303,6 +2306,8 @@ extern "C" int geneo_batch_create(geneo_batch **out, geneo_ctx *const *ctxs, int
   B->stream = (cudaStream_t)cuda_stream;
   B->f32 = f32;
   GENEO_CUDA_TRY(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking));
+  GENEO_CUDA_TRY(cudaEventCreate(&B->ev0));
+  GENEO_CUDA_TRY(cudaEventCreate(&B->ev1));
   for (geneo_ctx *c : B->ctx) GENEO_CUDA_TRY(cudaStreamSynchronize(c->stream));
   // instances and work tables (host)
   std::vector<long long> task_off(n + 1, 0), node_off(n + 1, 0);
@@ -2452,9 +2457,7 @@ extern "C" int geneo_batch_create(geneo_batch **out, geneo_ctx *const *ctxs, int
   B->rows = cand[0].first;
   B->staged = cand[0].second;
   if (cand.size() > 1) {
-    cudaEvent_t e0, e1;
-    GENEO_CUDA_TRY(cudaEventCreate(&e0));
-    GENEO_CUDA_TRY(cudaEventCreate(&e1));
+    cudaEvent_t e0 = B->ev0, e1 = B->ev1;
     float best = 1e30f;
     std::pair<int, int> pick = cand[0];
     for (const auto &cd : cand) {
@@ -2476,8 +2479,6 @@ extern "C" int geneo_batch_create(geneo_batch **out, geneo_ctx *const *ctxs, int
     }
     B->rows = pick.first;
     B->staged = pick.second;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     if ((st = batch_check_status(B))) return st;
   }
   guard.b = nullptr;
@@ -2498,9 +2499,7 @@ extern "C" int geneo_batch_solve(geneo_batch *B, double tol, int max_it, double 
     h.flexible = B->inst[i].flexible;
     B->cg_host[i] = h;
   }
-  cudaEvent_t e0, e1;
-  GENEO_CUDA_TRY(cudaEventCreate(&e0));
-  GENEO_CUDA_TRY(cudaEventCreate(&e1));
+  cudaEvent_t e0 = B->ev0, e1 = B->ev1;
   GENEO_CUDA_TRY(cudaEventRecord(e0, s));
   for (int i = 0; i < n; ++i) {               // each context's current right-hand side
     GENEO_CUDA_TRY(cudaStreamSynchronize(B->ctx[i]->stream));
@@ -2553,8 +2552,6 @@ extern "C" int geneo_batch_solve(geneo_batch *B, double tol, int max_it, double 
   GENEO_CUDA_TRY(cudaStreamSynchronize(s));
   float ms = 0.f;
   GENEO_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   int worst = GENEO_OK;
   for (int i = 0; i < n; ++i) {
     geneo_ctx *c = B->ctx[i];
