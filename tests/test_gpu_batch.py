@@ -108,3 +108,27 @@ def test_batch_launch_shapes_agree(pkg, monkeypatch, rows, staged):
         ref = oracle(k, p, 1e-8)
         assert rel(u, ref["u"]) <= 1e-6, p.get("name")
         assert abs(st["iterations"] - ref["iterations"]) <= 2
+
+
+def test_batch_refuses_mixed_precisions_and_unsolved_contexts(pkg):
+    ps = instances()[:2]
+    a, b = _setup(pkg, ps[:1], 0)[0], _setup(pkg, ps[1:2], 1)[0]
+    with pytest.raises(pkg.GeneoError) as e:
+        pkg.GeneoBatch([a, b])
+    assert e.value.status == 1
+    c = pkg.GeneoSolver()
+    c.assemble(ps[1])                               # assembled, not set up
+    with pytest.raises(pkg.GeneoError) as e:
+        pkg.GeneoBatch([a, c])
+    assert "set up" in str(e.value)
+    with pytest.raises(pkg.GeneoError):
+        pkg.GeneoBatch([a, a])
+    d = pkg.GeneoSolver()
+    q = dict(ps[1], coarse_solver="cg")
+    d.assemble(q)
+    d.setup(q, 0)
+    with pytest.raises(pkg.GeneoError) as e:
+        pkg.GeneoBatch([a, d])
+    assert "direct coarse" in str(e.value)
+    for s in (a, b, c, d):
+        s.close()

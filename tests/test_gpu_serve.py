@@ -108,3 +108,25 @@ def test_memory_estimate_covers_bound_workspace():
                 s.close()
             # the estimate is the two workspaces; the binding adds 256 B of alignment each
             assert est + 512 >= bound >= est, (p["name"], prec, est, bound)
+
+
+def test_same_result_when_slots_are_released():
+    """A budget that holds one resident problem besides a new one forces the
+    server to release idle slots' workspaces (GpuSlotExecutor.release) between
+    requests; every result is still the one computed alone."""
+    pkg = require_gpu()
+    from paper_1901_05188_gb300.serve import GeneoServer, request_memory
+    probs = _problems()
+    alone = [_alone(pkg, p, 1) for _, p in probs]
+    need = max(request_memory(p, 1) for _, p in probs)
+    srv = GeneoServer(slots=2, mem_budget=int(1.2 * need))
+    try:
+        reqs = [srv.submit(p, prec=1, tol=1e-8, key=k) for k, p in probs]
+        for r in reqs:
+            r.wait(600)
+    finally:
+        srv.close()
+    assert srv.evictions > 0
+    for r, (ua, sa) in zip(reqs, alone):
+        assert r.error is None, r.error
+        assert np.array_equal(r.u, ua) and r.stats["iterations"] == sa["iterations"]
