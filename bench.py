@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--no-darcy", action="store_true")
     ap.add_argument("--batch-blocks", type=int, default=256,
                     help="blocks of the uneven batched-solve workload to run (0 skips it)")
+    ap.add_argument("--batch-concurrency", type=int, default=8,
+                    help="contexts that assemble and set up the batch's blocks concurrently")
     ap.add_argument("--serve-requests", type=int, default=10,
                     help="requests of the serving sample (uneven laminate blocks)")
     ap.add_argument("--serve-rates", default="0.5,0.8",
@@ -486,7 +488,7 @@ def serving_leg(pkg, args):
                       for r in sv["runs"]])
 
 
-def batched_uneven(pkg, torch, dev, nblocks):
+def batched_uneven(pkg, torch, dev, nblocks, nconc=8):
     import concurrent.futures as cf
     from paper_1901_05188_gb300.serve import request_memory
     from workloads.batch import batch_blocks
@@ -504,7 +506,6 @@ def batched_uneven(pkg, torch, dev, nblocks):
         cur.append(k)
         used += e
     waves.append(cur)
-    nconc = 8
     streams = [torch.cuda.Stream(dev) for _ in range(nconc)]
 
     def build(k, st):
@@ -714,7 +715,7 @@ def run_ours(args):
     # work-queue launch, iterations in a CUDA graph)
     batch = None
     if rank == 0 and world == 1 and args.batch_blocks > 0:
-        batch = batched_uneven(pkg, torch, dev, args.batch_blocks)
+        batch = batched_uneven(pkg, torch, dev, args.batch_blocks, args.batch_concurrency)
 
     # the paper's second application at its full grid: Darcy on SPE10's 60x220x85
     # cells with a synthetic layered permeability (contrast 1.4e10), FP64
