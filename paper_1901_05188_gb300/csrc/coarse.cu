@@ -29,8 +29,14 @@ __device__ __forceinline__ int for_node_subdomains(int i, int jj, int k, int px,
   while (nci < kMaxCand && ci[nci] >= 0) ++nci;
   while (ncj < kMaxCand && cj[ncj] >= 0) ++ncj;
   while (nck < kMaxCand && ck[nck] >= 0) ++nck;
+  // not unrolled: the candidate counts are small and the nest only serves the
+  // set-up's gather map and the rare nodes in more than eight interiors (fully
+  // unrolled, its 64 copies of `visit` made this file slow to compile)
+#pragma unroll 1
   for (int c = 0; c < nck; ++c)
+#pragma unroll 1
     for (int b = 0; b < ncj; ++b)
+#pragma unroll 1
       for (int a = 0; a < nci; ++a) {
         const SubDesc &S = subs[ci[a] + px * (cj[b] + py * ck[c])];
         const int l = S.ibox.local(i, jj, k);
