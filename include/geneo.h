@@ -154,7 +154,9 @@ typedef struct {
   int lanczos_steps;              /* block-Lanczos steps of the last set-up (two band sweeps each) */
   int schwarz_cluster;            /* CTAs per subdomain chosen for the local solves */
   int schwarz_rows;               /* tile rows per cluster barrier chosen for them */
-  int schwarz_staged;             /* 1 if their tiles are staged in shared memory by bulk copies */
+  int schwarz_staged;             /* 1 if their tiles are staged in shared memory by bulk copies,
+                                     2 if the local vector streams through a ring of tile rows
+                                     (subdomains whose local vector exceeds shared memory) */
   int coarse_inner_iterations;    /* inner PCG steps of the iterative coarse solve, summed over
                                      the solve's preconditioner applications (0 if direct) */
 } geneo_stats;
@@ -288,7 +290,10 @@ int geneo_spmv(geneo_ctx *ctx, const double *x, double *y);
  * GenEO eigenproblems A_{Omega_j} p = lambda X_j A_{Omega_j^o} X_j p by
  * shift-and-invert block Lanczos, coarse basis Z = [R_j^T X_j p_k], coarse
  * matrix A_H = Z^T A Z and its Cholesky factor, and the band Cholesky factors
- * of A_j = R_j A R_j^T in the requested precision. */
+ * of A_j = R_j A R_j^T in the requested precision.  Subdomain size is bounded
+ * by device memory only: a local vector too large for shared memory is
+ * streamed through it (GENEO_ERR_INVALID_ARG only for a half-bandwidth above
+ * about 27,000 unknowns, the ring of tile rows the FP64 sweeps keep). */
 int geneo_setup(geneo_ctx *ctx, const geneo_partition *part,
                 const geneo_modes *modes, geneo_precision prec,
                 geneo_schwarz schwarz, geneo_coarse coarse);
@@ -415,8 +420,9 @@ int geneo_kappa_from_cg(const double *alphas, const double *betas, int k, double
  * While a batch exists its contexts must not run other work (it uses their
  * buffers).  Work goes to cuda_stream (NULL = legacy default stream).
  * Returns GENEO_ERR_STATE for a context that is not set up,
- * GENEO_ERR_INVALID_ARG for mixed precisions or devices or a repeated
- * context. */
+ * GENEO_ERR_INVALID_ARG for mixed precisions or devices, a repeated context,
+ * or a subdomain whose local vector does not fit in shared memory (the
+ * batched local solves hold it whole). */
 typedef struct geneo_batch geneo_batch;
 int geneo_batch_create(geneo_batch **out, geneo_ctx *const *ctxs, int n, void *cuda_stream);
 

@@ -304,13 +304,14 @@ int launch_band_cholesky(const BandLayout *d_lay, int nsys, int nt_max, int w_ma
 
 // The GenEO eigensolver's multi-right-hand-side solves run the one-CTA
 // look-ahead sweep of the local solves (schwarz.cu), one CTA per (system,
-// right-hand side), the column in shared memory.
-int launch_band_solve_dense(const BandLayout *d_lay, int nsys, int npad_max,
-                            const double *poolL, const double *poolU, const double *in,
+// right-hand side), the column in shared memory, or streamed through a ring
+// of tile rows when it does not fit.
+int launch_band_solve_dense(const BandLayout *d_lay, int nsys, int npad_max, int w_max,
+                            int ring, const double *poolL, const double *poolU, const double *in,
                             long long in_sys, int in_row, double *out, long long out_sys,
                             int out_row, int ncols, int mode, cudaStream_t s) {
-  return launch_band_solve_la(d_lay, nsys, npad_max, poolL, poolU, in, in_sys, in_row, out,
-                              out_sys, out_row, ncols, mode, s);
+  return launch_band_solve_la(d_lay, nsys, npad_max, w_max, ring, poolL, poolU, in, in_sys,
+                              in_row, out, out_sys, out_row, ncols, mode, s);
 }
 
 template <typename T>

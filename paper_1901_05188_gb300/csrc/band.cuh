@@ -23,19 +23,23 @@ int launch_band_cholesky(const BandLayout *d_lay, int nsys, int nt_max, int w_ma
 
 // Solve with ncols right-hand sides per system.  Column c of system j lives at
 // in[j*in_sys + l*in_row + c] (l = 0..n-1); the result goes to
-// out[j*out_sys + l*out_row + c] for l < nt*32 (padding rows written as zero).
+// out[j*out_sys + l*out_row + c] for l < n (padding rows are not written).
 // In-place use (in == out with equal strides) is allowed.
-// mode: 1 forward (L), 2 backward (L^T), 3 both.
-int launch_band_solve_dense(const BandLayout *d_lay, int nsys, int npad_max,
-                            const double *poolL, const double *poolU, const double *in,
+// mode: 1 forward (L), 2 backward (L^T), 3 both.  w_max: the largest tile
+// half-bandwidth; ring = 1 streams every column through a ring of max(w + 2, 3)
+// tile rows in shared memory (chosen anyway when a whole column does not fit).
+int launch_band_solve_dense(const BandLayout *d_lay, int nsys, int npad_max, int w_max,
+                            int ring, const double *poolL, const double *poolU, const double *in,
                             long long in_sys, int in_row, double *out, long long out_sys,
                             int out_row, int ncols, int mode, cudaStream_t s);
 
 // The same solve with the one-CTA look-ahead sweep of the local solves.
-int launch_band_solve_la(const BandLayout *d_lay, int nsys, int npad_max, const double *poolL,
-                         const double *poolU, const double *in, long long in_sys, int in_row,
-                         double *out, long long out_sys, int out_row, int ncols, int mode,
-                         cudaStream_t s);
+int launch_band_solve_la(const BandLayout *d_lay, int nsys, int npad_max, int w_max, int ring,
+                         const double *poolL, const double *poolU, const double *in,
+                         long long in_sys, int in_row, double *out, long long out_sys,
+                         int out_row, int ncols, int mode, cudaStream_t s);
+// Whether the ring form of the band solve fits for tile half-bandwidth w_max.
+bool band_solve_fits(int w_max);
 
 // FP32 trailing update of tile column J on the tensor cores (3xTF32 tcgen05
 // MMAs, blocks of 4 x 4 tiles); part as for the band Cholesky's update
@@ -65,7 +69,9 @@ int prepare_schwarz_solve(int npad_max, int w_max);
 // memory a step ahead by bulk asynchronous copies and the per-CTA partials
 // are exchanged by st.async on mbarriers instead of cluster barriers; a copy
 // or partial that does not land within about a second sets GENEO_ERR_TIMEOUT
-// in *status.
+// in *status.  staged = 2 (cluster 1, rows 0): the look-ahead sweep with the
+// local vector streamed through a ring of max(w + 2, 3) tile rows, for subdomains
+// whose local vector does not fit in shared memory.
 template <typename T>
 int launch_schwarz_solve(const SubDesc *d_subs, const BandLayout *d_lay, int nsub,
                          int npad_max, int w_max, int nnx, int nny, const T *poolL,
@@ -74,6 +80,9 @@ int launch_schwarz_solve(const SubDesc *d_subs, const BandLayout *d_lay, int nsu
 // True when the staged launch (cluster, rows) fits in shared memory.
 template <typename T>
 bool schwarz_staged_fits(int npad_max, int w_max, int cluster, int rows);
+// True when the launch shape (cluster, rows, staged 0, 1 or 2) fits.
+template <typename T>
+bool schwarz_shape_fits(int npad_max, int w_max, int cluster, int rows, int staged);
 // Cluster size that fills the GPU: the largest power of two <= 8 with
 // 2 * nsub * size <= number of SMs (at least 1).
 int schwarz_cluster_size(int nsub, int sm_count);

@@ -1021,11 +1021,12 @@ static int setup_coarse(geneo_ctx *c, SetupPlan &P, cudaStream_t s) {
     int *gate = pc.gate + j0;
     int r;
     // W = L^-1 B L^-T V_k
-    if ((r = launch_band_solve_dense(lay, n, npad, pc.neuL, pc.neuU, V + k * p, sV, ldv, T1, sW,
-                                     p, p, 2, gs)))
+    if ((r = launch_band_solve_dense(lay, n, npad, pc.w_neu_max, pc.eig_ring, pc.neuL, pc.neuU,
+                                     V + k * p, sV, ldv, T1, sW, p, p, 2, gs)))
       return r;
     launch_bloc_mv(subs, n, P.max_nodes_neu, pc.Bloc, T1, W, sW, p, gs);
-    if ((r = launch_band_solve_dense(lay, n, npad, pc.neuL, pc.neuU, W, sW, p, W, sW, p, p, 1, gs)))
+    if ((r = launch_band_solve_dense(lay, n, npad, pc.w_neu_max, pc.eig_ring, pc.neuL, pc.neuU, W,
+                                     sW, p, W, sW, p, p, 1, gs)))
       return r;
     const int na = (k + 1) * p;
     // full re-orthogonalisation against V: a second pass only for the
@@ -1124,8 +1125,8 @@ static int setup_coarse(geneo_ctx *c, SetupPlan &P, cudaStream_t s) {
   const long long sP = (long long)npad * mcap;
   launch_tsgemm(pc.d_subs, nsub, npad, pc.V, ldv, sV, kdim, pc.Evec, kdim, (long long)kdim * kdim,
                 pc.P, mcap, sP, mcap, 1.0, 0.0, s);
-  if ((st = launch_band_solve_dense(pc.d_lay_neu, nsub, npad, pc.neuL, pc.neuU, pc.P, sP, mcap,
-                                    pc.P, sP, mcap, mcap, 2, s)))
+  if ((st = launch_band_solve_dense(pc.d_lay_neu, nsub, npad, pc.w_neu_max, pc.eig_ring, pc.neuL,
+                                    pc.neuU, pc.P, sP, mcap, pc.P, sP, mcap, mcap, 2, s)))
     return st;
   launch_tsdots(pc.d_subs, nsub, npad, pc.P, mcap, sP, mcap, pc.P, mcap, sP, mcap, pc.Hpart,
                 kDotChunks, pc.G, (long long)mcap * mcap, s);
@@ -1228,8 +1229,8 @@ static int build_coarse_operator(geneo_ctx *c, SetupPlan &P, const std::vector<l
   if ((st = launch_band_cholesky<double>(pc.d_lay_H, 1, LH.nt, LH.w, pc.AHL, pc.AHU, c->status, s)))
     return st;
   launch_identity(pc.AHinv, nH, s);
-  if ((st = launch_band_solve_dense(pc.d_lay_H, 1, LH.nt * 32, pc.AHL, pc.AHU, pc.AHinv, 0, nH,
-                                    pc.AHinv, 0, nH, nH, 3, s)))
+  if ((st = launch_band_solve_dense(pc.d_lay_H, 1, LH.nt * 32, LH.w, 0, pc.AHL, pc.AHU, pc.AHinv,
+                                    0, nH, pc.AHinv, 0, nH, nH, 3, s)))
     return st;
   launch_symmetrize(pc.AHinv, nH, s);
   GENEO_CUDA_TRY(cudaGetLastError());
@@ -1346,8 +1347,8 @@ int geneo_plan_subdomains(const geneo_mesh *mesh, int unknowns_per_node,
 // cached for the process, keyed by precision, subdomain count, largest padded
 // subdomain, largest band width and SM count, so a repeated set-up of the same
 // shape does not tune again.  GENEO_SCHWARZ_CLUSTER, GENEO_SCHWARZ_ROWS
-// (0 = the look-ahead sweep) and GENEO_SCHWARZ_STAGED (0 or 1) fix a
-// dimension each.
+// (0 = the look-ahead sweep) and GENEO_SCHWARZ_STAGED (0, 1, or 2 for the
+// ring form) fix a dimension each.
 struct TuneKey {
   int prec, nsub, npad, w, sms;
   bool operator<(const TuneKey &o) const {
@@ -1372,10 +1373,10 @@ static int env_choice(const char *name, std::initializer_list<int> allowed) {
   return -1;
 }
 
-static bool staged_fits(const Precond &pc, int C, int R) {
+static bool shape_fits(const Precond &pc, int C, int R, int St) {
   return pc.prec == GENEO_MIXED_FP32
-             ? schwarz_staged_fits<float>(pc.npad_int_max, pc.w_int_max, C, R)
-             : schwarz_staged_fits<double>(pc.npad_int_max, pc.w_int_max, C, R);
+             ? schwarz_shape_fits<float>(pc.npad_int_max, pc.w_int_max, C, R, St)
+             : schwarz_shape_fits<double>(pc.npad_int_max, pc.w_int_max, C, R, St);
 }
 
 static int tune_schwarz(geneo_ctx *c, const SetupPlan &P, cudaStream_t s) {
@@ -1383,7 +1384,7 @@ static int tune_schwarz(geneo_ctx *c, const SetupPlan &P, cudaStream_t s) {
   const TuneKey key{(int)pc.prec, P.nsub, pc.npad_int_max, pc.w_int_max, pc.sms};
   const int fc = env_choice("GENEO_SCHWARZ_CLUSTER", {1, 2, 4, 8});
   const int fr = env_choice("GENEO_SCHWARZ_ROWS", {0, 1, 2, 4});
-  const int fs = env_choice("GENEO_SCHWARZ_STAGED", {0, 1});
+  const int fs = env_choice("GENEO_SCHWARZ_STAGED", {0, 1, 2});
   const bool pinned = fc >= 0 || fr >= 0 || fs >= 0;
   if (!pinned) {
     std::lock_guard<std::mutex> g(g_tune_mu);
@@ -1397,20 +1398,25 @@ static int tune_schwarz(geneo_ctx *c, const SetupPlan &P, cudaStream_t s) {
   }
   // Unpinned, the tuner skips the shapes that never won on the measured
   // workloads: four rows per step, and the global-memory form of a shape whose
-  // staged form fits in shared memory.
+  // staged form fits in shared memory.  The ring form (St = 2: the one-CTA
+  // look-ahead sweep with the same arithmetic, the local vector streamed
+  // through shared memory) is a candidate only when no shape that holds the
+  // whole local vector fits, or when pinned.
   std::vector<TuneChoice> cand;
   for (int C : {1, 2, 4, 8}) {
     if (fc >= 0 ? C != fc : (C > 1 && P.nsub * C > pc.sms)) continue;   // one wave of clusters
     for (int R : {0, 1, 2, 4}) {
       if (fr >= 0 ? R != fr : R == 4) continue;
-      const bool fits = staged_fits(pc, C, R);
+      const bool fits = shape_fits(pc, C, R, 1);
       for (int St : {0, 1}) {
         if (fs >= 0 ? St != fs : (St == 0 && fits)) continue;
-        if (St && !fits) continue;
+        if (!shape_fits(pc, C, R, St)) continue;
         cand.push_back({C, R, St});
       }
     }
   }
+  if ((fs == 2 || (fs < 0 && cand.empty())) && fc <= 1 && fr <= 0 && shape_fits(pc, 1, 0, 2))
+    cand.push_back({1, 0, 2});
   if (cand.empty()) return fail(GENEO_ERR_INVALID_ARG, "no Schwarz launch shape fits the pinned choice");
   pc.cluster = cand[0].cluster;
   pc.rows = cand[0].rows;
@@ -1558,12 +1564,13 @@ int geneo_setup(geneo_ctx *c, const geneo_partition *part, const geneo_modes *mo
   pc.staged = 0;
   pc.sms = sms;
   if (f32) {
-    if ((st = prepare_schwarz_solve<float>(pc.npad_int_max, pc.w_int_max))) return fail(st, "subdomain too large for shared memory");
+    if ((st = prepare_schwarz_solve<float>(pc.npad_int_max, pc.w_int_max))) return fail(st, "band too wide for shared memory");
   } else {
-    if ((st = prepare_schwarz_solve<double>(pc.npad_int_max, pc.w_int_max))) return fail(st, "subdomain too large for shared memory");
+    if ((st = prepare_schwarz_solve<double>(pc.npad_int_max, pc.w_int_max))) return fail(st, "band too wide for shared memory");
   }
-  if (pc.coarse == GENEO_COARSE_GENEO && pc.mcap > 1 && pc.npad_neu_max * 8 + 16 * 32 * 8 > 227 * 1024)
-    return fail(GENEO_ERR_INVALID_ARG, "subdomain too large for the eigensolver's shared memory");
+  if (pc.coarse == GENEO_COARSE_GENEO && pc.mcap > 1 && !band_solve_fits(pc.w_neu_max))
+    return fail(GENEO_ERR_INVALID_ARG, "band too wide for the eigensolver's shared memory");
+  pc.eig_ring = env_choice("GENEO_BAND_SOLVE_RING", {0, 1}) == 1;
   cudaEvent_t ev[4];
   for (auto &e : ev) GENEO_CUDA_TRY(cudaEventCreate(&e));
   GENEO_CUDA_TRY(cudaEventRecord(ev[0], s));
@@ -2123,9 +2130,9 @@ extern "C" int geneo_profile(geneo_ctx *c, int what, int reps, double *ms_per_la
         launch_spmv(A, c->r, c->q, s);
       } else if (what == 3) {
         const int p = kLanczosBlock, ldv = pc.kdim + p, npad = pc.npad_neu_max;
-        st = launch_band_solve_dense(pc.d_lay_neu, pc.nsub, npad, pc.neuL, pc.neuU, pc.V,
-                                     (long long)npad * ldv, ldv, pc.T1, (long long)npad * p, p, p,
-                                     2, s);
+        st = launch_band_solve_dense(pc.d_lay_neu, pc.nsub, npad, pc.w_neu_max, pc.eig_ring,
+                                     pc.neuL, pc.neuU, pc.V, (long long)npad * ldv, ldv, pc.T1,
+                                     (long long)npad * p, p, p, 2, s);
       } else if (what == 4) {
         // re-assemble S_j = A_j - sigma B_j and factor it again (same result)
         if (!(st = launch_band_clear<double>(pc.d_lay_neu, pc.nsub, pc.neuL, pc.fac_neu_elems, s))) {

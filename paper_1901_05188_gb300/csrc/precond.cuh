@@ -27,7 +27,8 @@ struct Precond {
   int nsub = 0;
   int cluster = 1;                // CTAs per subdomain in the Schwarz local solves
   int rows = 1;                   // tile rows per cluster barrier in the Schwarz local solves
-  int staged = 0;                 // Schwarz tiles staged in shared memory by bulk copies
+  int staged = 0;                 // Schwarz tiles staged in shared memory by bulk copies (1),
+                                  // or the local vector streamed through a ring of tile rows (2)
   int sms = 0;                    // SM count of the device
   std::vector<SubDesc> subs;
   SubDesc *d_subs = nullptr;
@@ -42,6 +43,7 @@ struct Precond {
   int cand_off[3] = {0, 0, 0}, ecnt_off[3] = {0, 0, 0};
   int nt_int_max = 0, w_int_max = 0, npad_int_max = 0;
   int nt_neu_max = 0, w_neu_max = 0, npad_neu_max = 0;
+  int eig_ring = 0;               // the eigensolver's band solves stream their columns through a ring
   long long fac_int_elems = 0, xloc_elems = 0;
   long long fac_neu_elems = 0, bloc_blocks = 0, xneu_elems = 0;
   // interior factors (T = double or float), L and U copies

@@ -893,10 +893,71 @@ __device__ __forceinline__ void cluster_wait() {
   asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-template <typename T, int C>
+// Where the look-ahead sweep keeps the local vector.  FullVec: all of it in
+// shared memory, tile row I at y + 32 I, filled before and read after the
+// sweep by the caller.  RingVec: only the tile rows the band can still touch,
+// in a ring of `rows` slots (row I in slot I mod rows); one far warp reads the
+// next row from `src` during each step and the chain writes each solved row to
+// `dst`, so shared memory no longer bounds the subdomain size.  Step q (row I)
+// reads rows I + 1 - w .. I and fills the slot of row I + 1, which last held
+// row I + 1 - rows: with rows = max(w + 2, 3) that row is no longer read (the
+// chain reads the previous row's slot even when w = 0 and its tile is zero).
+__host__ __device__ constexpr int ring_rows(int w) { return w + 2 > 3 ? w + 2 : 3; }
+struct FullVec {
+  static constexpr bool kRing = false;
+};
+
+template <typename T, typename Src, typename Dst>
+struct RingVec {
+  static constexpr bool kRing = true;
+  int rows;   // ring slots (tile rows)
+  int n;      // unknowns: rows past n read as zero and are not written
+  Src src;    // T operator()(int l): element l < n of the right-hand side
+  Dst dst;    // void operator()(int l, T v): element l < n of the solution
+};
+
+// Contiguous vector (L2-coherent loads: the backward sweep reads what the
+// forward sweep of the same launch wrote).
+template <typename T>
+struct ArraySrc {
+  const T *p;
+  __device__ T operator()(int l) const { return __ldcg(p + l); }
+};
+template <typename T>
+struct ArrayDst {
+  T *p;
+  __device__ void operator()(int l, T v) const { p[l] = v; }
+};
+// Column of a row-major block of right-hand sides (row stride `ld`).
+struct StridedSrc {
+  const double *p;
+  long long ld;
+  __device__ double operator()(int l) const { return __ldcg(p + l * ld); }
+};
+struct StridedDst {
+  double *p;
+  long long ld;
+  __device__ void operator()(int l, double v) const { p[l * ld] = v; }
+};
+// R_j r: the subdomain's interior unknowns gathered from the global vector.
+template <typename T>
+struct GatherSrc {
+  const SubDesc *S;
+  const double *r;
+  int nnx, nny;
+  __device__ T operator()(int l) const {
+    const int nc = S->nc;
+    const int node = l / nc, comp = l - nc * node;
+    int gi, gj, gk;
+    S->ibox.global(node, gi, gj, gk);
+    return T(__ldcg(r + nc * (gi + nnx * (gj + nny * gk)) + comp));
+  }
+};
+
+template <typename T, int C, typename V = FullVec>
 __device__ void cluster_sweep_la(const cg::cluster_group &cluster, const T *__restrict__ pool,
                                  const BandLayout &L, T *y, T *red, T *chn, T *part,
-                                 bool backward) {
+                                 bool backward, const V &vec = V()) {
   constexpr int kFar = kClWarps - kChain;
   constexpr int B = sizeof(T) == 8 ? 2 : 4;
   constexpr int kLinesPerUnit = 8 * 32 * (int)sizeof(T) / 128;
@@ -905,12 +966,33 @@ __device__ void cluster_sweep_la(const cg::cluster_group &cluster, const T *__re
   const int nt = L.nt, w = L.w;
   auto row = [&](int q) { return backward ? nt - 1 - q : q; };
   auto dmax = [&](int I) { return backward ? min(w, nt - 1 - I) : min(w, I); };
-  auto ycol = [&](int I, int d) { return backward ? I + d : I - d; };
+  // slot of tile row I, and of the row at distance d behind the row in slot s
+  auto slot = [&](int I) {
+    if constexpr (V::kRing) return I % vec.rows;
+    else return I;
+  };
+  auto yrow = [&](int s, int d) {
+    const int t = backward ? s + d : s - d;
+    if constexpr (V::kRing) return t < 0 ? t + vec.rows : (t >= vec.rows ? t - vec.rows : t);
+    else return t;
+  };
+  auto load_row = [&](int I) {                    // element `lane` of row I
+    if constexpr (V::kRing) {
+      const int l = I * 32 + lane;
+      return l < vec.n ? vec.src(l) : T(0);
+    } else {
+      return T(0);
+    }
+  };
   // far units of row I for this CTA: d = 2 + c + t*C, 4 column groups per tile
   auto nfar = [&](int I) {
     const int dm = dmax(I), d0 = 2 + c;
     return dm >= d0 ? ((dm - d0) / C + 1) * kGroups : 0;
   };
+  if constexpr (V::kRing) {
+    if (warp == 0 && nt > 0) y[slot(row(0)) * 32 + lane] = load_row(row(0));
+    __syncthreads();
+  }
   int buf = 0;
   T dv[8], nv[8];                                 // chain: this warp's 8 columns
   if (warp < kChain && nt > 0) {
@@ -923,13 +1005,16 @@ __device__ void cluster_sweep_la(const cg::cluster_group &cluster, const T *__re
   }
   for (int q = 0; q < nt; ++q) {
     const int I = row(q);
+    const int sI = slot(I);
     const int par = q & 1;
     if (warp >= kChain) {
       const int cw = warp - kChain;
       cluster_arrive();
       T a0 = T(0), a1 = T(0);
       if (q + 1 < nt) {
-        const int In = row(q + 1), nu = nfar(In);
+        const int In = row(q + 1), nu = nfar(In), sIn = slot(In);
+        T next = T(0);                            // ring: row In, read by the chain in step q + 1
+        if (V::kRing && cw == 0) next = load_row(In);
         if (q + 2 < nt) {                         // L2 prefetch of the next step's units
           const int I2 = row(q + 2), nu2 = nfar(I2);
           for (int u = cw; u < nu2; u += kFar)
@@ -953,7 +1038,7 @@ __device__ void cluster_sweep_la(const cg::cluster_group &cluster, const T *__re
             const int u = u0 + b * kFar;
             if (u < nu) {
               const int d = 2 + c + (u / kGroups) * C;
-              const T *yJ = y + ycol(In, d) * 32 + (u % kGroups) * 8;
+              const T *yJ = y + yrow(sIn, d) * 32 + (u % kGroups) * 8;
 #pragma unroll
               for (int e = 0; e < 8; e += 2) {
                 a0 += v[b][e] * yJ[e];
@@ -962,6 +1047,7 @@ __device__ void cluster_sweep_la(const cg::cluster_group &cluster, const T *__re
             }
           }
         }
+        if (V::kRing && cw == 0) y[sIn * 32 + lane] = next;
       }
       red[(par ^ 1) * kFar * 32 + cw * 32 + lane] = a0 + a1;
       cluster_wait();
@@ -985,7 +1071,7 @@ __device__ void cluster_sweep_la(const cg::cluster_group &cluster, const T *__re
       // coupling to the previous row, split by columns
       T p0 = T(0), p1 = T(0);
       if (q > 0) {
-        const T *yJ = y + ycol(I, 1) * 32 + warp * 8;
+        const T *yJ = y + yrow(sI, 1) * 32 + warp * 8;
 #pragma unroll
         for (int k = 0; k < 8; k += 2) {
           p0 += nv[k] * yJ[k];
@@ -996,7 +1082,7 @@ __device__ void cluster_sweep_la(const cg::cluster_group &cluster, const T *__re
       cb[warp * 32 + lane] = p0 + p1;
       chain_bar();
       ++buf;
-      T sv = y[I * 32 + lane] - (((cb[lane] + cb[32 + lane]) + cb[64 + lane]) + cb[96 + lane]);
+      T sv = y[sI * 32 + lane] - (((cb[lane] + cb[32 + lane]) + cb[64 + lane]) + cb[96 + lane]);
       cluster_wait();
       if (q > 0) {
 #pragma unroll
@@ -1013,7 +1099,12 @@ __device__ void cluster_sweep_la(const cg::cluster_group &cluster, const T *__re
       chain_bar();
       ++buf;
       const T yI = ((cb[lane] + cb[32 + lane]) + cb[64 + lane]) + cb[96 + lane];
-      if (warp == 0) y[I * 32 + lane] = yI;
+      if (warp == 0) {
+        y[sI * 32 + lane] = yI;
+        if constexpr (V::kRing) {
+          if (I * 32 + lane < vec.n) vec.dst(I * 32 + lane, yI);
+        }
+      }
       if (q + 1 < nt) {                           // next row's chain tiles, in flight over the barrier
         const int In = row(q + 1);
         const T *D = tile_at(pool, L, In, 0) + warp * 256;
@@ -1193,6 +1284,64 @@ __global__ void __launch_bounds__(kClWarps * 32)
   for (int l = threadIdx.x; l < n; l += blockDim.x) dst[(long long)l * out_row] = y[l];
 }
 
+// ---- the same sweeps with the local vector streamed through a ring ----------
+// For subdomains whose local vector does not fit in shared memory: one CTA per
+// subdomain (or per (system, right-hand side)), the look-ahead sweep with the
+// vector in a ring of max(w + 2, 3) tile rows.  The forward sweep writes y to the
+// output as it goes and the backward sweep reads it back from there and
+// overwrites it with x: two more passes over the n unknowns than the
+// shared-memory form, beside the 32 (w + 1) factor elements per unknown that
+// each sweep streams.  The arithmetic and its order are those of the one-CTA
+// look-ahead launch (bit-identical results).
+template <typename T>
+__global__ void __launch_bounds__(kClWarps * 32)
+    k_schwarz_ring(const SubDesc *subs, const BandLayout *lay, int nnx, int nny, const T *poolL,
+                   const T *poolU, const double *r, T *xloc, const CGScalars *cgs) {
+  if (cgs && cgs->done) return;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *red = reinterpret_cast<T *>(smraw);   // [2][kClWarps - kChain][32]
+  T *chn = red + 2 * (kClWarps - kChain) * 32;   // [2][kChain][32]
+  T *part = chn + 2 * kChain * 32;        // [2][1][32]
+  T *y = part + 2 * 32;                   // [ring_rows(w)][32]
+  const int j = blockIdx.x;
+  const SubDesc *S = subs + j;
+  const BandLayout L = lay[j];
+  const int n = S->n_int;
+  T *out = xloc + S->v_int;
+  const RingVec<T, GatherSrc<T>, ArrayDst<T>> fwd{ring_rows(L.w), n, {S, r, nnx, nny}, {out}};
+  cluster_sweep_la<T, 1>(cluster, poolL, L, y, red, chn, part, false, fwd);
+  cluster.sync();                          // y complete in the output; the ring is reused
+  const RingVec<T, ArraySrc<T>, ArrayDst<T>> bwd{ring_rows(L.w), n, {out}, {out}};
+  cluster_sweep_la<T, 1>(cluster, poolU, L, y, red, chn, part, true, bwd);
+}
+
+__global__ void __launch_bounds__(kClWarps * 32)
+    k_band_solve_ring(const BandLayout *lay, const double *poolL, const double *poolU,
+                      const double *in, long long in_sys, int in_row, double *out,
+                      long long out_sys, int out_row, int mode) {
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double *red = reinterpret_cast<double *>(smraw);   // [2][kClWarps - kChain][32]
+  double *chn = red + 2 * (kClWarps - kChain) * 32;   // [2][kChain][32]
+  double *part = chn + 2 * kChain * 32;               // [2][1][32]
+  double *y = part + 2 * 32;                          // [ring_rows(w)][32]
+  const int j = blockIdx.x, c = blockIdx.y;
+  const BandLayout L = lay[j];
+  const double *src = in + j * in_sys + c;
+  double *dst = out + j * out_sys + c;
+  if (mode & 1) {
+    const RingVec<double, StridedSrc, StridedDst> fwd{ring_rows(L.w), L.n, {src, in_row}, {dst, out_row}};
+    cluster_sweep_la<double, 1>(cluster, poolL, L, y, red, chn, part, false, fwd);
+    cluster.sync();
+  }
+  if (mode & 2) {
+    const StridedSrc b = (mode & 1) ? StridedSrc{dst, out_row} : StridedSrc{src, in_row};
+    const RingVec<double, StridedSrc, StridedDst> bwd{ring_rows(L.w), L.n, b, {dst, out_row}};
+    cluster_sweep_la<double, 1>(cluster, poolU, L, y, red, chn, part, true, bwd);
+  }
+}
+
 // ---- local solves of a batch of instances: one persistent launch ---------------
 // Every CTA takes (instance, subdomain) items from a device work queue (the
 // items are ordered largest local solve first, so the long ones start early
@@ -1296,6 +1445,13 @@ int smem_bytes(int npad, int C, int R) {
   return ((kClWarps + 2 * kChain + 2 * C) * R * 32 + npad) * (int)sizeof(T);
 }
 
+// The ring launches: the one-CTA look-ahead buffers and the ring's tile rows.
+template <typename T>
+long long smem_bytes_ring(int w_max) {
+  return ((2LL * (kClWarps - kChain) + 2 * kChain + 2) * 32 + (long long)ring_rows(w_max) * 32) *
+         sizeof(T);
+}
+
 // Tiles per stage of a staged launch; for the look-ahead sweep (R = 0) the two
 // chain tiles are staged too when the whole launch then fits.
 template <typename T>
@@ -1329,6 +1485,7 @@ template <typename T, int C, int R>
 int launch_cr(const SubDesc *d_subs, const BandLayout *d_lay, int nsub, int npad_max, int w_max,
               int staged, int nnx, int nny, const T *poolL, const T *poolU, const double *r,
               T *xloc, const CGScalars *cgs, DevStatus *status, cudaStream_t s) {
+  if (!staged && smem_bytes<T>(npad_max, C, R) > kSmemMax) return GENEO_ERR_INVALID_ARG;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nsub * C);
   cfg.blockDim = dim3(kClWarps * 32);
@@ -1385,13 +1542,16 @@ int launch_c(int rows, int staged, const SubDesc *d_subs, const BandLayout *d_la
   }
 }
 
+// Opt in to the shared memory of every shape that fits (the others are never
+// launched: the launchers refuse them).
 template <typename T, int C>
 int prepare_c(int npad_max, int w_max) {
   int st;
-  if ((st = ensure_smem(k_schwarz_cluster<T, C, 1>, smem_bytes<T>(npad_max, C, 1)))) return st;
-  if ((st = ensure_smem(k_schwarz_cluster<T, C, 2>, smem_bytes<T>(npad_max, C, 2)))) return st;
-  if ((st = ensure_smem(k_schwarz_cluster_la<T, C>, smem_bytes<T>(npad_max, C, 0)))) return st;
-  if ((st = ensure_smem(k_schwarz_cluster<T, C, 4>, smem_bytes<T>(npad_max, C, 4)))) return st;
+  auto fits = [&](int R) { return smem_bytes<T>(npad_max, C, R) <= kSmemMax; };
+  if (fits(1) && (st = ensure_smem(k_schwarz_cluster<T, C, 1>, smem_bytes<T>(npad_max, C, 1)))) return st;
+  if (fits(2) && (st = ensure_smem(k_schwarz_cluster<T, C, 2>, smem_bytes<T>(npad_max, C, 2)))) return st;
+  if (fits(0) && (st = ensure_smem(k_schwarz_cluster_la<T, C>, smem_bytes<T>(npad_max, C, 0)))) return st;
+  if (fits(4) && (st = ensure_smem(k_schwarz_cluster<T, C, 4>, smem_bytes<T>(npad_max, C, 4)))) return st;
   const long long s0 = smem_bytes_staged<T>(npad_max, w_max, C, 0);
   const long long s1 = smem_bytes_staged<T>(npad_max, w_max, C, 1);
   const long long s2 = smem_bytes_staged<T>(npad_max, w_max, C, 2);
@@ -1416,8 +1576,9 @@ int schwarz_cluster_size(int nsub, int sm_count) {
 
 template <typename T>
 int prepare_schwarz_solve(int npad_max, int w_max) {
-  if (smem_bytes<T>(npad_max, 8, 4) > kSmemMax) return GENEO_ERR_INVALID_ARG;
+  if (smem_bytes_ring<T>(w_max) > kSmemMax) return GENEO_ERR_INVALID_ARG;
   int st;
+  if ((st = ensure_smem(k_schwarz_ring<T>, (int)smem_bytes_ring<T>(w_max)))) return st;
   if ((st = prepare_c<T, 1>(npad_max, w_max))) return st;
   if ((st = prepare_c<T, 2>(npad_max, w_max))) return st;
   if ((st = prepare_c<T, 4>(npad_max, w_max))) return st;
@@ -1430,10 +1591,38 @@ bool schwarz_staged_fits(int npad_max, int w_max, int cluster, int rows) {
 }
 
 template <typename T>
+bool schwarz_shape_fits(int npad_max, int w_max, int cluster, int rows, int staged) {
+  if (staged == 2) return cluster == 1 && rows == 0 && smem_bytes_ring<T>(w_max) <= kSmemMax;
+  if (staged == 1) return schwarz_staged_fits<T>(npad_max, w_max, cluster, rows);
+  return smem_bytes<T>(npad_max, cluster, rows) <= kSmemMax;
+}
+
+template <typename T>
 int launch_schwarz_solve(const SubDesc *d_subs, const BandLayout *d_lay, int nsub, int npad_max,
                          int w_max, int nnx, int nny, const T *poolL, const T *poolU,
                          const double *r, T *xloc, const CGScalars *cgs, int cluster, int rows,
                          int staged, DevStatus *status, cudaStream_t s) {
+  if (staged == 2) {
+    if (cluster != 1 || rows != 0) return GENEO_ERR_INVALID_ARG;
+    const long long sm = smem_bytes_ring<T>(w_max);
+    if (sm > kSmemMax) return GENEO_ERR_INVALID_ARG;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nsub);
+    cfg.blockDim = dim3(kClWarps * 32);
+    cfg.dynamicSmemBytes = (size_t)sm;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 1;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_schwarz_ring<T>, d_subs, d_lay, nnx, nny, poolL,
+                                      poolU, r, xloc, cgs));
+    GENEO_COUNT_LAUNCH();
+    return GENEO_OK;
+  }
   switch (cluster) {
     case 8: return launch_c<T, 8>(rows, staged, d_subs, d_lay, nsub, npad_max, w_max, nnx, nny, poolL, poolU, r, xloc, cgs, status, s);
     case 4: return launch_c<T, 4>(rows, staged, d_subs, d_lay, nsub, npad_max, w_max, nnx, nny, poolL, poolU, r, xloc, cgs, status, s);
@@ -1442,13 +1631,17 @@ int launch_schwarz_solve(const SubDesc *d_subs, const BandLayout *d_lay, int nsu
   }
 }
 
-int launch_band_solve_la(const BandLayout *d_lay, int nsys, int npad_max, const double *poolL,
-                         const double *poolU, const double *in, long long in_sys, int in_row,
-                         double *out, long long out_sys, int out_row, int ncols, int mode,
-                         cudaStream_t s) {
-  const int sm = smem_bytes<double>(npad_max, 1, 0);
+bool band_solve_fits(int w_max) { return smem_bytes_ring<double>(w_max) <= kSmemMax; }
+
+int launch_band_solve_la(const BandLayout *d_lay, int nsys, int npad_max, int w_max, int ring,
+                         const double *poolL, const double *poolU, const double *in,
+                         long long in_sys, int in_row, double *out, long long out_sys,
+                         int out_row, int ncols, int mode, cudaStream_t s) {
+  const bool use_ring = ring || smem_bytes<double>(npad_max, 1, 0) > kSmemMax;
+  const long long sm = use_ring ? smem_bytes_ring<double>(w_max) : smem_bytes<double>(npad_max, 1, 0);
   if (sm > kSmemMax) return GENEO_ERR_INVALID_ARG;
-  if (int st = ensure_smem(k_band_solve_la, sm)) return st;
+  if (int st = use_ring ? ensure_smem(k_band_solve_ring, (int)sm) : ensure_smem(k_band_solve_la, (int)sm))
+    return st;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nsys, ncols);
   cfg.blockDim = dim3(kClWarps * 32);
@@ -1461,8 +1654,13 @@ int launch_band_solve_la(const BandLayout *d_lay, int nsys, int npad_max, const 
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_band_solve_la, d_lay, poolL, poolU, in, in_sys, in_row,
-                                    out, out_sys, out_row, mode));
+  if (use_ring) {
+    GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_band_solve_ring, d_lay, poolL, poolU, in, in_sys,
+                                      in_row, out, out_sys, out_row, mode));
+  } else {
+    GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_band_solve_la, d_lay, poolL, poolU, in, in_sys,
+                                      in_row, out, out_sys, out_row, mode));
+  }
   GENEO_COUNT_LAUNCH();
   return GENEO_OK;
 }
@@ -1560,6 +1758,8 @@ template int launch_batch_schwarz<float>(const BatchInst *, const CGScalars *, c
 
 template int prepare_schwarz_solve<double>(int, int);
 template int prepare_schwarz_solve<float>(int, int);
+template bool schwarz_shape_fits<double>(int, int, int, int, int);
+template bool schwarz_shape_fits<float>(int, int, int, int, int);
 template bool schwarz_staged_fits<double>(int, int, int, int);
 template bool schwarz_staged_fits<float>(int, int, int, int);
 template int launch_schwarz_solve<double>(const SubDesc *, const BandLayout *, int, int, int, int,

@@ -6,6 +6,7 @@ Lanczos condition estimate, the coarse dimension, per-subdomain mode counts
 and eigenvalues, the displacement at a fixed sample of dofs (every
 stride-th dof), its 2-norm, and the 2-norm of every consecutive chunk of
 CHUNK dofs (so a comparison touches every dof, not only the samples).
+Names starting with "d-" are the Darcy workloads (workloads.darcy).
 Usage: python tests/golden/make_golden.py c2 [nsamples]
 """
 import json
@@ -20,13 +21,14 @@ sys.path.insert(0, ROOT)
 
 import workloads  # noqa: E402
 from oracle import solver  # noqa: E402
+from workloads.darcy import darcy_config  # noqa: E402
 
 
 CHUNK = 1024
 
 
 def main(name, nsamples=600):
-    p = workloads.config(name)
+    p = darcy_config(name) if name.startswith("d-") else workloads.config(name)
     t = time.time()
     r = solver.solve(p, precond="geneo", tol=1e-8)
     u = r["u"]

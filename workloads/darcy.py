@@ -64,12 +64,15 @@ def make_darcy(nx, ny, nz, seed=5, partition=(2, 2, 1, 1), modes=None, source=1.
 
 def darcy_config(name, **over):
     """d-tiny: 6x5x4, 2x1x1 subdomains; d-small: 16x12x9, 2x2x1 (the paper decomposes
-    SPE10 in-plane, full height); d-spe10: the SPE10 grid 60x220x85, 6x18x1 (subdomains of
-    10 x 12 x 85 cells: a subdomain's local vector must fit in shared memory)."""
+    SPE10 in-plane, full height); d-large: 36x64x24, 1x2x1 (30,525 interior unknowns per
+    subdomain, more than a local vector held whole in shared memory allows); d-spe10: the
+    SPE10 grid 60x220x85, 6x18x1 (subdomains of 10 x 12 x 85 cells)."""
     if name == "d-tiny":
         kw = dict(nx=6, ny=5, nz=4, partition=(2, 1, 1, 1))
     elif name == "d-small":
         kw = dict(nx=16, ny=12, nz=9, partition=(2, 2, 1, 1))
+    elif name == "d-large":
+        kw = dict(nx=36, ny=64, nz=24, partition=(1, 2, 1, 1))
     elif name == "d-spe10":
         kw = dict(nx=60, ny=220, nz=85, partition=(6, 18, 1, 1))
     else:
