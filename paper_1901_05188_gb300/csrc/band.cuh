@@ -69,13 +69,14 @@ int prepare_schwarz_solve(int npad_max, int w_max);
 // memory a step ahead by bulk asynchronous copies and the per-CTA partials
 // are exchanged by st.async on mbarriers instead of cluster barriers; a copy
 // or partial that does not land within about a second sets GENEO_ERR_TIMEOUT
-// in *status.  staged = 2 (cluster 1, rows 0): the look-ahead sweep with the
-// local vector streamed through a ring of max(w + 2, 3) tile rows, for subdomains
-// whose local vector does not fit in shared memory.
+// in *status.  staged = 2 (rows 0): the look-ahead sweep with the local
+// vector streamed through a ring of max(w + 2, 3) tile rows, for subdomains
+// whose local vector does not fit in shared memory; its forward sweep leaves
+// y in yscr (same layout as xloc).
 template <typename T>
 int launch_schwarz_solve(const SubDesc *d_subs, const BandLayout *d_lay, int nsub,
                          int npad_max, int w_max, int nnx, int nny, const T *poolL,
-                         const T *poolU, const double *r, T *xloc, const CGScalars *cg,
+                         const T *poolU, const double *r, T *xloc, T *yscr, const CGScalars *cg,
                          int cluster, int rows, int staged, DevStatus *status, cudaStream_t s);
 // True when the staged launch (cluster, rows) fits in shared memory.
 template <typename T>

@@ -747,6 +747,7 @@ void plan_setup(Arena &A, geneo_ctx *c, const SetupPlan &P) {
   pc.facL = A.take<char>(pc.fac_int_elems * esz);
   pc.facU = A.take<char>(pc.fac_int_elems * esz);
   pc.xloc = A.take<char>(pc.xloc_elems * esz);
+  pc.yloc = A.take<char>(pc.xloc_elems * esz);   // forward-sweep scratch of the ring form
   pc.wloc = A.take<double>(pc.xloc_elems);     // Sarkis weights (filled for that PoU only)
   int cap = pc.modes.fixed_modes > 0 ? pc.modes.fixed_modes : pc.modes.max_modes;
   if (pc.coarse == GENEO_COARSE_NONE) cap = 0;
@@ -845,12 +846,12 @@ static int schwarz_local_solves(geneo_ctx *c, const double *r, const CGScalars *
   if (pc.prec == GENEO_MIXED_FP32)
     return launch_schwarz_solve<float>(pc.d_subs, pc.d_lay_int, pc.nsub, pc.npad_int_max,
                                        pc.w_int_max, nnx, nny, (const float *)pc.facL,
-                                       (const float *)pc.facU, r, (float *)pc.xloc, cg, cluster,
-                                       rows, staged, c->status, s);
+                                       (const float *)pc.facU, r, (float *)pc.xloc,
+                                       (float *)pc.yloc, cg, cluster, rows, staged, c->status, s);
   return launch_schwarz_solve<double>(pc.d_subs, pc.d_lay_int, pc.nsub, pc.npad_int_max,
                                       pc.w_int_max, nnx, nny, (const double *)pc.facL,
-                                      (const double *)pc.facU, r, (double *)pc.xloc, cg, cluster,
-                                      rows, staged, c->status, s);
+                                      (const double *)pc.facU, r, (double *)pc.xloc,
+                                      (double *)pc.yloc, cg, cluster, rows, staged, c->status, s);
 }
 
 static int precond_apply(geneo_ctx *c, const double *r, double *z, const CGScalars *cg,
@@ -1398,9 +1399,9 @@ static int tune_schwarz(geneo_ctx *c, const SetupPlan &P, cudaStream_t s) {
   }
   // Unpinned, the tuner skips the shapes that never won on the measured
   // workloads: four rows per step, and the global-memory form of a shape whose
-  // staged form fits in shared memory.  The ring form (St = 2: the one-CTA
+  // staged form fits in shared memory.  The ring forms (St = 2: the
   // look-ahead sweep with the same arithmetic, the local vector streamed
-  // through shared memory) is a candidate only when no shape that holds the
+  // through shared memory) are candidates only when no shape that holds the
   // whole local vector fits, or when pinned.
   std::vector<TuneChoice> cand;
   for (int C : {1, 2, 4, 8}) {
@@ -1415,8 +1416,11 @@ static int tune_schwarz(geneo_ctx *c, const SetupPlan &P, cudaStream_t s) {
       }
     }
   }
-  if ((fs == 2 || (fs < 0 && cand.empty())) && fc <= 1 && fr <= 0 && shape_fits(pc, 1, 0, 2))
-    cand.push_back({1, 0, 2});
+  if ((fs == 2 || (fs < 0 && cand.empty())) && fr <= 0)
+    for (int C : {1, 2, 4, 8}) {
+      if (fc >= 0 ? C != fc : (C > 1 && P.nsub * C > pc.sms)) continue;
+      if (shape_fits(pc, C, 0, 2)) cand.push_back({C, 0, 2});
+    }
   if (cand.empty()) return fail(GENEO_ERR_INVALID_ARG, "no Schwarz launch shape fits the pinned choice");
   pc.cluster = cand[0].cluster;
   pc.rows = cand[0].rows;

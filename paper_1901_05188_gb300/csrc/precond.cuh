@@ -49,6 +49,7 @@ struct Precond {
   // interior factors (T = double or float), L and U copies
   void *facL = nullptr, *facU = nullptr;
   void *xloc = nullptr;           // per-subdomain local solutions
+  void *yloc = nullptr;           // the ring form's forward-sweep results (layout of xloc)
   int pou = 0;                    // partition of unity: GENEO_POU_MULTIPLICITY or _SARKIS
   double *wloc = nullptr;         // Sarkis weights X_j on interior dofs (like xloc), or null
   // GenEO eigenproblem data (FP64)

@@ -1102,7 +1102,7 @@ __device__ void cluster_sweep_la(const cg::cluster_group &cluster, const T *__re
       if (warp == 0) {
         y[sI * 32 + lane] = yI;
         if constexpr (V::kRing) {
-          if (I * 32 + lane < vec.n) vec.dst(I * 32 + lane, yI);
+          if (c == 0 && I * 32 + lane < vec.n) vec.dst(I * 32 + lane, yI);
         }
       }
       if (q + 1 < nt) {                           // next row's chain tiles, in flight over the barrier
@@ -1285,35 +1285,41 @@ __global__ void __launch_bounds__(kClWarps * 32)
 }
 
 // ---- the same sweeps with the local vector streamed through a ring ----------
-// For subdomains whose local vector does not fit in shared memory: one CTA per
-// subdomain (or per (system, right-hand side)), the look-ahead sweep with the
-// vector in a ring of max(w + 2, 3) tile rows.  The forward sweep writes y to the
-// output as it goes and the backward sweep reads it back from there and
-// overwrites it with x: two more passes over the n unknowns than the
-// shared-memory form, beside the 32 (w + 1) factor elements per unknown that
-// each sweep streams.  The arithmetic and its order are those of the one-CTA
-// look-ahead launch (bit-identical results).
-template <typename T>
+// For subdomains whose local vector does not fit in shared memory: the
+// look-ahead sweep (one cluster of C CTAs per subdomain, or one CTA per
+// (system, right-hand side)) with the vector in a ring of max(w + 2, 3) tile
+// rows in every CTA.  The forward sweep writes y to a scratch vector as it
+// goes (rank 0) and the backward sweep reads it back from there: two more
+// passes over the n unknowns than the shared-memory form, beside the 32 (w + 1)
+// factor elements per unknown that each sweep streams.  Reading y from a
+// buffer the backward sweep does not write keeps a CTA that runs a step ahead
+// from overwriting a row another CTA of the cluster has still to read.  The
+// arithmetic and its order are those of the look-ahead launch with the same C
+// (bit-identical results).
+template <typename T, int C>
 __global__ void __launch_bounds__(kClWarps * 32)
     k_schwarz_ring(const SubDesc *subs, const BandLayout *lay, int nnx, int nny, const T *poolL,
-                   const T *poolU, const double *r, T *xloc, const CGScalars *cgs) {
-  if (cgs && cgs->done) return;
+                   const T *poolU, const double *r, T *xloc, T *yscr, const CGScalars *cgs) {
+  if (cgs && cgs->done) return;           // the same for every CTA of the cluster
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smraw[];
   T *red = reinterpret_cast<T *>(smraw);   // [2][kClWarps - kChain][32]
   T *chn = red + 2 * (kClWarps - kChain) * 32;   // [2][kChain][32]
-  T *part = chn + 2 * kChain * 32;        // [2][1][32]
-  T *y = part + 2 * 32;                   // [ring_rows(w)][32]
-  const int j = blockIdx.x;
+  T *part = chn + 2 * kChain * 32;        // [2][C][32]
+  T *y = part + 2 * C * 32;               // [ring_rows(w)][32]
+  const int j = blockIdx.x / C;
   const SubDesc *S = subs + j;
   const BandLayout L = lay[j];
   const int n = S->n_int;
-  T *out = xloc + S->v_int;
-  const RingVec<T, GatherSrc<T>, ArrayDst<T>> fwd{ring_rows(L.w), n, {S, r, nnx, nny}, {out}};
-  cluster_sweep_la<T, 1>(cluster, poolL, L, y, red, chn, part, false, fwd);
-  cluster.sync();                          // y complete in the output; the ring is reused
-  const RingVec<T, ArraySrc<T>, ArrayDst<T>> bwd{ring_rows(L.w), n, {out}, {out}};
-  cluster_sweep_la<T, 1>(cluster, poolU, L, y, red, chn, part, true, bwd);
+  cluster.sync();                          // every CTA's shared memory is live
+  const RingVec<T, GatherSrc<T>, ArrayDst<T>> fwd{ring_rows(L.w), n, {S, r, nnx, nny},
+                                                  {yscr + S->v_int}};
+  cluster_sweep_la<T, C>(cluster, poolL, L, y, red, chn, part, false, fwd);
+  cluster.sync();                          // y complete in the scratch; the ring is reused
+  const RingVec<T, ArraySrc<T>, ArrayDst<T>> bwd{ring_rows(L.w), n, {yscr + S->v_int},
+                                                 {xloc + S->v_int}};
+  cluster_sweep_la<T, C>(cluster, poolU, L, y, red, chn, part, true, bwd);
+  cluster.sync();                          // no CTA leaves while others may still write to it
 }
 
 __global__ void __launch_bounds__(kClWarps * 32)
@@ -1445,11 +1451,11 @@ int smem_bytes(int npad, int C, int R) {
   return ((kClWarps + 2 * kChain + 2 * C) * R * 32 + npad) * (int)sizeof(T);
 }
 
-// The ring launches: the one-CTA look-ahead buffers and the ring's tile rows.
+// The ring launches: the look-ahead buffers of C CTAs and the ring's tile rows.
 template <typename T>
-long long smem_bytes_ring(int w_max) {
-  return ((2LL * (kClWarps - kChain) + 2 * kChain + 2) * 32 + (long long)ring_rows(w_max) * 32) *
-         sizeof(T);
+long long smem_bytes_ring(int w_max, int C = 1) {
+  return ((2LL * (kClWarps - kChain) + 2 * kChain + 2 * C) * 32 +
+          (long long)ring_rows(w_max) * 32) * sizeof(T);
 }
 
 // Tiles per stage of a staged launch; for the look-ahead sweep (R = 0) the two
@@ -1576,9 +1582,12 @@ int schwarz_cluster_size(int nsub, int sm_count) {
 
 template <typename T>
 int prepare_schwarz_solve(int npad_max, int w_max) {
-  if (smem_bytes_ring<T>(w_max) > kSmemMax) return GENEO_ERR_INVALID_ARG;
+  if (smem_bytes_ring<T>(w_max, 8) > kSmemMax) return GENEO_ERR_INVALID_ARG;
   int st;
-  if ((st = ensure_smem(k_schwarz_ring<T>, (int)smem_bytes_ring<T>(w_max)))) return st;
+  if ((st = ensure_smem(k_schwarz_ring<T, 1>, (int)smem_bytes_ring<T>(w_max, 1)))) return st;
+  if ((st = ensure_smem(k_schwarz_ring<T, 2>, (int)smem_bytes_ring<T>(w_max, 2)))) return st;
+  if ((st = ensure_smem(k_schwarz_ring<T, 4>, (int)smem_bytes_ring<T>(w_max, 4)))) return st;
+  if ((st = ensure_smem(k_schwarz_ring<T, 8>, (int)smem_bytes_ring<T>(w_max, 8)))) return st;
   if ((st = prepare_c<T, 1>(npad_max, w_max))) return st;
   if ((st = prepare_c<T, 2>(npad_max, w_max))) return st;
   if ((st = prepare_c<T, 4>(npad_max, w_max))) return st;
@@ -1592,36 +1601,51 @@ bool schwarz_staged_fits(int npad_max, int w_max, int cluster, int rows) {
 
 template <typename T>
 bool schwarz_shape_fits(int npad_max, int w_max, int cluster, int rows, int staged) {
-  if (staged == 2) return cluster == 1 && rows == 0 && smem_bytes_ring<T>(w_max) <= kSmemMax;
+  if (staged == 2)
+    return (cluster == 1 || cluster == 2 || cluster == 4 || cluster == 8) && rows == 0 &&
+           smem_bytes_ring<T>(w_max, cluster) <= kSmemMax;
   if (staged == 1) return schwarz_staged_fits<T>(npad_max, w_max, cluster, rows);
   return smem_bytes<T>(npad_max, cluster, rows) <= kSmemMax;
+}
+
+template <typename T, int C>
+static int launch_ring(const SubDesc *d_subs, const BandLayout *d_lay, int nsub, int w_max,
+                       int nnx, int nny, const T *poolL, const T *poolU, const double *r, T *xloc,
+                       T *yscr, const CGScalars *cgs, cudaStream_t s) {
+  const long long sm = smem_bytes_ring<T>(w_max, C);
+  if (sm > kSmemMax || !yscr) return GENEO_ERR_INVALID_ARG;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nsub * C);
+  cfg.blockDim = dim3(kClWarps * 32);
+  cfg.dynamicSmemBytes = (size_t)sm;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_schwarz_ring<T, C>, d_subs, d_lay, nnx, nny, poolL,
+                                    poolU, r, xloc, yscr, cgs));
+  GENEO_COUNT_LAUNCH();
+  return GENEO_OK;
 }
 
 template <typename T>
 int launch_schwarz_solve(const SubDesc *d_subs, const BandLayout *d_lay, int nsub, int npad_max,
                          int w_max, int nnx, int nny, const T *poolL, const T *poolU,
-                         const double *r, T *xloc, const CGScalars *cgs, int cluster, int rows,
-                         int staged, DevStatus *status, cudaStream_t s) {
+                         const double *r, T *xloc, T *yscr, const CGScalars *cgs, int cluster,
+                         int rows, int staged, DevStatus *status, cudaStream_t s) {
   if (staged == 2) {
-    if (cluster != 1 || rows != 0) return GENEO_ERR_INVALID_ARG;
-    const long long sm = smem_bytes_ring<T>(w_max);
-    if (sm > kSmemMax) return GENEO_ERR_INVALID_ARG;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(nsub);
-    cfg.blockDim = dim3(kClWarps * 32);
-    cfg.dynamicSmemBytes = (size_t)sm;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 1;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    GENEO_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_schwarz_ring<T>, d_subs, d_lay, nnx, nny, poolL,
-                                      poolU, r, xloc, cgs));
-    GENEO_COUNT_LAUNCH();
-    return GENEO_OK;
+    if (rows != 0) return GENEO_ERR_INVALID_ARG;
+    switch (cluster) {
+      case 1: return launch_ring<T, 1>(d_subs, d_lay, nsub, w_max, nnx, nny, poolL, poolU, r, xloc, yscr, cgs, s);
+      case 2: return launch_ring<T, 2>(d_subs, d_lay, nsub, w_max, nnx, nny, poolL, poolU, r, xloc, yscr, cgs, s);
+      case 4: return launch_ring<T, 4>(d_subs, d_lay, nsub, w_max, nnx, nny, poolL, poolU, r, xloc, yscr, cgs, s);
+      case 8: return launch_ring<T, 8>(d_subs, d_lay, nsub, w_max, nnx, nny, poolL, poolU, r, xloc, yscr, cgs, s);
+      default: return GENEO_ERR_INVALID_ARG;
+    }
   }
   switch (cluster) {
     case 8: return launch_c<T, 8>(rows, staged, d_subs, d_lay, nsub, npad_max, w_max, nnx, nny, poolL, poolU, r, xloc, cgs, status, s);
@@ -1764,11 +1788,11 @@ template bool schwarz_staged_fits<double>(int, int, int, int);
 template bool schwarz_staged_fits<float>(int, int, int, int);
 template int launch_schwarz_solve<double>(const SubDesc *, const BandLayout *, int, int, int, int,
                                           int, const double *, const double *, const double *,
-                                          double *, const CGScalars *, int, int, int, DevStatus *,
-                                          cudaStream_t);
+                                          double *, double *, const CGScalars *, int, int, int,
+                                          DevStatus *, cudaStream_t);
 template int launch_schwarz_solve<float>(const SubDesc *, const BandLayout *, int, int, int, int,
                                          int, const float *, const float *, const double *,
-                                         float *, const CGScalars *, int, int, int, DevStatus *,
-                                         cudaStream_t);
+                                         float *, float *, const CGScalars *, int, int, int,
+                                         DevStatus *, cudaStream_t);
 
 }  // namespace geneo

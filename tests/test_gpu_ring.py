@@ -2,16 +2,17 @@
 
 The local solves and the GenEO eigensolver's band solves normally keep a
 subdomain's whole local vector in shared memory, which holds about 27,900
-FP64 (57,000 FP32) unknowns.  Beyond that the same one-CTA look-ahead sweep
-streams the vector through a ring of max(w + 2, 3) tile rows: the forward
-sweep writes y to global memory as it goes and the backward sweep reads it
-back (Sec. 3.1, eqn:onelevelAS; the shift-invert solves of Sec. 3.3.2).
+FP64 (57,000 FP32) unknowns.  Beyond that the same look-ahead sweep streams
+the vector through a ring of max(w + 2, 3) tile rows in every CTA: the
+forward sweep writes y to a scratch vector as it goes and the backward sweep
+reads it back (Sec. 3.1, eqn:onelevelAS; the shift-invert solves of
+Sec. 3.3.2).
 
-1. The ring form does the arithmetic of the one-CTA look-ahead launch in the
-   same order, so with both pinned (GENEO_SCHWARZ_STAGED=2 against
-   GENEO_SCHWARZ_CLUSTER=1, ROWS=0, STAGED=0) the preconditioner application
-   and the whole solve are bit-identical, FP64 and FP32, on narrow and wide
-   bands.
+1. The ring form does the arithmetic of the look-ahead launch with the same
+   cluster size in the same order, so with both pinned (GENEO_SCHWARZ_STAGED=2
+   against ROWS=0, STAGED=0, and GENEO_SCHWARZ_CLUSTER = 1, 2, 4 or 8) the
+   preconditioner application and the whole solve are bit-identical, FP64
+   and FP32, on narrow and wide bands.
 2. The eigensolver's ring (GENEO_BAND_SOLVE_RING=1) gives bit-identical
    eigenvalues, coarse spaces and solutions.
 3. The d-large Darcy block (36x64x24 cells, two subdomains of 30,525 interior
@@ -66,16 +67,19 @@ def _run_as(pkg, monkeypatch, p, prec, pins, r):
 
 @pytest.mark.parametrize("name", ["small", "c1", "wide"])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_ring_local_solves_bit_identical_to_one_cta_lookahead(pkg, monkeypatch, name, prec):
+@pytest.mark.parametrize("cluster", [1, 2, 4, 8])
+def test_ring_local_solves_bit_identical_to_lookahead(pkg, monkeypatch, name, prec, cluster):
     p = _problem(name)
     n = 3 * (p["nx"] + 1) * (p["ny"] + 1) * (p["nz"] + 1)
     r = np.random.default_rng(9).normal(size=n)
     r[p["dirichlet_dofs"]] = 0.0
-    la = {"GENEO_SCHWARZ_CLUSTER": "1", "GENEO_SCHWARZ_ROWS": "0", "GENEO_SCHWARZ_STAGED": "0"}
+    C = str(cluster)
+    la = {"GENEO_SCHWARZ_CLUSTER": C, "GENEO_SCHWARZ_ROWS": "0", "GENEO_SCHWARZ_STAGED": "0"}
+    ring = {"GENEO_SCHWARZ_CLUSTER": C, "GENEO_SCHWARZ_STAGED": "2"}
     z0, u0, st0 = _run_as(pkg, monkeypatch, p, prec, la, r)
-    z1, u1, st1 = _run_as(pkg, monkeypatch, p, prec, {"GENEO_SCHWARZ_STAGED": "2"}, r)
-    assert (st0["schwarz_cluster"], st0["schwarz_rows"], st0["schwarz_staged"]) == (1, 0, 0)
-    assert (st1["schwarz_cluster"], st1["schwarz_rows"], st1["schwarz_staged"]) == (1, 0, 2)
+    z1, u1, st1 = _run_as(pkg, monkeypatch, p, prec, ring, r)
+    assert (st0["schwarz_cluster"], st0["schwarz_rows"], st0["schwarz_staged"]) == (cluster, 0, 0)
+    assert (st1["schwarz_cluster"], st1["schwarz_rows"], st1["schwarz_staged"]) == (cluster, 0, 2)
     assert np.array_equal(z0, z1)
     assert np.array_equal(u0, u1)
     assert st0["iterations"] == st1["iterations"]
@@ -114,20 +118,27 @@ def test_large_subdomains_need_the_ring(pkg):
     assert plan[:, 14].min() > FP64_WHOLE_VECTOR      # Neumann unknowns (eigensolver)
 
 
-@pytest.mark.parametrize("prec,pin", [(0, None), (1, None), (1, "2")])
-def test_large_subdomains_against_oracle(pkg, monkeypatch, prec, pin):
+@pytest.mark.parametrize("prec,pins", [
+    (0, {}),                                                          # the tuner's ring shape
+    (0, {"GENEO_SCHWARZ_CLUSTER": "1"}),                              # one CTA per subdomain
+    (1, {}),                                                          # FP32 vectors fit whole
+    (1, {"GENEO_SCHWARZ_STAGED": "2", "GENEO_SCHWARZ_CLUSTER": "8"}),
+])
+def test_large_subdomains_against_oracle(pkg, monkeypatch, prec, pins):
     with open(os.path.join(GOLDEN, "d-large_oracle.json")) as f:
         gold = json.load(f)
     p = darcy_config("d-large")
-    if pin:
-        monkeypatch.setenv("GENEO_SCHWARZ_STAGED", pin)
+    for k, v in pins.items():
+        monkeypatch.setenv(k, v)
     s = pkg.GeneoSolver()
     s.assemble(p)
     s.setup(p, prec)
     coarse = s.coarse_info()
     u, st = s.solve(tol=1e-8, max_it=3000)
-    if prec == 0 or pin:
+    if prec == 0 or pins:
         assert st["schwarz_staged"] == 2
+    if "GENEO_SCHWARZ_CLUSTER" in pins:
+        assert st["schwarz_cluster"] == int(pins["GENEO_SCHWARZ_CLUSTER"])
     assert st["rel_res_true"] <= 2e-8
     check_against_golden(u, st, gold, coarse=coarse)
     s.close()
