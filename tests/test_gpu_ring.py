@@ -142,3 +142,19 @@ def test_large_subdomains_against_oracle(pkg, monkeypatch, prec, pins):
     assert st["rel_res_true"] <= 2e-8
     check_against_golden(u, st, gold, coarse=coarse)
     s.close()
+
+
+def test_batch_refuses_subdomains_larger_than_shared_memory(pkg):
+    """The batched persistent launch holds every item's whole local vector, so
+    a batch with a d-large context is refused; the context itself stays usable."""
+    p = darcy_config("d-large")
+    s = pkg.GeneoSolver()
+    s.assemble(p)
+    s.setup(p, pkg.GENEO_FP64, pkg.GENEO_AS, pkg.GENEO_COARSE_NONE)
+    with pytest.raises(pkg.GeneoError) as e:
+        pkg.GeneoBatch([s])
+    assert e.value.status == 1
+    assert "no batched local-solve shape fits" in str(e.value)
+    u, st = s.solve(tol=1e-8, max_it=3000)
+    assert st["schwarz_staged"] == 2 and st["rel_res_true"] <= 2e-8
+    s.close()
