@@ -20,6 +20,21 @@
  *  - Every function returns an int status (GENEO_OK = 0); nothing throws
  *    across the ABI.  geneo_status_string() names a status.
  *  - A context is not thread-safe; use one context per host thread/stream.
+ *  - Environment variables, read at geneo_setup (and geneo_batch_create for the
+ *    Schwarz pins), fix choices the set-up otherwise makes itself; a value
+ *    outside the listed set is ignored:
+ *      GENEO_SCHWARZ_CLUSTER  CTAs per subdomain of the local solves: 1, 2, 4, 8
+ *      GENEO_SCHWARZ_ROWS     tile rows per step: 1, 2, 4, or 0 (look-ahead)
+ *      GENEO_SCHWARZ_STAGED   0 tiles from global memory, 1 staged by bulk
+ *                             copies, 2 ring form (local vector streamed)
+ *      GENEO_BAND_SOLVE_RING  1: the eigensolver's band solves use the ring form
+ *      GENEO_LANCZOS_STEPS    block-Lanczos steps per restart: 10, 12, 16
+ *      GENEO_EIG_TOL          Ritz residual bound / theta: 1e-12 .. 1e-4
+ *      GENEO_TENSOR_CORES     0: FP32 factor updates on the FMA units
+ *    A fixed launch shape gives bit-reproducible results.  Unpinned, the
+ *    set-up times the shapes and keeps the fastest (cached per process); two
+ *    processes may pick different shapes when they time alike, and different
+ *    shapes sum partial products in different orders.
  */
 #ifndef GENEO_H
 #define GENEO_H
