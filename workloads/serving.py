@@ -12,7 +12,7 @@ pressure), which the server can answer from resident factors.  With
 block (one unknown per node) with the layered permeability of
 `workloads.darcy`, the same log-uniform unknown count, SPE10-like 60:220:85
 proportions and an in-plane decomposition over the full height (about 10 x 12
-cells per subdomain, which keeps a subdomain's local vector in shared memory);
+cells per subdomain: narrow bands, so cheap band factorisations);
 with `darcy_grid="spe10"` every new Darcy structure is instead the full
 60 x 220 x 85-cell SPE10 grid (1,159,366 unknowns, 6 x 18 subdomains) with its
 own seeded permeability.  Arrival times are a Poisson process.
